@@ -1,0 +1,223 @@
+"""Seeded synthetic problem generators shared by the tests, the benchmark and
+the oracle checks.
+
+This module only draws the problem: grid, groups, fluid and opacity fields,
+emissivities and the initial intensity.  It holds none of the solver's own
+arithmetic (no quadrature, harmonics, Lorentz transformation, scattering
+kernel or transfer), so both sides of every parity test can take their inputs
+from it.
+
+Recipes (numpy ``PCG64``, seed ``20150717 + index`` unless given):
+
+* ``relax_box``     (16^3, 1 group, L=3, 8x16 ordinates, at rest): extinction
+  5 across the unit box times a mean-preserving log-normal factor
+  ``exp(0.2 xi - 0.02)`` per node; absorption = scattering = chi/2
+  (isotropic scattering, albedo 1/2); thermal source B = 1; vacuum faces;
+  ``c dt`` = half a node spacing.
+* ``jet``           (64^3, 16 log groups over 1e-3..1e1 m_e c^2, L=7, 16x32):
+  a cylindrical jet along z through the box centre, Gamma = 1 + 9 s(r) with
+  s = 1 for r <= 0.2 falling smoothly to 0 at r = 0.3; Thomson scattering
+  with a uniform n_e sigma_T giving radial optical depth ``tau_r`` from the
+  axis to r = 0.5; comoving emissivity n_e eps^-1; vacuum faces;
+  ``c dt`` = half a node spacing.
+* ``compton_shell`` (96^3, 32 log groups over 1e-4..1e2, L=7, 16x32): a
+  Gaussian random electron-temperature field (FFT-filtered white noise,
+  correlation length 0.1 box) mapped to [0.01, 0.3] m_e c^2; a radial shell
+  flow 0.25 <= r <= 0.40 with Gamma rising 2 -> 5 across it and blending to
+  1 over 0.05 outside; n_e sigma_T = 5 per box length; grey absorption
+  n_e (1/0.95 - 1) (albedo 0.95 in the Thomson limit); thermal emission
+  alpha B_g(theta_e) with B_g the group average of x^3/(exp(x/theta)-1).
+
+Every recipe accepts reduced ``n``, ``G``, ``L`` for oracle-sized cases; the
+ordinate set follows ``nmu = 2(L+1)``, ``nphi = 4(L+1)``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 20150717
+
+
+@dataclass
+class ProblemSpec:
+    name: str
+    grid: tuple
+    box: tuple
+    L: int
+    nmu: int
+    nphi: int
+    edges: np.ndarray
+    alpha0: np.ndarray      # [Nc, G]
+    ne: np.ndarray          # [Nc]
+    u: np.ndarray           # [Nc, 3]
+    emis0: np.ndarray       # [Nc, G]
+    scattering: str         # "iso" | "thomson" | "kn"
+    kappa: float            # 1/(c dt) for the time steps
+    steps: int
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def Nc(self):
+        return int(np.prod(self.grid))
+
+    @property
+    def G(self):
+        return len(self.edges) - 1
+
+    @property
+    def N(self):
+        return self.nmu * self.nphi
+
+    @property
+    def NLM(self):
+        return (self.L + 1) ** 2
+
+    @property
+    def updates_per_step(self):
+        return self.Nc * self.N * self.G
+
+
+def _rng(index, seed):
+    return np.random.Generator(np.random.PCG64(BASE_SEED + index if seed is None else seed))
+
+
+def _coords(n, box=1.0):
+    h = box / (n - 1)
+    x = np.arange(n) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")  # c = (iz*ny + iy)*nx + ix
+    return X.ravel(), Y.ravel(), Z.ravel(), h
+
+
+def _smoothstep(t):
+    t = np.clip(t, 0.0, 1.0)
+    return t * t * (3.0 - 2.0 * t)
+
+
+def ordinate_counts(L):
+    return 2 * (L + 1), 4 * (L + 1)
+
+
+def relax_box(n=16, L=3, seed=None, index=0):
+    rng = _rng(index, seed)
+    Nc = n ** 3
+    chi = 5.0 * np.exp(0.2 * rng.standard_normal(Nc) - 0.02)
+    alpha0 = (chi / 2.0)[:, None]
+    ne = chi / 2.0
+    nmu, nphi = ordinate_counts(L)
+    h = 1.0 / (n - 1)
+    return ProblemSpec("relax_box", (n, n, n), (1.0, 1.0, 1.0), L, nmu, nphi,
+                       np.array([0.5, 1.5]), alpha0, ne, np.zeros((Nc, 3)),
+                       alpha0 * 1.0, "iso", kappa=1.0 / (0.5 * h), steps=10,
+                       extra={"static_tol": 1e-6})
+
+
+def jet_lorentz_factor(r, gmax=10.0, r_core=0.2, r_edge=0.3):
+    s = 1.0 - _smoothstep((r - r_core) / (r_edge - r_core))
+    return 1.0 + (gmax - 1.0) * s
+
+
+def jet(n=64, G=16, L=7, tau_r=10.0, gmax=10.0, seed=None, index=1, emin=1e-3, emax=1e1):
+    _rng(index, seed)  # the jet problem is deterministic; keep the stream reserved
+    X, Y, Z, h = _coords(n)
+    r = np.hypot(X - 0.5, Y - 0.5)
+    gam = jet_lorentz_factor(r, gmax)
+    u = np.zeros((n ** 3, 3))
+    u[:, 2] = np.sqrt(np.maximum(gam * gam - 1.0, 0.0))
+    edges = np.geomspace(emin, emax, G + 1)
+    centre = np.sqrt(edges[:-1] * edges[1:])
+    ne = np.full(n ** 3, tau_r / 0.5)
+    alpha0 = np.zeros((n ** 3, G))
+    emis0 = ne[:, None] * centre[None, :] ** -1.0
+    nmu, nphi = ordinate_counts(L)
+    return ProblemSpec("jet", (n, n, n), (1.0, 1.0, 1.0), L, nmu, nphi, edges, alpha0, ne, u,
+                       emis0, "thomson", kappa=1.0 / (0.5 * h), steps=100,
+                       extra={"tau_r": tau_r, "gmax": gmax})
+
+
+def gaussian_random_field(n, corr, rng):
+    w = rng.standard_normal((n, n, n))
+    k = np.fft.fftfreq(n, d=1.0 / (n - 1))
+    KZ, KY, KX = np.meshgrid(k, k, k, indexing="ij")
+    filt = np.exp(-0.5 * (2 * np.pi * corr) ** 2 * (KX ** 2 + KY ** 2 + KZ ** 2))
+    f = np.real(np.fft.ifftn(np.fft.fftn(w) * filt))
+    return f.ravel()
+
+
+def planck_group(edges, theta, nsub=8):
+    """Group average of x^3/(exp(x/theta) - 1) over each group (code units)."""
+    G = len(edges) - 1
+    xg, wg = np.polynomial.legendre.leggauss(nsub)
+    out = np.zeros((theta.size, G))
+    for g in range(G):
+        a, b = np.log(edges[g]), np.log(edges[g + 1])
+        s = 0.5 * (b - a) * xg + 0.5 * (a + b)
+        x = np.exp(s)
+        wq = 0.5 * (b - a) * wg * x
+        arg = x[None, :] / theta[:, None]
+        val = np.where(arg < 700.0, x[None, :] ** 3 / np.expm1(np.minimum(arg, 700.0)), 0.0)
+        out[:, g] = (val * wq[None, :]).sum(axis=1) / (edges[g + 1] - edges[g])
+    return out
+
+
+def compton_shell(n=96, G=32, L=7, seed=None, index=2, emin=1e-4, emax=1e2, albedo=0.95):
+    rng = _rng(index, seed)
+    X, Y, Z, h = _coords(n)
+    f = gaussian_random_field(n, 0.1, rng)
+    theta = 0.01 + (f - f.min()) / (f.max() - f.min()) * (0.3 - 0.01)
+    dx, dy, dz = X - 0.5, Y - 0.5, Z - 0.5
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    t = np.clip((r - 0.25) / 0.15, 0.0, 1.0)
+    gam_in = 2.0 + 3.0 * t
+    inside = (r >= 0.25) & (r <= 0.40)
+    blend = np.where(r < 0.25, 1.0 - _smoothstep((0.25 - r) / 0.05), 1.0 - _smoothstep((r - 0.40) / 0.05))
+    gam = np.where(inside, gam_in, 1.0 + (np.where(r < 0.25, 2.0, 5.0) - 1.0) * blend)
+    um = np.sqrt(np.maximum(gam * gam - 1.0, 0.0))
+    rs = np.maximum(r, 1e-30)
+    u = np.stack([um * dx / rs, um * dy / rs, um * dz / rs], axis=1)
+    u[r == 0.0] = 0.0
+    edges = np.geomspace(emin, emax, G + 1)
+    ne = np.full(n ** 3, 5.0)
+    alpha0 = np.repeat((ne * (1.0 / albedo - 1.0))[:, None], G, axis=1)
+    emis0 = alpha0 * planck_group(edges, theta)
+    nmu, nphi = ordinate_counts(L)
+    return ProblemSpec("compton_shell", (n, n, n), (1.0, 1.0, 1.0), L, nmu, nphi, edges, alpha0, ne,
+                       u, emis0, "kn", kappa=1.0 / (0.5 * h), steps=200, extra={"theta_e": theta})
+
+
+def random_state(spec: ProblemSpec, seed=12345, scale=1.0, layout="cgk"):
+    """A positive seeded intensity for single-step parity checks, [c][g][k]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    I = scale * (0.5 + rng.random((spec.Nc, spec.G, spec.N)))
+    return I
+
+
+def ragged_mixed(grid=(11, 9, 7), G=5, L=3, gmax=3.0, seed=None, index=7, scattering="thomson"):
+    """A small non-cubic problem with flow, absorption, emission and
+    scattering, for element-by-element parity on sizes that leave ragged
+    tiles.  Velocity: a tilted jet plus a weak random component."""
+    rng = _rng(index, seed)
+    nx, ny, nz = grid
+    hx, hy, hz = 1.0 / (nx - 1), 1.2 / (ny - 1), 0.9 / (nz - 1)
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    X = (ix * hx).transpose(2, 1, 0).ravel()
+    Y = (iy * hy).transpose(2, 1, 0).ravel()
+    Z = (iz * hz).transpose(2, 1, 0).ravel()
+    Nc = nx * ny * nz
+    axis = np.array([0.3, -0.2, 1.0])
+    axis /= np.linalg.norm(axis)
+    p = np.stack([X - 0.5, Y - 0.6, Z - 0.45], axis=1)
+    r = np.linalg.norm(p - (p @ axis)[:, None] * axis[None, :], axis=1)
+    gam = jet_lorentz_factor(r, gmax, 0.15, 0.3)
+    u = np.sqrt(np.maximum(gam ** 2 - 1.0, 0.0))[:, None] * axis[None, :]
+    u += 0.05 * rng.standard_normal((Nc, 3))
+    u[rng.random(Nc) < 0.3] = 0.0  # a share of nodes at rest
+    edges = np.geomspace(1e-2, 3.0, G + 1)
+    centre = np.sqrt(edges[:-1] * edges[1:])
+    ne = 2.0 * np.exp(0.3 * rng.standard_normal(Nc))
+    alpha0 = 0.5 * np.exp(0.3 * rng.standard_normal((Nc, G)))
+    emis0 = (1.0 + rng.random((Nc, 1))) * centre[None, :] ** -0.5
+    nmu, nphi = ordinate_counts(L)
+    return ProblemSpec("ragged_mixed", grid, (1.0, 1.2, 0.9), L, nmu, nphi, edges, alpha0, ne, u,
+                       emis0, scattering, kappa=1.0 / (0.5 * hx), steps=3)
