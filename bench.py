@@ -1,0 +1,296 @@
+"""Benchmark: cell-ordinate-group updates per second of the SHDOM time step.
+
+Workload (one GPU): the relativistic jet problem, 64^3 nodes, 16 log-spaced
+groups over 1e-3..1e1 m_e c^2, L = 7 (64 harmonics), 16 x 32 ordinates,
+Thomson scattering with radial optical depth 10, bulk Lorentz factor 10 in the
+jet core; one source iteration per time step (project -> source -> sh2lab ->
+sweep -> sums), c dt = half a node spacing.  Synthetic seeded inputs; the
+state (8.6 GB in FP32) is far larger than L2, so no flush is needed between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|mixed|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+
+Under torchrun each rank runs its own replica of the problem (the problems
+are independent: weak scaling, no collective in the data path); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-ordinate-group updates/s"
+UNIT = "updates/s"
+WORKLOAD = "relativistic jet 64^3, 16 groups (1e-3..1e1 m_e c^2), L=7, 16x32 ordinates, Thomson tau_r=10, Gamma<=10"
+# algorithmic bytes per update of the sweep kernel (FP32): read I^n, eta_lab,
+# chi_lab, write I^{n+1}
+SWEEP_BYTES_PER_UPDATE = {"fp32": 16, "mixed": 16, "fp64": 32}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.rows.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_sample_spec():
+    """Bounded CPU sample: the same recipe (groups, harmonics, ordinates, flow,
+    opacities) on a 20^3 grid."""
+    from paper_1507_05141_gb300 import inputs
+    return inputs.jet(n=20)
+
+
+def run_oracle_steps(spec, steps):
+    """Time `steps` oracle steps of spec on the host cores; returns (updates/s, seconds)."""
+    from oracle import oracle as O
+    from paper_1507_05141_gb300 import inputs
+    K, so = O.thomson_table(spec.G, spec.L)
+    P = O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
+                        alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=K, sigma_out=so,
+                        kappa=spec.kappa, box=spec.box)
+    I = inputs.random_state(spec, seed=1)
+    t0 = time.perf_counter()
+    P.step(I, steps)
+    dt = time.perf_counter() - t0
+    return spec.updates_per_step * steps / dt, dt
+
+
+def cpu_baseline(steps=1):
+    spec = cpu_sample_spec()
+    v, dt = run_oracle_steps(spec, steps)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle step(s) of the jet recipe on a 20^3 grid "
+                      f"({spec.updates_per_step:.3g} updates/step, {dt:.1f} s)"}
+
+
+def bench_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    spec = cpu_sample_spec()
+    run_oracle_steps(spec, max(0, min(args.warmup, 1)))
+    times = []
+    for _ in range(args.steps):
+        _, dt = run_oracle_steps(spec, 1)
+        times.append(dt)
+    tot = sum(times)
+    v = spec.updates_per_step * args.steps / tot
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (CPU sample: 20^3 grid, same recipe)", "grid": spec.grid,
+                       "groups": spec.G, "L": spec.L, "ordinates": spec.N},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "FP64 oracle step of the jet recipe on a 20^3 grid, per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1507_05141_gb300 import inputs, native
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    spec = inputs.jet()
+    prec = args.precision
+    solver = native.Solver.from_spec(spec, device=local, precision=prec)
+    solver.zero_state()
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up (also fills the state with a physical solution)
+    solver.step(args.warmup, sptr)
+    torch.cuda.synchronize(dev)
+
+    # device-resident timed region
+    solver.set_timing(True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        solver.step(args.steps, sptr)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, nrec = solver.timing()
+    solver.set_timing(False)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    upd = spec.updates_per_step
+    value = upd * args.steps * ws / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: per step the fields
+    # are uploaded from pinned host memory, one step runs, and the FP64 sums
+    # are read back.
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+        return t, t.numpy()
+    hold = [pinned(x) for x in (spec.alpha0, spec.ne, spec.u, spec.emis0)]
+    arrs = [h[1] for h in hold]
+    h2d = sum(a.nbytes for a in arrs)
+    d2h = 3 * 8
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_fields(*arrs)
+        solver.step(1, sptr)
+        solver.sums()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = upd * e2e_steps * ws / e2e_s
+
+    peak, peak_kind = _peaks()
+    sweep_ms = stage_ms["sweep"] / max(1, nrec)
+    sweep_bytes = upd * SWEEP_BYTES_PER_UPDATE[prec]
+    achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"sweep_traffic_{prec}.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                traffic = json.load(f).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    if rank == 0:
+        cpu = cpu_baseline() if (ws == 1 and not args.no_cpu) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "mixed": "f32", "fp64": "f64"}[prec], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(spec.grid), "groups": spec.G, "L": spec.L,
+                       "ordinates": spec.N, "precision": prec, "updates_per_step": upd,
+                       "l2": "no flush: the 8.6 GB state is far larger than L2",
+                       "parallelism": f"replicas x{ws}"},
+            "stage_ms": {k: v / max(1, nrec) for k, v in stage_ms.items()},
+            "roofline": {"kernel": "k_sweep", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "algorithmic_bytes": f"{SWEEP_BYTES_PER_UPDATE[prec]} B/update x {upd} updates"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": 6 * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    solver.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

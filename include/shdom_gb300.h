@@ -1,0 +1,194 @@
+/*
+ * shdom_gb300.h -- C ABI of the GB300 (sm_103a) library for one source
+ * iteration per time step of the time-dependent, multi-group, mixed-frame
+ * SHDOM method (Tominaga, Shibata & Blinnikov, arXiv:1507.05141).
+ *
+ * One step (Sec. 2, Sec. 2.2 frame order) runs, on the GPU:
+ *   a1  project   laboratory intensity -> comoving ordinates/groups (Lorentz,
+ *                 eq:lorentzfreq, eq:lorentzray, I/nu^3 invariant) -> real
+ *                 spherical harmonics I_lm (Sec. 2.3); laboratory moments J,
+ *                 H_i, K_ij (the Eddington tensor f_ij = K_ij / J);
+ *   a2  source    S_lm = n_e/chi0 sum_g' K_l[g][g'] I_lm(g') + T_lm
+ *                 (Sec. 2.3: Thomson / Klein-Nishina, eq:comptoncross);
+ *   a3  sh2lab    S_lm -> comoving ordinates -> laboratory eta, chi
+ *                 (eta/nu^2, chi nu invariant; Sec. 2.2);
+ *   a4  sweep     short-characteristic transfer along every laboratory
+ *                 ordinate and group with the time term chi~ = chi + 1/(c dt),
+ *                 eta~ = eta + I^n/(c dt)  (Sec. 2 eq:shdom, Sec. 2.1 eq:time);
+ *   a5  sums      FP64 energy, photon number and relative source change.
+ *
+ * Conventions (every entry point):
+ *   - Return SHD_OK (0) on success, a negative SHD_ERR_* code otherwise; the
+ *     message of the last failure on the calling thread is shd_last_error().
+ *   - Host pointers are caller-owned; the library copies what it needs before
+ *     returning.  Device state is library-owned and freed by shd_destroy().
+ *   - Node index c = (iz*ny + iy)*nx + ix; node spacing h_a = l_a/(n_a - 1)
+ *     (nodes on the faces).
+ *   - Ordinate index k = a*n_phi + b: mu_a ascending Gauss-Legendre, phi_b =
+ *     2 pi b / n_phi from +x towards +y; weights sum to 4 pi.
+ *   - Spherical-harmonic index p = l*l + l + m, real orthonormal, no
+ *     Condon-Shortley phase, all l <= L.
+ *   - Host intensity arrays are [c][g][k] (double); SH arrays [c][g][p].
+ *   - Energies are in units of m_e c^2; group g spans [edges[g], edges[g+1]],
+ *     its specific intensity is taken at the centre sqrt(e_g e_{g+1}).
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - Setters validate their arguments before touching the GPU.  A setter
+ *     that changes sizes (grid, angles, groups) discards the fields, state
+ *     and scattering table that depended on them.
+ */
+#ifndef SHDOM_GB300_H
+#define SHDOM_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct shd_ctx shd_ctx;
+
+enum shd_status {
+    SHD_OK = 0,
+    SHD_ERR_ARG = -1,     /* invalid argument or call order            */
+    SHD_ERR_OOM = -2,     /* device or host allocation failed          */
+    SHD_ERR_CUDA = -3,    /* a CUDA runtime call or kernel failed      */
+    SHD_ERR_STATE = -4,   /* context not fully configured              */
+    SHD_ERR_NAN = -5,     /* non-finite or out-of-range input rejected */
+    SHD_ERR_TIMEOUT = -6  /* iteration limit reached without converging */
+};
+
+enum shd_precision {
+    SHD_FP64 = 0,  /* every stage in FP64 (parity path)                       */
+    SHD_FP32 = 1,  /* every stage in FP32 ("plain FP32")                      */
+    SHD_MIXED = 2  /* FP32 transfer; FP64 where stability needs it             */
+};
+
+enum shd_scattering {
+    SHD_SCAT_ISO = 1,      /* isotropic: K_0 = 1, sigma_out = 1                 */
+    SHD_SCAT_THOMSON = 2,  /* Thomson: K_0 = 1, K_2 = 1/10, sigma_out = 1       */
+    SHD_SCAT_KN = 3,       /* cold-electron Klein-Nishina multigroup kernel,
+                              built on the GPU from the group edges            */
+    SHD_SCAT_TABLE = 4     /* caller-supplied K[l][g][g'] and sigma_out[g']     */
+};
+
+enum shd_boundary {
+    SHD_BC_VACUUM = 0,  /* inflow intensity 0                                  */
+    SHD_BC_ISO = 1,     /* inflow intensity data[g], same for every ordinate   */
+    SHD_BC_FULL = 2     /* inflow intensity data[c][g][k] (only inflow-face
+                           nodes are read)                                     */
+};
+
+/* Create a context on CUDA device `device` computing in `precision`
+ * (enum shd_precision).  *out receives an opaque handle. */
+int shd_create(shd_ctx **out, int device, int precision);
+
+/* Free every device and host resource of ctx (NULL is ignored). */
+void shd_destroy(shd_ctx *ctx);
+
+/* Message of the last failure on this thread ("" if none).  The pointer
+ * stays valid until the next call on this thread. */
+const char *shd_last_error(void);
+
+/* Grid of nx*ny*nz nodes spanning [0,lx]x[0,ly]x[0,lz] (Sec. 2: 3-D
+ * Cartesian mesh; every n >= 2, every l > 0). */
+int shd_set_grid(shd_ctx *ctx, int nx, int ny, int nz, double lx, double ly, double lz);
+
+/* Angular order L (NLM = (L+1)^2 harmonics, Sec. 2.3) and the ordinate mesh
+ * n_mu x n_phi (Sec. 2.2 (theta, phi) mesh).  Requires n_mu >= L+1 and
+ * n_phi >= 2L+1 (discrete orthogonality of the harmonics), L <= 15,
+ * n_mu*n_phi <= 4096. */
+int shd_set_angles(shd_ctx *ctx, int L, int n_mu, int n_phi);
+
+/* G groups with G+1 strictly ascending positive edges (units m_e c^2;
+ * Sec. 2.3 multi-group treatment).  1 <= G <= 256. */
+int shd_set_groups(shd_ctx *ctx, int G, const double *edges);
+
+/* Comoving-frame fields (Sec. 2, Sec. 2.2):
+ *   alpha0 [Nc][G]  absorption coefficient (>= 0)
+ *   ne     [Nc]     scattering coefficient scale n_e sigma_T (>= 0)
+ *   u      [Nc][3]  spatial 4-velocity Gamma v/c (finite)
+ *   emis0  [Nc][G]  isotropic emissivity eta0 (>= 0)
+ * Requires grid and groups.  Non-finite or negative values -> SHD_ERR_NAN. */
+int shd_set_fields(shd_ctx *ctx, const double *alpha0, const double *ne, const double *u,
+                   const double *emis0);
+
+/* Scattering kernel (Sec. 2.3): kind from enum shd_scattering.  For
+ * SHD_SCAT_TABLE, K is [L+1][G][G] (row = final group) and sigma_out [G];
+ * both are ignored (may be NULL) for the built-in kinds.  The extinction is
+ * chi0(c,g) = alpha0 + n_e sigma_out(g).  Requires angles and groups. */
+int shd_set_scattering(shd_ctx *ctx, int kind, const double *K, const double *sigma_out);
+
+/* Copy the active scattering table out: K [L+1][G][G], sigma_out [G]. */
+int shd_get_scattering(shd_ctx *ctx, double *K, double *sigma_out);
+
+/* Inflow boundary intensity (enum shd_boundary); data as described there,
+ * NULL for SHD_BC_VACUUM. */
+int shd_set_boundary(shd_ctx *ctx, int mode, const double *data);
+
+/* kappa = 1/(c dt) of the backward-Euler time term (Sec. 2.1); 0 gives the
+ * static equation.  kappa >= 0. */
+int shd_set_time(shd_ctx *ctx, double kappa);
+
+/* Set / read the laboratory intensity state I [c][g][k] (host, double).
+ * shd_get_state synchronises with the library's stream. */
+int shd_set_state(shd_ctx *ctx, const double *I);
+int shd_get_state(shd_ctx *ctx, double *I);
+
+/* Run `nsteps` time steps, one source iteration each (stages a1..a5), on
+ * `cuda_stream` (a cudaStream_t; NULL = the context's own stream).  Returns
+ * once the work is enqueued.  The state must have been set (or zeroed by
+ * shd_zero_state). */
+int shd_step(shd_ctx *ctx, int nsteps, void *cuda_stream);
+
+/* Zero the intensity state on the device. */
+int shd_zero_state(shd_ctx *ctx);
+
+/* Lambda iteration of the static problem (kappa treated as 0) from the
+ * current state until the relative L2 change of S_lm is <= rel_tol
+ * (Sec. 2: iterate source and transfer).  Writes the iteration count and
+ * final residual; returns SHD_ERR_TIMEOUT if max_iter is reached first. */
+int shd_solve_static(shd_ctx *ctx, double rel_tol, int max_iter, int *iters_out, double *resid_out);
+
+/* Laboratory moments of the current state (stage a1 is run on it):
+ *   J [c][g], H [c][g][3], K [c][g][6] (xx, yy, zz, xy, xz, yz) -- all
+ * divided by 4 pi so that J is the mean intensity -- and the comoving SH
+ * projection Ish [c][g][p].  Any output may be NULL.  Synchronous. */
+int shd_get_moments(shd_ctx *ctx, double *J, double *H, double *K, double *Ish);
+
+/* FP64 diagnostics of the last step (stage a5) of the state it started
+ * from: energy = sum 4 pi J de_g, photons = sum 4 pi J de_g / ebar_g, resid =
+ * ||S_new - S_old|| / ||S_new|| over all (c, g, p).  Synchronous. */
+int shd_get_sums(shd_ctx *ctx, double *energy, double *photons, double *resid);
+
+/* ---- single stages on caller-supplied host data (tests, composition) ----
+ * Each runs one stage of the step on the fields and tables already set and
+ * is synchronous.  Layouts as above: DO arrays [c][g][k], SH [c][g][p]. */
+int shd_stage_project(shd_ctx *ctx, const double *I, double *Ish, double *J, double *H, double *K);
+int shd_stage_source(shd_ctx *ctx, const double *Ish, double *Ssh);
+int shd_stage_sh2lab(shd_ctx *ctx, const double *Ssh, double *eta_lab, double *chi_lab);
+int shd_stage_sweep(shd_ctx *ctx, const double *I_old, const double *eta_lab, const double *chi_lab,
+                    double *I_new);
+
+/* Device-pointer forms for callers that own device memory (e.g. PyTorch).
+ * dev_I points to Nc*G*N doubles in the [c][g][k] layout on ctx's device. */
+int shd_set_state_dev(shd_ctx *ctx, const double *dev_I, void *cuda_stream);
+int shd_get_state_dev(shd_ctx *ctx, double *dev_I, void *cuda_stream);
+
+/* Sizes of the configured problem (any output may be NULL). */
+int shd_get_sizes(shd_ctx *ctx, long long *n_nodes, int *n_ord, int *n_groups, int *n_lm);
+
+/* Device bytes held by the context. */
+long long shd_device_bytes(shd_ctx *ctx);
+
+/* Per-stage timing of shd_step: with on != 0, every later step records CUDA
+ * events around its stages on the stream it runs on (no host
+ * synchronisation; at most 2048 steps per enable).  shd_get_timing waits for
+ * the last recorded step and returns the summed milliseconds of the stages
+ * {project, source, sums, sh2lab, sweep} in stage_ms[5] and the number of
+ * steps recorded. */
+int shd_set_timing(shd_ctx *ctx, int on);
+int shd_get_timing(shd_ctx *ctx, double *stage_ms, long long *steps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHDOM_GB300_H */

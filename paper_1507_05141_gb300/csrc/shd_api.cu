@@ -1,0 +1,928 @@
+// Host side of the C ABI declared in include/shdom_gb300.h: argument
+// validation, set-up tables (ordinate mesh, real harmonics, sweep geometry),
+// device allocation, and the order of the stages of one step (Sec. 2.2:
+// lab DO -> comoving -> SH; source in SH; SH -> comoving DO -> lab; ray
+// tracing).  All arithmetic of a step runs in the kernels of shd_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "shd_internal.cuh"
+
+using namespace shd;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? SHD_ERR_OOM : SHD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                              \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool finite_all(const double *a, size_t n, bool nonneg)
+{
+    for (size_t i = 0; i < n; ++i) {
+        if (!std::isfinite(a[i])) return false;
+        if (nonneg && a[i] < 0.0) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// set-up tables (FP64, host)
+// ---------------------------------------------------------------------------
+
+// Gauss-Legendre nodes ascending on [-1, 1]: Newton iteration on P_n from the
+// Chebyshev-like guess, weights 2 / ((1 - x^2) P_n'(x)^2).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (n - i - 0.25) / (n + 0.5));  // ascending guess
+        double pn = 0, dpn = 0;
+        for (int it = 0; it < 100; ++it) {
+            double pm = 1.0, pc = z;  // P_0, P_1
+            for (int j = 1; j < n; ++j) {
+                double pnext = ((2 * j + 1) * z * pc - j * pm) / (j + 1);
+                pm = pc;
+                pc = pnext;
+            }
+            if (n == 0) pc = 1.0;
+            pn = pc;                                   // P_n
+            dpn = n * (pm - z * pc) / (1.0 - z * z);  // P_n' from P_{n-1}
+            if (n == 1) dpn = 1.0;
+            double dz = pn / dpn;
+            z -= dz;
+            if (std::fabs(dz) <= 1e-16 * std::fmax(1.0, std::fabs(z))) break;
+        }
+        double pm = 1.0, pc = z;
+        for (int j = 1; j < n; ++j) {
+            double pnext = ((2 * j + 1) * z * pc - j * pm) / (j + 1);
+            pm = pc;
+            pc = pnext;
+        }
+        dpn = (n == 1) ? 1.0 : n * (pm - z * pc) / (1.0 - z * z);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dpn * dpn);
+    }
+}
+
+// Real orthonormal harmonics Y_p(mu, phi), p = l*l + l + m (Sec. 2.3): the
+// associated Legendre functions without the (-1)^m phase by the standard
+// upward recurrences in l, times sqrt((2 - d_m0)(2l+1)/4pi (l-m)!/(l+m)!)
+// and cos(m phi) (m > 0) / sin(|m| phi) (m < 0).
+void real_harmonics(int L, double mu, double phi, double *Y)
+{
+    double sth = std::sqrt(std::fmax(0.0, (1.0 - mu) * (1.0 + mu)));
+    double pmm = 1.0;  // P_m^m
+    for (int m = 0; m <= L; ++m) {
+        if (m > 0) pmm *= (2.0 * m - 1.0) * sth;
+        double cm = std::cos(m * phi), sm = std::sin(m * phi);
+        double p_lm2 = 0.0, p_lm1 = pmm;
+        for (int l = m; l <= L; ++l) {
+            double plm;
+            if (l == m) {
+                plm = pmm;
+            } else if (l == m + 1) {
+                plm = (2.0 * m + 1.0) * mu * pmm;
+            } else {
+                plm = ((2.0 * l - 1.0) * mu * p_lm1 - (l + m - 1.0) * p_lm2) / (double)(l - m);
+            }
+            if (l > m) { p_lm2 = p_lm1; p_lm1 = plm; }
+            double ratio = 1.0;  // (l-m)!/(l+m)!
+            for (int q = l - m + 1; q <= l + m; ++q) ratio /= (double)q;
+            double nrm = std::sqrt((m ? 2.0 : 1.0) * (2.0 * l + 1.0) / (4.0 * kPi) * ratio);
+            if (m == 0) {
+                Y[l * l + l] = nrm * plm;
+            } else {
+                Y[l * l + l + m] = nrm * plm * cm;
+                Y[l * l + l - m] = nrm * plm * sm;
+            }
+        }
+    }
+}
+
+template <class T>
+void *to_device_vec(const std::vector<double> &v, long long &bytes, cudaError_t &err)
+{
+    std::vector<T> tmp(v.begin(), v.end());
+    void *p = nullptr;
+    err = cudaMalloc(&p, tmp.size() * sizeof(T) + 16);
+    if (err != cudaSuccess) return nullptr;
+    bytes += (long long)(tmp.size() * sizeof(T));
+    err = cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return p;
+}
+
+void dfree(void *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void free_all(shd_ctx *c)
+{
+    void **ptrs[] = {&c->d_ord, &c->d_W, &c->d_dirs, &c->d_Y, &c->d_mu, (void **)&c->d_edges, (void **)&c->d_centre,
+                     &c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
+                     &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
+                     (void **)&c->d_sums, (void **)&c->d_partial, (void **)&c->d_stage};
+    for (void **p : ptrs) dfree(*p);
+    c->bytes = 0;
+}
+
+bool is_fp64(const shd_ctx *c) { return c->precision == SHD_FP64; }
+
+int ctx_check(shd_ctx *c)
+{
+    if (!c) return fail(SHD_ERR_ARG, "null context");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return SHD_OK;
+}
+
+int dalloc(shd_ctx *c, void **p, size_t bytes, const char *what)
+{
+    dfree(*p);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(SHD_ERR_OOM, "cudaMalloc %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+    }
+    c->bytes += (long long)bytes;
+    return SHD_OK;
+}
+
+// drop everything that depends on the problem sizes
+void drop_sized(shd_ctx *c)
+{
+    void **ptrs[] = {&c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
+                     &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
+                     (void **)&c->d_partial, (void **)&c->d_stage};
+    for (void **p : ptrs) dfree(*p);
+    c->have_fields = c->have_scat = c->have_state = false;
+    c->bc_mode = SHD_BC_VACUUM;
+    c->sprev_valid = false;
+}
+
+// Sweep geometry of every ordinate: the face crossed first (largest
+// |n_a|/h_a, ties to the lowest axis), the path length s = h_d/|n_d| back to
+// it, and the in-plane offsets s |n_e| / h_e of the upwind point.
+void build_geometry(shd_ctx *c)
+{
+    c->h_ord.assign(c->N, Ordinate());
+    for (int k = 0; k < c->N; ++k) {
+        Ordinate &o = c->h_ord[k];
+        for (int a = 0; a < 3; ++a) o.n[a] = c->h_dirs[3 * k + a];
+        o.W = c->h_W[k];
+        o.ring = k / c->nphi;
+        o.phi = k % c->nphi;
+        if (!c->have_grid) continue;
+        int d = 0;
+        double best = std::fabs(o.n[0]) / c->h[0];
+        for (int a = 1; a < 3; ++a) {
+            double v = std::fabs(o.n[a]) / c->h[a];
+            if (v > best) { best = v; d = a; }
+        }
+        o.d = d;
+        if (d == 2) { o.e1 = 1; o.e2 = 0; }
+        else if (d == 1) { o.e1 = 2; o.e2 = 0; }
+        else { o.e1 = 2; o.e2 = 1; }
+        o.s = c->h[d] / std::fabs(o.n[d]);
+        o.fr1 = o.s * std::fabs(o.n[o.e1]) / c->h[o.e1];
+        o.fr2 = o.s * std::fabs(o.n[o.e2]) / c->h[o.e2];
+        auto sgn = [](double v) { return (v > 0.0) - (v < 0.0); };
+        o.sd = sgn(o.n[d]);
+        o.s1 = sgn(o.n[o.e1]);
+        o.s2 = sgn(o.n[o.e2]);
+    }
+}
+
+int upload_angles(shd_ctx *c)
+{
+    dfree(c->d_ord); dfree(c->d_W); dfree(c->d_dirs); dfree(c->d_Y); dfree(c->d_mu);
+    build_geometry(c);
+    cudaError_t e;
+    CK(cudaMalloc(&c->d_ord, sizeof(Ordinate) * c->N), "cudaMalloc ordinates");
+    CK(cudaMemcpy(c->d_ord, c->h_ord.data(), sizeof(Ordinate) * c->N, cudaMemcpyHostToDevice), "copy ordinates");
+    if (is_fp64(c)) {
+        c->d_W = to_device_vec<double>(c->h_W, c->bytes, e); CK(e, "W");
+        c->d_dirs = to_device_vec<double>(c->h_dirs, c->bytes, e); CK(e, "dirs");
+        c->d_Y = to_device_vec<double>(c->h_Y, c->bytes, e); CK(e, "Y");
+        c->d_mu = to_device_vec<double>(c->h_mu, c->bytes, e); CK(e, "mu");
+    } else {
+        c->d_W = to_device_vec<float>(c->h_W, c->bytes, e); CK(e, "W");
+        c->d_dirs = to_device_vec<float>(c->h_dirs, c->bytes, e); CK(e, "dirs");
+        c->d_Y = to_device_vec<float>(c->h_Y, c->bytes, e); CK(e, "Y");
+        c->d_mu = to_device_vec<float>(c->h_mu, c->bytes, e); CK(e, "mu");
+    }
+    return SHD_OK;
+}
+
+bool sized(const shd_ctx *c) { return c->have_grid && c->have_angles && c->have_groups; }
+
+// Allocate the state-sized buffers once grid, angles and groups are known.
+int ensure_buffers(shd_ctx *c)
+{
+    if (!sized(c)) return fail(SHD_ERR_STATE, "grid, angles and groups must be set first");
+    if (c->d_I) return SHD_OK;
+    size_t es = c->esize;
+    size_t nDO = (size_t)c->Nc * c->G * c->N, nSH = (size_t)c->Nc * c->G * c->NLM, nCG = (size_t)c->Nc * c->G;
+    int rc;
+    if ((rc = dalloc(c, &c->d_I, nDO * es, "I"))) return rc;
+    if ((rc = dalloc(c, &c->d_eta, nDO * es, "eta_lab"))) return rc;
+    if ((rc = dalloc(c, &c->d_chi, nDO * es, "chi_lab"))) return rc;
+    if ((rc = dalloc(c, &c->d_Ip, nSH * es, "I_lm"))) return rc;
+    if ((rc = dalloc(c, &c->d_Sp, nSH * es, "S_lm"))) return rc;
+    if ((rc = dalloc(c, &c->d_Sprev, nSH * es, "S_lm prev"))) return rc;
+    if ((rc = dalloc(c, &c->d_mom, nCG * 10 * es, "moments"))) return rc;
+    if ((rc = dalloc(c, &c->d_alpha0, nCG * es, "alpha0"))) return rc;
+    if ((rc = dalloc(c, &c->d_emis0, nCG * es, "emis0"))) return rc;
+    if ((rc = dalloc(c, &c->d_chi0, nCG * es, "chi0"))) return rc;
+    if ((rc = dalloc(c, &c->d_ne, (size_t)c->Nc * es, "ne"))) return rc;
+    if ((rc = dalloc(c, &c->d_u, (size_t)c->Nc * 3 * es, "u"))) return rc;
+    c->n_partial = 2 * 152;
+    if ((rc = dalloc(c, (void **)&c->d_partial, sizeof(double) * 4 * c->n_partial, "partials"))) return rc;
+    size_t per_node = (size_t)c->G * c->N;
+    size_t want = per_node > ((size_t)1 << 24) ? per_node : ((size_t)1 << 24);  // >= 16 Mi doubles or one node
+    size_t cap = (size_t)c->Nc * per_node;
+    if (want > cap) want = cap;
+    if ((rc = dalloc(c, (void **)&c->d_stage, sizeof(double) * want, "staging"))) return rc;
+    c->stage_elems = want;
+    CK(cudaMemsetAsync(c->d_Sprev, 0, nSH * es, c->stream), "memset");
+    return SHD_OK;
+}
+
+template <class T>
+int set_state_impl(shd_ctx *c, const double *src, bool host, cudaStream_t st, T *dst)
+{
+    size_t per_node = (size_t)c->G * c->N;
+    long long chunk = (long long)(c->stage_elems / per_node);
+    if (chunk < 1) chunk = 1;
+    for (long long c0 = 0; c0 < c->Nc; c0 += chunk) {
+        long long nc = c->Nc - c0 < chunk ? c->Nc - c0 : chunk;
+        const double *s = src + (size_t)c0 * per_node;
+        if (host) {
+            CK(cudaMemcpyAsync(c->d_stage, s, sizeof(double) * nc * per_node, cudaMemcpyHostToDevice, st), "H2D state");
+            s = c->d_stage;
+        }
+        CK(launch_canon_to_do<T>(c, s, dst, c0, nc, st), "canon_to_do");
+    }
+    return SHD_OK;
+}
+
+template <class T>
+int get_state_impl(shd_ctx *c, const T *src, double *dst, bool host, cudaStream_t st)
+{
+    size_t per_node = (size_t)c->G * c->N;
+    long long chunk = (long long)(c->stage_elems / per_node);
+    if (chunk < 1) chunk = 1;
+    for (long long c0 = 0; c0 < c->Nc; c0 += chunk) {
+        long long nc = c->Nc - c0 < chunk ? c->Nc - c0 : chunk;
+        double *d = dst + (size_t)c0 * per_node;
+        if (host) {
+            CK(launch_do_to_canon<T>(c, src, c->d_stage, c0, nc, st), "do_to_canon");
+            CK(cudaMemcpyAsync(d, c->d_stage, sizeof(double) * nc * per_node, cudaMemcpyDeviceToHost, st), "D2H state");
+            CK(cudaStreamSynchronize(st), "sync");
+        } else {
+            CK(launch_do_to_canon<T>(c, src, d, c0, nc, st), "do_to_canon");
+        }
+    }
+    return SHD_OK;
+}
+
+// Upload a host FP64 array of n reals into a device real array (via staging).
+template <class T>
+int upload_reals(shd_ctx *c, const double *h, void *dst, size_t n)
+{
+    size_t off = 0;
+    while (off < n) {
+        size_t m = n - off < c->stage_elems ? n - off : c->stage_elems;
+        CK(cudaMemcpyAsync(c->d_stage, h + off, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream), "H2D");
+        CK(launch_convert<T>(c->d_stage, (T *)dst + off, (long long)m, c->stream), "convert");
+        off += m;
+    }
+    return SHD_OK;
+}
+
+template <class T>
+int download_reals(shd_ctx *c, const void *src, double *h, size_t n)
+{
+    size_t off = 0;
+    while (off < n) {
+        size_t m = n - off < c->stage_elems ? n - off : c->stage_elems;
+        CK(launch_convert_back<T>((const T *)src + off, c->d_stage, (long long)m, c->stream), "convert");
+        CK(cudaMemcpyAsync(h + off, c->d_stage, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream), "D2H");
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        off += m;
+    }
+    return SHD_OK;
+}
+
+int ready_for_step(shd_ctx *c)
+{
+    if (!sized(c)) return fail(SHD_ERR_STATE, "grid, angles and groups must be set");
+    if (!c->have_fields) return fail(SHD_ERR_STATE, "fields not set");
+    if (!c->have_scat) return fail(SHD_ERR_STATE, "scattering not set");
+    size_t limit = 227 * 1024;
+    if (project_smem_bytes(c) > limit || sh2lab_smem_bytes(c) > limit)
+        return fail(SHD_ERR_ARG, "groups x ordinates too large for the per-node kernels (%zu bytes shared memory)",
+                    project_smem_bytes(c));
+    if (sweep_smem_bytes(c) > limit) return fail(SHD_ERR_ARG, "grid planes too large for the sweep kernel");
+    return SHD_OK;
+}
+
+template <class T>
+int run_steps(shd_ctx *c, int nsteps, cudaStream_t st)
+{
+    for (int s = 0; s < nsteps; ++s) {
+        bool tm = c->timing.on && c->timing.count < Timing::kCap;
+        cudaEvent_t *ev = tm ? &c->timing.pool[(size_t)c->timing.count * (Timing::kStages + 1)] : nullptr;
+        if (tm) CK(cudaEventRecord(ev[0], st), "event");
+        CK(launch_project<T>(c, (const T *)c->d_I, (T *)c->d_Ip, (T *)c->d_mom, st), "project");
+        if (tm) CK(cudaEventRecord(ev[1], st), "event");
+        CK(launch_source<T>(c, (const T *)c->d_Ip, (T *)c->d_Sp, st), "source");
+        if (tm) CK(cudaEventRecord(ev[2], st), "event");
+        CK(launch_sums<T>(c, (const T *)c->d_mom, (const T *)c->d_Sp, (const T *)c->d_Sprev, c->sprev_valid, st),
+           "sums");
+        if (tm) CK(cudaEventRecord(ev[3], st), "event");
+        CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st), "sh2lab");
+        if (tm) CK(cudaEventRecord(ev[4], st), "event");
+        CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st), "sweep");
+        if (tm) {
+            CK(cudaEventRecord(ev[5], st), "event");
+            c->timing.count++;
+        }
+        std::swap(c->d_Sp, c->d_Sprev);
+        c->sprev_valid = true;
+    }
+    return SHD_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *shd_last_error(void) { return g_err; }
+
+int shd_create(shd_ctx **out, int device, int precision)
+{
+    if (!out) return fail(SHD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (precision != SHD_FP64 && precision != SHD_FP32 && precision != SHD_MIXED)
+        return fail(SHD_ERR_ARG, "unknown precision %d", precision);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(SHD_ERR_ARG, "device %d out of range (%d devices)", device, ndev);
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    shd_ctx *c = new (std::nothrow) shd_ctx();
+    if (!c) return fail(SHD_ERR_OOM, "host allocation");
+    c->device = device;
+    c->precision = precision;
+    c->esize = precision == SHD_FP64 ? 8 : 4;
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaStreamCreate"); }
+    e = cudaMalloc(&c->d_sums, sizeof(double) * 4);
+    if (e != cudaSuccess) { cudaStreamDestroy(c->stream); delete c; return cuda_fail(e, "cudaMalloc"); }
+    cudaMemset(c->d_sums, 0, sizeof(double) * 4);
+    *out = c;
+    g_err[0] = 0;
+    return SHD_OK;
+}
+
+void shd_destroy(shd_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    for (cudaEvent_t e : c->timing.pool) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int shd_set_grid(shd_ctx *c, int nx, int ny, int nz, double lx, double ly, double lz)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (nx < 2 || ny < 2 || nz < 2) return fail(SHD_ERR_ARG, "every grid dimension must be >= 2");
+    if (!(lx > 0 && ly > 0 && lz > 0) || !std::isfinite(lx) || !std::isfinite(ly) || !std::isfinite(lz))
+        return fail(SHD_ERR_ARG, "box lengths must be positive and finite");
+    long long Nc = (long long)nx * ny * nz;
+    if (Nc > (1LL << 31)) return fail(SHD_ERR_ARG, "too many nodes");
+    drop_sized(c);
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->lx = lx; c->ly = ly; c->lz = lz;
+    c->h[0] = lx / (nx - 1); c->h[1] = ly / (ny - 1); c->h[2] = lz / (nz - 1);
+    c->Nc = Nc;
+    c->have_grid = true;
+    if (c->have_angles) return upload_angles(c);
+    return SHD_OK;
+}
+
+int shd_set_angles(shd_ctx *c, int L, int n_mu, int n_phi)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (L < 0 || L > 15) return fail(SHD_ERR_ARG, "L must be in [0, 15]");
+    if (n_mu < L + 1 || n_phi < 2 * L + 1) return fail(SHD_ERR_ARG, "need n_mu >= L+1 and n_phi >= 2L+1");
+    if (n_mu < 1 || n_phi < 1 || (long long)n_mu * n_phi > 4096) return fail(SHD_ERR_ARG, "n_mu*n_phi must be in [1, 4096]");
+    drop_sized(c);
+    c->L = L; c->nmu = n_mu; c->nphi = n_phi;
+    c->N = n_mu * n_phi;
+    c->NLM = (L + 1) * (L + 1);
+    gauss_legendre(n_mu, c->h_mu, c->h_wmu);
+    c->h_dirs.assign(3 * c->N, 0.0);
+    c->h_W.assign(c->N, 0.0);
+    c->h_Y.assign((size_t)c->N * c->NLM, 0.0);
+    for (int a = 0; a < n_mu; ++a) {
+        double sth = std::sqrt((1.0 - c->h_mu[a]) * (1.0 + c->h_mu[a]));
+        for (int b = 0; b < n_phi; ++b) {
+            int k = a * n_phi + b;
+            double phi = 2.0 * kPi * b / n_phi;
+            double n[3] = {sth * std::cos(phi), sth * std::sin(phi), c->h_mu[a]};
+            for (int q = 0; q < 3; ++q) c->h_dirs[3 * k + q] = std::fabs(n[q]) < 1e-12 ? 0.0 : n[q];
+            c->h_W[k] = c->h_wmu[a] * (2.0 * kPi / n_phi);
+            real_harmonics(L, c->h_mu[a], phi, &c->h_Y[(size_t)k * c->NLM]);
+        }
+    }
+    c->have_angles = true;
+    return upload_angles(c);
+}
+
+int shd_set_groups(shd_ctx *c, int G, const double *edges)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (G < 1 || G > 256 || !edges) return fail(SHD_ERR_ARG, "need 1 <= G <= 256 and edges");
+    for (int g = 0; g <= G; ++g)
+        if (!std::isfinite(edges[g]) || edges[g] <= 0.0 || (g > 0 && !(edges[g] > edges[g - 1])))
+            return fail(SHD_ERR_ARG, "edges must be positive, finite and strictly ascending");
+    drop_sized(c);
+    c->G = G;
+    c->h_edges.assign(edges, edges + G + 1);
+    c->h_centre.assign(G, 0.0);
+    for (int g = 0; g < G; ++g) c->h_centre[g] = std::sqrt(edges[g] * edges[g + 1]);
+    dfree((void *&)c->d_edges);
+    dfree((void *&)c->d_centre);
+    cudaError_t e;
+    c->d_edges = (double *)to_device_vec<double>(c->h_edges, c->bytes, e); CK(e, "edges");
+    c->d_centre = (double *)to_device_vec<double>(c->h_centre, c->bytes, e); CK(e, "centres");
+    c->have_groups = true;
+    return SHD_OK;
+}
+
+int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const double *u, const double *emis0)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!c->have_grid || !c->have_groups) return fail(SHD_ERR_STATE, "grid and groups must be set first");
+    if (!alpha0 || !ne || !u || !emis0) return fail(SHD_ERR_ARG, "null field");
+    size_t nCG = (size_t)c->Nc * c->G;
+    if (!finite_all(alpha0, nCG, true)) return fail(SHD_ERR_NAN, "alpha0 must be finite and >= 0");
+    if (!finite_all(ne, (size_t)c->Nc, true)) return fail(SHD_ERR_NAN, "ne must be finite and >= 0");
+    if (!finite_all(u, (size_t)c->Nc * 3, false)) return fail(SHD_ERR_NAN, "u must be finite");
+    if (!finite_all(emis0, nCG, true)) return fail(SHD_ERR_NAN, "emis0 must be finite and >= 0");
+    if ((rc = ensure_buffers(c))) return rc;
+    if (is_fp64(c)) {
+        if ((rc = upload_reals<double>(c, alpha0, c->d_alpha0, nCG))) return rc;
+        if ((rc = upload_reals<double>(c, ne, c->d_ne, c->Nc))) return rc;
+        if ((rc = upload_reals<double>(c, u, c->d_u, 3 * c->Nc))) return rc;
+        if ((rc = upload_reals<double>(c, emis0, c->d_emis0, nCG))) return rc;
+    } else {
+        if ((rc = upload_reals<float>(c, alpha0, c->d_alpha0, nCG))) return rc;
+        if ((rc = upload_reals<float>(c, ne, c->d_ne, c->Nc))) return rc;
+        if ((rc = upload_reals<float>(c, u, c->d_u, 3 * c->Nc))) return rc;
+        if ((rc = upload_reals<float>(c, emis0, c->d_emis0, nCG))) return rc;
+    }
+    c->have_fields = true;
+    if (c->have_scat) {
+        if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
+        else CK(launch_chi0<float>(c, c->stream), "chi0");
+    }
+    return SHD_OK;
+}
+
+int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigma_out)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!c->have_angles || !c->have_groups) return fail(SHD_ERR_STATE, "angles and groups must be set first");
+    if ((rc = ensure_buffers(c))) return rc;
+    int G = c->G, L = c->L;
+    size_t nK = (size_t)(L + 1) * G * G;
+    std::vector<double> hK(nK, 0.0), hs(G, 1.0);
+    if (kind == SHD_SCAT_ISO || kind == SHD_SCAT_THOMSON) {
+        for (int g = 0; g < G; ++g) {
+            hK[(size_t)g * G + g] = 1.0;
+            if (kind == SHD_SCAT_THOMSON && L >= 2) hK[((size_t)2 * G + g) * G + g] = 0.1;
+        }
+    } else if (kind == SHD_SCAT_TABLE) {
+        if (!K || !sigma_out) return fail(SHD_ERR_ARG, "table kind needs K and sigma_out");
+        if (!finite_all(K, nK, false) || !finite_all(sigma_out, G, true))
+            return fail(SHD_ERR_NAN, "scattering table must be finite (sigma_out >= 0)");
+        hK.assign(K, K + nK);
+        hs.assign(sigma_out, sigma_out + G);
+    } else if (kind != SHD_SCAT_KN) {
+        return fail(SHD_ERR_ARG, "unknown scattering kind %d", kind);
+    }
+    if ((rc = dalloc(c, &c->d_K, nK * c->esize, "K"))) return rc;
+    if ((rc = dalloc(c, &c->d_sigma_out, (size_t)G * c->esize, "sigma_out"))) return rc;
+    if (kind == SHD_SCAT_KN) {
+        // built on the device in FP64, then converted to the working precision
+        const int nq = 32;
+        std::vector<double> gx, gw;
+        gauss_legendre(nq, gx, gw);
+        double *dK = nullptr, *ds = nullptr, *dgx = nullptr, *dgw = nullptr;
+        CK(cudaMalloc(&dK, sizeof(double) * nK), "KN scratch");
+        CK(cudaMalloc(&ds, sizeof(double) * G), "KN scratch");
+        CK(cudaMalloc(&dgx, sizeof(double) * nq), "KN scratch");
+        CK(cudaMalloc(&dgw, sizeof(double) * nq), "KN scratch");
+        CK(cudaMemcpy(dgx, gx.data(), sizeof(double) * nq, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(dgw, gw.data(), sizeof(double) * nq, cudaMemcpyHostToDevice), "copy");
+        CK(launch_kn_table(G, c->d_edges, L, dK, ds, dgx, dgw, nq, c->stream), "kn_table");
+        if (is_fp64(c)) {
+            CK(cudaMemcpyAsync(c->d_K, dK, sizeof(double) * nK, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            CK(cudaMemcpyAsync(c->d_sigma_out, ds, sizeof(double) * G, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        } else {
+            CK(launch_convert<float>(dK, (float *)c->d_K, (long long)nK, c->stream), "convert");
+            CK(launch_convert<float>(ds, (float *)c->d_sigma_out, G, c->stream), "convert");
+        }
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        cudaFree(dK); cudaFree(ds); cudaFree(dgx); cudaFree(dgw);
+    } else {
+        if (is_fp64(c)) {
+            if ((rc = upload_reals<double>(c, hK.data(), c->d_K, nK))) return rc;
+            if ((rc = upload_reals<double>(c, hs.data(), c->d_sigma_out, G))) return rc;
+        } else {
+            if ((rc = upload_reals<float>(c, hK.data(), c->d_K, nK))) return rc;
+            if ((rc = upload_reals<float>(c, hs.data(), c->d_sigma_out, G))) return rc;
+        }
+    }
+    c->scat_kind = kind;
+    c->have_scat = true;
+    if (c->have_fields) {
+        if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
+        else CK(launch_chi0<float>(c, c->stream), "chi0");
+    }
+    return SHD_OK;
+}
+
+int shd_get_scattering(shd_ctx *c, double *K, double *sigma_out)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!c->have_scat) return fail(SHD_ERR_STATE, "scattering not set");
+    size_t nK = (size_t)(c->L + 1) * c->G * c->G;
+    if (is_fp64(c)) {
+        if (K && (rc = download_reals<double>(c, c->d_K, K, nK))) return rc;
+        if (sigma_out && (rc = download_reals<double>(c, c->d_sigma_out, sigma_out, c->G))) return rc;
+    } else {
+        if (K && (rc = download_reals<float>(c, c->d_K, K, nK))) return rc;
+        if (sigma_out && (rc = download_reals<float>(c, c->d_sigma_out, sigma_out, c->G))) return rc;
+    }
+    return SHD_OK;
+}
+
+int shd_set_boundary(shd_ctx *c, int mode, const double *data)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (mode == SHD_BC_VACUUM) {
+        dfree(c->d_bc);
+        c->bc_mode = mode;
+        return SHD_OK;
+    }
+    if (!sized(c)) return fail(SHD_ERR_STATE, "grid, angles and groups must be set first");
+    if (!data) return fail(SHD_ERR_ARG, "boundary data is NULL");
+    if ((rc = ensure_buffers(c))) return rc;
+    if (mode == SHD_BC_ISO) {
+        if (!finite_all(data, c->G, true)) return fail(SHD_ERR_NAN, "boundary intensity must be finite and >= 0");
+        if ((rc = dalloc(c, &c->d_bc, (size_t)c->G * c->esize, "bc"))) return rc;
+        rc = is_fp64(c) ? upload_reals<double>(c, data, c->d_bc, c->G) : upload_reals<float>(c, data, c->d_bc, c->G);
+        if (rc) return rc;
+    } else if (mode == SHD_BC_FULL) {
+        size_t n = (size_t)c->Nc * c->G * c->N;
+        if (!finite_all(data, n, false)) return fail(SHD_ERR_NAN, "boundary intensity must be finite");
+        if ((rc = dalloc(c, &c->d_bc, n * c->esize, "bc"))) return rc;
+        rc = is_fp64(c) ? set_state_impl<double>(c, data, true, c->stream, (double *)c->d_bc)
+                        : set_state_impl<float>(c, data, true, c->stream, (float *)c->d_bc);
+        if (rc) return rc;
+    } else {
+        return fail(SHD_ERR_ARG, "unknown boundary mode %d", mode);
+    }
+    c->bc_mode = mode;
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return SHD_OK;
+}
+
+int shd_set_time(shd_ctx *c, double kappa)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!std::isfinite(kappa) || kappa < 0) return fail(SHD_ERR_ARG, "kappa must be finite and >= 0");
+    c->kappa = kappa;
+    return SHD_OK;
+}
+
+int shd_set_state(shd_ctx *c, const double *I)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!I) return fail(SHD_ERR_ARG, "I is NULL");
+    if ((rc = ensure_buffers(c))) return rc;
+    rc = is_fp64(c) ? set_state_impl<double>(c, I, true, c->stream, (double *)c->d_I)
+                    : set_state_impl<float>(c, I, true, c->stream, (float *)c->d_I);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    c->have_state = true;
+    c->sprev_valid = false;
+    return SHD_OK;
+}
+
+int shd_set_state_dev(shd_ctx *c, const double *dev_I, void *stream)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!dev_I) return fail(SHD_ERR_ARG, "dev_I is NULL");
+    if ((rc = ensure_buffers(c))) return rc;
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    rc = is_fp64(c) ? set_state_impl<double>(c, dev_I, false, st, (double *)c->d_I)
+                    : set_state_impl<float>(c, dev_I, false, st, (float *)c->d_I);
+    if (rc) return rc;
+    c->have_state = true;
+    c->sprev_valid = false;
+    return SHD_OK;
+}
+
+int shd_zero_state(shd_ctx *c)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if ((rc = ensure_buffers(c))) return rc;
+    CK(cudaMemsetAsync(c->d_I, 0, (size_t)c->Nc * c->G * c->N * c->esize, c->stream), "memset");
+    c->have_state = true;
+    c->sprev_valid = false;
+    return SHD_OK;
+}
+
+int shd_get_state(shd_ctx *c, double *I)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!I) return fail(SHD_ERR_ARG, "I is NULL");
+    if (!c->have_state) return fail(SHD_ERR_STATE, "state not set");
+    return is_fp64(c) ? get_state_impl<double>(c, (const double *)c->d_I, I, true, c->stream)
+                      : get_state_impl<float>(c, (const float *)c->d_I, I, true, c->stream);
+}
+
+int shd_get_state_dev(shd_ctx *c, double *dev_I, void *stream)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!dev_I) return fail(SHD_ERR_ARG, "dev_I is NULL");
+    if (!c->have_state) return fail(SHD_ERR_STATE, "state not set");
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    return is_fp64(c) ? get_state_impl<double>(c, (const double *)c->d_I, dev_I, false, st)
+                      : get_state_impl<float>(c, (const float *)c->d_I, dev_I, false, st);
+}
+
+int shd_step(shd_ctx *c, int nsteps, void *stream)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(SHD_ERR_ARG, "nsteps < 0");
+    if ((rc = ready_for_step(c))) return rc;
+    if (!c->have_state) return fail(SHD_ERR_STATE, "state not set");
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    if (st != c->stream) {
+        // order against the library's own stream (uploads) in both directions
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+        CK(cudaEventRecord(ev, c->stream), "event");
+        CK(cudaStreamWaitEvent(st, ev, 0), "wait");
+        cudaEventDestroy(ev);
+    }
+    rc = is_fp64(c) ? run_steps<double>(c, nsteps, st) : run_steps<float>(c, nsteps, st);
+    if (rc) return rc;
+    if (st != c->stream) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+        CK(cudaEventRecord(ev, st), "event");
+        CK(cudaStreamWaitEvent(c->stream, ev, 0), "wait");
+        cudaEventDestroy(ev);
+    }
+    return SHD_OK;
+}
+
+int shd_solve_static(shd_ctx *c, double rel_tol, int max_iter, int *iters_out, double *resid_out)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!(rel_tol > 0) || max_iter < 1) return fail(SHD_ERR_ARG, "need rel_tol > 0 and max_iter >= 1");
+    if ((rc = ready_for_step(c))) return rc;
+    if (!c->have_state && (rc = shd_zero_state(c))) return rc;
+    double kap = c->kappa;
+    c->kappa = 0.0;
+    c->sprev_valid = false;
+    int it = 0;
+    double sums[3] = {0, 0, 0};
+    while (it < max_iter) {
+        rc = is_fp64(c) ? run_steps<double>(c, 1, c->stream) : run_steps<float>(c, 1, c->stream);
+        if (rc) break;
+        ++it;
+        cudaError_t e = cudaMemcpyAsync(sums, c->d_sums, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "residual read"); break; }
+        if (it > 1 && sums[2] <= rel_tol) break;
+    }
+    c->kappa = kap;
+    if (iters_out) *iters_out = it;
+    if (resid_out) *resid_out = sums[2];
+    if (rc) return rc;
+    if (!(sums[2] <= rel_tol)) return fail(SHD_ERR_TIMEOUT, "not converged after %d iterations (resid %g)", it, sums[2]);
+    return SHD_OK;
+}
+
+int shd_get_moments(shd_ctx *c, double *J, double *H, double *K, double *Ish)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if ((rc = ready_for_step(c))) return rc;
+    if (!c->have_state) return fail(SHD_ERR_STATE, "state not set");
+    size_t nCG = (size_t)c->Nc * c->G;
+    std::vector<double> mom(nCG * 10);
+    if (is_fp64(c)) {
+        CK(launch_project<double>(c, (const double *)c->d_I, (double *)c->d_Ip, (double *)c->d_mom, c->stream), "project");
+        if ((rc = download_reals<double>(c, c->d_mom, mom.data(), nCG * 10))) return rc;
+        if (Ish && (rc = download_reals<double>(c, c->d_Ip, Ish, nCG * c->NLM))) return rc;
+    } else {
+        CK(launch_project<float>(c, (const float *)c->d_I, (float *)c->d_Ip, (float *)c->d_mom, c->stream), "project");
+        if ((rc = download_reals<float>(c, c->d_mom, mom.data(), nCG * 10))) return rc;
+        if (Ish && (rc = download_reals<float>(c, c->d_Ip, Ish, nCG * c->NLM))) return rc;
+    }
+    for (size_t i = 0; i < nCG; ++i) {
+        if (J) J[i] = mom[i * 10];
+        if (H) for (int q = 0; q < 3; ++q) H[i * 3 + q] = mom[i * 10 + 1 + q];
+        if (K) for (int q = 0; q < 6; ++q) K[i * 6 + q] = mom[i * 10 + 4 + q];
+    }
+    return SHD_OK;
+}
+
+int shd_get_sums(shd_ctx *c, double *energy, double *photons, double *resid)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    double s[3];
+    CK(cudaMemcpyAsync(s, c->d_sums, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream), "D2H sums");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (energy) *energy = s[0];
+    if (photons) *photons = s[1];
+    if (resid) *resid = s[2];
+    return SHD_OK;
+}
+
+// ---- single stages --------------------------------------------------------
+
+int shd_stage_project(shd_ctx *c, const double *I, double *Ish, double *J, double *H, double *K)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if ((rc = ready_for_step(c))) return rc;
+    if (!I) return fail(SHD_ERR_ARG, "I is NULL");
+    if ((rc = shd_set_state(c, I))) return rc;
+    return shd_get_moments(c, J, H, K, Ish);
+}
+
+int shd_stage_source(shd_ctx *c, const double *Ish, double *Ssh)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if ((rc = ready_for_step(c))) return rc;
+    if (!Ish || !Ssh) return fail(SHD_ERR_ARG, "null array");
+    size_t n = (size_t)c->Nc * c->G * c->NLM;
+    if (is_fp64(c)) {
+        if ((rc = upload_reals<double>(c, Ish, c->d_Ip, n))) return rc;
+        CK(launch_source<double>(c, (const double *)c->d_Ip, (double *)c->d_Sp, c->stream), "source");
+        return download_reals<double>(c, c->d_Sp, Ssh, n);
+    }
+    if ((rc = upload_reals<float>(c, Ish, c->d_Ip, n))) return rc;
+    CK(launch_source<float>(c, (const float *)c->d_Ip, (float *)c->d_Sp, c->stream), "source");
+    return download_reals<float>(c, c->d_Sp, Ssh, n);
+}
+
+int shd_stage_sh2lab(shd_ctx *c, const double *Ssh, double *eta_lab, double *chi_lab)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if ((rc = ready_for_step(c))) return rc;
+    if (!Ssh || !eta_lab || !chi_lab) return fail(SHD_ERR_ARG, "null array");
+    size_t n = (size_t)c->Nc * c->G * c->NLM;
+    if (is_fp64(c)) {
+        if ((rc = upload_reals<double>(c, Ssh, c->d_Sp, n))) return rc;
+        CK(launch_sh2lab<double>(c, (const double *)c->d_Sp, (double *)c->d_eta, (double *)c->d_chi, c->stream), "sh2lab");
+        if ((rc = get_state_impl<double>(c, (const double *)c->d_eta, eta_lab, true, c->stream))) return rc;
+        return get_state_impl<double>(c, (const double *)c->d_chi, chi_lab, true, c->stream);
+    }
+    if ((rc = upload_reals<float>(c, Ssh, c->d_Sp, n))) return rc;
+    CK(launch_sh2lab<float>(c, (const float *)c->d_Sp, (float *)c->d_eta, (float *)c->d_chi, c->stream), "sh2lab");
+    if ((rc = get_state_impl<float>(c, (const float *)c->d_eta, eta_lab, true, c->stream))) return rc;
+    return get_state_impl<float>(c, (const float *)c->d_chi, chi_lab, true, c->stream);
+}
+
+int shd_stage_sweep(shd_ctx *c, const double *I_old, const double *eta_lab, const double *chi_lab, double *I_new)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if ((rc = ready_for_step(c))) return rc;
+    if (!I_old || !eta_lab || !chi_lab || !I_new) return fail(SHD_ERR_ARG, "null array");
+    if (is_fp64(c)) {
+        if ((rc = set_state_impl<double>(c, eta_lab, true, c->stream, (double *)c->d_eta))) return rc;
+        if ((rc = set_state_impl<double>(c, chi_lab, true, c->stream, (double *)c->d_chi))) return rc;
+        if ((rc = set_state_impl<double>(c, I_old, true, c->stream, (double *)c->d_I))) return rc;
+        CK(launch_sweep<double>(c, (double *)c->d_I, (const double *)c->d_eta, (const double *)c->d_chi, c->stream), "sweep");
+    } else {
+        if ((rc = set_state_impl<float>(c, eta_lab, true, c->stream, (float *)c->d_eta))) return rc;
+        if ((rc = set_state_impl<float>(c, chi_lab, true, c->stream, (float *)c->d_chi))) return rc;
+        if ((rc = set_state_impl<float>(c, I_old, true, c->stream, (float *)c->d_I))) return rc;
+        CK(launch_sweep<float>(c, (float *)c->d_I, (const float *)c->d_eta, (const float *)c->d_chi, c->stream), "sweep");
+    }
+    c->have_state = true;
+    return shd_get_state(c, I_new);
+}
+
+int shd_get_sizes(shd_ctx *c, long long *n_nodes, int *n_ord, int *n_groups, int *n_lm)
+{
+    if (!c) return fail(SHD_ERR_ARG, "null context");
+    if (n_nodes) *n_nodes = c->Nc;
+    if (n_ord) *n_ord = c->N;
+    if (n_groups) *n_groups = c->G;
+    if (n_lm) *n_lm = c->NLM;
+    return SHD_OK;
+}
+
+long long shd_device_bytes(shd_ctx *c) { return c ? c->bytes : 0; }
+
+int shd_set_timing(shd_ctx *c, int on)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (on && c->timing.pool.empty()) {
+        c->timing.pool.assign((size_t)Timing::kCap * (Timing::kStages + 1), nullptr);
+        for (cudaEvent_t &e : c->timing.pool) CK(cudaEventCreate(&e), "cudaEventCreate");
+    }
+    c->timing.on = on != 0;
+    c->timing.count = 0;
+    return SHD_OK;
+}
+
+int shd_get_timing(shd_ctx *c, double *stage_ms, long long *steps)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    double ms[Timing::kStages] = {0, 0, 0, 0, 0};
+    long long n = c->timing.count;
+    if (n > 0) {
+        CK(cudaEventSynchronize(c->timing.pool[(size_t)(n - 1) * (Timing::kStages + 1) + Timing::kStages]), "sync");
+        for (long long s = 0; s < n; ++s) {
+            cudaEvent_t *ev = &c->timing.pool[(size_t)s * (Timing::kStages + 1)];
+            for (int q = 0; q < Timing::kStages; ++q) {
+                float t = 0;
+                CK(cudaEventElapsedTime(&t, ev[q], ev[q + 1]), "elapsed");
+                ms[q] += t;
+            }
+        }
+    }
+    if (stage_ms)
+        for (int q = 0; q < Timing::kStages; ++q) stage_ms[q] = ms[q];
+    if (steps) *steps = n;
+    return SHD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,368 @@
+// Internal declarations of the GB300 SHDOM library: context, device tables,
+// device helpers shared by the kernels, and the kernel launchers.
+//
+// Device layouts
+//   discrete-ordinate arrays (I, eta_lab, chi_lab, full boundary):
+//     [k][g][o]  with o the node offset in the ordinate's *sweep layout*:
+//     the axis the ordinate crosses first (its dominant axis d) is the
+//     slowest index, so that every plane normal to d is one contiguous block:
+//       d = z : o = (iz*ny + iy)*nx + ix
+//       d = y : o = (iy*nz + iz)*nx + ix
+//       d = x : o = (ix*nz + iz)*ny + iy
+//   spherical-harmonic arrays (I_lm, S_lm): [c][g][p]
+//   moments: [c][g][10] = J, H_x, H_y, H_z, K_xx, K_yy, K_zz, K_xy, K_xz, K_yz
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/shdom_gb300.h"
+
+namespace shd {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Per-ordinate constants, built on the host in FP64 (Sec. 2.2 mesh; the
+// sweep geometry of the short characteristic).
+struct Ordinate {
+    double n[3];     // direction
+    double W;        // quadrature weight (sum 4 pi)
+    double fr1, fr2; // upwind-point offsets on the two in-plane axes, in cells
+    double s;        // path length from the upwind face to the node
+    int d, e1, e2;   // dominant axis and in-plane axes (layout order)
+    int sd, s1, s2;  // signs of n along d, e1, e2 (-1, 0, +1)
+    int ring, phi;   // (a, b) mesh indices
+};
+
+// Everything a kernel needs about the problem, passed by value.
+template <class T>
+struct Prob {
+    int nx, ny, nz;
+    long long Nc;
+    int N, nmu, nphi, NLM, L, G;
+    T kappa;
+    const Ordinate *ord;   // [N]
+    const T *W;            // [N]
+    const T *dirs;         // [N][3]
+    const T *Y;            // [N][NLM]
+    const T *mu;           // [nmu]
+    const double *edges;   // [G+1]
+    const double *centre;  // [G]
+    const T *alpha0;       // [Nc][G]
+    const T *ne;           // [Nc]
+    const T *u;            // [Nc][3]
+    const T *emis0;        // [Nc][G]
+    const T *chi0;         // [Nc][G]  alpha0 + ne sigma_out
+    const T *K;            // [L+1][G][G]
+    const T *sigma_out;    // [G]
+    int bc_mode;
+    const T *bc;           // ISO: [G]; FULL: DO layout
+};
+
+// Per-stage CUDA events recorded on the launching stream without any host
+// synchronisation; read (and summed) only by shd_get_timing.
+struct Timing {
+    static constexpr int kStages = 5;  // project, source, sums, sh2lab, sweep
+    static constexpr int kCap = 2048;  // steps recorded per enable
+    bool on = false;
+    std::vector<cudaEvent_t> pool;     // (kStages + 1) per recorded step
+    long long count = 0;               // steps recorded
+};
+
+}  // namespace shd
+
+struct shd_ctx {
+    int device = 0;
+    int precision = SHD_FP64;
+    size_t esize = 8;  // bytes per real on the device
+    cudaStream_t stream = nullptr;
+
+    // grid
+    int nx = 0, ny = 0, nz = 0;
+    double lx = 0, ly = 0, lz = 0, h[3] = {0, 0, 0};
+    long long Nc = 0;
+    // angles
+    int L = -1, nmu = 0, nphi = 0, N = 0, NLM = 0;
+    std::vector<double> h_mu, h_wmu, h_dirs, h_W, h_Y;  // host tables (FP64)
+    std::vector<shd::Ordinate> h_ord;
+    // groups
+    int G = 0;
+    std::vector<double> h_edges, h_centre;
+
+    bool have_grid = false, have_angles = false, have_groups = false;
+    bool have_fields = false, have_scat = false, have_state = false;
+    int scat_kind = 0;
+    int bc_mode = SHD_BC_VACUUM;
+    double kappa = 0.0;
+
+    // device buffers (reals are T = double or float per precision)
+    void *d_ord = nullptr;
+    void *d_W = nullptr, *d_dirs = nullptr, *d_Y = nullptr, *d_mu = nullptr;
+    double *d_edges = nullptr, *d_centre = nullptr;
+    void *d_alpha0 = nullptr, *d_ne = nullptr, *d_u = nullptr, *d_emis0 = nullptr, *d_chi0 = nullptr;
+    void *d_K = nullptr, *d_sigma_out = nullptr;
+    void *d_bc = nullptr;
+    void *d_I = nullptr, *d_eta = nullptr, *d_chi = nullptr;
+    void *d_Ip = nullptr, *d_Sp = nullptr, *d_Sprev = nullptr, *d_mom = nullptr;
+    double *d_sums = nullptr;     // [3] energy, photons, resid
+    double *d_partial = nullptr;  // reduction scratch
+    int n_partial = 0;
+    double *d_stage = nullptr;    // staging buffer for host <-> device copies (FP64)
+    size_t stage_elems = 0;
+    long long bytes = 0;
+    bool sprev_valid = false;
+
+    shd::Timing timing;
+};
+
+namespace shd {
+
+// -------------------------------------------------------------------------
+// device helpers
+// -------------------------------------------------------------------------
+
+__host__ __device__ inline long long perm_offset(int d, int ix, int iy, int iz, int nx, int ny, int nz)
+{
+    if (d == 2) return ((long long)iz * ny + iy) * nx + ix;
+    if (d == 1) return ((long long)iy * nz + iz) * nx + ix;
+    return ((long long)ix * nz + iz) * ny + iy;
+}
+
+template <class T>
+__device__ inline T dsqrt(T x);
+template <>
+__device__ inline double dsqrt<double>(double x) { return sqrt(x); }
+template <>
+__device__ inline float dsqrt<float>(float x) { return sqrtf(x); }
+
+template <class T>
+__device__ inline T dexp(T x);
+template <>
+__device__ inline double dexp<double>(double x) { return exp(x); }
+template <>
+__device__ inline float dexp<float>(float x) { return expf(x); }
+
+template <class T>
+__device__ inline T dlog(T x);
+template <>
+__device__ inline double dlog<double>(double x) { return log(x); }
+template <>
+__device__ inline float dlog<float>(float x) { return logf(x); }
+
+template <class T>
+__device__ inline T datan2(T y, T x);
+template <>
+__device__ inline double datan2<double>(double y, double x) { return atan2(y, x); }
+template <>
+__device__ inline float datan2<float>(float y, float x) { return atan2f(y, x); }
+
+// Lorentz boost of a direction (Sec. 2.2, eq:lorentzfreq and eq:lorentzray
+// with u = Gamma v/c).  sgn = +1: laboratory n -> comoving, returning
+// nu0/nu = Gamma - u.n;  sgn = -1: comoving n -> laboratory, returning
+// nu/nu0 = Gamma + u.n.  The ratio is formed as 1/(Gamma+|u|) + |u||n -+ u^|^2/2,
+// free of cancellation at large Gamma.
+template <class R>
+__device__ inline R boost_dir(const R u[3], const R n[3], R out[3], R sgn)
+{
+    R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    R gam = dsqrt<R>(R(1) + uu), um = dsqrt<R>(uu);
+    if (!(um > R(0))) {  // at rest (or |u|^2 underflowed): the identity
+        out[0] = n[0]; out[1] = n[1]; out[2] = n[2];
+        return R(1);
+    }
+    R un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+    R d2 = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R dd = n[i] - sgn * u[i] / um;
+        d2 += dd * dd;
+    }
+    R r = R(1) / (gam + um) + R(0.5) * um * d2;
+    R f = R(1) - sgn * un / (gam + R(1));
+    R ir = R(1) / r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i] = (n[i] - sgn * u[i] * f) * ir;
+    return r;
+}
+
+// Bilinear stencil on an ordinate mesh (mu ascending Gauss rings, phi
+// uniform from 0): four (ordinate, weight) pairs plus an optional pole term
+// whose value is the average of ring `pole_ring`.
+template <class T>
+struct Stencil {
+    int k[4];
+    T w[4];
+    int pole_ring;  // -1: none
+    T wpole;
+};
+
+template <class T>
+__device__ inline Stencil<T> make_stencil(const T *mu, int nmu, int nphi, const T n[3])
+{
+    Stencil<T> s;
+    T m = n[2];
+    m = m > T(1) ? T(1) : (m < T(-1) ? T(-1) : m);
+    T phi = datan2<T>(n[1], n[0]);
+    if (phi < T(0)) phi += T(2 * kPi);
+    T x = phi * (T(nphi) / T(2 * kPi));
+    int b = (int)x;  // x >= 0
+    T tp = x - T(b);
+    if (b >= nphi) b -= nphi;
+    if (!(b >= 0 && b < nphi)) { b = 0; tp = 0; }  // non-finite direction: stay in bounds
+    int b1 = b + 1 == nphi ? 0 : b + 1;
+    s.pole_ring = -1;
+    s.wpole = 0;
+    if (m < mu[0] || m > mu[nmu - 1]) {
+        int ring = m < mu[0] ? 0 : nmu - 1;
+        T t = m < mu[0] ? (m + T(1)) / (mu[0] + T(1)) : (T(1) - m) / (T(1) - mu[nmu - 1]);
+        s.pole_ring = ring;
+        s.wpole = T(1) - t;
+        s.k[0] = ring * nphi + b;  s.w[0] = t * (T(1) - tp);
+        s.k[1] = ring * nphi + b1; s.w[1] = t * tp;
+        s.k[2] = s.k[0]; s.w[2] = 0;
+        s.k[3] = s.k[1]; s.w[3] = 0;
+        return s;
+    }
+    int a = 0;
+    if (nmu > 1) {
+        while (a < nmu - 2 && m > mu[a + 1]) ++a;
+        T t = (m - mu[a]) / (mu[a + 1] - mu[a]);
+        s.k[0] = a * nphi + b;       s.w[0] = (T(1) - t) * (T(1) - tp);
+        s.k[1] = a * nphi + b1;      s.w[1] = (T(1) - t) * tp;
+        s.k[2] = (a + 1) * nphi + b; s.w[2] = t * (T(1) - tp);
+        s.k[3] = (a + 1) * nphi + b1; s.w[3] = t * tp;
+    } else {
+        s.k[0] = b; s.w[0] = T(1) - tp;
+        s.k[1] = b1; s.w[1] = tp;
+        s.k[2] = b; s.w[2] = 0;
+        s.k[3] = b1; s.w[3] = 0;
+    }
+    return s;
+}
+
+// F points at one group's N ordinate values; poles at that group's two ring
+// averages (south, north).
+template <class T>
+__device__ inline T eval_stencil(const Stencil<T> &s, const T *F, const T *poles)
+{
+    T v = s.w[0] * F[s.k[0]] + s.w[1] * F[s.k[1]] + s.w[2] * F[s.k[2]] + s.w[3] * F[s.k[3]];
+    if (s.pole_ring >= 0) v += s.wpole * poles[s.pole_ring == 0 ? 0 : 1];
+    return v;
+}
+
+// Group bracket for energy eps (Sec. 2.3 multi-group, group value at the
+// centre): returns mode 0 = outside the edges, 1 = a single group ga (between
+// an outer centre and its edge), 2 = between centres ga and ga+1 with
+// log-fraction t.
+struct FreqBracket {
+    int mode, ga;
+    double t;
+};
+
+__device__ inline FreqBracket freq_bracket(const double *edges, const double *centre, int G, double eps)
+{
+    FreqBracket b;
+    b.t = 0;
+    if (eps < edges[0] || eps > edges[G]) { b.mode = 0; b.ga = eps < edges[0] ? 0 : G - 1; return b; }
+    if (eps <= centre[0]) { b.mode = 1; b.ga = 0; return b; }
+    if (eps >= centre[G - 1]) { b.mode = 1; b.ga = G - 1; return b; }
+    int lo = 0, hi = G - 1;  // centre[lo] < eps < centre[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (centre[mid] <= eps) lo = mid; else hi = mid;
+    }
+    b.mode = 2;
+    b.ga = lo;
+    b.t = log(eps / centre[lo]) / log(centre[lo + 1] / centre[lo]);
+    return b;
+}
+
+// Geometric between positive values, linear in log(eps) otherwise.
+template <class T>
+__device__ inline T freq_mix(T fa, T fb, T t)
+{
+    if (fa > T(0) && fb > T(0)) return fa * dexp<T>(t * dlog<T>(fb / fa));
+    return (T(1) - t) * fa + t * fb;
+}
+
+// Linear-in-tau short-characteristic weights with e = exp(-x):
+//   I_P = I_U e + S_P wp + S_U wu,  wp = 1 - (1-e)/x,  wu = (1-e)/x - e.
+// Below the threshold the Taylor series (Horner) avoids the cancellation.
+template <class T>
+__device__ inline void sc_weights(T x, T &e, T &wp, T &wu);
+
+template <>
+__device__ inline void sc_weights<double>(double x, double &e, double &wp, double &wu)
+{
+    if (x < 0.05) {
+        // wp = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!,  wu = sum_{n>=1} (-1)^{n+1} n x^n/(n+1)!
+        wp = x * (1.0 / 2 - x * (1.0 / 6 - x * (1.0 / 24 - x * (1.0 / 120 - x * (1.0 / 720 - x * (1.0 / 5040 - x * (1.0 / 40320 - x / 362880.0)))))));
+        wu = x * (1.0 / 2 - x * (1.0 / 3 - x * (1.0 / 8 - x * (1.0 / 30 - x * (1.0 / 144 - x * (1.0 / 840 - x * (1.0 / 5760 - x / 45360.0)))))));
+        e = exp(-x);
+        return;
+    }
+    double em1 = -expm1(-x);
+    e = 1.0 - em1;
+    double a0 = em1 / x;
+    wp = 1.0 - a0;
+    wu = a0 - e;
+}
+
+template <>
+__device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu)
+{
+    if (x < 0.5f) {
+        wp = x * (1.f / 2 - x * (1.f / 6 - x * (1.f / 24 - x * (1.f / 120 - x * (1.f / 720 - x * (1.f / 5040 - x * (1.f / 40320 - x / 362880.f)))))));
+        wu = x * (1.f / 2 - x * (1.f / 3 - x * (1.f / 8 - x * (1.f / 30 - x * (1.f / 144 - x * (1.f / 840 - x * (1.f / 5760 - x / 45360.f)))))));
+        e = expf(-x);
+        return;
+    }
+    float em1 = -expm1f(-x);
+    e = 1.f - em1;
+    float a0 = em1 / x;
+    wp = 1.f - a0;
+    wu = a0 - e;
+}
+
+// -------------------------------------------------------------------------
+// launchers (shd_kernels.cu)
+// -------------------------------------------------------------------------
+template <class T>
+Prob<T> make_prob(const shd_ctx *ctx);
+
+template <class T>
+cudaError_t launch_chi0(const shd_ctx *ctx, cudaStream_t st);
+template <class T>
+cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st);
+template <class T>
+cudaError_t launch_source(const shd_ctx *ctx, const T *Ip, T *Sp, cudaStream_t st);
+template <class T>
+cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st);
+template <class T>
+cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st);
+template <class T>
+cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev, bool have_prev, cudaStream_t st);
+
+// layout conversions: canonical FP64 [c][g][k] chunk <-> device DO layout
+template <class T>
+cudaError_t launch_canon_to_do(const shd_ctx *ctx, const double *src, T *dst, long long c0, long long nc,
+                               cudaStream_t st);
+template <class T>
+cudaError_t launch_do_to_canon(const shd_ctx *ctx, const T *src, double *dst, long long c0, long long nc,
+                               cudaStream_t st);
+template <class T>
+cudaError_t launch_convert(const double *src, T *dst, long long n, cudaStream_t st);
+template <class T>
+cudaError_t launch_convert_back(const T *src, double *dst, long long n, cudaStream_t st);
+
+cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, double *d_sigma_out,
+                            const double *d_gx, const double *d_gw, int nq, cudaStream_t st);
+
+size_t project_smem_bytes(const shd_ctx *ctx);
+size_t sh2lab_smem_bytes(const shd_ctx *ctx);
+size_t sweep_smem_bytes(const shd_ctx *ctx);
+
+}  // namespace shd

@@ -1,0 +1,688 @@
+// Kernels of one source iteration (stages a1..a5) for FP64 and FP32.
+//
+//   k_project   a1  lab -> comoving remap, SH projection, lab moments
+//   k_source    a2  comoving SH source with the group-to-group kernel
+//   k_sh2lab    a3  SH -> comoving ordinates -> laboratory eta, chi
+//   k_sweep     a4  short-characteristic transfer, plane by plane
+//   k_sums_*    a5  FP64 diagnostics (deterministic two-pass reductions)
+//
+// Paper passages: Sec. 2 (eq:shdom, Lambda iteration, SH <-> DO transforms),
+// Sec. 2.1 (eq:time), Sec. 2.2 (eq:lorentzfreq, eq:lorentzray, invariants,
+// remap between frame meshes), Sec. 2.3 (SH source, Thomson, eq:comptoncross).
+#include <cuda_runtime.h>
+
+#include "shd_internal.cuh"
+
+namespace shd {
+
+template <class T>
+Prob<T> make_prob(const shd_ctx *c)
+{
+    Prob<T> p;
+    p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.Nc = c->Nc;
+    p.N = c->N; p.nmu = c->nmu; p.nphi = c->nphi; p.NLM = c->NLM; p.L = c->L; p.G = c->G;
+    p.kappa = (T)c->kappa;
+    p.ord = (const Ordinate *)c->d_ord;
+    p.W = (const T *)c->d_W; p.dirs = (const T *)c->d_dirs; p.Y = (const T *)c->d_Y; p.mu = (const T *)c->d_mu;
+    p.edges = c->d_edges; p.centre = c->d_centre;
+    p.alpha0 = (const T *)c->d_alpha0; p.ne = (const T *)c->d_ne; p.u = (const T *)c->d_u;
+    p.emis0 = (const T *)c->d_emis0; p.chi0 = (const T *)c->d_chi0;
+    p.K = (const T *)c->d_K; p.sigma_out = (const T *)c->d_sigma_out;
+    p.bc_mode = c->bc_mode; p.bc = (const T *)c->d_bc;
+    return p;
+}
+
+__device__ inline void node_xyz(long long c, int nx, int ny, int &ix, int &iy, int &iz)
+{
+    ix = (int)(c % nx);
+    long long r = c / nx;
+    iy = (int)(r % ny);
+    iz = (int)(r / ny);
+}
+
+// -------------------------------------------------------------------------
+// chi0(c,g) = alpha0 + n_e sigma_out(g)  (Sec. 2: chi = alpha + sigma)
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void k_chi0(Prob<T> P, T *chi0)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long n = P.Nc * P.G;
+    if (i >= n) return;
+    long long c = i / P.G;
+    int g = (int)(i % P.G);
+    chi0[i] = P.alpha0[i] + P.ne[c] * P.sigma_out[g];
+}
+
+// -------------------------------------------------------------------------
+// a1: one CTA per node.  Shared memory holds the node's laboratory
+// intensities [G][N] and, for a moving node, the comoving ones [G][N].
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void k_project(Prob<T> P, const T *__restrict__ I, T *__restrict__ Ip, T *__restrict__ mom)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sI = reinterpret_cast<T *>(smem_raw);
+    const int G = P.G, N = P.N, NLM = P.NLM;
+    T *sI0 = sI + (size_t)G * N;
+    T *spole = sI0 + (size_t)G * N;  // [G][2]
+    const long long c = blockIdx.x;
+    int ix, iy, iz;
+    node_xyz(c, P.nx, P.ny, ix, iy, iz);
+    long long off[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) off[d] = perm_offset(d, ix, iy, iz, P.nx, P.ny, P.nz);
+
+    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
+        int g = i / N, k = i - g * N;
+        sI[i] = I[((long long)k * G + g) * P.Nc + off[P.ord[k].d]];
+    }
+    const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
+    const bool moving = !(u[0] == T(0) && u[1] == T(0) && u[2] == T(0));
+    __syncthreads();
+    const T *src = sI;
+    if (moving) {
+        for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
+            int g = i >> 1, r = i & 1;
+            const T *F = sI + (size_t)g * N + (r ? (P.nmu - 1) * P.nphi : 0);
+            T s = 0;
+            for (int j = 0; j < P.nphi; ++j) s += F[j];
+            spole[i] = s / T(P.nphi);
+        }
+        __syncthreads();
+        for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
+            T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
+            T n[3];
+            T q = boost_dir<T>(u, n0, n, T(-1));  // nu/nu0
+            Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n);
+            T iq3 = T(1) / (q * q * q);
+            for (int g0 = 0; g0 < G; ++g0) {
+                double eps = P.centre[g0] * (double)q;
+                FreqBracket fb = freq_bracket(P.edges, P.centre, G, eps);
+                T v = 0;
+                if (fb.mode == 1) {
+                    v = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                } else if (fb.mode == 2) {
+                    T fa = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                    T fbv = eval_stencil<T>(st, sI + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
+                    v = freq_mix<T>(fa, fbv, (T)fb.t);
+                }
+                sI0[(size_t)g0 * N + k0] = v * iq3;
+            }
+        }
+        __syncthreads();
+        src = sI0;
+    }
+    // I_p(g) = sum_k W_k Y_p(n_k) I0(k, g)
+    for (int i = threadIdx.x; i < G * NLM; i += blockDim.x) {
+        int g = i / NLM, p = i - g * NLM;
+        const T *F = src + (size_t)g * N;
+        T s = 0;
+        for (int k = 0; k < N; ++k) s += P.W[k] * P.Y[(size_t)k * NLM + p] * F[k];
+        Ip[((long long)c * G + g) * NLM + p] = s;
+    }
+    // laboratory moments (1/4pi) sum_k W_k {1, n_i, n_i n_j} I(k, g)
+    for (int i = threadIdx.x; i < G * 10; i += blockDim.x) {
+        int g = i / 10, m = i - g * 10;
+        const T *F = sI + (size_t)g * N;
+        T s = 0;
+        for (int k = 0; k < N; ++k) {
+            T n0 = P.dirs[3 * k], n1 = P.dirs[3 * k + 1], n2 = P.dirs[3 * k + 2];
+            T f;
+            switch (m) {
+                case 0: f = T(1); break;
+                case 1: f = n0; break;
+                case 2: f = n1; break;
+                case 3: f = n2; break;
+                case 4: f = n0 * n0; break;
+                case 5: f = n1 * n1; break;
+                case 6: f = n2 * n2; break;
+                case 7: f = n0 * n1; break;
+                case 8: f = n0 * n2; break;
+                default: f = n1 * n2; break;
+            }
+            s += P.W[k] * f * F[k];
+        }
+        mom[((long long)c * G + g) * 10 + m] = s * T(1.0 / (4.0 * kPi));
+    }
+}
+
+// -------------------------------------------------------------------------
+// a2: S_p(c,g) = n_e/chi0 sum_g' K_l[g][g'] I_p(c,g') + delta_p0 sqrt(4pi) eta0/chi0
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void k_source(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int G = P.G, NLM = P.NLM;
+    long long n = P.Nc * G * NLM;
+    if (i >= n) return;
+    int p = (int)(i % NLM);
+    long long cg = i / NLM;
+    int g = (int)(cg % G);
+    long long c = cg / G;
+    int l = 0;
+    while ((l + 1) * (l + 1) <= p) ++l;
+    T chi = P.chi0[cg];
+    T s = 0;
+    if (chi > T(0)) {
+        const T *Kr = P.K + ((size_t)l * G + g) * G;
+        const T *Ic = Ip + (long long)c * G * NLM + p;
+        T acc = 0;
+        for (int gp = 0; gp < G; ++gp) acc += Kr[gp] * Ic[(size_t)gp * NLM];
+        s = P.ne[c] / chi * acc;
+        if (p == 0) s += T(3.5449077018110320546) * P.emis0[cg] / chi;  // sqrt(4 pi)
+    }
+    Sp[i] = s;
+}
+
+// -------------------------------------------------------------------------
+// a3: one CTA per node.  S0 on comoving ordinates [G][N] in shared memory,
+// then every laboratory (k, g) of the node (Lorentz remap when moving).
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void k_sh2lab(Prob<T> P, const T *__restrict__ Sp, T *__restrict__ eta, T *__restrict__ chi)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sS0 = reinterpret_cast<T *>(smem_raw);
+    const int G = P.G, N = P.N, NLM = P.NLM;
+    T *spole = sS0 + (size_t)G * N;  // [G][2]
+    T *schi = spole + 2 * G;         // [G]
+    const long long c = blockIdx.x;
+    int ix, iy, iz;
+    node_xyz(c, P.nx, P.ny, ix, iy, iz);
+    long long off[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) off[d] = perm_offset(d, ix, iy, iz, P.nx, P.ny, P.nz);
+
+    const T *Sc = Sp + (long long)c * G * NLM;
+    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
+        int g = i / N, k = i - g * N;
+        const T *Yk = P.Y + (size_t)k * NLM;
+        const T *Sg = Sc + (size_t)g * NLM;
+        T s = 0;
+        for (int p = 0; p < NLM; ++p) s += Yk[p] * Sg[p];
+        sS0[i] = s;
+    }
+    for (int g = threadIdx.x; g < G; g += blockDim.x) schi[g] = P.chi0[(long long)c * G + g];
+    const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
+    const bool moving = !(u[0] == T(0) && u[1] == T(0) && u[2] == T(0));
+    __syncthreads();
+    if (!moving) {
+        for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
+            int k = i / G, g = i - k * G;
+            long long o = ((long long)k * G + g) * P.Nc + off[P.ord[k].d];
+            T ch = schi[g];
+            chi[o] = ch;
+            eta[o] = ch * sS0[(size_t)g * N + k];
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
+        int g = i >> 1, r = i & 1;
+        const T *F = sS0 + (size_t)g * N + (r ? (P.nmu - 1) * P.nphi : 0);
+        T s = 0;
+        for (int j = 0; j < P.nphi; ++j) s += F[j];
+        spole[i] = s / T(P.nphi);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
+        T n0[3];
+        T D = boost_dir<T>(u, n, n0, T(1));  // nu0/nu
+        Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n0);
+        T iD3 = T(1) / (D * D * D);
+        long long base = (long long)k * G * P.Nc + off[P.ord[k].d];
+        for (int g = 0; g < G; ++g) {
+            double eps0 = P.centre[g] * (double)D;
+            FreqBracket fb = freq_bracket(P.edges, P.centre, G, eps0);
+            T s = 0, ch;
+            if (fb.mode == 0) {
+                ch = schi[fb.ga];
+            } else if (fb.mode == 1) {
+                s = eval_stencil<T>(st, sS0 + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                ch = schi[fb.ga];
+            } else {
+                T fa = eval_stencil<T>(st, sS0 + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                T fbv = eval_stencil<T>(st, sS0 + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
+                s = freq_mix<T>(fa, fbv, (T)fb.t);
+                ch = freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], (T)fb.t);
+            }
+            T chl = ch * D;
+            long long o = base + (long long)g * P.Nc;
+            chi[o] = chl;
+            eta[o] = chl * s * iD3;
+        }
+    }
+}
+
+// -------------------------------------------------------------------------
+// a4: one CTA per (ordinate, group).  Planes normal to the dominant axis are
+// contiguous in the sweep layout and depend only on the previous plane, so
+// the CTA walks them in upwind order holding the previous plane's I^{n+1},
+// S~ and chi~ in shared memory; each thread keeps its own nodes' values in
+// registers between the two barriers of a plane.
+// -------------------------------------------------------------------------
+template <class T, int NPT>
+__global__ void __launch_bounds__(1024) k_sweep(Prob<T> P, T *__restrict__ I, const T *__restrict__ eta,
+                                                const T *__restrict__ chi)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int k = blockIdx.x / P.G;
+    const int g = blockIdx.x - k * P.G;
+    const Ordinate o = P.ord[k];
+    const int dims[3] = {P.nx, P.ny, P.nz};
+    const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
+    const int plane = n1 * n2;
+    T *pI = reinterpret_cast<T *>(smem_raw);
+    T *pS = pI + plane;
+    T *pC = pS + plane;
+    const long long base = ((long long)k * P.G + g) * P.Nc;
+    const T fr1 = (T)o.fr1, fr2 = (T)o.fr2, s = (T)o.s, kap = P.kappa;
+    const int first1 = o.s1 > 0 ? 0 : n1 - 1, first2 = o.s2 > 0 ? 0 : n2 - 1;
+    const T w00 = (T(1) - fr1) * (T(1) - fr2), w10 = fr1 * (T(1) - fr2), w01 = (T(1) - fr1) * fr2, w11 = fr1 * fr2;
+    T bc_iso = P.bc_mode == SHD_BC_ISO ? P.bc[g] : T(0);
+
+    T rI[NPT], rS[NPT], rC[NPT];
+    for (int step = 0; step < nd; ++step) {
+        const int id = o.sd > 0 ? step : nd - 1 - step;
+        const long long pbase = base + (long long)id * plane;
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            int j = threadIdx.x + t * blockDim.x;
+            if (j >= plane) break;
+            int i1 = j / n2, i2 = j - i1 * n2;
+            long long oo = pbase + j;
+            T In = I[oo];
+            T ct = chi[oo] + kap;
+            T st = ct > T(0) ? (eta[oo] + kap * In) / ct : T(0);
+            bool inflow = step == 0 || (o.s1 != 0 && i1 == first1) || (o.s2 != 0 && i2 == first2);
+            T inew;
+            if (inflow) {
+                inew = P.bc_mode == SHD_BC_FULL ? P.bc[oo] : bc_iso;
+            } else {
+                int j1 = i1 - o.s1, j2 = i2 - o.s2;  // upwind neighbours on the previous plane
+                int a00 = i1 * n2 + i2, a10 = j1 * n2 + i2, a01 = i1 * n2 + j2, a11 = j1 * n2 + j2;
+                // a zero weight may pair with an index outside the plane when the
+                // component is zero; clamp it to a valid slot (its weight is 0)
+                if (o.s1 == 0) { a10 = a00; a11 = a01; }
+                if (o.s2 == 0) { a01 = a00; a11 = a10; }
+                T iu = w00 * pI[a00] + w10 * pI[a10] + w01 * pI[a01] + w11 * pI[a11];
+                T su = w00 * pS[a00] + w10 * pS[a10] + w01 * pS[a01] + w11 * pS[a11];
+                T cu = w00 * pC[a00] + w10 * pC[a10] + w01 * pC[a01] + w11 * pC[a11];
+                T dtau = s * T(0.5) * (cu + ct);
+                T e, wp, wu;
+                sc_weights<T>(dtau, e, wp, wu);
+                inew = iu * e + st * wp + su * wu;
+            }
+            rI[t] = inew;
+            rS[t] = st;
+            rC[t] = ct;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            int j = threadIdx.x + t * blockDim.x;
+            if (j >= plane) break;
+            pI[j] = rI[t];
+            pS[j] = rS[t];
+            pC[j] = rC[t];
+            I[pbase + j] = rI[t];
+        }
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------------------
+// a5: FP64 diagnostics; pass 1 per-block partials, pass 2 a single block
+// adds them in a fixed order (deterministic).
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void k_sums_partial(Prob<T> P, const T *__restrict__ mom, const T *__restrict__ Sp,
+                               const T *__restrict__ Sprev, int have_prev, double *partial)
+{
+    __shared__ double red[4][256];
+    double e = 0, ph = 0, num = 0, den = 0;
+    const long long nJ = P.Nc * P.G;
+    const long long nS = nJ * P.NLM;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nJ; i += stride) {
+        int g = (int)(i % P.G);
+        double J = (double)mom[i * 10];
+        double de = P.edges[g + 1] - P.edges[g];
+        e += 4.0 * kPi * J * de;
+        ph += 4.0 * kPi * J * de / P.centre[g];
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nS; i += stride) {
+        double sn = (double)Sp[i];
+        den += sn * sn;
+        if (have_prev) {
+            double d = sn - (double)Sprev[i];
+            num += d * d;
+        }
+    }
+    red[0][threadIdx.x] = e;
+    red[1][threadIdx.x] = ph;
+    red[2][threadIdx.x] = num;
+    red[3][threadIdx.x] = den;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) partial[blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_sums_final(const double *partial, int nblocks, int have_prev, double *out)
+{
+    if (threadIdx.x != 0) return;
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+        for (int q = 0; q < 4; ++q) acc[q] += partial[b * 4 + q];
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = (have_prev && acc[3] > 0) ? sqrt(acc[2] / acc[3]) : 0.0;
+}
+
+// -------------------------------------------------------------------------
+// layout conversions
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void k_canon_to_do(Prob<T> P, const double *__restrict__ src, T *__restrict__ dst, long long c0,
+                              long long nc)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int G = P.G, N = P.N;
+    long long n = nc * G * N;
+    if (i >= n) return;
+    int k = (int)(i % N);
+    long long cg = i / N;
+    int g = (int)(cg % G);
+    long long c = c0 + cg / G;
+    int ix, iy, iz;
+    node_xyz(c, P.nx, P.ny, ix, iy, iz);
+    dst[((long long)k * G + g) * P.Nc + perm_offset(P.ord[k].d, ix, iy, iz, P.nx, P.ny, P.nz)] = (T)src[i];
+}
+
+template <class T>
+__global__ void k_do_to_canon(Prob<T> P, const T *__restrict__ src, double *__restrict__ dst, long long c0,
+                              long long nc)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int G = P.G, N = P.N;
+    long long n = nc * G * N;
+    if (i >= n) return;
+    int k = (int)(i % N);
+    long long cg = i / N;
+    int g = (int)(cg % G);
+    long long c = c0 + cg / G;
+    int ix, iy, iz;
+    node_xyz(c, P.nx, P.ny, ix, iy, iz);
+    dst[i] = (double)src[((long long)k * G + g) * P.Nc + perm_offset(P.ord[k].d, ix, iy, iz, P.nx, P.ny, P.nz)];
+}
+
+template <class T>
+__global__ void k_convert(const double *__restrict__ src, T *__restrict__ dst, long long n)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (T)src[i];
+}
+
+template <class T>
+__global__ void k_convert_back(const T *__restrict__ src, double *__restrict__ dst, long long n)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+
+// -------------------------------------------------------------------------
+// Klein-Nishina multigroup table (Sec. 2.3, eq:comptoncross), FP64, one
+// thread per (final group g, incident group g'):
+//   K_l[g][g'] = (2 pi / de_g) Int_{g'} d eps Int d mu P_l(mu) dsigma/dOmega (eps1/eps) 1[eps1 in g]
+//   sigma_out[g'] = (1/de_g') Int_{g'} sigma_KN(eps) d eps        (sigma_T units)
+// dsigma/dOmega = (3/16pi) r^2 (1/r + r - sin^2), r = eps1/eps = 1/(1+eps(1-mu)).
+// Angles are integrated in ln(eps1) (mu = 1 + 1/eps - 1/eps1), energies in
+// ln(eps), each on pieces split where a group edge stops being reachable.
+// -------------------------------------------------------------------------
+__device__ inline double kn_angle_integral(int l, double eps, double lo, double hi, int weighted,
+                                           const double *gx, const double *gw, int nq)
+{
+    double s0 = log(lo), s1 = log(hi);
+    double hs = 0.5 * (s1 - s0), ms = 0.5 * (s1 + s0);
+    double acc = 0.0;
+    for (int i = 0; i < nq; ++i) {
+        double e1 = exp(ms + hs * gx[i]);
+        double mu = 1.0 + 1.0 / eps - 1.0 / e1;
+        mu = fmin(1.0, fmax(-1.0, mu));
+        double r = e1 / eps;
+        double dsdo = 3.0 / (16.0 * kPi) * r * r * (1.0 / r + r - (1.0 - mu * mu));
+        // Legendre P_l(mu) by recurrence
+        double pl = 1.0;
+        if (l >= 1) {
+            double p0 = 1.0, p1 = mu;
+            for (int j = 2; j <= l; ++j) {
+                double p2 = ((2.0 * j - 1.0) * mu * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            pl = p1;
+        }
+        double f = pl * dsdo / e1;
+        if (weighted) f *= r;
+        acc += gw[i] * f;
+    }
+    return acc * hs;
+}
+
+__global__ void k_kn_table(int G, const double *edges, int L, double *K, double *sigma_out, const double *gx,
+                           const double *gw, int nq)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G * G) return;
+    int g = idx / G, gp = idx - g * G;
+    double ea = edges[gp], eb = edges[gp + 1];
+    // breakpoints of the incident-energy integral
+    double bp[2 * 257 + 2];
+    int nb = 0;
+    bp[nb++] = ea;
+    bp[nb++] = eb;
+    for (int j = 0; j <= G; ++j) {
+        double e = edges[j];
+        if (e > ea && e < eb) bp[nb++] = e;
+        if (e < 0.5) {
+            double e2 = e / (1.0 - 2.0 * e);
+            if (e2 > ea && e2 < eb) bp[nb++] = e2;
+        }
+    }
+    for (int i = 1; i < nb; ++i) {  // insertion sort
+        double v = bp[i];
+        int j = i - 1;
+        while (j >= 0 && bp[j] > v) { bp[j + 1] = bp[j]; --j; }
+        bp[j + 1] = v;
+    }
+    double acc[16];
+    for (int l = 0; l <= L; ++l) acc[l] = 0.0;
+    double tot = 0.0;
+    for (int sgm = 0; sgm + 1 < nb; ++sgm) {
+        if (!(bp[sgm + 1] > bp[sgm])) continue;
+        double t0 = log(bp[sgm]), t1 = log(bp[sgm + 1]);
+        double ht = 0.5 * (t1 - t0), mt = 0.5 * (t1 + t0);
+        for (int i = 0; i < nq; ++i) {
+            double eps = exp(mt + ht * gx[i]);
+            double wq = gw[i] * ht * eps;
+            double e1min = eps / (1.0 + 2.0 * eps), e1max = eps;
+            if (g == 0) tot += wq * 2.0 * kPi * kn_angle_integral(0, eps, e1min, e1max, 0, gx, gw, nq);
+            double lo = fmax(edges[g], e1min), hi = fmin(edges[g + 1], e1max);
+            if (!(hi > lo)) continue;
+            for (int l = 0; l <= L; ++l) acc[l] += wq * kn_angle_integral(l, eps, lo, hi, 1, gx, gw, nq);
+        }
+    }
+    double norm = 2.0 * kPi / (edges[g + 1] - edges[g]);
+    for (int l = 0; l <= L; ++l) K[((size_t)l * G + g) * G + gp] = acc[l] * norm;
+    if (g == 0) sigma_out[gp] = tot / (eb - ea);
+}
+
+// -------------------------------------------------------------------------
+// launchers
+// -------------------------------------------------------------------------
+static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+size_t project_smem_bytes(const shd_ctx *c)
+{
+    return (size_t)c->esize * ((size_t)2 * c->G * c->N + 2 * c->G);
+}
+size_t sh2lab_smem_bytes(const shd_ctx *c)
+{
+    return (size_t)c->esize * ((size_t)c->G * c->N + 3 * c->G);
+}
+static int sweep_plane_max(const shd_ctx *c)
+{
+    int a = c->nx * c->ny, b = c->ny * c->nz, d = c->nx * c->nz;
+    int m = a > b ? a : b;
+    return m > d ? m : d;
+}
+size_t sweep_smem_bytes(const shd_ctx *c) { return (size_t)3 * c->esize * sweep_plane_max(c); }
+
+template <class T>
+cudaError_t launch_chi0(const shd_ctx *ctx, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    long long n = ctx->Nc * ctx->G;
+    k_chi0<T><<<blocks_for(n, 256), 256, 0, st>>>(P, (T *)ctx->d_chi0);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    size_t sm = project_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_project<T><<<(unsigned)ctx->Nc, 256, sm, st>>>(P, I, Ip, mom);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_source(const shd_ctx *ctx, const T *Ip, T *Sp, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    long long n = ctx->Nc * ctx->G * ctx->NLM;
+    k_source<T><<<blocks_for(n, 256), 256, 0, st>>>(P, Ip, Sp);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    size_t sm = sh2lab_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_sh2lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sh2lab<T><<<(unsigned)ctx->Nc, 256, sm, st>>>(P, Sp, eta, chi);
+    return cudaGetLastError();
+}
+
+template <class T, int NPT>
+static cudaError_t launch_sweep_npt(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st,
+                                    int threads)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    size_t sm = sweep_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<T, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sweep<T, NPT><<<(unsigned)(ctx->N * ctx->G), threads, sm, st>>>(P, I, eta, chi);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st)
+{
+    int plane = sweep_plane_max(ctx);
+    int threads = plane < 1024 ? ((plane + 31) / 32) * 32 : 1024;
+    int npt = (plane + threads - 1) / threads;
+    if (npt <= 1) return launch_sweep_npt<T, 1>(ctx, I, eta, chi, st, threads);
+    if (npt <= 2) return launch_sweep_npt<T, 2>(ctx, I, eta, chi, st, threads);
+    if (npt <= 4) return launch_sweep_npt<T, 4>(ctx, I, eta, chi, st, threads);
+    if (npt <= 8) return launch_sweep_npt<T, 8>(ctx, I, eta, chi, st, threads);
+    if (npt <= 16) return launch_sweep_npt<T, 16>(ctx, I, eta, chi, st, threads);
+    return cudaErrorInvalidConfiguration;
+}
+
+template <class T>
+cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev, bool have_prev, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    int nb = ctx->n_partial;
+    k_sums_partial<T><<<nb, 256, 0, st>>>(P, mom, Sp, Sprev, have_prev ? 1 : 0, ctx->d_partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sums_final<<<1, 32, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_canon_to_do(const shd_ctx *ctx, const double *src, T *dst, long long c0, long long nc,
+                               cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    long long n = nc * ctx->G * ctx->N;
+    if (n == 0) return cudaSuccess;
+    k_canon_to_do<T><<<blocks_for(n, 256), 256, 0, st>>>(P, src, dst, c0, nc);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_do_to_canon(const shd_ctx *ctx, const T *src, double *dst, long long c0, long long nc,
+                               cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    long long n = nc * ctx->G * ctx->N;
+    if (n == 0) return cudaSuccess;
+    k_do_to_canon<T><<<blocks_for(n, 256), 256, 0, st>>>(P, src, dst, c0, nc);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_convert(const double *src, T *dst, long long n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_convert<T><<<blocks_for(n, 256), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_convert_back(const T *src, double *dst, long long n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_convert_back<T><<<blocks_for(n, 256), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, double *d_sigma_out,
+                            const double *d_gx, const double *d_gw, int nq, cudaStream_t st)
+{
+    k_kn_table<<<blocks_for((long long)G * G, 64), 64, 0, st>>>(G, d_edges, L, d_K, d_sigma_out, d_gx, d_gw, nq);
+    return cudaGetLastError();
+}
+
+#define SHD_INSTANTIATE(T)                                                                                  \
+    template Prob<T> make_prob<T>(const shd_ctx *);                                                         \
+    template cudaError_t launch_chi0<T>(const shd_ctx *, cudaStream_t);                                     \
+    template cudaError_t launch_project<T>(const shd_ctx *, const T *, T *, T *, cudaStream_t);             \
+    template cudaError_t launch_source<T>(const shd_ctx *, const T *, T *, cudaStream_t);                   \
+    template cudaError_t launch_sh2lab<T>(const shd_ctx *, const T *, T *, T *, cudaStream_t);              \
+    template cudaError_t launch_sweep<T>(const shd_ctx *, T *, const T *, const T *, cudaStream_t);         \
+    template cudaError_t launch_sums<T>(shd_ctx *, const T *, const T *, const T *, bool, cudaStream_t);    \
+    template cudaError_t launch_canon_to_do<T>(const shd_ctx *, const double *, T *, long long, long long,  \
+                                               cudaStream_t);                                               \
+    template cudaError_t launch_do_to_canon<T>(const shd_ctx *, const T *, double *, long long, long long,  \
+                                               cudaStream_t);                                               \
+    template cudaError_t launch_convert<T>(const double *, T *, long long, cudaStream_t);                   \
+    template cudaError_t launch_convert_back<T>(const T *, double *, long long, cudaStream_t);
+
+SHD_INSTANTIATE(double)
+SHD_INSTANTIATE(float)
+
+}  // namespace shd

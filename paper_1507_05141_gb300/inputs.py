@@ -221,3 +221,64 @@ def ragged_mixed(grid=(11, 9, 7), G=5, L=3, gmax=3.0, seed=None, index=7, scatte
     nmu, nphi = ordinate_counts(L)
     return ProblemSpec("ragged_mixed", grid, (1.0, 1.2, 0.9), L, nmu, nphi, edges, alpha0, ne, u,
                        emis0, scattering, kappa=1.0 / (0.5 * hx), steps=3)
+
+
+# ----------------------------------------------------------------------------
+# counter-based seeded intensities, computable for any element on either side
+# ----------------------------------------------------------------------------
+# value(i) = 0.5 + fmix32((i + seed * 0x9E3779B9) mod 2^32) / 2^32 for the
+# flat index i = (c*G + g)*N + k of the [c][g][k] layout; fmix32 is the
+# MurmurHash3 32-bit finaliser.  Products are split so that every
+# intermediate fits in a signed 64-bit integer (numpy and torch alike).
+
+_M32 = 0xFFFFFFFF
+
+
+def _mul32(h, c):
+    lo = h & 0xFFFF
+    hi = h >> 16
+    return ((lo * c) + (((hi * c) & 0xFFFF) << 16)) & _M32
+
+
+def _fmix32(h):
+    h = h ^ (h >> 16)
+    h = _mul32(h, 0x85EBCA6B)
+    h = h ^ (h >> 13)
+    h = _mul32(h, 0xC2B2AE35)
+    h = h ^ (h >> 16)
+    return h
+
+
+def _hash_unit(idx, seed):
+    h = _fmix32((idx + seed * 0x9E3779B9) & _M32)
+    h = h.double() if hasattr(h, "double") else h.astype(np.float64)  # torch or numpy
+    return 0.5 + h / 4294967296.0
+
+
+def hash_state_numpy(spec: ProblemSpec, seed: int, nodes=None):
+    """Seeded intensity [len(nodes)][G][N] (all nodes when nodes is None)."""
+    nodes = np.arange(spec.Nc) if nodes is None else np.asarray(nodes)
+    per = spec.G * spec.N
+    idx = nodes.astype(np.int64)[:, None] * per + np.arange(per, dtype=np.int64)[None, :]
+    return _hash_unit(idx, int(seed)).reshape(len(nodes), spec.G, spec.N)
+
+
+def hash_state_torch(spec: ProblemSpec, seed: int, device="cuda", chunk=1 << 26):
+    """The same seeded intensity as one flat FP64 tensor on ``device``."""
+    import torch
+    n = spec.Nc * spec.G * spec.N
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        idx = torch.arange(s, e, dtype=torch.int64, device=device)
+        out[s:e] = _hash_unit(idx, int(seed))
+    return out
+
+
+def sub_spec(spec: ProblemSpec, nodes):
+    """The per-node fields of a subset of nodes as a (len, 1, 1) problem, for
+    checks of the per-node stages (projection, source, transforms)."""
+    nodes = np.asarray(nodes)
+    return ProblemSpec(spec.name + "_sub", (len(nodes), 1, 1), spec.box, spec.L, spec.nmu, spec.nphi,
+                       spec.edges, spec.alpha0[nodes], spec.ne[nodes], spec.u[nodes], spec.emis0[nodes],
+                       spec.scattering, spec.kappa, spec.steps, dict(spec.extra))

@@ -1,0 +1,206 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+FP64 path: 1e-10 relative (the plain-FP64 bar).  FP32 path: per-field
+relative error <= 2e-5 on one step of well-conditioned inputs (single-precision
+arithmetic over sums of up to 512 ordinates x 64 harmonics).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1507_05141_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 2e-5
+
+
+def _native():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_05141_gb300 import native
+    return native
+
+
+def _oracle_tables(spec, kind):
+    if kind == "thomson":
+        return O.thomson_table(spec.G, spec.L)
+    if kind == "iso":
+        return O.iso_table(spec.G, spec.L)
+    return O.kn_table(spec.edges, spec.L)
+
+
+def _oracle(spec, kind=None, kappa=None):
+    kind = kind or spec.scattering
+    K, so = _oracle_tables(spec, kind)
+    return O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
+                           alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=K, sigma_out=so,
+                           kappa=spec.kappa if kappa is None else kappa, box=spec.box)
+
+
+def rel(a, b, floor=0.0):
+    """max |a - b| / max(|b|), i.e. error relative to the field's scale."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    scale = max(np.max(np.abs(b)), floor)
+    return float(np.max(np.abs(a - b)) / scale) if scale > 0 else float(np.max(np.abs(a - b)))
+
+
+def rel_elem(a, b, floor_frac=1e-12):
+    """max over elements of |a - b| / |b| (elements below floor_frac * max|b| use the floor)."""
+    b = np.asarray(b)
+    den = np.maximum(np.abs(b), floor_frac * np.max(np.abs(b)))
+    return float(np.max(np.abs(np.asarray(a) - b) / den))
+
+
+@pytest.fixture(scope="module")
+def native():
+    return _native()
+
+
+@pytest.mark.parametrize("kind", ["thomson", "kn"])
+def test_scattering_table_matches_oracle(native, kind):
+    spec = inputs.ragged_mixed(G=7, L=5, scattering=kind)
+    s = native.Solver.from_spec(spec, precision="fp64")
+    K, so = s.get_scattering()
+    Kr, sor = _oracle_tables(spec, kind)
+    assert rel(K, Kr) < 1e-13
+    assert rel_elem(so, sor) < 1e-13
+
+
+@pytest.mark.parametrize("kind", ["thomson", "kn"])
+def test_stages_fp64(native, kind):
+    spec = inputs.ragged_mixed(scattering=kind)
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision="fp64")
+    rng = np.random.default_rng(11)
+    I = inputs.random_state(spec, seed=3)
+    # a1 project
+    Ish, J, H, K = s.stage_project(I)
+    Ish_r, J_r, H_r, K_r = P.project(I)
+    assert rel_elem(J, J_r) < FP64_TOL
+    assert rel(H, H_r) < FP64_TOL and rel(K, K_r) < FP64_TOL
+    assert rel(Ish, Ish_r) < FP64_TOL
+    # a2 source
+    Ssh = s.stage_source(Ish_r)
+    assert rel(Ssh, P.source(Ish_r)) < FP64_TOL
+    # a3 sh2lab on a random (signed) source expansion
+    Sp = rng.normal(size=Ish_r.shape) * 0.1
+    Sp[..., 0] = 1.0 + rng.random(Sp.shape[:2])
+    eta, chi = s.stage_sh2lab(Sp)
+    eta_r, chi_r = P.sh2lab(Sp)
+    assert rel(eta, eta_r) < FP64_TOL
+    assert rel_elem(chi, chi_r) < FP64_TOL
+    # a4 sweep on positive random inputs
+    eta4 = rng.random(I.shape) * 3.0
+    chi4 = rng.random(I.shape) * 20.0 + 1e-3
+    out = s.stage_sweep(I, eta4, chi4)
+    out_r = P.sweep(I, eta4, chi4)
+    assert rel_elem(out, out_r, 1e-14) < FP64_TOL
+
+
+@pytest.mark.parametrize("kind", ["thomson", "kn", "iso"])
+def test_steps_fp64(native, kind):
+    spec = inputs.ragged_mixed(scattering=kind)
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision="fp64")
+    I0 = inputs.random_state(spec, seed=5)
+    s.set_state(I0)
+    s.step(spec.steps)
+    I_gpu = s.get_state()
+    J, H, K = s.moments()
+    e_g, p_g, r_g = s.sums()
+    I_ref, _, sums_ref = P.step(I0, spec.steps)
+    _, J_r, H_r, K_r = P.project(I_ref)
+    assert rel_elem(I_gpu, I_ref, 1e-13) < FP64_TOL
+    assert rel_elem(J, J_r) < FP64_TOL
+    f = O.moments_to_eddington(J, K)
+    f_r = O.moments_to_eddington(J_r, K_r)
+    assert np.max(np.abs(f - f_r)) < FP64_TOL
+    assert abs(e_g - sums_ref[0]) <= FP64_TOL * abs(sums_ref[0])
+    assert abs(p_g - sums_ref[1]) <= FP64_TOL * abs(sums_ref[1])
+    assert abs(r_g - sums_ref[2]) <= 1e-8 * abs(sums_ref[2]) + 1e-14
+
+
+def test_vacuum_boundaries_and_time_term_fp64(native):
+    """Equilibrium with isotropic inflow B: the GPU keeps I = B exactly too."""
+    spec = inputs.ragged_mixed(scattering="iso")
+    G = spec.G
+    B = np.linspace(0.5, 2.0, G)
+    s = native.Solver.from_spec(spec, precision="fp64")
+    s.set_boundary(native.BC_ISO, B)
+    eta = spec.alpha0[:, :, None] * B[None, :, None] * np.ones((1, 1, spec.N)) * 3.0
+    chi = eta / B[None, :, None]
+    I = np.broadcast_to(B[None, :, None], eta.shape)
+    out = s.stage_sweep(I, eta, chi)
+    assert np.allclose(out, I, rtol=1e-14)
+
+
+def test_static_relax_box_fp64(native):
+    """Isotropic scattering box (16^3, L=3, 8x16, tau 5, albedo 1/2): Lambda
+    iteration to 1e-6, then 10 time steps with c dt = half a cell."""
+    spec = inputs.relax_box()
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision="fp64")
+    s.zero_state()
+    it_g, r_g = s.solve_static(1e-6, 500)
+    I_ref, it_r, r_r = P.solve_static(tol=1e-6, max_iter=500)
+    assert it_g == it_r
+    I_gpu = s.get_state()
+    assert rel_elem(I_gpu, I_ref, 1e-13) < FP64_TOL
+    s.step(spec.steps)
+    I_gpu = s.get_state()
+    I_ref, _, _ = P.step(I_ref, spec.steps)
+    assert rel_elem(I_gpu, I_ref, 1e-13) < FP64_TOL
+    J, H, K = s.moments()
+    _, J_r, _, K_r = P.project(I_ref)
+    assert rel_elem(J, J_r) < FP64_TOL
+    f = O.moments_to_eddington(J, K)
+    assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < FP64_TOL
+    # thick static limit: interior Eddington factor near 1/3
+    c = (8 * 16 + 8) * 16 + 8
+    assert np.allclose(f[c, 0, :3], 1 / 3, atol=0.02)
+
+
+@pytest.mark.parametrize("kind", ["thomson", "kn"])
+def test_steps_fp32(native, kind):
+    spec = inputs.ragged_mixed(scattering=kind)
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision="fp32")
+    I0 = inputs.random_state(spec, seed=5)
+    s.set_state(I0)
+    s.step(1)
+    J, H, K = s.moments()
+    I_ref, _, _ = P.step(I0, 1)
+    _, J_r, H_r, K_r = P.project(I_ref)
+    assert rel_elem(J, J_r) < FP32_TOL
+    assert rel(H, H_r) < FP32_TOL
+    f = O.moments_to_eddington(J, K)
+    assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < FP32_TOL
+
+
+def test_jet_full_size_projection_sampled(native):
+    """64^3 nodes, 16 groups, L=7, 16x32 ordinates (the jet workload) in the
+    benchmark's FP32 configuration: the projection of a seeded state at
+    sampled nodes against the oracle."""
+    import torch
+    spec = inputs.jet()
+    s = native.Solver.from_spec(spec, precision="fp32")
+    dev = inputs.hash_state_torch(spec, seed=9, device="cuda")
+    s.set_state_dev(dev)
+    del dev
+    J, H, K, Ish = s.moments(with_sh=True)
+    rng = np.random.default_rng(0)
+    nodes = np.sort(rng.choice(spec.Nc, size=48, replace=False))
+    moving = np.nonzero(np.any(spec.u != 0, axis=1))[0]
+    nodes = np.unique(np.concatenate([nodes, moving[:: max(1, len(moving) // 16)][:16]]))
+    sub = inputs.sub_spec(spec, nodes)
+    Psub = _oracle(sub)
+    I_sub = inputs.hash_state_numpy(spec, seed=9, nodes=nodes)
+    Ish_r, J_r, H_r, K_r = Psub.project(I_sub)
+    assert rel_elem(J[nodes], J_r) < FP32_TOL
+    assert rel(H[nodes], H_r) < FP32_TOL
+    assert rel(Ish[nodes], Ish_r) < 5 * FP32_TOL
+    torch.cuda.synchronize()
