@@ -93,7 +93,7 @@ int shd_set_grid(shd_ctx *ctx, int nx, int ny, int nz, double lx, double ly, dou
 
 /* Angular order L (NLM = (L+1)^2 harmonics, Sec. 2.3) and the ordinate mesh
  * n_mu x n_phi (Sec. 2.2 (theta, phi) mesh).  Requires n_mu >= L+1 and
- * n_phi >= 2L+1 (discrete orthogonality of the harmonics), L <= 15,
+ * n_phi >= 2L+1 (discrete orthogonality of the harmonics), L <= 9,
  * n_mu*n_phi <= 4096. */
 int shd_set_angles(shd_ctx *ctx, int L, int n_mu, int n_phi);
 
@@ -133,9 +133,11 @@ int shd_set_state(shd_ctx *ctx, const double *I);
 int shd_get_state(shd_ctx *ctx, double *I);
 
 /* Run `nsteps` time steps, one source iteration each (stages a1..a5), on
- * `cuda_stream` (a cudaStream_t; NULL = the context's own stream).  Returns
- * once the work is enqueued.  The state must have been set (or zeroed by
- * shd_zero_state). */
+ * `cuda_stream` (a cudaStream_t; NULL = the context's own stream, which is a
+ * non-blocking stream: pass cudaStreamLegacy to run on the legacy default
+ * stream).  The steps are ordered after all earlier work of the context and
+ * before its later calls.  Returns once the work is enqueued.  The state must
+ * have been set (or zeroed by shd_zero_state). */
 int shd_step(shd_ctx *ctx, int nsteps, void *cuda_stream);
 
 /* Zero the intensity state on the device. */
@@ -168,7 +170,10 @@ int shd_stage_sweep(shd_ctx *ctx, const double *I_old, const double *eta_lab, co
                     double *I_new);
 
 /* Device-pointer forms for callers that own device memory (e.g. PyTorch).
- * dev_I points to Nc*G*N doubles in the [c][g][k] layout on ctx's device. */
+ * dev_I points to Nc*G*N doubles in the [c][g][k] layout on ctx's device;
+ * the copy runs on cuda_stream (the stream that produced / will consume
+ * dev_I; NULL = the context's stream, cudaStreamLegacy = the legacy default
+ * stream) and is ordered before the context's later calls. */
 int shd_set_state_dev(shd_ctx *ctx, const double *dev_I, void *cuda_stream);
 int shd_get_state_dev(shd_ctx *ctx, double *dev_I, void *cuda_stream);
 

@@ -147,7 +147,8 @@ void free_all(shd_ctx *c)
     void **ptrs[] = {&c->d_ord, &c->d_W, &c->d_dirs, &c->d_Y, &c->d_mu, (void **)&c->d_edges, (void **)&c->d_centre,
                      &c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
                      &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
-                     (void **)&c->d_sums, (void **)&c->d_partial, (void **)&c->d_stage};
+                     (void **)&c->d_sums, (void **)&c->d_partial, (void **)&c->d_stage,
+                     &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag, &c->d_Bproj, &c->d_buf};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
 }
@@ -179,8 +180,11 @@ void drop_sized(shd_ctx *c)
 {
     void **ptrs[] = {&c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
                      &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
-                     (void **)&c->d_partial, (void **)&c->d_stage};
+                     (void **)&c->d_partial, (void **)&c->d_stage,
+                     &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag, &c->d_buf};
     for (void **p : ptrs) dfree(*p);
+    c->ntiles = 0;
+    c->nmoving = 0;
     c->have_fields = c->have_scat = c->have_state = false;
     c->bc_mode = SHD_BC_VACUUM;
     c->sprev_valid = false;
@@ -219,10 +223,31 @@ void build_geometry(shd_ctx *c)
     }
 }
 
+// Projection matrix of stage a1, [N][NB]: W_k Y_p(n_k) for p < NLM, then the
+// ten moment weights W_k {1, n_x, n_y, n_z, n_x^2, n_y^2, n_z^2, n_x n_y,
+// n_x n_z, n_y n_z} / (4 pi), then zero padding to NB = 16 ceil((NLM+10)/16).
+std::vector<double> projection_matrix(const shd_ctx *c)
+{
+    int NB = c->NB;
+    std::vector<double> B((size_t)c->N * NB, 0.0);
+    for (int k = 0; k < c->N; ++k) {
+        double W = c->h_W[k];
+        const double *n = &c->h_dirs[3 * k];
+        double *row = &B[(size_t)k * NB];
+        for (int p = 0; p < c->NLM; ++p) row[p] = W * c->h_Y[(size_t)k * c->NLM + p];
+        double f[10] = {1.0, n[0], n[1], n[2], n[0] * n[0], n[1] * n[1], n[2] * n[2], n[0] * n[1], n[0] * n[2],
+                        n[1] * n[2]};
+        for (int m = 0; m < 10; ++m) row[c->NLM + m] = W * f[m] / (4.0 * kPi);
+    }
+    return B;
+}
+
 int upload_angles(shd_ctx *c)
 {
-    dfree(c->d_ord); dfree(c->d_W); dfree(c->d_dirs); dfree(c->d_Y); dfree(c->d_mu);
+    dfree(c->d_ord); dfree(c->d_W); dfree(c->d_dirs); dfree(c->d_Y); dfree(c->d_mu); dfree(c->d_Bproj);
     build_geometry(c);
+    c->NB = 16 * ((c->NLM + 10 + 15) / 16);
+    std::vector<double> Bp = projection_matrix(c);
     cudaError_t e;
     CK(cudaMalloc(&c->d_ord, sizeof(Ordinate) * c->N), "cudaMalloc ordinates");
     CK(cudaMemcpy(c->d_ord, c->h_ord.data(), sizeof(Ordinate) * c->N, cudaMemcpyHostToDevice), "copy ordinates");
@@ -231,11 +256,13 @@ int upload_angles(shd_ctx *c)
         c->d_dirs = to_device_vec<double>(c->h_dirs, c->bytes, e); CK(e, "dirs");
         c->d_Y = to_device_vec<double>(c->h_Y, c->bytes, e); CK(e, "Y");
         c->d_mu = to_device_vec<double>(c->h_mu, c->bytes, e); CK(e, "mu");
+        c->d_Bproj = to_device_vec<double>(Bp, c->bytes, e); CK(e, "Bproj");
     } else {
         c->d_W = to_device_vec<float>(c->h_W, c->bytes, e); CK(e, "W");
         c->d_dirs = to_device_vec<float>(c->h_dirs, c->bytes, e); CK(e, "dirs");
         c->d_Y = to_device_vec<float>(c->h_Y, c->bytes, e); CK(e, "Y");
         c->d_mu = to_device_vec<float>(c->h_mu, c->bytes, e); CK(e, "mu");
+        c->d_Bproj = to_device_vec<float>(Bp, c->bytes, e); CK(e, "Bproj");
     }
     return SHD_OK;
 }
@@ -271,6 +298,62 @@ int ensure_buffers(shd_ctx *c)
     if ((rc = dalloc(c, (void **)&c->d_stage, sizeof(double) * want, "staging"))) return rc;
     c->stage_elems = want;
     CK(cudaMemsetAsync(c->d_Sprev, 0, nSH * es, c->stream), "memset");
+    return SHD_OK;
+}
+
+// Make `waiter` wait for the work enqueued so far on `producer`.
+int stream_after(cudaStream_t waiter, cudaStream_t producer)
+{
+    if (waiter == producer) return SHD_OK;
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    cudaError_t e = cudaEventRecord(ev, producer);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(waiter, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+    return SHD_OK;
+}
+
+// Node bricks of the transform kernels and the list of moving nodes (u != 0),
+// brick by brick so that a brick's remap CTAs run side by side.
+int build_tiles(shd_ctx *c, const double *u)
+{
+    dfree(c->d_tiles); dfree((void *&)c->d_moving); dfree((void *&)c->d_mflag); dfree(c->d_buf);
+    int tx = (c->nx + 7) / 8, ty = (c->ny + 7) / 8;
+    std::vector<TileInfo> tiles;
+    tiles.reserve((size_t)tx * ty * c->nz);
+    std::vector<long long> moving;
+    std::vector<unsigned char> mflag((size_t)c->Nc, 0);
+    for (int z = 0; z < c->nz; ++z)
+        for (int by = 0; by < ty; ++by)
+            for (int bx = 0; bx < tx; ++bx) {
+                TileInfo t{8 * bx, 8 * by, z, 0};
+                for (int r = 0; r < 64; ++r) {
+                    int ix = t.x0 + (r & 7), iy = t.y0 + (r >> 3);
+                    if (ix >= c->nx || iy >= c->ny) continue;
+                    long long node = ((long long)z * c->ny + iy) * c->nx + ix;
+                    const double *un = u + 3 * node;
+                    if (un[0] != 0.0 || un[1] != 0.0 || un[2] != 0.0) {
+                        t.flags |= 1;
+                        mflag[node] = 1;
+                        moving.push_back(node);
+                    }
+                }
+                tiles.push_back(t);
+            }
+    c->ntiles = (long long)tiles.size();
+    c->nmoving = (long long)moving.size();
+    int rc;
+    if ((rc = dalloc(c, &c->d_tiles, sizeof(TileInfo) * tiles.size(), "tiles"))) return rc;
+    CK(cudaMemcpy(c->d_tiles, tiles.data(), sizeof(TileInfo) * tiles.size(), cudaMemcpyHostToDevice), "tiles");
+    if ((rc = dalloc(c, (void **)&c->d_mflag, mflag.size(), "mflag"))) return rc;
+    CK(cudaMemcpy(c->d_mflag, mflag.data(), mflag.size(), cudaMemcpyHostToDevice), "mflag");
+    if (c->nmoving > 0) {
+        if ((rc = dalloc(c, (void **)&c->d_moving, sizeof(long long) * moving.size(), "moving"))) return rc;
+        CK(cudaMemcpy(c->d_moving, moving.data(), sizeof(long long) * moving.size(), cudaMemcpyHostToDevice), "moving");
+        size_t nDO = (size_t)c->Nc * c->G * c->N;
+        if ((rc = dalloc(c, &c->d_buf, nDO * c->esize, "remap scratch"))) return rc;
+    }
     return SHD_OK;
 }
 
@@ -346,9 +429,12 @@ int ready_for_step(shd_ctx *c)
     if (!c->have_fields) return fail(SHD_ERR_STATE, "fields not set");
     if (!c->have_scat) return fail(SHD_ERR_STATE, "scattering not set");
     size_t limit = 227 * 1024;
-    if (project_smem_bytes(c) > limit || sh2lab_smem_bytes(c) > limit)
-        return fail(SHD_ERR_ARG, "groups x ordinates too large for the per-node kernels (%zu bytes shared memory)",
-                    project_smem_bytes(c));
+    if (remap_smem_bytes(c) > limit)
+        return fail(SHD_ERR_ARG, "groups x ordinates too large for the remap kernels (%zu bytes shared memory)",
+                    remap_smem_bytes(c));
+    if (sh2lab_tile_smem_bytes(c) > limit)
+        return fail(SHD_ERR_ARG, "too many harmonics for the sh2lab kernel (%zu bytes shared memory)",
+                    sh2lab_tile_smem_bytes(c));
     if (sweep_smem_bytes(c) > limit) return fail(SHD_ERR_ARG, "grid planes too large for the sweep kernel");
     return SHD_OK;
 }
@@ -449,7 +535,7 @@ int shd_set_angles(shd_ctx *c, int L, int n_mu, int n_phi)
 {
     int rc = ctx_check(c);
     if (rc) return rc;
-    if (L < 0 || L > 15) return fail(SHD_ERR_ARG, "L must be in [0, 15]");
+    if (L < 0 || L > 9) return fail(SHD_ERR_ARG, "L must be in [0, 9]");
     if (n_mu < L + 1 || n_phi < 2 * L + 1) return fail(SHD_ERR_ARG, "need n_mu >= L+1 and n_phi >= 2L+1");
     if (n_mu < 1 || n_phi < 1 || (long long)n_mu * n_phi > 4096) return fail(SHD_ERR_ARG, "n_mu*n_phi must be in [1, 4096]");
     drop_sized(c);
@@ -520,6 +606,7 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         if ((rc = upload_reals<float>(c, u, c->d_u, 3 * c->Nc))) return rc;
         if ((rc = upload_reals<float>(c, emis0, c->d_emis0, nCG))) return rc;
     }
+    if ((rc = build_tiles(c, u))) return rc;
     c->have_fields = true;
     if (c->have_scat) {
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
@@ -672,9 +759,11 @@ int shd_set_state_dev(shd_ctx *c, const double *dev_I, void *stream)
     if (!dev_I) return fail(SHD_ERR_ARG, "dev_I is NULL");
     if ((rc = ensure_buffers(c))) return rc;
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    if ((rc = stream_after(st, c->stream))) return rc;
     rc = is_fp64(c) ? set_state_impl<double>(c, dev_I, false, st, (double *)c->d_I)
                     : set_state_impl<float>(c, dev_I, false, st, (float *)c->d_I);
     if (rc) return rc;
+    if ((rc = stream_after(c->stream, st))) return rc;
     c->have_state = true;
     c->sprev_valid = false;
     return SHD_OK;
@@ -708,6 +797,7 @@ int shd_get_state_dev(shd_ctx *c, double *dev_I, void *stream)
     if (!dev_I) return fail(SHD_ERR_ARG, "dev_I is NULL");
     if (!c->have_state) return fail(SHD_ERR_STATE, "state not set");
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    if ((rc = stream_after(st, c->stream))) return rc;
     return is_fp64(c) ? get_state_impl<double>(c, (const double *)c->d_I, dev_I, false, st)
                       : get_state_impl<float>(c, (const float *)c->d_I, dev_I, false, st);
 }
@@ -720,24 +810,11 @@ int shd_step(shd_ctx *c, int nsteps, void *stream)
     if ((rc = ready_for_step(c))) return rc;
     if (!c->have_state) return fail(SHD_ERR_STATE, "state not set");
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
-    if (st != c->stream) {
-        // order against the library's own stream (uploads) in both directions
-        cudaEvent_t ev;
-        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
-        CK(cudaEventRecord(ev, c->stream), "event");
-        CK(cudaStreamWaitEvent(st, ev, 0), "wait");
-        cudaEventDestroy(ev);
-    }
+    // order against the library's own stream (uploads, reads) both ways
+    if ((rc = stream_after(st, c->stream))) return rc;
     rc = is_fp64(c) ? run_steps<double>(c, nsteps, st) : run_steps<float>(c, nsteps, st);
     if (rc) return rc;
-    if (st != c->stream) {
-        cudaEvent_t ev;
-        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
-        CK(cudaEventRecord(ev, st), "event");
-        CK(cudaStreamWaitEvent(c->stream, ev, 0), "wait");
-        cudaEventDestroy(ev);
-    }
-    return SHD_OK;
+    return stream_after(c->stream, st);
 }
 
 int shd_solve_static(shd_ctx *c, double rel_tol, int max_iter, int *iters_out, double *resid_out)

@@ -37,6 +37,12 @@ struct Ordinate {
     int ring, phi;   // (a, b) mesh indices
 };
 
+// An 8 x 8 brick of nodes in (x, y) at one z (the unit of the transform
+// kernels); flags bit 0: the brick holds at least one moving node.
+struct TileInfo {
+    int x0, y0, z, flags;
+};
+
 // Everything a kernel needs about the problem, passed by value.
 template <class T>
 struct Prob {
@@ -60,6 +66,13 @@ struct Prob {
     const T *sigma_out;    // [G]
     int bc_mode;
     const T *bc;           // ISO: [G]; FULL: DO layout
+    const TileInfo *tiles; // [ntiles]
+    long long ntiles;
+    const long long *moving;      // [nmoving] node ids with u != 0, brick by brick
+    long long nmoving;
+    const unsigned char *mflag;   // [Nc] 1 where u != 0
+    const T *Bproj;        // [N][NB]: W_k Y_p(n_k) | W_k {1, n, nn}/(4 pi) | 0
+    int NB;
 };
 
 // Per-stage CUDA events recorded on the launching stream without any host
@@ -110,6 +123,14 @@ struct shd_ctx {
     double *d_sums = nullptr;     // [3] energy, photons, resid
     double *d_partial = nullptr;  // reduction scratch
     int n_partial = 0;
+    void *d_tiles = nullptr;          // TileInfo[ntiles]
+    long long ntiles = 0;
+    long long *d_moving = nullptr;    // moving node ids
+    long long nmoving = 0;
+    unsigned char *d_mflag = nullptr; // [Nc]
+    void *d_Bproj = nullptr;          // [N][NB]
+    int NB = 0;
+    void *d_buf = nullptr;            // DO-layout scratch: I0 / S0 of moving nodes
     double *d_stage = nullptr;    // staging buffer for host <-> device copies (FP64)
     size_t stage_elems = 0;
     long long bytes = 0;
@@ -361,8 +382,8 @@ cudaError_t launch_convert_back(const T *src, double *dst, long long n, cudaStre
 cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, double *d_sigma_out,
                             const double *d_gx, const double *d_gw, int nq, cudaStream_t st);
 
-size_t project_smem_bytes(const shd_ctx *ctx);
-size_t sh2lab_smem_bytes(const shd_ctx *ctx);
+size_t remap_smem_bytes(const shd_ctx *ctx);
+size_t sh2lab_tile_smem_bytes(const shd_ctx *ctx);
 size_t sweep_smem_bytes(const shd_ctx *ctx);
 
 }  // namespace shd

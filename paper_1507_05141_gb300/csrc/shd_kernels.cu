@@ -1,9 +1,8 @@
 // Kernels of one source iteration (stages a1..a5) for FP64 and FP32.
 //
-//   k_project   a1  lab -> comoving remap, SH projection, lab moments
 //   k_source    a2  comoving SH source with the group-to-group kernel
-//   k_sh2lab    a3  SH -> comoving ordinates -> laboratory eta, chi
 //   k_sweep     a4  short-characteristic transfer, plane by plane
+// (a1 project and a3 sh2lab are in shd_transforms.cu)
 //   k_sums_*    a5  FP64 diagnostics (deterministic two-pass reductions)
 //
 // Paper passages: Sec. 2 (eq:shdom, Lambda iteration, SH <-> DO transforms),
@@ -29,6 +28,9 @@ Prob<T> make_prob(const shd_ctx *c)
     p.emis0 = (const T *)c->d_emis0; p.chi0 = (const T *)c->d_chi0;
     p.K = (const T *)c->d_K; p.sigma_out = (const T *)c->d_sigma_out;
     p.bc_mode = c->bc_mode; p.bc = (const T *)c->d_bc;
+    p.tiles = (const TileInfo *)c->d_tiles; p.ntiles = c->ntiles;
+    p.moving = c->d_moving; p.nmoving = c->nmoving; p.mflag = c->d_mflag;
+    p.Bproj = (const T *)c->d_Bproj; p.NB = c->NB;
     return p;
 }
 
@@ -52,99 +54,6 @@ __global__ void k_chi0(Prob<T> P, T *chi0)
     long long c = i / P.G;
     int g = (int)(i % P.G);
     chi0[i] = P.alpha0[i] + P.ne[c] * P.sigma_out[g];
-}
-
-// -------------------------------------------------------------------------
-// a1: one CTA per node.  Shared memory holds the node's laboratory
-// intensities [G][N] and, for a moving node, the comoving ones [G][N].
-// -------------------------------------------------------------------------
-template <class T>
-__global__ void k_project(Prob<T> P, const T *__restrict__ I, T *__restrict__ Ip, T *__restrict__ mom)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sI = reinterpret_cast<T *>(smem_raw);
-    const int G = P.G, N = P.N, NLM = P.NLM;
-    T *sI0 = sI + (size_t)G * N;
-    T *spole = sI0 + (size_t)G * N;  // [G][2]
-    const long long c = blockIdx.x;
-    int ix, iy, iz;
-    node_xyz(c, P.nx, P.ny, ix, iy, iz);
-    long long off[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) off[d] = perm_offset(d, ix, iy, iz, P.nx, P.ny, P.nz);
-
-    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
-        int g = i / N, k = i - g * N;
-        sI[i] = I[((long long)k * G + g) * P.Nc + off[P.ord[k].d]];
-    }
-    const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
-    const bool moving = !(u[0] == T(0) && u[1] == T(0) && u[2] == T(0));
-    __syncthreads();
-    const T *src = sI;
-    if (moving) {
-        for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
-            int g = i >> 1, r = i & 1;
-            const T *F = sI + (size_t)g * N + (r ? (P.nmu - 1) * P.nphi : 0);
-            T s = 0;
-            for (int j = 0; j < P.nphi; ++j) s += F[j];
-            spole[i] = s / T(P.nphi);
-        }
-        __syncthreads();
-        for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
-            T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
-            T n[3];
-            T q = boost_dir<T>(u, n0, n, T(-1));  // nu/nu0
-            Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n);
-            T iq3 = T(1) / (q * q * q);
-            for (int g0 = 0; g0 < G; ++g0) {
-                double eps = P.centre[g0] * (double)q;
-                FreqBracket fb = freq_bracket(P.edges, P.centre, G, eps);
-                T v = 0;
-                if (fb.mode == 1) {
-                    v = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
-                } else if (fb.mode == 2) {
-                    T fa = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
-                    T fbv = eval_stencil<T>(st, sI + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
-                    v = freq_mix<T>(fa, fbv, (T)fb.t);
-                }
-                sI0[(size_t)g0 * N + k0] = v * iq3;
-            }
-        }
-        __syncthreads();
-        src = sI0;
-    }
-    // I_p(g) = sum_k W_k Y_p(n_k) I0(k, g)
-    for (int i = threadIdx.x; i < G * NLM; i += blockDim.x) {
-        int g = i / NLM, p = i - g * NLM;
-        const T *F = src + (size_t)g * N;
-        T s = 0;
-        for (int k = 0; k < N; ++k) s += P.W[k] * P.Y[(size_t)k * NLM + p] * F[k];
-        Ip[((long long)c * G + g) * NLM + p] = s;
-    }
-    // laboratory moments (1/4pi) sum_k W_k {1, n_i, n_i n_j} I(k, g)
-    for (int i = threadIdx.x; i < G * 10; i += blockDim.x) {
-        int g = i / 10, m = i - g * 10;
-        const T *F = sI + (size_t)g * N;
-        T s = 0;
-        for (int k = 0; k < N; ++k) {
-            T n0 = P.dirs[3 * k], n1 = P.dirs[3 * k + 1], n2 = P.dirs[3 * k + 2];
-            T f;
-            switch (m) {
-                case 0: f = T(1); break;
-                case 1: f = n0; break;
-                case 2: f = n1; break;
-                case 3: f = n2; break;
-                case 4: f = n0 * n0; break;
-                case 5: f = n1 * n1; break;
-                case 6: f = n2 * n2; break;
-                case 7: f = n0 * n1; break;
-                case 8: f = n0 * n2; break;
-                default: f = n1 * n2; break;
-            }
-            s += P.W[k] * f * F[k];
-        }
-        mom[((long long)c * G + g) * 10 + m] = s * T(1.0 / (4.0 * kPi));
-    }
 }
 
 // -------------------------------------------------------------------------
@@ -174,86 +83,6 @@ __global__ void k_source(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp
         if (p == 0) s += T(3.5449077018110320546) * P.emis0[cg] / chi;  // sqrt(4 pi)
     }
     Sp[i] = s;
-}
-
-// -------------------------------------------------------------------------
-// a3: one CTA per node.  S0 on comoving ordinates [G][N] in shared memory,
-// then every laboratory (k, g) of the node (Lorentz remap when moving).
-// -------------------------------------------------------------------------
-template <class T>
-__global__ void k_sh2lab(Prob<T> P, const T *__restrict__ Sp, T *__restrict__ eta, T *__restrict__ chi)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sS0 = reinterpret_cast<T *>(smem_raw);
-    const int G = P.G, N = P.N, NLM = P.NLM;
-    T *spole = sS0 + (size_t)G * N;  // [G][2]
-    T *schi = spole + 2 * G;         // [G]
-    const long long c = blockIdx.x;
-    int ix, iy, iz;
-    node_xyz(c, P.nx, P.ny, ix, iy, iz);
-    long long off[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) off[d] = perm_offset(d, ix, iy, iz, P.nx, P.ny, P.nz);
-
-    const T *Sc = Sp + (long long)c * G * NLM;
-    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
-        int g = i / N, k = i - g * N;
-        const T *Yk = P.Y + (size_t)k * NLM;
-        const T *Sg = Sc + (size_t)g * NLM;
-        T s = 0;
-        for (int p = 0; p < NLM; ++p) s += Yk[p] * Sg[p];
-        sS0[i] = s;
-    }
-    for (int g = threadIdx.x; g < G; g += blockDim.x) schi[g] = P.chi0[(long long)c * G + g];
-    const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
-    const bool moving = !(u[0] == T(0) && u[1] == T(0) && u[2] == T(0));
-    __syncthreads();
-    if (!moving) {
-        for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
-            int k = i / G, g = i - k * G;
-            long long o = ((long long)k * G + g) * P.Nc + off[P.ord[k].d];
-            T ch = schi[g];
-            chi[o] = ch;
-            eta[o] = ch * sS0[(size_t)g * N + k];
-        }
-        return;
-    }
-    for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
-        int g = i >> 1, r = i & 1;
-        const T *F = sS0 + (size_t)g * N + (r ? (P.nmu - 1) * P.nphi : 0);
-        T s = 0;
-        for (int j = 0; j < P.nphi; ++j) s += F[j];
-        spole[i] = s / T(P.nphi);
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
-        T n0[3];
-        T D = boost_dir<T>(u, n, n0, T(1));  // nu0/nu
-        Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n0);
-        T iD3 = T(1) / (D * D * D);
-        long long base = (long long)k * G * P.Nc + off[P.ord[k].d];
-        for (int g = 0; g < G; ++g) {
-            double eps0 = P.centre[g] * (double)D;
-            FreqBracket fb = freq_bracket(P.edges, P.centre, G, eps0);
-            T s = 0, ch;
-            if (fb.mode == 0) {
-                ch = schi[fb.ga];
-            } else if (fb.mode == 1) {
-                s = eval_stencil<T>(st, sS0 + (size_t)fb.ga * N, spole + 2 * fb.ga);
-                ch = schi[fb.ga];
-            } else {
-                T fa = eval_stencil<T>(st, sS0 + (size_t)fb.ga * N, spole + 2 * fb.ga);
-                T fbv = eval_stencil<T>(st, sS0 + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
-                s = freq_mix<T>(fa, fbv, (T)fb.t);
-                ch = freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], (T)fb.t);
-            }
-            T chl = ch * D;
-            long long o = base + (long long)g * P.Nc;
-            chi[o] = chl;
-            eta[o] = chl * s * iD3;
-        }
-    }
 }
 
 // -------------------------------------------------------------------------
@@ -528,14 +357,6 @@ __global__ void k_kn_table(int G, const double *edges, int L, double *K, double 
 // -------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-size_t project_smem_bytes(const shd_ctx *c)
-{
-    return (size_t)c->esize * ((size_t)2 * c->G * c->N + 2 * c->G);
-}
-size_t sh2lab_smem_bytes(const shd_ctx *c)
-{
-    return (size_t)c->esize * ((size_t)c->G * c->N + 3 * c->G);
-}
 static int sweep_plane_max(const shd_ctx *c)
 {
     int a = c->nx * c->ny, b = c->ny * c->nz, d = c->nx * c->nz;
@@ -554,33 +375,11 @@ cudaError_t launch_chi0(const shd_ctx *ctx, cudaStream_t st)
 }
 
 template <class T>
-cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st)
-{
-    Prob<T> P = make_prob<T>(ctx);
-    size_t sm = project_smem_bytes(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_project<T><<<(unsigned)ctx->Nc, 256, sm, st>>>(P, I, Ip, mom);
-    return cudaGetLastError();
-}
-
-template <class T>
 cudaError_t launch_source(const shd_ctx *ctx, const T *Ip, T *Sp, cudaStream_t st)
 {
     Prob<T> P = make_prob<T>(ctx);
     long long n = ctx->Nc * ctx->G * ctx->NLM;
     k_source<T><<<blocks_for(n, 256), 256, 0, st>>>(P, Ip, Sp);
-    return cudaGetLastError();
-}
-
-template <class T>
-cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st)
-{
-    Prob<T> P = make_prob<T>(ctx);
-    size_t sm = sh2lab_smem_bytes(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_sh2lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_sh2lab<T><<<(unsigned)ctx->Nc, 256, sm, st>>>(P, Sp, eta, chi);
     return cudaGetLastError();
 }
 
@@ -670,9 +469,7 @@ cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, do
 #define SHD_INSTANTIATE(T)                                                                                  \
     template Prob<T> make_prob<T>(const shd_ctx *);                                                         \
     template cudaError_t launch_chi0<T>(const shd_ctx *, cudaStream_t);                                     \
-    template cudaError_t launch_project<T>(const shd_ctx *, const T *, T *, T *, cudaStream_t);             \
     template cudaError_t launch_source<T>(const shd_ctx *, const T *, T *, cudaStream_t);                   \
-    template cudaError_t launch_sh2lab<T>(const shd_ctx *, const T *, T *, T *, cudaStream_t);              \
     template cudaError_t launch_sweep<T>(const shd_ctx *, T *, const T *, const T *, cudaStream_t);         \
     template cudaError_t launch_sums<T>(shd_ctx *, const T *, const T *, const T *, bool, cudaStream_t);    \
     template cudaError_t launch_canon_to_do<T>(const shd_ctx *, const double *, T *, long long, long long,  \

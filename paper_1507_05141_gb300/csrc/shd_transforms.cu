@@ -1,0 +1,380 @@
+// Stages a1 (project) and a3 (sh2lab) as node-tiled contractions on CUDA
+// cores, plus the Lorentz remaps of moving nodes (Sec. 2.2).
+//
+// A node tile is an 8 x 8 brick in (x, y) at one z.  In every sweep layout
+// (see shd_internal.cuh) such a brick is 8 contiguous runs of 8 nodes, so the
+// tile of one (ordinate, group) is read or written as eight 32-byte runs.
+//
+//   a1  I_lm(c,g)  = sum_k W_k Y_p(n_k) I0(c,k,g)          (Sec. 2.3 SH)
+//       moments    = sum_k W_k {1, n_i, n_i n_j}/(4 pi) I(c,k,g)
+//     as one contraction per (tile, g): [64 nodes x N] x [N x (NLM + 10)].
+//     For a moving node I0 is the comoving intensity from k_remap_to_comoving
+//     (in the scratch buffer); its moments still use the laboratory I.
+//   a3  S0(c,k,g)  = sum_p Y_p(n_k) S_p(c,g)   per (tile, g): [64 x NLM] x [NLM x N];
+//     a node at rest writes eta = chi0 S0, chi = chi0 directly; a moving node
+//     writes S0 to the scratch buffer and k_remap_to_lab does the transform.
+#include <cuda_runtime.h>
+
+#include "shd_internal.cuh"
+
+namespace shd {
+
+__device__ inline int tile_row(int d, int q)
+{
+    // element q of a run-ordered brick -> row r = (iy - y0)*8 + (ix - x0);
+    // runs follow x for the z- and y-dominant layouts and y for the x-dominant one
+    return d == 0 ? ((q & 7) << 3) | (q >> 3) : q;
+}
+
+// -------------------------------------------------------------------------
+// a1: [64 x N] x [N x NB] per (tile, group); 128 threads = 8 row groups of 8
+// rows x 16 column groups of TC columns (NB = 16 TC >= NLM + 10).
+// -------------------------------------------------------------------------
+template <class T, int TC>
+__global__ void __launch_bounds__(128) k_project_tile(Prob<T> P, const T *__restrict__ I, const T *__restrict__ I0,
+                                                      T *__restrict__ Ip, T *__restrict__ mom)
+{
+    constexpr int R = 64, KC = 32, NB = 16 * TC, TR = 8;
+    __shared__ T As[KC][R];
+    __shared__ T Bs[KC][NB];
+    const int tile = blockIdx.x / P.G, g = blockIdx.x - (blockIdx.x / P.G) * P.G;
+    const TileInfo ti = P.tiles[tile];
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    const int NLM = P.NLM;
+    const int passes = (ti.flags & 1) ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        T acc[TR][TC];
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < TC; ++j) acc[i][j] = T(0);
+        for (int k0 = 0; k0 < P.N; k0 += KC) {
+            for (int e = tid; e < KC * R; e += 128) {
+                int kk = e >> 6, q = e & 63, k = k0 + kk;
+                T v = T(0);
+                int r = q;
+                if (k < P.N) {
+                    int d = P.ord[k].d;
+                    r = tile_row(d, q);
+                    int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+                    if (ix < P.nx && iy < P.ny) {
+                        long long a = ((long long)k * P.G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
+                        const T *src = I;
+                        if (pass == 1 && P.mflag[((long long)ti.z * P.ny + iy) * P.nx + ix]) src = I0;
+                        v = src[a];
+                    }
+                }
+                As[kk][r] = v;
+            }
+            for (int e = tid; e < KC * NB; e += 128) {
+                int kk = e / NB, j = e - kk * NB, k = k0 + kk;
+                Bs[kk][j] = k < P.N ? P.Bproj[(size_t)k * NB + j] : T(0);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < KC; ++kk) {
+                T a[TR], b[TC];
+#pragma unroll
+                for (int i = 0; i < TR; ++i) a[i] = As[kk][tr * TR + i];
+#pragma unroll
+                for (int j = 0; j < TC; ++j) b[j] = Bs[kk][tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < TR; ++i)
+#pragma unroll
+                    for (int j = 0; j < TC; ++j) acc[i][j] += a[i] * b[j];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+            int r = tr * TR + i;
+            int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+            if (ix >= P.nx || iy >= P.ny) continue;
+            long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+            bool moving = P.mflag[c] != 0;
+#pragma unroll
+            for (int j = 0; j < TC; ++j) {
+                int col = tc + 16 * j;
+                if (col < NLM) {
+                    if ((pass == 0 && !moving) || (pass == 1 && moving)) Ip[(c * P.G + g) * NLM + col] = acc[i][j];
+                } else if (col < NLM + 10 && pass == 0) {
+                    mom[(c * P.G + g) * 10 + (col - NLM)] = acc[i][j];
+                }
+            }
+        }
+    }
+}
+
+// -------------------------------------------------------------------------
+// a3: [64 x NLM] x [NLM x N] per (tile, group), N in chunks of 128
+// ordinates; 256 threads = 8 row groups of 8 rows x 32 column groups of 4.
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_sh2lab_tile(Prob<T> P, const T *__restrict__ Sp, T *__restrict__ eta,
+                                                     T *__restrict__ chi, T *__restrict__ S0)
+{
+    constexpr int R = 64, KC = 128, TR = 8, TC = 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NLM = P.NLM;
+    T *As = reinterpret_cast<T *>(smem_raw);  // [NLM][R]
+    T *Bs = As + (size_t)NLM * R;             // [NLM][KC]
+    T *Cs = Bs + (size_t)NLM * KC;            // [KC][R + 1]
+    T *chir = Cs + (size_t)KC * (R + 1);      // [R]
+    unsigned char *mv = reinterpret_cast<unsigned char *>(chir + R);  // [R]
+    const int tile = blockIdx.x / P.G, g = blockIdx.x - (blockIdx.x / P.G) * P.G;
+    const TileInfo ti = P.tiles[tile];
+    const int tid = threadIdx.x, tr = tid >> 5, tc = tid & 31;
+
+    for (int e = tid; e < R * NLM; e += 256) {
+        int r = e / NLM, p = e - r * NLM;
+        int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+        T v = T(0);
+        if (ix < P.nx && iy < P.ny) {
+            long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+            v = Sp[(c * P.G + g) * NLM + p];
+        }
+        As[(size_t)p * R + r] = v;
+    }
+    for (int r = tid; r < R; r += 256) {
+        int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+        T ch = T(0);
+        unsigned char m = 0;
+        if (ix < P.nx && iy < P.ny) {
+            long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+            ch = P.chi0[c * P.G + g];
+            m = P.mflag[c];
+        }
+        chir[r] = ch;
+        mv[r] = m;
+    }
+    for (int k0 = 0; k0 < P.N; k0 += KC) {
+        for (int e = tid; e < KC * NLM; e += 256) {
+            int kk = e / NLM, p = e - kk * NLM, k = k0 + kk;
+            Bs[(size_t)p * KC + kk] = k < P.N ? P.Y[(size_t)k * NLM + p] : T(0);
+        }
+        __syncthreads();
+        T acc[TR][TC];
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < TC; ++j) acc[i][j] = T(0);
+        for (int p = 0; p < NLM; ++p) {
+            T a[TR], b[TC];
+#pragma unroll
+            for (int i = 0; i < TR; ++i) a[i] = As[(size_t)p * R + tr * TR + i];
+#pragma unroll
+            for (int j = 0; j < TC; ++j) b[j] = Bs[(size_t)p * KC + tc + 32 * j];
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) acc[i][j] += a[i] * b[j];
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < TC; ++j) Cs[(size_t)(tc + 32 * j) * (R + 1) + tr * TR + i] = acc[i][j];
+        __syncthreads();
+        for (int e = tid; e < KC * R; e += 256) {
+            int kk = e >> 6, q = e & 63, k = k0 + kk;
+            if (k >= P.N) continue;
+            int d = P.ord[k].d;
+            int r = tile_row(d, q);
+            int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+            if (ix >= P.nx || iy >= P.ny) continue;
+            long long a = ((long long)k * P.G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
+            T v = Cs[(size_t)kk * (R + 1) + r];
+            if (mv[r]) {
+                S0[a] = v;
+            } else {
+                T ch = chir[r];
+                eta[a] = ch * v;
+                chi[a] = ch;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------------------
+// Lorentz remaps of moving nodes, one CTA per node (blocks of a brick are
+// consecutive so that their scattered accesses share L2 sectors).
+// -------------------------------------------------------------------------
+
+// laboratory I(c, k, g) -> comoving I0(c, k0, g0) = (ebar_g0/eps)^3 I_lab(n, eps),
+// n = boost of n_k0 to the laboratory, eps = ebar_g0 (Gamma + u.n_k0)
+template <class T>
+__global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ I, T *__restrict__ I0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = P.G, N = P.N;
+    T *sI = reinterpret_cast<T *>(smem_raw);  // [G][N]
+    T *spole = sI + (size_t)G * N;            // [G][2]
+    const long long c = P.moving[blockIdx.x];
+    int ix = (int)(c % P.nx), iy = (int)((c / P.nx) % P.ny), iz = (int)(c / ((long long)P.nx * P.ny));
+    long long off[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) off[d] = perm_offset(d, ix, iy, iz, P.nx, P.ny, P.nz);
+    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
+        int k = i / G, g = i - k * G;
+        sI[(size_t)g * N + k] = I[((long long)k * G + g) * P.Nc + off[P.ord[k].d]];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
+        int g = i >> 1, rr = i & 1;
+        const T *F = sI + (size_t)g * N + (rr ? (P.nmu - 1) * P.nphi : 0);
+        T s = 0;
+        for (int j = 0; j < P.nphi; ++j) s += F[j];
+        spole[i] = s / T(P.nphi);
+    }
+    __syncthreads();
+    const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
+    for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
+        T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
+        T n[3];
+        T q = boost_dir<T>(u, n0, n, T(-1));  // nu/nu0
+        Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n);
+        T iq3 = T(1) / (q * q * q);
+        long long base = (long long)k0 * G * P.Nc + off[P.ord[k0].d];
+        for (int g0 = 0; g0 < G; ++g0) {
+            FreqBracket fb = freq_bracket(P.edges, P.centre, G, P.centre[g0] * (double)q);
+            T v = 0;
+            if (fb.mode == 1) {
+                v = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
+            } else if (fb.mode == 2) {
+                T fa = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                T fbv = eval_stencil<T>(st, sI + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
+                v = freq_mix<T>(fa, fbv, (T)fb.t);
+            }
+            I0[base + (long long)g0 * P.Nc] = v * iq3;
+        }
+    }
+}
+
+// comoving S0(c, k0, g) (scratch buffer) -> laboratory eta, chi:
+// D = Gamma - u.n_k, n0 = comoving direction, eps0 = ebar_g D,
+// S_lab = S0(n0, eps0)/D^3, chi_lab = chi0(eps0) D, eta_lab = chi_lab S_lab
+template <class T>
+__global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restrict__ eta, T *__restrict__ chi)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = P.G, N = P.N;
+    T *sS = reinterpret_cast<T *>(smem_raw);  // [G][N]
+    T *spole = sS + (size_t)G * N;            // [G][2]
+    T *schi = spole + 2 * G;                  // [G]
+    const long long c = P.moving[blockIdx.x];
+    int ix = (int)(c % P.nx), iy = (int)((c / P.nx) % P.ny), iz = (int)(c / ((long long)P.nx * P.ny));
+    long long off[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) off[d] = perm_offset(d, ix, iy, iz, P.nx, P.ny, P.nz);
+    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
+        int k = i / G, g = i - k * G;
+        sS[(size_t)g * N + k] = S0[((long long)k * G + g) * P.Nc + off[P.ord[k].d]];
+    }
+    for (int g = threadIdx.x; g < G; g += blockDim.x) schi[g] = P.chi0[c * G + g];
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
+        int g = i >> 1, rr = i & 1;
+        const T *F = sS + (size_t)g * N + (rr ? (P.nmu - 1) * P.nphi : 0);
+        T s = 0;
+        for (int j = 0; j < P.nphi; ++j) s += F[j];
+        spole[i] = s / T(P.nphi);
+    }
+    __syncthreads();
+    const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
+        T n0[3];
+        T D = boost_dir<T>(u, n, n0, T(1));  // nu0/nu
+        Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n0);
+        T iD3 = T(1) / (D * D * D);
+        long long base = (long long)k * G * P.Nc + off[P.ord[k].d];
+        for (int g = 0; g < G; ++g) {
+            FreqBracket fb = freq_bracket(P.edges, P.centre, G, P.centre[g] * (double)D);
+            T s = 0, ch;
+            if (fb.mode == 0) {
+                ch = schi[fb.ga];
+            } else if (fb.mode == 1) {
+                s = eval_stencil<T>(st, sS + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                ch = schi[fb.ga];
+            } else {
+                T fa = eval_stencil<T>(st, sS + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                T fbv = eval_stencil<T>(st, sS + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
+                s = freq_mix<T>(fa, fbv, (T)fb.t);
+                ch = freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], (T)fb.t);
+            }
+            T chl = ch * D;
+            long long o = base + (long long)g * P.Nc;
+            chi[o] = chl;
+            eta[o] = chl * s * iD3;
+        }
+    }
+}
+
+// -------------------------------------------------------------------------
+// launchers
+// -------------------------------------------------------------------------
+size_t remap_smem_bytes(const shd_ctx *c) { return (size_t)c->esize * ((size_t)c->G * c->N + 3 * c->G); }
+
+size_t sh2lab_tile_smem_bytes(const shd_ctx *c)
+{
+    return (size_t)c->esize * ((size_t)c->NLM * 64 + (size_t)c->NLM * 128 + 128 * 65 + 64) + 64;
+}
+
+template <class T, int TC>
+static cudaError_t launch_project_tc(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    k_project_tile<T, TC><<<(unsigned)(ctx->ntiles * ctx->G), 128, 0, st>>>(P, I, (const T *)ctx->d_buf, Ip, mom);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    cudaError_t e;
+    if (ctx->nmoving > 0) {
+        size_t sm = remap_smem_bytes(ctx);
+        e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, I, (T *)ctx->d_buf);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    switch (ctx->NB / 16) {
+        case 1: return launch_project_tc<T, 1>(ctx, I, Ip, mom, st);
+        case 2: return launch_project_tc<T, 2>(ctx, I, Ip, mom, st);
+        case 3: return launch_project_tc<T, 3>(ctx, I, Ip, mom, st);
+        case 4: return launch_project_tc<T, 4>(ctx, I, Ip, mom, st);
+        case 5: return launch_project_tc<T, 5>(ctx, I, Ip, mom, st);
+        case 6: return launch_project_tc<T, 6>(ctx, I, Ip, mom, st);
+        case 7: return launch_project_tc<T, 7>(ctx, I, Ip, mom, st);
+        case 8: return launch_project_tc<T, 8>(ctx, I, Ip, mom, st);
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+
+template <class T>
+cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    size_t sm = sh2lab_tile_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_sh2lab_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sh2lab_tile<T><<<(unsigned)(ctx->ntiles * ctx->G), 256, sm, st>>>(P, Sp, eta, chi, (T *)ctx->d_buf);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ctx->nmoving > 0) {
+        size_t sr = remap_smem_bytes(ctx);
+        e = cudaFuncSetAttribute(k_remap_to_lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+        if (e != cudaSuccess) return e;
+        k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, (const T *)ctx->d_buf, eta, chi);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template cudaError_t launch_project<double>(const shd_ctx *, const double *, double *, double *, cudaStream_t);
+template cudaError_t launch_project<float>(const shd_ctx *, const float *, float *, float *, cudaStream_t);
+template cudaError_t launch_sh2lab<double>(const shd_ctx *, const double *, double *, double *, cudaStream_t);
+template cudaError_t launch_sh2lab<float>(const shd_ctx *, const float *, float *, float *, cudaStream_t);
+
+}  // namespace shd

@@ -89,6 +89,18 @@ def lib(build_if_missing: bool = False):
     return _lib
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
+
+
+def torch_stream():
+    """torch's current CUDA stream as a handle the library can order against
+    (torch reports the legacy default stream as 0, which the C ABI reads as
+    'the context's own stream')."""
+    import torch
+    h = torch.cuda.current_stream().cuda_stream
+    return h if h else CUDA_STREAM_LEGACY
+
+
 def exported_symbols():
     return list(_SIGS)
 
@@ -188,9 +200,8 @@ class Solver:
         import torch
         assert tensor.dtype == torch.float64 and tensor.is_cuda and tensor.is_contiguous()
         assert tensor.numel() == self.Nc * self.G * self.N
-        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        st = torch_stream() if stream is None else stream
         _check(self._L.shd_set_state_dev(self._h, ctypes.c_void_p(tensor.data_ptr()), ctypes.c_void_p(st)))
-        torch.cuda.current_stream().synchronize()
 
     def get_state(self):
         out = np.zeros((self.Nc, self.G, self.N))
