@@ -192,6 +192,37 @@ long long shd_device_bytes(shd_ctx *ctx);
 int shd_set_timing(shd_ctx *ctx, int on);
 int shd_get_timing(shd_ctx *ctx, double *stage_ms, long long *steps);
 
+/* ---- projection without allocation --------------------------------------
+ * No counterpart in the paper.  For callers that cannot call cudaMalloc when
+ * they need the moments: programs whose device memory belongs to another
+ * allocator (a framework's pool), loops that must not meet the allocator's
+ * implicit device synchronisation, processes at their memory limit.
+ *
+ * shd_project_noalloc runs stage a1 on the context's current state and writes
+ *   dev_Ish [c][g][p]  comoving SH projection I_lm
+ *   dev_mom [c][g][10] laboratory moments J, H_x, H_y, H_z, K_xx, K_yy, K_zz,
+ *                      K_xy, K_xz, K_yz (divided by 4 pi)
+ * to caller-owned device memory, in the context's working precision (double
+ * for SHD_FP64, float otherwise).  It allocates nothing: the comoving
+ * intensities of moving nodes live in one static device array of
+ * SHD_NOALLOC_SCRATCH_BYTES (64 MiB), present on every device that loads the
+ * library until the process exits.  Problems with a moving node and
+ * Nc*G*N*(bytes per real) above that limit are rejected with SHD_ERR_ARG
+ * (message: shd_noalloc_last_error()); at rest they need no scratch.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Work runs on cuda_stream (NULL: the context's stream, ordered after the
+ *     context's earlier work); with another stream the caller orders it after
+ *     the steps that produced the state.
+ *   - Every call shares the one array and leaves its contents behind; nothing
+ *     in it needs to start at zero (each call writes every entry it reads).
+ *     Calls that overlap on the GPU race on it.
+ * Returns SHD_OK, SHD_ERR_ARG (null pointer, too large), SHD_ERR_STATE (not
+ * configured) or SHD_ERR_CUDA. */
+#define SHD_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int shd_project_noalloc(shd_ctx *ctx, void *dev_Ish, void *dev_mom, void *cuda_stream);
+const char *shd_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

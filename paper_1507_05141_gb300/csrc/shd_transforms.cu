@@ -372,6 +372,47 @@ cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaS
     return e;
 }
 
+// Stage a1 with the comoving intensities of moving nodes kept in `scratch`
+// (at least Nc*G*N reals when any node moves) instead of the context's buffer.
+template <class T, int TC>
+static cudaError_t launch_project_tile_scratch(const shd_ctx *ctx, const T *I, const T *scratch, T *Ip, T *mom,
+                                               cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    k_project_tile<T, TC><<<(unsigned)(ctx->ntiles * ctx->G), 128, 0, st>>>(P, I, scratch, Ip, mom);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_project_scratch(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *scratch, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    cudaError_t e;
+    if (ctx->nmoving > 0) {
+        size_t sm = remap_smem_bytes(ctx);
+        e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, I, scratch);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    switch (ctx->NB / 16) {
+        case 1: return launch_project_tile_scratch<T, 1>(ctx, I, scratch, Ip, mom, st);
+        case 2: return launch_project_tile_scratch<T, 2>(ctx, I, scratch, Ip, mom, st);
+        case 3: return launch_project_tile_scratch<T, 3>(ctx, I, scratch, Ip, mom, st);
+        case 4: return launch_project_tile_scratch<T, 4>(ctx, I, scratch, Ip, mom, st);
+        case 5: return launch_project_tile_scratch<T, 5>(ctx, I, scratch, Ip, mom, st);
+        case 6: return launch_project_tile_scratch<T, 6>(ctx, I, scratch, Ip, mom, st);
+        case 7: return launch_project_tile_scratch<T, 7>(ctx, I, scratch, Ip, mom, st);
+        case 8: return launch_project_tile_scratch<T, 8>(ctx, I, scratch, Ip, mom, st);
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+
+template cudaError_t launch_project_scratch<double>(const shd_ctx *, const double *, double *, double *, double *,
+                                                    cudaStream_t);
+template cudaError_t launch_project_scratch<float>(const shd_ctx *, const float *, float *, float *, float *,
+                                                   cudaStream_t);
+
 template cudaError_t launch_project<double>(const shd_ctx *, const double *, double *, double *, cudaStream_t);
 template cudaError_t launch_project<float>(const shd_ctx *, const float *, float *, float *, cudaStream_t);
 template cudaError_t launch_sh2lab<double>(const shd_ctx *, const double *, double *, double *, cudaStream_t);

@@ -56,6 +56,8 @@ _SIGS = {
     "shd_device_bytes": (_ll, [_vp]),
     "shd_set_timing": (_i, [_vp, _i]),
     "shd_get_timing": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
+    "shd_project_noalloc": (_i, [_vp, _vp, _vp, _vp]),
+    "shd_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -284,6 +286,15 @@ class Solver:
         n = _ll()
         _check(self._L.shd_get_timing(self._h, _ptr(ms), ctypes.byref(n)))
         return dict(zip(STAGES, ms)), n.value
+
+    def project_noalloc(self, Ish, mom, stream=None):
+        """Stage a1 of the current state into caller-owned CUDA tensors
+        ``Ish`` [c][g][p] and ``mom`` [c][g][10] (working precision) without
+        any allocation in the library."""
+        rc = self._L.shd_project_noalloc(self._h, ctypes.c_void_p(Ish.data_ptr()), ctypes.c_void_p(mom.data_ptr()),
+                                         None if stream is None else ctypes.c_void_p(stream))
+        if rc != 0:
+            raise ShdError(rc, self._L.shd_noalloc_last_error().decode() or "shd_project_noalloc failed")
 
     def device_bytes(self):
         return int(self._L.shd_device_bytes(self._h))
