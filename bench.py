@@ -175,7 +175,7 @@ def bench_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    spec = inputs.jet()
+    spec = inputs.jet(n=args.grid)
     prec = args.precision
     solver = native.Solver.from_spec(spec, device=local, precision=prec)
     solver.zero_state()
@@ -262,7 +262,8 @@ def bench_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "mixed": "f32", "fp64": "f64"}[prec], "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": list(spec.grid), "groups": spec.G, "L": spec.L,
+            "config": {"workload": WORKLOAD if args.grid == 64 else WORKLOAD.replace("64^3", f"{args.grid}^3"),
+                       "grid": list(spec.grid), "groups": spec.G, "L": spec.L,
                        "ordinates": spec.N, "precision": prec, "updates_per_step": upd,
                        "l2": "no flush: the 8.6 GB state is far larger than L2",
                        "parallelism": f"replicas x{ws}"},
@@ -293,6 +294,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--grid", type=int, default=64,
+                    help="nodes per axis of the jet workload (64 is the benchmark; smaller for profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

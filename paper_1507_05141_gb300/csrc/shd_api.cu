@@ -148,7 +148,8 @@ void free_all(shd_ctx *c)
                      &c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
                      &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
                      (void **)&c->d_sums, (void **)&c->d_partial, (void **)&c->d_stage,
-                     &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag, &c->d_Bproj, &c->d_buf};
+                     &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag, &c->d_Bproj, &c->d_buf,
+                     &c->d_lc, &c->d_linv};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
 }
@@ -289,7 +290,7 @@ int ensure_buffers(shd_ctx *c)
     if ((rc = dalloc(c, &c->d_chi0, nCG * es, "chi0"))) return rc;
     if ((rc = dalloc(c, &c->d_ne, (size_t)c->Nc * es, "ne"))) return rc;
     if ((rc = dalloc(c, &c->d_u, (size_t)c->Nc * 3 * es, "u"))) return rc;
-    c->n_partial = 2 * 152;
+    c->n_partial = 8 * 152;
     if ((rc = dalloc(c, (void **)&c->d_partial, sizeof(double) * 4 * c->n_partial, "partials"))) return rc;
     size_t per_node = (size_t)c->G * c->N;
     size_t want = per_node > ((size_t)1 << 24) ? per_node : ((size_t)1 << 24);  // >= 16 Mi doubles or one node
@@ -579,6 +580,19 @@ int shd_set_groups(shd_ctx *c, int G, const double *edges)
     cudaError_t e;
     c->d_edges = (double *)to_device_vec<double>(c->h_edges, c->bytes, e); CK(e, "edges");
     c->d_centre = (double *)to_device_vec<double>(c->h_centre, c->bytes, e); CK(e, "centres");
+    // log-energy tables of the frame remaps: log centres and inverse spacings
+    std::vector<double> lc(G), linv(G, 0.0);
+    for (int g = 0; g < G; ++g) lc[g] = std::log(c->h_centre[g]);
+    for (int g = 0; g + 1 < G; ++g) linv[g] = 1.0 / (lc[g + 1] - lc[g]);
+    dfree(c->d_lc);
+    dfree(c->d_linv);
+    if (is_fp64(c)) {
+        c->d_lc = to_device_vec<double>(lc, c->bytes, e); CK(e, "log centres");
+        c->d_linv = to_device_vec<double>(linv, c->bytes, e); CK(e, "log spacings");
+    } else {
+        c->d_lc = to_device_vec<float>(lc, c->bytes, e); CK(e, "log centres");
+        c->d_linv = to_device_vec<float>(linv, c->bytes, e); CK(e, "log spacings");
+    }
     c->have_groups = true;
     return SHD_OK;
 }

@@ -73,6 +73,9 @@ struct Prob {
     const unsigned char *mflag;   // [Nc] 1 where u != 0
     const T *Bproj;        // [N][NB]: W_k Y_p(n_k) | W_k {1, n, nn}/(4 pi) | 0
     int NB;
+    const T *lc;           // [G] log of the group centres
+    const T *linv;         // [G] 1/(lc[g+1] - lc[g])
+    T le0, leG;            // log of the outer edges
 };
 
 // Per-stage CUDA events recorded on the launching stream without any host
@@ -131,6 +134,7 @@ struct shd_ctx {
     void *d_Bproj = nullptr;          // [N][NB]
     int NB = 0;
     void *d_buf = nullptr;            // DO-layout scratch: I0 / S0 of moving nodes
+    void *d_lc = nullptr, *d_linv = nullptr;  // log-energy group tables
     double *d_stage = nullptr;    // staging buffer for host <-> device copies (FP64)
     size_t stage_elems = 0;
     long long bytes = 0;
@@ -274,39 +278,51 @@ __device__ inline T eval_stencil(const Stencil<T> &s, const T *F, const T *poles
     return v;
 }
 
-// Group bracket for energy eps (Sec. 2.3 multi-group, group value at the
-// centre): returns mode 0 = outside the edges, 1 = a single group ga (between
-// an outer centre and its edge), 2 = between centres ga and ga+1 with
-// log-fraction t.
+// Group bracket for an energy, in log energy (Sec. 2.3 multi-group; the group
+// value is taken at the centre).  lc[g] = log centre, inv[g] = 1/(lc[g+1] -
+// lc[g]), le0 / leG = log of the outer edges.  Modes: 0 outside the edges
+// (ga = nearest group), 1 a single group ga (between an outer centre and its
+// edge), 2 between centres ga and ga+1 with fraction t in log energy.
+template <class T>
 struct FreqBracket {
     int mode, ga;
-    double t;
+    T t;
 };
 
-__device__ inline FreqBracket freq_bracket(const double *edges, const double *centre, int G, double eps)
+// `hint` is a lower bound for the bracket index carried between calls with
+// non-decreasing energies; the search moves forward from it.
+template <class T>
+__device__ inline FreqBracket<T> freq_bracket(const T *lc, const T *inv, T le0, T leG, int G, T le, int &hint)
 {
-    FreqBracket b;
-    b.t = 0;
-    if (eps < edges[0] || eps > edges[G]) { b.mode = 0; b.ga = eps < edges[0] ? 0 : G - 1; return b; }
-    if (eps <= centre[0]) { b.mode = 1; b.ga = 0; return b; }
-    if (eps >= centre[G - 1]) { b.mode = 1; b.ga = G - 1; return b; }
-    int lo = 0, hi = G - 1;  // centre[lo] < eps < centre[hi]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (centre[mid] <= eps) lo = mid; else hi = mid;
-    }
+    FreqBracket<T> b;
+    b.t = T(0);
+    if (le < le0 || le > leG) { b.mode = 0; b.ga = le < le0 ? 0 : G - 1; return b; }
+    if (le <= lc[0]) { b.mode = 1; b.ga = 0; return b; }
+    if (le >= lc[G - 1]) { b.mode = 1; b.ga = G - 1; return b; }
+    int lo = hint < 0 ? 0 : (hint > G - 2 ? G - 2 : hint);
+    if (lc[lo] > le) lo = 0;
+    while (lo < G - 2 && lc[lo + 1] <= le) ++lo;
+    hint = lo;
     b.mode = 2;
     b.ga = lo;
-    b.t = log(eps / centre[lo]) / log(centre[lo + 1] / centre[lo]);
+    b.t = (le - lc[lo]) * inv[lo];
     return b;
 }
 
 // Geometric between positive values, linear in log(eps) otherwise.
 template <class T>
-__device__ inline T freq_mix(T fa, T fb, T t)
+__device__ inline T freq_mix(T fa, T fb, T t);
+template <>
+__device__ inline double freq_mix<double>(double fa, double fb, double t)
 {
-    if (fa > T(0) && fb > T(0)) return fa * dexp<T>(t * dlog<T>(fb / fa));
-    return (T(1) - t) * fa + t * fb;
+    if (fa > 0.0 && fb > 0.0) return fa * exp(t * log(fb / fa));
+    return (1.0 - t) * fa + t * fb;
+}
+template <>
+__device__ inline float freq_mix<float>(float fa, float fb, float t)
+{
+    if (fa > 0.f && fb > 0.f) return fa * __expf(t * __logf(fb / fa));
+    return (1.f - t) * fa + t * fb;
 }
 
 // Linear-in-tau short-characteristic weights with e = exp(-x):
@@ -335,15 +351,14 @@ __device__ inline void sc_weights<double>(double x, double &e, double &wp, doubl
 template <>
 __device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu)
 {
+    e = __expf(-x);
     if (x < 0.5f) {
         wp = x * (1.f / 2 - x * (1.f / 6 - x * (1.f / 24 - x * (1.f / 120 - x * (1.f / 720 - x * (1.f / 5040 - x * (1.f / 40320 - x / 362880.f)))))));
         wu = x * (1.f / 2 - x * (1.f / 3 - x * (1.f / 8 - x * (1.f / 30 - x * (1.f / 144 - x * (1.f / 840 - x * (1.f / 5760 - x / 45360.f)))))));
-        e = expf(-x);
         return;
     }
-    float em1 = -expm1f(-x);
-    e = 1.f - em1;
-    float a0 = em1 / x;
+    // x >= 1/2: e <= 0.61, so 1 - e carries no cancellation
+    float a0 = (1.f - e) * __frcp_rn(x);
     wp = 1.f - a0;
     wu = a0 - e;
 }

@@ -10,6 +10,8 @@
 // remap between frame meshes), Sec. 2.3 (SH source, Thomson, eq:comptoncross).
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "shd_internal.cuh"
 
 namespace shd {
@@ -31,6 +33,9 @@ Prob<T> make_prob(const shd_ctx *c)
     p.tiles = (const TileInfo *)c->d_tiles; p.ntiles = c->ntiles;
     p.moving = c->d_moving; p.nmoving = c->nmoving; p.mflag = c->d_mflag;
     p.Bproj = (const T *)c->d_Bproj; p.NB = c->NB;
+    p.lc = (const T *)c->d_lc; p.linv = (const T *)c->d_linv;
+    p.le0 = c->G ? (T)std::log(c->h_edges[0]) : T(0);
+    p.leG = c->G ? (T)std::log(c->h_edges[c->G]) : T(0);
     return p;
 }
 
@@ -58,31 +63,35 @@ __global__ void k_chi0(Prob<T> P, T *chi0)
 
 // -------------------------------------------------------------------------
 // a2: S_p(c,g) = n_e/chi0 sum_g' K_l[g][g'] I_p(c,g') + delta_p0 sqrt(4pi) eta0/chi0
+// One CTA per node: the node's I_lm [G][NLM] is staged in shared memory
+// (coalesced), every thread forms outputs of all groups from it.
 // -------------------------------------------------------------------------
 template <class T>
-__global__ void k_source(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp)
+__global__ void __launch_bounds__(256) k_source(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp)
 {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sI = reinterpret_cast<T *>(smem_raw);  // [G][NLM]
     const int G = P.G, NLM = P.NLM;
-    long long n = P.Nc * G * NLM;
-    if (i >= n) return;
-    int p = (int)(i % NLM);
-    long long cg = i / NLM;
-    int g = (int)(cg % G);
-    long long c = cg / G;
-    int l = 0;
-    while ((l + 1) * (l + 1) <= p) ++l;
-    T chi = P.chi0[cg];
-    T s = 0;
-    if (chi > T(0)) {
-        const T *Kr = P.K + ((size_t)l * G + g) * G;
-        const T *Ic = Ip + (long long)c * G * NLM + p;
-        T acc = 0;
-        for (int gp = 0; gp < G; ++gp) acc += Kr[gp] * Ic[(size_t)gp * NLM];
-        s = P.ne[c] / chi * acc;
-        if (p == 0) s += T(3.5449077018110320546) * P.emis0[cg] / chi;  // sqrt(4 pi)
+    const long long c = blockIdx.x;
+    const long long base = c * G * NLM;
+    for (int i = threadIdx.x; i < G * NLM; i += blockDim.x) sI[i] = Ip[base + i];
+    __syncthreads();
+    const T ne = P.ne[c];
+    for (int i = threadIdx.x; i < G * NLM; i += blockDim.x) {
+        int g = i / NLM, p = i - g * NLM;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= p) ++l;
+        T chi = P.chi0[c * G + g];
+        T s = T(0);
+        if (chi > T(0)) {
+            const T *Kr = P.K + ((size_t)l * G + g) * G;
+            T acc = T(0);
+            for (int gp = 0; gp < G; ++gp) acc += Kr[gp] * sI[gp * NLM + p];
+            s = ne / chi * acc;
+            if (p == 0) s += T(3.5449077018110320546) * P.emis0[c * G + g] / chi;  // sqrt(4 pi)
+        }
+        Sp[base + i] = s;
     }
-    Sp[i] = s;
 }
 
 // -------------------------------------------------------------------------
@@ -157,6 +166,155 @@ __global__ void __launch_bounds__(1024) k_sweep(Prob<T> P, T *__restrict__ I, co
             pS[j] = rS[t];
             pC[j] = rC[t];
             I[pbase + j] = rI[t];
+        }
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------------------
+// a4, pipelined: the same plane walk with the inputs of the next plane
+// (I^n, eta_lab, chi_lab) already streaming into a two-stage shared-memory
+// ring by cp.async while the current plane is computed.  Lane i of a warp
+// owns node j = slot*V + e with consecutive slots on consecutive lanes, so
+// every shared-memory access of a warp is to consecutive words (no bank
+// conflicts) and every global access is coalesced.  A thread reads only the
+// ring slots it filled, so the ring needs no barrier; the two barriers per
+// plane guard the previous-plane state.
+// -------------------------------------------------------------------------
+template <class T>
+__device__ inline T fast_recip(T x);
+template <>
+__device__ inline double fast_recip<double>(double x) { return 1.0 / x; }
+template <>
+__device__ inline float fast_recip<float>(float x) { return __frcp_rn(x); }
+
+template <int BYTES>
+__device__ inline void cp_async_n(void *smem, const void *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES));
+}
+
+template <class T, int V, int U>
+__global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict__ I, const T *__restrict__ eta,
+                                                        const T *__restrict__ chi)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NT = 1024;
+    const int k = blockIdx.x / P.G;
+    const int g = blockIdx.x - k * P.G;
+    const Ordinate o = P.ord[k];
+    const int dims[3] = {P.nx, P.ny, P.nz};
+    const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
+    const int plane = n1 * n2;
+    const int pstride = (int)(((size_t)plane + 3) & ~(size_t)3);  // keep every array 16-byte aligned
+    T *pI = reinterpret_cast<T *>(smem_raw);
+    T *pS = pI + pstride;
+    T *pC = pS + pstride;
+    T *ring = pC + pstride;  // [2][3][pstride]
+    const long long base = ((long long)k * P.G + g) * P.Nc;
+    const T fr1 = (T)o.fr1, fr2 = (T)o.fr2, s = (T)o.s, kap = P.kappa;
+    const int first1 = o.s1 > 0 ? 0 : n1 - 1, first2 = o.s2 > 0 ? 0 : n2 - 1;
+    const T w00 = (T(1) - fr1) * (T(1) - fr2), w10 = fr1 * (T(1) - fr2), w01 = (T(1) - fr1) * fr2, w11 = fr1 * fr2;
+    const T bc_iso = P.bc_mode == SHD_BC_ISO ? P.bc[g] : T(0);
+    const int nslot = (plane + V - 1) / V;
+    const int tid = threadIdx.x;
+
+    auto issue = [&](int step) {
+        if (step < nd) {
+            const int id = o.sd > 0 ? step : nd - 1 - step;
+            const long long pb = base + (long long)id * plane;
+            T *r = ring + (size_t)(step & 1) * 3 * pstride;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int slot = tid + NT * u;
+                if (slot >= nslot) break;
+                int j = slot * V;
+                cp_async_n<V * sizeof(T)>(&r[j], &I[pb + j]);
+                cp_async_n<V * sizeof(T)>(&r[pstride + j], &eta[pb + j]);
+                cp_async_n<V * sizeof(T)>(&r[2 * pstride + j], &chi[pb + j]);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+
+    issue(0);
+    T rI[U][V], rS[U][V], rC[U][V];
+    for (int step = 0; step < nd; ++step) {
+        issue(step + 1);
+        asm volatile("cp.async.wait_group 1;\n" ::);
+        const T *r = ring + (size_t)(step & 1) * 3 * pstride;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int slot = tid + NT * u;
+            if (slot >= nslot) break;
+            int j0 = slot * V;
+            int i1 = j0 / n2, i2 = j0 - i1 * n2;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                int j = j0 + e;
+                if (j < plane) {
+                    T In = r[j];
+                    T ct = r[2 * pstride + j] + kap;
+                    T st = ct > T(0) ? (r[pstride + j] + kap * In) * fast_recip<T>(ct) : T(0);
+                    bool inflow = step == 0 || (o.s1 != 0 && i1 == first1) || (o.s2 != 0 && i2 == first2);
+                    T inew;
+                    if (inflow) {
+                        if (P.bc_mode == SHD_BC_FULL) {
+                            const int id = o.sd > 0 ? step : nd - 1 - step;
+                            inew = P.bc[base + (long long)id * plane + j];
+                        } else {
+                            inew = bc_iso;
+                        }
+                    } else {
+                        int j1 = i1 - o.s1, j2 = i2 - o.s2;
+                        int a00 = i1 * n2 + i2, a10 = j1 * n2 + i2, a01 = i1 * n2 + j2, a11 = j1 * n2 + j2;
+                        T iu = w00 * pI[a00] + w10 * pI[a10] + w01 * pI[a01] + w11 * pI[a11];
+                        T su = w00 * pS[a00] + w10 * pS[a10] + w01 * pS[a01] + w11 * pS[a11];
+                        T cu = w00 * pC[a00] + w10 * pC[a10] + w01 * pC[a01] + w11 * pC[a11];
+                        T dtau = s * T(0.5) * (cu + ct);
+                        T ew, wp, wu;
+                        sc_weights<T>(dtau, ew, wp, wu);
+                        inew = iu * ew + st * wp + su * wu;
+                    }
+                    rI[u][e] = inew;
+                    rS[u][e] = st;
+                    rC[u][e] = ct;
+                }
+                if (++i2 == n2) { i2 = 0; ++i1; }
+            }
+        }
+        __syncthreads();
+        const int id = o.sd > 0 ? step : nd - 1 - step;
+        const long long pb = base + (long long)id * plane;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int slot = tid + NT * u;
+            if (slot >= nslot) break;
+            int j0 = slot * V;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                int j = j0 + e;
+                if (j < plane) {
+                    pI[j] = rI[u][e];
+                    pS[j] = rS[u][e];
+                    pC[j] = rC[u][e];
+                }
+            }
+            if constexpr (V * sizeof(T) == 16) {
+                if constexpr (sizeof(T) == 4) {
+                    *reinterpret_cast<float4 *>(&I[pb + j0]) = make_float4(rI[u][0], rI[u][1], rI[u][2], rI[u][3]);
+                } else {
+                    *reinterpret_cast<double2 *>(&I[pb + j0]) = make_double2(rI[u][0], rI[u][1]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (j0 + e < plane) I[pb + j0 + e] = rI[u][e];
+            }
         }
         __syncthreads();
     }
@@ -378,8 +536,10 @@ template <class T>
 cudaError_t launch_source(const shd_ctx *ctx, const T *Ip, T *Sp, cudaStream_t st)
 {
     Prob<T> P = make_prob<T>(ctx);
-    long long n = ctx->Nc * ctx->G * ctx->NLM;
-    k_source<T><<<blocks_for(n, 256), 256, 0, st>>>(P, Ip, Sp);
+    size_t sm = (size_t)ctx->G * ctx->NLM * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_source<T><<<(unsigned)ctx->Nc, 256, sm, st>>>(P, Ip, Sp);
     return cudaGetLastError();
 }
 
@@ -395,10 +555,37 @@ static cudaError_t launch_sweep_npt(const shd_ctx *ctx, T *I, const T *eta, cons
     return cudaGetLastError();
 }
 
+template <class T, int V, int U>
+static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st,
+                                     size_t sm)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_pipe<T, V, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sweep_pipe<T, V, U><<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi);
+    return cudaGetLastError();
+}
+
+// shared memory of the pipelined sweep: previous plane (3 arrays) + 2-stage
+// ring of the three inputs, each array padded to a multiple of 4 reals
+size_t sweep_pipe_smem_bytes(const shd_ctx *c)
+{
+    size_t ps = ((size_t)sweep_plane_max(c) + 3) & ~(size_t)3;
+    return c->esize * ps * 9;
+}
+
 template <class T>
 cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st)
 {
     int plane = sweep_plane_max(ctx);
+    size_t smp = sweep_pipe_smem_bytes(ctx);
+    if (smp <= 227 * 1024) {
+        int u = (plane + 1023) / 1024;
+        if (u <= 1) return launch_sweep_pipe<T, 1, 1>(ctx, I, eta, chi, st, smp);
+        if (u <= 2) return launch_sweep_pipe<T, 1, 2>(ctx, I, eta, chi, st, smp);
+        if (u <= 4) return launch_sweep_pipe<T, 1, 4>(ctx, I, eta, chi, st, smp);
+        if (u <= 8) return launch_sweep_pipe<T, 1, 8>(ctx, I, eta, chi, st, smp);
+    }
     int threads = plane < 1024 ? ((plane + 31) / 32) * 32 : 1024;
     int npt = (plane + threads - 1) / threads;
     if (npt <= 1) return launch_sweep_npt<T, 1>(ctx, I, eta, chi, st, threads);

@@ -196,6 +196,221 @@ __global__ void __launch_bounds__(256) k_sh2lab_tile(Prob<T> P, const T *__restr
 }
 
 // -------------------------------------------------------------------------
+// Persistent forms (used when the right-hand matrix fits in shared memory):
+// one CTA per SM loads W Y (project) or Y (sh2lab) once and then walks the
+// (tile, group) work items, so the matrix crosses L2 once per SM instead of
+// once per item.  A chunks are double-buffered with cp.async.
+// -------------------------------------------------------------------------
+__device__ inline void cp_async4(void *smem, const void *gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// a1, persistent: 256 threads = 16 row groups of 4 rows x 16 column groups of
+// TC contiguous columns (NB = 16 TC).  Shared: Bs[N][NB] + As[2][KC][64].
+template <int TC>
+__global__ void __launch_bounds__(256, 1) k_project_persist(Prob<float> P, const float *__restrict__ I,
+                                                            const float *__restrict__ I0, float *__restrict__ Ip,
+                                                            float *__restrict__ mom)
+{
+    constexpr int R = 64, KC = 32, NB = 16 * TC, TR = 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Bs = reinterpret_cast<float *>(smem_raw);        // [N][NB]
+    float *As = Bs + (size_t)P.N * NB;                       // [2][KC][R]
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    const int NLM = P.NLM, N = P.N, G = P.G;
+    for (int e = tid; e < N * NB; e += 256) Bs[e] = P.Bproj[e];
+    const long long items = P.ntiles * G;
+    const int nchunk = (N + KC - 1) / KC;
+    for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+        const long long tile = w / G;
+        const int g = (int)(w - tile * G);
+        const TileInfo ti = P.tiles[tile];
+        const int passes = (ti.flags & 1) ? 2 : 1;
+        for (int pass = 0; pass < passes; ++pass) {
+            // columns this pass needs: everything in pass 0, the SH part in pass 1
+            const int ncol = pass == 0 ? NB : NLM;
+            float acc[TR][TC];
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) acc[i][j] = 0.f;
+            auto load_chunk = [&](int ch, int buf) {
+                float *A = As + (size_t)buf * KC * R;
+                for (int e = tid; e < KC * R; e += 256) {
+                    int kk = e >> 6, q = e & 63, k = ch * KC + kk;
+                    int r = q;
+                    bool ok = false;
+                    const float *src = nullptr;
+                    if (k < N) {
+                        int d = P.ord[k].d;
+                        r = tile_row(d, q);
+                        int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+                        if (ix < P.nx && iy < P.ny) {
+                            long long a = ((long long)k * G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
+                            src = I;
+                            if (pass == 1 && P.mflag[((long long)ti.z * P.ny + iy) * P.nx + ix]) src = I0;
+                            src += a;
+                            ok = true;
+                        }
+                    }
+                    if (ok) cp_async4(&A[kk * R + r], src);
+                    else A[kk * R + r] = 0.f;
+                }
+                cp_async_commit();
+            };
+            __syncthreads();  // previous item's readers of As are done (and Bs is loaded)
+            load_chunk(0, 0);
+            for (int ch = 0; ch < nchunk; ++ch) {
+                if (ch + 1 < nchunk) {
+                    load_chunk(ch + 1, (ch + 1) & 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+                const float *A = As + (size_t)(ch & 1) * KC * R;
+                const int kbase = ch * KC;
+                const int kmax = N - kbase < KC ? N - kbase : KC;
+                if (tc * TC < ncol) {
+                    for (int kk = 0; kk < kmax; ++kk) {
+                        float4 a4 = *reinterpret_cast<const float4 *>(&A[kk * R + tr * TR]);
+                        const float *b = &Bs[(size_t)(kbase + kk) * NB + tc * TC];
+                        float bv[TC];
+#pragma unroll
+                        for (int j = 0; j < TC; ++j) bv[j] = b[j];
+                        float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                        for (int i = 0; i < TR; ++i)
+#pragma unroll
+                            for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                    }
+                }
+                __syncthreads();  // buffer (ch & 1) may be refilled next
+            }
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+                int r = tr * TR + i;
+                int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+                if (ix >= P.nx || iy >= P.ny) continue;
+                long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+                bool moving = P.mflag[c] != 0;
+#pragma unroll
+                for (int j = 0; j < TC; ++j) {
+                    int col = tc * TC + j;
+                    if (col < NLM) {
+                        if ((pass == 0 && !moving) || (pass == 1 && moving)) Ip[(c * G + g) * NLM + col] = acc[i][j];
+                    } else if (col < NLM + 10 && pass == 0) {
+                        mom[(c * G + g) * 10 + (col - NLM)] = acc[i][j];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// a3, persistent: Bs = Y^T [NLM][N] resident; per item As [NLM][64], the
+// result staged per 128-ordinate chunk in Cs [128][65] and written as runs.
+__global__ void __launch_bounds__(256, 1) k_sh2lab_persist(Prob<float> P, const float *__restrict__ Sp,
+                                                           float *__restrict__ eta, float *__restrict__ chi,
+                                                           float *__restrict__ S0)
+{
+    constexpr int R = 64, KC = 128, TR = 8, TC = 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NLM = P.NLM, N = P.N, G = P.G;
+    float *Bs = reinterpret_cast<float *>(smem_raw);  // [NLM][N]
+    float *As = Bs + (size_t)NLM * N;                  // [NLM][R]
+    float *Cs = As + (size_t)NLM * R;                  // [KC][R + 1]
+    float *chir = Cs + (size_t)KC * (R + 1);           // [R]
+    unsigned char *mv = reinterpret_cast<unsigned char *>(chir + R);  // [R]
+    const int tid = threadIdx.x, tr = tid >> 5, tc = tid & 31;
+    for (int e = tid; e < N * NLM; e += 256) {
+        int k = e / NLM, p = e - k * NLM;
+        Bs[(size_t)p * N + k] = P.Y[e];
+    }
+    const long long items = P.ntiles * G;
+    for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+        const long long tile = w / G;
+        const int g = (int)(w - tile * G);
+        const TileInfo ti = P.tiles[tile];
+        __syncthreads();
+        for (int e = tid; e < R * NLM; e += 256) {
+            int r = e / NLM, p = e - r * NLM;
+            int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+            float v = 0.f;
+            if (ix < P.nx && iy < P.ny) {
+                long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+                v = Sp[(c * G + g) * NLM + p];
+            }
+            As[(size_t)p * R + r] = v;
+        }
+        for (int r = tid; r < R; r += 256) {
+            int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+            float ch = 0.f;
+            unsigned char m = 0;
+            if (ix < P.nx && iy < P.ny) {
+                long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+                ch = P.chi0[c * G + g];
+                m = P.mflag[c];
+            }
+            chir[r] = ch;
+            mv[r] = m;
+        }
+        __syncthreads();
+        for (int k0 = 0; k0 < N; k0 += KC) {
+            float acc[TR][TC];
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) acc[i][j] = 0.f;
+            for (int p = 0; p < NLM; ++p) {
+                const float *a = &As[(size_t)p * R + tr * TR];
+                float4 a0 = *reinterpret_cast<const float4 *>(a);
+                float4 a1 = *reinterpret_cast<const float4 *>(a + 4);
+                float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                float bv[TC];
+#pragma unroll
+                for (int j = 0; j < TC; ++j) {
+                    int k = k0 + tc + 32 * j;
+                    bv[j] = k < N ? Bs[(size_t)p * N + k] : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < TR; ++i)
+#pragma unroll
+                    for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) Cs[(size_t)(tc + 32 * j) * (R + 1) + tr * TR + i] = acc[i][j];
+            __syncthreads();
+            for (int e = tid; e < KC * R; e += 256) {
+                int kk = e >> 6, q = e & 63, k = k0 + kk;
+                if (k >= N) continue;
+                int d = P.ord[k].d;
+                int r = tile_row(d, q);
+                int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+                if (ix >= P.nx || iy >= P.ny) continue;
+                long long a = ((long long)k * G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
+                float v = Cs[(size_t)kk * (R + 1) + r];
+                if (mv[r]) {
+                    S0[a] = v;
+                } else {
+                    float ch = chir[r];
+                    eta[a] = ch * v;
+                    chi[a] = ch;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// -------------------------------------------------------------------------
 // Lorentz remaps of moving nodes, one CTA per node (blocks of a brick are
 // consecutive so that their scattered accesses share L2 sectors).
 // -------------------------------------------------------------------------
@@ -234,16 +449,18 @@ __global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ I, T *__res
         T q = boost_dir<T>(u, n0, n, T(-1));  // nu/nu0
         Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n);
         T iq3 = T(1) / (q * q * q);
+        T lq = dlog<T>(q);
+        int hint = 0;
         long long base = (long long)k0 * G * P.Nc + off[P.ord[k0].d];
         for (int g0 = 0; g0 < G; ++g0) {
-            FreqBracket fb = freq_bracket(P.edges, P.centre, G, P.centre[g0] * (double)q);
+            FreqBracket<T> fb = freq_bracket<T>(P.lc, P.linv, P.le0, P.leG, G, P.lc[g0] + lq, hint);
             T v = 0;
             if (fb.mode == 1) {
                 v = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
             } else if (fb.mode == 2) {
                 T fa = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
                 T fbv = eval_stencil<T>(st, sI + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
-                v = freq_mix<T>(fa, fbv, (T)fb.t);
+                v = freq_mix<T>(fa, fbv, fb.t);
             }
             I0[base + (long long)g0 * P.Nc] = v * iq3;
         }
@@ -287,9 +504,11 @@ __global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restric
         T D = boost_dir<T>(u, n, n0, T(1));  // nu0/nu
         Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n0);
         T iD3 = T(1) / (D * D * D);
+        T lD = dlog<T>(D);
+        int hint = 0;
         long long base = (long long)k * G * P.Nc + off[P.ord[k].d];
         for (int g = 0; g < G; ++g) {
-            FreqBracket fb = freq_bracket(P.edges, P.centre, G, P.centre[g] * (double)D);
+            FreqBracket<T> fb = freq_bracket<T>(P.lc, P.linv, P.le0, P.leG, G, P.lc[g] + lD, hint);
             T s = 0, ch;
             if (fb.mode == 0) {
                 ch = schi[fb.ga];
@@ -299,8 +518,8 @@ __global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restric
             } else {
                 T fa = eval_stencil<T>(st, sS + (size_t)fb.ga * N, spole + 2 * fb.ga);
                 T fbv = eval_stencil<T>(st, sS + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
-                s = freq_mix<T>(fa, fbv, (T)fb.t);
-                ch = freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], (T)fb.t);
+                s = freq_mix<T>(fa, fbv, fb.t);
+                ch = freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], fb.t);
             }
             T chl = ch * D;
             long long o = base + (long long)g * P.Nc;
@@ -328,6 +547,55 @@ static cudaError_t launch_project_tc(const shd_ctx *ctx, const T *I, T *Ip, T *m
     return cudaGetLastError();
 }
 
+static int num_sms(const shd_ctx *ctx)
+{
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || n <= 0) n = 148;
+    return n;
+}
+
+static const size_t kSmemLimit = 227 * 1024;
+
+size_t project_persist_smem_bytes(const shd_ctx *c)
+{
+    return sizeof(float) * ((size_t)c->N * c->NB + 2 * 32 * 64);
+}
+size_t sh2lab_persist_smem_bytes(const shd_ctx *c)
+{
+    return sizeof(float) * ((size_t)c->NLM * c->N + (size_t)c->NLM * 64 + 128 * 65 + 64) + 64;
+}
+
+template <int TC>
+static cudaError_t launch_project_persist_tc(const shd_ctx *ctx, const float *I, float *Ip, float *mom,
+                                             const float *scratch, cudaStream_t st)
+{
+    Prob<float> P = make_prob<float>(ctx);
+    size_t sm = project_persist_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_project_persist<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    long long items = ctx->ntiles * ctx->G;
+    int grid = num_sms(ctx);
+    if (items < grid) grid = (int)items;
+    k_project_persist<TC><<<grid, 256, sm, st>>>(P, I, scratch, Ip, mom);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_project_persist(const shd_ctx *ctx, const float *I, float *Ip, float *mom,
+                                          const float *scratch, cudaStream_t st)
+{
+    switch (ctx->NB / 16) {
+        case 1: return launch_project_persist_tc<1>(ctx, I, Ip, mom, scratch, st);
+        case 2: return launch_project_persist_tc<2>(ctx, I, Ip, mom, scratch, st);
+        case 3: return launch_project_persist_tc<3>(ctx, I, Ip, mom, scratch, st);
+        case 4: return launch_project_persist_tc<4>(ctx, I, Ip, mom, scratch, st);
+        case 5: return launch_project_persist_tc<5>(ctx, I, Ip, mom, scratch, st);
+        case 6: return launch_project_persist_tc<6>(ctx, I, Ip, mom, scratch, st);
+        case 7: return launch_project_persist_tc<7>(ctx, I, Ip, mom, scratch, st);
+        case 8: return launch_project_persist_tc<8>(ctx, I, Ip, mom, scratch, st);
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+
 template <class T>
 cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st)
 {
@@ -339,6 +607,10 @@ cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaSt
         if (e != cudaSuccess) return e;
         k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, I, (T *)ctx->d_buf);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (project_persist_smem_bytes(ctx) <= kSmemLimit)
+            return launch_project_persist(ctx, I, Ip, mom, (const float *)ctx->d_buf, st);
     }
     switch (ctx->NB / 16) {
         case 1: return launch_project_tc<T, 1>(ctx, I, Ip, mom, st);
@@ -357,11 +629,28 @@ template <class T>
 cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st)
 {
     Prob<T> P = make_prob<T>(ctx);
-    size_t sm = sh2lab_tile_smem_bytes(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_sh2lab_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_sh2lab_tile<T><<<(unsigned)(ctx->ntiles * ctx->G), 256, sm, st>>>(P, Sp, eta, chi, (T *)ctx->d_buf);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cudaError_t e;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        size_t smp = sh2lab_persist_smem_bytes(ctx);
+        if (smp <= kSmemLimit) {
+            e = cudaFuncSetAttribute(k_sh2lab_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+            if (e != cudaSuccess) return e;
+            long long items = ctx->ntiles * ctx->G;
+            int grid = num_sms(ctx);
+            if (items < grid) grid = (int)items;
+            k_sh2lab_persist<<<grid, 256, smp, st>>>(P, Sp, eta, chi, (T *)ctx->d_buf);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            done = true;
+        }
+    }
+    if (!done) {
+        size_t sm = sh2lab_tile_smem_bytes(ctx);
+        e = cudaFuncSetAttribute(k_sh2lab_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_sh2lab_tile<T><<<(unsigned)(ctx->ntiles * ctx->G), 256, sm, st>>>(P, Sp, eta, chi, (T *)ctx->d_buf);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (ctx->nmoving > 0) {
         size_t sr = remap_smem_bytes(ctx);
         e = cudaFuncSetAttribute(k_remap_to_lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
