@@ -206,9 +206,10 @@ int shd_get_timing(shd_ctx *ctx, double *stage_ms, long long *steps);
  * for SHD_FP64, float otherwise).  It allocates nothing: the comoving
  * intensities of moving nodes live in one static device array of
  * SHD_NOALLOC_SCRATCH_BYTES (64 MiB), present on every device that loads the
- * library until the process exits.  Problems with a moving node and
- * Nc*G*N*(bytes per real) above that limit are rejected with SHD_ERR_ARG
- * (message: shd_noalloc_last_error()); at rest they need no scratch.
+ * library until the process exits.  Problems whose moving nodes need more
+ * than that -- 2 * (moving nodes) * G * N * (bytes per real) -- are
+ * rejected with SHD_ERR_ARG (message: shd_noalloc_last_error()); nodes at
+ * rest need no scratch.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
  *   - Work runs on cuda_stream (NULL: the context's stream, ordered after the

@@ -148,8 +148,10 @@ void free_all(shd_ctx *c)
                      &c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
                      &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
                      (void **)&c->d_sums, (void **)&c->d_partial, (void **)&c->d_stage,
-                     &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag, &c->d_Bproj, &c->d_buf,
-                     &c->d_lc, &c->d_linv};
+                     &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag, &c->d_Bproj,
+                     (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
+                     &c->d_lc, &c->d_linv, &c->d_tc_Bh, &c->d_tc_Bl, &c->d_tc_Yh, &c->d_tc_Yl,
+                     (void **)&c->d_tc_err};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
 }
@@ -182,7 +184,8 @@ void drop_sized(shd_ctx *c)
     void **ptrs[] = {&c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
                      &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
                      (void **)&c->d_partial, (void **)&c->d_stage,
-                     &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag, &c->d_buf};
+                     &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag,
+                     (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2]};
     for (void **p : ptrs) dfree(*p);
     c->ntiles = 0;
     c->nmoving = 0;
@@ -243,6 +246,66 @@ std::vector<double> projection_matrix(const shd_ctx *c)
     return B;
 }
 
+// BF16 round-to-nearest-even of a float (finite inputs).
+uint16_t bf16_rne(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+double bf16_val(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+int canon_offset(int r, int k, int K) { return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7); }
+
+// Tensor-core operands of the mixed path: a value x is stored as BF16
+// hi = bf16(x) and lo = bf16(x - hi), in the canonical K-major layout.
+int upload_tc_operands(shd_ctx *c, const std::vector<double> &Bp)
+{
+    dfree(c->d_tc_Bh); dfree(c->d_tc_Bl); dfree(c->d_tc_Yh); dfree(c->d_tc_Yl);
+    if (c->precision != SHD_MIXED) return SHD_OK;
+    auto up = [](int v, int m) { return (v + m - 1) / m * m; };
+    c->tc_Kp = up(c->N, 32);
+    c->tc_Np = up(c->N, 32);
+    c->tc_Kq = up(c->NLM, 16);
+    std::vector<uint16_t> bh((size_t)c->NB * c->tc_Kp, 0), bl(bh.size(), 0);
+    for (int k = 0; k < c->N; ++k)
+        for (int j = 0; j < c->NB; ++j) {
+            double x = Bp[(size_t)k * c->NB + j];
+            uint16_t h = bf16_rne((float)x);
+            uint16_t l = bf16_rne((float)(x - bf16_val(h)));
+            int o = canon_offset(j, k, c->tc_Kp);
+            bh[o] = h;
+            bl[o] = l;
+        }
+    std::vector<uint16_t> yh((size_t)c->tc_Np * c->tc_Kq, 0), yl(yh.size(), 0);
+    for (int k = 0; k < c->N; ++k)
+        for (int p = 0; p < c->NLM; ++p) {
+            double x = c->h_Y[(size_t)k * c->NLM + p];
+            uint16_t h = bf16_rne((float)x);
+            uint16_t l = bf16_rne((float)(x - bf16_val(h)));
+            int o = canon_offset(k, p, c->tc_Kq);
+            yh[o] = h;
+            yl[o] = l;
+        }
+    int rc;
+    if ((rc = dalloc(c, &c->d_tc_Bh, bh.size() * 2, "tc Bh"))) return rc;
+    if ((rc = dalloc(c, &c->d_tc_Bl, bl.size() * 2, "tc Bl"))) return rc;
+    if ((rc = dalloc(c, &c->d_tc_Yh, yh.size() * 2, "tc Yh"))) return rc;
+    if ((rc = dalloc(c, &c->d_tc_Yl, yl.size() * 2, "tc Yl"))) return rc;
+    CK(cudaMemcpy(c->d_tc_Bh, bh.data(), bh.size() * 2, cudaMemcpyHostToDevice), "tc Bh");
+    CK(cudaMemcpy(c->d_tc_Bl, bl.data(), bl.size() * 2, cudaMemcpyHostToDevice), "tc Bl");
+    CK(cudaMemcpy(c->d_tc_Yh, yh.data(), yh.size() * 2, cudaMemcpyHostToDevice), "tc Yh");
+    CK(cudaMemcpy(c->d_tc_Yl, yl.data(), yl.size() * 2, cudaMemcpyHostToDevice), "tc Yl");
+    return SHD_OK;
+}
+
 int upload_angles(shd_ctx *c)
 {
     dfree(c->d_ord); dfree(c->d_W); dfree(c->d_dirs); dfree(c->d_Y); dfree(c->d_mu); dfree(c->d_Bproj);
@@ -265,7 +328,7 @@ int upload_angles(shd_ctx *c)
         c->d_mu = to_device_vec<float>(c->h_mu, c->bytes, e); CK(e, "mu");
         c->d_Bproj = to_device_vec<float>(Bp, c->bytes, e); CK(e, "Bproj");
     }
-    return SHD_OK;
+    return upload_tc_operands(c, Bp);
 }
 
 bool sized(const shd_ctx *c) { return c->have_grid && c->have_angles && c->have_groups; }
@@ -319,12 +382,15 @@ int stream_after(cudaStream_t waiter, cudaStream_t producer)
 // brick by brick so that a brick's remap CTAs run side by side.
 int build_tiles(shd_ctx *c, const double *u)
 {
-    dfree(c->d_tiles); dfree((void *&)c->d_moving); dfree((void *&)c->d_mflag); dfree(c->d_buf);
+    dfree(c->d_tiles); dfree((void *&)c->d_moving); dfree((void *&)c->d_mflag);
+    dfree((void *&)c->d_midx); dfree((void *&)c->d_mtiles);
+    for (int i = 0; i < 3; ++i) dfree(c->d_nm[i]);
     int tx = (c->nx + 7) / 8, ty = (c->ny + 7) / 8;
     std::vector<TileInfo> tiles;
     tiles.reserve((size_t)tx * ty * c->nz);
     std::vector<long long> moving;
     std::vector<unsigned char> mflag((size_t)c->Nc, 0);
+    std::vector<int> midx((size_t)c->Nc, -1), mtiles;
     for (int z = 0; z < c->nz; ++z)
         for (int by = 0; by < ty; ++by)
             for (int bx = 0; bx < tx; ++bx) {
@@ -337,9 +403,11 @@ int build_tiles(shd_ctx *c, const double *u)
                     if (un[0] != 0.0 || un[1] != 0.0 || un[2] != 0.0) {
                         t.flags |= 1;
                         mflag[node] = 1;
+                        midx[node] = (int)moving.size();
                         moving.push_back(node);
                     }
                 }
+                if (t.flags & 1) mtiles.push_back((int)tiles.size());
                 tiles.push_back(t);
             }
     c->ntiles = (long long)tiles.size();
@@ -349,11 +417,17 @@ int build_tiles(shd_ctx *c, const double *u)
     CK(cudaMemcpy(c->d_tiles, tiles.data(), sizeof(TileInfo) * tiles.size(), cudaMemcpyHostToDevice), "tiles");
     if ((rc = dalloc(c, (void **)&c->d_mflag, mflag.size(), "mflag"))) return rc;
     CK(cudaMemcpy(c->d_mflag, mflag.data(), mflag.size(), cudaMemcpyHostToDevice), "mflag");
+    if ((rc = dalloc(c, (void **)&c->d_midx, sizeof(int) * midx.size(), "midx"))) return rc;
+    CK(cudaMemcpy(c->d_midx, midx.data(), sizeof(int) * midx.size(), cudaMemcpyHostToDevice), "midx");
+    c->nmtiles = (long long)mtiles.size();
     if (c->nmoving > 0) {
         if ((rc = dalloc(c, (void **)&c->d_moving, sizeof(long long) * moving.size(), "moving"))) return rc;
         CK(cudaMemcpy(c->d_moving, moving.data(), sizeof(long long) * moving.size(), cudaMemcpyHostToDevice), "moving");
-        size_t nDO = (size_t)c->Nc * c->G * c->N;
-        if ((rc = dalloc(c, &c->d_buf, nDO * c->esize, "remap scratch"))) return rc;
+        if ((rc = dalloc(c, (void **)&c->d_mtiles, sizeof(int) * mtiles.size(), "mtiles"))) return rc;
+        CK(cudaMemcpy(c->d_mtiles, mtiles.data(), sizeof(int) * mtiles.size(), cudaMemcpyHostToDevice), "mtiles");
+        size_t nNM = (size_t)c->nmoving * c->G * c->N;
+        for (int i = 0; i < 3; ++i)
+            if ((rc = dalloc(c, &c->d_nm[i], nNM * c->esize, "remap scratch"))) return rc;
     }
     return SHD_OK;
 }
@@ -420,6 +494,20 @@ int download_reals(shd_ctx *c, const void *src, double *h, size_t n)
         CK(cudaMemcpyAsync(h + off, c->d_stage, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream), "D2H");
         CK(cudaStreamSynchronize(c->stream), "sync");
         off += m;
+    }
+    return SHD_OK;
+}
+
+// A tensor-core kernel that gave up on a bounded wait leaves a flag behind;
+// the next synchronous call reports it (and clears it).
+int check_device_flags(shd_ctx *c)
+{
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read flag");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (flag) {
+        cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream);
+        return fail(SHD_ERR_TIMEOUT, "a tensor-core kernel timed out waiting for its MMAs");
     }
     return SHD_OK;
 }
@@ -497,6 +585,9 @@ int shd_create(shd_ctx **out, int device, int precision)
     e = cudaMalloc(&c->d_sums, sizeof(double) * 4);
     if (e != cudaSuccess) { cudaStreamDestroy(c->stream); delete c; return cuda_fail(e, "cudaMalloc"); }
     cudaMemset(c->d_sums, 0, sizeof(double) * 4);
+    e = cudaMalloc(&c->d_tc_err, sizeof(int));
+    if (e != cudaSuccess) { cudaFree(c->d_sums); cudaStreamDestroy(c->stream); delete c; return cuda_fail(e, "cudaMalloc"); }
+    cudaMemset(c->d_tc_err, 0, sizeof(int));
     *out = c;
     g_err[0] = 0;
     return SHD_OK;
@@ -877,6 +968,7 @@ int shd_get_moments(shd_ctx *c, double *J, double *H, double *K, double *Ish)
         if ((rc = download_reals<float>(c, c->d_mom, mom.data(), nCG * 10))) return rc;
         if (Ish && (rc = download_reals<float>(c, c->d_Ip, Ish, nCG * c->NLM))) return rc;
     }
+    if ((rc = check_device_flags(c))) return rc;
     for (size_t i = 0; i < nCG; ++i) {
         if (J) J[i] = mom[i * 10];
         if (H) for (int q = 0; q < 3; ++q) H[i * 3 + q] = mom[i * 10 + 1 + q];
@@ -889,6 +981,7 @@ int shd_get_sums(shd_ctx *c, double *energy, double *photons, double *resid)
 {
     int rc = ctx_check(c);
     if (rc) return rc;
+    if ((rc = check_device_flags(c))) return rc;
     double s[3];
     CK(cudaMemcpyAsync(s, c->d_sums, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream), "D2H sums");
     CK(cudaStreamSynchronize(c->stream), "sync");

@@ -71,8 +71,12 @@ struct Prob {
     const long long *moving;      // [nmoving] node ids with u != 0, brick by brick
     long long nmoving;
     const unsigned char *mflag;   // [Nc] 1 where u != 0
+    const int *midx;              // [Nc] index of the node in `moving`, -1 at rest
+    const int *mtiles;            // [nmtiles] tiles holding a moving node
+    long long nmtiles;
     const T *Bproj;        // [N][NB]: W_k Y_p(n_k) | W_k {1, n, nn}/(4 pi) | 0
     int NB;
+    int fp64_boost;        // Doppler factor and aberration in FP64 where Gamma > 10
     const T *lc;           // [G] log of the group centres
     const T *linv;         // [G] 1/(lc[g+1] - lc[g])
     T le0, leG;            // log of the outer edges
@@ -133,8 +137,19 @@ struct shd_ctx {
     unsigned char *d_mflag = nullptr; // [Nc]
     void *d_Bproj = nullptr;          // [N][NB]
     int NB = 0;
-    void *d_buf = nullptr;            // DO-layout scratch: I0 / S0 of moving nodes
+    int *d_midx = nullptr;            // [Nc] moving index or -1
+    int *d_mtiles = nullptr;          // tiles holding a moving node
+    long long nmtiles = 0;
+    // node-major scratch [m][g][k] of the moving nodes (Lorentz remaps):
+    // project: nm[0] = laboratory I, nm[1] = comoving I0;
+    // sh2lab:  nm[0] = comoving S0, nm[1] = eta_lab, nm[2] = chi_lab
+    void *d_nm[3] = {nullptr, nullptr, nullptr};
     void *d_lc = nullptr, *d_linv = nullptr;  // log-energy group tables
+    // tensor-core operands of the mixed path (BF16 hi / lo, canonical K-major)
+    void *d_tc_Bh = nullptr, *d_tc_Bl = nullptr;  // [NB][tc_Kp]   projection matrix
+    void *d_tc_Yh = nullptr, *d_tc_Yl = nullptr;  // [tc_Np][tc_Kq] harmonics
+    int tc_Kp = 0, tc_Np = 0, tc_Kq = 0;
+    int *d_tc_err = nullptr;                      // set by a kernel whose wait timed out
     double *d_stage = nullptr;    // staging buffer for host <-> device copies (FP64)
     size_t stage_elems = 0;
     long long bytes = 0;
@@ -211,6 +226,28 @@ __device__ inline R boost_dir(const R u[3], const R n[3], R out[3], R sgn)
 #pragma unroll
     for (int i = 0; i < 3; ++i) out[i] = (n[i] - sgn * u[i] * f) * ir;
     return r;
+}
+
+// The boost of boost_dir evaluated in FP64 for a float problem (the mixed
+// path's FP64 island for Lorentz factors above 10).
+__device__ inline float boost_dir_fp64(const float u[3], const float n[3], float out[3], float sgn)
+{
+    double ud[3] = {u[0], u[1], u[2]}, nd[3] = {n[0], n[1], n[2]}, od[3];
+    double r = boost_dir<double>(ud, nd, od, (double)sgn);
+    out[0] = (float)od[0]; out[1] = (float)od[1]; out[2] = (float)od[2];
+    return (float)r;
+}
+
+template <class T>
+__device__ inline T boost_any(const T u[3], const T n[3], T out[3], T sgn, int fp64_boost)
+{
+    return boost_dir<T>(u, n, out, sgn);
+}
+template <>
+__device__ inline float boost_any<float>(const float u[3], const float n[3], float out[3], float sgn, int fp64_boost)
+{
+    if (fp64_boost && u[0] * u[0] + u[1] * u[1] + u[2] * u[2] > 99.f) return boost_dir_fp64(u, n, out, sgn);
+    return boost_dir<float>(u, n, out, sgn);
 }
 
 // Bilinear stencil on an ordinate mesh (mu ascending Gauss rings, phi
@@ -375,6 +412,13 @@ template <class T>
 cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st);
 template <class T>
 cudaError_t launch_project_scratch(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *scratch, cudaStream_t st);
+bool tc_usable(const shd_ctx *ctx);
+size_t project_tc_smem_bytes(const shd_ctx *ctx);
+size_t sh2lab_tc_smem_bytes(const shd_ctx *ctx);
+cudaError_t launch_project_tc(const shd_ctx *ctx, const float *I, float *Ip, float *mom, const float *I0n,
+                              cudaStream_t st);
+cudaError_t launch_sh2lab_tc(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *S0n,
+                             cudaStream_t st);
 template <class T>
 cudaError_t launch_source(const shd_ctx *ctx, const T *Ip, T *Sp, cudaStream_t st);
 template <class T>
@@ -400,6 +444,8 @@ cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, do
                             const double *d_gx, const double *d_gw, int nq, cudaStream_t st);
 
 size_t remap_smem_bytes(const shd_ctx *ctx);
+template <class T>
+cudaError_t launch_project_nm(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *nm0, T *nm1, cudaStream_t st);
 size_t sh2lab_tile_smem_bytes(const shd_ctx *ctx);
 size_t sweep_smem_bytes(const shd_ctx *ctx);
 

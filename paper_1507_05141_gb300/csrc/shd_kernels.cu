@@ -32,7 +32,9 @@ Prob<T> make_prob(const shd_ctx *c)
     p.bc_mode = c->bc_mode; p.bc = (const T *)c->d_bc;
     p.tiles = (const TileInfo *)c->d_tiles; p.ntiles = c->ntiles;
     p.moving = c->d_moving; p.nmoving = c->nmoving; p.mflag = c->d_mflag;
+    p.midx = c->d_midx; p.mtiles = c->d_mtiles; p.nmtiles = c->nmtiles;
     p.Bproj = (const T *)c->d_Bproj; p.NB = c->NB;
+    p.fp64_boost = c->precision == SHD_MIXED ? 1 : 0;
     p.lc = (const T *)c->d_lc; p.linv = (const T *)c->d_linv;
     p.le0 = c->G ? (T)std::log(c->h_edges[0]) : T(0);
     p.leG = c->G ? (T)std::log(c->h_edges[c->G]) : T(0);

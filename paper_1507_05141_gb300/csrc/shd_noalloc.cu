@@ -69,7 +69,7 @@ extern "C" int shd_project_noalloc(shd_ctx *c, void *dev_Ish, void *dev_mom, voi
         return SHD_ERR_CUDA;
     }
     if (c->nmoving > 0) {
-        size_t need = (size_t)c->Nc * c->G * c->N * c->esize;
+        size_t need = (size_t)2 * c->nmoving * c->G * c->N * c->esize;
         if (need > (size_t)SHD_NOALLOC_SCRATCH_BYTES) {
             snprintf(g_msg, sizeof(g_msg), "needs %zu bytes of scratch, the static scratch holds %zu", need,
                      (size_t)SHD_NOALLOC_SCRATCH_BYTES);

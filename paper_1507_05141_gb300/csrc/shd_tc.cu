@@ -1,0 +1,522 @@
+// Stages a1 (project) and a3 (sh2lab) of the mixed-precision path on the
+// tcgen05 tensor cores.
+//
+// Both are contractions over a node brick (8 x 8 nodes in (x, y) at one z)
+// and a pair of groups, i.e. M = 128 rows = 2 groups x 64 nodes:
+//   a1  D[128 x NB] = A[128 x N] . Bp^T,  A = intensities (laboratory, or
+//       comoving for moving nodes), Bp = [W_k Y_p(n_k) | moment weights]
+//   a3  D[128 x N]  = S[128 x NLM] . Y^T, then eta = chi0 D, chi = chi0
+//       (moving nodes: D to the node-major remap scratch)
+// FP32 operands are split into BF16 hi + lo (x = hi + lo to ~16 bits) and
+// the three products hi.hi + hi.lo + lo.hi accumulate in FP32 in tensor
+// memory; the dropped lo.lo term is below 2^-16 of the result.  The
+// right-hand matrix stays resident in shared memory for the whole
+// persistent CTA; A chunks are built by the threads in the canonical K-major
+// layout and double-buffered against the MMAs with two mbarriers.  Every
+// mbarrier wait is bounded: on timeout the kernel raises *err, drains what it
+// issued (again bounded), frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "shd_internal.cuh"
+#include "shd_tc.cuh"
+
+namespace shd {
+
+namespace {
+
+constexpr long long kWaitLimit = 1LL << 24;  // mbarrier polls before giving up (order of a second)
+
+__device__ inline int brick_row(int d, int q)
+{
+    // element q of a run-ordered brick -> row (iy - y0)*8 + (ix - x0); runs
+    // follow x in the z- and y-dominant layouts and y in the x-dominant one
+    return d == 0 ? ((q & 7) << 3) | (q >> 3) : q;
+}
+
+template <class V>
+__device__ inline V pick3(int d, V a, V b, V c)
+{
+    return d == 0 ? a : (d == 1 ? b : c);
+}
+
+__device__ inline void split_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+    __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+    hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+}
+
+// one thread waits (bounded), the CTA learns the outcome
+__device__ inline bool cta_wait(uint64_t *bar, uint32_t parity, int *abort_flag)
+{
+    if (threadIdx.x == 0) {
+        if (!tc::mbar_wait(bar, parity, kWaitLimit)) *abort_flag = 1;
+    }
+    __syncthreads();
+    return *abort_flag == 0;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------------
+// a1 on tensor cores.  Shared memory: Bh, Bl [NB][Kp] (resident), A stages
+// [2][hi, lo][128][KC], two mbarriers, the tensor-memory address.
+// -------------------------------------------------------------------------
+template <int KC>
+__global__ void __launch_bounds__(256, 1) k_project_tc(Prob<float> P, const float *__restrict__ I,
+                                                       const float *__restrict__ I0, float *__restrict__ Ip,
+                                                       float *__restrict__ mom, const uint16_t *__restrict__ gBh,
+                                                       const uint16_t *__restrict__ gBl, int NB, int Kp,
+                                                       int tmem_cols, int *err)
+{
+    constexpr int NV = KC / 2;  // A values a thread gathers per chunk
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    uint16_t *Bh = reinterpret_cast<uint16_t *>(smem_raw);
+    uint16_t *Bl = Bh + (size_t)NB * Kp;
+    uint16_t *As = Bl + (size_t)NB * Kp;  // [2][2][128 * KC]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(As + (size_t)4 * 128 * KC);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    unsigned char *cls = reinterpret_cast<unsigned char *>(abort_flag + 1);  // [Kp] sweep layout of each ordinate
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = P.N, G = P.G, NLM = P.NLM;
+    {
+        const uint4 *sh = reinterpret_cast<const uint4 *>(gBh), *sl = reinterpret_cast<const uint4 *>(gBl);
+        uint4 *dh = reinterpret_cast<uint4 *>(Bh), *dl = reinterpret_cast<uint4 *>(Bl);
+        const int n16 = NB * Kp / 8;
+        for (int i = tid; i < n16; i += 256) {
+            dh[i] = sh[i];
+            dl[i] = sl[i];
+        }
+        for (int k = tid; k < Kp; k += 256) cls[k] = k < N ? (unsigned char)P.ord[k].d : 0;
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, tmem_cols);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16(128, NB);
+    const uint32_t a_sbo = (KC / 8) * 128, b_sbo = (Kp / 8) * 128;
+
+    uint32_t phase[2] = {0, 0};
+    bool pending[2] = {false, false};
+    long long chunk_ctr = 0;
+    const int nchunk = Kp / KC;
+    const int npair = (G + 1) / 2;
+    const long long items = P.ntiles * npair;
+    // a thread always gathers row slot q = tid & 127 (group gi, brick element
+    // qq) and the ordinate pairs kp = (tid >> 7) + 2i of every chunk
+    const int q = tid & 127, gi = q >> 6, qq = q & 63, kp0 = tid >> 7;
+
+    for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+        const long long tile = w / npair;
+        const int pair = (int)(w - tile * npair);
+        const TileInfo ti = P.tiles[tile];
+        const int passes = (ti.flags & 1) ? 2 : 1;
+        const int g = 2 * pair + gi;
+        // per sweep layout d: the node of this slot, its offset, validity
+        // per sweep layout d = 0, 1, 2 (scalars, selected with pick3: no
+        // dynamically indexed arrays)
+        long long off0, off1, off2;
+        int row0, row1, row2, m0, m1, m2;
+        bool ok0, ok1, ok2;
+        {
+            auto setup = [&](int d, long long &off, int &row, bool &ok, int &m) {
+                const int rr = brick_row(d, qq);
+                const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
+                row = gi * 64 + rr;
+                ok = g < G && ix < P.nx && iy < P.ny;
+                off = ok ? perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz) : 0;
+                m = ok ? P.midx[((long long)ti.z * P.ny + iy) * P.nx + ix] : -1;
+            };
+            setup(0, off0, row0, ok0, m0);
+            setup(1, off1, row1, ok1, m1);
+            setup(2, off2, row2, ok2, m2);
+        }
+        const long long gNc = (long long)(g < G ? g : 0) * P.Nc, GNc = (long long)G * P.Nc;
+        for (int pass = 0; pass < passes; ++pass) {
+            // element kk of layout d: base_d + kk * stride_d -- the sweep layout,
+            // or (pass 1, moving node) the node-major comoving row
+            auto base_of = [&](int m, long long off) -> const float * {
+                return (pass == 1 && m >= 0) ? I0 + ((long long)m * G + g) * N : I + gNc + off;
+            };
+            const float *base0 = base_of(m0, off0), *base1 = base_of(m1, off1), *base2 = base_of(m2, off2);
+            const long long str0 = (pass == 1 && m0 >= 0) ? 1 : GNc;
+            const long long str1 = (pass == 1 && m1 >= 0) ? 1 : GNc;
+            const long long str2 = (pass == 1 && m2 >= 0) ? 1 : GNc;
+            auto load = [&](int ch, float (&v)[NV]) {
+#pragma unroll
+                for (int i = 0; i < NV / 2; ++i) {
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const int kk = ch * KC + 2 * (kp0 + 2 * i) + t;
+                        float x = 0.f;
+                        if (kk < N) {
+                            const int d = cls[kk];
+                            if (pick3(d, ok0, ok1, ok2))
+                                x = __ldg(pick3(d, base0, base1, base2) + (long long)kk * pick3(d, str0, str1, str2));
+                        }
+                        v[2 * i + t] = x;
+                    }
+                }
+            };
+            auto step = [&](int ch, const float (&v)[NV]) -> bool {
+                const int s = (int)(chunk_ctr & 1);
+                if (pending[s]) {
+                    if (!cta_wait(&bars[s], phase[s], abort_flag)) return false;
+                    phase[s] ^= 1;
+                    pending[s] = false;
+                }
+                uint16_t *Ah = As + (size_t)(2 * s) * 128 * KC;
+                uint16_t *Al = Ah + (size_t)128 * KC;
+#pragma unroll
+                for (int i = 0; i < NV / 2; ++i) {
+                    const int kl = 2 * (kp0 + 2 * i);
+                    const int kk = ch * KC + kl;
+                    const int d0 = kk < N ? cls[kk] : 2, d1 = kk + 1 < N ? cls[kk + 1] : 2;
+                    const int r0 = kk < N ? pick3(d0, row0, row1, row2) : gi * 64 + qq;
+                    const int r1 = kk + 1 < N ? pick3(d1, row0, row1, row2) : gi * 64 + qq;
+                    if (r0 == r1) {
+                        uint32_t hi, lo;
+                        split_bf16x2(v[2 * i], v[2 * i + 1], hi, lo);
+                        const int o = tc::canon_off(r0, kl, KC);
+                        *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
+                        *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
+                    } else {
+                        // the two ordinates use different layouts, so the same slot q
+                        // is a different row; each (row, k) is still written once,
+                        // because the brick permutation of a layout is a bijection
+                        const int rs[2] = {r0, r1};
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            __nv_bfloat16 h = __float2bfloat16_rn(v[2 * i + t]);
+                            __nv_bfloat16 l = __float2bfloat16_rn(v[2 * i + t] - __bfloat162float(h));
+                            const int o = tc::canon_off(rs[t], kl + t, KC);
+                            Ah[o] = __bfloat16_as_ushort(h);
+                            Al[o] = __bfloat16_as_ushort(l);
+                        }
+                    }
+                }
+                tc::fence_proxy_async();
+                __syncthreads();
+                if (tid == 0) {
+                    tc::fence_after_sync();
+                    const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al);
+                    const uint32_t bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
+#pragma unroll
+                    for (int j = 0; j < KC / 16; ++j) {
+                        const uint32_t aoff = j * 256;  // 2 core matrices of 128 B
+                        const uint32_t boff = (uint32_t)(ch * KC / 16 + j) * 256;
+                        const uint64_t dah = tc::sdesc(ah + aoff, 128, a_sbo), dal = tc::sdesc(al + aoff, 128, a_sbo);
+                        const uint64_t dbh = tc::sdesc(bh + boff, 128, b_sbo), dbl = tc::sdesc(bl + boff, 128, b_sbo);
+                        const uint32_t acc0 = (ch > 0 || j > 0) ? 1u : 0u;
+                        tc::mma_bf16(tmem, dah, dbh, idesc, acc0);
+                        tc::mma_bf16(tmem, dah, dbl, idesc, 1u);
+                        tc::mma_bf16(tmem, dal, dbh, idesc, 1u);
+                    }
+                    tc::mma_commit(&bars[s]);
+                }
+                pending[s] = true;
+                ++chunk_ctr;
+                return true;
+            };
+            // two register sets: chunk ch+2 loads while chunks ch, ch+1 are stored
+            float va[NV], vb[NV];
+            load(0, va);
+            if (nchunk > 1) load(1, vb);
+            for (int ch = 0; ch < nchunk; ch += 2) {
+                if (!step(ch, va)) goto drain;
+                if (ch + 2 < nchunk) load(ch + 2, va);
+                if (ch + 1 < nchunk) {
+                    if (!step(ch + 1, vb)) goto drain;
+                    if (ch + 3 < nchunk) load(ch + 3, vb);
+                }
+            }
+            // all MMAs of this pass done
+            for (int s = 0; s < 2; ++s) {
+                if (pending[s]) {
+                    if (!cta_wait(&bars[s], phase[s], abort_flag)) goto drain;
+                    phase[s] ^= 1;
+                    pending[s] = false;
+                }
+            }
+            tc::fence_after_sync();
+            if (warp < 4) {
+                const int r = warp * 32 + lane;
+                const int egi = r >> 6, rr = r & 63;
+                const int eg = 2 * pair + egi;
+                const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
+                const bool valid = eg < G && ix < P.nx && iy < P.ny;
+                const long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+                const bool moving = valid && P.midx[c] >= 0;
+                const bool write_sh = valid && ((pass == 0 && !moving) || (pass == 1 && moving));
+                const bool write_mom = valid && pass == 0;
+                float *ip = Ip + (c * G + eg) * NLM;
+                float *mp = mom + (c * G + eg) * 10;
+                for (int c0 = 0; c0 < NB; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = c0 + j;
+                        if (col < NLM) {
+                            if (write_sh) ip[col] = v[j];
+                        } else if (col < NLM + 10) {
+                            if (write_mom) mp[col - NLM] = v[j];
+                        }
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+        }
+    }
+    goto done;
+drain:
+    if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        for (int s = 0; s < 2; ++s)
+            if (pending[s]) tc::mbar_wait(&bars[s], phase[s], kWaitLimit);
+    }
+done:
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+// -------------------------------------------------------------------------
+// a3 on tensor cores.  Shared memory: Yh, Yl [Np][Kq] (resident), A hi/lo
+// [128][Kq], chi0 and moving flags of the 128 rows, one mbarrier.
+// -------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 1) k_sh2lab_tc(Prob<float> P, const float *__restrict__ Sp,
+                                                      float *__restrict__ eta, float *__restrict__ chi,
+                                                      float *__restrict__ S0, const uint16_t *__restrict__ gYh,
+                                                      const uint16_t *__restrict__ gYl, int Np, int Kq, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    uint16_t *Yh = reinterpret_cast<uint16_t *>(smem_raw);
+    uint16_t *Yl = Yh + (size_t)Np * Kq;
+    uint16_t *Ah = Yl + (size_t)Np * Kq;
+    uint16_t *Al = Ah + (size_t)128 * Kq;
+    float *chir = reinterpret_cast<float *>(Al + (size_t)128 * Kq);
+    int *mrow = reinterpret_cast<int *>(chir + 128);  // moving index of the row, -1 at rest
+    uint64_t *bar = reinterpret_cast<uint64_t *>(mrow + 128);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    unsigned char *cls = reinterpret_cast<unsigned char *>(abort_flag + 1);  // [Np]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = P.N, G = P.G, NLM = P.NLM;
+    {
+        const uint4 *sh = reinterpret_cast<const uint4 *>(gYh), *sl = reinterpret_cast<const uint4 *>(gYl);
+        uint4 *dh = reinterpret_cast<uint4 *>(Yh), *dl = reinterpret_cast<uint4 *>(Yl);
+        const int n16 = Np * Kq / 8;
+        for (int i = tid; i < n16; i += 256) {
+            dh[i] = sh[i];
+            dl[i] = sl[i];
+        }
+        for (int k = tid; k < Np; k += 256) cls[k] = k < N ? (unsigned char)P.ord[k].d : 0;
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t a_sbo = (Kq / 8) * 128, b_sbo = (Kq / 8) * 128;
+    uint32_t phase = 0;
+    bool pending = false;
+    const int npair = (G + 1) / 2;
+    const long long items = P.ntiles * npair;
+
+    for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+        const long long tile = w / npair;
+        const int pair = (int)(w - tile * npair);
+        const TileInfo ti = P.tiles[tile];
+        // rows of S (coalesced along p), split into hi / lo
+        for (int e = tid; e < 128 * (Kq / 2); e += 256) {
+            const int r = e / (Kq / 2), pp = 2 * (e - r * (Kq / 2));
+            const int gi = r >> 6, rr = r & 63;
+            const int g = 2 * pair + gi;
+            const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
+            float v0 = 0.f, v1 = 0.f;
+            if (g < G && ix < P.nx && iy < P.ny) {
+                const long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+                const float *row = Sp + (c * G + g) * NLM;
+                if (pp < NLM) v0 = row[pp];
+                if (pp + 1 < NLM) v1 = row[pp + 1];
+            }
+            uint32_t hi, lo;
+            split_bf16x2(v0, v1, hi, lo);
+            const int o = tc::canon_off(r, pp, Kq);
+            *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
+            *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
+        }
+        if (tid < 128) {
+            const int r = tid, gi = r >> 6, rr = r & 63, g = 2 * pair + gi;
+            const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
+            float ch = 0.f;
+            int m = -1;
+            if (g < G && ix < P.nx && iy < P.ny) {
+                const long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+                ch = P.chi0[c * G + g];
+                m = P.midx[c];
+            }
+            chir[r] = ch;
+            mrow[r] = m;
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al);
+            for (int h = 0; h * 256 < Np; ++h) {
+                const int nh = Np - 256 * h < 256 ? Np - 256 * h : 256;
+                const uint32_t idesc = tc::idesc_bf16(128, nh);
+                const uint32_t yoff = (uint32_t)(256 * h / 8) * b_sbo;  // 256 rows = 32 core-matrix rows
+                const uint32_t yh = tc::smem_u32(Yh) + yoff, yl = tc::smem_u32(Yl) + yoff;
+                for (int j = 0; j < Kq / 16; ++j) {
+                    const uint32_t koff = j * 256;
+                    const uint64_t dah = tc::sdesc(ah + koff, 128, a_sbo), dal = tc::sdesc(al + koff, 128, a_sbo);
+                    const uint64_t dbh = tc::sdesc(yh + koff, 128, b_sbo), dbl = tc::sdesc(yl + koff, 128, b_sbo);
+                    const uint32_t d = tmem + (uint32_t)(256 * h);
+                    tc::mma_bf16(d, dah, dbh, idesc, j > 0 ? 1u : 0u);
+                    tc::mma_bf16(d, dah, dbl, idesc, 1u);
+                    tc::mma_bf16(d, dal, dbh, idesc, 1u);
+                }
+            }
+            tc::mma_commit(bar);
+        }
+        pending = true;
+        if (!cta_wait(bar, phase, abort_flag)) goto drain;
+        phase ^= 1;
+        pending = false;
+        tc::fence_after_sync();
+        {
+            // warps w and w+4 share tensor-memory lanes 32*(w%4)..; they split the columns
+            const int quad = warp & 3, half = warp >> 2;
+            const int r = quad * 32 + lane;
+            const int gi = r >> 6, rr = r & 63;
+            const int g = 2 * pair + gi;
+            const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
+            const bool valid = g < G && ix < P.nx && iy < P.ny;
+            const float ch = chir[r];
+            const int mr = mrow[r];
+            float *s0row = mr >= 0 ? S0 + ((long long)mr * G + (g < G ? g : 0)) * N : nullptr;
+            const long long gNc = (long long)(g < G ? g : 0) * P.Nc;
+            const long long off0 = valid ? gNc + perm_offset(0, ix, iy, ti.z, P.nx, P.ny, P.nz) : 0;
+            const long long off1 = valid ? gNc + perm_offset(1, ix, iy, ti.z, P.nx, P.ny, P.nz) : 0;
+            const long long off2 = valid ? gNc + perm_offset(2, ix, iy, ti.z, P.nx, P.ny, P.nz) : 0;
+            const long long GNc = (long long)G * P.Nc;
+            const int cbeg = half * (Np / 2), cend = half ? Np : Np / 2;
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+                if (!valid) continue;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int k = c0 + j;
+                    if (k < N) {
+                        if (mr >= 0) {
+                            s0row[k] = v[j];  // comoving, node-major
+                        } else {
+                            const long long a = (long long)k * GNc + pick3((int)cls[k], off0, off1, off2);
+                            eta[a] = ch * v[j];
+                            chi[a] = ch;
+                        }
+                    }
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    goto done;
+drain:
+    if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        if (pending) tc::mbar_wait(bar, phase, kWaitLimit);
+    }
+done:
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// -------------------------------------------------------------------------
+// host side
+// -------------------------------------------------------------------------
+static constexpr int kProjKC = 32;
+
+size_t project_tc_smem_bytes(const shd_ctx *c)
+{
+    return (size_t)2 * c->NB * c->tc_Kp * 2 + (size_t)4 * 128 * kProjKC * 2 + 64 + (size_t)c->tc_Kp;
+}
+size_t sh2lab_tc_smem_bytes(const shd_ctx *c)
+{
+    return (size_t)2 * c->tc_Np * c->tc_Kq * 2 + (size_t)2 * 128 * c->tc_Kq * 2 + 128 * 4 + 128 * 4 + 64 +
+           (size_t)c->tc_Np;
+}
+
+bool tc_usable(const shd_ctx *c)
+{
+    if (c->precision != SHD_MIXED || !c->d_tc_Bh || !c->d_tc_Yh) return false;
+    if (c->NB > 256 || c->tc_Np > 512) return false;
+    return project_tc_smem_bytes(c) <= 227 * 1024 && sh2lab_tc_smem_bytes(c) <= 227 * 1024;
+}
+
+static int num_sms_tc(const shd_ctx *ctx)
+{
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || n <= 0) n = 148;
+    return n;
+}
+
+cudaError_t launch_project_tc(const shd_ctx *ctx, const float *I, float *Ip, float *mom, const float *I0n,
+                              cudaStream_t st)
+{
+    Prob<float> P = make_prob<float>(ctx);
+    size_t sm = project_tc_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_project_tc<kProjKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    long long items = ctx->ntiles * ((ctx->G + 1) / 2);
+    int grid = num_sms_tc(ctx);
+    if (items < grid) grid = (int)items;
+    int cols = ctx->NB <= 32 ? 32 : ctx->NB <= 64 ? 64 : ctx->NB <= 128 ? 128 : 256;
+    k_project_tc<kProjKC><<<grid, 256, sm, st>>>(P, I, I0n, Ip, mom, (const uint16_t *)ctx->d_tc_Bh,
+                                                 (const uint16_t *)ctx->d_tc_Bl, ctx->NB, ctx->tc_Kp, cols,
+                                                 ctx->d_tc_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sh2lab_tc(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *S0n, cudaStream_t st)
+{
+    Prob<float> P = make_prob<float>(ctx);
+    size_t sm = sh2lab_tc_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_sh2lab_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    long long items = ctx->ntiles * ((ctx->G + 1) / 2);
+    int grid = num_sms_tc(ctx);
+    if (items < grid) grid = (int)items;
+    k_sh2lab_tc<<<grid, 256, sm, st>>>(P, Sp, eta, chi, S0n, (const uint16_t *)ctx->d_tc_Yh,
+                                      (const uint16_t *)ctx->d_tc_Yl, ctx->tc_Np, ctx->tc_Kq, ctx->d_tc_err);
+    return cudaGetLastError();
+}
+
+}  // namespace shd

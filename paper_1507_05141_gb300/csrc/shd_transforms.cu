@@ -58,10 +58,11 @@ __global__ void __launch_bounds__(128) k_project_tile(Prob<T> P, const T *__rest
                     r = tile_row(d, q);
                     int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
                     if (ix < P.nx && iy < P.ny) {
-                        long long a = ((long long)k * P.G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
-                        const T *src = I;
-                        if (pass == 1 && P.mflag[((long long)ti.z * P.ny + iy) * P.nx + ix]) src = I0;
-                        v = src[a];
+                        const int m = P.midx[((long long)ti.z * P.ny + iy) * P.nx + ix];
+                        if (pass == 1 && m >= 0)
+                            v = I0[((long long)m * P.G + g) * P.N + k];  // comoving, node-major
+                        else
+                            v = I[((long long)k * P.G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz)];
                     }
                 }
                 As[kk][r] = v;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(256) k_sh2lab_tile(Prob<T> P, const T *__restr
     T *Bs = As + (size_t)NLM * R;             // [NLM][KC]
     T *Cs = Bs + (size_t)NLM * KC;            // [KC][R + 1]
     T *chir = Cs + (size_t)KC * (R + 1);      // [R]
-    unsigned char *mv = reinterpret_cast<unsigned char *>(chir + R);  // [R]
+    int *mrow = reinterpret_cast<int *>(chir + R);  // [R] moving index of the row, -1 at rest
     const int tile = blockIdx.x / P.G, g = blockIdx.x - (blockIdx.x / P.G) * P.G;
     const TileInfo ti = P.tiles[tile];
     const int tid = threadIdx.x, tr = tid >> 5, tc = tid & 31;
@@ -138,14 +139,14 @@ __global__ void __launch_bounds__(256) k_sh2lab_tile(Prob<T> P, const T *__restr
     for (int r = tid; r < R; r += 256) {
         int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
         T ch = T(0);
-        unsigned char m = 0;
+        int m = -1;
         if (ix < P.nx && iy < P.ny) {
             long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
             ch = P.chi0[c * P.G + g];
-            m = P.mflag[c];
+            m = P.midx[c];
         }
         chir[r] = ch;
-        mv[r] = m;
+        mrow[r] = m;
     }
     for (int k0 = 0; k0 < P.N; k0 += KC) {
         for (int e = tid; e < KC * NLM; e += 256) {
@@ -181,11 +182,12 @@ __global__ void __launch_bounds__(256) k_sh2lab_tile(Prob<T> P, const T *__restr
             int r = tile_row(d, q);
             int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
             if (ix >= P.nx || iy >= P.ny) continue;
-            long long a = ((long long)k * P.G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
             T v = Cs[(size_t)kk * (R + 1) + r];
-            if (mv[r]) {
-                S0[a] = v;
+            const int m = mrow[r];
+            if (m >= 0) {
+                S0[((long long)m * P.G + g) * P.N + k] = v;  // comoving, node-major
             } else {
+                long long a = ((long long)k * P.G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
                 T ch = chir[r];
                 eta[a] = ch * v;
                 chi[a] = ch;
@@ -251,10 +253,11 @@ __global__ void __launch_bounds__(256, 1) k_project_persist(Prob<float> P, const
                         r = tile_row(d, q);
                         int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
                         if (ix < P.nx && iy < P.ny) {
-                            long long a = ((long long)k * G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
-                            src = I;
-                            if (pass == 1 && P.mflag[((long long)ti.z * P.ny + iy) * P.nx + ix]) src = I0;
-                            src += a;
+                            const int m = P.midx[((long long)ti.z * P.ny + iy) * P.nx + ix];
+                            if (pass == 1 && m >= 0)
+                                src = I0 + ((long long)m * G + g) * N + k;  // comoving, node-major
+                            else
+                                src = I + ((long long)k * G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
                             ok = true;
                         }
                     }
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(256, 1) k_sh2lab_persist(Prob<float> P, const 
     float *As = Bs + (size_t)NLM * N;                  // [NLM][R]
     float *Cs = As + (size_t)NLM * R;                  // [KC][R + 1]
     float *chir = Cs + (size_t)KC * (R + 1);           // [R]
-    unsigned char *mv = reinterpret_cast<unsigned char *>(chir + R);  // [R]
+    int *mrow = reinterpret_cast<int *>(chir + R);     // [R] moving index, -1 at rest
     const int tid = threadIdx.x, tr = tid >> 5, tc = tid & 31;
     for (int e = tid; e < N * NLM; e += 256) {
         int k = e / NLM, p = e - k * NLM;
@@ -351,14 +354,14 @@ __global__ void __launch_bounds__(256, 1) k_sh2lab_persist(Prob<float> P, const 
         for (int r = tid; r < R; r += 256) {
             int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
             float ch = 0.f;
-            unsigned char m = 0;
+            int m = -1;
             if (ix < P.nx && iy < P.ny) {
                 long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
                 ch = P.chi0[c * G + g];
-                m = P.mflag[c];
+                m = P.midx[c];
             }
             chir[r] = ch;
-            mv[r] = m;
+            mrow[r] = m;
         }
         __syncthreads();
         for (int k0 = 0; k0 < N; k0 += KC) {
@@ -395,11 +398,12 @@ __global__ void __launch_bounds__(256, 1) k_sh2lab_persist(Prob<float> P, const 
                 int r = tile_row(d, q);
                 int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
                 if (ix >= P.nx || iy >= P.ny) continue;
-                long long a = ((long long)k * G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
                 float v = Cs[(size_t)kk * (R + 1) + r];
-                if (mv[r]) {
-                    S0[a] = v;
+                const int m = mrow[r];
+                if (m >= 0) {
+                    S0[((long long)m * G + g) * N + k] = v;  // comoving, node-major
                 } else {
+                    long long a = ((long long)k * G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
                     float ch = chir[r];
                     eta[a] = ch * v;
                     chi[a] = ch;
@@ -411,28 +415,110 @@ __global__ void __launch_bounds__(256, 1) k_sh2lab_persist(Prob<float> P, const 
 }
 
 // -------------------------------------------------------------------------
-// Lorentz remaps of moving nodes, one CTA per node (blocks of a brick are
-// consecutive so that their scattered accesses share L2 sectors).
+// Moving nodes.  Their per-node Lorentz remaps need all (ordinate, group)
+// values of one node at once, so they work on a node-major scratch
+// [m][g][k] (m = index in the moving list).  Brick transposes move data
+// between the sweep layout and that scratch through shared memory, both
+// sides coalesced: a brick is read / written as 32-byte runs per (k, g) and
+// the scratch as contiguous runs of ordinates per (m, g).
 // -------------------------------------------------------------------------
 
-// laboratory I(c, k, g) -> comoving I0(c, k0, g0) = (ebar_g0/eps)^3 I_lab(n, eps),
-// n = boost of n_k0 to the laboratory, eps = ebar_g0 (Gamma + u.n_k0)
+// sweep layout -> node-major scratch for the moving nodes of the bricks in
+// the moving-tile list; one CTA per (brick, group)
 template <class T>
-__global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ I, T *__restrict__ I0)
+__global__ void __launch_bounds__(256) k_brick_to_nodes(Prob<T> P, const T *__restrict__ src, T *__restrict__ dst)
+{
+    constexpr int R = 64, KC = 32;
+    __shared__ T S[KC][R + 1];
+    __shared__ int mrow[R];
+    const int tile = P.mtiles[blockIdx.x / P.G];
+    const int g = blockIdx.x - (blockIdx.x / P.G) * P.G;
+    const TileInfo ti = P.tiles[tile];
+    const int tid = threadIdx.x;
+    for (int r = tid; r < R; r += 256) {
+        int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+        mrow[r] = (ix < P.nx && iy < P.ny) ? P.midx[((long long)ti.z * P.ny + iy) * P.nx + ix] : -1;
+    }
+    __syncthreads();
+    for (int k0 = 0; k0 < P.N; k0 += KC) {
+        for (int e = tid; e < KC * R; e += 256) {
+            int kk = e >> 6, q = e & 63, k = k0 + kk;
+            if (k >= P.N) continue;
+            int d = P.ord[k].d;
+            int r = tile_row(d, q);
+            if (mrow[r] < 0) continue;
+            int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+            S[kk][r] = src[((long long)k * P.G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz)];
+        }
+        __syncthreads();
+        for (int e = tid; e < R * KC; e += 256) {
+            int r = e / KC, kk = e - r * KC, k = k0 + kk;
+            int m = mrow[r];
+            if (m >= 0 && k < P.N) dst[((long long)m * P.G + g) * P.N + k] = S[kk][r];
+        }
+        __syncthreads();
+    }
+}
+
+// node-major scratch (two arrays) -> sweep layout, moving nodes only
+template <class T>
+__global__ void __launch_bounds__(256) k_nodes_to_brick(Prob<T> P, const T *__restrict__ srcA,
+                                                        const T *__restrict__ srcB, T *__restrict__ dstA,
+                                                        T *__restrict__ dstB)
+{
+    constexpr int R = 64, KC = 32;
+    __shared__ T SA[KC][R + 1];
+    __shared__ T SB[KC][R + 1];
+    __shared__ int mrow[R];
+    const int tile = P.mtiles[blockIdx.x / P.G];
+    const int g = blockIdx.x - (blockIdx.x / P.G) * P.G;
+    const TileInfo ti = P.tiles[tile];
+    const int tid = threadIdx.x;
+    for (int r = tid; r < R; r += 256) {
+        int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+        mrow[r] = (ix < P.nx && iy < P.ny) ? P.midx[((long long)ti.z * P.ny + iy) * P.nx + ix] : -1;
+    }
+    __syncthreads();
+    for (int k0 = 0; k0 < P.N; k0 += KC) {
+        for (int e = tid; e < R * KC; e += 256) {
+            int r = e / KC, kk = e - r * KC, k = k0 + kk;
+            int m = mrow[r];
+            if (m >= 0 && k < P.N) {
+                long long o = ((long long)m * P.G + g) * P.N + k;
+                SA[kk][r] = srcA[o];
+                SB[kk][r] = srcB[o];
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < KC * R; e += 256) {
+            int kk = e >> 6, q = e & 63, k = k0 + kk;
+            if (k >= P.N) continue;
+            int d = P.ord[k].d;
+            int r = tile_row(d, q);
+            if (mrow[r] < 0) continue;
+            int ix = ti.x0 + (r & 7), iy = ti.y0 + (r >> 3);
+            long long a = ((long long)k * P.G + g) * P.Nc + perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz);
+            dstA[a] = SA[kk][r];
+            dstB[a] = SB[kk][r];
+        }
+        __syncthreads();
+    }
+}
+
+// laboratory I (node-major) -> comoving I0 (node-major), one CTA per moving
+// node: I0(k0, g0) = (ebar_g0/eps)^3 I_lab(n, eps), n = boost of n_k0 to the
+// laboratory, eps = ebar_g0 (Gamma + u.n_k0)   (Sec. 2.2)
+template <class T>
+__global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__restrict__ I0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G, N = P.N;
     T *sI = reinterpret_cast<T *>(smem_raw);  // [G][N]
     T *spole = sI + (size_t)G * N;            // [G][2]
-    const long long c = P.moving[blockIdx.x];
-    int ix = (int)(c % P.nx), iy = (int)((c / P.nx) % P.ny), iz = (int)(c / ((long long)P.nx * P.ny));
-    long long off[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) off[d] = perm_offset(d, ix, iy, iz, P.nx, P.ny, P.nz);
-    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
-        int k = i / G, g = i - k * G;
-        sI[(size_t)g * N + k] = I[((long long)k * G + g) * P.Nc + off[P.ord[k].d]];
-    }
+    const long long m = blockIdx.x;
+    const long long c = P.moving[m];
+    const T *src = In + m * G * N;
+    for (int i = threadIdx.x; i < G * N; i += blockDim.x) sI[i] = src[i];
     __syncthreads();
     for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
         int g = i >> 1, rr = i & 1;
@@ -443,15 +529,15 @@ __global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ I, T *__res
     }
     __syncthreads();
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
+    T *dst = I0 + m * G * N;
     for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
         T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
         T n[3];
-        T q = boost_dir<T>(u, n0, n, T(-1));  // nu/nu0
+        T q = boost_any<T>(u, n0, n, T(-1), P.fp64_boost);  // nu/nu0
         Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n);
         T iq3 = T(1) / (q * q * q);
         T lq = dlog<T>(q);
         int hint = 0;
-        long long base = (long long)k0 * G * P.Nc + off[P.ord[k0].d];
         for (int g0 = 0; g0 < G; ++g0) {
             FreqBracket<T> fb = freq_bracket<T>(P.lc, P.linv, P.le0, P.leG, G, P.lc[g0] + lq, hint);
             T v = 0;
@@ -462,31 +548,26 @@ __global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ I, T *__res
                 T fbv = eval_stencil<T>(st, sI + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
                 v = freq_mix<T>(fa, fbv, fb.t);
             }
-            I0[base + (long long)g0 * P.Nc] = v * iq3;
+            dst[(size_t)g0 * N + k0] = v * iq3;
         }
     }
 }
 
-// comoving S0(c, k0, g) (scratch buffer) -> laboratory eta, chi:
+// comoving S0 (node-major) -> laboratory eta, chi (node-major):
 // D = Gamma - u.n_k, n0 = comoving direction, eps0 = ebar_g D,
 // S_lab = S0(n0, eps0)/D^3, chi_lab = chi0(eps0) D, eta_lab = chi_lab S_lab
 template <class T>
-__global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restrict__ eta, T *__restrict__ chi)
+__global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restrict__ eta_n, T *__restrict__ chi_n)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G, N = P.N;
     T *sS = reinterpret_cast<T *>(smem_raw);  // [G][N]
     T *spole = sS + (size_t)G * N;            // [G][2]
     T *schi = spole + 2 * G;                  // [G]
-    const long long c = P.moving[blockIdx.x];
-    int ix = (int)(c % P.nx), iy = (int)((c / P.nx) % P.ny), iz = (int)(c / ((long long)P.nx * P.ny));
-    long long off[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) off[d] = perm_offset(d, ix, iy, iz, P.nx, P.ny, P.nz);
-    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
-        int k = i / G, g = i - k * G;
-        sS[(size_t)g * N + k] = S0[((long long)k * G + g) * P.Nc + off[P.ord[k].d]];
-    }
+    const long long m = blockIdx.x;
+    const long long c = P.moving[m];
+    const T *src = S0 + m * G * N;
+    for (int i = threadIdx.x; i < G * N; i += blockDim.x) sS[i] = src[i];
     for (int g = threadIdx.x; g < G; g += blockDim.x) schi[g] = P.chi0[c * G + g];
     __syncthreads();
     for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
@@ -498,15 +579,15 @@ __global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restric
     }
     __syncthreads();
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
+    T *de = eta_n + m * G * N, *dc = chi_n + m * G * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
         T n0[3];
-        T D = boost_dir<T>(u, n, n0, T(1));  // nu0/nu
+        T D = boost_any<T>(u, n, n0, T(1), P.fp64_boost);  // nu0/nu
         Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n0);
         T iD3 = T(1) / (D * D * D);
         T lD = dlog<T>(D);
         int hint = 0;
-        long long base = (long long)k * G * P.Nc + off[P.ord[k].d];
         for (int g = 0; g < G; ++g) {
             FreqBracket<T> fb = freq_bracket<T>(P.lc, P.linv, P.le0, P.leG, G, P.lc[g] + lD, hint);
             T s = 0, ch;
@@ -522,9 +603,8 @@ __global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restric
                 ch = freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], fb.t);
             }
             T chl = ch * D;
-            long long o = base + (long long)g * P.Nc;
-            chi[o] = chl;
-            eta[o] = chl * s * iD3;
+            dc[(size_t)g * N + k] = chl;
+            de[(size_t)g * N + k] = chl * s * iD3;
         }
     }
 }
@@ -536,14 +616,15 @@ size_t remap_smem_bytes(const shd_ctx *c) { return (size_t)c->esize * ((size_t)c
 
 size_t sh2lab_tile_smem_bytes(const shd_ctx *c)
 {
-    return (size_t)c->esize * ((size_t)c->NLM * 64 + (size_t)c->NLM * 128 + 128 * 65 + 64) + 64;
+    return (size_t)c->esize * ((size_t)c->NLM * 64 + (size_t)c->NLM * 128 + 128 * 65 + 64) + 64 * 4 + 64;
 }
 
 template <class T, int TC>
-static cudaError_t launch_project_tc(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st)
+static cudaError_t launch_project_tile_tc(const shd_ctx *ctx, const T *I, const T *I0n, T *Ip, T *mom,
+                                          cudaStream_t st)
 {
     Prob<T> P = make_prob<T>(ctx);
-    k_project_tile<T, TC><<<(unsigned)(ctx->ntiles * ctx->G), 128, 0, st>>>(P, I, (const T *)ctx->d_buf, Ip, mom);
+    k_project_tile<T, TC><<<(unsigned)(ctx->ntiles * ctx->G), 128, 0, st>>>(P, I, I0n, Ip, mom);
     return cudaGetLastError();
 }
 
@@ -562,7 +643,7 @@ size_t project_persist_smem_bytes(const shd_ctx *c)
 }
 size_t sh2lab_persist_smem_bytes(const shd_ctx *c)
 {
-    return sizeof(float) * ((size_t)c->NLM * c->N + (size_t)c->NLM * 64 + 128 * 65 + 64) + 64;
+    return sizeof(float) * ((size_t)c->NLM * c->N + (size_t)c->NLM * 64 + 128 * 65 + 64) + 64 * 4 + 64;
 }
 
 template <int TC>
@@ -596,50 +677,66 @@ static cudaError_t launch_project_persist(const shd_ctx *ctx, const float *I, fl
     }
 }
 
+// Moving nodes first: brick transpose of I into nm0, comoving remap into
+// nm1; then the projection contraction (reading nm1 for moving rows).
 template <class T>
-cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st)
+cudaError_t launch_project_nm(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *nm0, T *nm1, cudaStream_t st)
 {
     Prob<T> P = make_prob<T>(ctx);
     cudaError_t e;
     if (ctx->nmoving > 0) {
+        k_brick_to_nodes<T><<<(unsigned)(ctx->nmtiles * ctx->G), 256, 0, st>>>(P, I, nm0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         size_t sm = remap_smem_bytes(ctx);
         e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, I, (T *)ctx->d_buf);
+        k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if constexpr (sizeof(T) == 4) {
-        if (project_persist_smem_bytes(ctx) <= kSmemLimit)
-            return launch_project_persist(ctx, I, Ip, mom, (const float *)ctx->d_buf, st);
+        if (tc_usable(ctx)) return launch_project_tc(ctx, I, Ip, mom, nm1, st);
+        if (project_persist_smem_bytes(ctx) <= kSmemLimit) return launch_project_persist(ctx, I, Ip, mom, nm1, st);
     }
     switch (ctx->NB / 16) {
-        case 1: return launch_project_tc<T, 1>(ctx, I, Ip, mom, st);
-        case 2: return launch_project_tc<T, 2>(ctx, I, Ip, mom, st);
-        case 3: return launch_project_tc<T, 3>(ctx, I, Ip, mom, st);
-        case 4: return launch_project_tc<T, 4>(ctx, I, Ip, mom, st);
-        case 5: return launch_project_tc<T, 5>(ctx, I, Ip, mom, st);
-        case 6: return launch_project_tc<T, 6>(ctx, I, Ip, mom, st);
-        case 7: return launch_project_tc<T, 7>(ctx, I, Ip, mom, st);
-        case 8: return launch_project_tc<T, 8>(ctx, I, Ip, mom, st);
+        case 1: return launch_project_tile_tc<T, 1>(ctx, I, nm1, Ip, mom, st);
+        case 2: return launch_project_tile_tc<T, 2>(ctx, I, nm1, Ip, mom, st);
+        case 3: return launch_project_tile_tc<T, 3>(ctx, I, nm1, Ip, mom, st);
+        case 4: return launch_project_tile_tc<T, 4>(ctx, I, nm1, Ip, mom, st);
+        case 5: return launch_project_tile_tc<T, 5>(ctx, I, nm1, Ip, mom, st);
+        case 6: return launch_project_tile_tc<T, 6>(ctx, I, nm1, Ip, mom, st);
+        case 7: return launch_project_tile_tc<T, 7>(ctx, I, nm1, Ip, mom, st);
+        case 8: return launch_project_tile_tc<T, 8>(ctx, I, nm1, Ip, mom, st);
         default: return cudaErrorInvalidConfiguration;
     }
 }
 
 template <class T>
+cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaStream_t st)
+{
+    return launch_project_nm<T>(ctx, I, Ip, mom, (T *)ctx->d_nm[0], (T *)ctx->d_nm[1], st);
+}
+
+// The contraction writes S0 of moving rows to nm0; their laboratory eta, chi
+// go to nm1, nm2 and are transposed into the sweep layout.
+template <class T>
 cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st)
 {
     Prob<T> P = make_prob<T>(ctx);
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
+    T *nm0 = (T *)ctx->d_nm[0], *nm1 = (T *)ctx->d_nm[1], *nm2 = (T *)ctx->d_nm[2];
     bool done = false;
     if constexpr (sizeof(T) == 4) {
         size_t smp = sh2lab_persist_smem_bytes(ctx);
-        if (smp <= kSmemLimit) {
+        if (tc_usable(ctx)) {
+            if ((e = launch_sh2lab_tc(ctx, Sp, eta, chi, nm0, st)) != cudaSuccess) return e;
+            done = true;
+        } else if (smp <= kSmemLimit) {
             e = cudaFuncSetAttribute(k_sh2lab_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
             if (e != cudaSuccess) return e;
             long long items = ctx->ntiles * ctx->G;
             int grid = num_sms(ctx);
             if (items < grid) grid = (int)items;
-            k_sh2lab_persist<<<grid, 256, smp, st>>>(P, Sp, eta, chi, (T *)ctx->d_buf);
+            k_sh2lab_persist<<<grid, 256, smp, st>>>(P, Sp, eta, chi, nm0);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             done = true;
         }
@@ -648,53 +745,29 @@ cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaS
         size_t sm = sh2lab_tile_smem_bytes(ctx);
         e = cudaFuncSetAttribute(k_sh2lab_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_sh2lab_tile<T><<<(unsigned)(ctx->ntiles * ctx->G), 256, sm, st>>>(P, Sp, eta, chi, (T *)ctx->d_buf);
+        k_sh2lab_tile<T><<<(unsigned)(ctx->ntiles * ctx->G), 256, sm, st>>>(P, Sp, eta, chi, nm0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (ctx->nmoving > 0) {
         size_t sr = remap_smem_bytes(ctx);
         e = cudaFuncSetAttribute(k_remap_to_lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
         if (e != cudaSuccess) return e;
-        k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, (const T *)ctx->d_buf, eta, chi);
+        k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_nodes_to_brick<T><<<(unsigned)(ctx->nmtiles * ctx->G), 256, 0, st>>>(P, nm1, nm2, eta, chi);
         e = cudaGetLastError();
     }
     return e;
 }
 
-// Stage a1 with the comoving intensities of moving nodes kept in `scratch`
-// (at least Nc*G*N reals when any node moves) instead of the context's buffer.
-template <class T, int TC>
-static cudaError_t launch_project_tile_scratch(const shd_ctx *ctx, const T *I, const T *scratch, T *Ip, T *mom,
-                                               cudaStream_t st)
-{
-    Prob<T> P = make_prob<T>(ctx);
-    k_project_tile<T, TC><<<(unsigned)(ctx->ntiles * ctx->G), 128, 0, st>>>(P, I, scratch, Ip, mom);
-    return cudaGetLastError();
-}
-
+// Stage a1 with the moving nodes' node-major intermediates (laboratory I and
+// comoving I0: 2 * nmoving * G * N reals) in caller-provided `scratch`
+// instead of the context's buffers.
 template <class T>
 cudaError_t launch_project_scratch(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *scratch, cudaStream_t st)
 {
-    Prob<T> P = make_prob<T>(ctx);
-    cudaError_t e;
-    if (ctx->nmoving > 0) {
-        size_t sm = remap_smem_bytes(ctx);
-        e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, I, scratch);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    switch (ctx->NB / 16) {
-        case 1: return launch_project_tile_scratch<T, 1>(ctx, I, scratch, Ip, mom, st);
-        case 2: return launch_project_tile_scratch<T, 2>(ctx, I, scratch, Ip, mom, st);
-        case 3: return launch_project_tile_scratch<T, 3>(ctx, I, scratch, Ip, mom, st);
-        case 4: return launch_project_tile_scratch<T, 4>(ctx, I, scratch, Ip, mom, st);
-        case 5: return launch_project_tile_scratch<T, 5>(ctx, I, scratch, Ip, mom, st);
-        case 6: return launch_project_tile_scratch<T, 6>(ctx, I, scratch, Ip, mom, st);
-        case 7: return launch_project_tile_scratch<T, 7>(ctx, I, scratch, Ip, mom, st);
-        case 8: return launch_project_tile_scratch<T, 8>(ctx, I, scratch, Ip, mom, st);
-        default: return cudaErrorInvalidConfiguration;
-    }
+    T *nm0 = scratch, *nm1 = scratch + (size_t)ctx->nmoving * ctx->G * ctx->N;
+    return launch_project_nm<T>(ctx, I, Ip, mom, nm0, nm1, st);
 }
 
 template cudaError_t launch_project_scratch<double>(const shd_ctx *, const double *, double *, double *, double *,

@@ -225,3 +225,62 @@ def test_steps_aligned_grid(native, precision, tol):
     assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < 3 * tol
     if precision == "fp64":
         assert rel_elem(s.get_state(), I_ref, 1e-13) < tol
+
+
+MIXED_TOL = 1e-4  # per-field relative error bound of the mixed path against the FP64 oracle
+
+
+@pytest.mark.parametrize("kind", ["thomson", "kn"])
+def test_steps_mixed_ragged(native, kind):
+    """Mixed path (tensor-core transforms with BF16 hi/lo split, FP32
+    transfer) on the ragged flow problem, one step, per-field errors."""
+    spec = inputs.ragged_mixed(scattering=kind)
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision="mixed")
+    I0 = inputs.random_state(spec, seed=5)
+    s.set_state(I0)
+    s.step(1)
+    J, H, K, Ish = s.moments(with_sh=True)
+    I_ref, _, _ = P.step(I0, 1)
+    Ish_r, J_r, H_r, K_r = P.project(I_ref)
+    assert rel_elem(J, J_r) < MIXED_TOL
+    assert rel(H, H_r) < MIXED_TOL
+    assert rel(Ish, Ish_r) < MIXED_TOL
+    f = O.moments_to_eddington(J, K)
+    assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < MIXED_TOL
+
+
+def test_steps_mixed_aligned(native):
+    spec = inputs.jet(n=16, G=4, L=3, tau_r=4.0, gmax=12.0)  # Gamma > 10: FP64 Doppler island
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision="mixed")
+    I0 = inputs.random_state(spec, seed=8)
+    s.set_state(I0)
+    s.step(3)
+    J, H, K = s.moments()
+    I_ref, _, _ = P.step(I0, 3)
+    _, J_r, H_r, K_r = P.project(I_ref)
+    assert rel_elem(J, J_r) < MIXED_TOL
+    assert rel(H, H_r) < MIXED_TOL
+    f = O.moments_to_eddington(J, K)
+    assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < MIXED_TOL
+
+
+def test_jet_full_size_projection_sampled_mixed(native):
+    """The 64^3 jet in the benchmark's mixed configuration: tensor-core
+    projection of a seeded state at sampled nodes against the oracle."""
+    spec = inputs.jet()
+    s = native.Solver.from_spec(spec, precision="mixed")
+    dev = inputs.hash_state_torch(spec, seed=4, device="cuda")
+    s.set_state_dev(dev)
+    del dev
+    J, H, K, Ish = s.moments(with_sh=True)
+    rng = np.random.default_rng(1)
+    nodes = np.sort(rng.choice(spec.Nc, size=40, replace=False))
+    moving = np.nonzero(np.any(spec.u != 0, axis=1))[0]
+    nodes = np.unique(np.concatenate([nodes, moving[:: max(1, len(moving) // 16)][:16]]))
+    Psub = _oracle(inputs.sub_spec(spec, nodes))
+    Ish_r, J_r, H_r, K_r = Psub.project(inputs.hash_state_numpy(spec, seed=4, nodes=nodes))
+    assert rel_elem(J[nodes], J_r) < MIXED_TOL
+    assert rel(H[nodes], H_r) < MIXED_TOL
+    assert rel(Ish[nodes], Ish_r) < MIXED_TOL
