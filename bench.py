@@ -105,11 +105,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def cpu_sample_spec():
+def cpu_sample_spec(n=24):
     """Bounded CPU sample: the same recipe (groups, harmonics, ordinates, flow,
-    opacities) on a 20^3 grid."""
+    opacities) on an n^3 grid."""
     from paper_1507_05141_gb300 import inputs
-    return inputs.jet(n=20)
+    return inputs.jet(n=n)
 
 
 def run_oracle_steps(spec, steps):
@@ -127,12 +127,12 @@ def run_oracle_steps(spec, steps):
     return spec.updates_per_step * steps / dt, dt
 
 
-def cpu_baseline(steps=1):
+def cpu_baseline(steps=6):
     spec = cpu_sample_spec()
     v, dt = run_oracle_steps(spec, steps)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} FP64 oracle step(s) of the jet recipe on a 20^3 grid "
+            "sample": f"{steps} FP64 oracle steps of the jet recipe on a {spec.grid[0]}^3 grid "
                       f"({spec.updates_per_step:.3g} updates/step, {dt:.1f} s)"}
 
 
@@ -153,13 +153,73 @@ def bench_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (CPU sample: 20^3 grid, same recipe)", "grid": spec.grid,
+            "config": {"workload": WORKLOAD + f" (CPU sample: {spec.grid[0]}^3 grid, same recipe)", "grid": spec.grid,
                        "groups": spec.G, "L": spec.L, "ordinates": spec.N},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "FP64 oracle step of the jet recipe on a 20^3 grid, per step"},
+                             "sample": f"one FP64 oracle step of the jet recipe on a {spec.grid[0]}^3 grid per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def field_errors(precision, device, n=16, steps=3):
+    """Per-field error of a GPU precision against the FP64 oracle on the jet
+    recipe at a reduced grid (same groups, harmonics and ordinates), after
+    `steps` steps from a seeded state: J and I_lm relative to their maxima
+    per (node, group), H and K relative to J, f_ij absolute."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_1507_05141_gb300 import inputs, native
+    spec = inputs.jet(n=n)
+    I0 = inputs.random_state(spec, seed=11)
+    s = native.Solver.from_spec(spec, device=device, precision=precision)
+    s.set_state(I0)
+    s.step(steps)
+    J, H, K, Ish = s.moments(with_sh=True)
+    s.close()
+    Kt, so = O.thomson_table(spec.G, spec.L)
+    P = O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
+                        alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=Kt, sigma_out=so,
+                        kappa=spec.kappa, box=spec.box)
+    Ir, _, _ = P.step(I0, steps)
+    Ish_r, J_r, H_r, K_r = P.project(Ir)
+    Jd = np.maximum(np.abs(J_r), 1e-300)
+    f, f_r = O.moments_to_eddington(J, K), O.moments_to_eddington(J_r, K_r)
+    return {"J": float(np.max(np.abs(J - J_r) / Jd)),
+            "H": float(np.max(np.abs(H - H_r) / Jd[..., None])),
+            "K": float(np.max(np.abs(K - K_r) / Jd[..., None])),
+            "f_ij": float(np.max(np.abs(f - f_r))),
+            "I_lm": float(np.max(np.abs(Ish - Ish_r)) / np.max(np.abs(Ish_r))),
+            "case": f"jet recipe {n}^3, G={spec.G}, L={spec.L}, {spec.N} ordinates, {steps} steps"}
+
+
+def time_steps(solver, spec, steps, warmup, stream, dev, barrier, with_timing=True):
+    """Warm-up, then `steps` device-timed steps on `stream`; returns
+    (ms, per-stage ms per step, clock summary)."""
+    import torch
+    sptr = stream.cuda_stream
+    solver.step(warmup, sptr)
+    torch.cuda.synchronize(dev)
+    if with_timing:
+        solver.set_timing(True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        ev0.record(stream)
+        solver.step(steps, sptr)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage = {}
+    if with_timing:
+        stage_ms, nrec = solver.timing()
+        solver.set_timing(False)
+        stage = {k: v / max(1, nrec) for k, v in stage_ms.items()}
+    return ms, stage, clk.summary()
 
 
 def bench_ours(args):
@@ -188,25 +248,9 @@ def bench_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    # warm-up (also fills the state with a physical solution)
-    solver.step(args.warmup, sptr)
-    torch.cuda.synchronize(dev)
-
+    # warm-up (also fills the state with a physical solution), then the
     # device-resident timed region
-    solver.set_timing(True)
-    barrier()
-    torch.cuda.synchronize(dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        solver.step(args.steps, sptr)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    stage_ms, nrec = solver.timing()
-    solver.set_timing(False)
+    ms, stage, clk_summary = time_steps(solver, spec, args.steps, args.warmup, stream, dev, barrier)
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device=dev)
@@ -243,7 +287,7 @@ def bench_ours(args):
     e2e_value = upd * e2e_steps * ws / e2e_s
 
     peak, peak_kind = _peaks()
-    sweep_ms = stage_ms["sweep"] / max(1, nrec)
+    sweep_ms = stage["sweep"]
     sweep_bytes = upd * SWEEP_BYTES_PER_UPDATE[prec]
     achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9
     traffic = None
@@ -254,6 +298,27 @@ def bench_ours(args):
                 traffic = json.load(f).get("bytes_per_launch")
         except Exception:
             traffic = None
+
+    # the plain-FP32 arm on the same GPU, same workload and timing
+    plain = None
+    if prec == "mixed" and not args.no_compare:
+        solver.close()
+        torch.cuda.empty_cache()
+        s32 = native.Solver.from_spec(spec, device=local, precision="fp32")
+        s32.zero_state()
+        ms32, stage32, _ = time_steps(s32, spec, args.steps, args.warmup, stream, dev, barrier)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms32], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms32 = float(t.item())
+        s32.close()
+        solver = None
+        plain = {"value": upd * args.steps * ws / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / args.steps,
+                 "stage_ms": stage32}
+    errors = None
+    if rank == 0 and not args.no_errors:
+        errors = {p: field_errors(p, local) for p in ([prec, "fp32"] if prec == "mixed" else [prec])}
 
     if rank == 0:
         cpu = cpu_baseline() if (ws == 1 and not args.no_cpu) else None
@@ -267,7 +332,9 @@ def bench_ours(args):
                        "ordinates": spec.N, "precision": prec, "updates_per_step": upd,
                        "l2": "no flush: the 8.6 GB state is far larger than L2",
                        "parallelism": f"replicas x{ws}"},
-            "stage_ms": {k: v / max(1, nrec) for k, v in stage_ms.items()},
+            "stage_ms": stage,
+            "plain_fp32": plain,
+            "err_vs_fp64_oracle": errors,
             "roofline": {"kernel": "k_sweep", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
@@ -275,11 +342,12 @@ def bench_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "gpu_launches": launches_per_step(spec) * args.steps,
-            "clocks": clk.summary(),
+            "clocks": clk_summary,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
-    solver.close()
+    if solver is not None:
+        solver.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -292,7 +360,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 arm of a mixed run")
+    ap.add_argument("--no-errors", action="store_true", help="skip the per-field error check against the oracle")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
     ap.add_argument("--grid", type=int, default=64,
                     help="nodes per axis of the jet workload (64 is the benchmark; smaller for profiling)")

@@ -176,12 +176,13 @@ __global__ void __launch_bounds__(1024) k_sweep(Prob<T> P, T *__restrict__ I, co
 // -------------------------------------------------------------------------
 // a4, pipelined: the same plane walk with the inputs of the next plane
 // (I^n, eta_lab, chi_lab) already streaming into a two-stage shared-memory
-// ring by cp.async while the current plane is computed.  Lane i of a warp
-// owns node j = slot*V + e with consecutive slots on consecutive lanes, so
+// ring by cp.async (16-byte pieces when aligned) while the current plane is
+// computed.  Lane i of a warp owns node j = tid + 1024 u of every plane, so
 // every shared-memory access of a warp is to consecutive words (no bank
-// conflicts) and every global access is coalesced.  A thread reads only the
-// ring slots it filled, so the ring needs no barrier; the two barriers per
-// plane guard the previous-plane state.
+// conflicts) and every global access is coalesced; the node's in-plane
+// upwind neighbours and inflow flags are computed once.  Two barriers per
+// plane: after the copies land (they and the previous plane's state become
+// visible) and after the reads of the previous plane.
 // -------------------------------------------------------------------------
 template <class T>
 __device__ inline T fast_recip(T x);
@@ -200,12 +201,13 @@ __device__ inline void cp_async_n(void *smem, const void *gmem)
         asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES));
 }
 
-template <class T, int V, int U>
+template <class T, int U, bool VEC>
 __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict__ I, const T *__restrict__ eta,
                                                         const T *__restrict__ chi)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NT = 1024;
+    constexpr int V = 16 / sizeof(T);  // reals per 16-byte copy
     const int k = blockIdx.x / P.G;
     const int g = blockIdx.x - k * P.G;
     const Ordinate o = P.ord[k];
@@ -219,107 +221,98 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
     T *ring = pC + pstride;  // [2][3][pstride]
     const long long base = ((long long)k * P.G + g) * P.Nc;
     const T fr1 = (T)o.fr1, fr2 = (T)o.fr2, s = (T)o.s, kap = P.kappa;
-    const int first1 = o.s1 > 0 ? 0 : n1 - 1, first2 = o.s2 > 0 ? 0 : n2 - 1;
     const T w00 = (T(1) - fr1) * (T(1) - fr2), w10 = fr1 * (T(1) - fr2), w01 = (T(1) - fr1) * fr2, w11 = fr1 * fr2;
     const T bc_iso = P.bc_mode == SHD_BC_ISO ? P.bc[g] : T(0);
-    const int nslot = (plane + V - 1) / V;
+    const bool bc_full = P.bc_mode == SHD_BC_FULL;
     const int tid = threadIdx.x;
+
+    // node j = tid + NT*u of every plane; bit u of `face` marks an inflow
+    // face of one of the two in-plane axes; the upwind neighbours on the
+    // previous plane are j - d1, j - d2, j - d1 - d2
+    unsigned face = 0;
+    {
+        const int first1 = o.s1 > 0 ? 0 : n1 - 1, first2 = o.s2 > 0 ? 0 : n2 - 1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int j = tid + NT * u;
+            int i1 = j / n2, i2 = j - i1 * n2;
+            if ((o.s1 != 0 && i1 == first1) || (o.s2 != 0 && i2 == first2)) face |= 1u << u;
+        }
+    }
+    const int d1 = o.s1 * n2, d2 = o.s2;
 
     auto issue = [&](int step) {
         if (step < nd) {
             const int id = o.sd > 0 ? step : nd - 1 - step;
             const long long pb = base + (long long)id * plane;
             T *r = ring + (size_t)(step & 1) * 3 * pstride;
+            if constexpr (VEC) {
+                const int nv = plane / V;  // 16-byte pieces per array
+                for (int c = tid; c < 3 * nv; c += NT) {
+                    const int a = c / nv, off = (c - a * nv) * V;
+                    const T *src = a == 0 ? I : (a == 1 ? eta : chi);
+                    cp_async_n<16>(&r[a * pstride + off], &src[pb + off]);
+                }
+            } else {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int slot = tid + NT * u;
-                if (slot >= nslot) break;
-                int j = slot * V;
-                cp_async_n<V * sizeof(T)>(&r[j], &I[pb + j]);
-                cp_async_n<V * sizeof(T)>(&r[pstride + j], &eta[pb + j]);
-                cp_async_n<V * sizeof(T)>(&r[2 * pstride + j], &chi[pb + j]);
+                for (int u = 0; u < U; ++u) {
+                    const int j = tid + NT * u;
+                    if (j >= plane) break;
+                    cp_async_n<sizeof(T)>(&r[j], &I[pb + j]);
+                    cp_async_n<sizeof(T)>(&r[pstride + j], &eta[pb + j]);
+                    cp_async_n<sizeof(T)>(&r[2 * pstride + j], &chi[pb + j]);
+                }
             }
         }
         asm volatile("cp.async.commit_group;\n" ::);
     };
 
     issue(0);
-    T rI[U][V], rS[U][V], rC[U][V];
+    T rI[U], rS[U], rC[U];
     for (int step = 0; step < nd; ++step) {
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncthreads();  // every copy of this plane and the previous plane's state are visible
         issue(step + 1);
-        asm volatile("cp.async.wait_group 1;\n" ::);
         const T *r = ring + (size_t)(step & 1) * 3 * pstride;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            int slot = tid + NT * u;
-            if (slot >= nslot) break;
-            int j0 = slot * V;
-            int i1 = j0 / n2, i2 = j0 - i1 * n2;
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                int j = j0 + e;
-                if (j < plane) {
-                    T In = r[j];
-                    T ct = r[2 * pstride + j] + kap;
-                    T st = ct > T(0) ? (r[pstride + j] + kap * In) * fast_recip<T>(ct) : T(0);
-                    bool inflow = step == 0 || (o.s1 != 0 && i1 == first1) || (o.s2 != 0 && i2 == first2);
-                    T inew;
-                    if (inflow) {
-                        if (P.bc_mode == SHD_BC_FULL) {
-                            const int id = o.sd > 0 ? step : nd - 1 - step;
-                            inew = P.bc[base + (long long)id * plane + j];
-                        } else {
-                            inew = bc_iso;
-                        }
-                    } else {
-                        int j1 = i1 - o.s1, j2 = i2 - o.s2;
-                        int a00 = i1 * n2 + i2, a10 = j1 * n2 + i2, a01 = i1 * n2 + j2, a11 = j1 * n2 + j2;
-                        T iu = w00 * pI[a00] + w10 * pI[a10] + w01 * pI[a01] + w11 * pI[a11];
-                        T su = w00 * pS[a00] + w10 * pS[a10] + w01 * pS[a01] + w11 * pS[a11];
-                        T cu = w00 * pC[a00] + w10 * pC[a10] + w01 * pC[a01] + w11 * pC[a11];
-                        T dtau = s * T(0.5) * (cu + ct);
-                        T ew, wp, wu;
-                        sc_weights<T>(dtau, ew, wp, wu);
-                        inew = iu * ew + st * wp + su * wu;
-                    }
-                    rI[u][e] = inew;
-                    rS[u][e] = st;
-                    rC[u][e] = ct;
-                }
-                if (++i2 == n2) { i2 = 0; ++i1; }
-            }
-        }
-        __syncthreads();
+        const bool first = step == 0;
         const int id = o.sd > 0 ? step : nd - 1 - step;
         const long long pb = base + (long long)id * plane;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            int slot = tid + NT * u;
-            if (slot >= nslot) break;
-            int j0 = slot * V;
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                int j = j0 + e;
-                if (j < plane) {
-                    pI[j] = rI[u][e];
-                    pS[j] = rS[u][e];
-                    pC[j] = rC[u][e];
-                }
-            }
-            if constexpr (V * sizeof(T) == 16) {
-                if constexpr (sizeof(T) == 4) {
-                    *reinterpret_cast<float4 *>(&I[pb + j0]) = make_float4(rI[u][0], rI[u][1], rI[u][2], rI[u][3]);
-                } else {
-                    *reinterpret_cast<double2 *>(&I[pb + j0]) = make_double2(rI[u][0], rI[u][1]);
-                }
+            const int j = tid + NT * u;
+            if (j >= plane) break;
+            const T In = r[j];
+            const T ct = r[2 * pstride + j] + kap;
+            const T st = ct > T(0) ? (r[pstride + j] + kap * In) * fast_recip<T>(ct) : T(0);
+            T inew;
+            if (first || ((face >> u) & 1u)) {
+                inew = bc_full ? P.bc[pb + j] : bc_iso;
             } else {
-#pragma unroll
-                for (int e = 0; e < V; ++e)
-                    if (j0 + e < plane) I[pb + j0 + e] = rI[u][e];
+                const int b00 = j, b10 = j - d1, b01 = j - d2, b11 = j - d1 - d2;
+                const T iu = w00 * pI[b00] + w10 * pI[b10] + w01 * pI[b01] + w11 * pI[b11];
+                const T su = w00 * pS[b00] + w10 * pS[b10] + w01 * pS[b01] + w11 * pS[b11];
+                const T cu = w00 * pC[b00] + w10 * pC[b10] + w01 * pC[b01] + w11 * pC[b11];
+                const T dtau = s * T(0.5) * (cu + ct);
+                T ew, wp, wu;
+                sc_weights<T>(dtau, ew, wp, wu);
+                inew = iu * ew + st * wp + su * wu;
             }
+            rI[u] = inew;
+            rS[u] = st;
+            rC[u] = ct;
         }
-        __syncthreads();
+        __syncthreads();  // all reads of the previous plane are done
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = tid + NT * u;
+            if (j >= plane) break;
+            pI[j] = rI[u];
+            pS[j] = rS[u];
+            pC[j] = rC[u];
+            I[pb + j] = rI[u];
+        }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
 // -------------------------------------------------------------------------
@@ -557,14 +550,14 @@ static cudaError_t launch_sweep_npt(const shd_ctx *ctx, T *I, const T *eta, cons
     return cudaGetLastError();
 }
 
-template <class T, int V, int U>
+template <class T, int U, bool VEC>
 static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st,
                                      size_t sm)
 {
     Prob<T> P = make_prob<T>(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_pipe<T, V, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_pipe<T, U, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_sweep_pipe<T, V, U><<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi);
+    k_sweep_pipe<T, U, VEC><<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi);
     return cudaGetLastError();
 }
 
@@ -582,11 +575,22 @@ cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, c
     int plane = sweep_plane_max(ctx);
     size_t smp = sweep_pipe_smem_bytes(ctx);
     if (smp <= 227 * 1024) {
+        // 16-byte copies when every plane and the array base stay 16-byte aligned
+        constexpr int V = 16 / sizeof(T);
+        const bool vec = ctx->Nc % V == 0 && ((long long)ctx->nx * ctx->ny) % V == 0 &&
+                         ((long long)ctx->ny * ctx->nz) % V == 0 && ((long long)ctx->nx * ctx->nz) % V == 0;
         int u = (plane + 1023) / 1024;
-        if (u <= 1) return launch_sweep_pipe<T, 1, 1>(ctx, I, eta, chi, st, smp);
-        if (u <= 2) return launch_sweep_pipe<T, 1, 2>(ctx, I, eta, chi, st, smp);
-        if (u <= 4) return launch_sweep_pipe<T, 1, 4>(ctx, I, eta, chi, st, smp);
-        if (u <= 8) return launch_sweep_pipe<T, 1, 8>(ctx, I, eta, chi, st, smp);
+        if (vec) {
+            if (u <= 1) return launch_sweep_pipe<T, 1, true>(ctx, I, eta, chi, st, smp);
+            if (u <= 2) return launch_sweep_pipe<T, 2, true>(ctx, I, eta, chi, st, smp);
+            if (u <= 4) return launch_sweep_pipe<T, 4, true>(ctx, I, eta, chi, st, smp);
+            if (u <= 8) return launch_sweep_pipe<T, 8, true>(ctx, I, eta, chi, st, smp);
+        } else {
+            if (u <= 1) return launch_sweep_pipe<T, 1, false>(ctx, I, eta, chi, st, smp);
+            if (u <= 2) return launch_sweep_pipe<T, 2, false>(ctx, I, eta, chi, st, smp);
+            if (u <= 4) return launch_sweep_pipe<T, 4, false>(ctx, I, eta, chi, st, smp);
+            if (u <= 8) return launch_sweep_pipe<T, 8, false>(ctx, I, eta, chi, st, smp);
+        }
     }
     int threads = plane < 1024 ? ((plane + 31) / 32) * 32 : 1024;
     int npt = (plane + threads - 1) / threads;
