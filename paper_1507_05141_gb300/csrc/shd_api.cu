@@ -151,6 +151,7 @@ void free_all(shd_ctx *c)
                      &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag, &c->d_Bproj,
                      (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
                      &c->d_lc, &c->d_linv, &c->d_tc_Bh, &c->d_tc_Bl, &c->d_tc_Yh, &c->d_tc_Yl,
+                     (void **)&c->d_int2mesh, (void **)&c->d_mesh2int,
                      (void **)&c->d_tc_err};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
@@ -204,8 +205,8 @@ void build_geometry(shd_ctx *c)
         Ordinate &o = c->h_ord[k];
         for (int a = 0; a < 3; ++a) o.n[a] = c->h_dirs[3 * k + a];
         o.W = c->h_W[k];
-        o.ring = k / c->nphi;
-        o.phi = k % c->nphi;
+        o.ring = c->h_int2mesh[k] / c->nphi;
+        o.phi = c->h_int2mesh[k] % c->nphi;
         if (!c->have_grid) continue;
         int d = 0;
         double best = std::fabs(o.n[0]) / c->h[0];
@@ -306,10 +307,57 @@ int upload_tc_operands(shd_ctx *c, const std::vector<double> &Bp)
     return SHD_OK;
 }
 
+// Internal ordinate order: grouped by the axis each ordinate crosses first
+// (z, then y, then x; mesh order within a group), so that the ordinates of
+// a group share one sweep layout.  Without a grid yet: mesh order.
+void order_ordinates(shd_ctx *c)
+{
+    const int N = c->N;
+    std::vector<int> cls(N, 2);
+    if (c->have_grid) {
+        for (int k = 0; k < N; ++k) {
+            const double *n = &c->h_dirs_mesh[3 * k];
+            int d = 0;
+            double best = std::fabs(n[0]) / c->h[0];
+            for (int a = 1; a < 3; ++a) {
+                double v = std::fabs(n[a]) / c->h[a];
+                if (v > best) { best = v; d = a; }
+            }
+            cls[k] = d;
+        }
+    }
+    c->h_int2mesh.clear();
+    for (int want : {2, 1, 0})
+        for (int k = 0; k < N; ++k)
+            if (cls[k] == want) c->h_int2mesh.push_back(k);
+    c->nA = 0;
+    for (int k = 0; k < N; ++k) c->nA += cls[k] != 0;
+    c->h_mesh2int.assign(N, 0);
+    for (int i = 0; i < N; ++i) c->h_mesh2int[c->h_int2mesh[i]] = i;
+    c->h_dirs.assign(3 * (size_t)N, 0.0);
+    c->h_W.assign(N, 0.0);
+    c->h_Y.assign((size_t)N * c->NLM, 0.0);
+    for (int i = 0; i < N; ++i) {
+        const int k = c->h_int2mesh[i];
+        for (int q = 0; q < 3; ++q) c->h_dirs[3 * i + q] = c->h_dirs_mesh[3 * k + q];
+        c->h_W[i] = c->h_W_mesh[k];
+        for (int p = 0; p < c->NLM; ++p) c->h_Y[(size_t)i * c->NLM + p] = c->h_Y_mesh[(size_t)k * c->NLM + p];
+    }
+}
+
 int upload_angles(shd_ctx *c)
 {
     dfree(c->d_ord); dfree(c->d_W); dfree(c->d_dirs); dfree(c->d_Y); dfree(c->d_mu); dfree(c->d_Bproj);
+    dfree((void *&)c->d_int2mesh); dfree((void *&)c->d_mesh2int);
+    order_ordinates(c);
     build_geometry(c);
+    {
+        int rc;
+        if ((rc = dalloc(c, (void **)&c->d_int2mesh, sizeof(int) * c->N, "int2mesh"))) return rc;
+        if ((rc = dalloc(c, (void **)&c->d_mesh2int, sizeof(int) * c->N, "mesh2int"))) return rc;
+        CK(cudaMemcpy(c->d_int2mesh, c->h_int2mesh.data(), sizeof(int) * c->N, cudaMemcpyHostToDevice), "int2mesh");
+        CK(cudaMemcpy(c->d_mesh2int, c->h_mesh2int.data(), sizeof(int) * c->N, cudaMemcpyHostToDevice), "mesh2int");
+    }
     c->NB = 16 * ((c->NLM + 10 + 15) / 16);
     std::vector<double> Bp = projection_matrix(c);
     cudaError_t e;
@@ -635,18 +683,18 @@ int shd_set_angles(shd_ctx *c, int L, int n_mu, int n_phi)
     c->N = n_mu * n_phi;
     c->NLM = (L + 1) * (L + 1);
     gauss_legendre(n_mu, c->h_mu, c->h_wmu);
-    c->h_dirs.assign(3 * c->N, 0.0);
-    c->h_W.assign(c->N, 0.0);
-    c->h_Y.assign((size_t)c->N * c->NLM, 0.0);
+    c->h_dirs_mesh.assign(3 * c->N, 0.0);
+    c->h_W_mesh.assign(c->N, 0.0);
+    c->h_Y_mesh.assign((size_t)c->N * c->NLM, 0.0);
     for (int a = 0; a < n_mu; ++a) {
         double sth = std::sqrt((1.0 - c->h_mu[a]) * (1.0 + c->h_mu[a]));
         for (int b = 0; b < n_phi; ++b) {
             int k = a * n_phi + b;
             double phi = 2.0 * kPi * b / n_phi;
             double n[3] = {sth * std::cos(phi), sth * std::sin(phi), c->h_mu[a]};
-            for (int q = 0; q < 3; ++q) c->h_dirs[3 * k + q] = std::fabs(n[q]) < 1e-12 ? 0.0 : n[q];
-            c->h_W[k] = c->h_wmu[a] * (2.0 * kPi / n_phi);
-            real_harmonics(L, c->h_mu[a], phi, &c->h_Y[(size_t)k * c->NLM]);
+            for (int q = 0; q < 3; ++q) c->h_dirs_mesh[3 * k + q] = std::fabs(n[q]) < 1e-12 ? 0.0 : n[q];
+            c->h_W_mesh[k] = c->h_wmu[a] * (2.0 * kPi / n_phi);
+            real_harmonics(L, c->h_mu[a], phi, &c->h_Y_mesh[(size_t)k * c->NLM]);
         }
     }
     c->have_angles = true;

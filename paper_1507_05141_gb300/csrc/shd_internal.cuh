@@ -77,6 +77,9 @@ struct Prob {
     const T *Bproj;        // [N][NB]: W_k Y_p(n_k) | W_k {1, n, nn}/(4 pi) | 0
     int NB;
     int fp64_boost;        // Doppler factor and aberration in FP64 where Gamma > 10
+    const int *int2mesh;   // [N] mesh index (a*nphi + b) of internal ordinate k
+    const int *mesh2int;   // [N] inverse
+    int nA;                // internal ordinates [0, nA) cross z or y first, [nA, N) x
     const T *lc;           // [G] log of the group centres
     const T *linv;         // [G] 1/(lc[g+1] - lc[g])
     T le0, leG;            // log of the outer edges
@@ -106,7 +109,14 @@ struct shd_ctx {
     long long Nc = 0;
     // angles
     int L = -1, nmu = 0, nphi = 0, N = 0, NLM = 0;
-    std::vector<double> h_mu, h_wmu, h_dirs, h_W, h_Y;  // host tables (FP64)
+    // host tables (FP64).  *_mesh are in mesh order k = a*nphi + b; the others
+    // in the internal order, which groups the ordinates by the axis they cross
+    // first (z, then y, then x) so that each group shares one sweep layout
+    std::vector<double> h_mu, h_wmu, h_dirs, h_W, h_Y;
+    std::vector<double> h_dirs_mesh, h_W_mesh, h_Y_mesh;
+    std::vector<int> h_int2mesh, h_mesh2int;
+    int nA = 0;  // internal ordinates crossing z or y first
+    int *d_int2mesh = nullptr, *d_mesh2int = nullptr;
     std::vector<shd::Ordinate> h_ord;
     // groups
     int G = 0;

@@ -35,6 +35,7 @@ Prob<T> make_prob(const shd_ctx *c)
     p.midx = c->d_midx; p.mtiles = c->d_mtiles; p.nmtiles = c->nmtiles;
     p.Bproj = (const T *)c->d_Bproj; p.NB = c->NB;
     p.fp64_boost = c->precision == SHD_MIXED ? 1 : 0;
+    p.int2mesh = c->d_int2mesh; p.mesh2int = c->d_mesh2int; p.nA = c->nA;
     p.lc = (const T *)c->d_lc; p.linv = (const T *)c->d_linv;
     p.le0 = c->G ? (T)std::log(c->h_edges[0]) : T(0);
     p.leG = c->G ? (T)std::log(c->h_edges[c->G]) : T(0);
@@ -384,7 +385,8 @@ __global__ void k_canon_to_do(Prob<T> P, const double *__restrict__ src, T *__re
     long long c = c0 + cg / G;
     int ix, iy, iz;
     node_xyz(c, P.nx, P.ny, ix, iy, iz);
-    dst[((long long)k * G + g) * P.Nc + perm_offset(P.ord[k].d, ix, iy, iz, P.nx, P.ny, P.nz)] = (T)src[i];
+    const int ki = P.mesh2int[k];  // canonical arrays are in mesh order
+    dst[((long long)ki * G + g) * P.Nc + perm_offset(P.ord[ki].d, ix, iy, iz, P.nx, P.ny, P.nz)] = (T)src[i];
 }
 
 template <class T>
@@ -401,7 +403,8 @@ __global__ void k_do_to_canon(Prob<T> P, const T *__restrict__ src, double *__re
     long long c = c0 + cg / G;
     int ix, iy, iz;
     node_xyz(c, P.nx, P.ny, ix, iy, iz);
-    dst[i] = (double)src[((long long)k * G + g) * P.Nc + perm_offset(P.ord[k].d, ix, iy, iz, P.nx, P.ny, P.nz)];
+    const int ki = P.mesh2int[k];  // canonical arrays are in mesh order
+    dst[i] = (double)src[((long long)ki * G + g) * P.Nc + perm_offset(P.ord[ki].d, ix, iy, iz, P.nx, P.ny, P.nz)];
 }
 
 template <class T>

@@ -25,7 +25,7 @@ namespace shd {
 
 namespace {
 
-constexpr long long kWaitLimit = 1LL << 24;  // mbarrier polls before giving up (order of a second)
+constexpr long long kWaitLimit = 1LL << 22;  // mbarrier polls before giving up (about a second)
 
 __device__ inline int brick_row(int d, int q)
 {
@@ -62,25 +62,41 @@ __device__ inline bool cta_wait(uint64_t *bar, uint32_t parity, int *abort_flag)
 }  // namespace
 
 // -------------------------------------------------------------------------
-// a1 on tensor cores.  Shared memory: Bh, Bl [NB][Kp] (resident), A stages
-// [2][hi, lo][128][KC], two mbarriers, the tensor-memory address.
+// a1 on tensor cores, warp-specialised.  A job is one (brick, group pair,
+// pass); every role walks the same job sequence.
+//   warps 0-11  producers: cp.async a chunk of KC ordinates for the 128 rows
+//               into an FP32 staging area (the next chunk's copies in flight
+//               meanwhile), split into BF16 hi / lo, store it in ring stage s
+//               in the canonical layout, arrive on full[s]
+//   warp  16    MMA issuer (lane 0): wait full[s], 3 x KC/16 MMAs into the
+//               job's accumulator (two alternate in tensor memory), commit to
+//               empty[s]; after a job's last chunk commit to tfull[b]
+//   warps 12-15 epilogue (tensor-memory lane quadrants 0-3): wait tfull[b],
+//               read the accumulator, write I_lm / moments, arrive tempty[b]
+// Shared memory: Bh, Bl [NB][Kp] resident, the ring [NS][hi, lo][128][KC],
+// the FP32 staging [2][KC][128], the barriers, the ordinate layout table.
 // -------------------------------------------------------------------------
-template <int KC>
-__global__ void __launch_bounds__(256, 1) k_project_tc(Prob<float> P, const float *__restrict__ I,
+template <int KC, int NS>
+__global__ void __launch_bounds__(544, 1) k_project_tc(Prob<float> P, const float *__restrict__ I,
                                                        const float *__restrict__ I0, float *__restrict__ Ip,
                                                        float *__restrict__ mom, const uint16_t *__restrict__ gBh,
-                                                       const uint16_t *__restrict__ gBl, int NB, int Kp,
-                                                       int tmem_cols, int *err)
+                                                       const uint16_t *__restrict__ gBl, int NB, int Kp, int *err)
 {
-    constexpr int NV = KC / 2;  // A values a thread gathers per chunk
+    constexpr int NPROD = 384;                           // producer threads (warps 0-11)
+    constexpr int NPAIR = 128 * KC / 2 / NPROD + 1;      // element pairs a producer covers per chunk (bound)
+    constexpr uint32_t ACC_COLS = 128;   // columns per accumulator (NB <= 128)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint16_t *Bh = reinterpret_cast<uint16_t *>(smem_raw);
     uint16_t *Bl = Bh + (size_t)NB * Kp;
-    uint16_t *As = Bl + (size_t)NB * Kp;  // [2][2][128 * KC]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(As + (size_t)4 * 128 * KC);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
-    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
-    unsigned char *cls = reinterpret_cast<unsigned char *>(abort_flag + 1);  // [Kp] sweep layout of each ordinate
+    uint16_t *ring = Bl + (size_t)NB * Kp;  // [NS][2][128 * KC]
+    float *stg = reinterpret_cast<float *>(ring + (size_t)NS * 2 * 128 * KC);  // [2][KC][128]
+    uint64_t *full = reinterpret_cast<uint64_t *>(stg + (size_t)2 * KC * 128);
+    uint64_t *empty = full + NS;
+    uint64_t *tfull = empty + NS;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    unsigned char *cls = reinterpret_cast<unsigned char *>(tslot + 2);  // [Kp]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = P.N, G = P.G, NLM = P.NLM;
@@ -88,185 +104,247 @@ __global__ void __launch_bounds__(256, 1) k_project_tc(Prob<float> P, const floa
         const uint4 *sh = reinterpret_cast<const uint4 *>(gBh), *sl = reinterpret_cast<const uint4 *>(gBl);
         uint4 *dh = reinterpret_cast<uint4 *>(Bh), *dl = reinterpret_cast<uint4 *>(Bl);
         const int n16 = NB * Kp / 8;
-        for (int i = tid; i < n16; i += 256) {
+        for (int i = tid; i < n16; i += blockDim.x) {
             dh[i] = sh[i];
             dl[i] = sl[i];
         }
-        for (int k = tid; k < Kp; k += 256) cls[k] = k < N ? (unsigned char)P.ord[k].d : 0;
+        for (int k = tid; k < Kp; k += blockDim.x) cls[k] = k < N ? (unsigned char)P.ord[k].d : 0;
     }
     if (tid == 0) {
-        tc::mbar_init(&bars[0], 1);
-        tc::mbar_init(&bars[1], 1);
+        for (int i = 0; i < NS; ++i) {
+            tc::mbar_init(&full[i], NPROD);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&tfull[i], 1);
+            tc::mbar_init(&tempty[i], 128);
+        }
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 0) tc::tmem_alloc(tslot, tmem_cols);
+    if (warp == 0) tc::tmem_alloc(tslot, 2 * ACC_COLS);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = tc::idesc_bf16(128, NB);
-    const uint32_t a_sbo = (KC / 8) * 128, b_sbo = (Kp / 8) * 128;
 
-    uint32_t phase[2] = {0, 0};
-    bool pending[2] = {false, false};
-    long long chunk_ctr = 0;
     const int nchunk = Kp / KC;
     const int npair = (G + 1) / 2;
     const long long items = P.ntiles * npair;
-    // a thread always gathers row slot q = tid & 127 (group gi, brick element
-    // qq) and the ordinate pairs kp = (tid >> 7) + 2i of every chunk
-    const int q = tid & 127, gi = q >> 6, qq = q & 63, kp0 = tid >> 7;
-
-    for (long long w = blockIdx.x; w < items; w += gridDim.x) {
-        const long long tile = w / npair;
-        const int pair = (int)(w - tile * npair);
-        const TileInfo ti = P.tiles[tile];
-        const int passes = (ti.flags & 1) ? 2 : 1;
-        const int g = 2 * pair + gi;
-        // per sweep layout d: the node of this slot, its offset, validity
-        // per sweep layout d = 0, 1, 2 (scalars, selected with pick3: no
-        // dynamically indexed arrays)
-        long long off0, off1, off2;
-        int row0, row1, row2, m0, m1, m2;
-        bool ok0, ok1, ok2;
-        {
-            auto setup = [&](int d, long long &off, int &row, bool &ok, int &m) {
-                const int rr = brick_row(d, qq);
-                const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
-                row = gi * 64 + rr;
-                ok = g < G && ix < P.nx && iy < P.ny;
-                off = ok ? perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz) : 0;
-                m = ok ? P.midx[((long long)ti.z * P.ny + iy) * P.nx + ix] : -1;
-            };
-            setup(0, off0, row0, ok0, m0);
-            setup(1, off1, row1, ok1, m1);
-            setup(2, off2, row2, ok2, m2);
+    // bounded wait that also gives up as soon as another role has given up
+    auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        for (long long i = 0; i < kWaitLimit; ++i) {
+            if (tc::mbar_try_wait(bar, parity)) return true;
+            if ((i & 255) == 255 && *abort_flag) return false;
         }
-        const long long gNc = (long long)(g < G ? g : 0) * P.Nc, GNc = (long long)G * P.Nc;
-        for (int pass = 0; pass < passes; ++pass) {
-            // element kk of layout d: base_d + kk * stride_d -- the sweep layout,
-            // or (pass 1, moving node) the node-major comoving row
-            auto base_of = [&](int m, long long off) -> const float * {
-                return (pass == 1 && m >= 0) ? I0 + ((long long)m * G + g) * N : I + gNc + off;
-            };
-            const float *base0 = base_of(m0, off0), *base1 = base_of(m1, off1), *base2 = base_of(m2, off2);
-            const long long str0 = (pass == 1 && m0 >= 0) ? 1 : GNc;
-            const long long str1 = (pass == 1 && m1 >= 0) ? 1 : GNc;
-            const long long str2 = (pass == 1 && m2 >= 0) ? 1 : GNc;
-            auto load = [&](int ch, float (&v)[NV]) {
+        *abort_flag = 1;
+        atomicExch(err, 1);
+        return false;
+    };
+
+    if (warp < 12) {
+        // ---------------- producers ----------------
+        // pair i of a chunk covers ordinates (2 kp, 2 kp + 1), kp = kp0 + 3 i, of
+        // row slot q: the slot stays the same because NPROD is a multiple of 128
+        const int q = tid & 127, gi = q >> 6, qq = q & 63, kp0 = tid >> 7;
+        constexpr int KPS = NPROD / 128;  // pair stride
+        long long it = 0;
+        for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+            const long long tile = w / npair;
+            const int pair = (int)(w - tile * npair);
+            const TileInfo ti = P.tiles[tile];
+            const int passes = (ti.flags & 1) ? 2 : 1;
+            const int g = 2 * pair + gi;
+            long long off0, off1, off2;
+            int row0, row1, row2, m0, m1, m2;
+            bool ok0, ok1, ok2;
+            {
+                auto setup = [&](int d, long long &off, int &row, bool &ok, int &m) {
+                    const int rr = brick_row(d, qq);
+                    const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
+                    row = gi * 64 + rr;
+                    ok = g < G && ix < P.nx && iy < P.ny;
+                    off = ok ? perm_offset(d, ix, iy, ti.z, P.nx, P.ny, P.nz) : 0;
+                    m = ok ? P.midx[((long long)ti.z * P.ny + iy) * P.nx + ix] : -1;
+                };
+                setup(0, off0, row0, ok0, m0);
+                setup(1, off1, row1, ok1, m1);
+                setup(2, off2, row2, ok2, m2);
+            }
+            const long long gNc = (long long)(g < G ? g : 0) * P.Nc, GNc = (long long)G * P.Nc;
+            for (int pass = 0; pass < passes; ++pass) {
+                // element kk of layout d sits at base_d + kk * stride_d: the sweep
+                // layout, or in pass 1 the moving node's comoving row; in pass 1
+                // the rows of nodes at rest are not needed (zero)
+                auto base_of = [&](int m, long long off) -> const float * {
+                    return (pass == 1 && m >= 0) ? I0 + ((long long)m * G + g) * N : I + gNc + off;
+                };
+                const float *base0 = base_of(m0, off0), *base1 = base_of(m1, off1), *base2 = base_of(m2, off2);
+                const long long str0 = (pass == 1 && m0 >= 0) ? 1 : GNc;
+                const long long str1 = (pass == 1 && m1 >= 0) ? 1 : GNc;
+                const long long str2 = (pass == 1 && m2 >= 0) ? 1 : GNc;
+                const bool use0 = ok0 && (pass == 0 || m0 >= 0), use1 = ok1 && (pass == 0 || m1 >= 0),
+                           use2 = ok2 && (pass == 0 || m2 >= 0);
+                // element (kk, q) of a chunk goes to staging [kk][q]: a warp's copies
+                // and reads touch consecutive words
+                auto copy = [&](int ch, float *S) {
 #pragma unroll
-                for (int i = 0; i < NV / 2; ++i) {
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        const int kk = ch * KC + 2 * (kp0 + 2 * i) + t;
-                        float x = 0.f;
-                        if (kk < N) {
-                            const int d = cls[kk];
-                            if (pick3(d, ok0, ok1, ok2))
-                                x = __ldg(pick3(d, base0, base1, base2) + (long long)kk * pick3(d, str0, str1, str2));
-                        }
-                        v[2 * i + t] = x;
-                    }
-                }
-            };
-            auto step = [&](int ch, const float (&v)[NV]) -> bool {
-                const int s = (int)(chunk_ctr & 1);
-                if (pending[s]) {
-                    if (!cta_wait(&bars[s], phase[s], abort_flag)) return false;
-                    phase[s] ^= 1;
-                    pending[s] = false;
-                }
-                uint16_t *Ah = As + (size_t)(2 * s) * 128 * KC;
-                uint16_t *Al = Ah + (size_t)128 * KC;
-#pragma unroll
-                for (int i = 0; i < NV / 2; ++i) {
-                    const int kl = 2 * (kp0 + 2 * i);
-                    const int kk = ch * KC + kl;
-                    const int d0 = kk < N ? cls[kk] : 2, d1 = kk + 1 < N ? cls[kk + 1] : 2;
-                    const int r0 = kk < N ? pick3(d0, row0, row1, row2) : gi * 64 + qq;
-                    const int r1 = kk + 1 < N ? pick3(d1, row0, row1, row2) : gi * 64 + qq;
-                    if (r0 == r1) {
-                        uint32_t hi, lo;
-                        split_bf16x2(v[2 * i], v[2 * i + 1], hi, lo);
-                        const int o = tc::canon_off(r0, kl, KC);
-                        *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
-                        *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
-                    } else {
-                        // the two ordinates use different layouts, so the same slot q
-                        // is a different row; each (row, k) is still written once,
-                        // because the brick permutation of a layout is a bijection
-                        const int rs[2] = {r0, r1};
+                    for (int i = 0; i < NPAIR; ++i) {
 #pragma unroll
                         for (int t = 0; t < 2; ++t) {
-                            __nv_bfloat16 h = __float2bfloat16_rn(v[2 * i + t]);
-                            __nv_bfloat16 l = __float2bfloat16_rn(v[2 * i + t] - __bfloat162float(h));
-                            const int o = tc::canon_off(rs[t], kl + t, KC);
-                            Ah[o] = __bfloat16_as_ushort(h);
-                            Al[o] = __bfloat16_as_ushort(l);
+                            const int kp = kp0 + KPS * i;
+                            if (kp >= KC / 2) break;
+                            const int kl = 2 * kp + t, kk = ch * KC + kl;
+                            float *dst = &S[kl * 128 + q];
+                            bool on = false;
+                            const float *src = nullptr;
+                            if (kk < N) {
+                                const int d = cls[kk];
+                                if (pick3(d, use0, use1, use2)) {
+                                    src = pick3(d, base0, base1, base2) + (long long)kk * pick3(d, str0, str1, str2);
+                                    on = true;
+                                }
+                            }
+                            if (on) {
+                                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+                                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+                            } else {
+                                *dst = 0.f;
+                            }
                         }
                     }
-                }
-                tc::fence_proxy_async();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::fence_after_sync();
-                    const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al);
-                    const uint32_t bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
-#pragma unroll
-                    for (int j = 0; j < KC / 16; ++j) {
-                        const uint32_t aoff = j * 256;  // 2 core matrices of 128 B
-                        const uint32_t boff = (uint32_t)(ch * KC / 16 + j) * 256;
-                        const uint64_t dah = tc::sdesc(ah + aoff, 128, a_sbo), dal = tc::sdesc(al + aoff, 128, a_sbo);
-                        const uint64_t dbh = tc::sdesc(bh + boff, 128, b_sbo), dbl = tc::sdesc(bl + boff, 128, b_sbo);
-                        const uint32_t acc0 = (ch > 0 || j > 0) ? 1u : 0u;
-                        tc::mma_bf16(tmem, dah, dbh, idesc, acc0);
-                        tc::mma_bf16(tmem, dah, dbl, idesc, 1u);
-                        tc::mma_bf16(tmem, dal, dbh, idesc, 1u);
+                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                };
+                copy(0, stg);
+                for (int ch = 0; ch < nchunk; ++ch, ++it) {
+                    float *S = stg + (size_t)(ch & 1) * KC * 128;
+                    if (ch + 1 < nchunk) {
+                        copy(ch + 1, stg + (size_t)((ch + 1) & 1) * KC * 128);
+                        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                    } else {
+                        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
                     }
-                    tc::mma_commit(&bars[s]);
-                }
-                pending[s] = true;
-                ++chunk_ctr;
-                return true;
-            };
-            // two register sets: chunk ch+2 loads while chunks ch, ch+1 are stored
-            float va[NV], vb[NV];
-            load(0, va);
-            if (nchunk > 1) load(1, vb);
-            for (int ch = 0; ch < nchunk; ch += 2) {
-                if (!step(ch, va)) goto drain;
-                if (ch + 2 < nchunk) load(ch + 2, va);
-                if (ch + 1 < nchunk) {
-                    if (!step(ch + 1, vb)) goto drain;
-                    if (ch + 3 < nchunk) load(ch + 3, vb);
+                    const int s = (int)(it % NS);
+                    const long long round = it / NS;
+                    if (round > 0 && !wait(&empty[s], (uint32_t)((round - 1) & 1))) {
+                        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                        goto prod_out;
+                    }
+                    uint16_t *Ah = ring + (size_t)(2 * s) * 128 * KC;
+                    uint16_t *Al = Ah + (size_t)128 * KC;
+#pragma unroll
+                    for (int i = 0; i < NPAIR; ++i) {
+                        const int kp = kp0 + KPS * i;
+                        if (kp >= KC / 2) break;
+                        const int kl = 2 * kp;
+                        const int kk = ch * KC + kl;
+                        const float v0 = S[kl * 128 + q], v1 = S[(kl + 1) * 128 + q];
+                        const int d0 = kk < N ? cls[kk] : 2, d1 = kk + 1 < N ? cls[kk + 1] : 2;
+                        const int r0 = kk < N ? pick3(d0, row0, row1, row2) : gi * 64 + qq;
+                        const int r1 = kk + 1 < N ? pick3(d1, row0, row1, row2) : gi * 64 + qq;
+                        if (r0 == r1) {
+                            uint32_t hi, lo;
+                            split_bf16x2(v0, v1, hi, lo);
+                            const int o = tc::canon_off(r0, kl, KC);
+                            *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
+                            *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
+                        } else {
+                            // the two ordinates use different layouts (different rows for
+                            // slot q); each (row, k) is still written once
+                            const int rs[2] = {r0, r1};
+                            const float vv[2] = {v0, v1};
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                __nv_bfloat16 h = __float2bfloat16_rn(vv[t]);
+                                __nv_bfloat16 l = __float2bfloat16_rn(vv[t] - __bfloat162float(h));
+                                const int o = tc::canon_off(rs[t], kl + t, KC);
+                                Ah[o] = __bfloat16_as_ushort(h);
+                                Al[o] = __bfloat16_as_ushort(l);
+                            }
+                        }
+                    }
+                    tc::fence_proxy_async();
+                    tc::mbar_arrive(&full[s]);
                 }
             }
-            // all MMAs of this pass done
-            for (int s = 0; s < 2; ++s) {
-                if (pending[s]) {
-                    if (!cta_wait(&bars[s], phase[s], abort_flag)) goto drain;
-                    phase[s] ^= 1;
-                    pending[s] = false;
+        }
+    prod_out:;
+    } else if (warp == 16) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16(128, NB);
+            const uint32_t a_sbo = (KC / 8) * 128, b_sbo = (Kp / 8) * 128;
+            const uint32_t bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
+            long long it = 0, job = 0;
+            bool ok = true;
+            for (long long w = blockIdx.x; w < items && ok; w += gridDim.x) {
+                const TileInfo ti = P.tiles[w / npair];
+                const int passes = (ti.flags & 1) ? 2 : 1;
+                for (int pass = 0; pass < passes && ok; ++pass, ++job) {
+                    const int b = (int)(job & 1);
+                    const long long use = job >> 1;
+                    if (use > 0 && !wait(&tempty[b], (uint32_t)((use - 1) & 1))) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)b * ACC_COLS;
+                    for (int ch = 0; ch < nchunk; ++ch, ++it) {
+                        const int s = (int)(it % NS);
+                        if (!wait(&full[s], (uint32_t)((it / NS) & 1))) { ok = false; break; }
+                        tc::fence_after_sync();
+                        const uint32_t ah = tc::smem_u32(ring + (size_t)(2 * s) * 128 * KC);
+                        const uint32_t al = ah + 128 * KC * 2;
+#pragma unroll
+                        for (int j = 0; j < KC / 16; ++j) {
+                            const uint32_t aoff = j * 256;
+                            const uint32_t boff = (uint32_t)(ch * KC / 16 + j) * 256;
+                            const uint64_t dah = tc::sdesc(ah + aoff, 128, a_sbo), dal = tc::sdesc(al + aoff, 128, a_sbo);
+                            const uint64_t dbh = tc::sdesc(bh + boff, 128, b_sbo), dbl = tc::sdesc(bl + boff, 128, b_sbo);
+                            tc::mma_bf16(d, dah, dbh, idesc, (ch > 0 || j > 0) ? 1u : 0u);
+                            tc::mma_bf16(d, dah, dbl, idesc, 1u);
+                            tc::mma_bf16(d, dal, dbh, idesc, 1u);
+                        }
+                        tc::mma_commit(&empty[s]);
+                    }
+                    if (ok) tc::mma_commit(&tfull[b]);
                 }
             }
-            tc::fence_after_sync();
-            if (warp < 4) {
-                const int r = warp * 32 + lane;
-                const int egi = r >> 6, rr = r & 63;
-                const int eg = 2 * pair + egi;
-                const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
-                const bool valid = eg < G && ix < P.nx && iy < P.ny;
-                const long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
-                const bool moving = valid && P.midx[c] >= 0;
+        }
+    } else if (warp >= 12 && warp < 16) {
+        // ---------------- epilogue ----------------
+        const int quad = warp - 12;
+        const int r = quad * 32 + lane;
+        long long job = 0;
+        for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+            const long long tile = w / npair;
+            const int pair = (int)(w - tile * npair);
+            const TileInfo ti = P.tiles[tile];
+            const int passes = (ti.flags & 1) ? 2 : 1;
+            const int egi = r >> 6, rr = r & 63;
+            const int eg = 2 * pair + egi;
+            const int ix = ti.x0 + (rr & 7), iy = ti.y0 + (rr >> 3);
+            const bool valid = eg < G && ix < P.nx && iy < P.ny;
+            const long long c = ((long long)ti.z * P.ny + iy) * P.nx + ix;
+            const bool moving = valid && P.midx[c] >= 0;
+            float *ip = Ip + (c * G + eg) * NLM;
+            float *mp = mom + (c * G + eg) * 10;
+            for (int pass = 0; pass < passes; ++pass, ++job) {
+                const int b = (int)(job & 1);
+                if (!wait(&tfull[b], (uint32_t)((job >> 1) & 1))) goto epi_out;
+                tc::fence_after_sync();
                 const bool write_sh = valid && ((pass == 0 && !moving) || (pass == 1 && moving));
                 const bool write_mom = valid && pass == 0;
-                float *ip = Ip + (c * G + eg) * NLM;
-                float *mp = mom + (c * G + eg) * 10;
                 for (int c0 = 0; c0 < NB; c0 += 16) {
                     float v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                    tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * ACC_COLS + (uint32_t)c0, v);
+                    if (c0 + 16 <= NLM && (NLM & 3) == 0) {
+                        // a full block of harmonics: four 16-byte stores
+                        if (write_sh) {
+#pragma unroll
+                            for (int j = 0; j < 16; j += 4)
+                                *reinterpret_cast<float4 *>(&ip[c0 + j]) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        }
+                        continue;
+                    }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int col = c0 + j;
@@ -277,22 +355,15 @@ __global__ void __launch_bounds__(256, 1) k_project_tc(Prob<float> P, const floa
                         }
                     }
                 }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&tempty[b]);
             }
-            tc::fence_before_sync();
-            __syncthreads();
         }
+    epi_out:;
     }
-    goto done;
-drain:
-    if (threadIdx.x == 0) {
-        atomicExch(err, 1);
-        for (int s = 0; s < 2; ++s)
-            if (pending[s]) tc::mbar_wait(&bars[s], phase[s], kWaitLimit);
-    }
-done:
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * ACC_COLS);
 }
 
 // -------------------------------------------------------------------------
@@ -464,10 +535,12 @@ done:
 // -------------------------------------------------------------------------
 static constexpr int kProjKC = 32;
 
-size_t project_tc_smem_bytes(const shd_ctx *c)
+static size_t project_tc_smem_ns(const shd_ctx *c, int ns)
 {
-    return (size_t)2 * c->NB * c->tc_Kp * 2 + (size_t)4 * 128 * kProjKC * 2 + 64 + (size_t)c->tc_Kp;
+    return (size_t)2 * c->NB * c->tc_Kp * 2 + (size_t)ns * 2 * 128 * kProjKC * 2 + (size_t)2 * kProjKC * 128 * 4 +
+           (2 * ns + 4) * 8 + 16 + (size_t)c->tc_Kp;
 }
+size_t project_tc_smem_bytes(const shd_ctx *c) { return project_tc_smem_ns(c, 2); }
 size_t sh2lab_tc_smem_bytes(const shd_ctx *c)
 {
     return (size_t)2 * c->tc_Np * c->tc_Kq * 2 + (size_t)2 * 128 * c->tc_Kq * 2 + 128 * 4 + 128 * 4 + 64 +
@@ -477,7 +550,7 @@ size_t sh2lab_tc_smem_bytes(const shd_ctx *c)
 bool tc_usable(const shd_ctx *c)
 {
     if (c->precision != SHD_MIXED || !c->d_tc_Bh || !c->d_tc_Yh) return false;
-    if (c->NB > 256 || c->tc_Np > 512) return false;
+    if (c->NB > 128 || c->tc_Np > 512) return false;
     return project_tc_smem_bytes(c) <= 227 * 1024 && sh2lab_tc_smem_bytes(c) <= 227 * 1024;
 }
 
@@ -492,16 +565,16 @@ cudaError_t launch_project_tc(const shd_ctx *ctx, const float *I, float *Ip, flo
                               cudaStream_t st)
 {
     Prob<float> P = make_prob<float>(ctx);
-    size_t sm = project_tc_smem_bytes(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_project_tc<kProjKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const bool three = project_tc_smem_ns(ctx, 3) <= 227 * 1024;
+    size_t sm = project_tc_smem_ns(ctx, three ? 3 : 2);
+    auto kern = three ? k_project_tc<kProjKC, 3> : k_project_tc<kProjKC, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     long long items = ctx->ntiles * ((ctx->G + 1) / 2);
     int grid = num_sms_tc(ctx);
     if (items < grid) grid = (int)items;
-    int cols = ctx->NB <= 32 ? 32 : ctx->NB <= 64 ? 64 : ctx->NB <= 128 ? 128 : 256;
-    k_project_tc<kProjKC><<<grid, 256, sm, st>>>(P, I, I0n, Ip, mom, (const uint16_t *)ctx->d_tc_Bh,
-                                                 (const uint16_t *)ctx->d_tc_Bl, ctx->NB, ctx->tc_Kp, cols,
-                                                 ctx->d_tc_err);
+    kern<<<grid, 544, sm, st>>>(P, I, I0n, Ip, mom, (const uint16_t *)ctx->d_tc_Bh, (const uint16_t *)ctx->d_tc_Bl,
+                                ctx->NB, ctx->tc_Kp, ctx->d_tc_err);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,12 @@ __device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+__device__ inline void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
 // Bounded wait on the phase with the given parity: false after `limit` polls.
 __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit)
 {

@@ -518,7 +518,11 @@ __global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__re
     const long long m = blockIdx.x;
     const long long c = P.moving[m];
     const T *src = In + m * G * N;
-    for (int i = threadIdx.x; i < G * N; i += blockDim.x) sI[i] = src[i];
+    // staged in mesh order: the angle stencils address the (theta, phi) mesh
+    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
+        const int g = i / N, k = i - g * N;
+        sI[(size_t)g * N + P.int2mesh[k]] = src[i];
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
         int g = i >> 1, rr = i & 1;
@@ -567,7 +571,11 @@ __global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restric
     const long long m = blockIdx.x;
     const long long c = P.moving[m];
     const T *src = S0 + m * G * N;
-    for (int i = threadIdx.x; i < G * N; i += blockDim.x) sS[i] = src[i];
+    // staged in mesh order: the angle stencils address the (theta, phi) mesh
+    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
+        const int g = i / N, k = i - g * N;
+        sS[(size_t)g * N + P.int2mesh[k]] = src[i];
+    }
     for (int g = threadIdx.x; g < G; g += blockDim.x) schi[g] = P.chi0[c * G + g];
     __syncthreads();
     for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
