@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUTDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libshdom_gb300.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["shd_api.cu", "shd_kernels.cu", "shd_transforms.cu", "shd_tc.cu", "shd_noalloc.cu"]
+SOURCES = ["shd_api.cu", "shd_kernels.cu", "shd_transforms.cu", "shd_tc.cu", "shd_tc_seg.cu", "shd_noalloc.cu"]
 
 
 def nvcc():

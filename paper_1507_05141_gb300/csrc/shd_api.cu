@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <functional>
 #include <vector>
 
 #include "shd_internal.cuh"
@@ -152,6 +153,8 @@ void free_all(shd_ctx *c)
                      (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
                      &c->d_lc, &c->d_linv, &c->d_tc_Bh, &c->d_tc_Bl, &c->d_tc_Yh, &c->d_tc_Yl,
                      (void **)&c->d_int2mesh, (void **)&c->d_mesh2int,
+                     &c->d_seg[0], &c->d_seg[1], &c->d_tcs_Bh[0], &c->d_tcs_Bh[1], &c->d_tcs_Bl[0],
+                     &c->d_tcs_Bl[1], &c->d_tcs_Yh[0], &c->d_tcs_Yh[1], &c->d_tcs_Yl[0], &c->d_tcs_Yl[1],
                      (void **)&c->d_tc_err};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
@@ -265,6 +268,69 @@ double bf16_val(uint16_t h)
 
 int canon_offset(int r, int k, int K) { return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7); }
 
+// BF16 hi / lo device copies (canonical K-major layout) of the rows [0, nr)
+// x columns [0, nk) of at(r, k), zero-padded to rows x K.
+static void split_upload(shd_ctx *c, void **dh, void **dl, int rows, int K, const std::function<double(int, int)> &at,
+                         int nr, int nk, int &rc)
+{
+    std::vector<uint16_t> h((size_t)rows * K, 0), l(h.size(), 0);
+    for (int r = 0; r < nr; ++r)
+        for (int k = 0; k < nk; ++k) {
+            const double x = at(r, k);
+            const uint16_t hh = bf16_rne((float)x);
+            const int o = canon_offset(r, k, K);
+            h[o] = hh;
+            l[o] = bf16_rne((float)(x - bf16_val(hh)));
+        }
+    if ((rc = dalloc(c, dh, h.size() * 2, "tc segment operand"))) return;
+    if ((rc = dalloc(c, dl, l.size() * 2, "tc segment operand"))) return;
+    cudaError_t e = cudaMemcpy(*dh, h.data(), h.size() * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(*dl, l.data(), l.size() * 2, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_fail(e, "tc segment operand");
+}
+
+// Segment tiling and per-group operands of the mixed path (needs the grid:
+// the groups follow the axis each ordinate crosses first).
+int upload_seg_operands(shd_ctx *c, const std::vector<double> &Bp)
+{
+    for (int grp = 0; grp < 2; ++grp) {
+        dfree(c->d_seg[grp]); dfree(c->d_tcs_Bh[grp]); dfree(c->d_tcs_Bl[grp]);
+        dfree(c->d_tcs_Yh[grp]); dfree(c->d_tcs_Yl[grp]);
+        c->nseg[grp] = 0;
+    }
+    if (c->precision != SHD_MIXED || !c->have_grid) return SHD_OK;
+    auto up = [](int v, int m) { return (v + m - 1) / m * m; };
+    int rc = SHD_OK;
+    for (int grp = 0; grp < 2; ++grp) {
+        const int kbeg = grp ? c->nA : 0, kcnt = grp ? c->N - c->nA : c->nA;
+        if (kcnt == 0) continue;
+        c->tcs_Kp[grp] = up(kcnt, 32);
+        c->tcs_Np[grp] = up(kcnt, 16);
+        split_upload(c, &c->d_tcs_Bh[grp], &c->d_tcs_Bl[grp], c->NB, c->tcs_Kp[grp],
+                     [&](int j, int k) { return Bp[(size_t)(kbeg + k) * c->NB + j]; }, c->NB, kcnt, rc);
+        if (rc) return rc;
+        split_upload(c, &c->d_tcs_Yh[grp], &c->d_tcs_Yl[grp], c->tcs_Np[grp], c->tc_Kq,
+                     [&](int k, int p) { return c->h_Y[(size_t)(kbeg + k) * c->NLM + p]; }, kcnt, c->NLM, rc);
+        if (rc) return rc;
+        // group 0: runs of 128 nodes of each z-plane in (y, x) order;
+        // group 1: of each x-plane in (z, y) order
+        const int nplane = grp ? c->nx : c->nz;
+        const long long per = grp ? (long long)c->nz * c->ny : (long long)c->nx * c->ny;
+        std::vector<int> seg;
+        for (int pl = 0; pl < nplane; ++pl)
+            for (long long p0 = 0; p0 < per; p0 += 128) {
+                seg.push_back(pl);
+                seg.push_back((int)p0);
+                seg.push_back(0);
+                seg.push_back(0);
+            }
+        c->nseg[grp] = (long long)seg.size() / 4;
+        if ((rc = dalloc(c, &c->d_seg[grp], seg.size() * sizeof(int), "segments"))) return rc;
+        CK(cudaMemcpy(c->d_seg[grp], seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice), "segments");
+    }
+    return SHD_OK;
+}
+
 // Tensor-core operands of the mixed path: a value x is stored as BF16
 // hi = bf16(x) and lo = bf16(x - hi), in the canonical K-major layout.
 int upload_tc_operands(shd_ctx *c, const std::vector<double> &Bp)
@@ -304,7 +370,7 @@ int upload_tc_operands(shd_ctx *c, const std::vector<double> &Bp)
     CK(cudaMemcpy(c->d_tc_Bl, bl.data(), bl.size() * 2, cudaMemcpyHostToDevice), "tc Bl");
     CK(cudaMemcpy(c->d_tc_Yh, yh.data(), yh.size() * 2, cudaMemcpyHostToDevice), "tc Yh");
     CK(cudaMemcpy(c->d_tc_Yl, yl.data(), yl.size() * 2, cudaMemcpyHostToDevice), "tc Yl");
-    return SHD_OK;
+    return upload_seg_operands(c, Bp);
 }
 
 // Internal ordinate order: grouped by the axis each ordinate crosses first

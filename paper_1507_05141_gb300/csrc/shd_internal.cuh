@@ -160,6 +160,15 @@ struct shd_ctx {
     void *d_tc_Yh = nullptr, *d_tc_Yl = nullptr;  // [tc_Np][tc_Kq] harmonics
     int tc_Kp = 0, tc_Np = 0, tc_Kq = 0;
     int *d_tc_err = nullptr;                      // set by a kernel whose wait timed out
+    // segment tiling of the mixed path: group 0 = ordinates [0, nA) over
+    // 128-node runs of z-planes, group 1 = [nA, N) over runs of x-planes;
+    // segments {plane, first in-plane position, 0, 0} and the group's
+    // operands (local ordinate index, BF16 hi / lo, canonical K-major)
+    void *d_seg[2] = {nullptr, nullptr};
+    long long nseg[2] = {0, 0};
+    void *d_tcs_Bh[2] = {nullptr, nullptr}, *d_tcs_Bl[2] = {nullptr, nullptr};  // [NB][tcs_Kp]
+    void *d_tcs_Yh[2] = {nullptr, nullptr}, *d_tcs_Yl[2] = {nullptr, nullptr};  // [tcs_Np][tc_Kq]
+    int tcs_Kp[2] = {0, 0}, tcs_Np[2] = {0, 0};
     double *d_stage = nullptr;    // staging buffer for host <-> device copies (FP64)
     size_t stage_elems = 0;
     long long bytes = 0;
@@ -423,6 +432,11 @@ cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaSt
 template <class T>
 cudaError_t launch_project_scratch(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *scratch, cudaStream_t st);
 bool tc_usable(const shd_ctx *ctx);
+bool seg_usable(const shd_ctx *ctx);
+cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, float *mom, const float *I0n,
+                               cudaStream_t st);
+cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *S0n,
+                              cudaStream_t st);
 size_t project_tc_smem_bytes(const shd_ctx *ctx);
 size_t sh2lab_tc_smem_bytes(const shd_ctx *ctx);
 cudaError_t launch_project_tc(const shd_ctx *ctx, const float *I, float *Ip, float *mom, const float *I0n,

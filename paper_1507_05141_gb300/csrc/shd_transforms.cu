@@ -702,6 +702,7 @@ cudaError_t launch_project_nm(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if constexpr (sizeof(T) == 4) {
+        if (seg_usable(ctx)) return launch_project_seg(ctx, I, Ip, mom, nm1, st);
         if (tc_usable(ctx)) return launch_project_tc(ctx, I, Ip, mom, nm1, st);
         if (project_persist_smem_bytes(ctx) <= kSmemLimit) return launch_project_persist(ctx, I, Ip, mom, nm1, st);
     }
@@ -735,7 +736,10 @@ cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaS
     bool done = false;
     if constexpr (sizeof(T) == 4) {
         size_t smp = sh2lab_persist_smem_bytes(ctx);
-        if (tc_usable(ctx)) {
+        if (seg_usable(ctx)) {
+            if ((e = launch_sh2lab_seg(ctx, Sp, eta, chi, nm0, st)) != cudaSuccess) return e;
+            done = true;
+        } else if (tc_usable(ctx)) {
             if ((e = launch_sh2lab_tc(ctx, Sp, eta, chi, nm0, st)) != cudaSuccess) return e;
             done = true;
         } else if (smp <= kSmemLimit) {
