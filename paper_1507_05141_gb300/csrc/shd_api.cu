@@ -290,44 +290,72 @@ static void split_upload(shd_ctx *c, void **dh, void **dl, int rows, int K, cons
 }
 
 // Segment tiling and per-group operands of the mixed path (needs the grid:
-// the groups follow the axis each ordinate crosses first).
+// the classes follow the axis each ordinate crosses first).
 int upload_seg_operands(shd_ctx *c, const std::vector<double> &Bp)
 {
     for (int grp = 0; grp < 2; ++grp) {
         dfree(c->d_seg[grp]); dfree(c->d_tcs_Bh[grp]); dfree(c->d_tcs_Bl[grp]);
         dfree(c->d_tcs_Yh[grp]); dfree(c->d_tcs_Yl[grp]);
         c->nseg[grp] = 0;
+        c->tcs_Kp[grp] = c->tcs_nchunk[grp] = 0;
     }
+    c->seg_ready = false;
     if (c->precision != SHD_MIXED || !c->have_grid) return SHD_OK;
-    auto up = [](int v, int m) { return (v + m - 1) / m * m; };
+    auto pow2_box = [](int n) {
+        int b = 4;
+        while (b < n && b < 128) b *= 2;
+        return b;
+    };
     int rc = SHD_OK;
     for (int grp = 0; grp < 2; ++grp) {
-        const int kbeg = grp ? c->nA : 0, kcnt = grp ? c->N - c->nA : c->nA;
-        if (kcnt == 0) continue;
-        c->tcs_Kp[grp] = up(kcnt, 32);
-        c->tcs_Np[grp] = up(kcnt, 16);
+        // the group's classes: {map index, first internal ordinate, count}
+        int cls[2][3];
+        int ncls = 0;
+        if (grp == 0) {
+            if (c->nZ > 0) { cls[ncls][0] = 0; cls[ncls][1] = 0; cls[ncls][2] = c->nZ; ++ncls; }
+            if (c->nA > c->nZ) { cls[ncls][0] = 1; cls[ncls][1] = c->nZ; cls[ncls][2] = c->nA - c->nZ; ++ncls; }
+        } else if (c->N > c->nA) {
+            cls[ncls][0] = 0; cls[ncls][1] = c->nA; cls[ncls][2] = c->N - c->nA; ++ncls;
+        }
+        if (ncls == 0) continue;
+        std::vector<int> slot;  // internal ordinate of each slot, -1 at padding
+        int nch = 0;
+        for (int q = 0; q < ncls; ++q)
+            for (int k0 = 0; k0 < cls[q][2]; k0 += 32) {
+                if (nch == 16) return SHD_OK;  // more than 512 slots: the brick kernels take over
+                c->tcs_chunk[grp][nch][0] = cls[q][0];
+                c->tcs_chunk[grp][nch][1] = k0;
+                ++nch;
+                for (int i = 0; i < 32; ++i) slot.push_back(k0 + i < cls[q][2] ? cls[q][1] + k0 + i : -1);
+            }
+        c->tcs_nchunk[grp] = nch;
+        c->tcs_Kp[grp] = 32 * nch;
         split_upload(c, &c->d_tcs_Bh[grp], &c->d_tcs_Bl[grp], c->NB, c->tcs_Kp[grp],
-                     [&](int j, int k) { return Bp[(size_t)(kbeg + k) * c->NB + j]; }, c->NB, kcnt, rc);
+                     [&](int j, int s) { return slot[s] < 0 ? 0.0 : Bp[(size_t)slot[s] * c->NB + j]; }, c->NB,
+                     c->tcs_Kp[grp], rc);
         if (rc) return rc;
-        split_upload(c, &c->d_tcs_Yh[grp], &c->d_tcs_Yl[grp], c->tcs_Np[grp], c->tc_Kq,
-                     [&](int k, int p) { return c->h_Y[(size_t)(kbeg + k) * c->NLM + p]; }, kcnt, c->NLM, rc);
+        split_upload(c, &c->d_tcs_Yh[grp], &c->d_tcs_Yl[grp], c->tcs_Kp[grp], c->tc_Kq,
+                     [&](int s, int p) { return slot[s] < 0 ? 0.0 : c->h_Y[(size_t)slot[s] * c->NLM + p]; },
+                     c->tcs_Kp[grp], c->NLM, rc);
         if (rc) return rc;
-        // group 0: runs of 128 nodes of each z-plane in (y, x) order;
-        // group 1: of each x-plane in (z, y) order
-        const int nplane = grp ? c->nx : c->nz;
-        const long long per = grp ? (long long)c->nz * c->ny : (long long)c->nx * c->ny;
+        // tiles: group 0 boxes of (x, y) at each z, group 1 of (y, z) at each x
+        const int na = grp ? c->ny : c->nx, nbb = grp ? c->nz : c->ny, nplane = grp ? c->nx : c->nz;
+        const int bw = pow2_box(na), bh = 128 / bw;
+        c->seg_bw[grp] = bw;
         std::vector<int> seg;
         for (int pl = 0; pl < nplane; ++pl)
-            for (long long p0 = 0; p0 < per; p0 += 128) {
-                seg.push_back(pl);
-                seg.push_back((int)p0);
-                seg.push_back(0);
-                seg.push_back(0);
-            }
+            for (int b0 = 0; b0 < nbb; b0 += bh)
+                for (int a0 = 0; a0 < na; a0 += bw) {
+                    seg.push_back(pl);
+                    seg.push_back(a0);
+                    seg.push_back(b0);
+                    seg.push_back(0);
+                }
         c->nseg[grp] = (long long)seg.size() / 4;
         if ((rc = dalloc(c, &c->d_seg[grp], seg.size() * sizeof(int), "segments"))) return rc;
         CK(cudaMemcpy(c->d_seg[grp], seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice), "segments");
     }
+    c->seg_ready = true;
     return SHD_OK;
 }
 
@@ -397,7 +425,11 @@ void order_ordinates(shd_ctx *c)
         for (int k = 0; k < N; ++k)
             if (cls[k] == want) c->h_int2mesh.push_back(k);
     c->nA = 0;
-    for (int k = 0; k < N; ++k) c->nA += cls[k] != 0;
+    c->nZ = 0;
+    for (int k = 0; k < N; ++k) {
+        c->nA += cls[k] != 0;
+        c->nZ += cls[k] == 2;
+    }
     c->h_mesh2int.assign(N, 0);
     for (int i = 0; i < N; ++i) c->h_mesh2int[c->h_int2mesh[i]] = i;
     c->h_dirs.assign(3 * (size_t)N, 0.0);

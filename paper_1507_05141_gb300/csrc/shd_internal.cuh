@@ -116,6 +116,7 @@ struct shd_ctx {
     std::vector<double> h_dirs_mesh, h_W_mesh, h_Y_mesh;
     std::vector<int> h_int2mesh, h_mesh2int;
     int nA = 0;  // internal ordinates crossing z or y first
+    int nZ = 0;  // internal ordinates crossing z first ([0, nZ))
     int *d_int2mesh = nullptr, *d_mesh2int = nullptr;
     std::vector<shd::Ordinate> h_ord;
     // groups
@@ -160,15 +161,20 @@ struct shd_ctx {
     void *d_tc_Yh = nullptr, *d_tc_Yl = nullptr;  // [tc_Np][tc_Kq] harmonics
     int tc_Kp = 0, tc_Np = 0, tc_Kq = 0;
     int *d_tc_err = nullptr;                      // set by a kernel whose wait timed out
-    // segment tiling of the mixed path: group 0 = ordinates [0, nA) over
-    // 128-node runs of z-planes, group 1 = [nA, N) over runs of x-planes;
-    // segments {plane, first in-plane position, 0, 0} and the group's
-    // operands (local ordinate index, BF16 hi / lo, canonical K-major)
+    // segment tiling of the mixed path: group 0 = z- and y-class ordinates
+    // over bw x (128/bw) boxes of (x, y) at one z; group 1 = x-class over
+    // boxes of (y, z) at one x.  Segments {plane, a0, b0, 0}; the group's
+    // ordinates in slots (each class padded to a multiple of 32) with the
+    // operands over slots (BF16 hi / lo, canonical K-major) and per chunk of
+    // 32 slots {class map index in the group, first ordinate in the class}
     void *d_seg[2] = {nullptr, nullptr};
     long long nseg[2] = {0, 0};
+    int seg_bw[2] = {0, 0};
     void *d_tcs_Bh[2] = {nullptr, nullptr}, *d_tcs_Bl[2] = {nullptr, nullptr};  // [NB][tcs_Kp]
-    void *d_tcs_Yh[2] = {nullptr, nullptr}, *d_tcs_Yl[2] = {nullptr, nullptr};  // [tcs_Np][tc_Kq]
-    int tcs_Kp[2] = {0, 0}, tcs_Np[2] = {0, 0};
+    void *d_tcs_Yh[2] = {nullptr, nullptr}, *d_tcs_Yl[2] = {nullptr, nullptr};  // [tcs_Kp][tc_Kq]
+    int tcs_Kp[2] = {0, 0}, tcs_nchunk[2] = {0, 0};
+    int tcs_chunk[2][16][2] = {};
+    bool seg_ready = false;
     double *d_stage = nullptr;    // staging buffer for host <-> device copies (FP64)
     size_t stage_elems = 0;
     long long bytes = 0;

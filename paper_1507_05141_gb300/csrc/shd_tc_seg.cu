@@ -1,34 +1,36 @@
 // Stages a1 (project) and a3 (sh2lab) of the mixed-precision path on the
-// tcgen05 tensor cores, with every global access a contiguous run.
+// tcgen05 tensor cores, fed and drained by TMA.
 //
-// The internal ordinate order puts the ordinates crossing z or y first
-// (group A, [0, nA)) ahead of those crossing x first (group B, [nA, N)).
-// Laboratory-frame rows are handled per group with a node tiling chosen so
-// that each (ordinate, group) row of a tile is contiguous in that ordinate's
-// sweep layout:
-//   group A: 128 consecutive nodes of a z-plane in (y, x) order -- one run
-//            in the z-layout, runs of nx nodes in the y-layout;
-//   group B: 128 consecutive nodes of an x-plane in (z, y) order -- one run
-//            in the x-layout.
-// A segment item is (segment, energy group g), M = 128 rows.  Comoving rows
-// of moving nodes live node-major ([m][g][k], contiguous in k) in the remap
-// scratch; they form a third, plain row-major contraction ("rows" mode) over
-// 128 consecutive (m, g) rows.
+// The internal ordinate order is z-class, y-class, x-class (the axis each
+// ordinate crosses first), so every class is one contiguous block of the
+// discrete-ordinate arrays and shares one sweep layout.  Laboratory-frame
+// rows are handled in two groups with a node tiling chosen per group so that
+// a tile of 128 nodes is one box of a 5-D tensor map over that layout:
+//   group A (z- and y-class): a bw x (128/bw) block of (x, y) at one z,
+//   group B (x-class):        a bw x (128/bw) block of (y, z) at one x.
+// The group's ordinates are laid out in "slots": each class padded to a
+// multiple of the 32-ordinate chunk, so that every chunk is one TMA box
+// (class map, 32 ordinates, 128 nodes, one energy group).  Comoving rows of
+// moving nodes live node-major ([m][g][k], contiguous in k) in the remap
+// scratch and form a third, row-major contraction ("rows" mode) read and
+// written through 2-D maps with the 128-byte swizzle.
 //
-//   a1  D[128 x nb] = A[128 x K] . Bp^T   (Bp = [W Y | moment weights] over
-//       the item's ordinates): group A stores the laboratory moments and the
-//       I_lm of nodes at rest, group B adds its part, rows mode stores the
-//       I_lm of moving nodes from their comoving intensities.  Warp-
-//       specialised: producers cp.async FP32 rows into a staging ring and
-//       convert them to BF16 hi / lo in the canonical layout, one thread
-//       issues the MMAs into two alternating tensor-memory accumulators,
-//       epilogue warps drain them.
-//   a3  D[128 x K] = S[128 x NLM] . Y^T: segment mode writes eta = chi0 D,
-//       chi = chi0 of nodes at rest into the sweep layout; rows mode writes
-//       the comoving source S0 of moving nodes node-major.
+//   a1  D[128 x nb] = A[128 x K] . Bp^T over the item's slots (Bp = [W Y |
+//       moment weights], zero at padding slots): group A stores the
+//       laboratory moments and the I_lm of nodes at rest, group B adds its
+//       part, rows mode stores the I_lm of moving nodes from their comoving
+//       intensities.  Warp-specialised: one thread issues TMA boxes into an
+//       FP32 staging ring, converter warps split them into BF16 hi / lo in
+//       the canonical layout, one thread issues the MMAs into two alternating
+//       tensor-memory accumulators, epilogue warps drain them.
+//   a3  D[128 x K] = S[128 x NLM] . Y^T: segment mode stages eta = chi0 D and
+//       chi = chi0 in shared memory and TMA-stores them into the sweep
+//       layout (moving nodes are overwritten afterwards by their Lorentz
+//       remap); rows mode stores the comoving source S0 of moving nodes.
 // FP32 operands are split into BF16 hi + lo and the three products hi.hi +
 // hi.lo + lo.hi accumulate in FP32.  Every mbarrier wait is bounded; on
 // timeout the kernel raises *err and winds down without hanging.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -40,10 +42,9 @@ namespace shd {
 namespace {
 
 constexpr long long kSegWaitLimit = 1LL << 22;  // mbarrier polls before giving up (about a second)
-constexpr int kSegKC = 32;                      // ordinates per pipeline chunk
-constexpr int kSP = 132;                        // segment staging [k][row] stride (floats)
-constexpr int kSR = kSegKC + 8;                 // rows staging [row][k] stride (floats)
-constexpr int kNProd = 384;                     // producer threads of a1
+constexpr int kKC = 32;                         // ordinates per chunk
+constexpr int kBox = 128 * kKC;                 // floats per TMA box (16 KB)
+constexpr int kNConv = 256;                     // converter threads of a1
 
 __device__ inline void split2(float a, float b, uint32_t &hi, uint32_t &lo)
 {
@@ -54,48 +55,6 @@ __device__ inline void split2(float a, float b, uint32_t &hi, uint32_t &lo)
     lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
 }
 
-// Node c of row r of a segment and its offsets in the sweep layouts of the
-// group's classes: off2 for z (group A) or x (group B), off1 for y.  False
-// beyond the end of the plane.
-__device__ inline bool seg_node(const Prob<float> &P, int groupB, int plane, int p0, int r, long long &c,
-                                long long &off2, long long &off1)
-{
-    const int p = p0 + r;
-    if (!groupB) {
-        const long long PA = (long long)P.nx * P.ny;
-        if (p >= PA) return false;
-        const int x = p % P.nx, y = p / P.nx, z = plane;
-        c = ((long long)z * P.ny + y) * P.nx + x;
-        off2 = (long long)z * PA + p;                 // (z, y, x)
-        off1 = ((long long)y * P.nz + z) * P.nx + x;  // (y, z, x)
-    } else {
-        const long long PB = (long long)P.nz * P.ny;
-        if (p >= PB) return false;
-        const int y = p % P.ny, z = p / P.ny, x = plane;
-        c = ((long long)z * P.ny + y) * P.nx + x;
-        off2 = (long long)x * PB + p;  // (x, z, y)
-        off1 = off2;
-    }
-    return true;
-}
-
-__device__ inline void named_bar(int id, int count)
-{
-    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
-}
-
-__device__ inline void cp_async4(float *dst, const float *src)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
-}
-__device__ inline void cp_async16(float *dst, const float *src)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
-}
-
-// value v into *dst, added to the old value when acc
 __device__ inline void put1(float *dst, float v, bool acc) { *dst = acc ? *dst + v : v; }
 __device__ inline void put4(float *dst, const float *v, bool acc)
 {
@@ -107,55 +66,108 @@ __device__ inline void put4(float *dst, const float *v, bool acc)
     *reinterpret_cast<float4 *>(dst) = o;
 }
 
+// float4 chunk j of row r of a [rows][32] FP32 tile written with the
+// 128-byte swizzle (the tile starts on a 1024-byte boundary)
+__device__ inline float4 *swz4(float *tile, int r, int j)
+{
+    return reinterpret_cast<float4 *>(tile + r * 32 + ((j ^ (r & 7)) << 2));
+}
+
 }  // namespace
+
+// Up to four tensor maps per launch: segment mode a1 {class 0, class 1};
+// a3 {eta class 0, eta class 1, chi class 0, chi class 1}; rows mode {A}.
+struct SegMaps {
+    CUtensorMap m[4];
+};
 
 // What one launch of the segment / rows kernels covers.
 struct SegArgs {
-    const int4 *segs;  // segment mode: {plane, first in-plane position, 0, 0}
-    long long nitem;   // segment mode: segments x G; rows mode: ceil(rows / 128)
-    long long nrows;   // rows mode: nmoving x G
-    int groupB;        // segment mode: 0 = group A, 1 = group B
-    int kbeg, kcnt;    // the ordinates [kbeg, kbeg + kcnt) of the contraction
-    int Kp;            // kcnt rounded up to the chunk (a1) or to 16 (a3)
-    int nb;            // a1: output columns (rows of Bp) of the MMA
-    int accumulate;    // a1: add to I_lm / moments instead of storing
+    const int4 *segs;   // segment mode: {plane, a0, b0, 0} (a fastest in the box)
+    long long nitem;    // segment mode: segments x G; rows mode: ceil(rows / 128)
+    long long nrows;    // rows mode: nmoving x G
+    int groupB;         // segment mode: 0 = group A (plane z, a = x, b = y); 1 = B (plane x, a = y, b = z)
+    int bw;             // segment mode: box width along a (a power of two, 4..128)
+    int nchunk;         // chunks of 32 slots
+    int Kp;             // slots = 32 nchunk
+    int nb;             // a1: output columns (rows of Bp) of the MMA
+    int accumulate;     // a1: add to I_lm / moments instead of storing
+    int2 chunk[16];     // {map index, first ordinate of the chunk within its class}
 };
 
+// Node of row r of a segment tile; false outside the grid.
+__device__ inline bool seg_node(const Prob<float> &P, const SegArgs &S, int4 sd, int r, long long &c)
+{
+    const int a = sd.y + (r & (S.bw - 1)), b = sd.z + r / S.bw;
+    int x, y, z;
+    if (!S.groupB) {
+        x = a; y = b; z = sd.x;
+        if (x >= P.nx || y >= P.ny) return false;
+    } else {
+        y = a; z = b; x = sd.x;
+        if (y >= P.ny || z >= P.nz) return false;
+    }
+    c = ((long long)z * P.ny + y) * P.nx + x;
+    return true;
+}
+
+// TMA box coordinates of chunk `ch` of item w.
+__device__ inline void box_coords(const SegArgs &S, int ROWS, long long w, int G, int ch, int (&cc)[5])
+{
+    const int k0 = S.chunk[ch].y;
+    if (ROWS) {
+        cc[0] = k0;
+        cc[1] = (int)(w * 128);
+        cc[2] = cc[3] = cc[4] = 0;
+        return;
+    }
+    const long long sg = w / G;
+    const int g = (int)(w - sg * G);
+    const int4 sd = S.segs[sg];
+    // group A: z-class map (x, y, z, g, k), y-class map (x, z, y, g, k);
+    // group B: x-class map (y, z, x, g, k)
+    const bool yclass = !S.groupB && S.chunk[ch].x == 1;
+    cc[0] = sd.y;
+    cc[1] = yclass ? sd.x : sd.z;
+    cc[2] = yclass ? sd.z : sd.x;
+    cc[3] = g;
+    cc[4] = k0;
+}
+
 // -------------------------------------------------------------------------
-// a1.  Warps 0-11 producers, 12-15 epilogue (tensor-memory lane quadrants),
-// 16 MMA issuer.  ROWS = 0: segment mode, laboratory I in the sweep layouts;
-// ROWS = 1: comoving I0 node-major (row (m, g) = I0 + (m G + g) N).
-// Shared memory: Bh, Bl [nb][Kp] resident; ring [NS][hi, lo][128][KC]
-// (BF16, canonical); FP32 staging [3] x ([KC][kSP] or [128][kSR]); barriers;
-// the classes of the item's ordinates.
+// a1.  Warps 0-7 converters, 8-11 epilogue (tensor-memory lane quadrants
+// 0-3), 12 TMA producer, 13 MMA issuer.  Shared memory: Bh, Bl [nb][Kp]
+// resident; FP32 staging [NSTG][box]; BF16 ring [NR][hi, lo][128][32]
+// (canonical); the barriers.
 // -------------------------------------------------------------------------
-template <int NS, int ROWS>
-__global__ void __launch_bounds__(544, 1) k_project_seg(Prob<float> P, SegArgs S, const float *__restrict__ A,
+template <int NSTG, int NR, int ROWS>
+__global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
                                                         float *__restrict__ Ip, float *__restrict__ mom,
                                                         const uint16_t *__restrict__ gBh,
                                                         const uint16_t *__restrict__ gBl, int *err)
 {
-    constexpr int KC = kSegKC;
     constexpr uint32_t ACC_COLS = 128;
-    constexpr int NCM = 16 * (KC / 8);  // core matrices per chunk
-    constexpr int STG = ROWS ? 128 * kSR : KC * kSP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int Kp = S.Kp, nb = S.nb;
+    if (tc::smem_u32(smem_raw) & 1023) {  // the swizzled staging needs 1024-byte alignment
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    const int Kp = S.Kp, nb = S.nb, nchunk = S.nchunk;
     uint16_t *Bh = reinterpret_cast<uint16_t *>(smem_raw);
     uint16_t *Bl = Bh + (size_t)nb * Kp;
-    uint16_t *ring = Bl + (size_t)nb * Kp;                                   // [NS][2][128*KC]
-    float *stg = reinterpret_cast<float *>(ring + (size_t)NS * 2 * 128 * KC);  // [3][STG]
-    uint64_t *full = reinterpret_cast<uint64_t *>(stg + (size_t)3 * STG);
-    uint64_t *empty = full + NS;
-    uint64_t *tfull = empty + NS;
+    float *stg = reinterpret_cast<float *>(Bl + (size_t)nb * Kp);  // [NSTG][kBox]
+    uint16_t *ring = reinterpret_cast<uint16_t *>(stg + (size_t)NSTG * kBox);  // [NR][2][128*32]
+    uint64_t *sfull = reinterpret_cast<uint64_t *>(ring + (size_t)NR * 2 * 128 * kKC);
+    uint64_t *sempty = sfull + NSTG;
+    uint64_t *rfull = sempty + NSTG;
+    uint64_t *rempty = rfull + NR;
+    uint64_t *tfull = rempty + NR;
     uint64_t *tempty = tfull + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
-    volatile int *stop = abort_flag + 1;  // [2] producer decisions, alternating per chunk
-    unsigned char *cls = reinterpret_cast<unsigned char *>(tslot + 4);  // [Kp]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = P.N, G = P.G, NLM = P.NLM;
+    const int G = P.G, NLM = P.NLM;
     {
         const uint4 *sh = reinterpret_cast<const uint4 *>(gBh), *sl = reinterpret_cast<const uint4 *>(gBl);
         uint4 *dh = reinterpret_cast<uint4 *>(Bh), *dl = reinterpret_cast<uint4 *>(Bl);
@@ -164,19 +176,21 @@ __global__ void __launch_bounds__(544, 1) k_project_seg(Prob<float> P, SegArgs S
             dh[i] = sh[i];
             dl[i] = sl[i];
         }
-        for (int k = tid; k < Kp; k += blockDim.x) cls[k] = k < S.kcnt ? (unsigned char)P.ord[S.kbeg + k].d : 2;
     }
     if (tid == 0) {
-        for (int i = 0; i < NS; ++i) {
-            tc::mbar_init(&full[i], kNProd);
-            tc::mbar_init(&empty[i], 1);
+        for (int i = 0; i < NSTG; ++i) {
+            tc::mbar_init(&sfull[i], 1);
+            tc::mbar_init(&sempty[i], kNConv);
+        }
+        for (int i = 0; i < NR; ++i) {
+            tc::mbar_init(&rfull[i], kNConv);
+            tc::mbar_init(&rempty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&tfull[i], 1);
             tc::mbar_init(&tempty[i], 128);
         }
         *abort_flag = 0;
-        stop[0] = stop[1] = 0;
         tc::fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(tslot, 2 * ACC_COLS);
@@ -186,7 +200,6 @@ __global__ void __launch_bounds__(544, 1) k_project_seg(Prob<float> P, SegArgs S
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
 
-    const int nchunk = Kp / KC;
     auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
         for (long long i = 0; i < kSegWaitLimit; ++i) {
             if (tc::mbar_try_wait(bar, parity)) return true;
@@ -197,112 +210,72 @@ __global__ void __launch_bounds__(544, 1) k_project_seg(Prob<float> P, SegArgs S
         return false;
     };
 
-    if (warp < 12) {
-        // ---------------- producers ----------------
-        const int r0 = tid & 127, kslot = tid >> 7;  // segment copies: one row, ordinates kslot + 3i
-        const bool vec16 = (N & 3) == 0;
+    if (warp < 8) {
+        // ---------------- converters ----------------
         long long it = 0;
-        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x) {
-            // the item's source rows
-            long long off2 = 0, off1 = 0, gNc = 0;
-            bool valid = false;
-            const long long GNc = (long long)G * P.Nc;
-            if (!ROWS) {
-                const long long sg = w / G;
-                const int g = (int)(w - sg * G);
-                const int4 sd = S.segs[sg];
-                long long c;
-                valid = seg_node(P, S.groupB, sd.x, sd.y, r0, c, off2, off1);
-                gNc = (long long)g * P.Nc;
-            }
-            auto copy = [&](int ch, int sb) {
-                float *Sb = stg + (size_t)sb * STG;
-                if (!ROWS) {
-                    for (int kl = kslot; kl < KC; kl += 3) {
-                        const int kk = ch * KC + kl;
-                        float *dst = &Sb[kl * kSP + r0];
-                        if (valid && kk < S.kcnt)
-                            cp_async4(dst, A + (long long)(S.kbeg + kk) * GNc + gNc + (cls[kk] == 1 ? off1 : off2));
-                        else
-                            *dst = 0.f;
-                    }
-                } else if (vec16) {
-                    // 128 rows x KC ordinates as float4: thread -> (row, quad)
-                    for (int q = tid; q < 128 * (KC / 4); q += kNProd) {
-                        const int r = q / (KC / 4), k4 = (q - r * (KC / 4)) * 4;
-                        const long long row = w * 128 + r;
-                        const int kk = ch * KC + k4;
-                        float *dst = &Sb[r * kSR + k4];
-                        if (row < S.nrows && kk < N)
-                            cp_async16(dst, A + row * N + kk);
-                        else
-                            *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                } else {
-                    for (int q = tid; q < 128 * KC; q += kNProd) {
-                        const int r = q / KC, kl = q - r * KC;
-                        const long long row = w * 128 + r;
-                        const int kk = ch * KC + kl;
-                        float *dst = &Sb[r * kSR + kl];
-                        if (row < S.nrows && kk < N)
-                            cp_async4(dst, A + row * N + kk);
-                        else
-                            *dst = 0.f;
-                    }
-                }
-                asm volatile("cp.async.commit_group;\n" ::: "memory");
-            };
-            copy(0, (int)(it % 3));
-            if (nchunk > 1) copy(1, (int)((it + 1) % 3));
+        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x)
             for (int ch = 0; ch < nchunk; ++ch, ++it) {
-                if (ch + 1 < nchunk) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-                else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-                const int s = (int)(it % NS);
-                const long long round = it / NS;
-                // one thread waits for ring stage s; the decision reaches every
-                // producer through the barrier (slot it & 1 is rewritten only
-                // after the next barrier, when everyone has read it)
-                if (tid == 0) stop[it & 1] = (round > 0 && !wait(&empty[s], (uint32_t)((round - 1) & 1))) ? 1 : 0;
-                named_bar(1, kNProd);  // chunk ch landed everywhere; chunk ch-1 converted; stage s free
-                if (stop[it & 1]) {
-                    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-                    goto prod_out;
-                }
-                if (ch + 2 < nchunk) copy(ch + 2, (int)((it + 2) % 3));
-                const float *Sb = stg + (size_t)(it % 3) * STG;
-                uint16_t *Ah = ring + (size_t)(2 * s) * 128 * KC;
-                uint16_t *Al = Ah + (size_t)128 * KC;
-                // one core matrix (8 rows x 8 ordinates) per warp step:
-                // conflict-free staging reads and canonical stores
-                const int j = lane >> 2, kq = lane & 3;
-                for (int cm = warp; cm < NCM; cm += 12) {
-                    const int rb = cm / (KC / 8), kb = cm - rb * (KC / 8);
-                    const int row = rb * 8 + j, kl = kb * 8 + 2 * kq;
-                    float v0, v1;
+                const int s = (int)(it % NSTG), r = (int)(it % NR);
+                if (!wait(&sfull[s], (uint32_t)((it / NSTG) & 1))) goto conv_out;
+                if (it >= NR && !wait(&rempty[r], (uint32_t)((it / NR - 1) & 1))) goto conv_out;
+                float *Sb = stg + (size_t)s * kBox;
+                uint16_t *Ah = ring + (size_t)(2 * r) * 128 * kKC;
+                uint16_t *Al = Ah + (size_t)128 * kKC;
+                // unit = 32 rows x 8 ordinates (one core-matrix column of
+                // four core matrices): lane = row
+#pragma unroll
+                for (int uu = 0; uu < 2; ++uu) {
+                    const int u = warp + 8 * uu;
+                    const int rq = u & 3, kb = u >> 2;
+                    const int row = rq * 32 + lane;
+                    float v[8];
                     if (!ROWS) {
-                        v0 = Sb[kl * kSP + row];
-                        v1 = Sb[(kl + 1) * kSP + row];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) v[i] = Sb[(kb * 8 + i) * 128 + row];
                     } else {
-                        const float2 t = *reinterpret_cast<const float2 *>(&Sb[row * kSR + kl]);
-                        v0 = t.x;
-                        v1 = t.y;
+                        const float4 a = *swz4(Sb, row, 2 * kb), b = *swz4(Sb, row, 2 * kb + 1);
+                        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
                     }
-                    uint32_t hi, lo;
-                    split2(v0, v1, hi, lo);
-                    const int o = tc::canon_off(row, kl, KC);
-                    *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
-                    *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
+                    uint4 h, l;
+                    split2(v[0], v[1], h.x, l.x);
+                    split2(v[2], v[3], h.y, l.y);
+                    split2(v[4], v[5], h.z, l.z);
+                    split2(v[6], v[7], h.w, l.w);
+                    const int o = tc::canon_off(row, kb * 8, kKC);
+                    *reinterpret_cast<uint4 *>(&Ah[o]) = h;
+                    *reinterpret_cast<uint4 *>(&Al[o]) = l;
                 }
                 tc::fence_proxy_async();
-                tc::mbar_arrive(&full[s]);
+                tc::mbar_arrive(&sempty[s]);
+                tc::mbar_arrive(&rfull[r]);
             }
+    conv_out:;
+    } else if (warp == 12) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            long long it = 0;
+            for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x)
+                for (int ch = 0; ch < nchunk; ++ch, ++it) {
+                    const int s = (int)(it % NSTG);
+                    if (it >= NSTG && !wait(&sempty[s], (uint32_t)((it / NSTG - 1) & 1))) goto prod_out;
+                    int cc[5];
+                    box_coords(S, ROWS, w, G, ch, cc);
+                    tc::mbar_arrive_expect_tx(&sfull[s], kBox * 4);
+                    const void *map = &maps.m[S.chunk[ch].x];
+                    if (ROWS) tc::tma_load_2d(stg + (size_t)s * kBox, map, cc[0], cc[1], &sfull[s]);
+                    else tc::tma_load_5d(stg + (size_t)s * kBox, map, cc[0], cc[1], cc[2], cc[3], cc[4], &sfull[s]);
+                }
+        prod_out:
+            // no copy may still be landing when the CTA leaves
+            for (long long i = it > NSTG ? it - NSTG : 0; i < it; ++i)
+                tc::mbar_wait(&sfull[i % NSTG], (uint32_t)((i / NSTG) & 1), kSegWaitLimit);
         }
-    prod_out:;
-    } else if (warp == 16) {
+    } else if (warp == 13) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16(128, nb);
-            const uint32_t a_sbo = (KC / 8) * 128, b_sbo = (uint32_t)(Kp / 8) * 128;
+            const uint32_t a_sbo = (kKC / 8) * 128, b_sbo = (uint32_t)(Kp / 8) * 128;
             const uint32_t bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
             long long it = 0, job = 0;
             bool ok = true;
@@ -313,42 +286,43 @@ __global__ void __launch_bounds__(544, 1) k_project_seg(Prob<float> P, SegArgs S
                 tc::fence_after_sync();
                 const uint32_t d = tmem + (uint32_t)b * ACC_COLS;
                 for (int ch = 0; ch < nchunk; ++ch, ++it) {
-                    const int s = (int)(it % NS);
-                    if (!wait(&full[s], (uint32_t)((it / NS) & 1))) { ok = false; break; }
+                    const int r = (int)(it % NR);
+                    if (!wait(&rfull[r], (uint32_t)((it / NR) & 1))) { ok = false; break; }
                     tc::fence_after_sync();
-                    const uint32_t ah = tc::smem_u32(ring + (size_t)(2 * s) * 128 * KC);
-                    const uint32_t al = ah + 128 * KC * 2;
+                    const uint32_t ah = tc::smem_u32(ring + (size_t)(2 * r) * 128 * kKC);
+                    const uint32_t al = ah + 128 * kKC * 2;
 #pragma unroll
-                    for (int jj = 0; jj < KC / 16; ++jj) {
+                    for (int jj = 0; jj < kKC / 16; ++jj) {
                         const uint32_t aoff = jj * 256;
-                        const uint32_t boff = (uint32_t)(ch * KC / 16 + jj) * 256;
+                        const uint32_t boff = (uint32_t)(ch * kKC / 16 + jj) * 256;
                         const uint64_t dah = tc::sdesc(ah + aoff, 128, a_sbo), dal = tc::sdesc(al + aoff, 128, a_sbo);
                         const uint64_t dbh = tc::sdesc(bh + boff, 128, b_sbo), dbl = tc::sdesc(bl + boff, 128, b_sbo);
                         tc::mma_bf16(d, dah, dbh, idesc, (ch > 0 || jj > 0) ? 1u : 0u);
                         tc::mma_bf16(d, dah, dbl, idesc, 1u);
                         tc::mma_bf16(d, dal, dbh, idesc, 1u);
                     }
-                    tc::mma_commit(&empty[s]);
+                    tc::mma_commit(&rempty[r]);
                 }
                 if (ok) tc::mma_commit(&tfull[b]);
             }
+            // no MMA may still be running when the tensor memory is freed
+            if (it > 0) tc::mbar_wait(&rempty[(it - 1) % NR], (uint32_t)(((it - 1) / NR) & 1), kSegWaitLimit);
         }
-    } else if (warp >= 12 && warp < 16) {
-        // ---------------- epilogue ----------------
-        const int quad = warp - 12;
+    } else {
+        // ---------------- epilogue (warps 8-11) ----------------
+        const int quad = warp - 8;
         const int r = quad * 32 + lane;
         const bool acc = S.accumulate != 0;
         const bool sh4 = (NLM & 3) == 0;
         long long job = 0;
         for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x, ++job) {
-            // destination of row r: I_lm row (when written) and moment row
+            // destinations of row r: its I_lm row (when written here) and moments
             float *ip = nullptr, *mp = nullptr;
             if (!ROWS) {
                 const long long sg = w / G;
                 const int g = (int)(w - sg * G);
-                const int4 sd = S.segs[sg];
-                long long c = 0, o2, o1;
-                if (seg_node(P, S.groupB, sd.x, sd.y, r, c, o2, o1)) {
+                long long c = 0;
+                if (seg_node(P, S, S.segs[sg], r, c)) {
                     mp = mom + (c * G + g) * 10;
                     if (P.midx[c] < 0) ip = Ip + (c * G + g) * NLM;
                 }
@@ -394,43 +368,45 @@ __global__ void __launch_bounds__(544, 1) k_project_seg(Prob<float> P, SegArgs S
 
 // -------------------------------------------------------------------------
 // a3.  512 threads, lock-step per item: the rows' S as BF16 hi / lo
-// (canonical), the MMAs over the item's ordinates in column blocks of <= 256,
-// all 16 warps drain the accumulator (4 per lane quadrant, each a quarter of
-// the 16-column blocks).  ROWS = 0: segment mode (rows at rest; eta, chi as
-// runs of the sweep layouts); ROWS = 1: moving rows (m, g) -> S0 node-major.
-// Shared memory: Yh, Yl [Np][Kq]; A hi / lo [128][Kq]; per row the S offset,
-// chi0; one mbarrier; the classes of the item's ordinates.
+// (canonical), the MMAs over the item's slots in column blocks of <= 256;
+// then chunk pairs: the 16 warps (4 per lane quadrant) stage 16 columns each
+// in shared memory and one thread TMA-stores the boxes.  Shared memory: Yh,
+// Yl [Kp][Kq]; A hi / lo [128][Kq]; 4 output tiles [box]; segment mode: the
+// chi tile [box]; per row the S offset; one mbarrier.
 // -------------------------------------------------------------------------
 template <int ROWS>
-__global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, SegArgs S, const float *__restrict__ Sp,
-                                                       float *__restrict__ eta, float *__restrict__ chi,
-                                                       float *__restrict__ S0, const uint16_t *__restrict__ gYh,
+__global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
+                                                       const float *__restrict__ Sp,
+                                                       const uint16_t *__restrict__ gYh,
                                                        const uint16_t *__restrict__ gYl, int Kq, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int Np = S.Kp;
+    if (tc::smem_u32(smem_raw) & 1023) {
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    const int Kp = S.Kp, nchunk = S.nchunk;
     uint16_t *Yh = reinterpret_cast<uint16_t *>(smem_raw);
-    uint16_t *Yl = Yh + (size_t)Np * Kq;
-    uint16_t *Ah = Yl + (size_t)Np * Kq;
+    uint16_t *Yl = Yh + (size_t)Kp * Kq;
+    uint16_t *Ah = Yl + (size_t)Kp * Kq;
     uint16_t *Al = Ah + (size_t)128 * Kq;
-    long long *rsrc = reinterpret_cast<long long *>(Al + (size_t)128 * Kq);  // [128] S row offset, -1: none
-    float *chir = reinterpret_cast<float *>(rsrc + 128);                     // [128]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(chir + 128);
+    float *tiles = reinterpret_cast<float *>(Al + (size_t)128 * Kq);  // [4][kBox]
+    float *chit = tiles + (size_t)4 * kBox;                            // [kBox], segment mode
+    long long *rsrc = reinterpret_cast<long long *>(chit + (ROWS ? 0 : kBox));  // [128] S row offset, -1: none
+    uint64_t *bar = reinterpret_cast<uint64_t *>(rsrc + 128);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
-    unsigned char *cls = reinterpret_cast<unsigned char *>(tslot + 2);  // [Np]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = P.N, G = P.G, NLM = P.NLM;
+    const int G = P.G, NLM = P.NLM;
     {
         const uint4 *sh = reinterpret_cast<const uint4 *>(gYh), *sl = reinterpret_cast<const uint4 *>(gYl);
         uint4 *dh = reinterpret_cast<uint4 *>(Yh), *dl = reinterpret_cast<uint4 *>(Yl);
-        const int n16 = Np * Kq / 8;
+        const int n16 = Kp * Kq / 8;
         for (int i = tid; i < n16; i += 512) {
             dh[i] = sh[i];
             dl[i] = sl[i];
         }
-        for (int k = tid; k < Np; k += 512) cls[k] = k < S.kcnt ? (unsigned char)P.ord[S.kbeg + k].d : 2;
     }
     if (tid == 0) {
         tc::mbar_init(bar, 1);
@@ -444,24 +420,27 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, SegArgs S,
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     const uint32_t a_sbo = (uint32_t)(Kq / 8) * 128, b_sbo = (uint32_t)(Kq / 8) * 128;
-    const long long GNc = (long long)G * P.Nc;
-    const bool s04 = (N & 3) == 0;
+    const int quad = warp & 3, part = warp >> 2;
     uint32_t phase = 0;
     bool pending = false;
 
     for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x) {
+        // the previous item's stores have finished reading the tiles
+        if (tid == 0) tc::bulk_wait_read<0>();
+        __syncthreads();
         if (tid < 128) {
             long long src = -1;
             float ch = 0.f;
             if (!ROWS) {
                 const long long sg = w / G;
                 const int g = (int)(w - sg * G);
-                const int4 sd = S.segs[sg];
-                long long c = 0, o2, o1;
-                if (seg_node(P, S.groupB, sd.x, sd.y, tid, c, o2, o1) && P.midx[c] < 0) {
-                    src = (c * G + g) * NLM;
+                long long c = 0;
+                if (seg_node(P, S, S.segs[sg], tid, c)) {
                     ch = P.chi0[c * G + g];
+                    if (P.midx[c] < 0) src = (c * G + g) * NLM;
                 }
+#pragma unroll 8
+                for (int k = 0; k < kKC; ++k) chit[k * 128 + tid] = ch;
             } else {
                 const long long row = w * 128 + tid;
                 if (row < S.nrows) {
@@ -470,7 +449,6 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, SegArgs S,
                 }
             }
             rsrc[tid] = src;
-            chir[tid] = ch;
         }
         __syncthreads();
         // A: the rows' S as BF16 hi / lo, one core matrix per warp step
@@ -497,8 +475,8 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, SegArgs S,
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al);
-            for (int h = 0; h * 256 < Np; ++h) {
-                const int nh = Np - 256 * h < 256 ? Np - 256 * h : 256;
+            for (int h = 0; h * 256 < Kp; ++h) {
+                const int nh = Kp - 256 * h < 256 ? Kp - 256 * h : 256;
                 const uint32_t idesc = tc::idesc_bf16(128, nh);
                 const uint32_t yoff = (uint32_t)(256 / 8) * b_sbo * h;
                 const uint32_t yh = tc::smem_u32(Yh) + yoff, yl = tc::smem_u32(Yl) + yoff;
@@ -522,48 +500,47 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, SegArgs S,
         phase ^= 1;
         tc::fence_after_sync();
         {
-            const int quad = warp & 3, part = warp >> 2;
             const int r = quad * 32 + lane;
-            const bool live = rsrc[r] >= 0;
-            const int nblk = Np / 16;
-            if (!ROWS) {
-                const long long sg = w / G;
-                const int g = (int)(w - sg * G);
-                const int4 sd = S.segs[sg];
-                long long c = 0, off2 = 0, off1 = 0;
-                seg_node(P, S.groupB, sd.x, sd.y, r, c, off2, off1);
-                const float ch = chir[r];
-                const long long gNc = (long long)g * P.Nc;
-                for (int blk = part; blk < nblk; blk += 4) {
-                    const int c0 = blk * 16;
+            float chr = 0.f;
+            if (!ROWS) chr = chit[r];
+            int cc[5];
+            for (int pc = 0; pc * 2 < nchunk; ++pc) {
+                float *T0 = tiles + (size_t)((pc & 1) * 2) * kBox;
+                // the stores of pair pc - 2 (same tiles) have read them
+                if (tid == 0) tc::bulk_wait_read<1>();
+                __syncthreads();
+                const int chn = 2 * pc + (part >> 1);
+                if (chn < nchunk) {
+                    const int c0 = chn * kKC + (part & 1) * 16;
                     float v[16];
                     tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-                    if (!live) continue;
+                    float *T = T0 + (size_t)(part >> 1) * kBox;
+                    if (!ROWS) {
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int kk = c0 + jj;
-                        if (kk < S.kcnt) {
-                            const long long a = (long long)(S.kbeg + kk) * GNc + gNc + (cls[kk] == 1 ? off1 : off2);
-                            eta[a] = ch * v[jj];
-                            chi[a] = ch;
-                        }
-                    }
-                }
-            } else {
-                float *s0row = S0 + (w * 128 + r) * (long long)N;
-                for (int blk = part; blk < nblk; blk += 4) {
-                    const int c0 = blk * 16;
-                    float v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-                    if (!live) continue;
-                    if (s04 && c0 + 16 <= N) {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) put4(s0row + c0 + 4 * q, &v[4 * q], false);
+                        for (int j = 0; j < 16; ++j) T[((part & 1) * 16 + j) * 128 + r] = chr * v[j];
                     } else {
 #pragma unroll
-                        for (int jj = 0; jj < 16; ++jj)
-                            if (c0 + jj < N) s0row[c0 + jj] = v[jj];
+                        for (int q = 0; q < 4; ++q)
+                            *swz4(T, r, (part & 1) * 4 + q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                     }
+                }
+                tc::fence_proxy_async();
+                __syncthreads();
+                if (tid == 0) {
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int cn = 2 * pc + hh;
+                        if (cn >= nchunk) break;
+                        const float *T = T0 + (size_t)hh * kBox;
+                        box_coords(S, ROWS, w, G, cn, cc);
+                        const int mi = S.chunk[cn].x;
+                        if (ROWS) {
+                            tc::tma_store_2d(&maps.m[0], cc[0], cc[1], T);
+                        } else {
+                            tc::tma_store_5d(&maps.m[mi], cc[0], cc[1], cc[2], cc[3], cc[4], T);
+                            tc::tma_store_5d(&maps.m[2 + mi], cc[0], cc[1], cc[2], cc[3], cc[4], chit);
+                        }
+                    }
+                    tc::bulk_commit();
                 }
             }
         }
@@ -577,6 +554,7 @@ drain:
         if (pending) tc::mbar_wait(bar, phase, kSegWaitLimit);
     }
 done:
+    if (threadIdx.x == 0) tc::bulk_wait_all();
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
@@ -587,45 +565,117 @@ done:
 // -------------------------------------------------------------------------
 static constexpr size_t kSegSmemLimit = 227 * 1024;
 
-static size_t project_seg_smem(int nb, int Kp, int ns, int rows)
+static size_t project_seg_smem(int nb, int Kp, int nstg, int nr)
 {
-    const size_t stg = rows ? (size_t)128 * kSR : (size_t)kSegKC * kSP;
-    return (size_t)2 * nb * Kp * 2 + (size_t)ns * 2 * 128 * kSegKC * 2 + 3 * stg * 4 + (size_t)(2 * ns + 4) * 8 +
-           16 + (size_t)Kp;
+    return (size_t)4 * nb * Kp + (size_t)(nstg + nr) * kBox * 4 + (size_t)(2 * nstg + 2 * nr + 4) * 8 + 8;
 }
-static size_t sh2lab_seg_smem(int Np, int Kq)
+static size_t sh2lab_seg_smem(int Kp, int Kq, int rows)
 {
-    return (size_t)2 * Np * Kq * 2 + (size_t)2 * 128 * Kq * 2 + 128 * 8 + 128 * 4 + 8 + 8 + (size_t)Np;
+    return (size_t)4 * Kp * Kq + (size_t)4 * 128 * Kq + (size_t)(rows ? 4 : 5) * kBox * 4 + 128 * 8 + 8 + 8;
 }
 
-static int pick_ns(int nb, int Kp, int rows)
+// staging / ring depths that fit: 0 when nothing does
+static int pick_depths(int nb, int Kp, int &nstg, int &nr)
 {
-    for (int ns = 4; ns >= 2; --ns)
-        if (project_seg_smem(nb, Kp, ns, rows) <= kSegSmemLimit) return ns;
+    const int opts[4][2] = {{4, 4}, {4, 3}, {4, 2}, {3, 2}};
+    for (auto &o : opts)
+        if (project_seg_smem(nb, Kp, o[0], o[1]) <= kSegSmemLimit) {
+            nstg = o[0];
+            nr = o[1];
+            return 1;
+        }
     return 0;
 }
 
-// The rows-mode contraction of a1 uses the first nlm16 rows of the full
-// projection matrix (the I_lm columns; moments are taken in the laboratory).
 static int nlm16(const shd_ctx *c) { return 16 * ((c->NLM + 15) / 16); }
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
 
 bool seg_usable(const shd_ctx *c)
 {
-    if (c->precision != SHD_MIXED || c->NB > 128 || !c->d_tc_Bh || !c->d_tc_Yh) return false;
-    if (c->tc_Np > 512) return false;
+    if (c->precision != SHD_MIXED || !c->seg_ready || c->NB > 128 || !c->d_tc_Bh || !c->d_tc_Yh || !encoder())
+        return false;
+    // 16-byte strides of the tensor maps
+    if (c->nx % 4 || c->ny % 4 || c->N % 4) return false;
+    if (c->tc_Kp > 512 || c->tc_Kp / kKC > 16) return false;
+    int a, b;
     for (int grp = 0; grp < 2; ++grp) {
-        const int cnt = grp ? c->N - c->nA : c->nA;
-        if (cnt == 0) continue;
+        if (c->tcs_nchunk[grp] == 0) continue;
         if (!c->d_seg[grp] || !c->d_tcs_Bh[grp] || !c->d_tcs_Yh[grp]) return false;
-        if (c->tcs_Np[grp] > 512) return false;
-        if (!pick_ns(c->NB, c->tcs_Kp[grp], 0)) return false;
-        if (sh2lab_seg_smem(c->tcs_Np[grp], c->tc_Kq) > kSegSmemLimit) return false;
+        if (c->tcs_Kp[grp] > 512 || c->tcs_nchunk[grp] > 16) return false;
+        if (!pick_depths(c->NB, c->tcs_Kp[grp], a, b)) return false;
+        if (sh2lab_seg_smem(c->tcs_Kp[grp], c->tc_Kq, 0) > kSegSmemLimit) return false;
     }
     if (c->nmoving > 0) {
-        if (!pick_ns(nlm16(c), c->tc_Kp, 1)) return false;
-        if (sh2lab_seg_smem(c->tc_Np, c->tc_Kq) > kSegSmemLimit) return false;
+        if (!pick_depths(nlm16(c), c->tc_Kp, a, b)) return false;
+        if (sh2lab_seg_smem(c->tc_Kp, c->tc_Kq, 1) > kSegSmemLimit) return false;
     }
     return true;
+}
+
+// 5-D map over one class of a discrete-ordinate array: dims (fastest first)
+// d0, d1, d2 of the class's sweep layout, then g, then the class's ordinates.
+static cudaError_t class_map(const shd_ctx *c, CUtensorMap *m, const float *base, int cls, int bw)
+{
+    const cuuint64_t nx = c->nx, ny = c->ny, nz = c->nz, Nc = (cuuint64_t)c->Nc;
+    const int kb = cls == 2 ? 0 : (cls == 1 ? c->nZ : c->nA);
+    const int kn = cls == 2 ? c->nZ : (cls == 1 ? c->nA - c->nZ : c->N - c->nA);
+    cuuint64_t dims[5], str[4];
+    cuuint32_t box[5], es[5] = {1, 1, 1, 1, 1};
+    if (cls == 2) {  // (x, y, z)
+        dims[0] = nx; dims[1] = ny; dims[2] = nz;
+        str[0] = nx * 4; str[1] = nx * ny * 4;
+        box[0] = bw; box[1] = 128 / bw; box[2] = 1;
+    } else if (cls == 1) {  // (x, z, y)
+        dims[0] = nx; dims[1] = nz; dims[2] = ny;
+        str[0] = nx * 4; str[1] = nx * nz * 4;
+        box[0] = bw; box[1] = 1; box[2] = 128 / bw;
+    } else {  // (y, z, x)
+        dims[0] = ny; dims[1] = nz; dims[2] = nx;
+        str[0] = ny * 4; str[1] = ny * nz * 4;
+        box[0] = bw; box[1] = 128 / bw; box[2] = 1;
+    }
+    dims[3] = (cuuint64_t)c->G;
+    dims[4] = (cuuint64_t)kn;
+    str[2] = Nc * 4;
+    str[3] = (cuuint64_t)c->G * Nc * 4;
+    box[3] = 1;
+    box[4] = kKC;
+    void *gaddr = const_cast<float *>(base + (size_t)kb * c->G * Nc);
+    CUresult r = encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, gaddr, dims, str, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// 2-D map over node-major rows [R][N], box 32 ordinates x 128 rows, 128-byte swizzle.
+static cudaError_t rows_map(const shd_ctx *c, CUtensorMap *m, const float *base)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)c->N, (cuuint64_t)(c->nmoving * c->G)};
+    cuuint64_t str[1] = {(cuuint64_t)c->N * 4};
+    cuuint32_t box[2] = {kKC, 128}, es[2] = {1, 1};
+    CUresult r = encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, str, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 static int num_sms_seg(const shd_ctx *ctx)
@@ -641,8 +691,10 @@ static SegArgs seg_args(const shd_ctx *c, int grp)
     a.segs = (const int4 *)c->d_seg[grp];
     a.nitem = c->nseg[grp] * c->G;
     a.groupB = grp;
-    a.kbeg = grp ? c->nA : 0;
-    a.kcnt = grp ? c->N - c->nA : c->nA;
+    a.bw = c->seg_bw[grp];
+    a.nchunk = c->tcs_nchunk[grp];
+    a.Kp = c->tcs_Kp[grp];
+    for (int i = 0; i < a.nchunk; ++i) a.chunk[i] = make_int2(c->tcs_chunk[grp][i][0], c->tcs_chunk[grp][i][1]);
     return a;
 }
 
@@ -651,23 +703,39 @@ static SegArgs rows_args(const shd_ctx *c)
     SegArgs a{};
     a.nrows = c->nmoving * c->G;
     a.nitem = (a.nrows + 127) / 128;
-    a.kbeg = 0;
-    a.kcnt = c->N;
+    a.Kp = c->tc_Kp;
+    a.nchunk = c->tc_Kp / kKC;
+    for (int i = 0; i < a.nchunk; ++i) a.chunk[i] = make_int2(0, i * kKC);
     return a;
 }
 
-template <int ROWS>
-static cudaError_t run_project_seg(const shd_ctx *ctx, const Prob<float> &P, SegArgs a, const float *A, float *Ip,
-                                   float *mom, const void *Bh, const void *Bl, cudaStream_t st)
+// the map of the classes of group grp: group A {z, y}, group B {x}
+static cudaError_t group_maps(const shd_ctx *c, int grp, const float *base, CUtensorMap *m0)
 {
-    const int ns = pick_ns(a.nb, a.Kp, ROWS);
-    const size_t sm = project_seg_smem(a.nb, a.Kp, ns, ROWS);
-    auto kern = ns == 4 ? k_project_seg<4, ROWS> : (ns == 3 ? k_project_seg<3, ROWS> : k_project_seg<2, ROWS>);
+    cudaError_t e;
+    if (grp == 0) {
+        if (c->nZ > 0 && (e = class_map(c, &m0[0], base, 2, c->seg_bw[0])) != cudaSuccess) return e;
+        if (c->nA > c->nZ && (e = class_map(c, &m0[1], base, 1, c->seg_bw[0])) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    return class_map(c, &m0[0], base, 0, c->seg_bw[1]);
+}
+
+template <int ROWS>
+static cudaError_t run_project_seg(const shd_ctx *ctx, const Prob<float> &P, const SegMaps &maps, const SegArgs &a,
+                                   float *Ip, float *mom, const void *Bh, const void *Bl, cudaStream_t st)
+{
+    int nstg = 0, nr = 0;
+    if (!pick_depths(a.nb, a.Kp, nstg, nr)) return cudaErrorInvalidConfiguration;
+    const size_t sm = project_seg_smem(a.nb, a.Kp, nstg, nr);
+    auto kern = nr == 4 ? k_project_seg<4, 4, ROWS>
+                        : (nr == 3 ? k_project_seg<4, 3, ROWS>
+                                   : (nstg == 4 ? k_project_seg<4, 2, ROWS> : k_project_seg<3, 2, ROWS>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int grid = num_sms_seg(ctx);
     if (a.nitem < grid) grid = (int)a.nitem;
-    kern<<<grid, 544, sm, st>>>(P, a, A, Ip, mom, (const uint16_t *)Bh, (const uint16_t *)Bl, ctx->d_tc_err);
+    kern<<<grid, 448, sm, st>>>(P, maps, a, Ip, mom, (const uint16_t *)Bh, (const uint16_t *)Bl, ctx->d_tc_err);
     return cudaGetLastError();
 }
 
@@ -680,59 +748,63 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
     bool first = true;
     cudaError_t e;
     for (int grp = 0; grp < 2; ++grp) {
+        if (ctx->tcs_nchunk[grp] == 0 || ctx->nseg[grp] == 0) continue;
         SegArgs a = seg_args(ctx, grp);
-        if (a.kcnt == 0 || a.nitem == 0) continue;
-        a.Kp = ctx->tcs_Kp[grp];
         a.nb = ctx->NB;
         a.accumulate = first ? 0 : 1;
         first = false;
-        if ((e = run_project_seg<0>(ctx, P, a, I, Ip, mom, ctx->d_tcs_Bh[grp], ctx->d_tcs_Bl[grp], st)) != cudaSuccess)
+        SegMaps maps{};
+        if ((e = group_maps(ctx, grp, I, maps.m)) != cudaSuccess) return e;
+        if ((e = run_project_seg<0>(ctx, P, maps, a, Ip, mom, ctx->d_tcs_Bh[grp], ctx->d_tcs_Bl[grp], st)) !=
+            cudaSuccess)
             return e;
     }
     if (ctx->nmoving > 0) {
         SegArgs a = rows_args(ctx);
-        a.Kp = ctx->tc_Kp;
         a.nb = nlm16(ctx);
-        if ((e = run_project_seg<1>(ctx, P, a, I0n, Ip, mom, ctx->d_tc_Bh, ctx->d_tc_Bl, st)) != cudaSuccess)
+        SegMaps maps{};
+        if ((e = rows_map(ctx, &maps.m[0], I0n)) != cudaSuccess) return e;
+        if ((e = run_project_seg<1>(ctx, P, maps, a, Ip, mom, ctx->d_tc_Bh, ctx->d_tc_Bl, st)) != cudaSuccess)
             return e;
     }
     return cudaSuccess;
 }
 
 template <int ROWS>
-static cudaError_t run_sh2lab_seg(const shd_ctx *ctx, const Prob<float> &P, SegArgs a, const float *Sp, float *eta,
-                                  float *chi, float *S0n, const void *Yh, const void *Yl, cudaStream_t st)
+static cudaError_t run_sh2lab_seg(const shd_ctx *ctx, const Prob<float> &P, const SegMaps &maps, const SegArgs &a,
+                                  const float *Sp, const void *Yh, const void *Yl, cudaStream_t st)
 {
-    const size_t sm = sh2lab_seg_smem(a.Kp, ctx->tc_Kq);
+    const size_t sm = sh2lab_seg_smem(a.Kp, ctx->tc_Kq, ROWS);
     cudaError_t e = cudaFuncSetAttribute(k_sh2lab_seg<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int grid = num_sms_seg(ctx);
     if (a.nitem < grid) grid = (int)a.nitem;
-    k_sh2lab_seg<ROWS><<<grid, 512, sm, st>>>(P, a, Sp, eta, chi, S0n, (const uint16_t *)Yh, (const uint16_t *)Yl,
-                                              ctx->tc_Kq, ctx->d_tc_err);
+    k_sh2lab_seg<ROWS><<<grid, 512, sm, st>>>(P, maps, a, Sp, (const uint16_t *)Yh, (const uint16_t *)Yl, ctx->tc_Kq,
+                                              ctx->d_tc_err);
     return cudaGetLastError();
 }
 
-// a3: eta, chi of nodes at rest (groups A, B) and the comoving S0 of moving
-// nodes node-major in S0n.
+// a3: eta, chi in the sweep layout (moving nodes get overwritten by their
+// remap afterwards) and the comoving S0 of moving nodes node-major in S0n.
 cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *S0n,
                               cudaStream_t st)
 {
     Prob<float> P = make_prob<float>(ctx);
     cudaError_t e;
     for (int grp = 0; grp < 2; ++grp) {
+        if (ctx->tcs_nchunk[grp] == 0 || ctx->nseg[grp] == 0) continue;
         SegArgs a = seg_args(ctx, grp);
-        if (a.kcnt == 0 || a.nitem == 0) continue;
-        a.Kp = ctx->tcs_Np[grp];
-        if ((e = run_sh2lab_seg<0>(ctx, P, a, Sp, eta, chi, S0n, ctx->d_tcs_Yh[grp], ctx->d_tcs_Yl[grp], st)) !=
-            cudaSuccess)
+        SegMaps maps{};
+        if ((e = group_maps(ctx, grp, eta, &maps.m[0])) != cudaSuccess) return e;
+        if ((e = group_maps(ctx, grp, chi, &maps.m[2])) != cudaSuccess) return e;
+        if ((e = run_sh2lab_seg<0>(ctx, P, maps, a, Sp, ctx->d_tcs_Yh[grp], ctx->d_tcs_Yl[grp], st)) != cudaSuccess)
             return e;
     }
     if (ctx->nmoving > 0) {
         SegArgs a = rows_args(ctx);
-        a.Kp = ctx->tc_Np;
-        if ((e = run_sh2lab_seg<1>(ctx, P, a, Sp, eta, chi, S0n, ctx->d_tc_Yh, ctx->d_tc_Yl, st)) != cudaSuccess)
-            return e;
+        SegMaps maps{};
+        if ((e = rows_map(ctx, &maps.m[0], S0n)) != cudaSuccess) return e;
+        if ((e = run_sh2lab_seg<1>(ctx, P, maps, a, Sp, ctx->d_tc_Yh, ctx->d_tc_Yl, st)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
