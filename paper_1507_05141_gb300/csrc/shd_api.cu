@@ -325,6 +325,8 @@ int upload_seg_operands(shd_ctx *c, const std::vector<double> &Bp)
                 if (nch == 16) return SHD_OK;  // more than 512 slots: the brick kernels take over
                 c->tcs_chunk[grp][nch][0] = cls[q][0];
                 c->tcs_chunk[grp][nch][1] = k0;
+                c->tcs_chunk[grp][nch][2] = cls[q][1];
+                c->tcs_chunk[grp][nch][3] = cls[q][2];
                 ++nch;
                 for (int i = 0; i < 32; ++i) slot.push_back(k0 + i < cls[q][2] ? cls[q][1] + k0 + i : -1);
             }

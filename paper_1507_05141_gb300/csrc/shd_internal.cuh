@@ -166,14 +166,15 @@ struct shd_ctx {
     // boxes of (y, z) at one x.  Segments {plane, a0, b0, 0}; the group's
     // ordinates in slots (each class padded to a multiple of 32) with the
     // operands over slots (BF16 hi / lo, canonical K-major) and per chunk of
-    // 32 slots {class map index in the group, first ordinate in the class}
+    // 32 slots {class map index in the group, first ordinate of the chunk in
+    // its class, internal index of the class's first ordinate, class size}
     void *d_seg[2] = {nullptr, nullptr};
     long long nseg[2] = {0, 0};
     int seg_bw[2] = {0, 0};
     void *d_tcs_Bh[2] = {nullptr, nullptr}, *d_tcs_Bl[2] = {nullptr, nullptr};  // [NB][tcs_Kp]
     void *d_tcs_Yh[2] = {nullptr, nullptr}, *d_tcs_Yl[2] = {nullptr, nullptr};  // [tcs_Kp][tc_Kq]
     int tcs_Kp[2] = {0, 0}, tcs_nchunk[2] = {0, 0};
-    int tcs_chunk[2][16][2] = {};
+    int tcs_chunk[2][16][4] = {};
     bool seg_ready = false;
     double *d_stage = nullptr;    // staging buffer for host <-> device copies (FP64)
     size_t stage_elems = 0;
@@ -439,10 +440,12 @@ template <class T>
 cudaError_t launch_project_scratch(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *scratch, cudaStream_t st);
 bool tc_usable(const shd_ctx *ctx);
 bool seg_usable(const shd_ctx *ctx);
-cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, float *mom, const float *I0n,
+cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, float *mom, float *nm0, float *nm1,
                                cudaStream_t st);
-cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *S0n,
-                              cudaStream_t st);
+cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,
+                              float *nm2, cudaStream_t st);
+cudaError_t launch_remap_to_comoving_f(const shd_ctx *ctx, const float *nm0, float *nm1, cudaStream_t st);
+cudaError_t launch_remap_to_lab_f(const shd_ctx *ctx, const float *nm0, float *nm1, float *nm2, cudaStream_t st);
 size_t project_tc_smem_bytes(const shd_ctx *ctx);
 size_t sh2lab_tc_smem_bytes(const shd_ctx *ctx);
 cudaError_t launch_project_tc(const shd_ctx *ctx, const float *I, float *Ip, float *mom, const float *I0n,

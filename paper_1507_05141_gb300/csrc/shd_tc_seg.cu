@@ -92,7 +92,8 @@ struct SegArgs {
     int Kp;             // slots = 32 nchunk
     int nb;             // a1: output columns (rows of Bp) of the MMA
     int accumulate;     // a1: add to I_lm / moments instead of storing
-    int2 chunk[16];     // {map index, first ordinate of the chunk within its class}
+    int4 chunk[16];     // {map index, first ordinate of the chunk within its class,
+                        //  internal index of the class's first ordinate, ordinates in the class}
 };
 
 // Node of row r of a segment tile; false outside the grid.
@@ -138,12 +139,13 @@ __device__ inline void box_coords(const SegArgs &S, int ROWS, long long w, int G
 // a1.  Warps 0-7 converters, 8-11 epilogue (tensor-memory lane quadrants
 // 0-3), 12 TMA producer, 13 MMA issuer.  Shared memory: Bh, Bl [nb][Kp]
 // resident; FP32 staging [NSTG][box]; BF16 ring [NR][hi, lo][128][32]
-// (canonical); the barriers.
+// (canonical); the barriers.  Segment mode: the converters also copy the
+// laboratory I of moving rows to nmo, node-major [m][g][k], for the remap.
 // -------------------------------------------------------------------------
 template <int NSTG, int NR, int ROWS>
 __global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
                                                         float *__restrict__ Ip, float *__restrict__ mom,
-                                                        const uint16_t *__restrict__ gBh,
+                                                        float *__restrict__ nmo, const uint16_t *__restrict__ gBh,
                                                         const uint16_t *__restrict__ gBl, int *err)
 {
     constexpr uint32_t ACC_COLS = 128;
@@ -213,7 +215,19 @@ __global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __g
     if (warp < 8) {
         // ---------------- converters ----------------
         long long it = 0;
-        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x)
+        const int crow = (warp & 3) * 32 + lane;  // the row this thread converts in every chunk
+        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x) {
+            // node-major destination of the row when its node moves
+            float *nrow = nullptr;
+            if (!ROWS && nmo) {
+                const long long sg = w / G;
+                const int g = (int)(w - sg * G);
+                long long c = 0;
+                if (seg_node(P, S, S.segs[sg], crow, c)) {
+                    const int m = P.midx[c];
+                    if (m >= 0) nrow = nmo + ((long long)m * G + g) * P.N;
+                }
+            }
             for (int ch = 0; ch < nchunk; ++ch, ++it) {
                 const int s = (int)(it % NSTG), r = (int)(it % NR);
                 if (!wait(&sfull[s], (uint32_t)((it / NSTG) & 1))) goto conv_out;
@@ -245,11 +259,25 @@ __global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __g
                     const int o = tc::canon_off(row, kb * 8, kKC);
                     *reinterpret_cast<uint4 *>(&Ah[o]) = h;
                     *reinterpret_cast<uint4 *>(&Al[o]) = l;
+                    if (!ROWS && nrow) {
+                        const int4 ci = S.chunk[ch];
+                        const int kl = ci.y + kb * 8;  // within the class
+                        float *dst = nrow + ci.z + kl;
+                        if (kl + 8 <= ci.w && ((ci.z + kl) & 3) == 0) {
+                            reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+                            reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                if (kl + i < ci.w) dst[i] = v[i];
+                        }
+                    }
                 }
                 tc::fence_proxy_async();
                 tc::mbar_arrive(&sempty[s]);
                 tc::mbar_arrive(&rfull[r]);
             }
+        }
     conv_out:;
     } else if (warp == 12) {
         // ---------------- TMA producer ----------------
@@ -368,15 +396,19 @@ __global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __g
 
 // -------------------------------------------------------------------------
 // a3.  512 threads, lock-step per item: the rows' S as BF16 hi / lo
-// (canonical), the MMAs over the item's slots in column blocks of <= 256;
-// then chunk pairs: the 16 warps (4 per lane quadrant) stage 16 columns each
-// in shared memory and one thread TMA-stores the boxes.  Shared memory: Yh,
-// Yl [Kp][Kq]; A hi / lo [128][Kq]; 4 output tiles [box]; segment mode: the
-// chi tile [box]; per row the S offset; one mbarrier.
+// (canonical), the MMAs over the item's slots in column blocks of <= 256,
+// then the output chunk by chunk through shared-memory tiles and TMA stores.
+// Segment mode: per chunk an eta and a chi tile [32][128]; rows at rest take
+// eta = chi0 D, chi = chi0, moving rows the laboratory eta, chi from their
+// remap (etan, chin node-major).  Rows mode: S0 of moving rows (m, g), two
+// chunks per step.  Shared memory: Yh, Yl [Kp][Kq]; A hi / lo [128][Kq]; 4
+// output tiles [box]; per row the S offset, chi0 and moving index; one
+// mbarrier.
 // -------------------------------------------------------------------------
 template <int ROWS>
 __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
-                                                       const float *__restrict__ Sp,
+                                                       const float *__restrict__ Sp, const float *__restrict__ etan,
+                                                       const float *__restrict__ chin,
                                                        const uint16_t *__restrict__ gYh,
                                                        const uint16_t *__restrict__ gYl, int Kq, int *err)
 {
@@ -391,14 +423,15 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
     uint16_t *Ah = Yl + (size_t)Kp * Kq;
     uint16_t *Al = Ah + (size_t)128 * Kq;
     float *tiles = reinterpret_cast<float *>(Al + (size_t)128 * Kq);  // [4][kBox]
-    float *chit = tiles + (size_t)4 * kBox;                            // [kBox], segment mode
-    long long *rsrc = reinterpret_cast<long long *>(chit + (ROWS ? 0 : kBox));  // [128] S row offset, -1: none
-    uint64_t *bar = reinterpret_cast<uint64_t *>(rsrc + 128);
+    long long *rsrc = reinterpret_cast<long long *>(tiles + (size_t)4 * kBox);  // [128] S row offset, -1: none
+    float *chir = reinterpret_cast<float *>(rsrc + 128);                       // [128] chi0 of the row
+    int *rowm = reinterpret_cast<int *>(chir + 128);                           // [128] moving index, -1
+    uint64_t *bar = reinterpret_cast<uint64_t *>(rowm + 128);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int G = P.G, NLM = P.NLM;
+    const int G = P.G, NLM = P.NLM, N = P.N;
     {
         const uint4 *sh = reinterpret_cast<const uint4 *>(gYh), *sl = reinterpret_cast<const uint4 *>(gYl);
         uint4 *dh = reinterpret_cast<uint4 *>(Yh), *dl = reinterpret_cast<uint4 *>(Yl);
@@ -425,30 +458,32 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
     bool pending = false;
 
     for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x) {
+        const long long sg = w / G;
+        const int g = (int)(w - sg * G);
         // the previous item's stores have finished reading the tiles
         if (tid == 0) tc::bulk_wait_read<0>();
         __syncthreads();
         if (tid < 128) {
             long long src = -1;
             float ch = 0.f;
+            int m = -1;
             if (!ROWS) {
-                const long long sg = w / G;
-                const int g = (int)(w - sg * G);
                 long long c = 0;
                 if (seg_node(P, S, S.segs[sg], tid, c)) {
                     ch = P.chi0[c * G + g];
-                    if (P.midx[c] < 0) src = (c * G + g) * NLM;
+                    m = P.midx[c];
+                    if (m < 0) src = (c * G + g) * NLM;
                 }
-#pragma unroll 8
-                for (int k = 0; k < kKC; ++k) chit[k * 128 + tid] = ch;
             } else {
                 const long long row = w * 128 + tid;
                 if (row < S.nrows) {
-                    const long long m = row / G;
-                    src = (P.moving[m] * G + (row - m * G)) * NLM;
+                    const long long mm = row / G;
+                    src = (P.moving[mm] * G + (row - mm * G)) * NLM;
                 }
             }
             rsrc[tid] = src;
+            chir[tid] = ch;
+            rowm[tid] = m;
         }
         __syncthreads();
         // A: the rows' S as BF16 hi / lo, one core matrix per warp step
@@ -501,46 +536,77 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
         tc::fence_after_sync();
         {
             const int r = quad * 32 + lane;
-            float chr = 0.f;
-            if (!ROWS) chr = chit[r];
+            const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
             int cc[5];
-            for (int pc = 0; pc * 2 < nchunk; ++pc) {
-                float *T0 = tiles + (size_t)((pc & 1) * 2) * kBox;
-                // the stores of pair pc - 2 (same tiles) have read them
-                if (tid == 0) tc::bulk_wait_read<1>();
-                __syncthreads();
-                const int chn = 2 * pc + (part >> 1);
-                if (chn < nchunk) {
-                    const int c0 = chn * kKC + (part & 1) * 16;
-                    float v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-                    float *T = T0 + (size_t)(part >> 1) * kBox;
-                    if (!ROWS) {
+            if constexpr (!ROWS) {
+                const float chr = chir[r];
+                const int m = rowm[r];
+                const long long nbase = m >= 0 ? ((long long)m * G + g) * N : 0;
+                const int half = part & 1;  // columns 16 half .. 16 half + 15 of the chunk
+                for (int cn = 0; cn < nchunk; ++cn) {
+                    float *Te = tiles + (size_t)((cn & 1) * 2) * kBox, *Tc = Te + kBox;
+                    // the stores of chunk cn - 2 (same tiles) have read them
+                    if (tid == 0) tc::bulk_wait_read<1>();
+                    __syncthreads();
+                    const int4 ci = S.chunk[cn];
+                    const int kl0 = ci.y + 16 * half;  // first ordinate (within the class) of these columns
+                    float *T = part < 2 ? Te : Tc;
+                    float *col = T + (size_t)(16 * half) * 128 + r;
+                    if (part < 2) {
+                        float v[16];
+                        tc::tmem_ld16(trow + (uint32_t)(cn * kKC + 16 * half), v);
+                        if (m < 0) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) T[((part & 1) * 16 + j) * 128 + r] = chr * v[j];
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            *swz4(T, r, (part & 1) * 4 + q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                    }
-                }
-                tc::fence_proxy_async();
-                __syncthreads();
-                if (tid == 0) {
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const int cn = 2 * pc + hh;
-                        if (cn >= nchunk) break;
-                        const float *T = T0 + (size_t)hh * kBox;
-                        box_coords(S, ROWS, w, G, cn, cc);
-                        const int mi = S.chunk[cn].x;
-                        if (ROWS) {
-                            tc::tma_store_2d(&maps.m[0], cc[0], cc[1], T);
+                            for (int j = 0; j < 16; ++j) col[j * 128] = chr * v[j];
                         } else {
-                            tc::tma_store_5d(&maps.m[mi], cc[0], cc[1], cc[2], cc[3], cc[4], T);
-                            tc::tma_store_5d(&maps.m[2 + mi], cc[0], cc[1], cc[2], cc[3], cc[4], chit);
+                            const float *src = etan + nbase + ci.z + kl0;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) col[j * 128] = kl0 + j < ci.w ? src[j] : 0.f;
+                        }
+                    } else {
+                        if (m < 0) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) col[j * 128] = chr;
+                        } else {
+                            const float *src = chin + nbase + ci.z + kl0;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) col[j * 128] = kl0 + j < ci.w ? src[j] : 0.f;
                         }
                     }
-                    tc::bulk_commit();
+                    tc::fence_proxy_async();
+                    __syncthreads();
+                    if (tid == 0) {
+                        box_coords(S, 0, w, G, cn, cc);
+                        tc::tma_store_5d(&maps.m[ci.x], cc[0], cc[1], cc[2], cc[3], cc[4], Te);
+                        tc::tma_store_5d(&maps.m[2 + ci.x], cc[0], cc[1], cc[2], cc[3], cc[4], Tc);
+                        tc::bulk_commit();
+                    }
+                }
+            } else {
+                for (int pc = 0; pc * 2 < nchunk; ++pc) {
+                    float *T0 = tiles + (size_t)((pc & 1) * 2) * kBox;
+                    // the stores of pair pc - 2 (same tiles) have read them
+                    if (tid == 0) tc::bulk_wait_read<1>();
+                    __syncthreads();
+                    const int chn = 2 * pc + (part >> 1);
+                    if (chn < nchunk) {
+                        float v[16];
+                        tc::tmem_ld16(trow + (uint32_t)(chn * kKC + (part & 1) * 16), v);
+                        float *T = T0 + (size_t)(part >> 1) * kBox;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            *swz4(T, r, (part & 1) * 4 + q) =
+                                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
+                    tc::fence_proxy_async();
+                    __syncthreads();
+                    if (tid == 0) {
+                        for (int hh = 0; hh < 2 && 2 * pc + hh < nchunk; ++hh) {
+                            box_coords(S, 1, w, G, 2 * pc + hh, cc);
+                            tc::tma_store_2d(&maps.m[0], cc[0], cc[1], T0 + (size_t)hh * kBox);
+                        }
+                        tc::bulk_commit();
+                    }
                 }
             }
         }
@@ -569,9 +635,9 @@ static size_t project_seg_smem(int nb, int Kp, int nstg, int nr)
 {
     return (size_t)4 * nb * Kp + (size_t)(nstg + nr) * kBox * 4 + (size_t)(2 * nstg + 2 * nr + 4) * 8 + 8;
 }
-static size_t sh2lab_seg_smem(int Kp, int Kq, int rows)
+static size_t sh2lab_seg_smem(int Kp, int Kq)
 {
-    return (size_t)4 * Kp * Kq + (size_t)4 * 128 * Kq + (size_t)(rows ? 4 : 5) * kBox * 4 + 128 * 8 + 8 + 8;
+    return (size_t)4 * Kp * Kq + (size_t)4 * 128 * Kq + (size_t)4 * kBox * 4 + 128 * (8 + 4 + 4) + 8 + 8;
 }
 
 // staging / ring depths that fit: 0 when nothing does
@@ -622,11 +688,11 @@ bool seg_usable(const shd_ctx *c)
         if (!c->d_seg[grp] || !c->d_tcs_Bh[grp] || !c->d_tcs_Yh[grp]) return false;
         if (c->tcs_Kp[grp] > 512 || c->tcs_nchunk[grp] > 16) return false;
         if (!pick_depths(c->NB, c->tcs_Kp[grp], a, b)) return false;
-        if (sh2lab_seg_smem(c->tcs_Kp[grp], c->tc_Kq, 0) > kSegSmemLimit) return false;
+        if (sh2lab_seg_smem(c->tcs_Kp[grp], c->tc_Kq) > kSegSmemLimit) return false;
     }
     if (c->nmoving > 0) {
         if (!pick_depths(nlm16(c), c->tc_Kp, a, b)) return false;
-        if (sh2lab_seg_smem(c->tc_Kp, c->tc_Kq, 1) > kSegSmemLimit) return false;
+        if (sh2lab_seg_smem(c->tc_Kp, c->tc_Kq) > kSegSmemLimit) return false;
     }
     return true;
 }
@@ -694,7 +760,10 @@ static SegArgs seg_args(const shd_ctx *c, int grp)
     a.bw = c->seg_bw[grp];
     a.nchunk = c->tcs_nchunk[grp];
     a.Kp = c->tcs_Kp[grp];
-    for (int i = 0; i < a.nchunk; ++i) a.chunk[i] = make_int2(c->tcs_chunk[grp][i][0], c->tcs_chunk[grp][i][1]);
+    for (int i = 0; i < a.nchunk; ++i) {
+        const int *t = c->tcs_chunk[grp][i];
+        a.chunk[i] = make_int4(t[0], t[1], t[2], t[3]);
+    }
     return a;
 }
 
@@ -705,7 +774,7 @@ static SegArgs rows_args(const shd_ctx *c)
     a.nitem = (a.nrows + 127) / 128;
     a.Kp = c->tc_Kp;
     a.nchunk = c->tc_Kp / kKC;
-    for (int i = 0; i < a.nchunk; ++i) a.chunk[i] = make_int2(0, i * kKC);
+    for (int i = 0; i < a.nchunk; ++i) a.chunk[i] = make_int4(0, i * kKC, 0, c->N);
     return a;
 }
 
@@ -723,7 +792,7 @@ static cudaError_t group_maps(const shd_ctx *c, int grp, const float *base, CUte
 
 template <int ROWS>
 static cudaError_t run_project_seg(const shd_ctx *ctx, const Prob<float> &P, const SegMaps &maps, const SegArgs &a,
-                                   float *Ip, float *mom, const void *Bh, const void *Bl, cudaStream_t st)
+                                   float *Ip, float *mom, float *nmo, const void *Bh, const void *Bl, cudaStream_t st)
 {
     int nstg = 0, nr = 0;
     if (!pick_depths(a.nb, a.Kp, nstg, nr)) return cudaErrorInvalidConfiguration;
@@ -735,13 +804,13 @@ static cudaError_t run_project_seg(const shd_ctx *ctx, const Prob<float> &P, con
     if (e != cudaSuccess) return e;
     int grid = num_sms_seg(ctx);
     if (a.nitem < grid) grid = (int)a.nitem;
-    kern<<<grid, 448, sm, st>>>(P, maps, a, Ip, mom, (const uint16_t *)Bh, (const uint16_t *)Bl, ctx->d_tc_err);
+    kern<<<grid, 448, sm, st>>>(P, maps, a, Ip, mom, nmo, (const uint16_t *)Bh, (const uint16_t *)Bl, ctx->d_tc_err);
     return cudaGetLastError();
 }
 
-// a1 over the laboratory rows (groups A, B) and the comoving rows of moving
-// nodes (I0n node-major).
-cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, float *mom, const float *I0n,
+// a1: the laboratory rows (groups A, B; moving rows also copied node-major
+// to nm0), the comoving remap nm0 -> nm1, the comoving rows of moving nodes.
+cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, float *mom, float *nm0, float *nm1,
                                cudaStream_t st)
 {
     Prob<float> P = make_prob<float>(ctx);
@@ -755,16 +824,17 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
         first = false;
         SegMaps maps{};
         if ((e = group_maps(ctx, grp, I, maps.m)) != cudaSuccess) return e;
-        if ((e = run_project_seg<0>(ctx, P, maps, a, Ip, mom, ctx->d_tcs_Bh[grp], ctx->d_tcs_Bl[grp], st)) !=
-            cudaSuccess)
+        if ((e = run_project_seg<0>(ctx, P, maps, a, Ip, mom, ctx->nmoving > 0 ? nm0 : nullptr, ctx->d_tcs_Bh[grp],
+                                    ctx->d_tcs_Bl[grp], st)) != cudaSuccess)
             return e;
     }
     if (ctx->nmoving > 0) {
+        if ((e = launch_remap_to_comoving_f(ctx, nm0, nm1, st)) != cudaSuccess) return e;
         SegArgs a = rows_args(ctx);
         a.nb = nlm16(ctx);
         SegMaps maps{};
-        if ((e = rows_map(ctx, &maps.m[0], I0n)) != cudaSuccess) return e;
-        if ((e = run_project_seg<1>(ctx, P, maps, a, Ip, mom, ctx->d_tc_Bh, ctx->d_tc_Bl, st)) != cudaSuccess)
+        if ((e = rows_map(ctx, &maps.m[0], nm1)) != cudaSuccess) return e;
+        if ((e = run_project_seg<1>(ctx, P, maps, a, Ip, mom, nullptr, ctx->d_tc_Bh, ctx->d_tc_Bl, st)) != cudaSuccess)
             return e;
     }
     return cudaSuccess;
@@ -772,39 +842,45 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
 
 template <int ROWS>
 static cudaError_t run_sh2lab_seg(const shd_ctx *ctx, const Prob<float> &P, const SegMaps &maps, const SegArgs &a,
-                                  const float *Sp, const void *Yh, const void *Yl, cudaStream_t st)
+                                  const float *Sp, const float *etan, const float *chin, const void *Yh,
+                                  const void *Yl, cudaStream_t st)
 {
-    const size_t sm = sh2lab_seg_smem(a.Kp, ctx->tc_Kq, ROWS);
+    const size_t sm = sh2lab_seg_smem(a.Kp, ctx->tc_Kq);
     cudaError_t e = cudaFuncSetAttribute(k_sh2lab_seg<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int grid = num_sms_seg(ctx);
     if (a.nitem < grid) grid = (int)a.nitem;
-    k_sh2lab_seg<ROWS><<<grid, 512, sm, st>>>(P, maps, a, Sp, (const uint16_t *)Yh, (const uint16_t *)Yl, ctx->tc_Kq,
-                                              ctx->d_tc_err);
+    k_sh2lab_seg<ROWS><<<grid, 512, sm, st>>>(P, maps, a, Sp, etan, chin, (const uint16_t *)Yh, (const uint16_t *)Yl,
+                                              ctx->tc_Kq, ctx->d_tc_err);
     return cudaGetLastError();
 }
 
-// a3: eta, chi in the sweep layout (moving nodes get overwritten by their
-// remap afterwards) and the comoving S0 of moving nodes node-major in S0n.
-cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *S0n,
-                              cudaStream_t st)
+// a3: the comoving S0 of moving nodes (node-major, nm0), their remap to the
+// laboratory eta, chi (nm1, nm2), then eta, chi of every node into the sweep
+// layout (moving rows taken from nm1, nm2).
+cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,
+                              float *nm2, cudaStream_t st)
 {
     Prob<float> P = make_prob<float>(ctx);
     cudaError_t e;
+    if (ctx->nmoving > 0) {
+        SegArgs a = rows_args(ctx);
+        SegMaps maps{};
+        if ((e = rows_map(ctx, &maps.m[0], nm0)) != cudaSuccess) return e;
+        if ((e = run_sh2lab_seg<1>(ctx, P, maps, a, Sp, nullptr, nullptr, ctx->d_tc_Yh, ctx->d_tc_Yl, st)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_remap_to_lab_f(ctx, nm0, nm1, nm2, st)) != cudaSuccess) return e;
+    }
     for (int grp = 0; grp < 2; ++grp) {
         if (ctx->tcs_nchunk[grp] == 0 || ctx->nseg[grp] == 0) continue;
         SegArgs a = seg_args(ctx, grp);
         SegMaps maps{};
         if ((e = group_maps(ctx, grp, eta, &maps.m[0])) != cudaSuccess) return e;
         if ((e = group_maps(ctx, grp, chi, &maps.m[2])) != cudaSuccess) return e;
-        if ((e = run_sh2lab_seg<0>(ctx, P, maps, a, Sp, ctx->d_tcs_Yh[grp], ctx->d_tcs_Yl[grp], st)) != cudaSuccess)
+        if ((e = run_sh2lab_seg<0>(ctx, P, maps, a, Sp, nm1, nm2, ctx->d_tcs_Yh[grp], ctx->d_tcs_Yl[grp], st)) !=
+            cudaSuccess)
             return e;
-    }
-    if (ctx->nmoving > 0) {
-        SegArgs a = rows_args(ctx);
-        SegMaps maps{};
-        if ((e = rows_map(ctx, &maps.m[0], S0n)) != cudaSuccess) return e;
-        if ((e = run_sh2lab_seg<1>(ctx, P, maps, a, Sp, ctx->d_tc_Yh, ctx->d_tc_Yl, st)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

@@ -685,6 +685,37 @@ static cudaError_t launch_project_persist(const shd_ctx *ctx, const float *I, fl
     }
 }
 
+template <class T>
+static cudaError_t run_remap_to_comoving(const shd_ctx *ctx, const T *nm0, T *nm1, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    size_t sm = remap_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1);
+    return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t run_remap_to_lab(const shd_ctx *ctx, const T *nm0, T *nm1, T *nm2, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    size_t sr = remap_smem_bytes(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_remap_to_lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+    if (e != cudaSuccess) return e;
+    k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_remap_to_comoving_f(const shd_ctx *ctx, const float *nm0, float *nm1, cudaStream_t st)
+{
+    return run_remap_to_comoving<float>(ctx, nm0, nm1, st);
+}
+cudaError_t launch_remap_to_lab_f(const shd_ctx *ctx, const float *nm0, float *nm1, float *nm2, cudaStream_t st)
+{
+    return run_remap_to_lab<float>(ctx, nm0, nm1, nm2, st);
+}
+
 // Moving nodes first: brick transpose of I into nm0, comoving remap into
 // nm1; then the projection contraction (reading nm1 for moving rows).
 template <class T>
@@ -692,17 +723,16 @@ cudaError_t launch_project_nm(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *
 {
     Prob<T> P = make_prob<T>(ctx);
     cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        // the segment kernels write the moving rows node-major themselves
+        if (seg_usable(ctx)) return launch_project_seg(ctx, I, Ip, mom, nm0, nm1, st);
+    }
     if (ctx->nmoving > 0) {
         k_brick_to_nodes<T><<<(unsigned)(ctx->nmtiles * ctx->G), 256, 0, st>>>(P, I, nm0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        size_t sm = remap_smem_bytes(ctx);
-        e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = run_remap_to_comoving<T>(ctx, nm0, nm1, st)) != cudaSuccess) return e;
     }
     if constexpr (sizeof(T) == 4) {
-        if (seg_usable(ctx)) return launch_project_seg(ctx, I, Ip, mom, nm1, st);
         if (tc_usable(ctx)) return launch_project_tc(ctx, I, Ip, mom, nm1, st);
         if (project_persist_smem_bytes(ctx) <= kSmemLimit) return launch_project_persist(ctx, I, Ip, mom, nm1, st);
     }
@@ -736,10 +766,9 @@ cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaS
     bool done = false;
     if constexpr (sizeof(T) == 4) {
         size_t smp = sh2lab_persist_smem_bytes(ctx);
-        if (seg_usable(ctx)) {
-            if ((e = launch_sh2lab_seg(ctx, Sp, eta, chi, nm0, st)) != cudaSuccess) return e;
-            done = true;
-        } else if (tc_usable(ctx)) {
+        // the segment kernels run the remap and write the moving rows themselves
+        if (seg_usable(ctx)) return launch_sh2lab_seg(ctx, Sp, eta, chi, nm0, nm1, nm2, st);
+        if (tc_usable(ctx)) {
             if ((e = launch_sh2lab_tc(ctx, Sp, eta, chi, nm0, st)) != cudaSuccess) return e;
             done = true;
         } else if (smp <= kSmemLimit) {
@@ -761,11 +790,7 @@ cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaS
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (ctx->nmoving > 0) {
-        size_t sr = remap_smem_bytes(ctx);
-        e = cudaFuncSetAttribute(k_remap_to_lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
-        if (e != cudaSuccess) return e;
-        k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = run_remap_to_lab<T>(ctx, nm0, nm1, nm2, st)) != cudaSuccess) return e;
         k_nodes_to_brick<T><<<(unsigned)(ctx->nmtiles * ctx->G), 256, 0, st>>>(P, nm1, nm2, eta, chi);
         e = cudaGetLastError();
     }
