@@ -37,14 +37,6 @@ WORKLOAD = "relativistic jet 64^3, 16 groups (1e-3..1e1 m_e c^2), L=7, 16x32 ord
 SWEEP_BYTES_PER_UPDATE = {"fp32": 16, "mixed": 16, "fp64": 32}
 
 
-def launches_per_step(spec):
-    """Kernels of one step: project (+ comoving remap when any node moves),
-    source, two-pass sums, sh2lab (+ laboratory remap), sweep."""
-    import numpy as np
-    moving = bool(np.any(spec.u != 0))
-    return 6 + (2 if moving else 0)
-
-
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -196,7 +188,8 @@ def field_errors(precision, device, n=16, steps=3):
 
 def time_steps(solver, spec, steps, warmup, stream, dev, barrier, with_timing=True):
     """Warm-up, then `steps` device-timed steps on `stream`; returns
-    (ms, per-stage ms per step, clock summary)."""
+    (ms, per-stage ms per step, clock summary, kernels the library launched
+    in the timed region)."""
     import torch
     sptr = stream.cuda_stream
     solver.step(warmup, sptr)
@@ -207,10 +200,13 @@ def time_steps(solver, spec, steps, warmup, stream, dev, barrier, with_timing=Tr
     torch.cuda.synchronize(dev)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    from paper_1507_05141_gb300 import native
     with ClockSampler(dev.index) as clk:
+        n0 = native.launch_count()
         ev0.record(stream)
         solver.step(steps, sptr)
         ev1.record(stream)
+        launches = native.launch_count() - n0
         torch.cuda.synchronize(dev)
     barrier()
     ms = ev0.elapsed_time(ev1)
@@ -219,7 +215,7 @@ def time_steps(solver, spec, steps, warmup, stream, dev, barrier, with_timing=Tr
         stage_ms, nrec = solver.timing()
         solver.set_timing(False)
         stage = {k: v / max(1, nrec) for k, v in stage_ms.items()}
-    return ms, stage, clk.summary()
+    return ms, stage, clk.summary(), launches
 
 
 def bench_ours(args):
@@ -250,7 +246,7 @@ def bench_ours(args):
 
     # warm-up (also fills the state with a physical solution), then the
     # device-resident timed region
-    ms, stage, clk_summary = time_steps(solver, spec, args.steps, args.warmup, stream, dev, barrier)
+    ms, stage, clk_summary, launches = time_steps(solver, spec, args.steps, args.warmup, stream, dev, barrier)
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device=dev)
@@ -306,7 +302,7 @@ def bench_ours(args):
         torch.cuda.empty_cache()
         s32 = native.Solver.from_spec(spec, device=local, precision="fp32")
         s32.zero_state()
-        ms32, stage32, _ = time_steps(s32, spec, args.steps, args.warmup, stream, dev, barrier)
+        ms32, stage32, _, _ = time_steps(s32, spec, args.steps, args.warmup, stream, dev, barrier)
         if ws > 1:
             import torch.distributed as dist
             t = torch.tensor([ms32], device=dev)
@@ -341,7 +337,7 @@ def bench_ours(args):
                          "algorithmic_bytes": f"{SWEEP_BYTES_PER_UPDATE[prec]} B/update x {upd} updates"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
-            "gpu_launches": launches_per_step(spec) * args.steps,
+            "gpu_launches": launches,
             "clocks": clk_summary,
             "cpu_baseline": cpu,
         }

@@ -192,6 +192,12 @@ long long shd_device_bytes(shd_ctx *ctx);
 int shd_set_timing(shd_ctx *ctx, int on);
 int shd_get_timing(shd_ctx *ctx, double *stage_ms, long long *steps);
 
+/* Number of CUDA kernels this library has launched in the process so far,
+ * over all contexts and threads (counted on the host as each launch is
+ * issued).  The difference across a region is how many of the library's
+ * kernels that region ran.  Never fails. */
+unsigned long long shd_launch_count(void);
+
 /* ---- projection without allocation --------------------------------------
  * No counterpart in the paper.  For callers that cannot call cudaMalloc when
  * they need the moments: programs whose device memory belongs to another

@@ -5,6 +5,7 @@
 // tracing).  All arithmetic of a step runs in the kernels of shd_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -708,7 +709,14 @@ int run_steps(shd_ctx *c, int nsteps, cudaStream_t st)
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace shd {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace shd
+
 extern "C" {
+
+unsigned long long shd_launch_count(void) { return shd::g_launches.load(std::memory_order_relaxed); }
 
 const char *shd_last_error(void) { return g_err; }
 

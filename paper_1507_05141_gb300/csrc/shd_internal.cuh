@@ -186,6 +186,9 @@ struct shd_ctx {
 
 namespace shd {
 
+// Counts a kernel launch issued by the library (see shd_launch_count).
+void note_launch();
+
 // -------------------------------------------------------------------------
 // device helpers
 // -------------------------------------------------------------------------

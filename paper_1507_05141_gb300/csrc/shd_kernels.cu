@@ -527,6 +527,7 @@ cudaError_t launch_chi0(const shd_ctx *ctx, cudaStream_t st)
     Prob<T> P = make_prob<T>(ctx);
     long long n = ctx->Nc * ctx->G;
     k_chi0<T><<<blocks_for(n, 256), 256, 0, st>>>(P, (T *)ctx->d_chi0);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -538,6 +539,7 @@ cudaError_t launch_source(const shd_ctx *ctx, const T *Ip, T *Sp, cudaStream_t s
     cudaError_t e = cudaFuncSetAttribute(k_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_source<T><<<(unsigned)ctx->Nc, 256, sm, st>>>(P, Ip, Sp);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -550,6 +552,7 @@ static cudaError_t launch_sweep_npt(const shd_ctx *ctx, T *I, const T *eta, cons
     cudaError_t e = cudaFuncSetAttribute(k_sweep<T, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_sweep<T, NPT><<<(unsigned)(ctx->N * ctx->G), threads, sm, st>>>(P, I, eta, chi);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -561,6 +564,7 @@ static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, con
     cudaError_t e = cudaFuncSetAttribute(k_sweep_pipe<T, U, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_sweep_pipe<T, U, VEC><<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -611,9 +615,11 @@ cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev,
     Prob<T> P = make_prob<T>(ctx);
     int nb = ctx->n_partial;
     k_sums_partial<T><<<nb, 256, 0, st>>>(P, mom, Sp, Sprev, have_prev ? 1 : 0, ctx->d_partial);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sums_final<<<1, 32, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -625,6 +631,7 @@ cudaError_t launch_canon_to_do(const shd_ctx *ctx, const double *src, T *dst, lo
     long long n = nc * ctx->G * ctx->N;
     if (n == 0) return cudaSuccess;
     k_canon_to_do<T><<<blocks_for(n, 256), 256, 0, st>>>(P, src, dst, c0, nc);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -636,6 +643,7 @@ cudaError_t launch_do_to_canon(const shd_ctx *ctx, const T *src, double *dst, lo
     long long n = nc * ctx->G * ctx->N;
     if (n == 0) return cudaSuccess;
     k_do_to_canon<T><<<blocks_for(n, 256), 256, 0, st>>>(P, src, dst, c0, nc);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -644,6 +652,7 @@ cudaError_t launch_convert(const double *src, T *dst, long long n, cudaStream_t 
 {
     if (n == 0) return cudaSuccess;
     k_convert<T><<<blocks_for(n, 256), 256, 0, st>>>(src, dst, n);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -652,6 +661,7 @@ cudaError_t launch_convert_back(const T *src, double *dst, long long n, cudaStre
 {
     if (n == 0) return cudaSuccess;
     k_convert_back<T><<<blocks_for(n, 256), 256, 0, st>>>(src, dst, n);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -659,6 +669,7 @@ cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, do
                             const double *d_gx, const double *d_gw, int nq, cudaStream_t st)
 {
     k_kn_table<<<blocks_for((long long)G * G, 64), 64, 0, st>>>(G, d_edges, L, d_K, d_sigma_out, d_gx, d_gw, nq);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -575,6 +575,7 @@ cudaError_t launch_project_tc(const shd_ctx *ctx, const float *I, float *Ip, flo
     if (items < grid) grid = (int)items;
     kern<<<grid, 544, sm, st>>>(P, I, I0n, Ip, mom, (const uint16_t *)ctx->d_tc_Bh, (const uint16_t *)ctx->d_tc_Bl,
                                 ctx->NB, ctx->tc_Kp, ctx->d_tc_err);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -589,6 +590,7 @@ cudaError_t launch_sh2lab_tc(const shd_ctx *ctx, const float *Sp, float *eta, fl
     if (items < grid) grid = (int)items;
     k_sh2lab_tc<<<grid, 256, sm, st>>>(P, Sp, eta, chi, S0n, (const uint16_t *)ctx->d_tc_Yh,
                                       (const uint16_t *)ctx->d_tc_Yl, ctx->tc_Np, ctx->tc_Kq, ctx->d_tc_err);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -805,6 +805,7 @@ static cudaError_t run_project_seg(const shd_ctx *ctx, const Prob<float> &P, con
     int grid = num_sms_seg(ctx);
     if (a.nitem < grid) grid = (int)a.nitem;
     kern<<<grid, 448, sm, st>>>(P, maps, a, Ip, mom, nmo, (const uint16_t *)Bh, (const uint16_t *)Bl, ctx->d_tc_err);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -852,6 +853,7 @@ static cudaError_t run_sh2lab_seg(const shd_ctx *ctx, const Prob<float> &P, cons
     if (a.nitem < grid) grid = (int)a.nitem;
     k_sh2lab_seg<ROWS><<<grid, 512, sm, st>>>(P, maps, a, Sp, etan, chin, (const uint16_t *)Yh, (const uint16_t *)Yl,
                                               ctx->tc_Kq, ctx->d_tc_err);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -633,6 +633,7 @@ static cudaError_t launch_project_tile_tc(const shd_ctx *ctx, const T *I, const 
 {
     Prob<T> P = make_prob<T>(ctx);
     k_project_tile<T, TC><<<(unsigned)(ctx->ntiles * ctx->G), 128, 0, st>>>(P, I, I0n, Ip, mom);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -666,6 +667,7 @@ static cudaError_t launch_project_persist_tc(const shd_ctx *ctx, const float *I,
     int grid = num_sms(ctx);
     if (items < grid) grid = (int)items;
     k_project_persist<TC><<<grid, 256, sm, st>>>(P, I, scratch, Ip, mom);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -693,6 +695,7 @@ static cudaError_t run_remap_to_comoving(const shd_ctx *ctx, const T *nm0, T *nm
     cudaError_t e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -704,6 +707,7 @@ static cudaError_t run_remap_to_lab(const shd_ctx *ctx, const T *nm0, T *nm1, T 
     cudaError_t e = cudaFuncSetAttribute(k_remap_to_lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
     if (e != cudaSuccess) return e;
     k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -729,6 +733,7 @@ cudaError_t launch_project_nm(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *
     }
     if (ctx->nmoving > 0) {
         k_brick_to_nodes<T><<<(unsigned)(ctx->nmtiles * ctx->G), 256, 0, st>>>(P, I, nm0);
+        note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = run_remap_to_comoving<T>(ctx, nm0, nm1, st)) != cudaSuccess) return e;
     }
@@ -778,6 +783,7 @@ cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaS
             int grid = num_sms(ctx);
             if (items < grid) grid = (int)items;
             k_sh2lab_persist<<<grid, 256, smp, st>>>(P, Sp, eta, chi, nm0);
+            note_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             done = true;
         }
@@ -787,11 +793,13 @@ cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaS
         e = cudaFuncSetAttribute(k_sh2lab_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         k_sh2lab_tile<T><<<(unsigned)(ctx->ntiles * ctx->G), 256, sm, st>>>(P, Sp, eta, chi, nm0);
+        note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (ctx->nmoving > 0) {
         if ((e = run_remap_to_lab<T>(ctx, nm0, nm1, nm2, st)) != cudaSuccess) return e;
         k_nodes_to_brick<T><<<(unsigned)(ctx->nmtiles * ctx->G), 256, 0, st>>>(P, nm1, nm2, eta, chi);
+        note_launch();
         e = cudaGetLastError();
     }
     return e;

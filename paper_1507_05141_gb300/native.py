@@ -56,6 +56,7 @@ _SIGS = {
     "shd_device_bytes": (_ll, [_vp]),
     "shd_set_timing": (_i, [_vp, _i]),
     "shd_get_timing": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
+    "shd_launch_count": (ctypes.c_ulonglong, []),
     "shd_project_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "shd_noalloc_last_error": (ctypes.c_char_p, []),
 }
@@ -105,6 +106,11 @@ def torch_stream():
 
 def exported_symbols():
     return list(_SIGS)
+
+
+def launch_count():
+    """Kernels the native library has launched in this process so far."""
+    return int(lib().shd_launch_count())
 
 
 def _check(rc):

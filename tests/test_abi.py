@@ -55,3 +55,11 @@ def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(native, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         native.lib()
+
+
+def test_launch_count_is_host_side(built):
+    """The launch counter needs no GPU: it only reads a host counter."""
+    from paper_1507_05141_gb300 import native
+    a = native.launch_count()
+    b = native.launch_count()
+    assert 0 <= a <= b
