@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
         const long long sg = w / G;
         const int g = (int)(w - sg * G);
         // the previous item's stores have finished reading the tiles
-        if (tid == 0) tc::bulk_wait_read<0>();
+        if (lane == 0) tc::bulk_wait_read<0>();
         __syncthreads();
         if (tid < 128) {
             long long src = -1;
@@ -539,48 +539,84 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
             const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
             int cc[5];
             if constexpr (!ROWS) {
+                // each warp stores its own box: 32 rows (quad) x 16 columns of
+                // eta (parts 0, 1) or chi (parts 2, 3) per chunk
                 const float chr = chir[r];
                 const int m = rowm[r];
                 const long long nbase = m >= 0 ? ((long long)m * G + g) * N : 0;
-                const int half = part & 1;  // columns 16 half .. 16 half + 15 of the chunk
-                for (int cn = 0; cn < nchunk; ++cn) {
-                    float *Te = tiles + (size_t)((cn & 1) * 2) * kBox, *Tc = Te + kBox;
-                    // the stores of chunk cn - 2 (same tiles) have read them
-                    if (tid == 0) tc::bulk_wait_read<1>();
-                    __syncthreads();
+                const int half = part & 1;
+                const bool eta_w = part < 2;
+                const float *nsrc = eta_w ? etan : chin;
+                const bool anym = __any_sync(0xffffffffu, m >= 0);
+                float *W = tiles + (size_t)warp * 2 * 512;  // [2][16][32]
+                const int4 sd = S.segs[sg];
+                const int r0 = quad * 32;
+                const int as = sd.y + r0 % S.bw, bs = sd.z + r0 / S.bw;
+                const CUtensorMap *mp_base = &maps.m[eta_w ? 0 : 2];
+                auto store = [&](int cn, const float *src) {
                     const int4 ci = S.chunk[cn];
-                    const int kl0 = ci.y + 16 * half;  // first ordinate (within the class) of these columns
-                    float *T = part < 2 ? Te : Tc;
-                    float *col = T + (size_t)(16 * half) * 128 + r;
-                    if (part < 2) {
-                        float v[16];
-                        tc::tmem_ld16(trow + (uint32_t)(cn * kKC + 16 * half), v);
-                        if (m < 0) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) col[j * 128] = chr * v[j];
-                        } else {
-                            const float *src = etan + nbase + ci.z + kl0;
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) col[j * 128] = kl0 + j < ci.w ? src[j] : 0.f;
+                    const int kk = ci.y + 16 * half;
+                    const bool yc = !S.groupB && ci.x == 1;
+                    tc::tma_store_5d(mp_base + ci.x, as, yc ? sd.x : bs, yc ? bs : sd.x, g, kk, src);
+                };
+                // moving rows: cp.async of their 16 values of chunk cn into buffer b
+                auto prefetch = [&](int cn, int b) {
+                    if (m < 0) return;
+                    const int4 ci = S.chunk[cn];
+                    const int kl0 = ci.y + 16 * half;
+                    const float *src = nsrc + nbase + ci.z + kl0;
+                    float *dst = W + (size_t)b * 512 + lane;
+                    for (int j = 0; j < 16; ++j)
+                        if (kl0 + j < ci.w) {
+                            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + j * 32);
+                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + j) : "memory");
                         }
-                    } else {
-                        if (m < 0) {
+                };
+                if (!eta_w && !anym) {
+                    // every row at rest: one constant chi tile serves every chunk
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) col[j * 128] = chr;
-                        } else {
-                            const float *src = chin + nbase + ci.z + kl0;
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) col[j * 128] = kl0 + j < ci.w ? src[j] : 0.f;
-                        }
-                    }
+                    for (int j = 0; j < 16; ++j) W[j * 32 + lane] = chr;
                     tc::fence_proxy_async();
-                    __syncthreads();
-                    if (tid == 0) {
-                        box_coords(S, 0, w, G, cn, cc);
-                        tc::tma_store_5d(&maps.m[ci.x], cc[0], cc[1], cc[2], cc[3], cc[4], Te);
-                        tc::tma_store_5d(&maps.m[2 + ci.x], cc[0], cc[1], cc[2], cc[3], cc[4], Tc);
+                    __syncwarp();
+                    if (lane == 0) {
+                        for (int cn = 0; cn < nchunk; ++cn) store(cn, W);
                         tc::bulk_commit();
                     }
+                } else {
+                    if (anym) prefetch(0, 0);
+                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                    for (int cn = 0; cn < nchunk; ++cn) {
+                        const int b = cn & 1;
+                        // buffer b ^ 1 (chunk cn - 1) is rewritten by the prefetch:
+                        // every earlier store must have read its source
+                        if (lane == 0) {
+                            if (anym) tc::bulk_wait_read<0>();
+                            else tc::bulk_wait_read<1>();
+                        }
+                        __syncwarp();
+                        if (anym && cn + 1 < nchunk) prefetch(cn + 1, b ^ 1);
+                        asm volatile("cp.async.commit_group;\n" ::: "memory");
+                        float *Wb = W + (size_t)b * 512 + lane;
+                        if (eta_w) {
+                            float v[16];
+                            tc::tmem_ld16(trow + (uint32_t)(cn * kKC + 16 * half), v);
+                            if (m < 0) {
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) Wb[j * 32] = chr * v[j];
+                            }
+                        } else if (m < 0) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) Wb[j * 32] = chr;
+                        }
+                        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                        tc::fence_proxy_async();
+                        __syncwarp();
+                        if (lane == 0) {
+                            store(cn, W + (size_t)b * 512);
+                            tc::bulk_commit();
+                        }
+                    }
+                    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
                 }
             } else {
                 for (int pc = 0; pc * 2 < nchunk; ++pc) {
@@ -620,7 +656,7 @@ drain:
         if (pending) tc::mbar_wait(bar, phase, kSegWaitLimit);
     }
 done:
-    if (threadIdx.x == 0) tc::bulk_wait_all();
+    if (lane == 0) tc::bulk_wait_all();
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
@@ -699,7 +735,8 @@ bool seg_usable(const shd_ctx *c)
 
 // 5-D map over one class of a discrete-ordinate array: dims (fastest first)
 // d0, d1, d2 of the class's sweep layout, then g, then the class's ordinates.
-static cudaError_t class_map(const shd_ctx *c, CUtensorMap *m, const float *base, int cls, int bw)
+// The box: ba x bb nodes (a fastest) x bk ordinates.
+static cudaError_t class_map(const shd_ctx *c, CUtensorMap *m, const float *base, int cls, int ba, int bb, int bk)
 {
     const cuuint64_t nx = c->nx, ny = c->ny, nz = c->nz, Nc = (cuuint64_t)c->Nc;
     const int kb = cls == 2 ? 0 : (cls == 1 ? c->nZ : c->nA);
@@ -709,22 +746,22 @@ static cudaError_t class_map(const shd_ctx *c, CUtensorMap *m, const float *base
     if (cls == 2) {  // (x, y, z)
         dims[0] = nx; dims[1] = ny; dims[2] = nz;
         str[0] = nx * 4; str[1] = nx * ny * 4;
-        box[0] = bw; box[1] = 128 / bw; box[2] = 1;
+        box[0] = ba; box[1] = bb; box[2] = 1;
     } else if (cls == 1) {  // (x, z, y)
         dims[0] = nx; dims[1] = nz; dims[2] = ny;
         str[0] = nx * 4; str[1] = nx * nz * 4;
-        box[0] = bw; box[1] = 1; box[2] = 128 / bw;
+        box[0] = ba; box[1] = 1; box[2] = bb;
     } else {  // (y, z, x)
         dims[0] = ny; dims[1] = nz; dims[2] = nx;
         str[0] = ny * 4; str[1] = ny * nz * 4;
-        box[0] = bw; box[1] = 128 / bw; box[2] = 1;
+        box[0] = ba; box[1] = bb; box[2] = 1;
     }
     dims[3] = (cuuint64_t)c->G;
     dims[4] = (cuuint64_t)kn;
     str[2] = Nc * 4;
     str[3] = (cuuint64_t)c->G * Nc * 4;
     box[3] = 1;
-    box[4] = kKC;
+    box[4] = bk;
     void *gaddr = const_cast<float *>(base + (size_t)kb * c->G * Nc);
     CUresult r = encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, gaddr, dims, str, box, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -778,16 +815,22 @@ static SegArgs rows_args(const shd_ctx *c)
     return a;
 }
 
-// the map of the classes of group grp: group A {z, y}, group B {x}
-static cudaError_t group_maps(const shd_ctx *c, int grp, const float *base, CUtensorMap *m0)
+// The maps of the classes of group grp (group A {z, y}, group B {x}).  Whole
+// tiles (a1 loads): bw x 128/bw nodes x 32 ordinates; quarter tiles (a3
+// per-warp stores): 32 consecutive rows of the tile x 16 ordinates.
+static cudaError_t group_maps(const shd_ctx *c, int grp, const float *base, CUtensorMap *m0, bool quarter)
 {
+    const int bw = c->seg_bw[grp];
+    const int ba = quarter ? (bw < 32 ? bw : 32) : bw;
+    const int bb = quarter ? 32 / ba : 128 / bw;
+    const int bk = quarter ? 16 : kKC;
     cudaError_t e;
     if (grp == 0) {
-        if (c->nZ > 0 && (e = class_map(c, &m0[0], base, 2, c->seg_bw[0])) != cudaSuccess) return e;
-        if (c->nA > c->nZ && (e = class_map(c, &m0[1], base, 1, c->seg_bw[0])) != cudaSuccess) return e;
+        if (c->nZ > 0 && (e = class_map(c, &m0[0], base, 2, ba, bb, bk)) != cudaSuccess) return e;
+        if (c->nA > c->nZ && (e = class_map(c, &m0[1], base, 1, ba, bb, bk)) != cudaSuccess) return e;
         return cudaSuccess;
     }
-    return class_map(c, &m0[0], base, 0, c->seg_bw[1]);
+    return class_map(c, &m0[0], base, 0, ba, bb, bk);
 }
 
 template <int ROWS>
@@ -824,7 +867,7 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
         a.accumulate = first ? 0 : 1;
         first = false;
         SegMaps maps{};
-        if ((e = group_maps(ctx, grp, I, maps.m)) != cudaSuccess) return e;
+        if ((e = group_maps(ctx, grp, I, maps.m, false)) != cudaSuccess) return e;
         if ((e = run_project_seg<0>(ctx, P, maps, a, Ip, mom, ctx->nmoving > 0 ? nm0 : nullptr, ctx->d_tcs_Bh[grp],
                                     ctx->d_tcs_Bl[grp], st)) != cudaSuccess)
             return e;
@@ -878,8 +921,8 @@ cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, f
         if (ctx->tcs_nchunk[grp] == 0 || ctx->nseg[grp] == 0) continue;
         SegArgs a = seg_args(ctx, grp);
         SegMaps maps{};
-        if ((e = group_maps(ctx, grp, eta, &maps.m[0])) != cudaSuccess) return e;
-        if ((e = group_maps(ctx, grp, chi, &maps.m[2])) != cudaSuccess) return e;
+        if ((e = group_maps(ctx, grp, eta, &maps.m[0], true)) != cudaSuccess) return e;
+        if ((e = group_maps(ctx, grp, chi, &maps.m[2], true)) != cudaSuccess) return e;
         if ((e = run_sh2lab_seg<0>(ctx, P, maps, a, Sp, nm1, nm2, ctx->d_tcs_Yh[grp], ctx->d_tcs_Yl[grp], st)) !=
             cudaSuccess)
             return e;
