@@ -317,9 +317,15 @@ __device__ inline Stencil<T> make_stencil(const T *mu, int nmu, int nphi, const 
         s.k[3] = s.k[1]; s.w[3] = 0;
         return s;
     }
-    int a = 0;
     if (nmu > 1) {
-        while (a < nmu - 2 && m > mu[a + 1]) ++a;
+        // ring bracket: the largest a <= nmu - 2 with mu[a] < m (0 if none),
+        // by bisection over the ascending nodes
+        int a = 0, hi = nmu - 2;
+        while (a < hi) {
+            const int mid = (a + hi + 1) >> 1;
+            if (mu[mid] < m) a = mid;
+            else hi = mid - 1;
+        }
         T t = (m - mu[a]) / (mu[a + 1] - mu[a]);
         s.k[0] = a * nphi + b;       s.w[0] = (T(1) - t) * (T(1) - tp);
         s.k[1] = a * nphi + b1;      s.w[1] = (T(1) - t) * tp;

@@ -15,6 +15,8 @@
 //     writes S0 to the scratch buffer and k_remap_to_lab does the transform.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "shd_internal.cuh"
 
 namespace shd {
@@ -505,32 +507,106 @@ __global__ void __launch_bounds__(256) k_nodes_to_brick(Prob<T> P, const T *__re
     }
 }
 
+// Shared tables of the remap kernels: mu[nmu], lc[G], linv[G] (working
+// precision) and mesh2int[N], staged once per CTA after the node's values.
+template <class T>
+struct RemapTables {
+    T *mu, *lc, *linv;
+    int *m2i;
+};
+
+template <class T>
+__device__ inline RemapTables<T> remap_tables(const Prob<T> &P, unsigned char *base)
+{
+    RemapTables<T> t;
+    t.mu = reinterpret_cast<T *>(base);
+    t.lc = t.mu + P.nmu;
+    t.linv = t.lc + P.G;
+    t.m2i = reinterpret_cast<int *>(t.linv + P.G);
+    for (int i = threadIdx.x; i < P.nmu; i += blockDim.x) t.mu[i] = P.mu[i];
+    for (int i = threadIdx.x; i < P.G; i += blockDim.x) {
+        t.lc[i] = P.lc[i];
+        t.linv[i] = P.linv[i];
+    }
+    for (int i = threadIdx.x; i < P.N; i += blockDim.x) t.m2i[i] = P.mesh2int[i];
+    return t;
+}
+
+// The node's G x N values (node-major, internal ordinate order) into shared
+// memory, vectorised when the rows allow it.
+template <class T>
+__device__ inline void stage_node(T *dst, const T *src, int n)
+{
+    constexpr int V = 16 / sizeof(T);
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && n % V == 0) {
+        using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        const V4 *s4 = reinterpret_cast<const V4 *>(src);
+        V4 *d4 = reinterpret_cast<V4 *>(dst);
+        for (int i = threadIdx.x; i < n / V; i += blockDim.x) d4[i] = s4[i];
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+// Ring averages at the two poles (mesh rings 0 and nmu - 1, summed in mesh
+// order) for every group.
+template <class T>
+__device__ inline void pole_averages(const Prob<T> &P, const T *sv, const int *m2i, T *spole)
+{
+    for (int i = threadIdx.x; i < 2 * P.G; i += blockDim.x) {
+        const int g = i >> 1, rr = i & 1;
+        const T *F = sv + (size_t)g * P.N;
+        const int base = rr ? (P.nmu - 1) * P.nphi : 0;
+        T s = 0;
+        for (int j = 0; j < P.nphi; ++j) s += F[m2i[base + j]];
+        spole[i] = s / T(P.nphi);
+    }
+}
+
+// Bilinear stencil of direction n over the (mu, phi) mesh (from the shared mu
+// table), with its four ordinates given as internal indices.
+template <class T>
+__device__ inline Stencil<T> stencil_internal(const Prob<T> &P, const RemapTables<T> &t, const T n[3])
+{
+    Stencil<T> s = make_stencil<T>(t.mu, P.nmu, P.nphi, n);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s.k[i] = t.m2i[s.k[i]];
+    return s;
+}
+
+// Stencil values of one direction per group, with the last two evaluations
+// kept: consecutive output groups usually bracket neighbouring input groups.
+template <class T>
+struct GroupCache {
+    int g0 = -1, g1 = -1;
+    T v0 = 0, v1 = 0;
+    __device__ inline T get(const Stencil<T> &st, const T *sv, const T *spole, int N, int g)
+    {
+        if (g == g1) return v1;
+        if (g == g0) return v0;
+        const T v = eval_stencil<T>(st, sv + (size_t)g * N, spole + 2 * g);
+        g0 = g1; v0 = v1;
+        g1 = g; v1 = v;
+        return v;
+    }
+};
+
 // laboratory I (node-major) -> comoving I0 (node-major), one CTA per moving
 // node: I0(k0, g0) = (ebar_g0/eps)^3 I_lab(n, eps), n = boost of n_k0 to the
 // laboratory, eps = ebar_g0 (Gamma + u.n_k0)   (Sec. 2.2)
 template <class T>
-__global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__restrict__ I0)
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__restrict__ I0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G, N = P.N;
-    T *sI = reinterpret_cast<T *>(smem_raw);  // [G][N]
+    T *sI = reinterpret_cast<T *>(smem_raw);  // [G][N] internal order
     T *spole = sI + (size_t)G * N;            // [G][2]
     const long long m = blockIdx.x;
     const long long c = P.moving[m];
-    const T *src = In + m * G * N;
-    // staged in mesh order: the angle stencils address the (theta, phi) mesh
-    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
-        const int g = i / N, k = i - g * N;
-        sI[(size_t)g * N + P.int2mesh[k]] = src[i];
-    }
+    stage_node<T>(sI, In + m * G * N, G * N);
+    const RemapTables<T> tb = remap_tables<T>(P, reinterpret_cast<unsigned char *>(spole + 2 * G));
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
-        int g = i >> 1, rr = i & 1;
-        const T *F = sI + (size_t)g * N + (rr ? (P.nmu - 1) * P.nphi : 0);
-        T s = 0;
-        for (int j = 0; j < P.nphi; ++j) s += F[j];
-        spole[i] = s / T(P.nphi);
-    }
+    pole_averages<T>(P, sI, tb.m2i, spole);
     __syncthreads();
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
     T *dst = I0 + m * G * N;
@@ -538,18 +614,19 @@ __global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__re
         T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
         T n[3];
         T q = boost_any<T>(u, n0, n, T(-1), P.fp64_boost);  // nu/nu0
-        Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n);
+        const Stencil<T> st = stencil_internal<T>(P, tb, n);
         T iq3 = T(1) / (q * q * q);
         T lq = dlog<T>(q);
         int hint = 0;
+        GroupCache<T> cache;
         for (int g0 = 0; g0 < G; ++g0) {
-            FreqBracket<T> fb = freq_bracket<T>(P.lc, P.linv, P.le0, P.leG, G, P.lc[g0] + lq, hint);
+            FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, tb.lc[g0] + lq, hint);
             T v = 0;
             if (fb.mode == 1) {
-                v = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                v = cache.get(st, sI, spole, N, fb.ga);
             } else if (fb.mode == 2) {
-                T fa = eval_stencil<T>(st, sI + (size_t)fb.ga * N, spole + 2 * fb.ga);
-                T fbv = eval_stencil<T>(st, sI + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
+                T fa = cache.get(st, sI, spole, N, fb.ga);
+                T fbv = cache.get(st, sI, spole, N, fb.ga + 1);
                 v = freq_mix<T>(fa, fbv, fb.t);
             }
             dst[(size_t)g0 * N + k0] = v * iq3;
@@ -561,30 +638,21 @@ __global__ void k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__re
 // D = Gamma - u.n_k, n0 = comoving direction, eps0 = ebar_g D,
 // S_lab = S0(n0, eps0)/D^3, chi_lab = chi0(eps0) D, eta_lab = chi_lab S_lab
 template <class T>
-__global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restrict__ eta_n, T *__restrict__ chi_n)
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restrict__ eta_n,
+                                                      T *__restrict__ chi_n)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G, N = P.N;
-    T *sS = reinterpret_cast<T *>(smem_raw);  // [G][N]
+    T *sS = reinterpret_cast<T *>(smem_raw);  // [G][N] internal order
     T *spole = sS + (size_t)G * N;            // [G][2]
     T *schi = spole + 2 * G;                  // [G]
     const long long m = blockIdx.x;
     const long long c = P.moving[m];
-    const T *src = S0 + m * G * N;
-    // staged in mesh order: the angle stencils address the (theta, phi) mesh
-    for (int i = threadIdx.x; i < G * N; i += blockDim.x) {
-        const int g = i / N, k = i - g * N;
-        sS[(size_t)g * N + P.int2mesh[k]] = src[i];
-    }
+    stage_node<T>(sS, S0 + m * G * N, G * N);
     for (int g = threadIdx.x; g < G; g += blockDim.x) schi[g] = P.chi0[c * G + g];
+    const RemapTables<T> tb = remap_tables<T>(P, reinterpret_cast<unsigned char *>(schi + G));
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) {
-        int g = i >> 1, rr = i & 1;
-        const T *F = sS + (size_t)g * N + (rr ? (P.nmu - 1) * P.nphi : 0);
-        T s = 0;
-        for (int j = 0; j < P.nphi; ++j) s += F[j];
-        spole[i] = s / T(P.nphi);
-    }
+    pole_averages<T>(P, sS, tb.m2i, spole);
     __syncthreads();
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
     T *de = eta_n + m * G * N, *dc = chi_n + m * G * N;
@@ -592,21 +660,22 @@ __global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restric
         T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
         T n0[3];
         T D = boost_any<T>(u, n, n0, T(1), P.fp64_boost);  // nu0/nu
-        Stencil<T> st = make_stencil<T>(P.mu, P.nmu, P.nphi, n0);
+        const Stencil<T> st = stencil_internal<T>(P, tb, n0);
         T iD3 = T(1) / (D * D * D);
         T lD = dlog<T>(D);
         int hint = 0;
+        GroupCache<T> cache;
         for (int g = 0; g < G; ++g) {
-            FreqBracket<T> fb = freq_bracket<T>(P.lc, P.linv, P.le0, P.leG, G, P.lc[g] + lD, hint);
+            FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, tb.lc[g] + lD, hint);
             T s = 0, ch;
             if (fb.mode == 0) {
                 ch = schi[fb.ga];
             } else if (fb.mode == 1) {
-                s = eval_stencil<T>(st, sS + (size_t)fb.ga * N, spole + 2 * fb.ga);
+                s = cache.get(st, sS, spole, N, fb.ga);
                 ch = schi[fb.ga];
             } else {
-                T fa = eval_stencil<T>(st, sS + (size_t)fb.ga * N, spole + 2 * fb.ga);
-                T fbv = eval_stencil<T>(st, sS + (size_t)(fb.ga + 1) * N, spole + 2 * (fb.ga + 1));
+                T fa = cache.get(st, sS, spole, N, fb.ga);
+                T fbv = cache.get(st, sS, spole, N, fb.ga + 1);
                 s = freq_mix<T>(fa, fbv, fb.t);
                 ch = freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], fb.t);
             }
@@ -620,7 +689,11 @@ __global__ void k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restric
 // -------------------------------------------------------------------------
 // launchers
 // -------------------------------------------------------------------------
-size_t remap_smem_bytes(const shd_ctx *c) { return (size_t)c->esize * ((size_t)c->G * c->N + 3 * c->G); }
+size_t remap_smem_bytes(const shd_ctx *c)
+{
+    // values [G][N], poles [G][2], chi0 [G], tables mu, lc, linv, mesh2int
+    return (size_t)c->esize * ((size_t)c->G * c->N + 3 * c->G + c->nmu + 2 * c->G) + sizeof(int) * (size_t)c->N + 16;
+}
 
 size_t sh2lab_tile_smem_bytes(const shd_ctx *c)
 {
