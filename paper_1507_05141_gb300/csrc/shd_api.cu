@@ -5,6 +5,7 @@
 // tracing).  All arithmetic of a step runs in the kernels of shd_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -154,7 +155,7 @@ void free_all(shd_ctx *c)
                      (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
                      &c->d_lc, &c->d_linv, &c->d_tc_Bh, &c->d_tc_Bl, &c->d_tc_Yh, &c->d_tc_Yl,
                      (void **)&c->d_int2mesh, (void **)&c->d_mesh2int,
-                     &c->d_seg[0], &c->d_seg[1], &c->d_tcs_Bh[0], &c->d_tcs_Bh[1], &c->d_tcs_Bl[0],
+                     &c->d_chi0L, (void **)&c->d_mbits, &c->d_seg[0], &c->d_seg[1], &c->d_tcs_Bh[0], &c->d_tcs_Bh[1], &c->d_tcs_Bl[0],
                      &c->d_tcs_Bl[1], &c->d_tcs_Yh[0], &c->d_tcs_Yh[1], &c->d_tcs_Yl[0], &c->d_tcs_Yl[1],
                      (void **)&c->d_tc_err};
     for (void **p : ptrs) dfree(*p);
@@ -500,6 +501,7 @@ int ensure_buffers(shd_ctx *c)
     if ((rc = dalloc(c, &c->d_alpha0, nCG * es, "alpha0"))) return rc;
     if ((rc = dalloc(c, &c->d_emis0, nCG * es, "emis0"))) return rc;
     if ((rc = dalloc(c, &c->d_chi0, nCG * es, "chi0"))) return rc;
+    if ((rc = dalloc(c, &c->d_chi0L, 3 * nCG * es, "chi0 layouts"))) return rc;
     if ((rc = dalloc(c, &c->d_ne, (size_t)c->Nc * es, "ne"))) return rc;
     if ((rc = dalloc(c, &c->d_u, (size_t)c->Nc * 3 * es, "u"))) return rc;
     c->n_partial = 8 * 152;
@@ -531,7 +533,7 @@ int stream_after(cudaStream_t waiter, cudaStream_t producer)
 // brick by brick so that a brick's remap CTAs run side by side.
 int build_tiles(shd_ctx *c, const double *u)
 {
-    dfree(c->d_tiles); dfree((void *&)c->d_moving); dfree((void *&)c->d_mflag);
+    dfree(c->d_tiles); dfree((void *&)c->d_moving); dfree((void *&)c->d_mflag); dfree((void *&)c->d_mbits);
     dfree((void *&)c->d_midx); dfree((void *&)c->d_mtiles);
     for (int i = 0; i < 3; ++i) dfree(c->d_nm[i]);
     int tx = (c->nx + 7) / 8, ty = (c->ny + 7) / 8;
@@ -561,6 +563,35 @@ int build_tiles(shd_ctx *c, const double *u)
             }
     c->ntiles = (long long)tiles.size();
     c->nmoving = (long long)moving.size();
+    {
+        // moving 4-node pieces of every plane of the three sweep layouts
+        const int dims[3] = {c->nx, c->ny, c->nz};
+        int npc = 0, nwin = 0;
+        for (int d = 0; d < 3; ++d) {
+            const int e1 = d == 0 ? 2 : (d == 1 ? 2 : 1), e2 = d == 0 ? 1 : 0;  // layout (d, e1, e2)
+            const int plane = dims[e1] * dims[e2];
+            npc = std::max(npc, (plane + 3) / 4);
+            nwin = std::max(nwin, (dims[d] + 63) / 64);
+        }
+        std::vector<unsigned long long> bits((size_t)3 * nwin * npc, 0ull);
+        for (long long node = 0; node < c->Nc; ++node) {
+            if (!mflag[node]) continue;
+            const int ix = (int)(node % c->nx), iy = (int)((node / c->nx) % c->ny), iz = (int)(node / ((long long)c->nx * c->ny));
+            for (int d = 0; d < 3; ++d) {
+                const long long o = perm_offset(d, ix, iy, iz, c->nx, c->ny, c->nz);
+                const int plane = d == 2 ? c->nx * c->ny : (d == 1 ? c->nx * c->nz : c->ny * c->nz);
+                const int id = (int)(o / plane), j = (int)(o % plane);
+                bits[((size_t)d * nwin + id / 64) * npc + j / 4] |= 1ull << (id % 64);
+            }
+        }
+        c->mbits_npc = npc;
+        c->mbits_nwin = nwin;
+        int rc0;
+        if ((rc0 = dalloc(c, (void **)&c->d_mbits, bits.size() * sizeof(unsigned long long), "moving pieces")))
+            return rc0;
+        CK(cudaMemcpy(c->d_mbits, bits.data(), bits.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice),
+           "moving pieces");
+    }
     int rc;
     if ((rc = dalloc(c, &c->d_tiles, sizeof(TileInfo) * tiles.size(), "tiles"))) return rc;
     CK(cudaMemcpy(c->d_tiles, tiles.data(), sizeof(TileInfo) * tiles.size(), cudaMemcpyHostToDevice), "tiles");
@@ -656,7 +687,7 @@ int check_device_flags(shd_ctx *c)
     CK(cudaStreamSynchronize(c->stream), "sync");
     if (flag) {
         cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream);
-        return fail(SHD_ERR_TIMEOUT, "a tensor-core kernel timed out waiting for its MMAs");
+        return fail(SHD_ERR_TIMEOUT, "a tensor-core kernel gave up (a bounded wait ran out)");
     }
     return SHD_OK;
 }
@@ -691,9 +722,12 @@ int run_steps(shd_ctx *c, int nsteps, cudaStream_t st)
         CK(launch_sums<T>(c, (const T *)c->d_mom, (const T *)c->d_Sp, (const T *)c->d_Sprev, c->sprev_valid, st),
            "sums");
         if (tm) CK(cudaEventRecord(ev[3], st), "event");
-        CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st), "sh2lab");
+        // the sweep takes chi at nodes at rest from the chi0 layouts, so chi_lab
+        // is needed only where a node moves
+        const bool c0L = sweep_uses_chi0L<T>(c);
+        CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st, !c0L), "sh2lab");
         if (tm) CK(cudaEventRecord(ev[4], st), "event");
-        CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st), "sweep");
+        CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st, c0L), "sweep");
         if (tm) {
             CK(cudaEventRecord(ev[5], st), "event");
             c->timing.count++;

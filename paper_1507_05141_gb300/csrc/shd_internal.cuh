@@ -134,6 +134,12 @@ struct shd_ctx {
     void *d_W = nullptr, *d_dirs = nullptr, *d_Y = nullptr, *d_mu = nullptr;
     double *d_edges = nullptr, *d_centre = nullptr;
     void *d_alpha0 = nullptr, *d_ne = nullptr, *d_u = nullptr, *d_emis0 = nullptr, *d_chi0 = nullptr;
+    // chi0 in the three sweep layouts [d][g][o] and, per layout, the 4-node
+    // pieces of each plane holding a moving node: bit (id % 64) of
+    // d_mbits[d][id / 64][piece] (mbits_nwin windows of mbits_npc words)
+    void *d_chi0L = nullptr;
+    unsigned long long *d_mbits = nullptr;
+    int mbits_npc = 0, mbits_nwin = 0;
     void *d_K = nullptr, *d_sigma_out = nullptr;
     void *d_bc = nullptr;
     void *d_I = nullptr, *d_eta = nullptr, *d_chi = nullptr;
@@ -452,7 +458,7 @@ bool seg_usable(const shd_ctx *ctx);
 cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, float *mom, float *nm0, float *nm1,
                                cudaStream_t st);
 cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,
-                              float *nm2, cudaStream_t st);
+                              float *nm2, cudaStream_t st, bool full_chi);
 cudaError_t launch_remap_to_comoving_f(const shd_ctx *ctx, const float *nm0, float *nm1, cudaStream_t st);
 cudaError_t launch_remap_to_lab_f(const shd_ctx *ctx, const float *nm0, float *nm1, float *nm2, cudaStream_t st);
 size_t project_tc_smem_bytes(const shd_ctx *ctx);
@@ -464,9 +470,12 @@ cudaError_t launch_sh2lab_tc(const shd_ctx *ctx, const float *Sp, float *eta, fl
 template <class T>
 cudaError_t launch_source(const shd_ctx *ctx, const T *Ip, T *Sp, cudaStream_t st);
 template <class T>
-cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st);
+cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st, bool full_chi = true);
 template <class T>
-cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st);
+cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st,
+                         bool use_chi0L = false);
+template <class T>
+bool sweep_uses_chi0L(const shd_ctx *ctx);
 template <class T>
 cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev, bool have_prev, cudaStream_t st);
 

@@ -64,6 +64,32 @@ __global__ void k_chi0(Prob<T> P, T *chi0)
     chi0[i] = P.alpha0[i] + P.ne[c] * P.sigma_out[g];
 }
 
+// chi0 in the three sweep layouts, chi0L[d][g][o] = chi0[c(o, d)][g]: at a
+// node at rest the laboratory opacity of every ordinate is chi0 (Sec. 2.2
+// with u = 0), so the sweep reads it from this small table instead of the
+// per-ordinate chi_lab.
+template <class T>
+__global__ void k_chi0_layout(Prob<T> P, const T *__restrict__ chi0, T *__restrict__ chi0L)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long per = (long long)P.G * P.Nc;
+    if (i >= 3 * per) return;
+    const int d = (int)(i / per);
+    const long long r = i - d * per;
+    const int g = (int)(r / P.Nc);
+    const long long o = r - (long long)g * P.Nc;
+    int ix, iy, iz;
+    if (d == 2) {  // (z, y, x)
+        ix = (int)(o % P.nx); iy = (int)((o / P.nx) % P.ny); iz = (int)(o / ((long long)P.nx * P.ny));
+    } else if (d == 1) {  // (y, z, x)
+        ix = (int)(o % P.nx); iz = (int)((o / P.nx) % P.nz); iy = (int)(o / ((long long)P.nx * P.nz));
+    } else {  // (x, z, y)
+        iy = (int)(o % P.ny); iz = (int)((o / P.ny) % P.nz); ix = (int)(o / ((long long)P.ny * P.nz));
+    }
+    const long long c = ((long long)iz * P.ny + iy) * P.nx + ix;
+    chi0L[i] = chi0[c * P.G + g];
+}
+
 // -------------------------------------------------------------------------
 // a2: S_p(c,g) = n_e/chi0 sum_g' K_l[g][g'] I_p(c,g') + delta_p0 sqrt(4pi) eta0/chi0
 // One CTA per node: the node's I_lm [G][NLM] is staged in shared memory
@@ -202,9 +228,15 @@ __device__ inline void cp_async_n(void *smem, const void *gmem)
         asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES));
 }
 
-template <class T, int U, bool VEC>
+// With `mbits` (16-byte copies only), chi comes from the per-ordinate chi_lab
+// only for the 4-node pieces of a plane that hold a moving node (bit id % 64
+// of mbits[d][id / 64][piece]) and from chi0L elsewhere; the CTA keeps the
+// current 64-plane window of its layout's bits in shared memory.
+template <class T, int U, bool VEC, bool CB>
 __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict__ I, const T *__restrict__ eta,
-                                                        const T *__restrict__ chi)
+                                                        const T *__restrict__ chi, const T *__restrict__ chi0L,
+                                                        const unsigned long long *__restrict__ mbits, int npc,
+                                                        int nwin)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NT = 1024;
@@ -220,7 +252,10 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
     T *pS = pI + pstride;
     T *pC = pS + pstride;
     T *ring = pC + pstride;  // [2][3][pstride]
+    unsigned long long *sbits = reinterpret_cast<unsigned long long *>(ring + 6 * pstride);  // [npc]
     const long long base = ((long long)k * P.G + g) * P.Nc;
+    constexpr bool cbits = VEC && CB;
+    const T *c0base = cbits ? chi0L + ((long long)o.d * P.G + g) * P.Nc : nullptr;
     const T fr1 = (T)o.fr1, fr2 = (T)o.fr2, s = (T)o.s, kap = P.kappa;
     const T w00 = (T(1) - fr1) * (T(1) - fr2), w10 = fr1 * (T(1) - fr2), w01 = (T(1) - fr1) * fr2, w11 = fr1 * fr2;
     const T bc_iso = P.bc_mode == SHD_BC_ISO ? P.bc[g] : T(0);
@@ -249,10 +284,13 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
             T *r = ring + (size_t)(step & 1) * 3 * pstride;
             if constexpr (VEC) {
                 const int nv = plane / V;  // 16-byte pieces per array
-                for (int c = tid; c < 3 * nv; c += NT) {
-                    const int a = c / nv, off = (c - a * nv) * V;
-                    const T *src = a == 0 ? I : (a == 1 ? eta : chi);
-                    cp_async_n<16>(&r[a * pstride + off], &src[pb + off]);
+                for (int q = tid; q < nv; q += NT) cp_async_n<16>(&r[q * V], &I[pb + q * V]);
+                for (int q = tid; q < nv; q += NT) cp_async_n<16>(&r[pstride + q * V], &eta[pb + q * V]);
+                for (int q = tid; q < nv; q += NT) {
+                    const int off = q * V;
+                    const T *src = chi + pb + off;
+                    if (cbits && !((sbits[off >> 2] >> (id & 63)) & 1ull)) src = c0base + (long long)id * plane + off;
+                    cp_async_n<16>(&r[2 * pstride + off], src);
                 }
             } else {
 #pragma unroll
@@ -268,11 +306,24 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
         asm volatile("cp.async.commit_group;\n" ::);
     };
 
+    // the window of moving-piece bits that holds plane `step`
+    int cur_w = -1;
+    auto window = [&](int step) {
+        if (!cbits || step >= nd) return;
+        const int w = (o.sd > 0 ? step : nd - 1 - step) >> 6;
+        if (w == cur_w) return;
+        for (int i = tid; i < npc; i += NT) sbits[i] = mbits[((size_t)o.d * nwin + w) * npc + i];
+        cur_w = w;
+        __syncthreads();
+    };
+
+    window(0);
     issue(0);
     T rI[U], rS[U], rC[U];
     for (int step = 0; step < nd; ++step) {
         asm volatile("cp.async.wait_group 0;\n" ::);
         __syncthreads();  // every copy of this plane and the previous plane's state are visible
+        window(step + 1);
         issue(step + 1);
         const T *r = ring + (size_t)(step & 1) * 3 * pstride;
         const bool first = step == 0;
@@ -528,6 +579,10 @@ cudaError_t launch_chi0(const shd_ctx *ctx, cudaStream_t st)
     long long n = ctx->Nc * ctx->G;
     k_chi0<T><<<blocks_for(n, 256), 256, 0, st>>>(P, (T *)ctx->d_chi0);
     note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !ctx->d_chi0L) return e;
+    k_chi0_layout<T><<<blocks_for(3 * n, 256), 256, 0, st>>>(P, (const T *)ctx->d_chi0, (T *)ctx->d_chi0L);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -558,12 +613,16 @@ static cudaError_t launch_sweep_npt(const shd_ctx *ctx, T *I, const T *eta, cons
 
 template <class T, int U, bool VEC>
 static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st,
-                                     size_t sm)
+                                     size_t sm, bool bits)
 {
     Prob<T> P = make_prob<T>(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_pipe<T, U, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const T *c0L = bits ? (const T *)ctx->d_chi0L : nullptr;
+    const unsigned long long *mb = bits ? ctx->d_mbits : nullptr;
+    if (bits) sm += sizeof(unsigned long long) * (size_t)ctx->mbits_npc;
+    auto kern = bits ? k_sweep_pipe<T, U, VEC, VEC> : k_sweep_pipe<T, U, VEC, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_sweep_pipe<T, U, VEC><<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi);
+    kern<<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi, c0L, mb, ctx->mbits_npc, ctx->mbits_nwin);
     note_launch();
     return cudaGetLastError();
 }
@@ -576,27 +635,44 @@ size_t sweep_pipe_smem_bytes(const shd_ctx *c)
     return c->esize * ps * 9;
 }
 
+// 16-byte copies when every plane and the array base stay 16-byte aligned
 template <class T>
-cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st)
+static bool sweep_vec(const shd_ctx *ctx)
+{
+    constexpr int V = 16 / sizeof(T);
+    return ctx->Nc % V == 0 && ((long long)ctx->nx * ctx->ny) % V == 0 && ((long long)ctx->ny * ctx->nz) % V == 0 &&
+           ((long long)ctx->nx * ctx->nz) % V == 0;
+}
+
+template <class T>
+bool sweep_uses_chi0L(const shd_ctx *ctx)
+{
+    const int u = (sweep_plane_max(ctx) + 1023) / 1024;
+    return ctx->d_chi0L && ctx->d_mbits && sweep_vec<T>(ctx) && u <= 8 &&
+           sweep_pipe_smem_bytes(ctx) + sizeof(unsigned long long) * (size_t)ctx->mbits_npc <= 227 * 1024;
+}
+
+// use_chi0L: the per-ordinate chi is only valid on the pieces that hold a
+// moving node (the stepping path); otherwise every chi value is read.
+template <class T>
+cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st, bool use_chi0L)
 {
     int plane = sweep_plane_max(ctx);
     size_t smp = sweep_pipe_smem_bytes(ctx);
     if (smp <= 227 * 1024) {
-        // 16-byte copies when every plane and the array base stay 16-byte aligned
-        constexpr int V = 16 / sizeof(T);
-        const bool vec = ctx->Nc % V == 0 && ((long long)ctx->nx * ctx->ny) % V == 0 &&
-                         ((long long)ctx->ny * ctx->nz) % V == 0 && ((long long)ctx->nx * ctx->nz) % V == 0;
+        const bool vec = sweep_vec<T>(ctx);
+        const bool bits = use_chi0L && sweep_uses_chi0L<T>(ctx);
         int u = (plane + 1023) / 1024;
         if (vec) {
-            if (u <= 1) return launch_sweep_pipe<T, 1, true>(ctx, I, eta, chi, st, smp);
-            if (u <= 2) return launch_sweep_pipe<T, 2, true>(ctx, I, eta, chi, st, smp);
-            if (u <= 4) return launch_sweep_pipe<T, 4, true>(ctx, I, eta, chi, st, smp);
-            if (u <= 8) return launch_sweep_pipe<T, 8, true>(ctx, I, eta, chi, st, smp);
+            if (u <= 1) return launch_sweep_pipe<T, 1, true>(ctx, I, eta, chi, st, smp, bits);
+            if (u <= 2) return launch_sweep_pipe<T, 2, true>(ctx, I, eta, chi, st, smp, bits);
+            if (u <= 4) return launch_sweep_pipe<T, 4, true>(ctx, I, eta, chi, st, smp, bits);
+            if (u <= 8) return launch_sweep_pipe<T, 8, true>(ctx, I, eta, chi, st, smp, bits);
         } else {
-            if (u <= 1) return launch_sweep_pipe<T, 1, false>(ctx, I, eta, chi, st, smp);
-            if (u <= 2) return launch_sweep_pipe<T, 2, false>(ctx, I, eta, chi, st, smp);
-            if (u <= 4) return launch_sweep_pipe<T, 4, false>(ctx, I, eta, chi, st, smp);
-            if (u <= 8) return launch_sweep_pipe<T, 8, false>(ctx, I, eta, chi, st, smp);
+            if (u <= 1) return launch_sweep_pipe<T, 1, false>(ctx, I, eta, chi, st, smp, false);
+            if (u <= 2) return launch_sweep_pipe<T, 2, false>(ctx, I, eta, chi, st, smp, false);
+            if (u <= 4) return launch_sweep_pipe<T, 4, false>(ctx, I, eta, chi, st, smp, false);
+            if (u <= 8) return launch_sweep_pipe<T, 8, false>(ctx, I, eta, chi, st, smp, false);
         }
     }
     int threads = plane < 1024 ? ((plane + 31) / 32) * 32 : 1024;
@@ -677,7 +753,8 @@ cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, do
     template Prob<T> make_prob<T>(const shd_ctx *);                                                         \
     template cudaError_t launch_chi0<T>(const shd_ctx *, cudaStream_t);                                     \
     template cudaError_t launch_source<T>(const shd_ctx *, const T *, T *, cudaStream_t);                   \
-    template cudaError_t launch_sweep<T>(const shd_ctx *, T *, const T *, const T *, cudaStream_t);         \
+    template cudaError_t launch_sweep<T>(const shd_ctx *, T *, const T *, const T *, cudaStream_t, bool);   \
+    template bool sweep_uses_chi0L<T>(const shd_ctx *);                                                     \
     template cudaError_t launch_sums<T>(shd_ctx *, const T *, const T *, const T *, bool, cudaStream_t);    \
     template cudaError_t launch_canon_to_do<T>(const shd_ctx *, const double *, T *, long long, long long,  \
                                                cudaStream_t);                                               \

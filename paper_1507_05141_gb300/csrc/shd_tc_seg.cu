@@ -92,6 +92,7 @@ struct SegArgs {
     int Kp;             // slots = 32 nchunk
     int nb;             // a1: output columns (rows of Bp) of the MMA
     int accumulate;     // a1: add to I_lm / moments instead of storing
+    int chi_all;        // a3: chi for every row (else only boxes that hold a moving row)
     int4 chunk[16];     // {map index, first ordinate of the chunk within its class,
                         //  internal index of the class's first ordinate, ordinates in the class}
 };
@@ -572,7 +573,9 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
                             asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + j) : "memory");
                         }
                 };
-                if (!eta_w && !anym) {
+                if (!eta_w && !anym && !S.chi_all) {
+                    // every row at rest and the sweep reads chi0 there: nothing to store
+                } else if (!eta_w && !anym) {
                     // every row at rest: one constant chi tile serves every chunk
 #pragma unroll
                     for (int j = 0; j < 16; ++j) W[j * 32 + lane] = chr;
@@ -902,9 +905,11 @@ static cudaError_t run_sh2lab_seg(const shd_ctx *ctx, const Prob<float> &P, cons
 
 // a3: the comoving S0 of moving nodes (node-major, nm0), their remap to the
 // laboratory eta, chi (nm1, nm2), then eta, chi of every node into the sweep
-// layout (moving rows taken from nm1, nm2).
+// layout (moving rows taken from nm1, nm2).  Without full_chi, chi is stored
+// only for the 32-node runs that hold a moving node: every 4-node piece the
+// sweep reads from chi lies in such a run.
 cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,
-                              float *nm2, cudaStream_t st)
+                              float *nm2, cudaStream_t st, bool full_chi)
 {
     Prob<float> P = make_prob<float>(ctx);
     cudaError_t e;
@@ -920,6 +925,7 @@ cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, f
     for (int grp = 0; grp < 2; ++grp) {
         if (ctx->tcs_nchunk[grp] == 0 || ctx->nseg[grp] == 0) continue;
         SegArgs a = seg_args(ctx, grp);
+        a.chi_all = full_chi ? 1 : 0;
         SegMaps maps{};
         if ((e = group_maps(ctx, grp, eta, &maps.m[0], true)) != cudaSuccess) return e;
         if ((e = group_maps(ctx, grp, chi, &maps.m[2], true)) != cudaSuccess) return e;

@@ -836,7 +836,7 @@ cudaError_t launch_project(const shd_ctx *ctx, const T *I, T *Ip, T *mom, cudaSt
 // The contraction writes S0 of moving rows to nm0; their laboratory eta, chi
 // go to nm1, nm2 and are transposed into the sweep layout.
 template <class T>
-cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st)
+cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaStream_t st, bool full_chi)
 {
     Prob<T> P = make_prob<T>(ctx);
     cudaError_t e = cudaSuccess;
@@ -845,7 +845,7 @@ cudaError_t launch_sh2lab(const shd_ctx *ctx, const T *Sp, T *eta, T *chi, cudaS
     if constexpr (sizeof(T) == 4) {
         size_t smp = sh2lab_persist_smem_bytes(ctx);
         // the segment kernels run the remap and write the moving rows themselves
-        if (seg_usable(ctx)) return launch_sh2lab_seg(ctx, Sp, eta, chi, nm0, nm1, nm2, st);
+        if (seg_usable(ctx)) return launch_sh2lab_seg(ctx, Sp, eta, chi, nm0, nm1, nm2, st, full_chi);
         if (tc_usable(ctx)) {
             if ((e = launch_sh2lab_tc(ctx, Sp, eta, chi, nm0, st)) != cudaSuccess) return e;
             done = true;
@@ -895,7 +895,7 @@ template cudaError_t launch_project_scratch<float>(const shd_ctx *, const float 
 
 template cudaError_t launch_project<double>(const shd_ctx *, const double *, double *, double *, cudaStream_t);
 template cudaError_t launch_project<float>(const shd_ctx *, const float *, float *, float *, cudaStream_t);
-template cudaError_t launch_sh2lab<double>(const shd_ctx *, const double *, double *, double *, cudaStream_t);
-template cudaError_t launch_sh2lab<float>(const shd_ctx *, const float *, float *, float *, cudaStream_t);
+template cudaError_t launch_sh2lab<double>(const shd_ctx *, const double *, double *, double *, cudaStream_t, bool);
+template cudaError_t launch_sh2lab<float>(const shd_ctx *, const float *, float *, float *, cudaStream_t, bool);
 
 }  // namespace shd
