@@ -717,11 +717,21 @@ int run_steps(shd_ctx *c, int nsteps, cudaStream_t st)
         if (tm) CK(cudaEventRecord(ev[0], st), "event");
         CK(launch_project<T>(c, (const T *)c->d_I, (T *)c->d_Ip, (T *)c->d_mom, st), "project");
         if (tm) CK(cudaEventRecord(ev[1], st), "event");
-        CK(launch_source<T>(c, (const T *)c->d_Ip, (T *)c->d_Sp, st), "source");
-        if (tm) CK(cudaEventRecord(ev[2], st), "event");
-        CK(launch_sums<T>(c, (const T *)c->d_mom, (const T *)c->d_Sp, (const T *)c->d_Sprev, c->sprev_valid, st),
-           "sums");
-        if (tm) CK(cudaEventRecord(ev[3], st), "event");
+        if (source_sums_usable<T>(c)) {
+            // a2 with the a5 partials in the same pass; the sums stage is the final reduction
+            CK(launch_source_sums<T>(c, (const T *)c->d_Ip, (T *)c->d_Sp, (const T *)c->d_mom,
+                                     (const T *)c->d_Sprev, c->sprev_valid, st),
+               "source and sums");
+            if (tm) CK(cudaEventRecord(ev[2], st), "event");
+            if (tm) CK(cudaEventRecord(ev[3], st), "event");
+        } else {
+            CK(launch_source<T>(c, (const T *)c->d_Ip, (T *)c->d_Sp, st), "source");
+            if (tm) CK(cudaEventRecord(ev[2], st), "event");
+            CK(launch_sums<T>(c, (const T *)c->d_mom, (const T *)c->d_Sp, (const T *)c->d_Sprev, c->sprev_valid,
+                              st),
+               "sums");
+            if (tm) CK(cudaEventRecord(ev[3], st), "event");
+        }
         // the sweep takes chi at nodes at rest from the chi0 layouts, so chi_lab
         // is needed only where a node moves
         const bool c0L = sweep_uses_chi0L<T>(c);

@@ -478,6 +478,11 @@ template <class T>
 bool sweep_uses_chi0L(const shd_ctx *ctx);
 template <class T>
 cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev, bool have_prev, cudaStream_t st);
+template <class T>
+cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, const T *Sprev, bool have_prev,
+                               cudaStream_t st);
+template <class T>
+bool source_sums_usable(const shd_ctx *ctx);
 
 // layout conversions: canonical FP64 [c][g][k] chunk <-> device DO layout
 template <class T>

@@ -123,6 +123,89 @@ __global__ void __launch_bounds__(256) k_source(Prob<T> P, const T *__restrict__
     }
 }
 
+// a2 + a5 fused for the stepping path: one warp per node (persistent grid of
+// n_partial CTAs x 8 warps), the node's I_lm staged in the warp's shared
+// tile, K_l in shared memory with rows padded against bank conflicts.  S_p
+// is formed exactly as k_source forms it; while it is written, every thread
+// accumulates in FP64 the residual |S - S_prev|^2, |S|^2 and, from J of the
+// moments, the energy and photon sums; the CTA's partials go to partial[b][4]
+// for k_sums_final.
+template <class T>
+__global__ void __launch_bounds__(256, 2) k_source_sums(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp,
+                                                     const T *__restrict__ mom, const T *__restrict__ Sprev,
+                                                     int have_prev, double *partial)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4][8];
+    const int G = P.G, NLM = P.NLM, L = P.L;
+    const int KS = G * G + 1;
+    T *sK = reinterpret_cast<T *>(smem_raw);  // [L+1][KS]
+    T *sI = sK + (((size_t)(L + 1) * KS + 1) & ~(size_t)1);  // [8][G][NLM]
+    for (int i = threadIdx.x; i < (L + 1) * G * G; i += blockDim.x) {
+        const int l = i / (G * G);
+        sK[(size_t)l * KS + (i - l * G * G)] = P.K[i];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *wI = sI + (size_t)warp * G * NLM;
+    double e = 0, ph = 0, num = 0, den = 0;
+    for (long long c = (long long)blockIdx.x * 8 + warp; c < P.Nc; c += (long long)gridDim.x * 8) {
+        const long long base = c * G * NLM;
+        for (int i = lane; i < G * NLM; i += 32) wI[i] = Ip[base + i];
+        __syncwarp();
+        const T ne = P.ne[c];
+        for (int p = lane; p < NLM; p += 32) {
+            int l = 0;
+            while ((l + 1) * (l + 1) <= p) ++l;
+            for (int g = 0; g < G; ++g) {
+                const T chi = P.chi0[c * G + g];
+                T s = T(0);
+                if (chi > T(0)) {
+                    const T *Kr = sK + (size_t)l * KS + g * G;
+                    T acc = T(0);
+                    for (int gp = 0; gp < G; ++gp) acc += Kr[gp] * wI[gp * NLM + p];
+                    s = ne / chi * acc;
+                    if (p == 0) s += T(3.5449077018110320546) * P.emis0[c * G + g] / chi;  // sqrt(4 pi)
+                }
+                const long long i = base + (long long)g * NLM + p;
+                Sp[i] = s;
+                const double sn = (double)s;
+                den += sn * sn;
+                if (have_prev) {
+                    const double d = sn - (double)Sprev[i];
+                    num += d * d;
+                }
+            }
+        }
+        for (int g = lane; g < G; g += 32) {
+            const double J = (double)mom[(c * G + g) * 10];
+            const double de = P.edges[g + 1] - P.edges[g];
+            e += 4.0 * kPi * J * de;
+            ph += 4.0 * kPi * J * de / P.centre[g];
+        }
+        __syncwarp();
+    }
+    // fixed-order reduction: lanes by shuffle, then the 8 warps
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_down_sync(0xffffffffu, e, o);
+        ph += __shfl_down_sync(0xffffffffu, ph, o);
+        num += __shfl_down_sync(0xffffffffu, num, o);
+        den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = e;
+        red[1][warp] = ph;
+        red[2][warp] = num;
+        red[3][warp] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double acc = 0;
+        for (int w = 0; w < 8; ++w) acc += red[threadIdx.x][w];
+        partial[blockIdx.x * 4 + threadIdx.x] = acc;
+    }
+}
+
 // -------------------------------------------------------------------------
 // a4: one CTA per (ordinate, group).  Planes normal to the dominant axis are
 // contiguous in the sweep layout and depend only on the previous plane, so
@@ -699,6 +782,35 @@ cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev,
     return cudaGetLastError();
 }
 
+static size_t source_sums_smem(const shd_ctx *c)
+{
+    return c->esize * ((((size_t)(c->L + 1) * (c->G * c->G + 1)) + 1 & ~(size_t)1) + (size_t)8 * c->G * c->NLM);
+}
+
+template <class T>
+bool source_sums_usable(const shd_ctx *ctx)
+{
+    return source_sums_smem(ctx) <= 227 * 1024;
+}
+
+// a2 and the a5 partials in one pass (see k_source_sums), then k_sums_final.
+template <class T>
+cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, const T *Sprev, bool have_prev,
+                               cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    const size_t sm = source_sums_smem(ctx);
+    cudaError_t e = cudaFuncSetAttribute(k_source_sums<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int nb = ctx->n_partial;
+    k_source_sums<T><<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, ctx->d_partial);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_sums_final<<<1, 32, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_canon_to_do(const shd_ctx *ctx, const double *src, T *dst, long long c0, long long nc,
                                cudaStream_t st)
@@ -756,6 +868,9 @@ cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, do
     template cudaError_t launch_sweep<T>(const shd_ctx *, T *, const T *, const T *, cudaStream_t, bool);   \
     template bool sweep_uses_chi0L<T>(const shd_ctx *);                                                     \
     template cudaError_t launch_sums<T>(shd_ctx *, const T *, const T *, const T *, bool, cudaStream_t);    \
+    template cudaError_t launch_source_sums<T>(shd_ctx *, const T *, T *, const T *, const T *, bool,       \
+                                               cudaStream_t);                                               \
+    template bool source_sums_usable<T>(const shd_ctx *);                                                   \
     template cudaError_t launch_canon_to_do<T>(const shd_ctx *, const double *, T *, long long, long long,  \
                                                cudaStream_t);                                               \
     template cudaError_t launch_do_to_canon<T>(const shd_ctx *, const T *, double *, long long, long long,  \

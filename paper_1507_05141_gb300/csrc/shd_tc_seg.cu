@@ -863,7 +863,9 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
     Prob<float> P = make_prob<float>(ctx);
     bool first = true;
     cudaError_t e;
-    for (int grp = 0; grp < 2; ++grp) {
+    // group B (fewer ordinates, short items) stores; group A, whose long items
+    // hide the latency of reading back, accumulates
+    for (int grp : {1, 0}) {
         if (ctx->tcs_nchunk[grp] == 0 || ctx->nseg[grp] == 0) continue;
         SegArgs a = seg_args(ctx, grp);
         a.nb = ctx->NB;
