@@ -35,6 +35,39 @@ WORKLOAD = "relativistic jet 64^3, 16 groups (1e-3..1e1 m_e c^2), L=7, 16x32 ord
 # algorithmic bytes per update of the sweep kernel (FP32): read I^n, eta_lab,
 # chi_lab, write I^{n+1}
 SWEEP_BYTES_PER_UPDATE = {"fp32": 16, "mixed": 16, "fp64": 32}
+# floor of the whole step's traffic per update: the intensity read and written
+# once plus the SH state, about 2 B at L = 7 with 512 ordinates
+STEP_FLOOR_BYTES_PER_UPDATE = {"fp32": 10, "mixed": 10, "fp64": 20}
+
+
+def _sha256(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def sweep_traffic(prec, spec):
+    """DRAM bytes (read + write) of one sweep launch from the committed ncu
+    summary of this workload and precision, or None when there is none or the
+    sweep's source has changed since it was captured."""
+    if spec.grid != (64, 64, 64):
+        return None
+    path = os.path.join(ROOT, "profiles", f"sweep_jet64_{prec}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for ln in f:
+            if ":" in ln and ln.startswith("- "):
+                k, v = ln[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+    src = os.path.join(ROOT, "paper_1507_05141_gb300", "csrc", "shd_kernels.cu")
+    try:
+        if fields.get("shd_kernels.cu sha256") != _sha256(src):
+            return None
+        return int(fields["dram bytes per launch"])
+    except (KeyError, ValueError, OSError):
+        return None
 
 
 def _dist():
@@ -283,17 +316,16 @@ def bench_ours(args):
     e2e_value = upd * e2e_steps * ws / e2e_s
 
     peak, peak_kind = _peaks()
+    do_gb = upd * (8 if prec == "fp64" else 4) / 1e9
     sweep_ms = stage["sweep"]
     sweep_bytes = upd * SWEEP_BYTES_PER_UPDATE[prec]
     achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"sweep_traffic_{prec}.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as f:
-                traffic = json.load(f).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = sweep_traffic(prec, spec)
+    # the whole step against the floor of its own traffic: I^n read and
+    # I^{n+1} written once (8 B at FP32) plus the SH state (I_lm, S_lm, S_prev,
+    # about 2 B per update at L = 7 and 512 ordinates)
+    step_floor = STEP_FLOOR_BYTES_PER_UPDATE[prec]
+    step_achieved = upd * step_floor / (ms / args.steps / 1e3) / 1e9
 
     # the plain-FP32 arm on the same GPU, same workload and timing
     plain = None
@@ -326,7 +358,7 @@ def bench_ours(args):
             "config": {"workload": WORKLOAD if args.grid == 64 else WORKLOAD.replace("64^3", f"{args.grid}^3"),
                        "grid": list(spec.grid), "groups": spec.G, "L": spec.L,
                        "ordinates": spec.N, "precision": prec, "updates_per_step": upd,
-                       "l2": "no flush: the 8.6 GB state is far larger than L2",
+                       "l2": f"no flush: the {do_gb:.1f} GB intensity state is far larger than L2",
                        "parallelism": f"replicas x{ws}"},
             "stage_ms": stage,
             "plain_fp32": plain,
@@ -335,6 +367,8 @@ def bench_ours(args):
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "algorithmic_bytes": f"{SWEEP_BYTES_PER_UPDATE[prec]} B/update x {upd} updates"},
+            "step_roofline": {"bound": "hbm", "floor_bytes_per_update": step_floor, "achieved": step_achieved,
+                              "peak": peak, "unit": "GB/s", "frac": step_achieved / peak},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "gpu_launches": launches,
