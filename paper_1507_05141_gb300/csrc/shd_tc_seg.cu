@@ -666,6 +666,277 @@ done:
 }
 
 // -------------------------------------------------------------------------
+// a3, segment mode, warp-specialised: the serial phases of an item (building
+// A from S, the MMAs) overlap the stores of the previous one.
+//   warps 0-7   eta: quadrant warp & 3 of the rows, 16-column half (warp >> 2)
+//               of every chunk; wait for a job's accumulator, stage eta in
+//               the warp's tile, TMA-store the 32-node x 16-ordinate box
+//   warps 8-15  chi: the same boxes of chi (chi0 at rows at rest, the remap's
+//               chi at moving rows; runs without a moving row skipped unless
+//               every chi is wanted)
+//   warps 16-19 A: row (warp - 16) * 32 + lane of the next item: its chi0 and
+//               moving index, its S row as BF16 hi / lo (canonical)
+//   warp 20     MMA: an item's slots in jobs of <= 256 columns (8 chunks),
+//               each into one of two tensor-memory accumulators of 256
+//               columns, alternating
+// Barriers: metaFull / itemDone per item parity (row tables), aFull / aEmpty
+// (the A operand), tFull / tEmpty per accumulator.
+// -------------------------------------------------------------------------
+__global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
+                                                      const float *__restrict__ Sp, const float *__restrict__ etan,
+                                                      const float *__restrict__ chin,
+                                                      const uint16_t *__restrict__ gYh,
+                                                      const uint16_t *__restrict__ gYl, int Kq, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    if (tc::smem_u32(smem_raw) & 1023) {
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    const int Kp = S.Kp, nchunk = S.nchunk;
+    uint16_t *Yh = reinterpret_cast<uint16_t *>(smem_raw);
+    uint16_t *Yl = Yh + (size_t)Kp * Kq;
+    uint16_t *Ah = Yl + (size_t)Kp * Kq;
+    uint16_t *Al = Ah + (size_t)128 * Kq;
+    float *tiles = reinterpret_cast<float *>(Al + (size_t)128 * Kq);  // [16 warps][2][16][32]
+    float *mchi = tiles + (size_t)16 * 1024;                           // [2][128]
+    int *mrow = reinterpret_cast<int *>(mchi + 256);                   // [2][128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(mrow + 256);
+    uint64_t *metaFull = bars, *itemDone = bars + 2, *aFull = bars + 4, *aEmpty = bars + 5;
+    uint64_t *tFull = bars + 6, *tEmpty = bars + 8;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 10);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = P.G, NLM = P.NLM, N = P.N;
+    {
+        const uint4 *sh = reinterpret_cast<const uint4 *>(gYh), *sl = reinterpret_cast<const uint4 *>(gYl);
+        uint4 *dh = reinterpret_cast<uint4 *>(Yh), *dl = reinterpret_cast<uint4 *>(Yl);
+        const int n16 = Kp * Kq / 8;
+        for (int i = tid; i < n16; i += blockDim.x) {
+            dh[i] = sh[i];
+            dl[i] = sl[i];
+        }
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&metaFull[i], 128);
+            tc::mbar_init(&itemDone[i], 512);
+            tc::mbar_init(&tFull[i], 1);
+            tc::mbar_init(&tEmpty[i], 256);
+        }
+        tc::mbar_init(aFull, 128);
+        tc::mbar_init(aEmpty, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        for (long long i = 0; i < kSegWaitLimit; ++i) {
+            if (tc::mbar_try_wait(bar, parity)) return true;
+            if ((i & 255) == 255 && *abort_flag) return false;
+        }
+        *abort_flag = 1;
+        atomicExch(err, 1);
+        return false;
+    };
+    const int njob = (Kp + 255) / 256;  // jobs per item
+
+    if (warp >= 16 && warp < 20) {
+        // ---------------- A builders ----------------
+        const int r = (warp - 16) * 32 + lane;
+        long long it = 0;
+        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x, ++it) {
+            const long long sg = w / G;
+            const int g = (int)(w - sg * G);
+            const int pb = (int)(it & 1);
+            if (it >= 2 && !wait(&itemDone[pb], (uint32_t)(((it >> 1) - 1) & 1))) break;
+            long long c = 0, src = -1;
+            float ch = 0.f;
+            int m = -1;
+            if (seg_node(P, S, S.segs[sg], r, c)) {
+                ch = P.chi0[c * G + g];
+                m = P.midx[c];
+                if (m < 0) src = (c * G + g) * NLM;
+            }
+            mchi[pb * 128 + r] = ch;
+            mrow[pb * 128 + r] = m;
+            tc::mbar_arrive(&metaFull[pb]);
+            if (it >= 1 && !wait(aEmpty, (uint32_t)((it - 1) & 1))) break;
+            for (int kb = 0; kb < Kq / 8; ++kb) {
+                float v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int p = kb * 8 + i;
+                    v[i] = (src >= 0 && p < NLM) ? Sp[src + p] : 0.f;
+                }
+                uint4 h, l;
+                split2(v[0], v[1], h.x, l.x);
+                split2(v[2], v[3], h.y, l.y);
+                split2(v[4], v[5], h.z, l.z);
+                split2(v[6], v[7], h.w, l.w);
+                const int o = tc::canon_off(r, kb * 8, Kq);
+                *reinterpret_cast<uint4 *>(&Ah[o]) = h;
+                *reinterpret_cast<uint4 *>(&Al[o]) = l;
+            }
+            tc::fence_proxy_async();
+            tc::mbar_arrive(aFull);
+        }
+    } else if (warp == 20) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t a_sbo = (uint32_t)(Kq / 8) * 128, b_sbo = (uint32_t)(Kq / 8) * 128;
+            const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al);
+            long long it = 0, j = 0;
+            bool ok = true;
+            for (long long w = blockIdx.x; w < S.nitem && ok; w += gridDim.x, ++it) {
+                if (!wait(aFull, (uint32_t)(it & 1))) break;
+                for (int h = 0; h < njob; ++h, ++j) {
+                    const int b = (int)(j & 1);
+                    if (j >= 2 && !wait(&tEmpty[b], (uint32_t)(((j >> 1) - 1) & 1))) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const int nh = Kp - 256 * h < 256 ? Kp - 256 * h : 256;
+                    const uint32_t idesc = tc::idesc_bf16(128, nh);
+                    const uint32_t yoff = (uint32_t)(256 / 8) * b_sbo * h;
+                    const uint32_t yh = tc::smem_u32(Yh) + yoff, yl = tc::smem_u32(Yl) + yoff;
+                    const uint32_t d = tmem + (uint32_t)(256 * b);
+                    for (int jj = 0; jj < Kq / 16; ++jj) {
+                        const uint32_t koff = jj * 256;
+                        const uint64_t dah = tc::sdesc(ah + koff, 128, a_sbo), dal = tc::sdesc(al + koff, 128, a_sbo);
+                        const uint64_t dbh = tc::sdesc(yh + koff, 128, b_sbo), dbl = tc::sdesc(yl + koff, 128, b_sbo);
+                        tc::mma_bf16(d, dah, dbh, idesc, jj > 0 ? 1u : 0u);
+                        tc::mma_bf16(d, dah, dbl, idesc, 1u);
+                        tc::mma_bf16(d, dal, dbh, idesc, 1u);
+                    }
+                    tc::mma_commit(&tFull[b]);
+                }
+                if (ok) tc::mma_commit(aEmpty);
+            }
+            // no MMA may still be running when the tensor memory is freed
+            if (it > 0) tc::mbar_wait(aEmpty, (uint32_t)((it - 1) & 1), kSegWaitLimit);
+        }
+    } else if (warp < 16) {
+        // ---------------- epilogue: eta (warps 0-7), chi (8-15) ----------------
+        const bool eta_w = warp < 8;
+        const int quad = warp & 3, half = (warp >> 2) & 1;
+        const int r = quad * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+        float *W = tiles + (size_t)warp * 1024;  // [2][16][32]
+        const float *nsrc = eta_w ? etan : chin;
+        const CUtensorMap *mp_base = &maps.m[eta_w ? 0 : 2];
+        long long it = 0, j = 0;
+        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x, ++it) {
+            const long long sg = w / G;
+            const int g = (int)(w - sg * G);
+            const int pb = (int)(it & 1);
+            const int4 sd = S.segs[sg];
+            const int r0 = quad * 32;
+            const int as = sd.y + r0 % S.bw, bs = sd.z + r0 / S.bw;
+            if (!wait(&metaFull[pb], (uint32_t)((it >> 1) & 1))) break;
+            const float chr = mchi[pb * 128 + r];
+            const int m = mrow[pb * 128 + r];
+            const long long nbase = m >= 0 ? ((long long)m * G + g) * N : 0;
+            const bool anym = __any_sync(0xffffffffu, m >= 0);
+            // the previous item's stores have read this warp's tiles
+            if (lane == 0) tc::bulk_wait_read<0>();
+            __syncwarp();
+            auto store = [&](int cn, const float *src) {
+                const int4 ci = S.chunk[cn];
+                const int kk = ci.y + 16 * half;
+                const bool yc = !S.groupB && ci.x == 1;
+                tc::tma_store_5d(mp_base + ci.x, as, yc ? sd.x : bs, yc ? bs : sd.x, g, kk, src);
+            };
+            auto prefetch = [&](int cn, int b) {
+                if (m < 0) return;
+                const int4 ci = S.chunk[cn];
+                const int kl0 = ci.y + 16 * half;
+                const float *src = nsrc + nbase + ci.z + kl0;
+                float *dst = W + (size_t)b * 512 + lane;
+                for (int q = 0; q < 16; ++q)
+                    if (kl0 + q < ci.w) {
+                        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + q * 32);
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + q) : "memory");
+                    }
+            };
+            bool ok = true;
+            if (!eta_w && !anym) {
+                if (S.chi_all) {
+                    // every row at rest: one constant chi tile serves every chunk
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) W[q * 32 + lane] = chr;
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        for (int cn = 0; cn < nchunk; ++cn) store(cn, W);
+                        tc::bulk_commit();
+                    }
+                }
+            } else {
+                if (anym) prefetch(0, 0);
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                int jb = -1;  // accumulator of the current job
+                for (int cn = 0; cn < nchunk; ++cn) {
+                    const int h = cn >> 3;
+                    if (eta_w && (cn & 7) == 0) {
+                        if (jb >= 0) {
+                            tc::fence_before_sync();
+                            tc::mbar_arrive(&tEmpty[jb]);
+                        }
+                        jb = (int)((j + h) & 1);
+                        if (!wait(&tFull[jb], (uint32_t)(((j + h) >> 1) & 1))) { ok = false; break; }
+                        tc::fence_after_sync();
+                    }
+                    const int b = cn & 1;
+                    if (lane == 0) {
+                        if (anym) tc::bulk_wait_read<0>();
+                        else tc::bulk_wait_read<1>();
+                    }
+                    __syncwarp();
+                    if (anym && cn + 1 < nchunk) prefetch(cn + 1, b ^ 1);
+                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                    float *Wb = W + (size_t)b * 512 + lane;
+                    if (eta_w) {
+                        float v[16];
+                        tc::tmem_ld16(trow + (uint32_t)(256 * jb + (cn & 7) * kKC + 16 * half), v);
+                        if (m < 0) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) Wb[q * 32] = chr * v[q];
+                        }
+                    } else if (m < 0) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) Wb[q * 32] = chr;
+                    }
+                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        store(cn, W + (size_t)b * 512);
+                        tc::bulk_commit();
+                    }
+                }
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                if (eta_w && ok && jb >= 0) {
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&tEmpty[jb]);
+                }
+            }
+            if (!ok) break;
+            j += njob;
+            tc::mbar_arrive(&itemDone[pb]);
+        }
+        if (lane == 0) tc::bulk_wait_all();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// -------------------------------------------------------------------------
 // host side
 // -------------------------------------------------------------------------
 static constexpr size_t kSegSmemLimit = 227 * 1024;
@@ -677,6 +948,10 @@ static size_t project_seg_smem(int nb, int Kp, int nstg, int nr)
 static size_t sh2lab_seg_smem(int Kp, int Kq)
 {
     return (size_t)4 * Kp * Kq + (size_t)4 * 128 * Kq + (size_t)4 * kBox * 4 + 128 * (8 + 4 + 4) + 8 + 8;
+}
+static size_t sh2lab_ws_smem(int Kp, int Kq)
+{
+    return (size_t)4 * Kp * Kq + (size_t)4 * 128 * Kq + (size_t)16 * 1024 * 4 + 2 * 128 * (4 + 4) + 10 * 8 + 8;
 }
 
 // staging / ring depths that fit: 0 when nothing does
@@ -727,7 +1002,7 @@ bool seg_usable(const shd_ctx *c)
         if (!c->d_seg[grp] || !c->d_tcs_Bh[grp] || !c->d_tcs_Yh[grp]) return false;
         if (c->tcs_Kp[grp] > 512 || c->tcs_nchunk[grp] > 16) return false;
         if (!pick_depths(c->NB, c->tcs_Kp[grp], a, b)) return false;
-        if (sh2lab_seg_smem(c->tcs_Kp[grp], c->tc_Kq) > kSegSmemLimit) return false;
+        if (sh2lab_ws_smem(c->tcs_Kp[grp], c->tc_Kq) > kSegSmemLimit) return false;
     }
     if (c->nmoving > 0) {
         if (!pick_depths(nlm16(c), c->tc_Kp, a, b)) return false;
@@ -931,9 +1206,16 @@ cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, f
         SegMaps maps{};
         if ((e = group_maps(ctx, grp, eta, &maps.m[0], true)) != cudaSuccess) return e;
         if ((e = group_maps(ctx, grp, chi, &maps.m[2], true)) != cudaSuccess) return e;
-        if ((e = run_sh2lab_seg<0>(ctx, P, maps, a, Sp, nm1, nm2, ctx->d_tcs_Yh[grp], ctx->d_tcs_Yl[grp], st)) !=
+        const size_t sm = sh2lab_ws_smem(a.Kp, ctx->tc_Kq);
+        if ((e = cudaFuncSetAttribute(k_sh2lab_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
             cudaSuccess)
             return e;
+        int grid = num_sms_seg(ctx);
+        if (a.nitem < grid) grid = (int)a.nitem;
+        k_sh2lab_ws<<<grid, 672, sm, st>>>(P, maps, a, Sp, nm1, nm2, (const uint16_t *)ctx->d_tcs_Yh[grp],
+                                           (const uint16_t *)ctx->d_tcs_Yl[grp], ctx->tc_Kq, ctx->d_tc_err);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
