@@ -768,21 +768,35 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
             mrow[pb * 128 + r] = m;
             tc::mbar_arrive(&metaFull[pb]);
             if (it >= 1 && !wait(aEmpty, (uint32_t)((it - 1) & 1))) break;
-            for (int kb = 0; kb < Kq / 8; ++kb) {
-                float v[8];
+            // the row in rounds of 32 harmonics: all of a round's loads are in
+            // flight together (16-byte loads when the rows are 16-byte aligned)
+            const bool vec = (NLM & 3) == 0;
+            for (int p0 = 0; p0 < Kq; p0 += 32) {
+                float v[32];
+                if (vec) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int p = kb * 8 + i;
-                    v[i] = (src >= 0 && p < NLM) ? Sp[src + p] : 0.f;
+                    for (int q = 0; q < 8; ++q) {
+                        const int p = p0 + 4 * q;
+                        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (src >= 0 && p < NLM) t = *reinterpret_cast<const float4 *>(Sp + src + p);
+                        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) v[q] = (src >= 0 && p0 + q < NLM) ? Sp[src + p0 + q] : 0.f;
                 }
-                uint4 h, l;
-                split2(v[0], v[1], h.x, l.x);
-                split2(v[2], v[3], h.y, l.y);
-                split2(v[4], v[5], h.z, l.z);
-                split2(v[6], v[7], h.w, l.w);
-                const int o = tc::canon_off(r, kb * 8, Kq);
-                *reinterpret_cast<uint4 *>(&Ah[o]) = h;
-                *reinterpret_cast<uint4 *>(&Al[o]) = l;
+#pragma unroll
+                for (int kb = 0; kb < 4; ++kb) {
+                    if (p0 + kb * 8 >= Kq) break;
+                    uint4 h, l;
+                    split2(v[8 * kb], v[8 * kb + 1], h.x, l.x);
+                    split2(v[8 * kb + 2], v[8 * kb + 3], h.y, l.y);
+                    split2(v[8 * kb + 4], v[8 * kb + 5], h.z, l.z);
+                    split2(v[8 * kb + 6], v[8 * kb + 7], h.w, l.w);
+                    const int o = tc::canon_off(r, p0 + kb * 8, Kq);
+                    *reinterpret_cast<uint4 *>(&Ah[o]) = h;
+                    *reinterpret_cast<uint4 *>(&Al[o]) = l;
+                }
             }
             tc::fence_proxy_async();
             tc::mbar_arrive(aFull);
