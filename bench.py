@@ -61,9 +61,11 @@ def sweep_traffic(prec, spec):
             if ":" in ln and ln.startswith("- "):
                 k, v = ln[2:].split(":", 1)
                 fields[k.strip()] = v.strip().strip("`")
-    src = os.path.join(ROOT, "paper_1507_05141_gb300", "csrc", "shd_kernels.cu")
+    csrc = os.path.join(ROOT, "paper_1507_05141_gb300", "csrc")
     try:
-        if fields.get("shd_kernels.cu sha256") != _sha256(src):
+        if fields.get("shd_kernels.cu sha256") != _sha256(os.path.join(csrc, "shd_kernels.cu")):
+            return None
+        if fields.get("shd_internal.cuh sha256") != _sha256(os.path.join(csrc, "shd_internal.cuh")):
             return None
         return int(fields["dram bytes per launch"])
     except (KeyError, ValueError, OSError):

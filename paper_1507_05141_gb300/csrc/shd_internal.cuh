@@ -426,9 +426,21 @@ __device__ inline void sc_weights<double>(double x, double &e, double &wp, doubl
     wu = a0 - e;
 }
 
+// Above this optical depth the single-precision exponential loses more than
+// ~1e-6 relative accuracy (its argument carries x times the rounding of the
+// scaling): the weights are then taken in FP64.
+constexpr float kFp64Tau = 16.f;
+
 template <>
 __device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu)
 {
+    if (x > kFp64Tau) {
+        const double xd = x, ed = exp(-xd), a0 = (1.0 - ed) / xd;
+        e = (float)ed;
+        wp = (float)(1.0 - a0);
+        wu = (float)(a0 - ed);
+        return;
+    }
     e = __expf(-x);
     if (x < 0.5f) {
         wp = x * (1.f / 2 - x * (1.f / 6 - x * (1.f / 24 - x * (1.f / 120 - x * (1.f / 720 - x * (1.f / 5040 - x * (1.f / 40320 - x / 362880.f)))))));

@@ -309,3 +309,25 @@ def test_steps_mixed_tma_tiles(native, grid):
     assert rel(Ish, Ish_r) < MIXED_TOL
     f = O.moments_to_eddington(J, K)
     assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("mixed", MIXED_TOL)])
+def test_steps_optically_thick(native, precision, tol):
+    """A box 400 times more opaque than the relaxation problem (optical depth
+    of 100 and more per node step): the FP32 sweep takes the transfer weights
+    in FP64 there.  Two steps against the oracle."""
+    import dataclasses
+    base = inputs.relax_box(n=12)
+    spec = dataclasses.replace(base, alpha0=base.alpha0 * 400.0, ne=base.ne * 400.0, emis0=base.emis0 * 400.0)
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision=precision)
+    I0 = inputs.random_state(spec, seed=3)
+    s.set_state(I0)
+    s.step(2)
+    J, H, K = s.moments()
+    I_ref, _, _ = P.step(I0, 2)
+    _, J_r, H_r, K_r = P.project(I_ref)
+    assert rel_elem(J, J_r) < tol
+    assert rel(H, H_r) < tol
+    f = O.moments_to_eddington(J, K)
+    assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < tol
