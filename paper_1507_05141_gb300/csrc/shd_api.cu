@@ -19,6 +19,18 @@
 
 using namespace shd;
 
+namespace shd {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace shd
+
+namespace {
+unsigned long long shd_launch_count_now() { return shd::g_launches.load(std::memory_order_relaxed); }
+// kernels of a captured graph are counted when it is replayed, not when captured
+void forget_launches(unsigned long long n) { shd::g_launches.fetch_sub(n, std::memory_order_relaxed); }
+void count_launches(unsigned long long n) { shd::g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace
+
 namespace {
 
 thread_local char g_err[512] = "";
@@ -708,40 +720,105 @@ int ready_for_step(shd_ctx *c)
     return SHD_OK;
 }
 
+// The kernels of one step on stream st (timing events around the stages when
+// ev is given); S_lm / S_prev are not swapped here.
 template <class T>
-int run_steps(shd_ctx *c, int nsteps, cudaStream_t st)
+int step_once(shd_ctx *c, cudaStream_t st, cudaEvent_t *ev)
+{
+    const bool tm = ev != nullptr;
+    if (tm) CK(cudaEventRecord(ev[0], st), "event");
+    CK(launch_project<T>(c, (const T *)c->d_I, (T *)c->d_Ip, (T *)c->d_mom, st), "project");
+    if (tm) CK(cudaEventRecord(ev[1], st), "event");
+    if (source_sums_usable<T>(c)) {
+        // a2 with the a5 partials in the same pass; the sums stage is the final reduction
+        CK(launch_source_sums<T>(c, (const T *)c->d_Ip, (T *)c->d_Sp, (const T *)c->d_mom, (const T *)c->d_Sprev,
+                                 c->sprev_valid, st),
+           "source and sums");
+        if (tm) CK(cudaEventRecord(ev[2], st), "event");
+        if (tm) CK(cudaEventRecord(ev[3], st), "event");
+    } else {
+        CK(launch_source<T>(c, (const T *)c->d_Ip, (T *)c->d_Sp, st), "source");
+        if (tm) CK(cudaEventRecord(ev[2], st), "event");
+        CK(launch_sums<T>(c, (const T *)c->d_mom, (const T *)c->d_Sp, (const T *)c->d_Sprev, c->sprev_valid, st),
+           "sums");
+        if (tm) CK(cudaEventRecord(ev[3], st), "event");
+    }
+    // the sweep takes chi at nodes at rest from the chi0 layouts, so chi_lab
+    // is needed only where a node moves
+    const bool c0L = sweep_uses_chi0L<T>(c);
+    CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st, !c0L), "sh2lab");
+    if (tm) CK(cudaEventRecord(ev[4], st), "event");
+    CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st, c0L), "sweep");
+    if (tm) CK(cudaEventRecord(ev[5], st), "event");
+    return SHD_OK;
+}
+
+void drop_graphs(shd_ctx *c)
+{
+    for (int i = 0; i < 2; ++i) {
+        if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
+        c->gexec[i] = nullptr;
+        c->graph_sp[i] = nullptr;
+        c->graph_kernels[i] = 0;
+    }
+}
+
+// Capture one step, as the context stands, into graph slot i.
+template <class T>
+int capture_step(shd_ctx *c, int i)
+{
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+    const unsigned long long n0 = shd_launch_count_now();
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    const int rc = step_once<T>(c, c->cap_stream, nullptr);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+    const unsigned long long n = shd_launch_count_now() - n0;
+    forget_launches(n);  // captured, not launched
+    cudaGetLastError();
+    if (rc != SHD_OK || ee != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        c->graphs_off = true;
+        return SHD_OK;  // the caller launches directly
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        c->graphs_off = true;
+        return SHD_OK;
+    }
+    c->gexec[i] = exec;
+    c->graph_sp[i] = c->d_Sp;
+    c->graph_kernels[i] = n;
+    return SHD_OK;
+}
+
+template <class T>
+int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false)
 {
     for (int s = 0; s < nsteps; ++s) {
         bool tm = c->timing.on && c->timing.count < Timing::kCap;
         cudaEvent_t *ev = tm ? &c->timing.pool[(size_t)c->timing.count * (Timing::kStages + 1)] : nullptr;
-        if (tm) CK(cudaEventRecord(ev[0], st), "event");
-        CK(launch_project<T>(c, (const T *)c->d_I, (T *)c->d_Ip, (T *)c->d_mom, st), "project");
-        if (tm) CK(cudaEventRecord(ev[1], st), "event");
-        if (source_sums_usable<T>(c)) {
-            // a2 with the a5 partials in the same pass; the sums stage is the final reduction
-            CK(launch_source_sums<T>(c, (const T *)c->d_Ip, (T *)c->d_Sp, (const T *)c->d_mom,
-                                     (const T *)c->d_Sprev, c->sprev_valid, st),
-               "source and sums");
-            if (tm) CK(cudaEventRecord(ev[2], st), "event");
-            if (tm) CK(cudaEventRecord(ev[3], st), "event");
-        } else {
-            CK(launch_source<T>(c, (const T *)c->d_Ip, (T *)c->d_Sp, st), "source");
-            if (tm) CK(cudaEventRecord(ev[2], st), "event");
-            CK(launch_sums<T>(c, (const T *)c->d_mom, (const T *)c->d_Sp, (const T *)c->d_Sprev, c->sprev_valid,
-                              st),
-               "sums");
-            if (tm) CK(cudaEventRecord(ev[3], st), "event");
+        // a replay of the captured step: a step with S_prev, no timing events
+        if (graphs && !tm && c->sprev_valid && !c->graphs_off) {
+            int i = c->graph_sp[0] == c->d_Sp ? 0 : (c->graph_sp[1] == c->d_Sp ? 1 : -1);
+            if (i < 0) {
+                i = c->gexec[0] ? 1 : 0;
+                int rc = capture_step<T>(c, i);
+                if (rc) return rc;
+            }
+            if (!c->graphs_off) {
+                CK(cudaGraphLaunch(c->gexec[i], st), "graph launch");
+                count_launches(c->graph_kernels[i]);
+                std::swap(c->d_Sp, c->d_Sprev);
+                continue;
+            }
         }
-        // the sweep takes chi at nodes at rest from the chi0 layouts, so chi_lab
-        // is needed only where a node moves
-        const bool c0L = sweep_uses_chi0L<T>(c);
-        CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st, !c0L), "sh2lab");
-        if (tm) CK(cudaEventRecord(ev[4], st), "event");
-        CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st, c0L), "sweep");
-        if (tm) {
-            CK(cudaEventRecord(ev[5], st), "event");
-            c->timing.count++;
-        }
+        int rc = step_once<T>(c, st, ev);
+        if (rc) return rc;
+        if (tm) c->timing.count++;
         std::swap(c->d_Sp, c->d_Sprev);
         c->sprev_valid = true;
     }
@@ -753,14 +830,10 @@ int run_steps(shd_ctx *c, int nsteps, cudaStream_t st)
 // ===========================================================================
 // C ABI
 // ===========================================================================
-namespace shd {
-static std::atomic<unsigned long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-}  // namespace shd
 
 extern "C" {
 
-unsigned long long shd_launch_count(void) { return shd::g_launches.load(std::memory_order_relaxed); }
+unsigned long long shd_launch_count(void) { return shd_launch_count_now(); }
 
 const char *shd_last_error(void) { return g_err; }
 
@@ -798,8 +871,11 @@ void shd_destroy(shd_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaDeviceSynchronize();  // graph replays may run on callers' streams
+    drop_graphs(c);
     free_all(c);
     for (cudaEvent_t e : c->timing.pool) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -808,6 +884,7 @@ int shd_set_grid(shd_ctx *c, int nx, int ny, int nz, double lx, double ly, doubl
 {
     int rc = ctx_check(c);
     if (rc) return rc;
+    drop_graphs(c);  // the captured step holds the old parameters
     if (nx < 2 || ny < 2 || nz < 2) return fail(SHD_ERR_ARG, "every grid dimension must be >= 2");
     if (!(lx > 0 && ly > 0 && lz > 0) || !std::isfinite(lx) || !std::isfinite(ly) || !std::isfinite(lz))
         return fail(SHD_ERR_ARG, "box lengths must be positive and finite");
@@ -827,6 +904,7 @@ int shd_set_angles(shd_ctx *c, int L, int n_mu, int n_phi)
 {
     int rc = ctx_check(c);
     if (rc) return rc;
+    drop_graphs(c);  // the captured step holds the old parameters
     if (L < 0 || L > 9) return fail(SHD_ERR_ARG, "L must be in [0, 9]");
     if (n_mu < L + 1 || n_phi < 2 * L + 1) return fail(SHD_ERR_ARG, "need n_mu >= L+1 and n_phi >= 2L+1");
     if (n_mu < 1 || n_phi < 1 || (long long)n_mu * n_phi > 4096) return fail(SHD_ERR_ARG, "n_mu*n_phi must be in [1, 4096]");
@@ -857,6 +935,7 @@ int shd_set_groups(shd_ctx *c, int G, const double *edges)
 {
     int rc = ctx_check(c);
     if (rc) return rc;
+    drop_graphs(c);  // the captured step holds the old parameters
     if (G < 1 || G > 256 || !edges) return fail(SHD_ERR_ARG, "need 1 <= G <= 256 and edges");
     for (int g = 0; g <= G; ++g)
         if (!std::isfinite(edges[g]) || edges[g] <= 0.0 || (g > 0 && !(edges[g] > edges[g - 1])))
@@ -911,7 +990,15 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         if ((rc = upload_reals<float>(c, u, c->d_u, 3 * c->Nc))) return rc;
         if ((rc = upload_reals<float>(c, emis0, c->d_emis0, nCG))) return rc;
     }
-    if ((rc = build_tiles(c, u))) return rc;
+    // the node tables (and with them the captured step) change only when the
+    // set of moving nodes does; new field values are read in place
+    std::vector<unsigned char> mf((size_t)c->Nc);
+    for (long long i = 0; i < c->Nc; ++i) mf[i] = (u[3 * i] != 0.0 || u[3 * i + 1] != 0.0 || u[3 * i + 2] != 0.0);
+    if (!c->have_fields || mf != c->h_mflag) {
+        drop_graphs(c);
+        if ((rc = build_tiles(c, u))) return rc;
+        c->h_mflag.swap(mf);
+    }
     c->have_fields = true;
     if (c->have_scat) {
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
@@ -924,6 +1011,7 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
 {
     int rc = ctx_check(c);
     if (rc) return rc;
+    drop_graphs(c);  // the captured step holds the old parameters
     if (!c->have_angles || !c->have_groups) return fail(SHD_ERR_STATE, "angles and groups must be set first");
     if ((rc = ensure_buffers(c))) return rc;
     int G = c->G, L = c->L;
@@ -1005,6 +1093,7 @@ int shd_set_boundary(shd_ctx *c, int mode, const double *data)
 {
     int rc = ctx_check(c);
     if (rc) return rc;
+    drop_graphs(c);  // the captured step holds the old parameters
     if (mode == SHD_BC_VACUUM) {
         dfree(c->d_bc);
         c->bc_mode = mode;
@@ -1037,6 +1126,7 @@ int shd_set_time(shd_ctx *c, double kappa)
 {
     int rc = ctx_check(c);
     if (rc) return rc;
+    drop_graphs(c);  // the captured step holds the old parameters
     if (!std::isfinite(kappa) || kappa < 0) return fail(SHD_ERR_ARG, "kappa must be finite and >= 0");
     c->kappa = kappa;
     return SHD_OK;
@@ -1117,7 +1207,7 @@ int shd_step(shd_ctx *c, int nsteps, void *stream)
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     // order against the library's own stream (uploads, reads) both ways
     if ((rc = stream_after(st, c->stream))) return rc;
-    rc = is_fp64(c) ? run_steps<double>(c, nsteps, st) : run_steps<float>(c, nsteps, st);
+    rc = is_fp64(c) ? run_steps<double>(c, nsteps, st, true) : run_steps<float>(c, nsteps, st, true);
     if (rc) return rc;
     return stream_after(c->stream, st);
 }

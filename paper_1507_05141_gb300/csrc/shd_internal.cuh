@@ -152,6 +152,7 @@ struct shd_ctx {
     long long *d_moving = nullptr;    // moving node ids
     long long nmoving = 0;
     unsigned char *d_mflag = nullptr; // [Nc]
+    std::vector<unsigned char> h_mflag;  // host copy of the moving flags the tables were built for
     void *d_Bproj = nullptr;          // [N][NB]
     int NB = 0;
     int *d_midx = nullptr;            // [Nc] moving index or -1
@@ -188,6 +189,15 @@ struct shd_ctx {
     bool sprev_valid = false;
 
     shd::Timing timing;
+
+    // one time step captured as a CUDA graph per parity of the S_lm / S_prev
+    // pair (graph_sp[i]: the buffer that step writes S_lm to); dropped by
+    // every setter, rebuilt on the next step
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    void *graph_sp[2] = {nullptr, nullptr};
+    unsigned long long graph_kernels[2] = {0, 0};  // kernel launches per replay
+    cudaStream_t cap_stream = nullptr;
+    bool graphs_off = false;  // a capture failed: launch directly from then on
 };
 
 namespace shd {
@@ -431,14 +441,19 @@ __device__ inline void sc_weights<double>(double x, double &e, double &wp, doubl
 // scaling): the weights are then taken in FP64.
 constexpr float kFp64Tau = 16.f;
 
+__device__ __noinline__ inline void sc_weights_fp64(float x, float &e, float &wp, float &wu)
+{
+    const double xd = x, ed = exp(-xd), a0 = (1.0 - ed) / xd;
+    e = (float)ed;
+    wp = (float)(1.0 - a0);
+    wu = (float)(a0 - ed);
+}
+
 template <>
 __device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu)
 {
     if (x > kFp64Tau) {
-        const double xd = x, ed = exp(-xd), a0 = (1.0 - ed) / xd;
-        e = (float)ed;
-        wp = (float)(1.0 - a0);
-        wu = (float)(a0 - ed);
+        sc_weights_fp64(x, e, wp, wu);
         return;
     }
     e = __expf(-x);
