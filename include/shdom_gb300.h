@@ -198,6 +198,30 @@ int shd_get_timing(shd_ctx *ctx, double *stage_ms, long long *steps);
  * kernels that region ran.  Never fails. */
 unsigned long long shd_launch_count(void);
 
+/* ---- many independent problems -------------------------------------------
+ * Independent problems of uneven size (grid, groups, angular order, flow,
+ * precision) stepped together: every step of a batch is one CUDA graph launch
+ * holding one captured time step per problem as independent branches, so the
+ * problems' kernels run side by side on the GPU.  Each problem is one step of
+ * the paper's method (Sec. 2, Sec. 2.1) as shd_step defines it.
+ *
+ * shd_batch_create: a batch over nprob (>= 1) configured contexts on one
+ *   device.  The batch does not own them: they must outlive it, and results
+ *   are read from each context (shd_get_moments, shd_get_sums, ...).  A context
+ *   may belong to several batches; setters on a context are allowed between
+ *   batch steps.  Errors: SHD_ERR_ARG (NULL or mixed devices), SHD_ERR_OOM.
+ * shd_batch_step: nsteps time steps of every problem on cuda_stream (NULL =
+ *   the first problem's stream), ordered after earlier work of every
+ *   problem's own stream and before its later work.  A problem's first step
+ *   after its state was set, and every step while its per-stage timing is on,
+ *   runs as direct launches.  Errors: those of shd_step, per problem (the
+ *   message names it).
+ * shd_batch_destroy: frees the batch (not the contexts). */
+typedef struct shd_batch shd_batch;
+int shd_batch_create(shd_batch **out, int nprob, shd_ctx *const *problems);
+int shd_batch_step(shd_batch *batch, int nsteps, void *cuda_stream);
+void shd_batch_destroy(shd_batch *batch);
+
 /* ---- projection without allocation --------------------------------------
  * No counterpart in the paper.  For callers that cannot call cudaMalloc when
  * they need the moments: programs whose device memory belongs to another

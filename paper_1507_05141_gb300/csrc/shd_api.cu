@@ -757,10 +757,13 @@ void drop_graphs(shd_ctx *c)
 {
     for (int i = 0; i < 2; ++i) {
         if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
+        if (c->graph[i]) cudaGraphDestroy(c->graph[i]);
         c->gexec[i] = nullptr;
+        c->graph[i] = nullptr;
         c->graph_sp[i] = nullptr;
         c->graph_kernels[i] = 0;
     }
+    c->graph_gen++;
 }
 
 // Capture one step, as the context stands, into graph slot i.
@@ -783,15 +786,36 @@ int capture_step(shd_ctx *c, int i)
     }
     cudaGraphExec_t exec = nullptr;
     const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
     if (ei != cudaSuccess) {
+        cudaGraphDestroy(graph);
         cudaGetLastError();
         c->graphs_off = true;
         return SHD_OK;
     }
+    c->graph[i] = graph;  // kept: a batch step embeds it as a child graph
     c->gexec[i] = exec;
     c->graph_sp[i] = c->d_Sp;
     c->graph_kernels[i] = n;
+    c->graph_gen++;
+    return SHD_OK;
+}
+
+// The graph slot of the context's next step (capturing it if needed), or -1
+// when that step runs as direct launches.
+template <class T>
+int graph_slot(shd_ctx *c, int &slot)
+{
+    slot = -1;
+    const bool tm = c->timing.on && c->timing.count < Timing::kCap;
+    if (tm || !c->sprev_valid || c->graphs_off) return SHD_OK;
+    int i = c->graph_sp[0] == c->d_Sp ? 0 : (c->graph_sp[1] == c->d_Sp ? 1 : -1);
+    if (i < 0) {
+        i = c->gexec[0] ? 1 : 0;
+        int rc = capture_step<T>(c, i);
+        if (rc) return rc;
+        if (c->graphs_off) return SHD_OK;
+    }
+    slot = i;
     return SHD_OK;
 }
 
@@ -802,14 +826,11 @@ int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false)
         bool tm = c->timing.on && c->timing.count < Timing::kCap;
         cudaEvent_t *ev = tm ? &c->timing.pool[(size_t)c->timing.count * (Timing::kStages + 1)] : nullptr;
         // a replay of the captured step: a step with S_prev, no timing events
-        if (graphs && !tm && c->sprev_valid && !c->graphs_off) {
-            int i = c->graph_sp[0] == c->d_Sp ? 0 : (c->graph_sp[1] == c->d_Sp ? 1 : -1);
-            if (i < 0) {
-                i = c->gexec[0] ? 1 : 0;
-                int rc = capture_step<T>(c, i);
-                if (rc) return rc;
-            }
-            if (!c->graphs_off) {
+        if (graphs) {
+            int i;
+            int rc = graph_slot<T>(c, i);
+            if (rc) return rc;
+            if (i >= 0) {
                 CK(cudaGraphLaunch(c->gexec[i], st), "graph launch");
                 count_launches(c->graph_kernels[i]);
                 std::swap(c->d_Sp, c->d_Sprev);
@@ -1397,6 +1418,128 @@ int shd_get_timing(shd_ctx *c, double *stage_ms, long long *steps)
         for (int q = 0; q < Timing::kStages; ++q) stage_ms[q] = ms[q];
     if (steps) *steps = n;
     return SHD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches of independent problems
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct shd_batch {
+    std::vector<shd_ctx *> probs;
+    int device = 0;
+    // cached graphs of one batch step: the key is each problem's graph
+    // generation and slot (slot -1: that problem steps by direct launches)
+    struct Entry {
+        std::vector<std::pair<unsigned long long, int>> key;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<Entry> cache;
+};
+
+namespace {
+void batch_drop(shd_batch *b)
+{
+    for (auto &e : b->cache)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    b->cache.clear();
+}
+}  // namespace
+
+extern "C" {
+
+int shd_batch_create(shd_batch **out, int nprob, shd_ctx *const *problems)
+{
+    if (!out) return fail(SHD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1 || !problems) return fail(SHD_ERR_ARG, "need at least one problem");
+    for (int i = 0; i < nprob; ++i) {
+        if (!problems[i]) return fail(SHD_ERR_ARG, "problem %d is NULL", i);
+        if (problems[i]->device != problems[0]->device) return fail(SHD_ERR_ARG, "problems on different devices");
+    }
+    shd_batch *b = new (std::nothrow) shd_batch;
+    if (!b) return fail(SHD_ERR_OOM, "batch");
+    b->probs.assign(problems, problems + nprob);
+    b->device = problems[0]->device;
+    *out = b;
+    return SHD_OK;
+}
+
+int shd_batch_step(shd_batch *b, int nsteps, void *stream)
+{
+    if (!b) return fail(SHD_ERR_ARG, "null batch");
+    if (nsteps < 0) return fail(SHD_ERR_ARG, "nsteps < 0");
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    const int np = (int)b->probs.size();
+    for (int p = 0; p < np; ++p) {
+        shd_ctx *c = b->probs[p];
+        int rc = ready_for_step(c);
+        if (!rc && !c->have_state) rc = fail(SHD_ERR_STATE, "state not set");
+        if (rc) return fail(rc, "problem %d: %s", p, std::string(g_err).c_str());
+    }
+    cudaStream_t st = stream ? (cudaStream_t)stream : b->probs[0]->stream;
+    for (int p = 0; p < np; ++p) {
+        int rc = stream_after(st, b->probs[p]->stream);
+        if (rc) return rc;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        std::vector<std::pair<unsigned long long, int>> key(np);
+        for (int p = 0; p < np; ++p) {
+            shd_ctx *c = b->probs[p];
+            int slot = -1, rc;
+            rc = is_fp64(c) ? graph_slot<double>(c, slot) : graph_slot<float>(c, slot);
+            if (rc) return fail(rc, "problem %d: %s", p, std::string(g_err).c_str());
+            if (slot < 0) {
+                // direct launches for this problem's step
+                rc = is_fp64(c) ? run_steps<double>(c, 1, st, false) : run_steps<float>(c, 1, st, false);
+                if (rc) return fail(rc, "problem %d: %s", p, std::string(g_err).c_str());
+            }
+            key[p] = {c->graph_gen, slot};
+        }
+        bool any = false;
+        for (auto &k : key) any |= k.second >= 0;
+        if (any) {
+            cudaGraphExec_t exec = nullptr;
+            for (auto &e : b->cache)
+                if (e.key == key) exec = e.exec;
+            if (!exec) {
+                cudaGraph_t bg = nullptr;
+                CK(cudaGraphCreate(&bg, 0), "batch graph");
+                cudaError_t e = cudaSuccess;
+                for (int p = 0; p < np && e == cudaSuccess; ++p) {
+                    if (key[p].second < 0) continue;
+                    cudaGraphNode_t node;
+                    e = cudaGraphAddChildGraphNode(&node, bg, nullptr, 0, b->probs[p]->graph[key[p].second]);
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, bg, 0);
+                cudaGraphDestroy(bg);
+                CK(e, "batch graph");
+                if (b->cache.size() >= 8) batch_drop(b);  // problems changed: start over
+                b->cache.push_back({key, exec});
+            }
+            CK(cudaGraphLaunch(exec, st), "batch graph launch");
+            for (int p = 0; p < np; ++p) {
+                if (key[p].second < 0) continue;
+                shd_ctx *c = b->probs[p];
+                count_launches(c->graph_kernels[key[p].second]);
+                std::swap(c->d_Sp, c->d_Sprev);
+            }
+        }
+    }
+    for (int p = 0; p < np; ++p) {
+        int rc = stream_after(b->probs[p]->stream, st);
+        if (rc) return rc;
+    }
+    return SHD_OK;
+}
+
+void shd_batch_destroy(shd_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    batch_drop(b);
+    delete b;
 }
 
 }  // extern "C"

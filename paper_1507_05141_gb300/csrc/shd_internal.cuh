@@ -193,7 +193,9 @@ struct shd_ctx {
     // one time step captured as a CUDA graph per parity of the S_lm / S_prev
     // pair (graph_sp[i]: the buffer that step writes S_lm to); dropped by
     // every setter, rebuilt on the next step
+    cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    unsigned long long graph_gen = 0;  // bumped whenever a graph is captured or dropped
     void *graph_sp[2] = {nullptr, nullptr};
     unsigned long long graph_kernels[2] = {0, 0};  // kernel launches per replay
     cudaStream_t cap_stream = nullptr;

@@ -57,6 +57,9 @@ _SIGS = {
     "shd_set_timing": (_i, [_vp, _i]),
     "shd_get_timing": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
     "shd_launch_count": (ctypes.c_ulonglong, []),
+    "shd_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
+    "shd_batch_step": (_i, [_vp, _i, _vp]),
+    "shd_batch_destroy": (None, [_vp]),
     "shd_project_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "shd_noalloc_last_error": (ctypes.c_char_p, []),
 }
@@ -304,3 +307,33 @@ class Solver:
 
     def device_bytes(self):
         return int(self._L.shd_device_bytes(self._h))
+
+
+class Batch:
+    """Independent problems stepped together: each batch step is one CUDA
+    graph launch with one time step per problem (see shd_batch_step).  The
+    solvers stay usable for reading results and must outlive the batch."""
+
+    def __init__(self, solvers):
+        self._L = lib()
+        self._solvers = list(solvers)
+        arr = (_vp * len(self._solvers))(*[s._h for s in self._solvers])
+        h = _vp()
+        _check(self._L.shd_batch_create(ctypes.byref(h), len(self._solvers), arr))
+        self._h = h
+
+    def step(self, nsteps=1, stream=None):
+        """Enqueue nsteps steps of every problem on ``stream`` (a cudaStream_t
+        as int, or None for the first problem's own stream)."""
+        _check(self._L.shd_batch_step(self._h, int(nsteps), stream))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.shd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
