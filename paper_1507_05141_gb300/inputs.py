@@ -28,6 +28,18 @@ Recipes (numpy ``PCG64``, seed ``20150717 + index`` unless given):
   n_e (1/0.95 - 1) (albedo 0.95 in the Thomson limit); thermal emission
   alpha B_g(theta_e) with B_g the group average of x^3/(exp(x/theta)-1).
 
+* ``jet_cocoon``    (128^3, 64 log groups over 1e-4..1e2, L=7, 16x32): a jet
+  core r <= 0.08 with Gamma = 30 along z inside a cocoon 0.08..0.3 with
+  u = 0.6 r_hat + 0.9 z_hat, smooth blends over 0.02; Klein-Nishina with
+  albedo 0.95 and thermal emission from a random electron temperature as in
+  ``compton_shell``.
+* ``batch_problem`` (problem i of a batch of independent problems): cubic n,
+  G, L drawn per problem; a jet of radius 0.2 along a random axis with Gamma
+  log-uniform in [1, 20]; box optical depth log-uniform in [0.1, 20];
+  Thomson or Klein-Nishina with probability 1/2 each.
+* ``ragged_mixed``  (default 11x9x7, 5 groups, L=3): a non-cubic box with a
+  tilted jet, random perturbations and 30 % of nodes at rest.
+
 Every recipe accepts reduced ``n``, ``G``, ``L`` for oracle-sized cases; the
 ordinate set follows ``nmu = 2(L+1)``, ``nphi = 4(L+1)``.
 """
@@ -184,6 +196,66 @@ def compton_shell(n=96, G=32, L=7, seed=None, index=2, emin=1e-4, emax=1e2, albe
     nmu, nphi = ordinate_counts(L)
     return ProblemSpec("compton_shell", (n, n, n), (1.0, 1.0, 1.0), L, nmu, nphi, edges, alpha0, ne,
                        u, emis0, "kn", kappa=1.0 / (0.5 * h), steps=200, extra={"theta_e": theta})
+
+
+def jet_cocoon(n=128, G=64, L=7, seed=None, index=5, emin=1e-4, emax=1e2, albedo=0.95, tau_box=5.0):
+    """A fast jet core (r <= 0.08, Gamma = 30 along z) inside a slower
+    cocoon (0.08 < r < 0.3, u = 0.6 r_hat + 0.9 z_hat, Gamma ~ 1.5), smooth
+    blends over 0.02; cold Klein-Nishina scattering with albedo 0.95 in every
+    group and thermal emission from a Gaussian random electron-temperature
+    field mapped to [0.01, 0.3]."""
+    rng = _rng(index, seed)
+    X, Y, Z, h = _coords(n)
+    f = gaussian_random_field(n, 0.1, rng)
+    theta = 0.01 + (f - f.min()) / (f.max() - f.min()) * (0.3 - 0.01)
+    dx, dy = X - 0.5, Y - 0.5
+    r = np.hypot(dx, dy)
+    rs = np.maximum(r, 1e-30)
+    rx, ry = np.where(r > 0, dx / rs, 0.0), np.where(r > 0, dy / rs, 0.0)
+    core = 1.0 - _smoothstep((r - 0.08) / 0.02)     # 1 inside the core
+    cocoon = 1.0 - _smoothstep((r - 0.30) / 0.02)   # 1 inside the cocoon's outer radius
+    u_core = np.stack([np.zeros_like(r), np.zeros_like(r), np.full_like(r, np.sqrt(30.0 ** 2 - 1.0))], axis=1)
+    u_coc = np.stack([0.6 * rx, 0.6 * ry, np.full_like(r, 0.9)], axis=1)
+    u = core[:, None] * u_core + (1.0 - core)[:, None] * cocoon[:, None] * u_coc
+    u[np.all(np.abs(u) < 1e-12, axis=1)] = 0.0
+    edges = np.geomspace(emin, emax, G + 1)
+    ne = np.full(n ** 3, tau_box)
+    alpha0 = np.repeat((ne * (1.0 / albedo - 1.0))[:, None], G, axis=1)
+    emis0 = alpha0 * planck_group(edges, theta)
+    nmu, nphi = ordinate_counts(L)
+    return ProblemSpec("jet_cocoon", (n, n, n), (1.0, 1.0, 1.0), L, nmu, nphi, edges, alpha0, ne, u, emis0, "kn",
+                       kappa=1.0 / (0.5 * h), steps=500, extra={"theta_e": theta})
+
+
+def batch_problem(i, seed=None, n_range=(16, 64), g_range=(8, 32), Ls=(3, 5, 7)):
+    """Problem i of the batch of independent problems: cubic grid n ~ U{n_range},
+    G ~ U{g_range} log groups over 1e-3..1e1, L from Ls, a jet of radius 0.2
+    along an isotropically random axis through the box centre with Gamma
+    log-uniform in [1, 20], box optical depth log-uniform in [0.1, 20],
+    Thomson or Klein-Nishina scattering with probability 1/2 each."""
+    rng = _rng(1000 * (i + 1) + 4, seed)
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    G = int(rng.integers(g_range[0], g_range[1] + 1))
+    L = int(rng.choice(Ls))
+    axis = rng.standard_normal(3)
+    axis /= np.linalg.norm(axis)
+    gmax = float(np.exp(rng.uniform(0.0, np.log(20.0))))
+    tau = float(np.exp(rng.uniform(np.log(0.1), np.log(20.0))))
+    kind = "kn" if rng.random() < 0.5 else "thomson"
+    X, Y, Z, h = _coords(n)
+    p = np.stack([X - 0.5, Y - 0.5, Z - 0.5], axis=1)
+    r = np.linalg.norm(p - (p @ axis)[:, None] * axis[None, :], axis=1)
+    gam = jet_lorentz_factor(r, gmax, 0.2, 0.3)
+    u = np.sqrt(np.maximum(gam * gam - 1.0, 0.0))[:, None] * axis[None, :]
+    u[gam <= 1.0] = 0.0
+    edges = np.geomspace(1e-3, 1e1, G + 1)
+    centre = np.sqrt(edges[:-1] * edges[1:])
+    ne = np.full(n ** 3, tau)
+    alpha0 = np.full((n ** 3, G), 0.1 * tau)
+    emis0 = ne[:, None] * centre[None, :] ** -1.0
+    nmu, nphi = ordinate_counts(L)
+    return ProblemSpec(f"batch_{i}", (n, n, n), (1.0, 1.0, 1.0), L, nmu, nphi, edges, alpha0, ne, u, emis0, kind,
+                       kappa=1.0 / (0.5 * h), steps=20, extra={"gmax": gmax, "tau": tau})
 
 
 def random_state(spec: ProblemSpec, seed=12345, scale=1.0, layout="cgk"):
