@@ -1000,6 +1000,14 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
     if (!finite_all(u, (size_t)c->Nc * 3, false)) return fail(SHD_ERR_NAN, "u must be finite");
     if (!finite_all(emis0, nCG, true)) return fail(SHD_ERR_NAN, "emis0 must be finite and >= 0");
     if ((rc = ensure_buffers(c))) return rc;
+    c->h_alpha_max = c->h_ne_max = 0.0;
+    c->h_gamma_max = 1.0;
+    for (size_t i = 0; i < nCG; ++i) c->h_alpha_max = std::max(c->h_alpha_max, alpha0[i]);
+    for (long long i = 0; i < c->Nc; ++i) {
+        c->h_ne_max = std::max(c->h_ne_max, ne[i]);
+        const double uu = u[3 * i] * u[3 * i] + u[3 * i + 1] * u[3 * i + 1] + u[3 * i + 2] * u[3 * i + 2];
+        c->h_gamma_max = std::max(c->h_gamma_max, std::sqrt(1.0 + uu));
+    }
     if (is_fp64(c)) {
         if ((rc = upload_reals<double>(c, alpha0, c->d_alpha0, nCG))) return rc;
         if ((rc = upload_reals<double>(c, ne, c->d_ne, c->Nc))) return rc;
@@ -1075,8 +1083,14 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
             CK(launch_convert<float>(ds, (float *)c->d_sigma_out, G, c->stream), "convert");
         }
         CK(cudaStreamSynchronize(c->stream), "sync");
+        std::vector<double> hso(G);
+        CK(cudaMemcpy(hso.data(), ds, sizeof(double) * G, cudaMemcpyDeviceToHost), "sigma_out");
+        c->h_sigma_max = 0.0;
+        for (double v : hso) c->h_sigma_max = std::max(c->h_sigma_max, v);
         cudaFree(dK); cudaFree(ds); cudaFree(dgx); cudaFree(dgw);
     } else {
+        c->h_sigma_max = 0.0;
+        for (double v : hs) c->h_sigma_max = std::max(c->h_sigma_max, v);
         if (is_fp64(c)) {
             if ((rc = upload_reals<double>(c, hK.data(), c->d_K, nK))) return rc;
             if ((rc = upload_reals<double>(c, hs.data(), c->d_sigma_out, G))) return rc;

@@ -134,6 +134,9 @@ struct shd_ctx {
     void *d_W = nullptr, *d_dirs = nullptr, *d_Y = nullptr, *d_mu = nullptr;
     double *d_edges = nullptr, *d_centre = nullptr;
     void *d_alpha0 = nullptr, *d_ne = nullptr, *d_u = nullptr, *d_emis0 = nullptr, *d_chi0 = nullptr;
+    // host maxima of the fields and of sigma_out: a bound on the optical depth
+    // of one short-characteristic step (the sweep's FP64 weights)
+    double h_alpha_max = 0, h_ne_max = 0, h_gamma_max = 1, h_sigma_max = 0;
     // chi0 in the three sweep layouts [d][g][o] and, per layout, the 4-node
     // pieces of each plane holding a moving node: bit (id % 64) of
     // d_mbits[d][id / 64][piece] (mbits_nwin windows of mbits_npc words)
@@ -451,13 +454,20 @@ __device__ __noinline__ inline void sc_weights_fp64(float x, float &e, float &wp
     wu = (float)(a0 - ed);
 }
 
+// The weights in working precision only: for sweeps whose optical depth per
+// step is bounded by kFp64Tau on the host (see the sweep launcher).
+template <class T>
+__device__ inline void sc_weights_narrow(T x, T &e, T &wp, T &wu);
+
 template <>
-__device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu)
+__device__ inline void sc_weights_narrow<double>(double x, double &e, double &wp, double &wu)
 {
-    if (x > kFp64Tau) {
-        sc_weights_fp64(x, e, wp, wu);
-        return;
-    }
+    sc_weights<double>(x, e, wp, wu);
+}
+
+template <>
+__device__ inline void sc_weights_narrow<float>(float x, float &e, float &wp, float &wu)
+{
     e = __expf(-x);
     if (x < 0.5f) {
         wp = x * (1.f / 2 - x * (1.f / 6 - x * (1.f / 24 - x * (1.f / 120 - x * (1.f / 720 - x * (1.f / 5040 - x * (1.f / 40320 - x / 362880.f)))))));
@@ -468,6 +478,16 @@ __device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu
     float a0 = (1.f - e) * __frcp_rn(x);
     wp = 1.f - a0;
     wu = a0 - e;
+}
+
+template <>
+__device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu)
+{
+    if (x > kFp64Tau) {
+        sc_weights_fp64(x, e, wp, wu);
+        return;
+    }
+    sc_weights_narrow<float>(x, e, wp, wu);
 }
 
 // -------------------------------------------------------------------------

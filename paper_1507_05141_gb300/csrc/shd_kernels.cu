@@ -315,7 +315,9 @@ __device__ inline void cp_async_n(void *smem, const void *gmem)
 // only for the 4-node pieces of a plane that hold a moving node (bit id % 64
 // of mbits[d][id / 64][piece]) and from chi0L elsewhere; the CTA keeps the
 // current 64-plane window of its layout's bits in shared memory.
-template <class T, int U, bool VEC, bool CB>
+// WIDE: the transfer weights switch to FP64 above optical depth kFp64Tau
+// (launched unless the host bound excludes such steps).
+template <class T, int U, bool VEC, bool CB, bool WIDE>
 __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict__ I, const T *__restrict__ eta,
                                                         const T *__restrict__ chi, const T *__restrict__ chi0L,
                                                         const unsigned long long *__restrict__ mbits, int npc,
@@ -429,7 +431,8 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
                 const T cu = w00 * pC[b00] + w10 * pC[b10] + w01 * pC[b01] + w11 * pC[b11];
                 const T dtau = s * T(0.5) * (cu + ct);
                 T ew, wp, wu;
-                sc_weights<T>(dtau, ew, wp, wu);
+                if constexpr (WIDE) sc_weights<T>(dtau, ew, wp, wu);
+                else sc_weights_narrow<T>(dtau, ew, wp, wu);
                 inew = iu * ew + st * wp + su * wu;
             }
             rI[u] = inew;
@@ -694,6 +697,17 @@ static cudaError_t launch_sweep_npt(const shd_ctx *ctx, T *I, const T *eta, cons
     return cudaGetLastError();
 }
 
+// Optical depth of one short-characteristic step is at most s_max chi~_max
+// with chi~ = chi_lab + kappa and chi_lab <= chi0_max D_max, D = Gamma - u.n <
+// 2 Gamma (R17): true when that stays within kFp64Tau.
+static bool sweep_tau_bounded(const shd_ctx *c)
+{
+    double smax = 0;
+    for (const Ordinate &o : c->h_ord) smax = o.s > smax ? o.s : smax;
+    const double chi = (c->h_alpha_max + c->h_ne_max * c->h_sigma_max) * 2.0 * c->h_gamma_max + c->kappa;
+    return std::isfinite(chi) && smax * chi <= (double)kFp64Tau;
+}
+
 template <class T, int U, bool VEC>
 static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st,
                                      size_t sm, bool bits)
@@ -702,7 +716,10 @@ static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, con
     const T *c0L = bits ? (const T *)ctx->d_chi0L : nullptr;
     const unsigned long long *mb = bits ? ctx->d_mbits : nullptr;
     if (bits) sm += sizeof(unsigned long long) * (size_t)ctx->mbits_npc;
-    auto kern = bits ? k_sweep_pipe<T, U, VEC, VEC> : k_sweep_pipe<T, U, VEC, false>;
+    // FP64 weights are needed only if a step's optical depth can exceed kFp64Tau
+    const bool wide = sizeof(T) == 4 && !sweep_tau_bounded(ctx);
+    auto kern = bits ? (wide ? k_sweep_pipe<T, U, VEC, VEC, (sizeof(T) == 4)> : k_sweep_pipe<T, U, VEC, VEC, false>)
+                     : (wide ? k_sweep_pipe<T, U, VEC, false, (sizeof(T) == 4)> : k_sweep_pipe<T, U, VEC, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi, c0L, mb, ctx->mbits_npc, ctx->mbits_nwin);
