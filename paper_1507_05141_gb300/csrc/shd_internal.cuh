@@ -446,14 +446,6 @@ __device__ inline void sc_weights<double>(double x, double &e, double &wp, doubl
 // scaling): the weights are then taken in FP64.
 constexpr float kFp64Tau = 16.f;
 
-__device__ __noinline__ inline void sc_weights_fp64(float x, float &e, float &wp, float &wu)
-{
-    const double xd = x, ed = exp(-xd), a0 = (1.0 - ed) / xd;
-    e = (float)ed;
-    wp = (float)(1.0 - a0);
-    wu = (float)(a0 - ed);
-}
-
 // The weights in working precision only: for sweeps whose optical depth per
 // step is bounded by kFp64Tau on the host (see the sweep launcher).
 template <class T>
@@ -484,7 +476,10 @@ template <>
 __device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu)
 {
     if (x > kFp64Tau) {
-        sc_weights_fp64(x, e, wp, wu);
+        const double xd = x, ed = exp(-xd), a0 = (1.0 - ed) / xd;
+        e = (float)ed;
+        wp = (float)(1.0 - a0);
+        wu = (float)(a0 - ed);
         return;
     }
     sc_weights_narrow<float>(x, e, wp, wu);
