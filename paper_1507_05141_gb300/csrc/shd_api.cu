@@ -1100,6 +1100,13 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
         }
     }
     c->scat_kind = kind;
+    // the source stage's one-product form needs every K_l diagonal
+    c->k_diagonal = kind != SHD_SCAT_KN;
+    if (kind == SHD_SCAT_TABLE)
+        for (size_t i = 0; i < nK && c->k_diagonal; ++i) {
+            const size_t r = i % ((size_t)G * G);
+            if (r / G != r % G && hK[i] != 0.0) c->k_diagonal = false;
+        }
     c->have_scat = true;
     if (c->have_fields) {
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");

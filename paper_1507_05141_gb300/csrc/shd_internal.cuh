@@ -126,6 +126,7 @@ struct shd_ctx {
     bool have_grid = false, have_angles = false, have_groups = false;
     bool have_fields = false, have_scat = false, have_state = false;
     int scat_kind = 0;
+    bool k_diagonal = false;  // every K_l[g][g'] is zero off the diagonal
     int bc_mode = SHD_BC_VACUUM;
     double kappa = 0.0;
 

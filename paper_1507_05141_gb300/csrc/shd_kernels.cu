@@ -129,8 +129,10 @@ __global__ void __launch_bounds__(256) k_source(Prob<T> P, const T *__restrict__
 // is formed exactly as k_source forms it; while it is written, every thread
 // accumulates in FP64 the residual |S - S_prev|^2, |S|^2 and, from J of the
 // moments, the energy and photon sums; the CTA's partials go to partial[b][4]
-// for k_sums_final.
-template <class T>
+// for k_sums_final.  DIAG: every K_l is diagonal (Thomson, isotropic), so an
+// output takes one product and the node's I_lm streams straight through
+// (the full sum's other terms are exact zeros: the same S_p).
+template <class T, bool DIAG>
 __global__ void __launch_bounds__(256, 2) k_source_sums(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp,
                                                      const T *__restrict__ mom, const T *__restrict__ Sprev,
                                                      int have_prev, double *partial)
@@ -151,9 +153,62 @@ __global__ void __launch_bounds__(256, 2) k_source_sums(Prob<T> P, const T *__re
     double e = 0, ph = 0, num = 0, den = 0;
     for (long long c = (long long)blockIdx.x * 8 + warp; c < P.Nc; c += (long long)gridDim.x * 8) {
         const long long base = c * G * NLM;
+        const T ne = P.ne[c];
+        if constexpr (DIAG) {
+            // lane g < G holds group g's chi0, n_e/chi0 and emission term
+            // (G <= 32 on this path), shared with the warp by shuffles
+            const T chi_l = lane < G ? P.chi0[c * G + lane] : T(0);
+            const T r_l = chi_l > T(0) ? ne / chi_l : T(0);
+            const T em_l = chi_l > T(0) ? T(3.5449077018110320546) * P.emis0[c * G + lane] / chi_l : T(0);  // sqrt(4 pi)
+            // the node's part of |S|^2 and |S - S_prev|^2 in working precision
+            // (a lane's at most G ceil(NLM/32) squares), added to the FP64
+            // totals once per node
+            T dn = T(0), nm = T(0);
+            // warp-uniform trip count: every lane takes part in the shuffles
+            for (int p0 = 0; p0 < NLM; p0 += 32) {
+                const int p = p0 + lane;
+                const bool act = p < NLM;
+                int l = 0;
+                while ((l + 1) * (l + 1) <= p) ++l;
+                // groups in rounds of 8: the round's loads are in flight together
+                for (int g0 = 0; g0 < G; g0 += 8) {
+                    T iv[8], pv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const long long i = base + (long long)(g0 + q) * NLM + p;
+                        const bool ok = act && g0 + q < G;
+                        iv[q] = ok ? Ip[i] : T(0);
+                        pv[q] = ok && have_prev ? Sprev[i] : T(0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int g = g0 + q;
+                        if (g >= G) break;
+                        const T chi = __shfl_sync(0xffffffffu, chi_l, g);
+                        const T r = __shfl_sync(0xffffffffu, r_l, g);
+                        const T em = __shfl_sync(0xffffffffu, em_l, g);
+                        if (!act) continue;
+                        T s = T(0);
+                        if (chi > T(0)) {
+                            T acc = T(0);
+                            acc += sK[(size_t)l * KS + g * G + g] * iv[q];
+                            s = r * acc;
+                            if (p == 0) s += em;
+                        }
+                        Sp[base + (long long)g * NLM + p] = s;
+                        dn += s * s;
+                        if (have_prev) {
+                            const T d = s - pv[q];
+                            nm += d * d;
+                        }
+                    }
+                }
+            }
+            den += (double)dn;
+            num += (double)nm;
+        } else {
         for (int i = lane; i < G * NLM; i += 32) wI[i] = Ip[base + i];
         __syncwarp();
-        const T ne = P.ne[c];
         for (int p = lane; p < NLM; p += 32) {
             int l = 0;
             while ((l + 1) * (l + 1) <= p) ++l;
@@ -176,6 +231,7 @@ __global__ void __launch_bounds__(256, 2) k_source_sums(Prob<T> P, const T *__re
                     num += d * d;
                 }
             }
+        }
         }
         for (int g = lane; g < G; g += 32) {
             const double J = (double)mom[(c * G + g) * 10];
@@ -817,10 +873,11 @@ cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, c
 {
     Prob<T> P = make_prob<T>(ctx);
     const size_t sm = source_sums_smem(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_source_sums<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto kern = ctx->k_diagonal && ctx->G <= 32 ? k_source_sums<T, true> : k_source_sums<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int nb = ctx->n_partial;
-    k_source_sums<T><<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, ctx->d_partial);
+    kern<<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, ctx->d_partial);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_sums_final<<<1, 32, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
