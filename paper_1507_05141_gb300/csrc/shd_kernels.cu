@@ -170,18 +170,18 @@ __global__ void __launch_bounds__(256, 2) k_source_sums(Prob<T> P, const T *__re
                 const bool act = p < NLM;
                 int l = 0;
                 while ((l + 1) * (l + 1) <= p) ++l;
-                // groups in rounds of 8: the round's loads are in flight together
-                for (int g0 = 0; g0 < G; g0 += 8) {
-                    T iv[8], pv[8];
+                // groups in rounds of 16: the round's loads are in flight together
+                for (int g0 = 0; g0 < G; g0 += 16) {
+                    T iv[16], pv[16];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < 16; ++q) {
                         const long long i = base + (long long)(g0 + q) * NLM + p;
                         const bool ok = act && g0 + q < G;
                         iv[q] = ok ? Ip[i] : T(0);
                         pv[q] = ok && have_prev ? Sprev[i] : T(0);
                     }
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < 16; ++q) {
                         const int g = g0 + q;
                         if (g >= G) break;
                         const T chi = __shfl_sync(0xffffffffu, chi_l, g);
