@@ -975,6 +975,12 @@ int shd_set_groups(shd_ctx *c, int G, const double *edges)
     std::vector<double> lc(G), linv(G, 0.0);
     for (int g = 0; g < G; ++g) lc[g] = std::log(c->h_centre[g]);
     for (int g = 0; g + 1 < G; ++g) linv[g] = 1.0 / (lc[g + 1] - lc[g]);
+    // centres equally spaced in log energy (geometric groups)?
+    c->lg_uniform = G >= 2;
+    c->lg_dl = G >= 2 ? (lc[G - 1] - lc[0]) / (G - 1) : 1.0;
+    c->lg_c0 = lc[0];
+    for (int g = 0; g + 1 < G && c->lg_uniform; ++g)
+        if (std::fabs((lc[g + 1] - lc[g]) - c->lg_dl) > 1e-9 * std::fabs(c->lg_dl)) c->lg_uniform = false;
     dfree(c->d_lc);
     dfree(c->d_linv);
     if (is_fp64(c)) {

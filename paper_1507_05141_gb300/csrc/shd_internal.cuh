@@ -83,6 +83,9 @@ struct Prob {
     const T *lc;           // [G] log of the group centres
     const T *linv;         // [G] 1/(lc[g+1] - lc[g])
     T le0, leG;            // log of the outer edges
+    int lgu;               // group centres equally spaced in log energy; then
+    T lgidl;               // 1 / that spacing,
+    T lgx0, lgx1;          // the outer edges in units of it, from lc[0]
 };
 
 // Per-stage CUDA events recorded on the launching stream without any host
@@ -122,6 +125,8 @@ struct shd_ctx {
     // groups
     int G = 0;
     std::vector<double> h_edges, h_centre;
+    bool lg_uniform = false;       // centres equally spaced in log energy
+    double lg_dl = 1.0, lg_c0 = 0; // that spacing, the first log centre
 
     bool have_grid = false, have_angles = false, have_groups = false;
     bool have_fields = false, have_scat = false, have_state = false;
@@ -415,8 +420,24 @@ __device__ inline double freq_mix<double>(double fa, double fb, double t)
 template <>
 __device__ inline float freq_mix<float>(float fa, float fb, float t)
 {
+    // the fast divide holds its 2-ulp bound for divisors of normal size
+    if (fa >= 1.17549435e-38f && fa < 8.5e37f && fb > 0.f) return fa * __expf(t * __logf(__fdividef(fb, fa)));
     if (fa > 0.f && fb > 0.f) return fa * __expf(t * __logf(fb / fa));
     return (1.f - t) * fa + t * fb;
+}
+
+// Geometric mix whose log ratio log(fb/fa) is already known (both positive).
+template <class T>
+__device__ inline T freq_mix_lr(T fa, T lr, T t);
+template <>
+__device__ inline double freq_mix_lr<double>(double fa, double lr, double t)
+{
+    return fa * exp(t * lr);
+}
+template <>
+__device__ inline float freq_mix_lr<float>(float fa, float lr, float t)
+{
+    return fa * __expf(t * lr);
 }
 
 // Linear-in-tau short-characteristic weights with e = exp(-x):

@@ -39,6 +39,10 @@ Prob<T> make_prob(const shd_ctx *c)
     p.lc = (const T *)c->d_lc; p.linv = (const T *)c->d_linv;
     p.le0 = c->G ? (T)std::log(c->h_edges[0]) : T(0);
     p.leG = c->G ? (T)std::log(c->h_edges[c->G]) : T(0);
+    p.lgu = c->lg_uniform ? 1 : 0;
+    p.lgidl = (T)(1.0 / c->lg_dl);
+    p.lgx0 = c->G ? (T)((std::log(c->h_edges[0]) - c->lg_c0) / c->lg_dl) : T(0);
+    p.lgx1 = c->G ? (T)((std::log(c->h_edges[c->G]) - c->lg_c0) / c->lg_dl) : T(0);
     return p;
 }
 

@@ -591,6 +591,38 @@ struct GroupCache {
     }
 };
 
+// Energy offset x = l / (log spacing) of equally spaced log centres, split
+// into its whole part s and fraction t.
+template <class T>
+struct UniformShift {
+    T x, t;
+    int s;
+};
+
+template <class T>
+__device__ inline UniformShift<T> uniform_shift(const Prob<T> &P, T l)
+{
+    UniformShift<T> u;
+    u.x = l * P.lgidl;
+    const T f = floor(u.x);
+    u.s = (int)f;
+    u.t = u.x - f;
+    return u;
+}
+
+// lower group of an inner bracket, kept in [0, G-2]
+__device__ inline int clamp_group(int ga, int G) { return ga < 0 ? 0 : (ga > G - 2 ? G - 2 : ga); }
+
+// chi0 between centres ga and ga+1: geometric from the node's log-ratio
+// table where both are positive, linear otherwise
+template <class T>
+__device__ inline T chi_mix(const T *schi, const T *slr, int ga, T t)
+{
+    const T a = schi[ga], b = schi[ga + 1];
+    if (a > T(0) && b > T(0)) return freq_mix_lr<T>(a, slr[ga], t);
+    return (T(1) - t) * a + t * b;
+}
+
 // laboratory I (node-major) -> comoving I0 (node-major), one CTA per moving
 // node: I0(k0, g0) = (ebar_g0/eps)^3 I_lab(n, eps), n = boost of n_k0 to the
 // laboratory, eps = ebar_g0 (Gamma + u.n_k0)   (Sec. 2.2)
@@ -617,8 +649,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
         const Stencil<T> st = stencil_internal<T>(P, tb, n);
         T iq3 = T(1) / (q * q * q);
         T lq = dlog<T>(q);
-        int hint = 0;
         GroupCache<T> cache;
+        if (sizeof(T) == 4 && P.lgu) {
+            // equally spaced log centres: energy lc[g0] + lq sits at g0 + x
+            // group spacings from lc[0], every group with the same fraction
+            const UniformShift<T> us = uniform_shift<T>(P, lq);
+            for (int g0 = 0; g0 < G; ++g0) {
+                const T pos = T(g0) + us.x;
+                T v = 0;
+                if (pos >= P.lgx0 && pos <= P.lgx1) {
+                    if (pos <= T(0)) {
+                        v = cache.get(st, sI, spole, N, 0);
+                    } else if (pos >= T(G - 1)) {
+                        v = cache.get(st, sI, spole, N, G - 1);
+                    } else {
+                        const int ga = clamp_group(g0 + us.s, G);
+                        T fa = cache.get(st, sI, spole, N, ga);
+                        T fbv = cache.get(st, sI, spole, N, ga + 1);
+                        v = freq_mix<T>(fa, fbv, us.t);
+                    }
+                }
+                dst[(size_t)g0 * N + k0] = v * iq3;
+            }
+            continue;
+        }
+        int hint = 0;
         for (int g0 = 0; g0 < G; ++g0) {
             FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, tb.lc[g0] + lq, hint);
             T v = 0;
@@ -646,13 +701,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
     T *sS = reinterpret_cast<T *>(smem_raw);  // [G][N] internal order
     T *spole = sS + (size_t)G * N;            // [G][2]
     T *schi = spole + 2 * G;                  // [G]
+    T *slr = schi + G;                        // [G] FP32: log(chi0[g+1]/chi0[g]) where both > 0
     const long long m = blockIdx.x;
     const long long c = P.moving[m];
     stage_node<T>(sS, S0 + m * G * N, G * N);
     for (int g = threadIdx.x; g < G; g += blockDim.x) schi[g] = P.chi0[c * G + g];
-    const RemapTables<T> tb = remap_tables<T>(P, reinterpret_cast<unsigned char *>(schi + G));
+    const RemapTables<T> tb = remap_tables<T>(P, reinterpret_cast<unsigned char *>(slr + G));
     __syncthreads();
     pole_averages<T>(P, sS, tb.m2i, spole);
+    for (int g = threadIdx.x; sizeof(T) == 4 && g + 1 < G; g += blockDim.x) {
+        const T a = schi[g], b = schi[g + 1];
+        slr[g] = (a > T(0) && b > T(0)) ? dlog<T>(b / a) : T(0);
+    }
     __syncthreads();
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
     T *de = eta_n + m * G * N, *dc = chi_n + m * G * N;
@@ -663,8 +723,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
         const Stencil<T> st = stencil_internal<T>(P, tb, n0);
         T iD3 = T(1) / (D * D * D);
         T lD = dlog<T>(D);
-        int hint = 0;
         GroupCache<T> cache;
+        if (sizeof(T) == 4 && P.lgu) {
+            // equally spaced log centres: energy lc[g] + lD sits at g + x
+            // group spacings from lc[0], every group with the same fraction
+            const UniformShift<T> us = uniform_shift<T>(P, lD);
+            for (int g = 0; g < G; ++g) {
+                const T pos = T(g) + us.x;
+                T s = 0, ch;
+                if (pos < P.lgx0) {
+                    ch = schi[0];
+                } else if (pos > P.lgx1) {
+                    ch = schi[G - 1];
+                } else if (pos <= T(0)) {
+                    s = cache.get(st, sS, spole, N, 0);
+                    ch = schi[0];
+                } else if (pos >= T(G - 1)) {
+                    s = cache.get(st, sS, spole, N, G - 1);
+                    ch = schi[G - 1];
+                } else {
+                    const int ga = clamp_group(g + us.s, G);
+                    T fa = cache.get(st, sS, spole, N, ga);
+                    T fbv = cache.get(st, sS, spole, N, ga + 1);
+                    s = freq_mix<T>(fa, fbv, us.t);
+                    ch = chi_mix<T>(schi, slr, ga, us.t);
+                }
+                T chl = ch * D;
+                dc[(size_t)g * N + k] = chl;
+                de[(size_t)g * N + k] = chl * s * iD3;
+            }
+            continue;
+        }
+        int hint = 0;
         for (int g = 0; g < G; ++g) {
             FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, tb.lc[g] + lD, hint);
             T s = 0, ch;
@@ -677,7 +767,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
                 T fa = cache.get(st, sS, spole, N, fb.ga);
                 T fbv = cache.get(st, sS, spole, N, fb.ga + 1);
                 s = freq_mix<T>(fa, fbv, fb.t);
-                ch = freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], fb.t);
+                ch = sizeof(T) == 4 ? chi_mix<T>(schi, slr, fb.ga, fb.t)
+                                    : freq_mix<T>(schi[fb.ga], schi[fb.ga + 1], fb.t);
             }
             T chl = ch * D;
             dc[(size_t)g * N + k] = chl;
@@ -691,8 +782,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
 // -------------------------------------------------------------------------
 size_t remap_smem_bytes(const shd_ctx *c)
 {
-    // values [G][N], poles [G][2], chi0 [G], tables mu, lc, linv, mesh2int
-    return (size_t)c->esize * ((size_t)c->G * c->N + 3 * c->G + c->nmu + 2 * c->G) + sizeof(int) * (size_t)c->N + 16;
+    // values [G][N], poles [G][2], chi0 [G], chi0 log ratios [G], tables mu,
+    // lc, linv, mesh2int
+    return (size_t)c->esize * ((size_t)c->G * c->N + 4 * c->G + c->nmu + 2 * c->G) + sizeof(int) * (size_t)c->N + 16;
 }
 
 size_t sh2lab_tile_smem_bytes(const shd_ctx *c)

@@ -250,6 +250,26 @@ def test_steps_mixed_ragged(native, kind):
     assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < MIXED_TOL
 
 
+@pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("mixed", MIXED_TOL)])
+def test_steps_uneven_groups(native, precision, tol):
+    """Group centres not equally spaced in log energy: the FP32 remaps take
+    the general bracket search instead of the constant shift."""
+    spec = inputs.ragged_mixed(scattering="kn")
+    spec.edges = np.array([1e-2, 2.5e-2, 4e-2, 0.15, 0.4, 3.0])
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision=precision)
+    I0 = inputs.random_state(spec, seed=6)
+    s.set_state(I0)
+    s.step(1)
+    J, H, K = s.moments()
+    I_ref, _, _ = P.step(I0, 1)
+    _, J_r, H_r, K_r = P.project(I_ref)
+    assert rel_elem(J, J_r) < tol
+    assert rel(H, H_r) < tol
+    f = O.moments_to_eddington(J, K)
+    assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < tol
+
+
 def test_steps_mixed_aligned(native):
     spec = inputs.jet(n=16, G=4, L=3, tau_r=4.0, gmax=12.0)  # Gamma > 10: FP64 Doppler island
     P = _oracle(spec)
