@@ -605,9 +605,37 @@ __device__ inline UniformShift<T> uniform_shift(const Prob<T> &P, T l)
     UniformShift<T> u;
     u.x = l * P.lgidl;
     const T f = floor(u.x);
-    u.s = (int)f;
+    const T lim = T(P.G + 1);  // shifts beyond the group range act alike
+    u.s = (int)fmin(fmax(f, -lim), lim);
     u.t = u.x - f;
     return u;
+}
+
+// A stencil flattened for the group loop: shared-memory offsets and weights
+// of the four ordinates plus the pole term, whose weight is 0 when the
+// direction lies between the outer rings (the pole slot read is then finite).
+template <class T>
+struct FlatStencil {
+    int o0, o1, o2, o3, po;
+    T w0, w1, w2, w3, wp;
+    // V(g) from the group-major values sv[g][N] and pole averages spole[g][2]
+    __device__ inline T eval(const T *sv, const T *spole, int N, int g) const
+    {
+        const T *F = sv + g * N;
+        T v = w0 * F[o0] + w1 * F[o1] + w2 * F[o2] + w3 * F[o3];
+        return v + wp * spole[2 * g + po];
+    }
+};
+
+template <class T>
+__device__ inline FlatStencil<T> flat_stencil(const Stencil<T> &s)
+{
+    FlatStencil<T> f;
+    f.o0 = s.k[0]; f.o1 = s.k[1]; f.o2 = s.k[2]; f.o3 = s.k[3];
+    f.w0 = s.w[0]; f.w1 = s.w[1]; f.w2 = s.w[2]; f.w3 = s.w[3];
+    f.po = s.pole_ring > 0 ? 1 : 0;
+    f.wp = s.pole_ring >= 0 ? s.wpole : T(0);
+    return f;
 }
 
 // lower group of an inner bracket, kept in [0, G-2]
@@ -652,24 +680,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
         GroupCache<T> cache;
         if (sizeof(T) == 4 && P.lgu) {
             // equally spaced log centres: energy lc[g0] + lq sits at g0 + x
-            // group spacings from lc[0], every group with the same fraction
+            // group spacings from lc[0], x = s + t with s whole, so output
+            // group g0 lies between input groups g0 + s and g0 + s + 1 at the
+            // same fraction t for every g0.  Output groups below [gm0, gm1)
+            // fall at or below the first centre, those above it at or beyond
+            // the last.
+            const FlatStencil<T> fs = flat_stencil<T>(st);
             const UniformShift<T> us = uniform_shift<T>(P, lq);
-            for (int g0 = 0; g0 < G; ++g0) {
-                const T pos = T(g0) + us.x;
-                T v = 0;
-                if (pos >= P.lgx0 && pos <= P.lgx1) {
-                    if (pos <= T(0)) {
-                        v = cache.get(st, sI, spole, N, 0);
-                    } else if (pos >= T(G - 1)) {
-                        v = cache.get(st, sI, spole, N, G - 1);
-                    } else {
-                        const int ga = clamp_group(g0 + us.s, G);
-                        T fa = cache.get(st, sI, spole, N, ga);
-                        T fbv = cache.get(st, sI, spole, N, ga + 1);
-                        v = freq_mix<T>(fa, fbv, us.t);
-                    }
+            const int gm0 = min(max(-us.s, 0), G), gm1 = max(min(G - 1 - us.s, G), gm0);
+            T *out = dst + k0;
+            if (gm0 > 0) {
+                const T v0 = fs.eval(sI, spole, N, 0);
+                for (int g0 = 0; g0 < gm0; ++g0, out += N) *out = (T(g0) + us.x >= P.lgx0 ? v0 : T(0)) * iq3;
+            }
+            if (gm1 > gm0) {
+                int ga = gm0 + us.s;
+                T va = fs.eval(sI, spole, N, ga);
+                for (int g0 = gm0; g0 < gm1; ++g0, ++ga, out += N) {
+                    const T vb = fs.eval(sI, spole, N, ga + 1);
+                    *out = freq_mix<T>(va, vb, us.t) * iq3;
+                    va = vb;
                 }
-                dst[(size_t)g0 * N + k0] = v * iq3;
+            }
+            if (gm1 < G) {
+                const T v1 = fs.eval(sI, spole, N, G - 1);
+                for (int g0 = gm1; g0 < G; ++g0, out += N) *out = (T(g0) + us.x <= P.lgx1 ? v1 : T(0)) * iq3;
             }
             continue;
         }
@@ -725,32 +760,45 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
         T lD = dlog<T>(D);
         GroupCache<T> cache;
         if (sizeof(T) == 4 && P.lgu) {
-            // equally spaced log centres: energy lc[g] + lD sits at g + x
-            // group spacings from lc[0], every group with the same fraction
+            // equally spaced log centres: the constant shift s and fraction t
+            // of the comoving remap above; below [gm0, gm1) chi0 is the first
+            // group's, above it the last group's
+            const FlatStencil<T> fs = flat_stencil<T>(st);
             const UniformShift<T> us = uniform_shift<T>(P, lD);
-            for (int g = 0; g < G; ++g) {
-                const T pos = T(g) + us.x;
-                T s = 0, ch;
-                if (pos < P.lgx0) {
-                    ch = schi[0];
-                } else if (pos > P.lgx1) {
-                    ch = schi[G - 1];
-                } else if (pos <= T(0)) {
-                    s = cache.get(st, sS, spole, N, 0);
-                    ch = schi[0];
-                } else if (pos >= T(G - 1)) {
-                    s = cache.get(st, sS, spole, N, G - 1);
-                    ch = schi[G - 1];
-                } else {
-                    const int ga = clamp_group(g + us.s, G);
-                    T fa = cache.get(st, sS, spole, N, ga);
-                    T fbv = cache.get(st, sS, spole, N, ga + 1);
-                    s = freq_mix<T>(fa, fbv, us.t);
-                    ch = chi_mix<T>(schi, slr, ga, us.t);
+            const int gm0 = min(max(-us.s, 0), G), gm1 = max(min(G - 1 - us.s, G), gm0);
+            T *oe = de + k, *oc = dc + k;
+            if (gm0 > 0) {
+                const T v0 = fs.eval(sS, spole, N, 0);
+                const T chl = schi[0] * D;
+                for (int g = 0; g < gm0; ++g, oe += N, oc += N) {
+                    *oc = chl;
+                    *oe = chl * (T(g) + us.x >= P.lgx0 ? v0 : T(0)) * iD3;
                 }
-                T chl = ch * D;
-                dc[(size_t)g * N + k] = chl;
-                de[(size_t)g * N + k] = chl * s * iD3;
+            }
+            if (gm1 > gm0) {
+                int ga = gm0 + us.s;
+                T va = fs.eval(sS, spole, N, ga);
+                T ca = schi[ga];
+                for (int g = gm0; g < gm1; ++g, ++ga, oe += N, oc += N) {
+                    const T vb = fs.eval(sS, spole, N, ga + 1);
+                    const T cb = schi[ga + 1];
+                    const T sv = freq_mix<T>(va, vb, us.t);
+                    const T ch = (ca > T(0) && cb > T(0)) ? freq_mix_lr<T>(ca, slr[ga], us.t)
+                                                          : (T(1) - us.t) * ca + us.t * cb;
+                    const T chl = ch * D;
+                    *oc = chl;
+                    *oe = chl * sv * iD3;
+                    va = vb;
+                    ca = cb;
+                }
+            }
+            if (gm1 < G) {
+                const T v1 = fs.eval(sS, spole, N, G - 1);
+                const T chl = schi[G - 1] * D;
+                for (int g = gm1; g < G; ++g, oe += N, oc += N) {
+                    *oc = chl;
+                    *oe = chl * (T(g) + us.x <= P.lgx1 ? v1 : T(0)) * iD3;
+                }
             }
             continue;
         }
