@@ -271,10 +271,20 @@ __device__ inline R boost_dir(const R u[3], const R n[3], R out[3], R sgn)
     }
     R un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
     R d2 = 0;
+    if constexpr (sizeof(R) == 4) {
+        // single precision: one reciprocal of |u| serves the three components
+        const R ium = R(1) / um;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        R dd = n[i] - sgn * u[i] / um;
-        d2 += dd * dd;
+        for (int i = 0; i < 3; ++i) {
+            R dd = n[i] - sgn * (u[i] * ium);
+            d2 += dd * dd;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            R dd = n[i] - sgn * u[i] / um;
+            d2 += dd * dd;
+        }
     }
     R r = R(1) / (gam + um) + R(0.5) * um * d2;
     R f = R(1) - sgn * un / (gam + R(1));

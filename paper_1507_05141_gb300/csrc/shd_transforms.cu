@@ -550,16 +550,21 @@ __device__ inline void stage_node(T *dst, const T *src, int n)
 
 // Ring averages at the two poles (mesh rings 0 and nmu - 1, summed in mesh
 // order) for every group.
+// One warp per (group, ring) pair: the lanes take the ring's ordinates in
+// strides of 32 and a butterfly adds their partial sums.
 template <class T>
 __device__ inline void pole_averages(const Prob<T> &P, const T *sv, const int *m2i, T *spole)
 {
-    for (int i = threadIdx.x; i < 2 * P.G; i += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x >> 5; i < 2 * P.G; i += nw) {
         const int g = i >> 1, rr = i & 1;
         const T *F = sv + (size_t)g * P.N;
         const int base = rr ? (P.nmu - 1) * P.nphi : 0;
         T s = 0;
-        for (int j = 0; j < P.nphi; ++j) s += F[m2i[base + j]];
-        spole[i] = s / T(P.nphi);
+        for (int j = lane; j < P.nphi; j += 32) s += F[m2i[base + j]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) spole[i] = s / T(P.nphi);
     }
 }
 
@@ -694,12 +699,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
                 for (int g0 = 0; g0 < gm0; ++g0, out += N) *out = (T(g0) + us.x >= P.lgx0 ? v0 : T(0)) * iq3;
             }
             if (gm1 > gm0) {
-                int ga = gm0 + us.s;
+                int ga = gm0 + us.s, g0 = gm0;
                 T va = fs.eval(sI, spole, N, ga);
-                for (int g0 = gm0; g0 < gm1; ++g0, ++ga, out += N) {
+                for (; g0 + 1 < gm1; g0 += 2, ga += 2, out += 2 * N) {
                     const T vb = fs.eval(sI, spole, N, ga + 1);
-                    *out = freq_mix<T>(va, vb, us.t) * iq3;
-                    va = vb;
+                    const T vc = fs.eval(sI, spole, N, ga + 2);
+                    out[0] = freq_mix<T>(va, vb, us.t) * iq3;
+                    out[N] = freq_mix<T>(vb, vc, us.t) * iq3;
+                    va = vc;
+                }
+                if (g0 < gm1) {
+                    *out = freq_mix<T>(va, fs.eval(sI, spole, N, ga + 1), us.t) * iq3;
+                    out += N;
                 }
             }
             if (gm1 < G) {
@@ -776,20 +787,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
                 }
             }
             if (gm1 > gm0) {
-                int ga = gm0 + us.s;
+                int ga = gm0 + us.s, g = gm0;
                 T va = fs.eval(sS, spole, N, ga);
-                T ca = schi[ga];
-                for (int g = gm0; g < gm1; ++g, ++ga, oe += N, oc += N) {
-                    const T vb = fs.eval(sS, spole, N, ga + 1);
-                    const T cb = schi[ga + 1];
-                    const T sv = freq_mix<T>(va, vb, us.t);
-                    const T ch = (ca > T(0) && cb > T(0)) ? freq_mix_lr<T>(ca, slr[ga], us.t)
-                                                          : (T(1) - us.t) * ca + us.t * cb;
+                // one output group: between ga and ga + 1, with V(ga + 1) = vb
+                auto emit = [&](int a, T v0, T v1, T *pe, T *pc) {
+                    const T c0 = schi[a], c1 = schi[a + 1];
+                    const T sv = freq_mix<T>(v0, v1, us.t);
+                    const T ch = (c0 > T(0) && c1 > T(0)) ? freq_mix_lr<T>(c0, slr[a], us.t)
+                                                          : (T(1) - us.t) * c0 + us.t * c1;
                     const T chl = ch * D;
-                    *oc = chl;
-                    *oe = chl * sv * iD3;
-                    va = vb;
-                    ca = cb;
+                    *pc = chl;
+                    *pe = chl * sv * iD3;
+                };
+                for (; g + 1 < gm1; g += 2, ga += 2, oe += 2 * N, oc += 2 * N) {
+                    const T vb = fs.eval(sS, spole, N, ga + 1);
+                    const T vc = fs.eval(sS, spole, N, ga + 2);
+                    emit(ga, va, vb, oe, oc);
+                    emit(ga + 1, vb, vc, oe + N, oc + N);
+                    va = vc;
+                }
+                if (g < gm1) {
+                    emit(ga, va, fs.eval(sS, spole, N, ga + 1), oe, oc);
+                    oe += N;
+                    oc += N;
                 }
             }
             if (gm1 < G) {
