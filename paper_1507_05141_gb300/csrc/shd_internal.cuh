@@ -499,7 +499,7 @@ __device__ inline void sc_weights_narrow<float>(float x, float &e, float &wp, fl
         return;
     }
     // x >= 1/2: e <= 0.61, so 1 - e carries no cancellation
-    float a0 = (1.f - e) * __frcp_rn(x);
+    float a0 = (1.f - e) * __fdividef(1.f, x);  // x >= 1/2: normal range, 1-2 ulp
     wp = 1.f - a0;
     wu = a0 - e;
 }

@@ -359,7 +359,7 @@ __device__ inline T fast_recip(T x);
 template <>
 __device__ inline double fast_recip<double>(double x) { return 1.0 / x; }
 template <>
-__device__ inline float fast_recip<float>(float x) { return __frcp_rn(x); }
+__device__ inline float fast_recip<float>(float x) { return __fdividef(1.f, x); }  // 1-2 ulp for normal x
 
 template <int BYTES>
 __device__ inline void cp_async_n(void *smem, const void *gmem)
@@ -393,10 +393,10 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
     const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
     const int plane = n1 * n2;
     const int pstride = (int)(((size_t)plane + 3) & ~(size_t)3);  // keep every array 16-byte aligned
+    using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     T *pI = reinterpret_cast<T *>(smem_raw);
-    T *pS = pI + pstride;
-    T *pC = pS + pstride;
-    T *ring = pC + pstride;  // [2][3][pstride]
+    T2 *pSC = reinterpret_cast<T2 *>(pI + pstride);  // previous plane's (S, chi) pairs
+    T *ring = pI + 3 * pstride;                       // [2][3][pstride]
     unsigned long long *sbits = reinterpret_cast<unsigned long long *>(ring + 6 * pstride);  // [npc]
     const long long base = ((long long)k * P.G + g) * P.Nc;
     constexpr bool cbits = VEC && CB;
@@ -487,8 +487,9 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
             } else {
                 const int b00 = j, b10 = j - d1, b01 = j - d2, b11 = j - d1 - d2;
                 const T iu = w00 * pI[b00] + w10 * pI[b10] + w01 * pI[b01] + w11 * pI[b11];
-                const T su = w00 * pS[b00] + w10 * pS[b10] + w01 * pS[b01] + w11 * pS[b11];
-                const T cu = w00 * pC[b00] + w10 * pC[b10] + w01 * pC[b01] + w11 * pC[b11];
+                const T2 q00 = pSC[b00], q10 = pSC[b10], q01 = pSC[b01], q11 = pSC[b11];
+                const T su = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                const T cu = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
                 const T dtau = s * T(0.5) * (cu + ct);
                 T ew, wp, wu;
                 if constexpr (WIDE) sc_weights<T>(dtau, ew, wp, wu);
@@ -505,8 +506,10 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
             const int j = tid + NT * u;
             if (j >= plane) break;
             pI[j] = rI[u];
-            pS[j] = rS[u];
-            pC[j] = rC[u];
+            T2 q;
+            q.x = rS[u];
+            q.y = rC[u];
+            pSC[j] = q;
             I[pb + j] = rI[u];
         }
     }
