@@ -418,6 +418,28 @@ __device__ inline FreqBracket<T> freq_bracket(const T *lc, const T *inv, T le0, 
     return b;
 }
 
+// Single-precision hardware approximations (PTX .approx.ftz: subnormal
+// arguments and results are flushed to zero): 2^x, log2(x), 1/x.
+__device__ inline float hw_exp2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ inline float hw_log2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ inline float hw_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kLog2eF = 1.44269504088896341f;  // 1/ln 2
+
 // Geometric between positive values, linear in log(eps) otherwise.
 template <class T>
 __device__ inline T freq_mix(T fa, T fb, T t);
@@ -430,24 +452,29 @@ __device__ inline double freq_mix<double>(double fa, double fb, double t)
 template <>
 __device__ inline float freq_mix<float>(float fa, float fb, float t)
 {
-    // the fast divide holds its 2-ulp bound for divisors of normal size
-    if (fa >= 1.17549435e-38f && fa < 8.5e37f && fb > 0.f) return fa * __expf(t * __logf(__fdividef(fb, fa)));
-    if (fa > 0.f && fb > 0.f) return fa * __expf(t * __logf(fb / fa));
+    // fa^(1-t) fb^t = fa 2^(t log2(fb/fa)) by the hardware approximations
+    // while every operand stays a normal number, else by the library
+    if (fa >= 1.17549435e-38f && fb >= 1.17549435e-38f) {
+        const float r = fb * hw_rcp(fa);
+        if (r >= 1.17549435e-38f && r <= 3.4e38f) return fa * hw_exp2(t * hw_log2(r));
+    }
+    if (fa > 0.f && fb > 0.f) return fa * expf(t * logf(fb / fa));
     return (1.f - t) * fa + t * fb;
 }
 
-// Geometric mix whose log ratio log(fb/fa) is already known (both positive).
+// Geometric mix whose log ratio lr = log2(fb/fa) is already known (both
+// positive).
 template <class T>
 __device__ inline T freq_mix_lr(T fa, T lr, T t);
 template <>
 __device__ inline double freq_mix_lr<double>(double fa, double lr, double t)
 {
-    return fa * exp(t * lr);
+    return fa * exp2(t * lr);
 }
 template <>
 __device__ inline float freq_mix_lr<float>(float fa, float lr, float t)
 {
-    return fa * __expf(t * lr);
+    return fa * hw_exp2(t * lr);
 }
 
 // Linear-in-tau short-characteristic weights with e = exp(-x):
@@ -492,14 +519,14 @@ __device__ inline void sc_weights_narrow<double>(double x, double &e, double &wp
 template <>
 __device__ inline void sc_weights_narrow<float>(float x, float &e, float &wp, float &wu)
 {
-    e = __expf(-x);
+    e = hw_exp2(-x * kLog2eF);
     if (x < 0.5f) {
         wp = x * (1.f / 2 - x * (1.f / 6 - x * (1.f / 24 - x * (1.f / 120 - x * (1.f / 720 - x * (1.f / 5040 - x * (1.f / 40320 - x / 362880.f)))))));
         wu = x * (1.f / 2 - x * (1.f / 3 - x * (1.f / 8 - x * (1.f / 30 - x * (1.f / 144 - x * (1.f / 840 - x * (1.f / 5760 - x / 45360.f)))))));
         return;
     }
     // x >= 1/2: e <= 0.61, so 1 - e carries no cancellation
-    float a0 = (1.f - e) * __fdividef(1.f, x);  // x >= 1/2: normal range, 1-2 ulp
+    float a0 = (1.f - e) * hw_rcp(x);
     wp = 1.f - a0;
     wu = a0 - e;
 }

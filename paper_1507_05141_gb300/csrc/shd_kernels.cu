@@ -359,7 +359,7 @@ __device__ inline T fast_recip(T x);
 template <>
 __device__ inline double fast_recip<double>(double x) { return 1.0 / x; }
 template <>
-__device__ inline float fast_recip<float>(float x) { return __fdividef(1.f, x); }  // 1-2 ulp for normal x
+__device__ inline float fast_recip<float>(float x) { return hw_rcp(x); }
 
 template <int BYTES>
 __device__ inline void cp_async_n(void *smem, const void *gmem)
@@ -393,10 +393,14 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
     const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
     const int plane = n1 * n2;
     const int pstride = (int)(((size_t)plane + 3) & ~(size_t)3);  // keep every array 16-byte aligned
+    // previous plane: FP32 keeps (I, S, chi) of a node in one float4, FP64
+    // keeps I apart from the (S, chi) pairs
+    constexpr bool PK = sizeof(T) == 4;
     using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    float4 *pQ = reinterpret_cast<float4 *>(smem_raw);
     T *pI = reinterpret_cast<T *>(smem_raw);
-    T2 *pSC = reinterpret_cast<T2 *>(pI + pstride);  // previous plane's (S, chi) pairs
-    T *ring = pI + 3 * pstride;                       // [2][3][pstride]
+    T2 *pSC = reinterpret_cast<T2 *>(pI + pstride);
+    T *ring = pI + (PK ? 4 : 3) * pstride;  // [2][3][pstride]
     unsigned long long *sbits = reinterpret_cast<unsigned long long *>(ring + 6 * pstride);  // [npc]
     const long long base = ((long long)k * P.G + g) * P.Nc;
     constexpr bool cbits = VEC && CB;
@@ -486,10 +490,18 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
                 inew = bc_full ? P.bc[pb + j] : bc_iso;
             } else {
                 const int b00 = j, b10 = j - d1, b01 = j - d2, b11 = j - d1 - d2;
-                const T iu = w00 * pI[b00] + w10 * pI[b10] + w01 * pI[b01] + w11 * pI[b11];
-                const T2 q00 = pSC[b00], q10 = pSC[b10], q01 = pSC[b01], q11 = pSC[b11];
-                const T su = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
-                const T cu = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                T iu, su, cu;
+                if constexpr (PK) {
+                    const float4 q00 = pQ[b00], q10 = pQ[b10], q01 = pQ[b01], q11 = pQ[b11];
+                    iu = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                    su = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                    cu = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+                } else {
+                    iu = w00 * pI[b00] + w10 * pI[b10] + w01 * pI[b01] + w11 * pI[b11];
+                    const T2 q00 = pSC[b00], q10 = pSC[b10], q01 = pSC[b01], q11 = pSC[b11];
+                    su = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                    cu = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                }
                 const T dtau = s * T(0.5) * (cu + ct);
                 T ew, wp, wu;
                 if constexpr (WIDE) sc_weights<T>(dtau, ew, wp, wu);
@@ -505,11 +517,15 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
         for (int u = 0; u < U; ++u) {
             const int j = tid + NT * u;
             if (j >= plane) break;
-            pI[j] = rI[u];
-            T2 q;
-            q.x = rS[u];
-            q.y = rC[u];
-            pSC[j] = q;
+            if constexpr (PK) {
+                pQ[j] = make_float4(rI[u], rS[u], rC[u], 0.f);
+            } else {
+                pI[j] = rI[u];
+                T2 q;
+                q.x = rS[u];
+                q.y = rC[u];
+                pSC[j] = q;
+            }
             I[pb + j] = rI[u];
         }
     }
@@ -790,12 +806,13 @@ static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, con
     return cudaGetLastError();
 }
 
-// shared memory of the pipelined sweep: previous plane (3 arrays) + 2-stage
-// ring of the three inputs, each array padded to a multiple of 4 reals
+// shared memory of the pipelined sweep: previous plane (4 reals a node in
+// FP32, 3 in FP64) + 2-stage ring of the three inputs, each array padded to
+// a multiple of 4 reals
 size_t sweep_pipe_smem_bytes(const shd_ctx *c)
 {
     size_t ps = ((size_t)sweep_plane_max(c) + 3) & ~(size_t)3;
-    return c->esize * ps * 9;
+    return c->esize * ps * (c->esize == 4 ? 10 : 9);
 }
 
 // 16-byte copies when every plane and the array base stay 16-byte aligned

@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
     T *sS = reinterpret_cast<T *>(smem_raw);  // [G][N] internal order
     T *spole = sS + (size_t)G * N;            // [G][2]
     T *schi = spole + 2 * G;                  // [G]
-    T *slr = schi + G;                        // [G] FP32: log(chi0[g+1]/chi0[g]) where both > 0
+    T *slr = schi + G;                        // [G] FP32: log2(chi0[g+1]/chi0[g]) where both > 0
     const long long m = blockIdx.x;
     const long long c = P.moving[m];
     stage_node<T>(sS, S0 + m * G * N, G * N);
@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
     pole_averages<T>(P, sS, tb.m2i, spole);
     for (int g = threadIdx.x; sizeof(T) == 4 && g + 1 < G; g += blockDim.x) {
         const T a = schi[g], b = schi[g + 1];
-        slr[g] = (a > T(0) && b > T(0)) ? dlog<T>(b / a) : T(0);
+        slr[g] = (a > T(0) && b > T(0)) ? T(log2f(float(b / a))) : T(0);
     }
     __syncthreads();
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
