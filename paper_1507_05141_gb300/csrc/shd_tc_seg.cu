@@ -865,17 +865,24 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
                 const bool yc = !S.groupB && ci.x == 1;
                 tc::tma_store_5d(mp_base + ci.x, as, yc ? sd.x : bs, yc ? bs : sd.x, g, kk, src);
             };
-            auto prefetch = [&](int cn, int b) {
+            // a moving row's 16 values of chunk cn (its own node-major row, 16-byte
+            // loads where aligned) into registers, one chunk ahead of their use
+            float mv[16];
+            auto load_moving = [&](int cn) {
                 if (m < 0) return;
                 const int4 ci = S.chunk[cn];
                 const int kl0 = ci.y + 16 * half;
                 const float *src = nsrc + nbase + ci.z + kl0;
-                float *dst = W + (size_t)b * 512 + lane;
-                for (int q = 0; q < 16; ++q)
-                    if (kl0 + q < ci.w) {
-                        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + q * 32);
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + q) : "memory");
+                if (kl0 + 16 <= ci.w && ((ci.z + kl0) & 3) == 0) {
+#pragma unroll
+                    for (int c4 = 0; c4 < 4; ++c4) {
+                        const float4 t = reinterpret_cast<const float4 *>(src)[c4];
+                        mv[4 * c4] = t.x; mv[4 * c4 + 1] = t.y; mv[4 * c4 + 2] = t.z; mv[4 * c4 + 3] = t.w;
                     }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) mv[q] = kl0 + q < ci.w ? src[q] : 0.f;
+                }
             };
             bool ok = true;
             if (!eta_w && !anym) {
@@ -891,8 +898,7 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
                     }
                 }
             } else {
-                if (anym) prefetch(0, 0);
-                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                if (anym) load_moving(0);
                 int jb = -1;  // accumulator of the current job
                 for (int cn = 0; cn < nchunk; ++cn) {
                     const int h = cn >> 3;
@@ -906,26 +912,22 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
                         tc::fence_after_sync();
                     }
                     const int b = cn & 1;
-                    if (lane == 0) {
-                        if (anym) tc::bulk_wait_read<0>();
-                        else tc::bulk_wait_read<1>();
-                    }
+                    if (lane == 0) tc::bulk_wait_read<1>();  // the store of chunk cn - 2 has read buffer b
                     __syncwarp();
-                    if (anym && cn + 1 < nchunk) prefetch(cn + 1, b ^ 1);
-                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                    float cur[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) cur[q] = mv[q];
+                    if (anym && cn + 1 < nchunk) load_moving(cn + 1);
                     float *Wb = W + (size_t)b * 512 + lane;
                     if (eta_w) {
                         float v[16];
                         tc::tmem_ld16(trow + (uint32_t)(256 * jb + (cn & 7) * kKC + 16 * half), v);
-                        if (m < 0) {
 #pragma unroll
-                            for (int q = 0; q < 16; ++q) Wb[q * 32] = chr * v[q];
-                        }
-                    } else if (m < 0) {
+                        for (int q = 0; q < 16; ++q) Wb[q * 32] = m < 0 ? chr * v[q] : cur[q];
+                    } else {
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) Wb[q * 32] = chr;
+                        for (int q = 0; q < 16; ++q) Wb[q * 32] = m < 0 ? chr : cur[q];
                     }
-                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
                     tc::fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) {
@@ -933,7 +935,6 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
                         tc::bulk_commit();
                     }
                 }
-                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
                 if (eta_w && ok && jb >= 0) {
                     tc::fence_before_sync();
                     tc::mbar_arrive(&tEmpty[jb]);
