@@ -362,28 +362,58 @@ __global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __g
                     ip = Ip + (P.moving[m] * G + (row - m * G)) * NLM;
                 }
             }
-            const int b = (int)(job & 1);
-            if (!wait(&tfull[b], (uint32_t)((job >> 1) & 1))) break;
-            tc::fence_after_sync();
-            for (int c0 = 0; c0 < nb; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * ACC_COLS + (uint32_t)c0, v);
+            // accumulating: the row's previous values, one block of 16 columns
+            // ahead of their use (the first block before the accumulator is
+            // ready), so that a block's loads are in flight together
+            auto load_old = [&](int c0, float (&o)[16]) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int col = c0 + 4 * q;
                     if (ip && sh4 && col + 4 <= NLM) {
-                        put4(ip + col, &v[4 * q], acc);
+                        const float4 a4 = *reinterpret_cast<const float4 *>(ip + col);
+                        o[4 * q] = a4.x; o[4 * q + 1] = a4.y; o[4 * q + 2] = a4.z; o[4 * q + 3] = a4.w;
+                        continue;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int cc = col + e;
+                        o[4 * q + e] = cc < NLM ? (ip ? ip[cc] : 0.f) : (cc < NLM + 10 && mp ? mp[cc - NLM] : 0.f);
+                    }
+                }
+            };
+            float oc[16], on[16];
+            if (acc) load_old(0, oc);
+            const int b = (int)(job & 1);
+            if (!wait(&tfull[b], (uint32_t)((job >> 1) & 1))) break;
+            tc::fence_after_sync();
+            for (int c0 = 0; c0 < nb; c0 += 16) {
+                if (acc && c0 + 16 < nb) load_old(c0 + 16, on);
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * ACC_COLS + (uint32_t)c0, v);
+                if (acc) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += oc[i];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int col = c0 + 4 * q;
+                    if (ip && sh4 && col + 4 <= NLM) {
+                        put4(ip + col, &v[4 * q], false);
                         continue;
                     }
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int cc = col + e;
                         if (cc < NLM) {
-                            if (ip) put1(ip + cc, v[4 * q + e], acc);
+                            if (ip) put1(ip + cc, v[4 * q + e], false);
                         } else if (cc < NLM + 10) {
-                            if (mp) put1(mp + (cc - NLM), v[4 * q + e], acc);
+                            if (mp) put1(mp + (cc - NLM), v[4 * q + e], false);
                         }
                     }
+                }
+                if (acc) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) oc[i] = on[i];
                 }
             }
             tc::fence_before_sync();
