@@ -573,15 +573,30 @@ __global__ void k_sums_partial(Prob<T> P, const T *__restrict__ mom, const T *__
     if (threadIdx.x < 4) partial[blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-__global__ void k_sums_final(const double *partial, int nblocks, int have_prev, double *out)
+// One CTA of kSumsThreads: thread t adds partials t, t + kSumsThreads, ...
+// in order, then a halving tree adds the threads' sums (a fixed order, so
+// the result does not change from run to run).
+constexpr int kSumsThreads = 256;
+__global__ void __launch_bounds__(kSumsThreads) k_sums_final(const double *partial, int nblocks, int have_prev,
+                                                             double *out)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double red[4][kSumsThreads];
+    const int t = threadIdx.x;
     double acc[4] = {0, 0, 0, 0};
-    for (int b = 0; b < nblocks; ++b)
+    for (int b = t; b < nblocks; b += kSumsThreads)
         for (int q = 0; q < 4; ++q) acc[q] += partial[b * 4 + q];
-    out[0] = acc[0];
-    out[1] = acc[1];
-    out[2] = (have_prev && acc[3] > 0) ? sqrt(acc[2] / acc[3]) : 0.0;
+    for (int q = 0; q < 4; ++q) red[q][t] = acc[q];
+    __syncthreads();
+    for (int w = kSumsThreads / 2; w > 0; w >>= 1) {
+        if (t < w)
+            for (int q = 0; q < 4; ++q) red[q][t] += red[q][t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[0] = red[0][0];
+        out[1] = red[1][0];
+        out[2] = (have_prev && red[3][0] > 0) ? sqrt(red[2][0] / red[3][0]) : 0.0;
+    }
 }
 
 // -------------------------------------------------------------------------
@@ -874,7 +889,7 @@ cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev,
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sums_final<<<1, 32, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
+    k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
     note_launch();
     return cudaGetLastError();
 }
@@ -904,7 +919,7 @@ cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, c
     kern<<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, ctx->d_partial);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_sums_final<<<1, 32, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
+    k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
     note_launch();
     return cudaGetLastError();
 }
