@@ -780,56 +780,80 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
     if (warp >= 16 && warp < 20) {
         // ---------------- A builders ----------------
         const int r = (warp - 16) * 32 + lane;
-        long long it = 0;
-        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x, ++it) {
+        const bool vec = (NLM & 3) == 0;
+        // row r of item w: its S offset (-1: none or moving), chi0, moving index
+        auto row_of = [&](long long w, long long &src, float &ch, int &m) {
             const long long sg = w / G;
             const int g = (int)(w - sg * G);
-            const int pb = (int)(it & 1);
-            if (it >= 2 && !wait(&itemDone[pb], (uint32_t)(((it >> 1) - 1) & 1))) break;
-            long long c = 0, src = -1;
-            float ch = 0.f;
-            int m = -1;
+            long long c = 0;
+            src = -1;
+            ch = 0.f;
+            m = -1;
             if (seg_node(P, S, S.segs[sg], r, c)) {
                 ch = P.chi0[c * G + g];
                 m = P.midx[c];
                 if (m < 0) src = (c * G + g) * NLM;
             }
+        };
+        // harmonics [p0, p0 + 32) of the row (16-byte loads when the rows are
+        // 16-byte aligned), all in flight together
+        auto load_round = [&](long long src, int p0, float (&v)[32]) {
+            if (vec) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int p = p0 + 4 * q;
+                    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (src >= 0 && p < NLM) t = *reinterpret_cast<const float4 *>(Sp + src + p);
+                    v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = (src >= 0 && p0 + q < NLM) ? Sp[src + p0 + q] : 0.f;
+            }
+        };
+        auto put_round = [&](int p0, const float (&v)[32]) {
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+                if (p0 + kb * 8 >= Kq) break;
+                uint4 h, l;
+                split2(v[8 * kb], v[8 * kb + 1], h.x, l.x);
+                split2(v[8 * kb + 2], v[8 * kb + 3], h.y, l.y);
+                split2(v[8 * kb + 4], v[8 * kb + 5], h.z, l.z);
+                split2(v[8 * kb + 6], v[8 * kb + 7], h.w, l.w);
+                const int o = tc::canon_off(r, p0 + kb * 8, Kq);
+                *reinterpret_cast<uint4 *>(&Ah[o]) = h;
+                *reinterpret_cast<uint4 *>(&Al[o]) = l;
+            }
+        };
+        // the first round of each item's row is loaded one item ahead (in
+        // flight while the A buffer is still in use)
+        float v[32];
+        long long src = -1;
+        float ch = 0.f;
+        int m = -1;
+        if (blockIdx.x < S.nitem) {
+            row_of(blockIdx.x, src, ch, m);
+            load_round(src, 0, v);
+        }
+        long long it = 0;
+        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x, ++it) {
+            const int pb = (int)(it & 1);
+            if (it >= 2 && !wait(&itemDone[pb], (uint32_t)(((it >> 1) - 1) & 1))) break;
             mchi[pb * 128 + r] = ch;
             mrow[pb * 128 + r] = m;
             tc::mbar_arrive(&metaFull[pb]);
             if (it >= 1 && !wait(aEmpty, (uint32_t)((it - 1) & 1))) break;
-            // the row in rounds of 32 harmonics: all of a round's loads are in
-            // flight together (16-byte loads when the rows are 16-byte aligned)
-            const bool vec = (NLM & 3) == 0;
-            for (int p0 = 0; p0 < Kq; p0 += 32) {
-                float v[32];
-                if (vec) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int p = p0 + 4 * q;
-                        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (src >= 0 && p < NLM) t = *reinterpret_cast<const float4 *>(Sp + src + p);
-                        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = (src >= 0 && p0 + q < NLM) ? Sp[src + p0 + q] : 0.f;
-                }
-#pragma unroll
-                for (int kb = 0; kb < 4; ++kb) {
-                    if (p0 + kb * 8 >= Kq) break;
-                    uint4 h, l;
-                    split2(v[8 * kb], v[8 * kb + 1], h.x, l.x);
-                    split2(v[8 * kb + 2], v[8 * kb + 3], h.y, l.y);
-                    split2(v[8 * kb + 4], v[8 * kb + 5], h.z, l.z);
-                    split2(v[8 * kb + 6], v[8 * kb + 7], h.w, l.w);
-                    const int o = tc::canon_off(r, p0 + kb * 8, Kq);
-                    *reinterpret_cast<uint4 *>(&Ah[o]) = h;
-                    *reinterpret_cast<uint4 *>(&Al[o]) = l;
-                }
+            put_round(0, v);
+            for (int p0 = 32; p0 < Kq; p0 += 32) {
+                load_round(src, p0, v);
+                put_round(p0, v);
             }
             tc::fence_proxy_async();
             tc::mbar_arrive(aFull);
+            if (w + gridDim.x < S.nitem) {
+                row_of(w + gridDim.x, src, ch, m);
+                load_round(src, 0, v);
+            }
         }
     } else if (warp == 20) {
         // ---------------- MMA issuer ----------------
