@@ -169,9 +169,11 @@ void free_all(shd_ctx *c)
                      (void **)&c->d_int2mesh, (void **)&c->d_mesh2int,
                      &c->d_chi0L, (void **)&c->d_mbits, &c->d_seg[0], &c->d_seg[1], &c->d_tcs_Bh[0], &c->d_tcs_Bh[1], &c->d_tcs_Bl[0],
                      &c->d_tcs_Bl[1], &c->d_tcs_Yh[0], &c->d_tcs_Yh[1], &c->d_tcs_Yl[0], &c->d_tcs_Yl[1],
-                     (void **)&c->d_tc_err};
+                     (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1]};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
+    c->rtab_n = 0;
+    c->rtab_valid = false;
 }
 
 bool is_fp64(const shd_ctx *c) { return c->precision == SHD_FP64; }
@@ -203,10 +205,13 @@ void drop_sized(shd_ctx *c)
                      &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
                      (void **)&c->d_partial, (void **)&c->d_stage,
                      &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag,
-                     (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2]};
+                     (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
+                     &c->d_rtab[0], &c->d_rtab[1]};
     for (void **p : ptrs) dfree(*p);
     c->ntiles = 0;
     c->nmoving = 0;
+    c->rtab_n = 0;
+    c->rtab_valid = false;
     c->have_fields = c->have_scat = c->have_state = false;
     c->bc_mode = SHD_BC_VACUUM;
     c->sprev_valid = false;
@@ -720,6 +725,27 @@ int ready_for_step(shd_ctx *c)
     return SHD_OK;
 }
 
+// The FP32 remap tables of the moving nodes, built on the library's stream
+// (and waited for) when the flow or the angles changed since the last build.
+// Without them the remap kernels compute the boosts and stencils in place.
+int ensure_remap_tables(shd_ctx *c)
+{
+    if (is_fp64(c) || c->rtab_valid || c->nmoving == 0 || !c->have_fields || !c->have_angles || c->nmu > 1024)
+        return SHD_OK;  // (the entries pack the ring index in 10 bits)
+    const size_t n = (size_t)c->nmoving * c->N;
+    int rc;
+    if (n != c->rtab_n || !c->d_rtab[0] || !c->d_rtab[1]) {
+        c->rtab_n = 0;
+        for (int i = 0; i < 2; ++i)
+            if ((rc = dalloc(c, &c->d_rtab[i], n * sizeof(float4), "remap tables"))) return rc;
+        c->rtab_n = n;
+    }
+    CK(launch_remap_tables_f(c, (float4 *)c->d_rtab[0], (float4 *)c->d_rtab[1], c->stream), "remap tables");
+    CK(cudaStreamSynchronize(c->stream), "remap tables");
+    c->rtab_valid = true;
+    return SHD_OK;
+}
+
 // The kernels of one step on stream st (timing events around the stages when
 // ev is given); S_lm / S_prev are not swapped here.
 template <class T>
@@ -771,6 +797,8 @@ template <class T>
 int capture_step(shd_ctx *c, int i)
 {
     if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+    int rt = ensure_remap_tables(c);  // built outside the graph, read in place by every replay
+    if (rt) return rt;
     const unsigned long long n0 = shd_launch_count_now();
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     const int rc = step_once<T>(c, c->cap_stream, nullptr);
@@ -822,6 +850,7 @@ int graph_slot(shd_ctx *c, int &slot)
 template <class T>
 int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false)
 {
+    if (int rc = ensure_remap_tables(c)) return rc;
     for (int s = 0; s < nsteps; ++s) {
         bool tm = c->timing.on && c->timing.count < Timing::kCap;
         cudaEvent_t *ev = tm ? &c->timing.pool[(size_t)c->timing.count * (Timing::kStages + 1)] : nullptr;
@@ -1025,6 +1054,7 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         if ((rc = upload_reals<float>(c, u, c->d_u, 3 * c->Nc))) return rc;
         if ((rc = upload_reals<float>(c, emis0, c->d_emis0, nCG))) return rc;
     }
+    c->rtab_valid = false;  // the flow may have changed
     // the node tables (and with them the captured step) change only when the
     // set of moving nodes does; new field values are read in place
     std::vector<unsigned char> mf((size_t)c->Nc);

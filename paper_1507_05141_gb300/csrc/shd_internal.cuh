@@ -171,6 +171,13 @@ struct shd_ctx {
     // project: nm[0] = laboratory I, nm[1] = comoving I0;
     // sh2lab:  nm[0] = comoving S0, nm[1] = eta_lab, nm[2] = chi_lab
     void *d_nm[3] = {nullptr, nullptr, nullptr};
+    // FP32 remap tables of the moving nodes, [m][k] float4 {stencil code,
+    // t, tp, Doppler ratio}: [0] comoving remap (n_k boosted to the
+    // laboratory, nu/nu0), [1] laboratory remap (n_k boosted to the comoving
+    // frame, nu0/nu); rebuilt after the fields or angles change
+    void *d_rtab[2] = {nullptr, nullptr};
+    size_t rtab_n = 0;
+    bool rtab_valid = false;
     void *d_lc = nullptr, *d_linv = nullptr;  // log-energy group tables
     // tensor-core operands of the mixed path (BF16 hi / lo, canonical K-major)
     void *d_tc_Bh = nullptr, *d_tc_Bl = nullptr;  // [NB][tc_Kp]   projection matrix
@@ -327,10 +334,19 @@ struct Stencil {
     T wpole;
 };
 
+// The stencil's placement on the mesh: between rings a and a+1 (mode 0),
+// between a pole and its outer ring a (1 south, 2 north), or on the single
+// ring of a one-ring mesh (3); phi bin b; fractions t (mu) and tp (phi).
 template <class T>
-__device__ inline Stencil<T> make_stencil(const T *mu, int nmu, int nphi, const T n[3])
+struct StencilParams {
+    int mode, a, b;
+    T t, tp;
+};
+
+template <class T>
+__device__ inline StencilParams<T> stencil_params(const T *mu, int nmu, int nphi, const T n[3])
 {
-    Stencil<T> s;
+    StencilParams<T> p;
     T m = n[2];
     m = m > T(1) ? T(1) : (m < T(-1) ? T(-1) : m);
     T phi = datan2<T>(n[1], n[0]);
@@ -340,19 +356,14 @@ __device__ inline Stencil<T> make_stencil(const T *mu, int nmu, int nphi, const 
     T tp = x - T(b);
     if (b >= nphi) b -= nphi;
     if (!(b >= 0 && b < nphi)) { b = 0; tp = 0; }  // non-finite direction: stay in bounds
-    int b1 = b + 1 == nphi ? 0 : b + 1;
-    s.pole_ring = -1;
-    s.wpole = 0;
+    p.b = b;
+    p.tp = tp;
     if (m < mu[0] || m > mu[nmu - 1]) {
-        int ring = m < mu[0] ? 0 : nmu - 1;
-        T t = m < mu[0] ? (m + T(1)) / (mu[0] + T(1)) : (T(1) - m) / (T(1) - mu[nmu - 1]);
-        s.pole_ring = ring;
-        s.wpole = T(1) - t;
-        s.k[0] = ring * nphi + b;  s.w[0] = t * (T(1) - tp);
-        s.k[1] = ring * nphi + b1; s.w[1] = t * tp;
-        s.k[2] = s.k[0]; s.w[2] = 0;
-        s.k[3] = s.k[1]; s.w[3] = 0;
-        return s;
+        const bool south = m < mu[0];
+        p.mode = south ? 1 : 2;
+        p.a = south ? 0 : nmu - 1;
+        p.t = south ? (m + T(1)) / (mu[0] + T(1)) : (T(1) - m) / (T(1) - mu[nmu - 1]);
+        return p;
     }
     if (nmu > 1) {
         // ring bracket: the largest a <= nmu - 2 with mu[a] < m (0 if none),
@@ -363,7 +374,36 @@ __device__ inline Stencil<T> make_stencil(const T *mu, int nmu, int nphi, const 
             if (mu[mid] < m) a = mid;
             else hi = mid - 1;
         }
-        T t = (m - mu[a]) / (mu[a + 1] - mu[a]);
+        p.mode = 0;
+        p.a = a;
+        p.t = (m - mu[a]) / (mu[a + 1] - mu[a]);
+    } else {
+        p.mode = 3;
+        p.a = 0;
+        p.t = 0;
+    }
+    return p;
+}
+
+// Four (mesh ordinate, weight) pairs plus the pole term of a placement.
+template <class T>
+__device__ inline Stencil<T> stencil_from_params(const StencilParams<T> &p, int nphi)
+{
+    Stencil<T> s;
+    const int b = p.b, b1 = b + 1 == nphi ? 0 : b + 1;
+    const T t = p.t, tp = p.tp;
+    s.pole_ring = -1;
+    s.wpole = 0;
+    if (p.mode == 1 || p.mode == 2) {
+        const int ring = p.a;
+        s.pole_ring = ring;
+        s.wpole = T(1) - t;
+        s.k[0] = ring * nphi + b;  s.w[0] = t * (T(1) - tp);
+        s.k[1] = ring * nphi + b1; s.w[1] = t * tp;
+        s.k[2] = s.k[0]; s.w[2] = 0;
+        s.k[3] = s.k[1]; s.w[3] = 0;
+    } else if (p.mode == 0) {
+        const int a = p.a;
         s.k[0] = a * nphi + b;       s.w[0] = (T(1) - t) * (T(1) - tp);
         s.k[1] = a * nphi + b1;      s.w[1] = (T(1) - t) * tp;
         s.k[2] = (a + 1) * nphi + b; s.w[2] = t * (T(1) - tp);
@@ -375,6 +415,12 @@ __device__ inline Stencil<T> make_stencil(const T *mu, int nmu, int nphi, const 
         s.k[3] = b1; s.w[3] = 0;
     }
     return s;
+}
+
+template <class T>
+__device__ inline Stencil<T> make_stencil(const T *mu, int nmu, int nphi, const T n[3])
+{
+    return stencil_from_params<T>(stencil_params<T>(mu, nmu, nphi, n), nphi);
 }
 
 // F points at one group's N ordinate values; poles at that group's two ring
@@ -562,6 +608,7 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
                                cudaStream_t st);
 cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,
                               float *nm2, cudaStream_t st, bool full_chi);
+cudaError_t launch_remap_tables_f(const shd_ctx *ctx, float4 *tc, float4 *tl, cudaStream_t st);
 cudaError_t launch_remap_to_comoving_f(const shd_ctx *ctx, const float *nm0, float *nm1, cudaStream_t st);
 cudaError_t launch_remap_to_lab_f(const shd_ctx *ctx, const float *nm0, float *nm1, float *nm2, cudaStream_t st);
 size_t project_tc_smem_bytes(const shd_ctx *ctx);

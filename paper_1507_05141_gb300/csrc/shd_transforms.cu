@@ -596,6 +596,51 @@ struct GroupCache {
     }
 };
 
+// Remap table entries: the stencil placement packed as mode | a << 2 | b << 12
+// in the first word (a < 1024 rings, b < 2^20 phi bins), then t, tp and the
+// Doppler ratio.
+__device__ inline float4 table_entry(const StencilParams<float> &p, float ratio)
+{
+    return make_float4(__int_as_float(p.mode | (p.a << 2) | (p.b << 12)), p.t, p.tp, ratio);
+}
+
+template <class T>
+__device__ inline Stencil<T> table_stencil(const float4 &e, int nphi, const int *m2i)
+{
+    const int code = __float_as_int(e.x);
+    StencilParams<T> p;
+    p.mode = code & 3;
+    p.a = (code >> 2) & 1023;
+    p.b = code >> 12;
+    p.t = (T)e.y;
+    p.tp = (T)e.z;
+    Stencil<T> s = stencil_from_params<T>(p, nphi);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s.k[i] = m2i[s.k[i]];
+    return s;
+}
+
+// One thread per (moving node m, internal ordinate k): the Lorentz boosts of
+// n_k (Sec. 2.2) and the stencils of the boosted directions, as the remap
+// kernels would compute them: tc for the comoving remap (n_k taken to the
+// laboratory, nu/nu0), tl for the laboratory remap (n_k taken to the
+// comoving frame, nu0/nu).  They depend only on the flow and the angles.
+__global__ void __launch_bounds__(256) k_remap_tables(Prob<float> P, float4 *__restrict__ tc, float4 *__restrict__ tl)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.nmoving * P.N) return;
+    const long long m = i / P.N;
+    const int k = (int)(i - m * P.N);
+    const long long c = P.moving[m];
+    const float u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
+    const float nk[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
+    float nb[3];
+    const float q = boost_any<float>(u, nk, nb, -1.f, P.fp64_boost);
+    tc[i] = table_entry(stencil_params<float>(P.mu, P.nmu, P.nphi, nb), q);
+    const float D = boost_any<float>(u, nk, nb, 1.f, P.fp64_boost);
+    tl[i] = table_entry(stencil_params<float>(P.mu, P.nmu, P.nphi, nb), D);
+}
+
 // Energy offset x = l / (log spacing) of equally spaced log centres, split
 // into its whole part s and fraction t.
 template <class T>
@@ -660,7 +705,8 @@ __device__ inline T chi_mix(const T *schi, const T *slr, int ga, T t)
 // node: I0(k0, g0) = (ebar_g0/eps)^3 I_lab(n, eps), n = boost of n_k0 to the
 // laboratory, eps = ebar_g0 (Gamma + u.n_k0)   (Sec. 2.2)
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__restrict__ I0)
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__restrict__ I0,
+                                                           const float4 *__restrict__ tab)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G, N = P.N;
@@ -676,10 +722,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
     T *dst = I0 + m * G * N;
     for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
-        T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
-        T n[3];
-        T q = boost_any<T>(u, n0, n, T(-1), P.fp64_boost);  // nu/nu0
-        const Stencil<T> st = stencil_internal<T>(P, tb, n);
+        T q;  // nu/nu0
+        Stencil<T> st;
+        if (sizeof(T) == 4 && tab) {
+            const float4 e = tab[m * N + k0];
+            q = (T)e.w;
+            st = table_stencil<T>(e, P.nphi, tb.m2i);
+        } else {
+            T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
+            T n[3];
+            q = boost_any<T>(u, n0, n, T(-1), P.fp64_boost);
+            st = stencil_internal<T>(P, tb, n);
+        }
         T iq3 = T(1) / (q * q * q);
         T lq = dlog<T>(q);
         GroupCache<T> cache;
@@ -740,7 +794,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
 // S_lab = S0(n0, eps0)/D^3, chi_lab = chi0(eps0) D, eta_lab = chi_lab S_lab
 template <class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restrict__ eta_n,
-                                                      T *__restrict__ chi_n)
+                                                      T *__restrict__ chi_n, const float4 *__restrict__ tab)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G, N = P.N;
@@ -763,10 +817,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
     T *de = eta_n + m * G * N, *dc = chi_n + m * G * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
-        T n0[3];
-        T D = boost_any<T>(u, n, n0, T(1), P.fp64_boost);  // nu0/nu
-        const Stencil<T> st = stencil_internal<T>(P, tb, n0);
+        T D;  // nu0/nu
+        Stencil<T> st;
+        if (sizeof(T) == 4 && tab) {
+            const float4 e = tab[m * N + k];
+            D = (T)e.w;
+            st = table_stencil<T>(e, P.nphi, tb.m2i);
+        } else {
+            T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
+            T n0[3];
+            D = boost_any<T>(u, n, n0, T(1), P.fp64_boost);
+            st = stencil_internal<T>(P, tb, n0);
+        }
         T iD3 = T(1) / (D * D * D);
         T lD = dlog<T>(D);
         GroupCache<T> cache;
@@ -927,7 +989,8 @@ static cudaError_t run_remap_to_comoving(const shd_ctx *ctx, const T *nm0, T *nm
     size_t sm = remap_smem_bytes(ctx);
     cudaError_t e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1);
+    const float4 *tab = sizeof(T) == 4 && ctx->rtab_valid ? (const float4 *)ctx->d_rtab[0] : nullptr;
+    k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1, tab);
     note_launch();
     return cudaGetLastError();
 }
@@ -939,7 +1002,18 @@ static cudaError_t run_remap_to_lab(const shd_ctx *ctx, const T *nm0, T *nm1, T 
     size_t sr = remap_smem_bytes(ctx);
     cudaError_t e = cudaFuncSetAttribute(k_remap_to_lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
     if (e != cudaSuccess) return e;
-    k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2);
+    const float4 *tab = sizeof(T) == 4 && ctx->rtab_valid ? (const float4 *)ctx->d_rtab[1] : nullptr;
+    k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2, tab);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_remap_tables_f(const shd_ctx *ctx, float4 *tc, float4 *tl, cudaStream_t st)
+{
+    Prob<float> P = make_prob<float>(ctx);
+    const long long n = ctx->nmoving * ctx->N;
+    if (n == 0) return cudaSuccess;
+    k_remap_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, tc, tl);
     note_launch();
     return cudaGetLastError();
 }
