@@ -714,6 +714,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
     T *spole = sI + (size_t)G * N;            // [G][2]
     const long long m = blockIdx.x;
     const long long c = P.moving[m];
+    // the first two table entries of this thread, in flight during the staging
+    float4 epre[2] = {};
+    if (sizeof(T) == 4 && tab) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int kk = threadIdx.x + i * blockDim.x;
+            if (kk < N) epre[i] = tab[m * N + kk];
+        }
+    }
     stage_node<T>(sI, In + m * G * N, G * N);
     const RemapTables<T> tb = remap_tables<T>(P, reinterpret_cast<unsigned char *>(spole + 2 * G));
     __syncthreads();
@@ -721,11 +730,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
     __syncthreads();
     const T u[3] = {P.u[3 * c], P.u[3 * c + 1], P.u[3 * c + 2]};
     T *dst = I0 + m * G * N;
-    for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
+    int iter = 0;
+    for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x, ++iter) {
         T q;  // nu/nu0
         Stencil<T> st;
         if (sizeof(T) == 4 && tab) {
-            const float4 e = tab[m * N + k0];
+            const float4 e = iter == 0 ? epre[0] : (iter == 1 ? epre[1] : tab[m * N + k0]);
             q = (T)e.w;
             st = table_stencil<T>(e, P.nphi, tb.m2i);
         } else {
