@@ -212,6 +212,8 @@ void drop_sized(shd_ctx *c)
     c->nmoving = 0;
     c->rtab_n = 0;
     c->rtab_valid = false;
+    c->h_u.clear();
+    c->h_mflag.clear();
     c->have_fields = c->have_scat = c->have_state = false;
     c->bc_mode = SHD_BC_VACUUM;
     c->sprev_valid = false;
@@ -726,9 +728,10 @@ int ready_for_step(shd_ctx *c)
 }
 
 // The FP32 remap tables of the moving nodes, built on the library's stream
-// (and waited for) when the flow or the angles changed since the last build.
-// Without them the remap kernels compute the boosts and stencils in place.
-int ensure_remap_tables(shd_ctx *c)
+// when the flow or the angles changed since the last build; stream st (if
+// any) then waits for them, else the host does.  Without them the remap
+// kernels compute the boosts and stencils in place.
+int ensure_remap_tables(shd_ctx *c, cudaStream_t st)
 {
     if (is_fp64(c) || c->rtab_valid || c->nmoving == 0 || !c->have_fields || !c->have_angles || c->nmu > 1024)
         return SHD_OK;  // (the entries pack the ring index in 10 bits)
@@ -741,7 +744,11 @@ int ensure_remap_tables(shd_ctx *c)
         c->rtab_n = n;
     }
     CK(launch_remap_tables_f(c, (float4 *)c->d_rtab[0], (float4 *)c->d_rtab[1], c->stream), "remap tables");
-    CK(cudaStreamSynchronize(c->stream), "remap tables");
+    if (st) {
+        if ((rc = stream_after(st, c->stream))) return rc;
+    } else {
+        CK(cudaStreamSynchronize(c->stream), "remap tables");
+    }
     c->rtab_valid = true;
     return SHD_OK;
 }
@@ -797,7 +804,7 @@ template <class T>
 int capture_step(shd_ctx *c, int i)
 {
     if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
-    int rt = ensure_remap_tables(c);  // built outside the graph, read in place by every replay
+    int rt = ensure_remap_tables(c, nullptr);  // built outside the graph, read in place by every replay
     if (rt) return rt;
     const unsigned long long n0 = shd_launch_count_now();
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -850,7 +857,7 @@ int graph_slot(shd_ctx *c, int &slot)
 template <class T>
 int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false)
 {
-    if (int rc = ensure_remap_tables(c)) return rc;
+    if (int rc = ensure_remap_tables(c, st)) return rc;
     for (int s = 0; s < nsteps; ++s) {
         bool tm = c->timing.on && c->timing.count < Timing::kCap;
         cudaEvent_t *ev = tm ? &c->timing.pool[(size_t)c->timing.count * (Timing::kStages + 1)] : nullptr;
@@ -1054,13 +1061,20 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         if ((rc = upload_reals<float>(c, u, c->d_u, 3 * c->Nc))) return rc;
         if ((rc = upload_reals<float>(c, emis0, c->d_emis0, nCG))) return rc;
     }
-    c->rtab_valid = false;  // the flow may have changed
+    // the remap tables follow the flow: rebuilt before the next step when it
+    // differs from the one they were built for
+    const size_t nu = (size_t)c->Nc * 3;
+    if (c->h_u.size() != nu || std::memcmp(c->h_u.data(), u, nu * sizeof(double)) != 0) {
+        c->rtab_valid = false;
+        c->h_u.assign(u, u + nu);
+    }
     // the node tables (and with them the captured step) change only when the
     // set of moving nodes does; new field values are read in place
     std::vector<unsigned char> mf((size_t)c->Nc);
     for (long long i = 0; i < c->Nc; ++i) mf[i] = (u[3 * i] != 0.0 || u[3 * i + 1] != 0.0 || u[3 * i + 2] != 0.0);
     if (!c->have_fields || mf != c->h_mflag) {
         drop_graphs(c);
+        c->rtab_valid = false;
         if ((rc = build_tiles(c, u))) return rc;
         c->h_mflag.swap(mf);
     }
@@ -1536,7 +1550,8 @@ int shd_batch_step(shd_batch *b, int nsteps, void *stream)
     }
     cudaStream_t st = stream ? (cudaStream_t)stream : b->probs[0]->stream;
     for (int p = 0; p < np; ++p) {
-        int rc = stream_after(st, b->probs[p]->stream);
+        int rc = ensure_remap_tables(b->probs[p], nullptr);
+        if (!rc) rc = stream_after(st, b->probs[p]->stream);
         if (rc) return rc;
     }
     for (int s = 0; s < nsteps; ++s) {

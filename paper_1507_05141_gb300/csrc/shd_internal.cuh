@@ -162,6 +162,7 @@ struct shd_ctx {
     long long nmoving = 0;
     unsigned char *d_mflag = nullptr; // [Nc]
     std::vector<unsigned char> h_mflag;  // host copy of the moving flags the tables were built for
+    std::vector<double> h_u;             // host copy of the flow the remap tables were built for
     void *d_Bproj = nullptr;          // [N][NB]
     int NB = 0;
     int *d_midx = nullptr;            // [Nc] moving index or -1
