@@ -169,11 +169,12 @@ void free_all(shd_ctx *c)
                      (void **)&c->d_int2mesh, (void **)&c->d_mesh2int,
                      &c->d_chi0L, (void **)&c->d_mbits, &c->d_seg[0], &c->d_seg[1], &c->d_tcs_Bh[0], &c->d_tcs_Bh[1], &c->d_tcs_Bl[0],
                      &c->d_tcs_Bl[1], &c->d_tcs_Yh[0], &c->d_tcs_Yh[1], &c->d_tcs_Yl[0], &c->d_tcs_Yl[1],
-                     (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1]};
+                     (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_fcheck};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
     c->rtab_n = 0;
     c->rtab_valid = false;
+    c->fstage_n = 0;
 }
 
 bool is_fp64(const shd_ctx *c) { return c->precision == SHD_FP64; }
@@ -206,14 +207,13 @@ void drop_sized(shd_ctx *c)
                      (void **)&c->d_partial, (void **)&c->d_stage,
                      &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag,
                      (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
-                     &c->d_rtab[0], &c->d_rtab[1]};
+                     &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage};
     for (void **p : ptrs) dfree(*p);
     c->ntiles = 0;
     c->nmoving = 0;
     c->rtab_n = 0;
     c->rtab_valid = false;
-    c->h_u.clear();
-    c->h_mflag.clear();
+    c->fstage_n = 0;
     c->have_fields = c->have_scat = c->have_state = false;
     c->bc_mode = SHD_BC_VACUUM;
     c->sprev_valid = false;
@@ -727,6 +727,84 @@ int ready_for_step(shd_ctx *c)
     return SHD_OK;
 }
 
+struct FieldCheck {
+    unsigned int bad, moving_changed, u_changed, pad;
+    unsigned long long max_alpha, max_ne, max_uu;
+};
+
+// One pass over the fields as given (FP64, device staging): which of them
+// hold a non-finite (or, for alpha0, ne, emis0, negative) value (bits 0-3:
+// alpha0, ne, u, emis0), the maxima of alpha0, ne and |u|^2 (bit patterns of
+// non-negative doubles, which order like the integers), whether a node's
+// moving flag differs from prev_mflag and whether u, rounded to the working
+// precision, differs from prev_u (the previous fields; null on the first call).
+template <class T>
+__global__ void __launch_bounds__(256) k_check_fields(const double *__restrict__ alpha0, const double *__restrict__ ne,
+                                                      const double *__restrict__ u, const double *__restrict__ emis0,
+                                                      long long nCG, long long Nc,
+                                                      const unsigned char *__restrict__ prev_mflag,
+                                                      const T *__restrict__ prev_u, FieldCheck *out)
+{
+    unsigned bad = 0, mch = 0, uch = 0;
+    double ma = 0.0, mn = 0.0, mu = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long i = i0; i < nCG; i += stride) {
+        const double a = alpha0[i], e = emis0[i];
+        if (!(isfinite(a) && a >= 0.0)) bad |= 1u;
+        else ma = fmax(ma, a);
+        if (!(isfinite(e) && e >= 0.0)) bad |= 8u;
+    }
+    for (long long i = i0; i < Nc; i += stride) {
+        const double n = ne[i];
+        if (!(isfinite(n) && n >= 0.0)) bad |= 2u;
+        else mn = fmax(mn, n);
+        const double u0 = u[3 * i], u1 = u[3 * i + 1], u2 = u[3 * i + 2];
+        if (!(isfinite(u0) && isfinite(u1) && isfinite(u2))) {
+            bad |= 4u;
+            continue;
+        }
+        mu = fmax(mu, u0 * u0 + u1 * u1 + u2 * u2);
+        const unsigned char mv = (u0 != 0.0 || u1 != 0.0 || u2 != 0.0) ? 1 : 0;
+        if (prev_mflag && mv != prev_mflag[i]) mch = 1u;
+        if (prev_u && ((T)u0 != prev_u[3 * i] || (T)u1 != prev_u[3 * i + 1] || (T)u2 != prev_u[3 * i + 2])) uch = 1u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        mch |= __shfl_xor_sync(0xffffffffu, mch, o);
+        uch |= __shfl_xor_sync(0xffffffffu, uch, o);
+        ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        mn = fmax(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(&out->bad, bad);
+        if (mch) atomicOr(&out->moving_changed, mch);
+        if (uch) atomicOr(&out->u_changed, uch);
+        atomicMax(&out->max_alpha, (unsigned long long)__double_as_longlong(ma));
+        atomicMax(&out->max_ne, (unsigned long long)__double_as_longlong(mn));
+        atomicMax(&out->max_uu, (unsigned long long)__double_as_longlong(mu));
+    }
+}
+
+template <class T>
+cudaError_t check_fields(shd_ctx *c, const double *alpha0, const double *ne, const double *u, const double *emis0,
+                         const unsigned char *prev_mflag, const T *prev_u, FieldCheck &fc)
+{
+    FieldCheck *d = (FieldCheck *)c->d_fcheck;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(FieldCheck), c->stream);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0) sms = 148;
+    k_check_fields<T><<<4 * sms, 256, 0, c->stream>>>(alpha0, ne, u, emis0, (long long)c->Nc * c->G, c->Nc,
+                                                       prev_mflag, prev_u, d);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(&fc, d, sizeof(FieldCheck), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);
+}
+
 // The FP32 remap tables of the moving nodes, built on the library's stream
 // when the flow or the angles changed since the last build; stream st (if
 // any) then waits for them, else the host does.  Without them the remap
@@ -1036,47 +1114,57 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
     if (rc) return rc;
     if (!c->have_grid || !c->have_groups) return fail(SHD_ERR_STATE, "grid and groups must be set first");
     if (!alpha0 || !ne || !u || !emis0) return fail(SHD_ERR_ARG, "null field");
-    size_t nCG = (size_t)c->Nc * c->G;
-    if (!finite_all(alpha0, nCG, true)) return fail(SHD_ERR_NAN, "alpha0 must be finite and >= 0");
-    if (!finite_all(ne, (size_t)c->Nc, true)) return fail(SHD_ERR_NAN, "ne must be finite and >= 0");
-    if (!finite_all(u, (size_t)c->Nc * 3, false)) return fail(SHD_ERR_NAN, "u must be finite");
-    if (!finite_all(emis0, nCG, true)) return fail(SHD_ERR_NAN, "emis0 must be finite and >= 0");
     if ((rc = ensure_buffers(c))) return rc;
-    c->h_alpha_max = c->h_ne_max = 0.0;
-    c->h_gamma_max = 1.0;
-    for (size_t i = 0; i < nCG; ++i) c->h_alpha_max = std::max(c->h_alpha_max, alpha0[i]);
-    for (long long i = 0; i < c->Nc; ++i) {
-        c->h_ne_max = std::max(c->h_ne_max, ne[i]);
-        const double uu = u[3 * i] * u[3 * i] + u[3 * i + 1] * u[3 * i + 1] + u[3 * i + 2] * u[3 * i + 2];
-        c->h_gamma_max = std::max(c->h_gamma_max, std::sqrt(1.0 + uu));
+    const size_t nCG = (size_t)c->Nc * c->G, Nc = (size_t)c->Nc;
+    // the four fields as given (FP64) into a staging area, checked and
+    // reduced there before any field array changes
+    const size_t nf = 2 * nCG + 4 * Nc;
+    if (c->fstage_n != nf || !c->d_fstage || !c->d_fcheck) {
+        c->fstage_n = 0;
+        if ((rc = dalloc(c, &c->d_fstage, nf * sizeof(double), "field staging"))) return rc;
+        if ((rc = dalloc(c, &c->d_fcheck, sizeof(FieldCheck), "field check"))) return rc;
+        c->fstage_n = nf;
     }
+    double *sa = (double *)c->d_fstage, *se = sa + nCG, *sn = se + nCG, *su = sn + Nc;
+    CK(cudaMemcpyAsync(sa, alpha0, nCG * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D alpha0");
+    CK(cudaMemcpyAsync(se, emis0, nCG * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D emis0");
+    CK(cudaMemcpyAsync(sn, ne, Nc * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D ne");
+    CK(cudaMemcpyAsync(su, u, 3 * Nc * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D u");
+    FieldCheck fc;
+    const unsigned char *pm = c->have_fields ? c->d_mflag : nullptr;
+    if (is_fp64(c)) CK(check_fields<double>(c, sa, sn, su, se, pm, c->have_fields ? (const double *)c->d_u : nullptr, fc), "field check");
+    else CK(check_fields<float>(c, sa, sn, su, se, pm, c->have_fields ? (const float *)c->d_u : nullptr, fc), "field check");
+    if (fc.bad & 1u) return fail(SHD_ERR_NAN, "alpha0 must be finite and >= 0");
+    if (fc.bad & 2u) return fail(SHD_ERR_NAN, "ne must be finite and >= 0");
+    if (fc.bad & 4u) return fail(SHD_ERR_NAN, "u must be finite");
+    if (fc.bad & 8u) return fail(SHD_ERR_NAN, "emis0 must be finite and >= 0");
+    double bits2d[3];
+    std::memcpy(&bits2d[0], &fc.max_alpha, sizeof(double));
+    std::memcpy(&bits2d[1], &fc.max_ne, sizeof(double));
+    std::memcpy(&bits2d[2], &fc.max_uu, sizeof(double));
+    c->h_alpha_max = bits2d[0];
+    c->h_ne_max = bits2d[1];
+    c->h_gamma_max = std::sqrt(1.0 + bits2d[2]);
     if (is_fp64(c)) {
-        if ((rc = upload_reals<double>(c, alpha0, c->d_alpha0, nCG))) return rc;
-        if ((rc = upload_reals<double>(c, ne, c->d_ne, c->Nc))) return rc;
-        if ((rc = upload_reals<double>(c, u, c->d_u, 3 * c->Nc))) return rc;
-        if ((rc = upload_reals<double>(c, emis0, c->d_emis0, nCG))) return rc;
+        CK(launch_convert<double>(sa, (double *)c->d_alpha0, (long long)nCG, c->stream), "convert");
+        CK(launch_convert<double>(se, (double *)c->d_emis0, (long long)nCG, c->stream), "convert");
+        CK(launch_convert<double>(sn, (double *)c->d_ne, (long long)Nc, c->stream), "convert");
+        CK(launch_convert<double>(su, (double *)c->d_u, (long long)(3 * Nc), c->stream), "convert");
     } else {
-        if ((rc = upload_reals<float>(c, alpha0, c->d_alpha0, nCG))) return rc;
-        if ((rc = upload_reals<float>(c, ne, c->d_ne, c->Nc))) return rc;
-        if ((rc = upload_reals<float>(c, u, c->d_u, 3 * c->Nc))) return rc;
-        if ((rc = upload_reals<float>(c, emis0, c->d_emis0, nCG))) return rc;
+        CK(launch_convert<float>(sa, (float *)c->d_alpha0, (long long)nCG, c->stream), "convert");
+        CK(launch_convert<float>(se, (float *)c->d_emis0, (long long)nCG, c->stream), "convert");
+        CK(launch_convert<float>(sn, (float *)c->d_ne, (long long)Nc, c->stream), "convert");
+        CK(launch_convert<float>(su, (float *)c->d_u, (long long)(3 * Nc), c->stream), "convert");
     }
-    // the remap tables follow the flow: rebuilt before the next step when it
-    // differs from the one they were built for
-    const size_t nu = (size_t)c->Nc * 3;
-    if (c->h_u.size() != nu || std::memcmp(c->h_u.data(), u, nu * sizeof(double)) != 0) {
-        c->rtab_valid = false;
-        c->h_u.assign(u, u + nu);
-    }
+    // the remap tables follow the flow in working precision: rebuilt before
+    // the next step when it changed
+    if (!c->have_fields || fc.u_changed) c->rtab_valid = false;
     // the node tables (and with them the captured step) change only when the
     // set of moving nodes does; new field values are read in place
-    std::vector<unsigned char> mf((size_t)c->Nc);
-    for (long long i = 0; i < c->Nc; ++i) mf[i] = (u[3 * i] != 0.0 || u[3 * i + 1] != 0.0 || u[3 * i + 2] != 0.0);
-    if (!c->have_fields || mf != c->h_mflag) {
+    if (!c->have_fields || fc.moving_changed) {
         drop_graphs(c);
         c->rtab_valid = false;
         if ((rc = build_tiles(c, u))) return rc;
-        c->h_mflag.swap(mf);
     }
     c->have_fields = true;
     if (c->have_scat) {

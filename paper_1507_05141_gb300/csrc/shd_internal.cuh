@@ -161,8 +161,10 @@ struct shd_ctx {
     long long *d_moving = nullptr;    // moving node ids
     long long nmoving = 0;
     unsigned char *d_mflag = nullptr; // [Nc]
-    std::vector<unsigned char> h_mflag;  // host copy of the moving flags the tables were built for
-    std::vector<double> h_u;             // host copy of the flow the remap tables were built for
+    // device staging of the fields as given (FP64) and the result of their check
+    void *d_fstage = nullptr;
+    size_t fstage_n = 0;
+    void *d_fcheck = nullptr;
     void *d_Bproj = nullptr;          // [N][NB]
     int NB = 0;
     int *d_midx = nullptr;            // [Nc] moving index or -1

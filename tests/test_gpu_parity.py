@@ -414,3 +414,27 @@ def test_flow_update_same_moving_nodes(native, precision, tol):
     assert rel(H, H_r) < tol
     f = O.moments_to_eddington(J, K)
     assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_invalid_fields_rejected_unchanged(native, precision):
+    """Fields are checked on the device before any field array changes: a
+    non-finite or negative value is refused with the field named, and the
+    step afterwards is bit-identical to one that never saw the bad fields."""
+    spec = inputs.ragged_mixed()
+    I0 = inputs.random_state(spec, seed=4)
+    s = native.Solver.from_spec(spec, precision=precision)
+    ref = native.Solver.from_spec(spec, precision=precision)
+    bad = []
+    a = spec.alpha0.copy(); a[3, 1] = np.nan; bad.append(((a, spec.ne, spec.u, spec.emis0), "alpha0"))
+    n = spec.ne.copy(); n[7] = -1.0; bad.append(((spec.alpha0, n, spec.u, spec.emis0), "ne"))
+    u = spec.u.copy(); u[5, 2] = np.inf; bad.append(((spec.alpha0, spec.ne, u, spec.emis0), "u must"))
+    e = spec.emis0.copy(); e[-1, 0] = -2.0; bad.append(((spec.alpha0, spec.ne, spec.u, e), "emis0"))
+    for args, what in bad:
+        with pytest.raises(native.ShdError, match=what):
+            s.set_fields(*args)
+    for x in (s, ref):
+        x.set_state(I0)
+        x.step(2)
+    assert np.array_equal(s.get_state(), ref.get_state())
+    assert s.sums() == ref.sums()
