@@ -16,17 +16,18 @@
 // written through 2-D maps with the 128-byte swizzle.
 //
 //   a1  D[128 x nb] = A[128 x K] . Bp^T over the item's slots (Bp = [W Y |
-//       moment weights], zero at padding slots): group A stores the
-//       laboratory moments and the I_lm of nodes at rest, group B adds its
+//       moment weights], zero at padding slots): group B stores the
+//       laboratory moments and the I_lm of nodes at rest, group A adds its
 //       part, rows mode stores the I_lm of moving nodes from their comoving
 //       intensities.  Warp-specialised: one thread issues TMA boxes into an
 //       FP32 staging ring, converter warps split them into BF16 hi / lo in
 //       the canonical layout, one thread issues the MMAs into two alternating
 //       tensor-memory accumulators, epilogue warps drain them.
-//   a3  D[128 x K] = S[128 x NLM] . Y^T: segment mode stages eta = chi0 D and
-//       chi = chi0 in shared memory and TMA-stores them into the sweep
-//       layout (moving nodes are overwritten afterwards by their Lorentz
-//       remap); rows mode stores the comoving source S0 of moving nodes.
+//   a3  D[128 x K] = S[128 x NLM] . Y^T: rows mode (k_sh2lab_rows) stores the
+//       comoving source S0 of moving nodes node-major for their Lorentz
+//       remap; then k_sh2lab_ws, per group, stages eta = chi0 D and chi =
+//       chi0 of nodes at rest and the remapped laboratory eta, chi of moving
+//       nodes in shared memory and TMA-stores them into the sweep layout.
 // FP32 operands are split into BF16 hi + lo and the three products hi.hi +
 // hi.lo + lo.hi accumulate in FP32.  Every mbarrier wait is bounded; on
 // timeout the kernel raises *err and winds down without hanging.
@@ -429,19 +430,13 @@ __global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __g
 // a3.  512 threads, lock-step per item: the rows' S as BF16 hi / lo
 // (canonical), the MMAs over the item's slots in column blocks of <= 256,
 // then the output chunk by chunk through shared-memory tiles and TMA stores.
-// Segment mode: per chunk an eta and a chi tile [32][128]; rows at rest take
-// eta = chi0 D, chi = chi0, moving rows the laboratory eta, chi from their
-// remap (etan, chin node-major).  Rows mode: S0 of moving rows (m, g), two
-// chunks per step.  Shared memory: Yh, Yl [Kp][Kq]; A hi / lo [128][Kq]; 4
-// output tiles [box]; per row the S offset, chi0 and moving index; one
-// mbarrier.
+// Rows mode: S0 of moving rows (m, g) into node-major rows, two chunks per
+// step.  Shared memory: Yh, Yl [Kp][Kq]; A hi / lo [128][Kq]; 4 output tiles
+// [box]; per row the S offset; one mbarrier.
 // -------------------------------------------------------------------------
-template <int ROWS>
-__global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
-                                                       const float *__restrict__ Sp, const float *__restrict__ etan,
-                                                       const float *__restrict__ chin,
-                                                       const uint16_t *__restrict__ gYh,
-                                                       const uint16_t *__restrict__ gYl, int Kq, int *err)
+__global__ void __launch_bounds__(512, 1) k_sh2lab_rows(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
+                                                        const float *__restrict__ Sp, const uint16_t *__restrict__ gYh,
+                                                        const uint16_t *__restrict__ gYl, int Kq, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (tc::smem_u32(smem_raw) & 1023) {
@@ -455,14 +450,12 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
     uint16_t *Al = Ah + (size_t)128 * Kq;
     float *tiles = reinterpret_cast<float *>(Al + (size_t)128 * Kq);  // [4][kBox]
     long long *rsrc = reinterpret_cast<long long *>(tiles + (size_t)4 * kBox);  // [128] S row offset, -1: none
-    float *chir = reinterpret_cast<float *>(rsrc + 128);                       // [128] chi0 of the row
-    int *rowm = reinterpret_cast<int *>(chir + 128);                           // [128] moving index, -1
-    uint64_t *bar = reinterpret_cast<uint64_t *>(rowm + 128);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(rsrc + 128);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int G = P.G, NLM = P.NLM, N = P.N;
+    const int G = P.G, NLM = P.NLM;
     {
         const uint4 *sh = reinterpret_cast<const uint4 *>(gYh), *sl = reinterpret_cast<const uint4 *>(gYl);
         uint4 *dh = reinterpret_cast<uint4 *>(Yh), *dl = reinterpret_cast<uint4 *>(Yl);
@@ -489,32 +482,17 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
     bool pending = false;
 
     for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x) {
-        const long long sg = w / G;
-        const int g = (int)(w - sg * G);
         // the previous item's stores have finished reading the tiles
         if (lane == 0) tc::bulk_wait_read<0>();
         __syncthreads();
         if (tid < 128) {
             long long src = -1;
-            float ch = 0.f;
-            int m = -1;
-            if (!ROWS) {
-                long long c = 0;
-                if (seg_node(P, S, S.segs[sg], tid, c)) {
-                    ch = P.chi0[c * G + g];
-                    m = P.midx[c];
-                    if (m < 0) src = (c * G + g) * NLM;
-                }
-            } else {
-                const long long row = w * 128 + tid;
-                if (row < S.nrows) {
-                    const long long mm = row / G;
-                    src = (P.moving[mm] * G + (row - mm * G)) * NLM;
-                }
+            const long long row = w * 128 + tid;
+            if (row < S.nrows) {
+                const long long mm = row / G;
+                src = (P.moving[mm] * G + (row - mm * G)) * NLM;
             }
             rsrc[tid] = src;
-            chir[tid] = ch;
-            rowm[tid] = m;
         }
         __syncthreads();
         // A: the rows' S as BF16 hi / lo, one core matrix per warp step
@@ -569,113 +547,29 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_seg(Prob<float> P, const __gr
             const int r = quad * 32 + lane;
             const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
             int cc[5];
-            if constexpr (!ROWS) {
-                // each warp stores its own box: 32 rows (quad) x 16 columns of
-                // eta (parts 0, 1) or chi (parts 2, 3) per chunk
-                const float chr = chir[r];
-                const int m = rowm[r];
-                const long long nbase = m >= 0 ? ((long long)m * G + g) * N : 0;
-                const int half = part & 1;
-                const bool eta_w = part < 2;
-                const float *nsrc = eta_w ? etan : chin;
-                const bool anym = __any_sync(0xffffffffu, m >= 0);
-                float *W = tiles + (size_t)warp * 2 * 512;  // [2][16][32]
-                const int4 sd = S.segs[sg];
-                const int r0 = quad * 32;
-                const int as = sd.y + r0 % S.bw, bs = sd.z + r0 / S.bw;
-                const CUtensorMap *mp_base = &maps.m[eta_w ? 0 : 2];
-                auto store = [&](int cn, const float *src) {
-                    const int4 ci = S.chunk[cn];
-                    const int kk = ci.y + 16 * half;
-                    const bool yc = !S.groupB && ci.x == 1;
-                    tc::tma_store_5d(mp_base + ci.x, as, yc ? sd.x : bs, yc ? bs : sd.x, g, kk, src);
-                };
-                // moving rows: cp.async of their 16 values of chunk cn into buffer b
-                auto prefetch = [&](int cn, int b) {
-                    if (m < 0) return;
-                    const int4 ci = S.chunk[cn];
-                    const int kl0 = ci.y + 16 * half;
-                    const float *src = nsrc + nbase + ci.z + kl0;
-                    float *dst = W + (size_t)b * 512 + lane;
-                    for (int j = 0; j < 16; ++j)
-                        if (kl0 + j < ci.w) {
-                            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + j * 32);
-                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + j) : "memory");
-                        }
-                };
-                if (!eta_w && !anym && !S.chi_all) {
-                    // every row at rest and the sweep reads chi0 there: nothing to store
-                } else if (!eta_w && !anym) {
-                    // every row at rest: one constant chi tile serves every chunk
+            for (int pc = 0; pc * 2 < nchunk; ++pc) {
+                float *T0 = tiles + (size_t)((pc & 1) * 2) * kBox;
+                // the stores of pair pc - 2 (same tiles) have read them
+                if (tid == 0) tc::bulk_wait_read<1>();
+                __syncthreads();
+                const int chn = 2 * pc + (part >> 1);
+                if (chn < nchunk) {
+                    float v[16];
+                    tc::tmem_ld16(trow + (uint32_t)(chn * kKC + (part & 1) * 16), v);
+                    float *T = T0 + (size_t)(part >> 1) * kBox;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) W[j * 32 + lane] = chr;
-                    tc::fence_proxy_async();
-                    __syncwarp();
-                    if (lane == 0) {
-                        for (int cn = 0; cn < nchunk; ++cn) store(cn, W);
-                        tc::bulk_commit();
-                    }
-                } else {
-                    if (anym) prefetch(0, 0);
-                    asm volatile("cp.async.commit_group;\n" ::: "memory");
-                    for (int cn = 0; cn < nchunk; ++cn) {
-                        const int b = cn & 1;
-                        // buffer b ^ 1 (chunk cn - 1) is rewritten by the prefetch:
-                        // every earlier store must have read its source
-                        if (lane == 0) {
-                            if (anym) tc::bulk_wait_read<0>();
-                            else tc::bulk_wait_read<1>();
-                        }
-                        __syncwarp();
-                        if (anym && cn + 1 < nchunk) prefetch(cn + 1, b ^ 1);
-                        asm volatile("cp.async.commit_group;\n" ::: "memory");
-                        float *Wb = W + (size_t)b * 512 + lane;
-                        if (eta_w) {
-                            float v[16];
-                            tc::tmem_ld16(trow + (uint32_t)(cn * kKC + 16 * half), v);
-                            if (m < 0) {
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) Wb[j * 32] = chr * v[j];
-                            }
-                        } else if (m < 0) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) Wb[j * 32] = chr;
-                        }
-                        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-                        tc::fence_proxy_async();
-                        __syncwarp();
-                        if (lane == 0) {
-                            store(cn, W + (size_t)b * 512);
-                            tc::bulk_commit();
-                        }
-                    }
-                    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                    for (int q = 0; q < 4; ++q)
+                        *swz4(T, r, (part & 1) * 4 + q) =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
-            } else {
-                for (int pc = 0; pc * 2 < nchunk; ++pc) {
-                    float *T0 = tiles + (size_t)((pc & 1) * 2) * kBox;
-                    // the stores of pair pc - 2 (same tiles) have read them
-                    if (tid == 0) tc::bulk_wait_read<1>();
-                    __syncthreads();
-                    const int chn = 2 * pc + (part >> 1);
-                    if (chn < nchunk) {
-                        float v[16];
-                        tc::tmem_ld16(trow + (uint32_t)(chn * kKC + (part & 1) * 16), v);
-                        float *T = T0 + (size_t)(part >> 1) * kBox;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            *swz4(T, r, (part & 1) * 4 + q) =
-                                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                tc::fence_proxy_async();
+                __syncthreads();
+                if (tid == 0) {
+                    for (int hh = 0; hh < 2 && 2 * pc + hh < nchunk; ++hh) {
+                        box_coords(S, 1, w, G, 2 * pc + hh, cc);
+                        tc::tma_store_2d(&maps.m[0], cc[0], cc[1], T0 + (size_t)hh * kBox);
                     }
-                    tc::fence_proxy_async();
-                    __syncthreads();
-                    if (tid == 0) {
-                        for (int hh = 0; hh < 2 && 2 * pc + hh < nchunk; ++hh) {
-                            box_coords(S, 1, w, G, 2 * pc + hh, cc);
-                            tc::tma_store_2d(&maps.m[0], cc[0], cc[1], T0 + (size_t)hh * kBox);
-                        }
-                        tc::bulk_commit();
-                    }
+                    tc::bulk_commit();
                 }
             }
         }
@@ -1016,7 +910,7 @@ static size_t project_seg_smem(int nb, int Kp, int nstg, int nr)
 }
 static size_t sh2lab_seg_smem(int Kp, int Kq)
 {
-    return (size_t)4 * Kp * Kq + (size_t)4 * 128 * Kq + (size_t)4 * kBox * 4 + 128 * (8 + 4 + 4) + 8 + 8;
+    return (size_t)4 * Kp * Kq + (size_t)4 * 128 * Kq + (size_t)4 * kBox * 4 + 128 * 8 + 8 + 8;
 }
 static size_t sh2lab_ws_smem(int Kp, int Kq)
 {
@@ -1233,18 +1127,16 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
     return cudaSuccess;
 }
 
-template <int ROWS>
-static cudaError_t run_sh2lab_seg(const shd_ctx *ctx, const Prob<float> &P, const SegMaps &maps, const SegArgs &a,
-                                  const float *Sp, const float *etan, const float *chin, const void *Yh,
-                                  const void *Yl, cudaStream_t st)
+static cudaError_t run_sh2lab_rows(const shd_ctx *ctx, const Prob<float> &P, const SegMaps &maps, const SegArgs &a,
+                                   const float *Sp, const void *Yh, const void *Yl, cudaStream_t st)
 {
     const size_t sm = sh2lab_seg_smem(a.Kp, ctx->tc_Kq);
-    cudaError_t e = cudaFuncSetAttribute(k_sh2lab_seg<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_sh2lab_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int grid = num_sms_seg(ctx);
     if (a.nitem < grid) grid = (int)a.nitem;
-    k_sh2lab_seg<ROWS><<<grid, 512, sm, st>>>(P, maps, a, Sp, etan, chin, (const uint16_t *)Yh, (const uint16_t *)Yl,
-                                              ctx->tc_Kq, ctx->d_tc_err);
+    k_sh2lab_rows<<<grid, 512, sm, st>>>(P, maps, a, Sp, (const uint16_t *)Yh, (const uint16_t *)Yl, ctx->tc_Kq,
+                                         ctx->d_tc_err);
     note_launch();
     return cudaGetLastError();
 }
@@ -1263,7 +1155,7 @@ cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, f
         SegArgs a = rows_args(ctx);
         SegMaps maps{};
         if ((e = rows_map(ctx, &maps.m[0], nm0)) != cudaSuccess) return e;
-        if ((e = run_sh2lab_seg<1>(ctx, P, maps, a, Sp, nullptr, nullptr, ctx->d_tc_Yh, ctx->d_tc_Yl, st)) !=
+        if ((e = run_sh2lab_rows(ctx, P, maps, a, Sp, ctx->d_tc_Yh, ctx->d_tc_Yl, st)) !=
             cudaSuccess)
             return e;
         if ((e = launch_remap_to_lab_f(ctx, nm0, nm1, nm2, st)) != cudaSuccess) return e;
