@@ -533,6 +533,112 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
 }
 
 // -------------------------------------------------------------------------
+// a4, FP32 with two previous-plane buffers: plane s reads the state of plane
+// s-1 from one float4 buffer (I, S, chi of a node) and writes its own into
+// the other, so one barrier per plane suffices: it makes plane s-1's state
+// and the copies of plane s visible, and every read of the buffer plane s
+// overwrites (plane s-2's) is done by then.  The inputs of plane s+1 stream
+// into a two-stage ring as in k_sweep_pipe (16-byte copies); with CB the
+// moving-piece bits are read from global memory when a plane's copies are
+// issued.
+// -------------------------------------------------------------------------
+template <int U, bool CB, bool WIDE>
+__global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__restrict__ I,
+                                                      const float *__restrict__ eta, const float *__restrict__ chi,
+                                                      const float *__restrict__ chi0L,
+                                                      const unsigned long long *__restrict__ mbits, int npc, int nwin)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NT = 1024;
+    const int k = blockIdx.x / P.G;
+    const int g = blockIdx.x - k * P.G;
+    const Ordinate o = P.ord[k];
+    const int dims[3] = {P.nx, P.ny, P.nz};
+    const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
+    const int plane = n1 * n2;
+    const int pstride = (plane + 3) & ~3;
+    float4 *Q = reinterpret_cast<float4 *>(smem_raw);              // [2][pstride]
+    float *ring = reinterpret_cast<float *>(Q + 2 * (size_t)pstride);  // [2][3][pstride]
+    const long long base = ((long long)k * P.G + g) * P.Nc;
+    const float *c0base = CB ? chi0L + ((long long)o.d * P.G + g) * P.Nc : nullptr;
+    const unsigned long long *mb = CB ? mbits + (size_t)o.d * nwin * npc : nullptr;
+    const float fr1 = (float)o.fr1, fr2 = (float)o.fr2, s = (float)o.s, kap = P.kappa;
+    const float w00 = (1.f - fr1) * (1.f - fr2), w10 = fr1 * (1.f - fr2), w01 = (1.f - fr1) * fr2, w11 = fr1 * fr2;
+    const float bc_iso = P.bc_mode == SHD_BC_ISO ? P.bc[g] : 0.f;
+    const bool bc_full = P.bc_mode == SHD_BC_FULL;
+    const int tid = threadIdx.x;
+
+    unsigned face = 0;
+    {
+        const int first1 = o.s1 > 0 ? 0 : n1 - 1, first2 = o.s2 > 0 ? 0 : n2 - 1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int j = tid + NT * u;
+            int i1 = j / n2, i2 = j - i1 * n2;
+            if ((o.s1 != 0 && i1 == first1) || (o.s2 != 0 && i2 == first2)) face |= 1u << u;
+        }
+    }
+    const int d1 = o.s1 * n2, d2 = o.s2;
+
+    auto issue = [&](int step) {
+        if (step < nd) {
+            const int id = o.sd > 0 ? step : nd - 1 - step;
+            const long long pb = base + (long long)id * plane;
+            float *r = ring + (size_t)(step & 1) * 3 * pstride;
+            const int nv = plane / 4;  // 16-byte pieces per array
+            for (int q = tid; q < nv; q += NT) cp_async_n<16>(&r[q * 4], &I[pb + q * 4]);
+            for (int q = tid; q < nv; q += NT) cp_async_n<16>(&r[pstride + q * 4], &eta[pb + q * 4]);
+            for (int q = tid; q < nv; q += NT) {
+                const int off = q * 4;
+                const float *src = chi + pb + off;
+                if (CB && !((mb[(size_t)(id >> 6) * npc + q] >> (id & 63)) & 1ull))
+                    src = c0base + (long long)id * plane + off;
+                cp_async_n<16>(&r[2 * pstride + off], src);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+
+    issue(0);
+    for (int step = 0; step < nd; ++step) {
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncthreads();  // this plane's copies and the previous plane's state are visible
+        issue(step + 1);
+        const float *r = ring + (size_t)(step & 1) * 3 * pstride;
+        const float4 *Qp = Q + (size_t)((step + 1) & 1) * pstride;  // plane step - 1
+        float4 *Qn = Q + (size_t)(step & 1) * pstride;               // plane step
+        const bool first = step == 0;
+        const int id = o.sd > 0 ? step : nd - 1 - step;
+        const long long pb = base + (long long)id * plane;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = tid + NT * u;
+            if (j >= plane) break;
+            const float In = r[j];
+            const float ct = r[2 * pstride + j] + kap;
+            const float st = ct > 0.f ? (r[pstride + j] + kap * In) * hw_rcp(ct) : 0.f;
+            float inew;
+            if (first || ((face >> u) & 1u)) {
+                inew = bc_full ? P.bc[pb + j] : bc_iso;
+            } else {
+                const float4 q00 = Qp[j], q10 = Qp[j - d1], q01 = Qp[j - d2], q11 = Qp[j - d1 - d2];
+                const float iu = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                const float su = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                const float cu = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+                const float dtau = s * 0.5f * (cu + ct);
+                float ew, wp, wu;
+                if constexpr (WIDE) sc_weights<float>(dtau, ew, wp, wu);
+                else sc_weights_narrow<float>(dtau, ew, wp, wu);
+                inew = iu * ew + st * wp + su * wu;
+            }
+            Qn[j] = make_float4(inew, st, ct, 0.f);
+            I[pb + j] = inew;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// -------------------------------------------------------------------------
 // a5: FP64 diagnostics; pass 1 per-block partials, pass 2 a single block
 // adds them in a fixed order (deterministic).
 // -------------------------------------------------------------------------
@@ -821,6 +927,32 @@ static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, con
     return cudaGetLastError();
 }
 
+// shared memory of the FP32 two-buffer sweep: two float4 planes and the
+// 2-stage ring of the three inputs
+static size_t sweep_pp_smem_bytes(const shd_ctx *c)
+{
+    size_t ps = ((size_t)sweep_plane_max(c) + 3) & ~(size_t)3;
+    return sizeof(float) * ps * 14;
+}
+
+template <int U>
+static cudaError_t launch_sweep_pp(const shd_ctx *ctx, float *I, const float *eta, const float *chi, cudaStream_t st,
+                                   bool bits)
+{
+    Prob<float> P = make_prob<float>(ctx);
+    const float *c0L = bits ? (const float *)ctx->d_chi0L : nullptr;
+    const unsigned long long *mb = bits ? ctx->d_mbits : nullptr;
+    const size_t sm = sweep_pp_smem_bytes(ctx);
+    const bool wide = !sweep_tau_bounded(ctx);
+    auto kern = bits ? (wide ? k_sweep_pp<U, true, true> : k_sweep_pp<U, true, false>)
+                     : (wide ? k_sweep_pp<U, false, true> : k_sweep_pp<U, false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi, c0L, mb, ctx->mbits_npc, ctx->mbits_nwin);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // shared memory of the pipelined sweep: previous plane (4 reals a node in
 // FP32, 3 in FP64) + 2-stage ring of the three inputs, each array padded to
 // a multiple of 4 reals
@@ -854,6 +986,15 @@ cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, c
 {
     int plane = sweep_plane_max(ctx);
     size_t smp = sweep_pipe_smem_bytes(ctx);
+    if constexpr (sizeof(T) == 4) {
+        const int u = (plane + 1023) / 1024;
+        if (sweep_vec<T>(ctx) && sweep_pp_smem_bytes(ctx) <= 227 * 1024 && u <= 4) {
+            const bool bits = use_chi0L && sweep_uses_chi0L<T>(ctx);
+            if (u <= 1) return launch_sweep_pp<1>(ctx, (float *)I, (const float *)eta, (const float *)chi, st, bits);
+            if (u <= 2) return launch_sweep_pp<2>(ctx, (float *)I, (const float *)eta, (const float *)chi, st, bits);
+            return launch_sweep_pp<4>(ctx, (float *)I, (const float *)eta, (const float *)chi, st, bits);
+        }
+    }
     if (smp <= 227 * 1024) {
         const bool vec = sweep_vec<T>(ctx);
         const bool bits = use_chi0L && sweep_uses_chi0L<T>(ctx);
