@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) k_source(Prob<T> P, const T *__restrict__
 // output takes one product and the node's I_lm streams straight through
 // (the full sum's other terms are exact zeros: the same S_p).
 template <class T, bool DIAG>
-__global__ void __launch_bounds__(256, 2) k_source_sums(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp,
+__global__ void __launch_bounds__(256, 3) k_source_sums(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp,
                                                      const T *__restrict__ mom, const T *__restrict__ Sprev,
                                                      int have_prev, double *partial)
 {
