@@ -79,6 +79,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, device=None):
+    """The largest of the ranks' values of x (x itself in a single process).
+    Timing only: the replicas exchange nothing else."""
+    ws, _, _ = _dist()
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(updates_per_step, steps, ws, seconds):
+    """Whole-job updates/s: every rank's steps over the slowest rank's time."""
+    return updates_per_step * steps * ws / seconds
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -282,13 +300,9 @@ def bench_ours(args):
     # warm-up (also fills the state with a physical solution), then the
     # device-resident timed region
     ms, stage, clk_summary, launches = time_steps(solver, spec, args.steps, args.warmup, stream, dev, barrier)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     upd = spec.updates_per_step
-    value = upd * args.steps * ws / (ms / 1e3)
+    value = job_rate(upd, args.steps, ws, ms / 1e3)
 
     # end to end through the C ABI with host buffers: per step the fields
     # are uploaded from pinned host memory, one step runs, and the FP64 sums
@@ -309,13 +323,8 @@ def bench_ours(args):
         solver.step(1, sptr)
         solver.sums()
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = upd * e2e_steps * ws / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = job_rate(upd, e2e_steps, ws, e2e_s)
 
     peak, peak_kind = _peaks()
     do_gb = upd * (8 if prec == "fp64" else 4) / 1e9
@@ -337,14 +346,10 @@ def bench_ours(args):
         s32 = native.Solver.from_spec(spec, device=local, precision="fp32")
         s32.zero_state()
         ms32, stage32, _, _ = time_steps(s32, spec, args.steps, args.warmup, stream, dev, barrier)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms32], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms32 = float(t.item())
+        ms32 = max_over_ranks(ms32, dev)
         s32.close()
         solver = None
-        plain = {"value": upd * args.steps * ws / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / args.steps,
+        plain = {"value": job_rate(upd, args.steps, ws, ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / args.steps,
                  "stage_ms": stage32}
     errors = None
     if rank == 0 and not args.no_errors:
