@@ -44,6 +44,7 @@ namespace {
 
 constexpr long long kSegWaitLimit = 1LL << 22;  // mbarrier polls before giving up (about a second)
 constexpr int kKC = 32;                         // ordinates per chunk
+constexpr int kABatch = 8;                      // k_sh2lab_rows: A-build steps whose loads fly together
 constexpr int kBox = 128 * kKC;                 // floats per TMA box (16 KB)
 constexpr int kNConv = 256;                     // converter threads of a1
 
@@ -495,23 +496,40 @@ __global__ void __launch_bounds__(512, 1) k_sh2lab_rows(Prob<float> P, const __g
             rsrc[tid] = src;
         }
         __syncthreads();
-        // A: the rows' S as BF16 hi / lo, one core matrix per warp step
+        // A: the rows' S as BF16 hi / lo, one core matrix per warp step; the
+        // loads of kABatch steps are issued together before their stores
         {
             const int j = lane >> 2, kq = lane & 3;
-            for (int cm = warp; cm < 16 * (Kq / 8); cm += 16) {
-                const int rb = cm / (Kq / 8), kb = cm - rb * (Kq / 8);
-                const int row = rb * 8 + j, p = kb * 8 + 2 * kq;
-                const long long src = rsrc[row];
-                float v0 = 0.f, v1 = 0.f;
-                if (src >= 0) {
-                    if (p < NLM) v0 = Sp[src + p];
-                    if (p + 1 < NLM) v1 = Sp[src + p + 1];
+            const int ncm = 16 * (Kq / 8);
+            for (int cm0 = warp; cm0 < ncm; cm0 += 16 * kABatch) {
+                float v0[kABatch], v1[kABatch];
+#pragma unroll
+                for (int i = 0; i < kABatch; ++i) {
+                    const int cm = cm0 + 16 * i;
+                    v0[i] = 0.f;
+                    v1[i] = 0.f;
+                    if (cm < ncm) {
+                        const int rb = cm / (Kq / 8), kb = cm - rb * (Kq / 8);
+                        const int row = rb * 8 + j, p = kb * 8 + 2 * kq;
+                        const long long src = rsrc[row];
+                        if (src >= 0) {
+                            if (p < NLM) v0[i] = Sp[src + p];
+                            if (p + 1 < NLM) v1[i] = Sp[src + p + 1];
+                        }
+                    }
                 }
-                uint32_t hi, lo;
-                split2(v0, v1, hi, lo);
-                const int o = tc::canon_off(row, p, Kq);
-                *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
-                *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
+#pragma unroll
+                for (int i = 0; i < kABatch; ++i) {
+                    const int cm = cm0 + 16 * i;
+                    if (cm >= ncm) break;
+                    const int rb = cm / (Kq / 8), kb = cm - rb * (Kq / 8);
+                    const int row = rb * 8 + j, p = kb * 8 + 2 * kq;
+                    uint32_t hi, lo;
+                    split2(v0[i], v1[i], hi, lo);
+                    const int o = tc::canon_off(row, p, Kq);
+                    *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
+                    *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
+                }
             }
         }
         tc::fence_proxy_async();
