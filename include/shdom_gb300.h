@@ -106,7 +106,12 @@ int shd_set_groups(shd_ctx *ctx, int G, const double *edges);
  *   ne     [Nc]     scattering coefficient scale n_e sigma_T (>= 0)
  *   u      [Nc][3]  spatial 4-velocity Gamma v/c (finite)
  *   emis0  [Nc][G]  isotropic emissivity eta0 (>= 0)
- * Requires grid and groups.  Non-finite or negative values -> SHD_ERR_NAN. */
+ * Requires grid, angles and groups.  The host arrays are copied (the call
+ * returns once the copies are done and checked); the check runs on the
+ * device over a staging copy, before any field array changes, so a refused
+ * call leaves the previous fields in place.  Non-finite or negative values
+ * -> SHD_ERR_NAN, naming the first offending field in the order alpha0, ne,
+ * u, emis0.  A new flow on the same moving nodes keeps the captured step. */
 int shd_set_fields(shd_ctx *ctx, const double *alpha0, const double *ne, const double *u,
                    const double *emis0);
 
