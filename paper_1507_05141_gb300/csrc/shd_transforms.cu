@@ -13,6 +13,12 @@
 //   a3  S0(c,k,g)  = sum_p Y_p(n_k) S_p(c,g)   per (tile, g): [64 x NLM] x [NLM x N];
 //     a node at rest writes eta = chi0 S0, chi = chi0 directly; a moving node
 //     writes S0 to the scratch buffer and k_remap_to_lab does the transform.
+//
+// The remaps (one CTA per moving node, its G x N values in shared memory)
+// are shared by every precision.  In single precision they read each
+// (node, ordinate)'s boosted stencil and Doppler ratio from the tables that
+// k_remap_tables builds once per flow field, and with group centres equally
+// spaced in log energy they replace the bracket search by a constant shift.
 #include <cuda_runtime.h>
 
 #include <type_traits>
