@@ -182,6 +182,19 @@ int shd_stage_sweep(shd_ctx *ctx, const double *I_old, const double *eta_lab, co
 int shd_set_state_dev(shd_ctx *ctx, const double *dev_I, void *cuda_stream);
 int shd_get_state_dev(shd_ctx *ctx, double *dev_I, void *cuda_stream);
 
+/* Self-check of the failure path of the tensor-core kernels' bounded waits
+ * (no counterpart in the paper).  Every mbarrier wait in those kernels polls
+ * a bounded number of times; when the limit runs out the kernel raises the
+ * context's device flag, finishes its outstanding copies and returns, and the
+ * next synchronous call (shd_get_moments, shd_get_sums, ...) returns
+ * SHD_ERR_TIMEOUT and clears the flag.  This call runs that path on purpose:
+ * one thread waits on an mbarrier that nothing arrives on, `polls` times
+ * (1 <= polls <= 2^22, about a second at the top), with no copy or MMA in
+ * flight, then the call synchronises and reports.  Expected result:
+ * SHD_ERR_TIMEOUT with the flag cleared.  A flag left by an earlier kernel is
+ * reported first (also SHD_ERR_TIMEOUT) without running the check. */
+int shd_check_bounded_wait(shd_ctx *ctx, long long polls);
+
 /* Sizes of the configured problem (any output may be NULL). */
 int shd_get_sizes(shd_ctx *ctx, long long *n_nodes, int *n_ord, int *n_groups, int *n_lm);
 
@@ -247,14 +260,24 @@ void shd_batch_destroy(shd_batch *batch);
  * rest need no scratch.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     The address is kept for the life of the process: it does not survive a
+ *     cudaDeviceReset of that device (the primary context, and with it the
+ *     array, is then a new one), so do not call this entry point after one.
+ *   - The call makes ctx's device current while it works and restores the
+ *     caller's current device before it returns.
  *   - Work runs on cuda_stream (NULL: the context's stream, ordered after the
  *     context's earlier work); with another stream the caller orders it after
  *     the steps that produced the state.
  *   - Every call shares the one array and leaves its contents behind; nothing
  *     in it needs to start at zero (each call writes every entry it reads).
  *     Calls that overlap on the GPU race on it.
- * Returns SHD_OK, SHD_ERR_ARG (null pointer, too large), SHD_ERR_STATE (not
- * configured) or SHD_ERR_CUDA. */
+ *   - In SHD_MIXED the tensor-core kernels give up on a wait that runs out
+ *     of its iteration limit and raise the context's device flag; this call
+ *     does not read it back (that would synchronise).  The next
+ *     shd_get_moments or shd_get_sums on ctx reports it as SHD_ERR_TIMEOUT:
+ *     call one of them before trusting outputs whose timing matters.
+ * Returns SHD_OK, SHD_ERR_ARG (null pointer, too large, a stage's shared
+ * memory over the limit), SHD_ERR_STATE (not configured) or SHD_ERR_CUDA. */
 #define SHD_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int shd_project_noalloc(shd_ctx *ctx, void *dev_Ish, void *dev_mom, void *cuda_stream);
 const char *shd_noalloc_last_error(void);

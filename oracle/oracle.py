@@ -62,7 +62,7 @@ def lib():
     with _lock:
         if _lib is None:
             _lib = ctypes.CDLL(build())
-            for name in ("orc_project", "orc_source", "orc_sh2lab", "orc_sweep", "orc_step"):
+            for name in ("orc_project", "orc_source", "orc_sh2lab", "orc_sweep", "orc_sweep_pairs", "orc_step"):
                 getattr(_lib, name).restype = ctypes.c_int
             _lib.orc_lab_to_comoving.restype = ctypes.c_double
             _lib.orc_comoving_to_lab.restype = ctypes.c_double
@@ -249,6 +249,23 @@ class OracleProblem:
         chi = _f64(chi).reshape(self.Nc, self.G, self.N)
         out = np.zeros_like(In)
         lib().orc_sweep(ctypes.byref(self.s), _p(In), _p(eta), _p(chi), _p(out))
+        return out
+
+    def sweep_pairs(self, pairs, In, eta, chi):
+        """Stage a4 for chosen (ordinate k, group g) pairs only (Sec. 2, 2.1):
+        In, eta, chi and the result are [pair][c] (a pair's column over every
+        node), for problems whose full DO arrays do not fit in host memory."""
+        pairs = np.asarray(pairs, dtype=np.int32).reshape(-1, 2)
+        kk = np.ascontiguousarray(pairs[:, 0])
+        gg = np.ascontiguousarray(pairs[:, 1])
+        n = len(pairs)
+        In = _f64(In).reshape(n, self.Nc)
+        eta = _f64(eta).reshape(n, self.Nc)
+        chi = _f64(chi).reshape(n, self.Nc)
+        out = np.zeros_like(In)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib().orc_sweep_pairs(ctypes.byref(self.s), ctypes.c_int(n), kk.ctypes.data_as(ip), gg.ctypes.data_as(ip),
+                              _p(In), _p(eta), _p(chi), _p(out))
         return out
 
     def sums(self, J, Snew, Sold=None):

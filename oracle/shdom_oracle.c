@@ -622,24 +622,91 @@ static double bc_value(const orc_problem *P, long c, int g, int k, int N)
     return 0.0;
 }
 
-/* Stage a4: laboratory-frame short-characteristic sweep for every
- * (ordinate, group), with the time term of Sec. 2.1 (eq:time):
+/* Sweep of one (ordinate k, group g) pair over the whole grid (Sec. 2,
+ * eq:shdom; Sec. 2.1, eq:time):
  *   chi~ = chi_lab + kappa,   S~ = (eta_lab + kappa I^n) / chi~,
  * kappa = 1/(c dt).  The upwind point U = P - s n lies on the face crossed
  * first, s = min_a h_a/|n_a|; I, S~ and chi~ at U are bilinear in the four
  * nodes of that face; dtau = s (chi~_U + chi~_P)/2.  Nodes on an inflow face
  * take the boundary intensity.  Nodes are visited in the octant order of n,
- * so every upwind node is final before it is used. */
+ * so every upwind node is final before it is used.  In, eta, chi and out
+ * hold element c at index c * stride (out may alias In); St, Ct and Iw are
+ * work arrays of Nc reals. */
+static void sweep_pair(const orc_problem *P, const orc_mesh *M, int k, int g, const double *In, const double *eta_lab,
+                       const double *chi_lab, long stride, double *out, double *St, double *Ct, double *Iw)
+{
+    int nx = P->nx, ny = P->ny, nz = P->nz;
+    long Nc = (long)nx * ny * nz;
+    int N = M->N;
+    int dim[3] = {nx, ny, nz};
+    double h[3] = {P->lx / (nx - 1), P->ly / (ny - 1), P->lz / (nz - 1)};
+    double kap = P->kappa;
+    const double *n = M->dirs + 3 * k;
+    /* face crossed first */
+    int d = 0;
+    double best = fabs(n[0]) / h[0];
+    for (int a = 1; a < 3; ++a)
+        if (fabs(n[a]) / h[a] > best) { best = fabs(n[a]) / h[a]; d = a; }
+    double s = h[d] / fabs(n[d]);
+    int sg[3];
+    double fr[3];
+    for (int a = 0; a < 3; ++a) {
+        sg[a] = (n[a] > 0.0) - (n[a] < 0.0);
+        fr[a] = s * fabs(n[a]) / h[a];
+    }
+    int e1 = (d == 0) ? 1 : 0, e2 = (d == 2) ? 1 : 2;
+    for (long c = 0; c < Nc; ++c) {
+        Ct[c] = chi_lab[c * stride] + kap;
+        St[c] = Ct[c] > 0.0 ? (eta_lab[c * stride] + kap * In[c * stride]) / Ct[c] : 0.0;
+    }
+    int lo[3], hi[3], st[3];
+    for (int a = 0; a < 3; ++a) {
+        if (sg[a] >= 0) { lo[a] = 0; hi[a] = dim[a]; st[a] = 1; }
+        else { lo[a] = dim[a] - 1; hi[a] = -1; st[a] = -1; }
+    }
+    for (int iz = lo[2]; iz != hi[2]; iz += st[2])
+        for (int iy = lo[1]; iy != hi[1]; iy += st[1])
+            for (int ix = lo[0]; ix != hi[0]; ix += st[0]) {
+                int idx[3] = {ix, iy, iz};
+                long c = ((long)iz * ny + iy) * nx + ix;
+                int inflow = 0;
+                for (int a = 0; a < 3; ++a)
+                    if (sg[a] != 0 && idx[a] == (sg[a] > 0 ? 0 : dim[a] - 1)) inflow = 1;
+                if (inflow) {
+                    Iw[c] = bc_value(P, c, g, k, N);
+                    continue;
+                }
+                /* the four face nodes: (e1, e2) offsets 0 or -sg */
+                double wsum_i = 0.0, wsum_s = 0.0, wsum_c = 0.0;
+                for (int j1 = 0; j1 < 2; ++j1)
+                    for (int j2 = 0; j2 < 2; ++j2) {
+                        double w = (j1 ? fr[e1] : 1.0 - fr[e1]) * (j2 ? fr[e2] : 1.0 - fr[e2]);
+                        if (w == 0.0) continue;
+                        int q[3] = {ix, iy, iz};
+                        q[d] -= sg[d];
+                        q[e1] -= j1 * sg[e1];
+                        q[e2] -= j2 * sg[e2];
+                        long cu = ((long)q[2] * ny + q[1]) * nx + q[0];
+                        wsum_i += w * Iw[cu];
+                        wsum_s += w * St[cu];
+                        wsum_c += w * Ct[cu];
+                    }
+                double dtau = s * 0.5 * (wsum_c + Ct[c]);
+                double e, wp, wu;
+                sc_weights(dtau, &e, &wp, &wu);
+                Iw[c] = wsum_i * e + St[c] * wp + wsum_s * wu;
+            }
+    for (long c = 0; c < Nc; ++c) out[c * stride] = Iw[c];
+}
+
+/* Stage a4: the sweep of every (ordinate, group) pair (sweep_pair), on
+ * arrays in the [c][g][k] layout. */
 int orc_sweep(const orc_problem *P, const double *In, const double *eta_lab, const double *chi_lab, double *Inew)
 {
     orc_mesh M;
     mesh_init(P, &M);
-    int nx = P->nx, ny = P->ny, nz = P->nz;
-    long Nc = (long)nx * ny * nz;
+    long Nc = (long)P->nx * P->ny * P->nz;
     int N = M.N, G = P->G;
-    int dim[3] = {nx, ny, nz};
-    double h[3] = {P->lx / (nx - 1), P->ly / (ny - 1), P->lz / (nz - 1)};
-    double kap = P->kappa;
 #pragma omp parallel
     {
         double *St = (double *)malloc(sizeof(double) * Nc);
@@ -648,63 +715,36 @@ int orc_sweep(const orc_problem *P, const double *In, const double *eta_lab, con
 #pragma omp for schedule(dynamic, 1)
         for (long kg = 0; kg < (long)N * G; ++kg) {
             int k = (int)(kg / G), g = (int)(kg % G);
-            const double *n = M.dirs + 3 * k;
-            /* face crossed first */
-            int d = 0;
-            double best = fabs(n[0]) / h[0];
-            for (int a = 1; a < 3; ++a)
-                if (fabs(n[a]) / h[a] > best) { best = fabs(n[a]) / h[a]; d = a; }
-            double s = h[d] / fabs(n[d]);
-            int sg[3];
-            double fr[3];
-            for (int a = 0; a < 3; ++a) {
-                sg[a] = (n[a] > 0.0) - (n[a] < 0.0);
-                fr[a] = s * fabs(n[a]) / h[a];
-            }
-            int e1 = (d == 0) ? 1 : 0, e2 = (d == 2) ? 1 : 2;
-            for (long c = 0; c < Nc; ++c) {
-                long o = (c * G + g) * N + k;
-                Ct[c] = chi_lab[o] + kap;
-                St[c] = Ct[c] > 0.0 ? (eta_lab[o] + kap * In[o]) / Ct[c] : 0.0;
-            }
-            int lo[3], hi[3], st[3];
-            for (int a = 0; a < 3; ++a) {
-                if (sg[a] >= 0) { lo[a] = 0; hi[a] = dim[a]; st[a] = 1; }
-                else { lo[a] = dim[a] - 1; hi[a] = -1; st[a] = -1; }
-            }
-            for (int iz = lo[2]; iz != hi[2]; iz += st[2])
-                for (int iy = lo[1]; iy != hi[1]; iy += st[1])
-                    for (int ix = lo[0]; ix != hi[0]; ix += st[0]) {
-                        int idx[3] = {ix, iy, iz};
-                        long c = ((long)iz * ny + iy) * nx + ix;
-                        int inflow = 0;
-                        for (int a = 0; a < 3; ++a)
-                            if (sg[a] != 0 && idx[a] == (sg[a] > 0 ? 0 : dim[a] - 1)) inflow = 1;
-                        if (inflow) {
-                            Iw[c] = bc_value(P, c, g, k, N);
-                            continue;
-                        }
-                        /* the four face nodes: (e1, e2) offsets 0 or -sg */
-                        double wsum_i = 0.0, wsum_s = 0.0, wsum_c = 0.0;
-                        for (int j1 = 0; j1 < 2; ++j1)
-                            for (int j2 = 0; j2 < 2; ++j2) {
-                                double w = (j1 ? fr[e1] : 1.0 - fr[e1]) * (j2 ? fr[e2] : 1.0 - fr[e2]);
-                                if (w == 0.0) continue;
-                                int q[3] = {ix, iy, iz};
-                                q[d] -= sg[d];
-                                q[e1] -= j1 * sg[e1];
-                                q[e2] -= j2 * sg[e2];
-                                long cu = ((long)q[2] * ny + q[1]) * nx + q[0];
-                                wsum_i += w * Iw[cu];
-                                wsum_s += w * St[cu];
-                                wsum_c += w * Ct[cu];
-                            }
-                        double dtau = s * 0.5 * (wsum_c + Ct[c]);
-                        double e, wp, wu;
-                        sc_weights(dtau, &e, &wp, &wu);
-                        Iw[c] = wsum_i * e + St[c] * wp + wsum_s * wu;
-                    }
-            for (long c = 0; c < Nc; ++c) Inew[(c * G + g) * N + k] = Iw[c];
+            long off = (long)g * N + k;
+            sweep_pair(P, &M, k, g, In + off, eta_lab + off, chi_lab + off, (long)G * N, Inew + off, St, Ct, Iw);
+        }
+        free(St);
+        free(Ct);
+        free(Iw);
+    }
+    mesh_free(&M);
+    return 0;
+}
+
+/* Stage a4 for a chosen list of (ordinate kk[i], group gg[i]) pairs only,
+ * each on its own column: In, eta_lab, chi_lab and Inew are [i][c].  The
+ * arithmetic is sweep_pair's; this form lets a check sample the sweep of a
+ * problem whose full [c][g][k] arrays would not fit in host memory. */
+int orc_sweep_pairs(const orc_problem *P, int npairs, const int *kk, const int *gg, const double *In,
+                    const double *eta_lab, const double *chi_lab, double *Inew)
+{
+    orc_mesh M;
+    mesh_init(P, &M);
+    long Nc = (long)P->nx * P->ny * P->nz;
+#pragma omp parallel
+    {
+        double *St = (double *)malloc(sizeof(double) * Nc);
+        double *Ct = (double *)malloc(sizeof(double) * Nc);
+        double *Iw = (double *)malloc(sizeof(double) * Nc);
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < npairs; ++i) {
+            long off = (long)i * Nc;
+            sweep_pair(P, &M, kk[i], gg[i], In + off, eta_lab + off, chi_lab + off, 1, Inew + off, St, Ct, Iw);
         }
         free(St);
         free(Ct);

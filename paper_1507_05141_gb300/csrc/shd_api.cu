@@ -727,6 +727,15 @@ int ready_for_step(shd_ctx *c)
     return SHD_OK;
 }
 
+}  // namespace
+
+namespace shd {
+// ready_for_step for the other translation units (its message: shd_last_error)
+int check_ready(shd_ctx *c) { return ready_for_step(c); }
+}  // namespace shd
+
+namespace {
+
 struct FieldCheck {
     unsigned int bad, moving_changed, u_changed, pad;
     unsigned long long max_alpha, max_ne, max_uu;
@@ -1459,6 +1468,16 @@ int shd_get_sums(shd_ctx *c, double *energy, double *photons, double *resid)
     if (photons) *photons = s[1];
     if (resid) *resid = s[2];
     return SHD_OK;
+}
+
+int shd_check_bounded_wait(shd_ctx *c, long long polls)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (polls < 1 || polls > (1LL << 22)) return fail(SHD_ERR_ARG, "polls must be in [1, 2^22]");
+    if ((rc = check_device_flags(c))) return rc;  // report (and clear) an earlier give-up first
+    CK(launch_wait_selftest(polls, c->d_tc_err, c->stream), "wait self-check");
+    return check_device_flags(c);
 }
 
 // ---- single stages --------------------------------------------------------

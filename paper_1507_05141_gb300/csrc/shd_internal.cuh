@@ -226,6 +226,10 @@ namespace shd {
 // Counts a kernel launch issued by the library (see shd_launch_count).
 void note_launch();
 
+// SHD_OK when ctx can run a step: configured, and every stage's shared
+// memory within the limit (else the code, with the message in shd_last_error).
+int check_ready(shd_ctx *ctx);
+
 // -------------------------------------------------------------------------
 // device helpers
 // -------------------------------------------------------------------------
@@ -651,6 +655,10 @@ cudaError_t launch_convert_back(const T *src, double *dst, long long n, cudaStre
 
 cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, double *d_sigma_out,
                             const double *d_gx, const double *d_gw, int nq, cudaStream_t st);
+
+// one thread waits on an mbarrier nothing arrives on, `polls` times at most,
+// then raises *flag (the bounded-wait failure path of the tensor-core kernels)
+cudaError_t launch_wait_selftest(long long polls, int *flag, cudaStream_t st);
 
 size_t remap_smem_bytes(const shd_ctx *ctx);
 template <class T>

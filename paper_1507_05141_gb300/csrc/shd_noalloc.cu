@@ -48,25 +48,19 @@ cudaError_t scratch_address(int dev, void **out)
 
 }  // namespace
 
-extern "C" int shd_project_noalloc(shd_ctx *c, void *dev_Ish, void *dev_mom, void *cuda_stream)
+// The body of shd_project_noalloc with c->device current.
+static int project_noalloc(shd_ctx *c, void *dev_Ish, void *dev_mom, void *cuda_stream)
 {
-    g_msg[0] = 0;
-    if (!c || !dev_Ish || !dev_mom) {
-        snprintf(g_msg, sizeof(g_msg), "null context or output pointer");
-        return SHD_ERR_ARG;
+    // the same readiness check as shd_get_moments (configured, every stage's
+    // shared memory within the limit); it allocates nothing
+    int rc = check_ready(c);
+    if (rc != SHD_OK) {
+        snprintf(g_msg, sizeof(g_msg), "%s", shd_last_error());
+        return rc;
     }
-    if (c->device < 0 || c->device >= kMaxDevices) {
-        snprintf(g_msg, sizeof(g_msg), "device %d out of range", c->device);
-        return SHD_ERR_ARG;
-    }
-    if (!c->have_grid || !c->have_angles || !c->have_groups || !c->have_fields || !c->have_scat || !c->have_state) {
-        snprintf(g_msg, sizeof(g_msg), "context not configured (grid, angles, groups, fields, scattering, state)");
+    if (!c->have_state) {
+        snprintf(g_msg, sizeof(g_msg), "state not set");
         return SHD_ERR_STATE;
-    }
-    cudaError_t e = cudaSetDevice(c->device);
-    if (e != cudaSuccess) {
-        snprintf(g_msg, sizeof(g_msg), "cudaSetDevice: %s", cudaGetErrorString(e));
-        return SHD_ERR_CUDA;
     }
     if (c->nmoving > 0) {
         size_t need = (size_t)2 * c->nmoving * c->G * c->N * c->esize;
@@ -77,7 +71,8 @@ extern "C" int shd_project_noalloc(shd_ctx *c, void *dev_Ish, void *dev_mom, voi
         }
     }
     void *scratch = nullptr;
-    if ((e = scratch_address(c->device, &scratch)) != cudaSuccess) {
+    cudaError_t e = scratch_address(c->device, &scratch);
+    if (e != cudaSuccess) {
         snprintf(g_msg, sizeof(g_msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         return SHD_ERR_CUDA;
     }
@@ -93,6 +88,36 @@ extern "C" int shd_project_noalloc(shd_ctx *c, void *dev_Ish, void *dev_mom, voi
         return SHD_ERR_CUDA;
     }
     return SHD_OK;
+}
+
+extern "C" int shd_project_noalloc(shd_ctx *c, void *dev_Ish, void *dev_mom, void *cuda_stream)
+{
+    g_msg[0] = 0;
+    if (!c || !dev_Ish || !dev_mom) {
+        snprintf(g_msg, sizeof(g_msg), "null context or output pointer");
+        return SHD_ERR_ARG;
+    }
+    if (c->device < 0 || c->device >= kMaxDevices) {
+        snprintf(g_msg, sizeof(g_msg), "device %d out of range", c->device);
+        return SHD_ERR_ARG;
+    }
+    // run with the context's device current, then give the caller back theirs
+    int prev = -1;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != c->device) e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) {
+        snprintf(g_msg, sizeof(g_msg), "cudaSetDevice: %s", cudaGetErrorString(e));
+        return SHD_ERR_CUDA;
+    }
+    int rc = project_noalloc(c, dev_Ish, dev_mom, cuda_stream);
+    if (prev != c->device && prev >= 0) {
+        e = cudaSetDevice(prev);
+        if (e != cudaSuccess && rc == SHD_OK) {
+            snprintf(g_msg, sizeof(g_msg), "restoring device %d: %s", prev, cudaGetErrorString(e));
+            rc = SHD_ERR_CUDA;
+        }
+    }
+    return rc;
 }
 
 extern "C" const char *shd_noalloc_last_error(void) { return g_msg; }

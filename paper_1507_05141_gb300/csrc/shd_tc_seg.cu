@@ -1199,4 +1199,25 @@ cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, f
     return cudaSuccess;
 }
 
+// Self-check of the bounded-wait path: one thread initialises an mbarrier
+// that nothing ever arrives on, waits for its first phase with the same
+// bounded poll loop the tensor-core kernels use, and raises the context's
+// device flag when the wait gives up.  No copy or MMA is in flight, so
+// giving up leaves nothing behind.
+__global__ void k_wait_selftest(long long polls, int *flag)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    if (!tc::mbar_wait(&bar, 0u, polls)) *flag = 1;
+}
+
+cudaError_t launch_wait_selftest(long long polls, int *flag, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(polls, flag);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace shd

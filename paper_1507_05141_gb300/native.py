@@ -14,6 +14,7 @@ import numpy as np
 
 from . import build as _build
 
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NAN, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 FP64, FP32, MIXED = 0, 1, 2
 SCAT_ISO, SCAT_THOMSON, SCAT_KN, SCAT_TABLE = 1, 2, 3, 4
 BC_VACUUM, BC_ISO, BC_FULL = 0, 1, 2
@@ -60,6 +61,7 @@ _SIGS = {
     "shd_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "shd_batch_step": (_i, [_vp, _i, _vp]),
     "shd_batch_destroy": (None, [_vp]),
+    "shd_check_bounded_wait": (_i, [_vp, _ll]),
     "shd_project_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "shd_noalloc_last_error": (ctypes.c_char_p, []),
 }
@@ -214,6 +216,15 @@ class Solver:
         st = torch_stream() if stream is None else stream
         _check(self._L.shd_set_state_dev(self._h, ctypes.c_void_p(tensor.data_ptr()), ctypes.c_void_p(st)))
 
+    def get_state_dev(self, tensor, stream=None):
+        """State into a contiguous FP64 CUDA tensor in the [c][g][k] layout
+        (written on ``stream``, default torch's current stream)."""
+        import torch
+        assert tensor.dtype == torch.float64 and tensor.is_cuda and tensor.is_contiguous()
+        assert tensor.numel() == self.Nc * self.G * self.N
+        st = torch_stream() if stream is None else stream
+        _check(self._L.shd_get_state_dev(self._h, ctypes.c_void_p(tensor.data_ptr()), ctypes.c_void_p(st)))
+
     def get_state(self):
         out = np.zeros((self.Nc, self.G, self.N))
         _check(self._L.shd_get_state(self._h, _ptr(out)))
@@ -304,6 +315,12 @@ class Solver:
                                          None if stream is None else ctypes.c_void_p(stream))
         if rc != 0:
             raise ShdError(rc, self._L.shd_noalloc_last_error().decode() or "shd_project_noalloc failed")
+
+    def check_bounded_wait(self, polls=1000):
+        """Run the bounded-wait failure path once; returns the status code
+        (SHD_ERR_TIMEOUT expected) and the library's message."""
+        rc = self._L.shd_check_bounded_wait(self._h, int(polls))
+        return rc, self._L.shd_last_error().decode()
 
     def device_bytes(self):
         return int(self._L.shd_device_bytes(self._h))

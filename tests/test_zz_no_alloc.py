@@ -17,7 +17,13 @@ from paper_1507_05141_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-6}
+TOL = {"fp64": 1e-12, "fp32": 1e-6, "mixed": 1e-6}
+
+# (precision, grid): FP64 and FP32 on the ragged grid (brick kernels); MIXED
+# on a grid whose planes are multiples of 4 nodes, where the projection runs
+# the TMA-fed tensor-core segment kernels with the static array as their
+# node-major scratch (tensor maps over an address inside it)
+CASES = [("fp64", (11, 9, 7), 5), ("fp32", (11, 9, 7), 5), ("mixed", (16, 12, 8), 2)]
 
 
 def _native():
@@ -28,14 +34,15 @@ def _native():
     return native
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_noalloc_projection_matches_get_moments(precision):
+@pytest.mark.parametrize("precision,grid,G", CASES)
+def test_noalloc_projection_matches_get_moments(precision, grid, G):
     import torch
     native = _native()
-    spec = inputs.ragged_mixed(scattering="thomson")
+    spec = inputs.ragged_mixed(grid=grid, G=G, scattering="thomson")
     assert np.any(spec.u != 0), "the case must exercise the scratch (moving nodes)"
     s = native.Solver.from_spec(spec, precision=precision)
     dt = torch.float64 if precision == "fp64" else torch.float32
+    dev_before = torch.cuda.current_device()
     Ish = torch.empty((spec.Nc, spec.G, spec.NLM), dtype=dt, device="cuda")
     mom = torch.empty((spec.Nc, spec.G, 10), dtype=dt, device="cuda")
     for seed in (21, 22):  # two calls in a row on different states
@@ -44,6 +51,7 @@ def test_noalloc_projection_matches_get_moments(precision):
         Ish.fill_(float("nan"))
         mom.fill_(float("nan"))
         s.project_noalloc(Ish, mom)
+        assert torch.cuda.current_device() == dev_before  # the caller's device is kept
         torch.cuda.synchronize()
         Ish_n = Ish.double().cpu().numpy()
         mom_n = mom.double().cpu().numpy()
