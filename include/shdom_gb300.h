@@ -182,6 +182,24 @@ int shd_stage_sweep(shd_ctx *ctx, const double *I_old, const double *eta_lab, co
 int shd_set_state_dev(shd_ctx *ctx, const double *dev_I, void *cuda_stream);
 int shd_get_state_dev(shd_ctx *ctx, double *dev_I, void *cuda_stream);
 
+/* Schedule of the single-precision sweep (SHD_FP32 and SHD_MIXED, grids
+ * whose planes are multiples of 4 nodes): every plane of an (ordinate,
+ * group) pair is split over a thread-block cluster of C CTAs (C = 1, 2, 4
+ * or 8) of NT threads (256, 512 or 1024; C = 1 takes 1024), each CTA owning
+ * a block of rows; rows next to another CTA's block read it through
+ * distributed shared memory.  The result does not depend on the schedule
+ * (the same arithmetic per node).  By default the library times every
+ * schedule that fits on the first sweep run outside a stream capture (over
+ * a sample of pairs, on a scratch intensity it allocates and frees there)
+ * and keeps the fastest until the grid, angles or groups change.
+ * shd_set_sweep_schedule forces (C, NT) (SHD_ERR_ARG if it does not fit the
+ * problem), or with C = 0 returns to the automatic choice.
+ * shd_get_sweep_schedule reports the schedule in use (0, 0 before the first
+ * choice) and, when cand is not NULL, the timing of the last choice:
+ * *ncand rows of {C, NT, milliseconds} (at most 16; cand holds 48 floats). */
+int shd_set_sweep_schedule(shd_ctx *ctx, int C, int NT);
+int shd_get_sweep_schedule(shd_ctx *ctx, int *C, int *NT, int *ncand, float *cand);
+
 /* Self-check of the failure path of the tensor-core kernels' bounded waits
  * (no counterpart in the paper).  Every mbarrier wait in those kernels polls
  * a bounded number of times; when the limit runs out the kernel raises the

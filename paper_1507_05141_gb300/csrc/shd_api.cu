@@ -202,6 +202,8 @@ int dalloc(shd_ctx *c, void **p, size_t bytes, const char *what)
 // drop everything that depends on the problem sizes
 void drop_sized(shd_ctx *c)
 {
+    c->sweep_C = c->sweep_NT = 0;  // the sweep schedule depends on the sizes
+    c->sweep_ntune = 0;
     void **ptrs[] = {&c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
                      &c->d_I, &c->d_eta, &c->d_chi, &c->d_Ip, &c->d_Sp, &c->d_Sprev, &c->d_mom,
                      (void **)&c->d_partial, (void **)&c->d_stage,
@@ -1467,6 +1469,39 @@ int shd_get_sums(shd_ctx *c, double *energy, double *photons, double *resid)
     if (energy) *energy = s[0];
     if (photons) *photons = s[1];
     if (resid) *resid = s[2];
+    return SHD_OK;
+}
+
+int shd_set_sweep_schedule(shd_ctx *c, int C, int NT)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (C == 0) {
+        c->sweep_force_C = c->sweep_force_NT = 0;
+        c->sweep_C = c->sweep_NT = 0;  // choose again on the next sweep
+        drop_graphs(c);
+        return SHD_OK;
+    }
+    if (!sized(c)) return fail(SHD_ERR_STATE, "grid, angles and groups must be set");
+    if (!sweep_schedule_valid(c, C, NT))
+        return fail(SHD_ERR_ARG, "sweep schedule C=%d NT=%d does not fit this problem (or it has no FP32 plane sweep)",
+                    C, NT);
+    c->sweep_force_C = C;
+    c->sweep_force_NT = NT;
+    drop_graphs(c);
+    return SHD_OK;
+}
+
+int shd_get_sweep_schedule(shd_ctx *c, int *C, int *NT, int *ncand, float *cand)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (C) *C = c->sweep_force_C ? c->sweep_force_C : c->sweep_C;
+    if (NT) *NT = c->sweep_force_C ? c->sweep_force_NT : c->sweep_NT;
+    if (ncand) *ncand = c->sweep_ntune;
+    if (cand)
+        for (int i = 0; i < c->sweep_ntune; ++i)
+            for (int q = 0; q < 3; ++q) cand[3 * i + q] = c->sweep_tune[i][q];
     return SHD_OK;
 }
 

@@ -207,6 +207,16 @@ struct shd_ctx {
     long long bytes = 0;
     bool sprev_valid = false;
 
+    // schedule of the FP32 plane sweep: planes split over clusters of
+    // sweep_C CTAs of sweep_NT threads (0 = not chosen yet).  Forced by
+    // shd_set_sweep_schedule, else chosen by timing the schedules that fit on
+    // the first sweep launched outside a stream capture (sweep_tune: C, NT
+    // and milliseconds of each candidate); dropped when the sizes change
+    int sweep_force_C = 0, sweep_force_NT = 0;
+    int sweep_C = 0, sweep_NT = 0;
+    int sweep_ntune = 0;
+    float sweep_tune[16][3] = {};
+
     shd::Timing timing;
 
     // one time step captured as a CUDA graph per parity of the S_lm / S_prev
@@ -633,6 +643,7 @@ cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, c
                          bool use_chi0L = false);
 template <class T>
 bool sweep_uses_chi0L(const shd_ctx *ctx);
+bool sweep_schedule_valid(const shd_ctx *ctx, int C, int NT);
 template <class T>
 cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev, bool have_prev, cudaStream_t st);
 template <class T>

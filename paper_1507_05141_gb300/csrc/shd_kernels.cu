@@ -8,11 +8,15 @@
 // Paper passages: Sec. 2 (eq:shdom, Lambda iteration, SH <-> DO transforms),
 // Sec. 2.1 (eq:time), Sec. 2.2 (eq:lorentzfreq, eq:lorentzray, invariants,
 // remap between frame meshes), Sec. 2.3 (SH source, Thomson, eq:comptoncross).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <vector>
 
 #include "shd_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace shd {
 
@@ -546,12 +550,16 @@ template <int U, bool CB, bool WIDE>
 __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__restrict__ I,
                                                       const float *__restrict__ eta, const float *__restrict__ chi,
                                                       const float *__restrict__ chi0L,
-                                                      const unsigned long long *__restrict__ mbits, int npc, int nwin)
+                                                      const unsigned long long *__restrict__ mbits, int npc, int nwin,
+                                                      int tune_stride)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NT = 1024;
-    const int k = blockIdx.x / P.G;
-    const int g = blockIdx.x - k * P.G;
+    // tune_stride > 0 (schedule timing only): CTA b sweeps pair b * tune_stride
+    // with its intensity in column b of a scratch array I [b][Nc]
+    const int pair = tune_stride > 0 ? (int)blockIdx.x * tune_stride : (int)blockIdx.x;
+    const int k = pair / P.G;
+    const int g = pair - k * P.G;
     const Ordinate o = P.ord[k];
     const int dims[3] = {P.nx, P.ny, P.nz};
     const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
@@ -560,6 +568,7 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
     float4 *Q = reinterpret_cast<float4 *>(smem_raw);              // [2][pstride]
     float *ring = reinterpret_cast<float *>(Q + 2 * (size_t)pstride);  // [2][3][pstride]
     const long long base = ((long long)k * P.G + g) * P.Nc;
+    if (tune_stride > 0) I += (long long)blockIdx.x * P.Nc - base;
     const float *c0base = CB ? chi0L + ((long long)o.d * P.G + g) * P.Nc : nullptr;
     const unsigned long long *mb = CB ? mbits + (size_t)o.d * nwin * npc : nullptr;
     const float fr1 = (float)o.fr1, fr2 = (float)o.fr2, s = (float)o.s, kap = P.kappa;
@@ -636,6 +645,154 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
         }
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// -------------------------------------------------------------------------
+// a4, FP32, one plane split over a cluster of C CTAs: CTA r of the cluster
+// owns rows [r R, r R + R) of the plane (R rows of the in-plane axis e1, a
+// contiguous block of the sweep layout) and keeps the two previous-plane
+// buffers of k_sweep_pp for them only.  Upwind neighbours one row back that
+// belong to the neighbouring CTA (the first row of a CTA when n sweeps
+// towards +e1, the last when towards -e1) are read from that CTA's buffer
+// through distributed shared memory.  One cluster barrier per plane orders
+// the buffers exactly as k_sweep_pp's block barrier does, now across the
+// cluster.  Smaller CTAs let two or more clusters share an SM, so one
+// cluster's barrier wait overlaps another's compute; planes larger than one
+// CTA's shared memory fit across the cluster.  Every CTA runs every barrier
+// (no early exit) and a final one keeps its buffers alive until the peers'
+// last reads are done.
+// -------------------------------------------------------------------------
+template <int U, bool CB, bool WIDE, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_sweep_cl(Prob<float> P, float *__restrict__ I, const float *__restrict__ eta,
+                                                 const float *__restrict__ chi, const float *__restrict__ chi0L,
+                                                 const unsigned long long *__restrict__ mbits, int npc, int nwin,
+                                                 int pstride, int tune_stride)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int r = (int)cl.block_rank();
+    // tune_stride > 0 (schedule timing only): cluster b sweeps pair b *
+    // tune_stride with its intensity in column b of a scratch array I [b][Nc]
+    const int cidx = (int)blockIdx.x / C;
+    const int pair = tune_stride > 0 ? cidx * tune_stride : cidx;
+    const int k = pair / P.G;
+    const int g = pair - k * P.G;
+    const Ordinate o = P.ord[k];
+    const int dims[3] = {P.nx, P.ny, P.nz};
+    const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
+    const int plane = n1 * n2;
+    // rows per CTA: ceil(n1 / C), rounded up so every CTA's block of the
+    // layout starts on a 16-byte boundary
+    int R = (n1 + C - 1) / C;
+    const int q4 = (n2 & 3) == 0 ? 1 : ((n2 & 1) == 0 ? 2 : 4);
+    R = (R + q4 - 1) / q4 * q4;
+    const int row0 = r * R;
+    const int nrows = row0 >= n1 ? 0 : (n1 - row0 < R ? n1 - row0 : R);
+    const int nloc = nrows * n2;
+    const int j0 = row0 * n2;
+    float4 *Q = reinterpret_cast<float4 *>(smem_raw);                  // [2][pstride]
+    float *ring = reinterpret_cast<float *>(Q + 2 * (size_t)pstride);  // [2][3][pstride]
+    const long long base = ((long long)k * P.G + g) * P.Nc;
+    if (tune_stride > 0) I += (long long)cidx * P.Nc - base;
+    const float *c0base = CB ? chi0L + ((long long)o.d * P.G + g) * P.Nc : nullptr;
+    const unsigned long long *mb = CB ? mbits + (size_t)o.d * nwin * npc : nullptr;
+    const float fr1 = (float)o.fr1, fr2 = (float)o.fr2, s = (float)o.s, kap = P.kappa;
+    const float w00 = (1.f - fr1) * (1.f - fr2), w10 = fr1 * (1.f - fr2), w01 = (1.f - fr1) * fr2, w11 = fr1 * fr2;
+    const float bc_iso = P.bc_mode == SHD_BC_ISO ? P.bc[g] : 0.f;
+    const bool bc_full = P.bc_mode == SHD_BC_FULL;
+    const int tid = threadIdx.x;
+    // the CTA holding the row one step upwind of this CTA's boundary row
+    const int pr = o.s1 > 0 ? r - 1 : (o.s1 < 0 ? r + 1 : -1);
+    const bool has_peer = pr >= 0 && pr < C;
+    float4 *Qpeer = has_peer ? cl.map_shared_rank(Q, pr) : Q;
+    const int jpeer = has_peer ? pr * R * n2 : 0;  // first node of the peer's block
+
+    // bit u of `face`: node j0 + tid + NT u is on an inflow face of an
+    // in-plane axis; bit u of `halo`: its row-upwind neighbours are the peer's
+    unsigned face = 0, halo = 0;
+    {
+        const int first1 = o.s1 > 0 ? 0 : n1 - 1, first2 = o.s2 > 0 ? 0 : n2 - 1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int jl = tid + NT * u;
+            if (jl >= nloc) break;
+            const int i1 = (j0 + jl) / n2, i2 = (j0 + jl) - i1 * n2;
+            if ((o.s1 != 0 && i1 == first1) || (o.s2 != 0 && i2 == first2)) face |= 1u << u;
+            const int jn = jl - o.s1 * n2;
+            if (jn < 0 || jn >= nloc) halo |= 1u << u;
+        }
+    }
+    const int d1 = o.s1 * n2, d2 = o.s2;
+
+    auto issue = [&](int step) {
+        if (step < nd) {
+            const int id = o.sd > 0 ? step : nd - 1 - step;
+            const long long pb = base + (long long)id * plane + j0;
+            float *rg = ring + (size_t)(step & 1) * 3 * pstride;
+            const int nv = nloc / 4;  // 16-byte pieces per array
+            for (int q = tid; q < nv; q += NT) cp_async_n<16>(&rg[q * 4], &I[pb + q * 4]);
+            for (int q = tid; q < nv; q += NT) cp_async_n<16>(&rg[pstride + q * 4], &eta[pb + q * 4]);
+            for (int q = tid; q < nv; q += NT) {
+                const int off = q * 4;
+                const float *src = chi + pb + off;
+                if (CB && !((mb[(size_t)(id >> 6) * npc + (j0 >> 2) + q] >> (id & 63)) & 1ull))
+                    src = c0base + (long long)id * plane + j0 + off;
+                cp_async_n<16>(&rg[2 * pstride + off], src);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+
+    issue(0);
+    for (int step = 0; step < nd; ++step) {
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        cl.sync();  // this plane's copies and the cluster's previous-plane state are visible
+        issue(step + 1);
+        const float *rg = ring + (size_t)(step & 1) * 3 * pstride;
+        const size_t pprev = (size_t)((step + 1) & 1) * pstride;
+        const float4 *Qp = Q + pprev;                   // plane step - 1, this CTA's rows
+        const float4 *Qr = Qpeer + pprev;               // plane step - 1, the peer's rows
+        float4 *Qn = Q + (size_t)(step & 1) * pstride;  // plane step
+        const bool first = step == 0;
+        const int id = o.sd > 0 ? step : nd - 1 - step;
+        const long long pb = base + (long long)id * plane + j0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = tid + NT * u;
+            if (j >= nloc) break;
+            const float In = rg[j];
+            const float ct = rg[2 * pstride + j] + kap;
+            const float st = ct > 0.f ? (rg[pstride + j] + kap * In) * hw_rcp(ct) : 0.f;
+            float inew;
+            if (first || ((face >> u) & 1u)) {
+                inew = bc_full ? P.bc[pb + j] : bc_iso;
+            } else {
+                const float4 q00 = Qp[j], q01 = Qp[j - d2];
+                float4 q10, q11;
+                if ((halo >> u) & 1u) {
+                    const int jr = j0 + j - d1 - jpeer;  // the peer's local index
+                    q10 = Qr[jr];
+                    q11 = Qr[jr - d2];
+                } else {
+                    q10 = Qp[j - d1];
+                    q11 = Qp[j - d1 - d2];
+                }
+                const float iu = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                const float su = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                const float cu = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+                const float dtau = s * 0.5f * (cu + ct);
+                float ew, wp, wu;
+                if constexpr (WIDE) sc_weights<float>(dtau, ew, wp, wu);
+                else sc_weights_narrow<float>(dtau, ew, wp, wu);
+                inew = iu * ew + st * wp + su * wu;
+            }
+            Qn[j] = make_float4(inew, st, ct, 0.f);
+            I[pb + j] = inew;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    cl.sync();  // the peers' reads of this CTA's buffers are done
 }
 
 // -------------------------------------------------------------------------
@@ -937,20 +1094,208 @@ static size_t sweep_pp_smem_bytes(const shd_ctx *c)
 
 template <int U>
 static cudaError_t launch_sweep_pp(const shd_ctx *ctx, float *I, const float *eta, const float *chi, cudaStream_t st,
-                                   bool bits)
+                                   bool bits, bool wide, unsigned nblocks, int tune_stride)
 {
     Prob<float> P = make_prob<float>(ctx);
     const float *c0L = bits ? (const float *)ctx->d_chi0L : nullptr;
     const unsigned long long *mb = bits ? ctx->d_mbits : nullptr;
     const size_t sm = sweep_pp_smem_bytes(ctx);
-    const bool wide = !sweep_tau_bounded(ctx);
     auto kern = bits ? (wide ? k_sweep_pp<U, true, true> : k_sweep_pp<U, true, false>)
                      : (wide ? k_sweep_pp<U, false, true> : k_sweep_pp<U, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi, c0L, mb, ctx->mbits_npc, ctx->mbits_nwin);
+    kern<<<nblocks, 1024, sm, st>>>(P, I, eta, chi, c0L, mb, ctx->mbits_npc, ctx->mbits_nwin, tune_stride);
     note_launch();
     return cudaGetLastError();
+}
+
+// ---- schedules of the FP32 plane sweep ------------------------------------
+// A schedule splits every plane over a cluster of C CTAs of NT threads, U
+// nodes a thread (C = 1: k_sweep_pp, one 1024-thread CTA a plane).
+
+struct SweepSched {
+    int C = 0, NT = 0, U = 0, pstride = 0;
+    size_t smem = 0;
+};
+
+// rows of a plane per CTA of a C-CTA cluster (the kernel's own rule)
+static int sweep_rows_per_cta(int n1, int n2, int C)
+{
+    int R = (n1 + C - 1) / C;
+    const int q4 = (n2 & 3) == 0 ? 1 : ((n2 & 1) == 0 ? 2 : 4);
+    return (R + q4 - 1) / q4 * q4;
+}
+
+// Nodes per CTA of the largest class plane under a C-CTA split.
+static int sweep_nloc_max(const shd_ctx *c, int C)
+{
+    const int dims[3] = {c->nx, c->ny, c->nz};
+    bool seen[3] = {false, false, false};
+    int m = 0;
+    for (const Ordinate &o : c->h_ord) {
+        if (seen[o.d]) continue;
+        seen[o.d] = true;
+        const int n1 = dims[o.e1], n2 = dims[o.e2];
+        const int R = sweep_rows_per_cta(n1, n2, C);
+        const int nl = (R < n1 ? R : n1) * n2;
+        m = nl > m ? nl : m;
+    }
+    return m;
+}
+
+template <int U, int NT>
+static cudaError_t launch_sweep_cl_t(const shd_ctx *ctx, const SweepSched &sc, float *I, const float *eta,
+                                     const float *chi, cudaStream_t st, bool bits, bool wide, int nclusters,
+                                     int tune_stride)
+{
+    Prob<float> P = make_prob<float>(ctx);
+    const float *c0L = bits ? (const float *)ctx->d_chi0L : nullptr;
+    const unsigned long long *mb = bits ? ctx->d_mbits : nullptr;
+    auto kern = bits ? (wide ? k_sweep_cl<U, true, true, NT> : k_sweep_cl<U, true, false, NT>)
+                     : (wide ? k_sweep_cl<U, false, true, NT> : k_sweep_cl<U, false, false, NT>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclusters * sc.C));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = sc.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)sc.C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, P, I, eta, chi, c0L, mb, ctx->mbits_npc, ctx->mbits_nwin, sc.pstride,
+                           tune_stride);
+    note_launch();
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// Run schedule sc over `n` (ordinate, group) pairs (all of them, or every
+// tune_stride-th into a scratch intensity when timing).
+static cudaError_t run_sweep_sched(const shd_ctx *ctx, const SweepSched &sc, float *I, const float *eta,
+                                   const float *chi, cudaStream_t st, bool bits, bool wide, int n, int tune_stride)
+{
+    if (sc.C == 1) {
+        if (sc.U <= 1) return launch_sweep_pp<1>(ctx, I, eta, chi, st, bits, wide, (unsigned)n, tune_stride);
+        if (sc.U <= 2) return launch_sweep_pp<2>(ctx, I, eta, chi, st, bits, wide, (unsigned)n, tune_stride);
+        return launch_sweep_pp<4>(ctx, I, eta, chi, st, bits, wide, (unsigned)n, tune_stride);
+    }
+#define SHD_CL(NTv, Uv) \
+    if (sc.NT == NTv && sc.U == Uv) return launch_sweep_cl_t<Uv, NTv>(ctx, sc, I, eta, chi, st, bits, wide, n, tune_stride);
+    SHD_CL(256, 2) SHD_CL(256, 4) SHD_CL(512, 2) SHD_CL(512, 4) SHD_CL(1024, 2) SHD_CL(1024, 4)
+#undef SHD_CL
+    return cudaErrorInvalidConfiguration;
+}
+
+// The schedule (C, NT) with its U, buffer stride and shared memory, if it
+// fits this problem; false otherwise.
+static bool sweep_sched_make(const shd_ctx *c, int C, int NT, SweepSched &sc)
+{
+    sc = SweepSched();
+    const size_t limit = 227 * 1024;
+    if (C == 1) {
+        if (NT != 1024) return false;
+        const int u = (sweep_plane_max(c) + 1023) / 1024;
+        if (u > 4 || sweep_pp_smem_bytes(c) > limit) return false;
+        sc.C = 1; sc.NT = 1024; sc.U = u <= 1 ? 1 : (u <= 2 ? 2 : 4);
+        sc.smem = sweep_pp_smem_bytes(c);
+        return true;
+    }
+    if (C != 2 && C != 4 && C != 8) return false;
+    if (NT != 256 && NT != 512 && NT != 1024) return false;
+    const int nl = sweep_nloc_max(c, C);
+    int U = 0;
+    if (nl <= 2 * NT) U = 2;
+    else if (nl <= 4 * NT) U = 4;
+    else return false;
+    if (nl <= NT / 2) return false;  // half the threads or more would idle
+    sc.C = C; sc.NT = NT; sc.U = U;
+    sc.pstride = (nl + 3) & ~3;
+    sc.smem = sizeof(float) * (size_t)sc.pstride * 14;
+    return sc.smem <= limit;
+}
+
+// Every schedule that fits, k_sweep_pp's first.
+static std::vector<SweepSched> sweep_candidates(const shd_ctx *c)
+{
+    std::vector<SweepSched> v;
+    SweepSched sc;
+    if (sweep_sched_make(c, 1, 1024, sc)) v.push_back(sc);
+    for (int C : {2, 4, 8})
+        for (int NT : {256, 512, 1024})
+            if (sweep_sched_make(c, C, NT, sc)) v.push_back(sc);
+    return v;
+}
+
+// The FP32 sweep's schedule: forced, chosen earlier, or chosen now by timing
+// each candidate (one warm-up and three timed launches over every
+// tune_stride-th pair, intensity in a scratch array) when the stream is not
+// being captured; under capture without a choice, the first candidate.
+static bool sweep_schedule(const shd_ctx *cc, cudaStream_t st, const float *eta, const float *chi, bool bits,
+                           bool wide, SweepSched &out)
+{
+    shd_ctx *c = const_cast<shd_ctx *>(cc);  // the choice is a cache of the context
+    if (c->sweep_force_C > 0) return sweep_sched_make(c, c->sweep_force_C, c->sweep_force_NT, out);
+    if (c->sweep_C > 0 && sweep_sched_make(c, c->sweep_C, c->sweep_NT, out)) return true;
+    std::vector<SweepSched> cand = sweep_candidates(c);
+    if (cand.empty()) return false;
+    out = cand[0];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return true;
+    c->sweep_ntune = 0;
+    if (cand.size() > 1) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0)
+            sms = 148;
+        const int npairs = c->N * c->G;
+        const int n = npairs < 4 * sms ? npairs : 4 * sms;
+        const int stride = npairs / n;
+        float *scratch = nullptr;
+        if (cudaMalloc(&scratch, sizeof(float) * (size_t)n * c->Nc) != cudaSuccess) {
+            cudaGetLastError();
+            return true;  // no room to time them: the first candidate
+        }
+        cudaMemsetAsync(scratch, 0, sizeof(float) * (size_t)n * c->Nc, st);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (const SweepSched &sc : cand) {
+            float ms = 1e30f;
+            if (run_sweep_sched(c, sc, scratch, eta, chi, st, bits, wide, n, stride) == cudaSuccess) {
+                cudaEventRecord(e0, st);
+                bool ok = true;
+                for (int r = 0; r < 3 && ok; ++r)
+                    ok = run_sweep_sched(c, sc, scratch, eta, chi, st, bits, wide, n, stride) == cudaSuccess;
+                cudaEventRecord(e1, st);
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= 3.f;
+                }
+            }
+            cudaGetLastError();  // a candidate that cannot launch here is skipped
+            if (c->sweep_ntune < 16) {
+                c->sweep_tune[c->sweep_ntune][0] = (float)sc.C;
+                c->sweep_tune[c->sweep_ntune][1] = (float)sc.NT;
+                c->sweep_tune[c->sweep_ntune][2] = ms;
+                c->sweep_ntune++;
+            }
+            if (ms < best) {
+                best = ms;
+                out = sc;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(scratch);
+    }
+    c->sweep_C = out.C;
+    c->sweep_NT = out.NT;
+    return true;
 }
 
 // shared memory of the pipelined sweep: previous plane (4 reals a node in
@@ -971,6 +1316,13 @@ static bool sweep_vec(const shd_ctx *ctx)
            ((long long)ctx->nx * ctx->nz) % V == 0;
 }
 
+// (C, NT) is a schedule of the FP32 plane sweep for this problem
+bool sweep_schedule_valid(const shd_ctx *c, int C, int NT)
+{
+    SweepSched sc;
+    return c->precision != SHD_FP64 && sweep_vec<float>(c) && sweep_sched_make(c, C, NT, sc);
+}
+
 template <class T>
 bool sweep_uses_chi0L(const shd_ctx *ctx)
 {
@@ -987,12 +1339,13 @@ cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, c
     int plane = sweep_plane_max(ctx);
     size_t smp = sweep_pipe_smem_bytes(ctx);
     if constexpr (sizeof(T) == 4) {
-        const int u = (plane + 1023) / 1024;
-        if (sweep_vec<T>(ctx) && sweep_pp_smem_bytes(ctx) <= 227 * 1024 && u <= 4) {
+        if (sweep_vec<T>(ctx)) {
             const bool bits = use_chi0L && sweep_uses_chi0L<T>(ctx);
-            if (u <= 1) return launch_sweep_pp<1>(ctx, (float *)I, (const float *)eta, (const float *)chi, st, bits);
-            if (u <= 2) return launch_sweep_pp<2>(ctx, (float *)I, (const float *)eta, (const float *)chi, st, bits);
-            return launch_sweep_pp<4>(ctx, (float *)I, (const float *)eta, (const float *)chi, st, bits);
+            const bool wide = !sweep_tau_bounded(ctx);
+            SweepSched sc;
+            if (sweep_schedule(ctx, st, (const float *)eta, (const float *)chi, bits, wide, sc))
+                return run_sweep_sched(ctx, sc, (float *)I, (const float *)eta, (const float *)chi, st, bits, wide,
+                                       ctx->N * ctx->G, 0);
         }
     }
     if (smp <= 227 * 1024) {

@@ -62,6 +62,9 @@ _SIGS = {
     "shd_batch_step": (_i, [_vp, _i, _vp]),
     "shd_batch_destroy": (None, [_vp]),
     "shd_check_bounded_wait": (_i, [_vp, _ll]),
+    "shd_set_sweep_schedule": (_i, [_vp, _i, _i]),
+    "shd_get_sweep_schedule": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                    ctypes.POINTER(ctypes.c_float)]),
     "shd_project_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "shd_noalloc_last_error": (ctypes.c_char_p, []),
 }
@@ -315,6 +318,19 @@ class Solver:
                                          None if stream is None else ctypes.c_void_p(stream))
         if rc != 0:
             raise ShdError(rc, self._L.shd_noalloc_last_error().decode() or "shd_project_noalloc failed")
+
+    def set_sweep_schedule(self, C=0, NT=0):
+        """Force the single-precision sweep's cluster split (C CTAs of NT
+        threads a plane); C = 0 returns to the timed automatic choice."""
+        _check(self._L.shd_set_sweep_schedule(self._h, int(C), int(NT)))
+
+    def sweep_schedule(self):
+        """((C, NT) in use, [(C, NT, ms), ...] of the last timed choice)."""
+        C, NT, n = _i(), _i(), _i()
+        buf = (ctypes.c_float * 48)()
+        _check(self._L.shd_get_sweep_schedule(self._h, ctypes.byref(C), ctypes.byref(NT), ctypes.byref(n), buf))
+        rows = [(int(buf[3 * i]), int(buf[3 * i + 1]), float(buf[3 * i + 2])) for i in range(n.value)]
+        return (C.value, NT.value), rows
 
     def check_bounded_wait(self, polls=1000):
         """Run the bounded-wait failure path once; returns the status code

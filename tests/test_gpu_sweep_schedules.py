@@ -1,0 +1,94 @@
+"""Every schedule of the single-precision sweep against the oracle and
+against each other.
+
+A schedule splits each (ordinate, group) plane over a thread-block cluster
+of C CTAs of NT threads, each CTA owning a block of rows, and reads the
+neighbouring block's row through distributed shared memory.  The arithmetic
+per node is the same for every schedule, so results are bit-identical to the
+one-CTA-a-plane kernel; each is also checked against the FP64 oracle (Sec. 2
+eq:shdom, Sec. 2.1 eq:time).  Grids:
+
+* (60, 52, 6): ragged blocks (52 rows over 8 CTAs), and classes with fewer
+  rows than CTAs (6 rows over 8: CTAs with no rows still take part in every
+  cluster barrier);
+* (62, 52, 6): rows of 62 nodes, so a block must hold an even number of rows
+  to start on a 16-byte boundary;
+* (96, 96, 4): 9216-node planes, too large for one CTA's shared memory (only
+  clusters can sweep them).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1507_05141_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 2e-5
+SCHEDULES = [(1, 1024), (2, 256), (2, 512), (2, 1024), (4, 256), (4, 512), (4, 1024), (8, 256), (8, 512),
+             (8, 1024)]
+
+
+@pytest.fixture(scope="module")
+def native():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_05141_gb300 import native
+    return native
+
+
+def _oracle_step(spec, I0):
+    K, so = O.thomson_table(spec.G, spec.L)
+    P = O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
+                        alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=K, sigma_out=so,
+                        kappa=spec.kappa, box=spec.box)
+    I, _, _ = P.step(I0, 1)
+    return I
+
+
+@pytest.mark.parametrize("grid", [(60, 52, 6), (62, 52, 6), (96, 96, 4)])
+def test_every_schedule(native, grid):
+    spec = inputs.ragged_mixed(grid=grid, G=2, L=3)
+    I0 = inputs.random_state(spec, seed=41)
+    I_ref = _oracle_step(spec, I0)
+    scale = np.max(np.abs(I_ref), axis=0, keepdims=True)
+    results = {}
+    s = native.Solver.from_spec(spec, precision="fp32")
+    for C, NT in SCHEDULES:
+        try:
+            s.set_sweep_schedule(C, NT)
+        except native.ShdError:
+            continue  # does not fit this grid
+        s.set_state(I0)
+        s.step(1)
+        I = s.get_state()
+        assert s.sweep_schedule()[0] == (C, NT)
+        err = float(np.max(np.abs(I - I_ref) / scale))
+        assert err < FP32_TOL, ((C, NT), err)
+        results[(C, NT)] = I
+    s.close()
+    assert any(c > 1 for c, _ in results), "no cluster schedule ran"
+    if grid == (96, 96, 4):
+        assert (1, 1024) not in results  # the 9216-node planes need a cluster
+    keys = list(results)
+    for key in keys[1:]:
+        assert np.array_equal(results[key], results[keys[0]]), (key, keys[0])
+
+
+def test_automatic_choice_is_timed_and_kept(native):
+    spec = inputs.ragged_mixed(grid=(64, 64, 6), G=2, L=3)
+    s = native.Solver.from_spec(spec, precision="mixed")
+    assert s.sweep_schedule()[0] == (0, 0)
+    s.set_state(inputs.random_state(spec, seed=3))
+    s.step(2)
+    (C, NT), rows = s.sweep_schedule()
+    assert (C, NT) != (0, 0)
+    assert len(rows) >= 2
+    times = {(c, nt): ms for c, nt, ms in rows}
+    assert (C, NT) in times and times[(C, NT)] == min(times.values())
+    s.step(1)
+    assert s.sweep_schedule()[0] == (C, NT)  # kept
+    with pytest.raises(native.ShdError):
+        s.set_sweep_schedule(3, 256)
+    s.close()
