@@ -305,6 +305,9 @@ def bench_ours(args):
     # device-resident timed region
     ms, stage, clk_summary, launches = time_steps(solver, spec, args.steps, args.warmup, stream, dev, barrier)
     ms = max_over_ranks(ms, dev)
+    (sw_C, sw_NT), sw_rows = solver.sweep_schedule()
+    sweep_sched = {"cluster_ctas": sw_C, "threads": sw_NT,
+                   "timed": [{"cluster_ctas": c, "threads": nt, "ms_sample": round(t, 4)} for c, nt, t in sw_rows]}
     upd = spec.updates_per_step
     value = job_rate(upd, args.steps, ws, ms / 1e3)
 
@@ -372,6 +375,7 @@ def bench_ours(args):
                        "l2": f"no flush: the {do_gb:.1f} GB intensity state is far larger than L2",
                        "parallelism": f"replicas x{ws}"},
             "stage_ms": stage,
+            "sweep_schedule": sweep_sched,
             "plain_fp32": plain,
             "err_vs_fp64_oracle": errors,
             "roofline": {"kernel": "k_sweep_pp", "bound": "hbm", "achieved": achieved, "peak": peak,
