@@ -69,6 +69,11 @@ enum shd_scattering {
     SHD_SCAT_TABLE = 4     /* caller-supplied K[l][g][g'] and sigma_out[g']     */
 };
 
+enum shd_time_scheme {
+    SHD_TIME_EULER = 0,  /* one backward-Euler source iteration per step (Sec. 2.1) */
+    SHD_TIME_RK4 = 1     /* four sub-solves combined as in App. A, eq:rk4th        */
+};
+
 enum shd_boundary {
     SHD_BC_VACUUM = 0,  /* inflow intensity 0                                  */
     SHD_BC_ISO = 1,     /* inflow intensity data[g], same for every ordinate   */
@@ -131,6 +136,32 @@ int shd_set_boundary(shd_ctx *ctx, int mode, const double *data);
 /* kappa = 1/(c dt) of the backward-Euler time term (Sec. 2.1); 0 gives the
  * static equation.  kappa >= 0. */
 int shd_set_time(shd_ctx *ctx, double kappa);
+
+/* Time scheme of shd_step (enum shd_time_scheme).  SHD_TIME_EULER (the
+ * default): one source iteration with the time term of Sec. 2.1, eq:time.
+ * SHD_TIME_RK4: App. A, eq:rk4th -- the step from t to t + dt is divided
+ * into four sub-solves of eq:time from I(t) with time steps dt/6, dt/3,
+ * dt/3, dt/6, each one source iteration; with dI_i = (result - input) of
+ * sub-solve i, the inputs are I(t), I(t) + 3 dI_1, I(t) + 3/2 dI_2,
+ * I(t) + 3 dI_3 and the new state is I(t) + dI_1 + dI_2 + dI_3 + dI_4.
+ * RK4 holds three more intensity-sized device arrays (allocated here when
+ * the sizes are known, else on the next step) and costs four source
+ * iterations per step; shd_get_sums then reports the energy and photon
+ * number of I(t) and the source change of the last sub-solve.  Per-stage
+ * timing records each sub-solve as one step.  shd_solve_static always
+ * iterates the static equation (the scheme does not apply). */
+int shd_set_time_scheme(shd_ctx *ctx, int scheme);
+
+/* Ng acceleration of shd_solve_static (Sec. 2: the Lambda iteration is
+ * accelerated by Ng's method).  period = 0 turns it off (the default);
+ * period >= 4 extrapolates the source at iterations n >= 4 with
+ * n - (last extrapolation) >= period:  S* = (1 - a - b) S^n + a S^(n-1) +
+ * b S^(n-2), where (a, b) minimise |Q3 - a Q1 - b Q2|^2 over all (c, g, p)
+ * with Q1 = S^n - 2 S^(n-1) + S^(n-2), Q2 = S^n - S^(n-1) - S^(n-2) + S^(n-3),
+ * Q3 = S^n - S^(n-1) (inner products in FP64; no extrapolation when that
+ * 2 x 2 system is singular), and S* replaces S^n before its transform to
+ * the ordinates.  Holds three more SH-sized device arrays during the solve. */
+int shd_set_ng(shd_ctx *ctx, int period);
 
 /* Set / read the laboratory intensity state I [c][g][k] (host, double).
  * shd_get_state synchronises with the library's stream. */

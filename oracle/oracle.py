@@ -286,6 +286,66 @@ class OracleProblem:
                 raise MemoryError("oracle step failed")
         return I, Sprev, sums
 
+    def solve(self, frac, I):
+        """One source iteration of eq:time over the time step frac * dt from
+        I (kappa = 1/(c dt) divided by frac): the paper's script-I."""
+        kap = self.s.kappa
+        self.s.kappa = kap / frac
+        try:
+            out, _, _ = self.step(np.array(I, dtype=np.float64), 1)
+        finally:
+            self.s.kappa = kap
+        return out
+
+    def step_rk4(self, I, nsteps=1):
+        """``nsteps`` time steps by the Runge-Kutta sub-stepping of App. A."""
+        I = np.array(I, dtype=np.float64).reshape(self.Nc, self.G, self.N)
+        for _ in range(nsteps):
+            I = rk4_combine(self.solve, I)
+        return I
+
+    def solve_static_ng(self, tol=1e-6, max_iter=500, period=4, I=None):
+        """Lambda iteration of the static problem (kappa = 0) from I (default
+        0) with Ng acceleration of the source (Sec. 2): each iteration projects
+        I, forms S^n, reports the relative change against the source used in
+        the previous iteration; at n >= 4 with n - (last extrapolation) >=
+        period, S^n is replaced by ng_extrapolate(S^n, S^(n-1), S^(n-2),
+        S^(n-3)); then S is transformed to the ordinates and swept.  Stops
+        after iteration n > 1 whose relative change is <= tol.  Returns
+        (I, iterations, residual)."""
+        kap = self.s.kappa
+        self.s.kappa = 0.0
+        if I is None:
+            I = np.zeros((self.Nc, self.G, self.N))
+        I = np.array(I, dtype=np.float64)
+        hist = {}
+        Sprev = None
+        last = 0
+        it = 0
+        resid = np.inf
+        try:
+            while it < max_iter:
+                n = it + 1
+                Ip, J, _, _ = self.project(I)
+                S = self.source(Ip)
+                resid = self.sums(J, S, Sprev)[2]
+                if period and n >= 4 and n - last >= period:
+                    x = ng_extrapolate(S, hist[n - 1], hist[n - 2], hist[n - 3])
+                    if x is not None:
+                        S = x
+                        last = n
+                hist[n] = S
+                hist.pop(n - 3, None)
+                eta, chi = self.sh2lab(S)
+                I = self.sweep(I, eta, chi)
+                Sprev = S
+                it += 1
+                if it > 1 and resid <= tol:
+                    break
+        finally:
+            self.s.kappa = kap
+        return I, it, resid
+
     def solve_static(self, tol=1e-6, max_iter=500, I=None):
         """Lambda iteration from I (default 0) with kappa = 0 until the relative
         S change is <= tol (Sec. 2)."""
@@ -306,6 +366,45 @@ class OracleProblem:
         finally:
             self.s.kappa = kap
         return I, it, resid
+
+
+def rk4_combine(solve, I):
+    """One time step by the Runge-Kutta sub-stepping of App. A (eq:rk4th).
+
+    ``solve(frac, X)`` returns the solution of eq:time over the time step
+    frac * dt from the intensity X (the paper's script-I(frac dt, X)).  In the
+    paper's order: dI1 = I(dt/6, I) - I, I1 = I + 3 dI1; dI2 = I(dt/3, I1) -
+    I1, I2 = I + 3/2 dI2; dI3 = I(dt/3, I2) - I2, I3 = I + 3 dI3; dI4 =
+    I(dt/6, I3) - I3; the new intensity is I + dI1 + dI2 + dI3 + dI4."""
+    d1 = solve(1.0 / 6.0, I) - I
+    I1 = I + 3.0 * d1
+    d2 = solve(1.0 / 3.0, I1) - I1
+    I2 = I + 1.5 * d2
+    d3 = solve(1.0 / 3.0, I2) - I2
+    I3 = I + 3.0 * d3
+    d4 = solve(1.0 / 6.0, I3) - I3
+    return I + d1 + d2 + d3 + d4
+
+
+def ng_extrapolate(x0, x1, x2, x3):
+    """Ng's acceleration of an iteration (Sec. 2 cites it for the Lambda
+    iteration; Ng 1974), from the newest iterate x0 and the three before it:
+    with Q1 = x0 - 2 x1 + x2, Q2 = x0 - x1 - x2 + x3, Q3 = x0 - x1, the
+    coefficients (a, b) minimise |Q3 - a Q1 - b Q2|^2 (normal equations of
+    the five inner products), and the extrapolated iterate is
+    (1 - a - b) x0 + a x1 + b x2.  Returns None when the 2 x 2 system is
+    singular (det <= 1e-14 <Q1,Q1><Q2,Q2>)."""
+    q1 = (x0 - 2.0 * x1 + x2).ravel()
+    q2 = (x0 - x1 - x2 + x3).ravel()
+    q3 = (x0 - x1).ravel()
+    a11, a12, a22 = q1 @ q1, q1 @ q2, q2 @ q2
+    b1, b2 = q1 @ q3, q2 @ q3
+    det = a11 * a22 - a12 * a12
+    if not (np.isfinite(det) and det > 1e-14 * a11 * a22):
+        return None
+    a = (b1 * a22 - b2 * a12) / det
+    b = (b2 * a11 - b1 * a12) / det
+    return (1.0 - a - b) * x0 + a * x1 + b * x2
 
 
 def moments_to_eddington(J, Kt, floor=1e-300):

@@ -169,7 +169,9 @@ void free_all(shd_ctx *c)
                      (void **)&c->d_int2mesh, (void **)&c->d_mesh2int,
                      &c->d_chi0L, (void **)&c->d_mbits, &c->d_seg[0], &c->d_seg[1], &c->d_tcs_Bh[0], &c->d_tcs_Bh[1], &c->d_tcs_Bl[0],
                      &c->d_tcs_Bl[1], &c->d_tcs_Yh[0], &c->d_tcs_Yh[1], &c->d_tcs_Yl[0], &c->d_tcs_Yl[1],
-                     (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_fcheck};
+                     (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_fcheck,
+                     &c->d_ng[0], &c->d_ng[1], &c->d_ng[2], (void **)&c->d_ngpart, &c->d_rk[0], &c->d_rk[1],
+                     &c->d_rk[2], (void **)&c->d_sums_save};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
     c->rtab_n = 0;
@@ -209,7 +211,8 @@ void drop_sized(shd_ctx *c)
                      (void **)&c->d_partial, (void **)&c->d_stage,
                      &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag,
                      (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
-                     &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage};
+                     &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_ng[0], &c->d_ng[1], &c->d_ng[2],
+                     &c->d_rk[0], &c->d_rk[1], &c->d_rk[2]};
     for (void **p : ptrs) dfree(*p);
     c->ntiles = 0;
     c->nmoving = 0;
@@ -845,7 +848,7 @@ int ensure_remap_tables(shd_ctx *c, cudaStream_t st)
 // The kernels of one step on stream st (timing events around the stages when
 // ev is given); S_lm / S_prev are not swapped here.
 template <class T>
-int step_once(shd_ctx *c, cudaStream_t st, cudaEvent_t *ev)
+int step_once(shd_ctx *c, cudaStream_t st, cudaEvent_t *ev, const std::function<int()> *after_source = nullptr)
 {
     const bool tm = ev != nullptr;
     if (tm) CK(cudaEventRecord(ev[0], st), "event");
@@ -865,6 +868,11 @@ int step_once(shd_ctx *c, cudaStream_t st, cudaEvent_t *ev)
            "sums");
         if (tm) CK(cudaEventRecord(ev[3], st), "event");
     }
+    // a caller's step between the source and its transform (Ng extrapolation)
+    if (after_source && *after_source) {
+        int rc = (*after_source)();
+        if (rc) return rc;
+    }
     // the sweep takes chi at nodes at rest from the chi0 layouts, so chi_lab
     // is needed only where a node moves
     const bool c0L = sweep_uses_chi0L<T>(c);
@@ -872,6 +880,69 @@ int step_once(shd_ctx *c, cudaStream_t st, cudaEvent_t *ev)
     if (tm) CK(cudaEventRecord(ev[4], st), "event");
     CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st, c0L), "sweep");
     if (tm) CK(cudaEventRecord(ev[5], st), "event");
+    return SHD_OK;
+}
+
+// The Runge-Kutta arrays (allocated before any capture needs them).
+int ensure_rk_buffers(shd_ctx *c)
+{
+    if (c->time_scheme != SHD_TIME_RK4) return SHD_OK;
+    const size_t n = (size_t)c->Nc * c->G * c->N;
+    int rc;
+    for (int i = 0; i < 3; ++i)
+        if (!c->d_rk[i] && (rc = dalloc(c, &c->d_rk[i], n * c->esize, "Runge-Kutta arrays"))) return rc;
+    if (!c->d_sums_save && (rc = dalloc(c, (void **)&c->d_sums_save, 2 * sizeof(double), "saved sums"))) return rc;
+    return SHD_OK;
+}
+
+// The next per-stage timing slot of a recorded sub-solve, or null.
+cudaEvent_t *timing_slot(shd_ctx *c)
+{
+    if (!(c->timing.on && c->timing.count < Timing::kCap)) return nullptr;
+    return &c->timing.pool[(size_t)c->timing.count++ * (Timing::kStages + 1)];
+}
+
+// One time step on stream st.  SHD_TIME_EULER: one source iteration with
+// the backward-Euler time term (Sec. 2.1, eq:time).  SHD_TIME_RK4: App. A,
+// eq:rk4th: four sub-solves from I(t) with time steps dt/6, dt/3, dt/3, dt/6
+// (kappa = 1/(c dt) scaled by 6, 3, 3, 6), each one source iteration; after
+// sub-solve i with increment dI_i = result - input, the next input is
+// I(t) + 3 dI_1, I(t) + 3/2 dI_2, I(t) + 3 dI_3, and the new state is
+// I(t) + dI_1 + dI_2 + dI_3 + dI_4.  The sums report the energy and photon
+// number of I(t) (first sub-solve) and the source change of the last.
+// S_lm / S_prev are swapped between sub-solves here, and after the step by
+// the caller.
+template <class T>
+int step_full(shd_ctx *c, cudaStream_t st)
+{
+    if (c->time_scheme != SHD_TIME_RK4) return step_once<T>(c, st, timing_slot(c));
+    const long long n = (long long)c->Nc * c->G * c->N;
+    T *I = (T *)c->d_I, *A = (T *)c->d_rk[0], *B = (T *)c->d_rk[1], *acc = (T *)c->d_rk[2];
+    if (!A || !B || !acc || !c->d_sums_save) return fail(SHD_ERR_STATE, "Runge-Kutta arrays missing");
+    CK(cudaMemcpyAsync(A, I, n * sizeof(T), cudaMemcpyDeviceToDevice, st), "RK copy");
+    CK(cudaMemcpyAsync(B, I, n * sizeof(T), cudaMemcpyDeviceToDevice, st), "RK copy");
+    static const double frac[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    static const double cnext[4] = {3.0, 1.5, 3.0, 0.0};
+    const double kap = c->kappa;
+    int rc = SHD_OK;
+    for (int i = 0; i < 4 && rc == SHD_OK; ++i) {
+        c->kappa = kap / frac[i];
+        rc = step_once<T>(c, st, timing_slot(c));
+        if (rc) break;
+        if (i == 0) {
+            cudaError_t e = cudaMemcpyAsync(c->d_sums_save, c->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "save sums"); break; }
+        }
+        cudaError_t e = launch_rk_stage<T>(I, A, B, acc, n, cnext[i], i == 0, i == 3, st);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "Runge-Kutta stage"); break; }
+        if (i < 3) {
+            std::swap(c->d_Sp, c->d_Sprev);
+            c->sprev_valid = true;
+        }
+    }
+    c->kappa = kap;
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->d_sums, c->d_sums_save, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st), "restore sums");
     return SHD_OK;
 }
 
@@ -895,11 +966,19 @@ int capture_step(shd_ctx *c, int i)
     if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
     int rt = ensure_remap_tables(c, nullptr);  // built outside the graph, read in place by every replay
     if (rt) return rt;
+    if ((rt = ensure_rk_buffers(c))) return rt;
     const unsigned long long n0 = shd_launch_count_now();
+    void *sp0 = c->d_Sp, *sprev0 = c->d_Sprev;
+    const bool valid0 = c->sprev_valid;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    const int rc = step_once<T>(c, c->cap_stream, nullptr);
+    const int rc = step_full<T>(c, c->cap_stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+    // nothing ran: the buffers the step swapped while it was captured are
+    // put back as they stand before the step
+    c->d_Sp = sp0;
+    c->d_Sprev = sprev0;
+    c->sprev_valid = valid0;
     const unsigned long long n = shd_launch_count_now() - n0;
     forget_launches(n);  // captured, not launched
     cudaGetLastError();
@@ -944,12 +1023,12 @@ int graph_slot(shd_ctx *c, int &slot)
 }
 
 template <class T>
-int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false)
+int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false,
+              const std::function<int()> *after_source = nullptr)
 {
     if (int rc = ensure_remap_tables(c, st)) return rc;
+    if (int rc = ensure_rk_buffers(c)) return rc;
     for (int s = 0; s < nsteps; ++s) {
-        bool tm = c->timing.on && c->timing.count < Timing::kCap;
-        cudaEvent_t *ev = tm ? &c->timing.pool[(size_t)c->timing.count * (Timing::kStages + 1)] : nullptr;
         // a replay of the captured step: a step with S_prev, no timing events
         if (graphs) {
             int i;
@@ -962,9 +1041,8 @@ int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false)
                 continue;
             }
         }
-        int rc = step_once<T>(c, st, ev);
+        int rc = after_source ? step_once<T>(c, st, timing_slot(c), after_source) : step_full<T>(c, st);
         if (rc) return rc;
-        if (tm) c->timing.count++;
         std::swap(c->d_Sp, c->d_Sprev);
         c->sprev_valid = true;
     }
@@ -1410,13 +1488,63 @@ int shd_solve_static(shd_ctx *c, double rel_tol, int max_iter, int *iters_out, d
     if (!(rel_tol > 0) || max_iter < 1) return fail(SHD_ERR_ARG, "need rel_tol > 0 and max_iter >= 1");
     if ((rc = ready_for_step(c))) return rc;
     if (!c->have_state && (rc = shd_zero_state(c))) return rc;
+    // Ng acceleration: the last three source iterates and the scratch of
+    // the inner products
+    const size_t nS = (size_t)c->Nc * c->G * c->NLM;
+    const int ng_blocks = 4 * 152;
+    if (c->ng_period >= 4) {
+        for (int i = 0; i < 3; ++i)
+            if (!c->d_ng[i] && (rc = dalloc(c, &c->d_ng[i], nS * c->esize, "Ng iterates"))) return rc;
+        if (!c->d_ngpart && (rc = dalloc(c, (void **)&c->d_ngpart, sizeof(double) * (5 * ng_blocks + 5), "Ng sums")))
+            return rc;
+    }
     double kap = c->kappa;
     c->kappa = 0.0;
     c->sprev_valid = false;
-    int it = 0;
+    int it = 0, last_ng = 0;
     double sums[3] = {0, 0, 0};
+    // Ng (Sec. 2; Ng 1974) on iterate it = S^it, just formed by the source
+    // stage: at it >= 4 with it - last_ng >= period, x* = (1 - a - b) S^it +
+    // a S^(it-1) + b S^(it-2), (a, b) minimising |Q3 - a Q1 - b Q2| (FP64
+    // inner products; skipped when that 2 x 2 system is singular); then
+    // S^it (or x*) is kept as the newest of the three stored iterates
+    std::function<int()> ng_step = [&]() -> int {
+        const int n = it + 1;  // the iterate being formed
+        auto slot = [&](int j) { return c->d_ng[((j % 3) + 3) % 3]; };
+        if (n >= 4 && n - last_ng >= c->ng_period) {
+            double d[5];
+            cudaError_t e = is_fp64(c)
+                ? launch_ng_dots<double>((const double *)c->d_Sp, (const double *)slot(n - 1),
+                                         (const double *)slot(n - 2), (const double *)slot(n - 3), (long long)nS,
+                                         c->d_ngpart, ng_blocks, c->d_ngpart + 5 * ng_blocks, c->stream)
+                : launch_ng_dots<float>((const float *)c->d_Sp, (const float *)slot(n - 1),
+                                        (const float *)slot(n - 2), (const float *)slot(n - 3), (long long)nS,
+                                        c->d_ngpart, ng_blocks, c->d_ngpart + 5 * ng_blocks, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d, c->d_ngpart + 5 * ng_blocks, sizeof(d), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "Ng inner products");
+            const double det = d[0] * d[2] - d[1] * d[1];
+            if (std::isfinite(det) && det > 1e-14 * d[0] * d[2]) {
+                const double a = (d[3] * d[2] - d[4] * d[1]) / det;
+                const double b = (d[4] * d[0] - d[3] * d[1]) / det;
+                e = is_fp64(c) ? launch_ng_combine<double>((double *)c->d_Sp, (const double *)slot(n - 1),
+                                                           (const double *)slot(n - 2), (long long)nS, a, b, c->stream)
+                               : launch_ng_combine<float>((float *)c->d_Sp, (const float *)slot(n - 1),
+                                                          (const float *)slot(n - 2), (long long)nS, a, b, c->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "Ng extrapolation");
+                last_ng = n;
+            }
+        }
+        CK(cudaMemcpyAsync(slot(n), c->d_Sp, nS * c->esize, cudaMemcpyDeviceToDevice, c->stream), "Ng iterate");
+        return SHD_OK;
+    };
+    const std::function<int()> *hook = c->ng_period >= 4 ? &ng_step : nullptr;
+    const int scheme = c->time_scheme;
+    c->time_scheme = SHD_TIME_EULER;  // the static iteration has no time term to sub-step
     while (it < max_iter) {
-        rc = is_fp64(c) ? run_steps<double>(c, 1, c->stream) : run_steps<float>(c, 1, c->stream);
+        rc = is_fp64(c) ? run_steps<double>(c, 1, c->stream, false, hook)
+                        : run_steps<float>(c, 1, c->stream, false, hook);
         if (rc) break;
         ++it;
         cudaError_t e = cudaMemcpyAsync(sums, c->d_sums, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream);
@@ -1424,6 +1552,7 @@ int shd_solve_static(shd_ctx *c, double rel_tol, int max_iter, int *iters_out, d
         if (e != cudaSuccess) { rc = cuda_fail(e, "residual read"); break; }
         if (it > 1 && sums[2] <= rel_tol) break;
     }
+    c->time_scheme = scheme;
     c->kappa = kap;
     if (iters_out) *iters_out = it;
     if (resid_out) *resid_out = sums[2];
@@ -1469,6 +1598,30 @@ int shd_get_sums(shd_ctx *c, double *energy, double *photons, double *resid)
     if (energy) *energy = s[0];
     if (photons) *photons = s[1];
     if (resid) *resid = s[2];
+    return SHD_OK;
+}
+
+int shd_set_ng(shd_ctx *c, int period)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (period != 0 && period < 4) return fail(SHD_ERR_ARG, "Ng period must be 0 (off) or >= 4");
+    c->ng_period = period;
+    return SHD_OK;
+}
+
+int shd_set_time_scheme(shd_ctx *c, int scheme)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (scheme != SHD_TIME_EULER && scheme != SHD_TIME_RK4) return fail(SHD_ERR_ARG, "unknown time scheme %d", scheme);
+    if (scheme != c->time_scheme) drop_graphs(c);
+    c->time_scheme = scheme;
+    if (scheme == SHD_TIME_EULER) {
+        for (int i = 0; i < 3; ++i) dfree(c->d_rk[i]);
+        return SHD_OK;
+    }
+    if (sized(c)) return ensure_rk_buffers(c);
     return SHD_OK;
 }
 

@@ -217,6 +217,18 @@ struct shd_ctx {
     int sweep_ntune = 0;
     float sweep_tune[16][3] = {};
 
+    // Ng acceleration of shd_solve_static (0: off; else the period >= 4):
+    // the last three source iterates and the inner-product scratch
+    int ng_period = 0;
+    void *d_ng[3] = {nullptr, nullptr, nullptr};
+    double *d_ngpart = nullptr;  // [kNgBlocks * 5 + 5]
+    // time scheme of shd_step (SHD_TIME_EULER / SHD_TIME_RK4) and the three
+    // discrete-ordinate arrays of the Runge-Kutta sub-steps: I(t), the
+    // sub-solve input, the sum of increments; plus the saved sums
+    int time_scheme = SHD_TIME_EULER;
+    void *d_rk[3] = {nullptr, nullptr, nullptr};
+    double *d_sums_save = nullptr;  // [2]
+
     shd::Timing timing;
 
     // one time step captured as a CUDA graph per parity of the S_lm / S_prev
@@ -666,6 +678,18 @@ cudaError_t launch_convert_back(const T *src, double *dst, long long n, cudaStre
 
 cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, double *d_sigma_out,
                             const double *d_gx, const double *d_gw, int nq, cudaStream_t st);
+
+// Ng acceleration: FP64 inner products of the last four source iterates
+// into out5 (part: nblk * 5 doubles of scratch), and the extrapolation
+template <class T>
+cudaError_t launch_ng_dots(const T *x0, const T *x1, const T *x2, const T *x3, long long n, double *part, int nblk,
+                           double *out5, cudaStream_t st);
+template <class T>
+cudaError_t launch_ng_combine(T *x0, const T *x1, const T *x2, long long n, double a, double b, cudaStream_t st);
+// one Runge-Kutta combination pass over a discrete-ordinate array (App. A)
+template <class T>
+cudaError_t launch_rk_stage(T *I, const T *A, T *B, T *acc, long long n, double cnext, bool first, bool last,
+                            cudaStream_t st);
 
 // one thread waits on an mbarrier nothing arrives on, `polls` times at most,
 // then raises *flag (the bounded-wait failure path of the tensor-core kernels)

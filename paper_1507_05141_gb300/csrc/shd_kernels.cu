@@ -863,6 +863,93 @@ __global__ void __launch_bounds__(kSumsThreads) k_sums_final(const double *parti
 }
 
 // -------------------------------------------------------------------------
+// Ng acceleration of the Lambda iteration (Sec. 2, the acceleration cited
+// there, Ng 1974): from the last four source iterates x0 = S^n, x1 = S^{n-1},
+// x2 = S^{n-2}, x3 = S^{n-3} (all (c, g, p) values), the five FP64 inner
+// products <Q1,Q1>, <Q1,Q2>, <Q2,Q2>, <Q1,Q3>, <Q2,Q3> of
+//   Q1 = x0 - 2 x1 + x2,  Q2 = x0 - x1 - x2 + x3,  Q3 = x0 - x1,
+// per CTA (fixed-order tree), then one CTA adds the CTAs' sums in order.
+// -------------------------------------------------------------------------
+constexpr int kNgThreads = 256;
+
+template <class T>
+__global__ void __launch_bounds__(kNgThreads) k_ng_dots(const T *__restrict__ x0, const T *__restrict__ x1,
+                                                        const T *__restrict__ x2, const T *__restrict__ x3,
+                                                        long long n, double *part)
+{
+    __shared__ double red[5][kNgThreads];
+    double a[5] = {0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double v0 = (double)x0[i], v1 = (double)x1[i], v2 = (double)x2[i], v3 = (double)x3[i];
+        const double q1 = v0 - 2.0 * v1 + v2, q2 = v0 - v1 - v2 + v3, q3 = v0 - v1;
+        a[0] += q1 * q1;
+        a[1] += q1 * q2;
+        a[2] += q2 * q2;
+        a[3] += q1 * q3;
+        a[4] += q2 * q3;
+    }
+    for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = a[q];
+    __syncthreads();
+    for (int w = kNgThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kNgThreads) k_ng_final(const double *part, int nblk, double *out)
+{
+    __shared__ double red[5][kNgThreads];
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblk; b += kNgThreads)
+        for (int q = 0; q < 5; ++q) a[q] += part[b * 5 + q];
+    for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = a[q];
+    __syncthreads();
+    for (int w = kNgThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+// The extrapolated iterate x0 <- (1 - a - b) x0 + a x1 + b x2 (in FP64).
+template <class T>
+__global__ void k_ng_combine(T *__restrict__ x0, const T *__restrict__ x1, const T *__restrict__ x2, long long n,
+                             double a, double b)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x0[i] = (T)((1.0 - a - b) * (double)x0[i] + a * (double)x1[i] + b * (double)x2[i]);
+}
+
+// -------------------------------------------------------------------------
+// Runge-Kutta sub-stepping of a time step (App. A, eq:rk4th).  A holds
+// I(t), B the input of the sub-solve just run, I its result; with
+// dI = I - B:  acc = dI (first) or acc + dI;  then either the next input
+// I = B = A + c dI, or (last) the new state I = A + acc.
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void k_rk_stage(T *__restrict__ I, const T *__restrict__ A, T *__restrict__ B, T *__restrict__ acc,
+                           long long n, T cnext, int first, int last)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T d = I[i] - B[i];
+    const T s = first ? d : acc[i] + d;
+    if (last) {
+        I[i] = A[i] + s;
+        return;
+    }
+    acc[i] = s;
+    const T x = A[i] + cnext * d;
+    I[i] = x;
+    B[i] = x;
+}
+
+// -------------------------------------------------------------------------
 // layout conversions
 // -------------------------------------------------------------------------
 template <class T>
@@ -1468,6 +1555,38 @@ cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, do
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_ng_dots(const T *x0, const T *x1, const T *x2, const T *x3, long long n, double *part, int nblk,
+                           double *out5, cudaStream_t st)
+{
+    k_ng_dots<T><<<nblk, kNgThreads, 0, st>>>(x0, x1, x2, x3, n, part);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_ng_final<<<1, kNgThreads, 0, st>>>(part, nblk, out5);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_ng_combine(T *x0, const T *x1, const T *x2, long long n, double a, double b, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_ng_combine<T><<<blocks_for(n, 256), 256, 0, st>>>(x0, x1, x2, n, a, b);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_rk_stage(T *I, const T *A, T *B, T *acc, long long n, double cnext, bool first, bool last,
+                            cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_rk_stage<T><<<blocks_for(n, 256), 256, 0, st>>>(I, A, B, acc, n, (T)cnext, first ? 1 : 0, last ? 1 : 0);
+    note_launch();
+    return cudaGetLastError();
+}
+
 #define SHD_INSTANTIATE(T)                                                                                  \
     template Prob<T> make_prob<T>(const shd_ctx *);                                                         \
     template cudaError_t launch_chi0<T>(const shd_ctx *, cudaStream_t);                                     \
@@ -1483,7 +1602,13 @@ cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, do
     template cudaError_t launch_do_to_canon<T>(const shd_ctx *, const T *, double *, long long, long long,  \
                                                cudaStream_t);                                               \
     template cudaError_t launch_convert<T>(const double *, T *, long long, cudaStream_t);                   \
-    template cudaError_t launch_convert_back<T>(const T *, double *, long long, cudaStream_t);
+    template cudaError_t launch_convert_back<T>(const T *, double *, long long, cudaStream_t);               \
+    template cudaError_t launch_ng_dots<T>(const T *, const T *, const T *, const T *, long long, double *,  \
+                                           int, double *, cudaStream_t);                                    \
+    template cudaError_t launch_ng_combine<T>(T *, const T *, const T *, long long, double, double,         \
+                                              cudaStream_t);                                                \
+    template cudaError_t launch_rk_stage<T>(T *, const T *, T *, T *, long long, double, bool, bool,         \
+                                            cudaStream_t);
 
 SHD_INSTANTIATE(double)
 SHD_INSTANTIATE(float)

@@ -18,6 +18,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NAN, ERR_TIMEOUT = 0, -1, -2, -3,
 FP64, FP32, MIXED = 0, 1, 2
 SCAT_ISO, SCAT_THOMSON, SCAT_KN, SCAT_TABLE = 1, 2, 3, 4
 BC_VACUUM, BC_ISO, BC_FULL = 0, 1, 2
+TIME_EULER, TIME_RK4 = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
 SCATTERING = {"iso": SCAT_ISO, "thomson": SCAT_THOMSON, "kn": SCAT_KN, "table": SCAT_TABLE}
 STAGES = ("project", "source", "sums", "sh2lab", "sweep")
@@ -62,6 +63,8 @@ _SIGS = {
     "shd_batch_step": (_i, [_vp, _i, _vp]),
     "shd_batch_destroy": (None, [_vp]),
     "shd_check_bounded_wait": (_i, [_vp, _ll]),
+    "shd_set_ng": (_i, [_vp, _i]),
+    "shd_set_time_scheme": (_i, [_vp, _i]),
     "shd_set_sweep_schedule": (_i, [_vp, _i, _i]),
     "shd_get_sweep_schedule": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                                     ctypes.POINTER(ctypes.c_float)]),
@@ -318,6 +321,16 @@ class Solver:
                                          None if stream is None else ctypes.c_void_p(stream))
         if rc != 0:
             raise ShdError(rc, self._L.shd_noalloc_last_error().decode() or "shd_project_noalloc failed")
+
+    def set_ng(self, period=4):
+        """Ng acceleration of solve_static every `period` (>= 4) iterations; 0 = off."""
+        _check(self._L.shd_set_ng(self._h, int(period)))
+
+    def set_time_scheme(self, scheme):
+        """'euler' (one backward-Euler source iteration per step) or 'rk4'
+        (the four sub-solves of the paper's App. A)."""
+        code = {"euler": TIME_EULER, "rk4": TIME_RK4}[scheme] if isinstance(scheme, str) else int(scheme)
+        _check(self._L.shd_set_time_scheme(self._h, code))
 
     def set_sweep_schedule(self, C=0, NT=0):
         """Force the single-precision sweep's cluster split (C CTAs of NT

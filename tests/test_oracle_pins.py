@@ -752,3 +752,96 @@ def test_moving_box_matches_monte_carlo():
     assert np.all(np.abs(Ho - Hmc) <= 3 * sH + 0.03 * Jmc), (Ho, Hmc, sH)
     assert Jmc[2] > Jmc[1] and Jo[2] > Jo[1]
     assert Hmc[0] > 10 * sH[0] and Ho[0] > 0
+
+
+# --------------------------------------------------------------------------
+# Runge-Kutta sub-stepping (App. A, eq:rk4th) and Ng acceleration (Sec. 2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("z", [0.3, -0.7, 1.9, -2.5])
+def test_rk4_combination_is_classical_rk4_for_explicit_increments(z):
+    """With sub-solves that return the explicit increment X + frac dt f(X),
+    f(y) = lambda y, App. A's combination is the classical fourth-order
+    Runge-Kutta method: one step multiplies y by 1 + z + z^2/2 + z^3/6 +
+    z^4/24 (z = lambda dt) exactly.  A wrong stage fraction or combination
+    weight changes that polynomial."""
+    y0 = np.array([1.25])
+    out = O.rk4_combine(lambda frac, X: X + frac * z * X, y0)
+    taylor = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    assert out[0] == pytest.approx(1.25 * taylor, rel=1e-14)
+
+
+def test_rk4_keeps_equilibrium_exactly():
+    """I = B everywhere with emission alpha B, isotropic inflow B: every
+    sub-solve returns B, so the Runge-Kutta step does too."""
+    grid = (5, 4, 6)
+    B = 1.7
+    P = _box(grid, L=3, G=1, alpha=2.0, ne=1.5, emis=2.0 * B)
+    P.set_bc(1, np.array([B]))
+    P.set_kappa(9.0)
+    I = np.full((int(np.prod(grid)), 1, P.N), B)
+    out = P.step_rk4(I, 2)
+    assert np.allclose(out, B, rtol=1e-14, atol=0)
+
+
+def test_rk4_more_accurate_than_one_euler_step():
+    """The purpose App. A gives the sub-steps: from a smooth state (half the
+    static solution of the relaxation box) one step of c dt = h/2 by the
+    Runge-Kutta combination is closer to a fine-time reference (128 backward-
+    Euler steps of dt/128) than one backward-Euler step."""
+    from paper_1507_05141_gb300 import inputs
+    spec = inputs.relax_box(n=10)
+    K, so = O.iso_table(spec.G, spec.L)
+    mk = lambda kap: O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
+                                     alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=K, sigma_out=so,
+                                     kappa=kap)
+    Ist, _, _ = mk(0.0).solve_static(tol=1e-10)
+    I0 = 0.5 * Ist
+    kap = 1.0 / (0.5 / 9.0)
+    P = mk(kap)
+    Ibe, _, _ = P.step(I0.copy(), 1)
+    Irk = P.step_rk4(I0.copy(), 1)
+    Iref, _, _ = mk(kap * 128).step(I0.copy(), 128)
+    err = lambda a: np.max(np.abs(a - Iref)) / np.max(np.abs(Iref))
+    assert err(Irk) < 0.6 * err(Ibe)
+
+
+def test_ng_exact_for_two_mode_linear_iteration():
+    """For a linear iteration x <- M x + c whose error lies in two eigenvectors
+    of M, the error polynomial of Ng's extrapolation can vanish on both
+    eigenvalues, so one extrapolation from four iterates hits the fixed point
+    (to rounding); with three modes it still cuts the error."""
+    rng = np.random.default_rng(5)
+    n = 12
+    V = np.linalg.qr(rng.normal(size=(n, n)))[0]
+    lam = np.concatenate([[0.9, -0.6, 0.3], rng.uniform(-0.2, 0.2, n - 3)])
+    M = V @ np.diag(lam) @ V.T
+    c = rng.normal(size=n)
+    xstar = np.linalg.solve(np.eye(n) - M, c)
+    for modes, bound in ((2, 1e-10), (3, None)):
+        x = xstar + V[:, :modes] @ rng.normal(size=modes)
+        it = [x]
+        for _ in range(3):
+            it.append(M @ it[-1] + c)
+        ext = O.ng_extrapolate(it[3], it[2], it[1], it[0])
+        e_plain = np.linalg.norm(it[3] - xstar)
+        e_ng = np.linalg.norm(ext - xstar)
+        if bound is not None:
+            assert e_ng < bound * np.linalg.norm(xstar)
+        else:
+            assert e_ng < e_plain
+
+
+def test_ng_static_solve_converges_faster_to_the_same_solution():
+    from paper_1507_05141_gb300 import inputs
+    spec = inputs.relax_box(n=12)
+    K, so = O.iso_table(spec.G, spec.L)
+    P = O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
+                        alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=K, sigma_out=so,
+                        kappa=spec.kappa)
+    I1, it1, _ = P.solve_static(tol=1e-8, max_iter=300)
+    I2, it2, r2 = P.solve_static_ng(tol=1e-8, max_iter=300, period=4)
+    assert r2 <= 1e-8 and it2 < 0.75 * it1
+    assert np.max(np.abs(I2 - I1)) < 1e-6 * np.max(np.abs(I1))
+    I3, it3, _ = P.solve_static_ng(tol=1e-8, max_iter=300, period=0)  # off: the plain iteration
+    assert it3 == it1 and np.array_equal(I3, I1)
