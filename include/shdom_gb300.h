@@ -74,6 +74,11 @@ enum shd_time_scheme {
     SHD_TIME_RK4 = 1     /* four sub-solves combined as in App. A, eq:rk4th        */
 };
 
+enum shd_integrator {
+    SHD_SC_LINEAR = 0,  /* source linear in optical depth along the segment    */
+    SHD_SC_BEZIER = 1   /* cubic Bezier source (Sec. 2, the paper's scheme)     */
+};
+
 enum shd_boundary {
     SHD_BC_VACUUM = 0,  /* inflow intensity 0                                  */
     SHD_BC_ISO = 1,     /* inflow intensity data[g], same for every ordinate   */
@@ -136,6 +141,24 @@ int shd_set_boundary(shd_ctx *ctx, int mode, const double *data);
 /* kappa = 1/(c dt) of the backward-Euler time term (Sec. 2.1); 0 gives the
  * static equation.  kappa >= 0. */
 int shd_set_time(shd_ctx *ctx, double kappa);
+
+/* Source interpolation of the short-characteristic sweep (enum
+ * shd_integrator).  SHD_SC_LINEAR (the default): S~ linear in optical depth
+ * between the upwind point U and the node P.  SHD_SC_BEZIER: the cubic
+ * Bezier interpolant of Sec. 2 (de la Cruz Rodriguez & Piskunov 2013): S~
+ * on the segment is the cubic Bezier curve through S_U and S_P whose control
+ * points lie a third of the segment's optical depth along the end
+ * derivatives dS~/dtau, each clamped into [S_U, S_P] (no overshoot); the
+ * derivative at P is Fritsch and Butland's weighted harmonic mean of the
+ * upwind slope and the slope to the downwind point D = P + s n (the upwind
+ * slope where D leaves the grid), the derivative at U is bilinear in those
+ * of the upwind face nodes that have one (weights renormalised; the
+ * segment's slope if none has), and inflow nodes take the downwind slope
+ * (none without a downwind point).  Exact
+ * for a source linear in optical depth, third order for a smooth one.  The
+ * Bezier sweep takes planes of at most 4096 nodes (2365 in SHD_FP64);
+ * larger grids are refused at the next step with SHD_ERR_ARG. */
+int shd_set_integrator(shd_ctx *ctx, int integrator);
 
 /* Time scheme of shd_step (enum shd_time_scheme).  SHD_TIME_EULER (the
  * default): one source iteration with the time term of Sec. 2.1, eq:time.

@@ -32,7 +32,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 
 class Problem(ctypes.Structure):
-    """Mirror of ``orc_problem``; build it with :func:`make_problem`."""
+    """Mirror of ``orc_problem`` (held by :class:`OracleProblem`)."""
 
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
@@ -43,6 +43,7 @@ class Problem(ctypes.Structure):
         ("K", _dp), ("sigma_out", _dp),
         ("kappa", ctypes.c_double),
         ("bc_mode", ctypes.c_int), ("bc", _dp),
+        ("integrator", ctypes.c_int),
     ]
 
 
@@ -144,6 +145,14 @@ def interp_freq(edges, F, eps, nearest_outside=False):
     return lib().orc_interp_freq(len(edges) - 1, _p(edges), _p(F), 1, float(eps), int(nearest_outside))
 
 
+def bezier_weights(x: float):
+    """(e^-x, wU, wCU, wCP, wP) of the cubic Bezier short characteristic
+    over optical depth x (Sec. 2; the C oracle's orc_bezier_weights)."""
+    w = np.zeros(5)
+    lib().orc_bezier_weights(ctypes.c_double(float(x)), _p(w))
+    return w
+
+
 def kn_table(edges, L: int, energy_weighted: bool = True):
     """(K[l][g][g'], sigma_out[g']) of the multigroup Klein-Nishina kernel
     (Sec. 2.3, eq:comptoncross), in sigma_T units."""
@@ -207,6 +216,11 @@ class OracleProblem:
         s.kappa = float(kappa)
         s.bc_mode = int(bc_mode)
         s.bc = _p(self.bc) if self.bc is not None else None
+
+    def set_integrator(self, name):
+        """'linear' (linear-in-tau short characteristic) or 'bezier' (the
+        cubic Bezier short characteristic the paper uses, Sec. 2)."""
+        self.s.integrator = {"linear": 0, "bezier": 1}[name]
 
     def set_kappa(self, kappa):
         self.s.kappa = float(kappa)

@@ -62,6 +62,7 @@ typedef struct {
     double kappa;            /* 1/(c dt); 0 for the static problem            */
     int bc_mode;             /* 0 vacuum, 1 isotropic per group, 2 full array */
     const double *bc;        /* mode 1: [G]; mode 2: [c][g][k]                */
+    int integrator;          /* 0 linear-in-tau, 1 cubic Bezier (sweep_pair) */
 } orc_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -615,6 +616,61 @@ static void sc_weights(double x, double *e, double *wp, double *wu)
     *wu = a0 - *e;
 }
 
+/* Cubic Bezier short characteristic (Sec. 2: the paper's ray tracing uses a
+ * cubic Bezier interpolant, after de la Cruz Rodriguez & Piskunov 2013).
+ * On a segment of optical depth x from U to P the source is the cubic
+ * Bezier curve with end values S_U, S_P and control points C_U, C_P:
+ *   S(u) = S_U (1-u)^3 + 3 C_U u (1-u)^2 + 3 C_P u^2 (1-u) + S_P u^3,
+ * u = t/x, so that
+ *   I_P = I_U e^-x + wU S_U + wCU C_U + wCP C_P + wP S_P,
+ * the weights being x times the integrals of the Bernstein polynomials
+ * against e^-(x - t) over the segment.  With E_k = int_0^1 v^k e^(-x v) dv
+ * (v = 1 - u):  wU = x E3,  wCU = 3x (E2 - E3),  wCP = 3x (E1 - 2E2 + E3),
+ * wP = x (E0 - 3E1 + 3E2 - E3).  E_k is summed as its power series
+ * sum_m (-x)^m / (m! (k + m + 1)) below x = 1, and from the closed forms
+ * E0 = (1 - e)/x, E_k = (k E_(k-1) - e)/x (e = e^-x) above. */
+void orc_bezier_weights(double x, double *w /* [5]: e, wU, wCU, wCP, wP */)
+{
+    double E[4];
+    double e = exp(-x);
+    if (x < 1.0) {
+        for (int k = 0; k < 4; ++k) {
+            double term = 1.0, sum = 0.0;
+            for (int m = 0; m < 40; ++m) {
+                sum += term / (k + m + 1);
+                term *= -x / (m + 1);
+            }
+            E[k] = sum;
+        }
+    } else {
+        E[0] = -expm1(-x) / x;
+        for (int k = 1; k < 4; ++k) E[k] = (k * E[k - 1] - e) / x;
+    }
+    w[0] = e;
+    w[1] = x * E[3];
+    w[2] = 3.0 * x * (E[2] - E[3]);
+    w[3] = 3.0 * x * (E[1] - 2.0 * E[2] + E[3]);
+    w[4] = x * (E[0] - 3.0 * E[1] + 3.0 * E[2] - E[3]);
+}
+
+/* Derivative of the source along the ray at a node from the slopes of its
+ * upwind and downwind segments (optical depths xu, xd): Fritsch and
+ * Butland's weighted harmonic mean when both slopes have the same sign,
+ *   S' = du dd / (a dd + (1 - a) du),  a = (1 + xd/(xu + xd))/3,
+ * else 0 (a local extremum). */
+static double fb_derivative(double du, double dd, double xu, double xd)
+{
+    if (!(du * dd > 0.0)) return 0.0;
+    double a = (1.0 + xd / (xu + xd)) / 3.0;
+    return du * dd / (a * dd + (1.0 - a) * du);
+}
+
+static double clamp_between(double v, double a, double b)
+{
+    double lo = a < b ? a : b, hi = a < b ? b : a;
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
 static double bc_value(const orc_problem *P, long c, int g, int k, int N)
 {
     if (P->bc_mode == 1) return P->bc[g];
@@ -630,10 +686,14 @@ static double bc_value(const orc_problem *P, long c, int g, int k, int N)
  * nodes of that face; dtau = s (chi~_U + chi~_P)/2.  Nodes on an inflow face
  * take the boundary intensity.  Nodes are visited in the octant order of n,
  * so every upwind node is final before it is used.  In, eta, chi and out
- * hold element c at index c * stride (out may alias In); St, Ct and Iw are
- * work arrays of Nc reals. */
+ * hold element c at index c * stride (out may alias In); St, Ct, Iw and Dw
+ * are work arrays of Nc reals.  P->integrator selects the source
+ * interpolation along the segment: linear in tau (sc_weights) or the cubic
+ * Bezier curve (orc_bezier_weights), whose end derivatives need the
+ * downwind point D = P + s n as well and are kept per node in Dw. */
 static void sweep_pair(const orc_problem *P, const orc_mesh *M, int k, int g, const double *In, const double *eta_lab,
-                       const double *chi_lab, long stride, double *out, double *St, double *Ct, double *Iw)
+                       const double *chi_lab, long stride, double *out, double *St, double *Ct, double *Iw,
+                       double *Dw)
 {
     int nx = P->nx, ny = P->ny, nz = P->nz;
     long Nc = (long)nx * ny * nz;
@@ -672,12 +732,40 @@ static void sweep_pair(const orc_problem *P, const orc_mesh *M, int k, int g, co
                 int inflow = 0;
                 for (int a = 0; a < 3; ++a)
                     if (sg[a] != 0 && idx[a] == (sg[a] > 0 ? 0 : dim[a] - 1)) inflow = 1;
+                /* the downwind point D = P + s n (cubic Bezier only): on
+                 * the next face along n, bilinear in its four nodes; absent
+                 * when any of them lies outside the grid */
+                int has_d = 0;
+                double sd_ = 0.0, cd_ = 0.0;
+                if (P->integrator == 1) {
+                    has_d = 1;
+                    for (int j1 = 0; j1 < 2 && has_d; ++j1)
+                        for (int j2 = 0; j2 < 2; ++j2) {
+                            double w = (j1 ? fr[e1] : 1.0 - fr[e1]) * (j2 ? fr[e2] : 1.0 - fr[e2]);
+                            if (w == 0.0) continue;
+                            int q[3] = {ix, iy, iz};
+                            q[d] += sg[d];
+                            q[e1] += j1 * sg[e1];
+                            q[e2] += j2 * sg[e2];
+                            if (q[0] < 0 || q[0] >= nx || q[1] < 0 || q[1] >= ny || q[2] < 0 || q[2] >= nz) {
+                                has_d = 0;
+                                break;
+                            }
+                            long cq = ((long)q[2] * ny + q[1]) * nx + q[0];
+                            sd_ += w * St[cq];
+                            cd_ += w * Ct[cq];
+                        }
+                }
+                double xd = s * 0.5 * (Ct[c] + cd_);
                 if (inflow) {
                     Iw[c] = bc_value(P, c, g, k, N);
+                    /* an inflow node's derivative is its downwind slope; with
+                     * no downwind point either it has none (NaN) */
+                    if (P->integrator == 1) Dw[c] = has_d ? (xd > 0.0 ? (sd_ - St[c]) / xd : 0.0) : NAN;
                     continue;
                 }
                 /* the four face nodes: (e1, e2) offsets 0 or -sg */
-                double wsum_i = 0.0, wsum_s = 0.0, wsum_c = 0.0;
+                double wsum_i = 0.0, wsum_s = 0.0, wsum_c = 0.0, wsum_d = 0.0, wdv = 0.0;
                 for (int j1 = 0; j1 < 2; ++j1)
                     for (int j2 = 0; j2 < 2; ++j2) {
                         double w = (j1 ? fr[e1] : 1.0 - fr[e1]) * (j2 ? fr[e2] : 1.0 - fr[e2]);
@@ -690,8 +778,33 @@ static void sweep_pair(const orc_problem *P, const orc_mesh *M, int k, int g, co
                         wsum_i += w * Iw[cu];
                         wsum_s += w * St[cu];
                         wsum_c += w * Ct[cu];
+                        if (P->integrator == 1 && !isnan(Dw[cu])) {
+                            wsum_d += w * Dw[cu];
+                            wdv += w;
+                        }
                     }
                 double dtau = s * 0.5 * (wsum_c + Ct[c]);
+                if (P->integrator == 1) {
+                    /* end derivatives: at P by Fritsch-Butland from the
+                     * upwind and downwind slopes (the upwind slope alone
+                     * without D); at U bilinear in the derivatives kept at
+                     * the upwind face nodes that have one (weights
+                     * renormalised; the segment's slope if none has).
+                     * Control points one third of the segment along them,
+                     * clamped into [S_U, S_P] (no overshoot: the curve stays
+                     * in their convex hull). */
+                    double du = dtau > 0.0 ? (St[c] - wsum_s) / dtau : 0.0;
+                    double dp = du;
+                    if (has_d) dp = (dtau > 0.0 && xd > 0.0) ? fb_derivative(du, (sd_ - St[c]) / xd, dtau, xd) : 0.0;
+                    Dw[c] = dp;
+                    double dU = wdv > 0.0 ? wsum_d / wdv : du;
+                    double cu = clamp_between(wsum_s + dtau * dU / 3.0, wsum_s, St[c]);
+                    double cp = clamp_between(St[c] - dtau * dp / 3.0, wsum_s, St[c]);
+                    double w[5];
+                    orc_bezier_weights(dtau, w);
+                    Iw[c] = wsum_i * w[0] + w[1] * wsum_s + w[2] * cu + w[3] * cp + w[4] * St[c];
+                    continue;
+                }
                 double e, wp, wu;
                 sc_weights(dtau, &e, &wp, &wu);
                 Iw[c] = wsum_i * e + St[c] * wp + wsum_s * wu;
@@ -712,15 +825,18 @@ int orc_sweep(const orc_problem *P, const double *In, const double *eta_lab, con
         double *St = (double *)malloc(sizeof(double) * Nc);
         double *Ct = (double *)malloc(sizeof(double) * Nc);
         double *Iw = (double *)malloc(sizeof(double) * Nc);
+        double *Dw = (double *)malloc(sizeof(double) * Nc);
 #pragma omp for schedule(dynamic, 1)
         for (long kg = 0; kg < (long)N * G; ++kg) {
             int k = (int)(kg / G), g = (int)(kg % G);
             long off = (long)g * N + k;
-            sweep_pair(P, &M, k, g, In + off, eta_lab + off, chi_lab + off, (long)G * N, Inew + off, St, Ct, Iw);
+            sweep_pair(P, &M, k, g, In + off, eta_lab + off, chi_lab + off, (long)G * N, Inew + off, St, Ct, Iw,
+                       Dw);
         }
         free(St);
         free(Ct);
         free(Iw);
+        free(Dw);
     }
     mesh_free(&M);
     return 0;
@@ -741,14 +857,16 @@ int orc_sweep_pairs(const orc_problem *P, int npairs, const int *kk, const int *
         double *St = (double *)malloc(sizeof(double) * Nc);
         double *Ct = (double *)malloc(sizeof(double) * Nc);
         double *Iw = (double *)malloc(sizeof(double) * Nc);
+        double *Dw = (double *)malloc(sizeof(double) * Nc);
 #pragma omp for schedule(dynamic, 1)
         for (int i = 0; i < npairs; ++i) {
             long off = (long)i * Nc;
-            sweep_pair(P, &M, kk[i], gg[i], In + off, eta_lab + off, chi_lab + off, 1, Inew + off, St, Ct, Iw);
+            sweep_pair(P, &M, kk[i], gg[i], In + off, eta_lab + off, chi_lab + off, 1, Inew + off, St, Ct, Iw, Dw);
         }
         free(St);
         free(Ct);
         free(Iw);
+        free(Dw);
     }
     mesh_free(&M);
     return 0;

@@ -729,6 +729,9 @@ int ready_for_step(shd_ctx *c)
         return fail(SHD_ERR_ARG, "too many harmonics for the sh2lab kernel (%zu bytes shared memory)",
                     sh2lab_tile_smem_bytes(c));
     if (sweep_smem_bytes(c) > limit) return fail(SHD_ERR_ARG, "grid planes too large for the sweep kernel");
+    if (c->integrator == SHD_SC_BEZIER && !sweep_bez_usable(c))
+        return fail(SHD_ERR_ARG, "grid planes too large for the Bezier sweep (at most 4096 nodes, %zu bytes "
+                                 "of shared memory a node pair in this precision)", 2 * 6 * c->esize);
     return SHD_OK;
 }
 
@@ -1622,6 +1625,17 @@ int shd_set_time_scheme(shd_ctx *c, int scheme)
         return SHD_OK;
     }
     if (sized(c)) return ensure_rk_buffers(c);
+    return SHD_OK;
+}
+
+int shd_set_integrator(shd_ctx *c, int integrator)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (integrator != SHD_SC_LINEAR && integrator != SHD_SC_BEZIER)
+        return fail(SHD_ERR_ARG, "unknown integrator %d", integrator);
+    if (integrator != c->integrator) drop_graphs(c);
+    c->integrator = integrator;
     return SHD_OK;
 }
 

@@ -226,6 +226,8 @@ struct shd_ctx {
     // discrete-ordinate arrays of the Runge-Kutta sub-steps: I(t), the
     // sub-solve input, the sum of increments; plus the saved sums
     int time_scheme = SHD_TIME_EULER;
+    // source interpolation of the sweep (SHD_SC_LINEAR / SHD_SC_BEZIER)
+    int integrator = SHD_SC_LINEAR;
     void *d_rk[3] = {nullptr, nullptr, nullptr};
     double *d_sums_save = nullptr;  // [2]
 
@@ -619,6 +621,56 @@ __device__ inline void sc_weights<float>(float x, float &e, float &wp, float &wu
     sc_weights_narrow<float>(x, e, wp, wu);
 }
 
+// Cubic Bezier short characteristic (Sec. 2: the paper's cubic Bezier ray
+// tracing): over a segment of optical depth x with end values S_U, S_P and
+// control points C_U, C_P,  I_P = I_U e + wU S_U + wCU C_U + wCP C_P + wP S_P,
+// the weights being x times the integrals of the cubic Bernstein polynomials
+// against e^-(x - t):  with E_k = int_0^1 v^k e^(-x v) dv,  wU = x E3,
+// wCU = 3x (E2 - E3), wCP = 3x (E1 - 2 E2 + E3), wP = x (E0 - 3 E1 + 3 E2 - E3).
+// Small x: E3 by its power series sum_m (-x)^m / (m! (m + 4)), then the
+// stable downward recursion E_(k-1) = (x E_k + e)/k; large x: E0 = (1 - e)/x
+// and the upward recursion E_k = (k E_(k-1) - e)/x.
+template <class T>
+__device__ inline void bezier_weights(T x, T &e, T &wU, T &wCU, T &wCP, T &wP)
+{
+    T E0, E1, E2, E3;
+    constexpr bool F = sizeof(T) == 4;
+    e = F ? (T)hw_exp2((float)(-x * kLog2eF)) : (T)exp((double)-x);
+    const T xs = F ? T(2) : T(1);
+    if (x < xs) {
+        constexpr int M = F ? 14 : 24;
+        // Horner over m of (-x)^m / (m! (m + 4))
+        T acc = T(1) / T(M + 4);
+#pragma unroll
+        for (int m = M - 1; m >= 0; --m) acc = T(1) / T(m + 4) - x * acc / T(m + 1);
+        E3 = acc;
+        E2 = (x * E3 + e) / T(3);
+        E1 = (x * E2 + e) / T(2);
+        E0 = x * E1 + e;
+    } else {
+        E0 = (T(1) - e) / x;
+        E1 = (E0 - e) / x;
+        E2 = (T(2) * E1 - e) / x;
+        E3 = (T(3) * E2 - e) / x;
+    }
+    wU = x * E3;
+    wCU = T(3) * x * (E2 - E3);
+    wCP = T(3) * x * (E1 - T(2) * E2 + E3);
+    wP = x * (E0 - T(3) * E1 + T(3) * E2 - E3);
+}
+
+// Derivative of the source along the ray at a node from its upwind and
+// downwind slopes du, dd over optical depths xu, xd: Fritsch and Butland's
+// weighted harmonic mean du dd / (a dd + (1 - a) du), a = (1 + xd/(xu+xd))/3,
+// when du and dd have the same sign, else 0.
+template <class T>
+__device__ inline T fb_derivative(T du, T dd, T xu, T xd)
+{
+    if (!(du * dd > T(0))) return T(0);
+    const T a = (T(1) + xd / (xu + xd)) / T(3);
+    return du * dd / (a * dd + (T(1) - a) * du);
+}
+
 // -------------------------------------------------------------------------
 // launchers (shd_kernels.cu)
 // -------------------------------------------------------------------------
@@ -656,6 +708,7 @@ cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, c
 template <class T>
 bool sweep_uses_chi0L(const shd_ctx *ctx);
 bool sweep_schedule_valid(const shd_ctx *ctx, int C, int NT);
+bool sweep_bez_usable(const shd_ctx *ctx);
 template <class T>
 cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev, bool have_prev, cudaStream_t st);
 template <class T>

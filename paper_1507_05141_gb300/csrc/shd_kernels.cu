@@ -796,6 +796,174 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sweep_cl(Prob<float> P, float
 }
 
 // -------------------------------------------------------------------------
+// a4 with the cubic Bezier short characteristic (Sec. 2), any precision, one
+// 1024-thread CTA per (ordinate, group).  Besides the upwind point U the
+// source's end derivatives need the downwind point D = P + s n on the next
+// plane, so the walk runs one plane behind its inputs: iteration t forms
+// S~, chi~ of plane t+1 (buffer NX) and sweeps plane t-1, whose downwind
+// values (plane t) were formed in iteration t-1.  Plane t-1 writes (I, S~,
+// chi~, dS/dtau) of each node into buffer Q for the next plane's upwind
+// interpolation.  One barrier per iteration orders both two-slot buffers.
+// The end derivative at P is Fritsch-Butland's from the upwind and downwind
+// slopes (the upwind slope where D leaves the grid); at U the bilinear mix of
+// the upwind face nodes' derivatives over those that have one (the segment's
+// slope if none); at inflow nodes the downwind slope, none (NaN) without D.
+// Control points a third of the segment along them, clamped into [S_U, S_P].
+// -------------------------------------------------------------------------
+template <class T>
+struct alignas(4 * sizeof(T)) Quad4 {
+    T x, y, z, w;
+};
+template <class T>
+struct alignas(2 * sizeof(T)) Pair2 {
+    T x, y;
+};
+
+template <class T>
+__device__ inline T clamp_between(T v, T a, T b)
+{
+    const T lo = a < b ? a : b, hi = a < b ? b : a;
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+template <class T, int U, bool WIDE>
+__global__ void __launch_bounds__(1024, 1) k_sweep_bez(Prob<T> P, T *__restrict__ I, const T *__restrict__ eta,
+                                                       const T *__restrict__ chi, int pstride)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NT = 1024;
+    const int k = blockIdx.x / P.G;
+    const int g = blockIdx.x - k * P.G;
+    const Ordinate o = P.ord[k];
+    const int dims[3] = {P.nx, P.ny, P.nz};
+    const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
+    const int plane = n1 * n2;
+    Quad4<T> *Q = reinterpret_cast<Quad4<T> *>(smem_raw);         // [2][pstride]
+    Pair2<T> *NX = reinterpret_cast<Pair2<T> *>(Q + 2 * (size_t)pstride);  // [2][pstride]
+    const long long base = ((long long)k * P.G + g) * P.Nc;
+    const T fr1 = (T)o.fr1, fr2 = (T)o.fr2, s = (T)o.s, kap = P.kappa;
+    const T w00 = (T(1) - fr1) * (T(1) - fr2), w10 = fr1 * (T(1) - fr2), w01 = (T(1) - fr1) * fr2, w11 = fr1 * fr2;
+    const T bc_iso = P.bc_mode == SHD_BC_ISO ? P.bc[g] : T(0);
+    const bool bc_full = P.bc_mode == SHD_BC_FULL;
+    const int tid = threadIdx.x;
+    // bit u of fin / fout: node tid + NT u is on an inflow / outflow face of
+    // an in-plane axis (no upwind / no downwind point inside the grid)
+    unsigned fin = 0, fout = 0;
+    {
+        const int first1 = o.s1 > 0 ? 0 : n1 - 1, first2 = o.s2 > 0 ? 0 : n2 - 1;
+        const int last1 = o.s1 > 0 ? n1 - 1 : 0, last2 = o.s2 > 0 ? n2 - 1 : 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = tid + NT * u;
+            const int i1 = j / n2, i2 = j - i1 * n2;
+            if ((o.s1 != 0 && i1 == first1) || (o.s2 != 0 && i2 == first2)) fin |= 1u << u;
+            if ((o.s1 != 0 && i1 == last1) || (o.s2 != 0 && i2 == last2)) fout |= 1u << u;
+        }
+    }
+    const int d1 = o.s1 * n2, d2 = o.s2;
+    auto plane_id = [&](int step) { return o.sd > 0 ? step : nd - 1 - step; };
+    auto form = [&](int step, const T *In, const T *Et, const T *Ch) {
+        Pair2<T> *dst = NX + (size_t)(step & 1) * pstride;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = tid + NT * u;
+            if (j >= plane) break;
+            const T ct = Ch[u] + kap;
+            Pair2<T> v;
+            v.x = ct > T(0) ? (Et[u] + kap * In[u]) / ct : T(0);
+            v.y = ct;
+            dst[j] = v;
+        }
+    };
+    {
+        T In[U], Et[U], Ch[U];
+        const long long pb = base + (long long)plane_id(0) * plane;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = tid + NT * u;
+            In[u] = Et[u] = Ch[u] = T(0);
+            if (j < plane) { In[u] = I[pb + j]; Et[u] = eta[pb + j]; Ch[u] = chi[pb + j]; }
+        }
+        form(0, In, Et, Ch);
+    }
+    for (int t = 0; t <= nd; ++t) {
+        __syncthreads();
+        T In[U], Et[U], Ch[U];
+        const bool more = t + 1 < nd;
+        if (more) {
+            const long long pb = base + (long long)plane_id(t + 1) * plane;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = tid + NT * u;
+                In[u] = Et[u] = Ch[u] = T(0);
+                if (j < plane) { In[u] = I[pb + j]; Et[u] = eta[pb + j]; Ch[u] = chi[pb + j]; }
+            }
+        }
+        if (t >= 1) {
+            const int p = t - 1;
+            const long long pb = base + (long long)plane_id(p) * plane;
+            const Pair2<T> *own = NX + (size_t)(p & 1) * pstride;
+            const Pair2<T> *dn = NX + (size_t)(t & 1) * pstride;
+            const Quad4<T> *up = Q + (size_t)(t & 1) * pstride;  // plane p - 1
+            Quad4<T> *out = Q + (size_t)(p & 1) * pstride;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = tid + NT * u;
+                if (j >= plane) break;
+                const Pair2<T> me = own[j];
+                const T sP = me.x, cP = me.y;
+                const bool has_d = t < nd && !((fout >> u) & 1u);
+                T sD = T(0), cD = T(0);
+                if (has_d) {
+                    const Pair2<T> a = dn[j], b = dn[j + d1], c2 = dn[j + d2], dd = dn[j + d1 + d2];
+                    sD = w00 * a.x + w10 * b.x + w01 * c2.x + w11 * dd.x;
+                    cD = w00 * a.y + w10 * b.y + w01 * c2.y + w11 * dd.y;
+                }
+                const T xd = s * T(0.5) * (cP + cD);
+                T inew, dP;
+                if (p == 0 || ((fin >> u) & 1u)) {
+                    inew = bc_full ? P.bc[pb + j] : bc_iso;
+                    // the downwind slope; no derivative (NaN) without a downwind point
+                    dP = has_d ? (xd > T(0) ? (sD - sP) / xd : T(0)) : T(NAN);
+                } else {
+                    const Quad4<T> q00 = up[j], q10 = up[j - d1], q01 = up[j - d2], q11 = up[j - d1 - d2];
+                    const T iu = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                    const T su = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                    const T cu = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+                    // the upwind face nodes' derivatives, over those that have one
+                    T dsum = T(0), dw = T(0);
+                    if (!isnan(q00.w)) { dsum += w00 * q00.w; dw += w00; }
+                    if (!isnan(q10.w)) { dsum += w10 * q10.w; dw += w10; }
+                    if (!isnan(q01.w)) { dsum += w01 * q01.w; dw += w01; }
+                    if (!isnan(q11.w)) { dsum += w11 * q11.w; dw += w11; }
+                    const T x = s * T(0.5) * (cu + cP);
+                    const T slope = x > T(0) ? (sP - su) / x : T(0);
+                    const T du = dw > T(0) ? dsum / dw : slope;
+                    dP = slope;
+                    if (has_d) dP = (x > T(0) && xd > T(0)) ? fb_derivative<T>(slope, (sD - sP) / xd, x, xd) : T(0);
+                    const T Cu = clamp_between<T>(su + x * du / T(3), su, sP);
+                    const T Cp = clamp_between<T>(sP - x * dP / T(3), su, sP);
+                    T e, wU, wCU, wCP, wP;
+                    if (WIDE && sizeof(T) == 4 && x > T(kFp64Tau)) {
+                        double ed, a1, a2, a3, a4;
+                        bezier_weights<double>((double)x, ed, a1, a2, a3, a4);
+                        e = (T)ed; wU = (T)a1; wCU = (T)a2; wCP = (T)a3; wP = (T)a4;
+                    } else {
+                        bezier_weights<T>(x, e, wU, wCU, wCP, wP);
+                    }
+                    inew = iu * e + wU * su + wCU * Cu + wCP * Cp + wP * sP;
+                }
+                Quad4<T> v;
+                v.x = inew; v.y = sP; v.z = cP; v.w = dP;
+                out[j] = v;
+                I[pb + j] = inew;
+            }
+        }
+        if (more) form(t + 1, In, Et, Ch);
+    }
+}
+
+// -------------------------------------------------------------------------
 // a5: FP64 diagnostics; pass 1 per-block partials, pass 2 a single block
 // adds them in a fixed order (deterministic).
 // -------------------------------------------------------------------------
@@ -1413,6 +1581,7 @@ bool sweep_schedule_valid(const shd_ctx *c, int C, int NT)
 template <class T>
 bool sweep_uses_chi0L(const shd_ctx *ctx)
 {
+    if (ctx->integrator != SHD_SC_LINEAR) return false;  // the Bezier sweep reads every chi_lab
     const int u = (sweep_plane_max(ctx) + 1023) / 1024;
     return ctx->d_chi0L && ctx->d_mbits && sweep_vec<T>(ctx) && u <= 8 &&
            sweep_pipe_smem_bytes(ctx) + sizeof(unsigned long long) * (size_t)ctx->mbits_npc <= 227 * 1024;
@@ -1420,10 +1589,46 @@ bool sweep_uses_chi0L(const shd_ctx *ctx)
 
 // use_chi0L: the per-ordinate chi is only valid on the pieces that hold a
 // moving node (the stepping path); otherwise every chi value is read.
+// shared memory of the Bezier sweep: (I, S~, chi~, dS/dtau) of the previous
+// plane and (S~, chi~) of the next, two slots each
+size_t sweep_bez_smem_bytes(const shd_ctx *c)
+{
+    const size_t ps = ((size_t)sweep_plane_max(c) + 3) & ~(size_t)3;
+    return c->esize * ps * 12;
+}
+
+template <class T, int U>
+static cudaError_t launch_sweep_bez_u(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    const size_t sm = sweep_bez_smem_bytes(ctx);
+    const int pstride = (int)(((size_t)sweep_plane_max(ctx) + 3) & ~(size_t)3);
+    const bool wide = sizeof(T) == 4 && !sweep_tau_bounded(ctx);
+    auto kern = wide ? k_sweep_bez<T, U, (sizeof(T) == 4)> : k_sweep_bez<T, U, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(ctx->N * ctx->G), 1024, sm, st>>>(P, I, eta, chi, pstride);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// The Bezier sweep fits: planes of at most 4096 nodes within shared memory.
+bool sweep_bez_usable(const shd_ctx *c)
+{
+    return sweep_plane_max(c) <= 4096 && sweep_bez_smem_bytes(c) <= 227 * 1024;
+}
+
 template <class T>
 cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, cudaStream_t st, bool use_chi0L)
 {
     int plane = sweep_plane_max(ctx);
+    if (ctx->integrator == SHD_SC_BEZIER) {
+        if (!sweep_bez_usable(ctx)) return cudaErrorInvalidConfiguration;
+        const int u = (plane + 1023) / 1024;
+        if (u <= 1) return launch_sweep_bez_u<T, 1>(ctx, I, eta, chi, st);
+        if (u <= 2) return launch_sweep_bez_u<T, 2>(ctx, I, eta, chi, st);
+        return launch_sweep_bez_u<T, 4>(ctx, I, eta, chi, st);
+    }
     size_t smp = sweep_pipe_smem_bytes(ctx);
     if constexpr (sizeof(T) == 4) {
         if (sweep_vec<T>(ctx)) {

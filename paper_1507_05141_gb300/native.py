@@ -19,6 +19,7 @@ FP64, FP32, MIXED = 0, 1, 2
 SCAT_ISO, SCAT_THOMSON, SCAT_KN, SCAT_TABLE = 1, 2, 3, 4
 BC_VACUUM, BC_ISO, BC_FULL = 0, 1, 2
 TIME_EULER, TIME_RK4 = 0, 1
+SC_LINEAR, SC_BEZIER = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
 SCATTERING = {"iso": SCAT_ISO, "thomson": SCAT_THOMSON, "kn": SCAT_KN, "table": SCAT_TABLE}
 STAGES = ("project", "source", "sums", "sh2lab", "sweep")
@@ -64,6 +65,7 @@ _SIGS = {
     "shd_batch_destroy": (None, [_vp]),
     "shd_check_bounded_wait": (_i, [_vp, _ll]),
     "shd_set_ng": (_i, [_vp, _i]),
+    "shd_set_integrator": (_i, [_vp, _i]),
     "shd_set_time_scheme": (_i, [_vp, _i]),
     "shd_set_sweep_schedule": (_i, [_vp, _i, _i]),
     "shd_get_sweep_schedule": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -321,6 +323,12 @@ class Solver:
                                          None if stream is None else ctypes.c_void_p(stream))
         if rc != 0:
             raise ShdError(rc, self._L.shd_noalloc_last_error().decode() or "shd_project_noalloc failed")
+
+    def set_integrator(self, name):
+        """'linear' (linear-in-tau short characteristic) or 'bezier' (the
+        paper's cubic Bezier short characteristic)."""
+        code = {"linear": SC_LINEAR, "bezier": SC_BEZIER}[name] if isinstance(name, str) else int(name)
+        _check(self._L.shd_set_integrator(self._h, code))
 
     def set_ng(self, period=4):
         """Ng acceleration of solve_static every `period` (>= 4) iterations; 0 = off."""

@@ -98,13 +98,19 @@ def test_ng_static_fp64_matches_oracle(native):
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
 def test_ng_static_single_precision(native, precision):
     """Single precision with Ng: converges to the tolerance in fewer
-    iterations than without, to the oracle's static solution."""
+    iterations than without, to the same fixed point as the plain iteration
+    in that precision.  The fixed point of a single-precision iteration
+    differs from the FP64 one by the per-iteration rounding amplified by the
+    iteration's 1/(1 - rho) (rho: its spectral radius, about 0.9 here), so
+    against the oracle's static solution the bound is ten times the
+    per-step tolerance."""
     spec = inputs.jet(n=12, G=3, L=3, tau_r=6.0, gmax=3.0)
     P = _oracle(spec)
-    I_ref, it_r, _ = P.solve_static(tol=1e-6, max_iter=300)
+    I_ref, it_r, _ = P.solve_static(tol=1e-7, max_iter=400)
     plain = native.Solver.from_spec(spec, precision=precision)
     plain.zero_state()
     it_p, _ = plain.solve_static(1e-6, 300)
+    I_p = plain.get_state()
     plain.close()
     s = native.Solver.from_spec(spec, precision=precision)
     s.set_ng(4)
@@ -112,7 +118,9 @@ def test_ng_static_single_precision(native, precision):
     it_g, r_g = s.solve_static(1e-6, 300)
     assert r_g <= 1e-6 and it_g < it_p
     I = s.get_state()
-    assert float(np.max(np.abs(I - I_ref)) / np.max(np.abs(I_ref))) < 2e-5 + 10 * 1e-6
+    scale = np.max(np.abs(I_ref))
+    assert float(np.max(np.abs(I - I_p)) / scale) < 2e-5
+    assert float(np.max(np.abs(I - I_ref)) / scale) < 10 * TOL[precision]
     with pytest.raises(native.ShdError):
         s.set_ng(3)
     s.close()

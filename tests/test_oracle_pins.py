@@ -845,3 +845,127 @@ def test_ng_static_solve_converges_faster_to_the_same_solution():
     assert np.max(np.abs(I2 - I1)) < 1e-6 * np.max(np.abs(I1))
     I3, it3, _ = P.solve_static_ng(tol=1e-8, max_iter=300, period=0)  # off: the plain iteration
     assert it3 == it1 and np.array_equal(I3, I1)
+
+
+# --------------------------------------------------------------------------
+# cubic Bezier short characteristic (Sec. 2: the paper's ray tracing scheme)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("x", [1e-8, 1e-3, 0.2, 0.999, 1.0, 1.5, 7.0, 40.0])
+def test_bezier_weights_match_quadrature(x):
+    """x times the integral over the segment of each cubic Bernstein
+    polynomial against e^-(x - t) (t the optical depth from U), by adaptive
+    quadrature; the weights add up to 1 - e^-x (a constant source)."""
+    from scipy.integrate import quad
+    w = O.bezier_weights(x)
+    basis = [lambda u: (1 - u) ** 3, lambda u: 3 * u * (1 - u) ** 2, lambda u: 3 * u * u * (1 - u),
+             lambda u: u ** 3]
+    assert w[0] == pytest.approx(np.exp(-x), rel=1e-15)
+    for j, B in enumerate(basis):
+        ref = x * quad(lambda u: B(u) * np.exp(-x * (1 - u)), 0, 1, epsabs=0, epsrel=1e-13, limit=200)[0]
+        assert w[1 + j] == pytest.approx(ref, rel=1e-12, abs=1e-300)
+    assert np.sum(w[1:]) == pytest.approx(-np.expm1(-x), rel=1e-13)
+
+
+def test_bezier_linear_source_exact_along_z():
+    """A source linear in optical depth has the same slope at every node, so
+    every end derivative is that slope, the control points lie on the line
+    (no clamping) and the Bezier curve is the line: exact, as for the linear
+    scheme."""
+    grid, box = (5, 4, 12), (1.0, 1.0, 1.0)
+    for chi_v in [0.3, 4.0, 60.0]:
+        P = _box(grid, L=3, G=1, alpha=chi_v, box=box)
+        P.set_integrator("bezier")
+        _, _, dirs, _ = O.ordinates(P.nmu, P.nphi)
+        X, Y, Z = _node_xyz(grid, box)
+        a_, b_, C = 0.7, 1.9, 0.4
+        S = a_ + b_ * chi_v * Z
+        Nc = Z.size
+        eta = np.repeat((chi_v * S)[:, None, None], P.N, axis=2)
+        chi = np.full((Nc, 1, P.N), chi_v)
+        zd = _z_dominant(dirs) & (dirs[:, 2] > 0)
+        mu_k = dirs[:, 2]
+        tau = chi_v * Z[:, None] / np.where(mu_k > 0, mu_k, 1.0)[None, :]
+        bb = b_ * mu_k[None, :]
+        exact = a_ + bb * (tau - 1.0) + C * np.exp(-tau)
+        P.set_bc(2, exact[:, None, :])
+        out = P.sweep(np.zeros_like(eta), eta, chi)
+        assert np.allclose(out[:, 0, zd], exact[:, zd], rtol=1e-12, atol=1e-13), chi_v
+
+
+def test_bezier_beam_and_equilibrium_exact():
+    grid, box = (6, 5, 9), (1.0, 1.0, 1.0)
+    alpha = 2.3
+    P = _box(grid, L=3, G=1, alpha=alpha, box=box)
+    P.set_integrator("bezier")
+    _, _, dirs, _ = O.ordinates(P.nmu, P.nphi)
+    X, Y, Z = _node_xyz(grid, box)
+    zp = np.where(dirs[None, :, 2] > 0, Z[:, None], box[2] - Z[:, None])
+    exact = 1.4 * np.exp(-alpha * zp / np.abs(dirs[None, :, 2]))
+    P.set_bc(2, exact[:, None, :])
+    Nc = X.size
+    out = P.sweep(np.zeros((Nc, 1, P.N)), np.zeros((Nc, 1, P.N)), np.full((Nc, 1, P.N), alpha))
+    zd = _z_dominant(dirs)
+    assert np.allclose(out[:, 0, zd], exact[:, zd], rtol=1e-13, atol=0)
+    rng = np.random.default_rng(4)
+    grid = (5, 6, 4)
+    for kappa in [0.0, 7.0]:
+        P = _box(grid, L=3, G=2, box=(1.0, 1.3, 0.8))
+        P.set_integrator("bezier")
+        P.set_kappa(kappa)
+        P.set_bc(1, np.array([2.0, 0.5]))
+        B = np.array([2.0, 0.5])[None, :, None]
+        chi = rng.uniform(0.01, 50.0, size=(120, 2, P.N))
+        out = P.sweep(np.broadcast_to(B, (120, 2, P.N)), chi * B, chi)
+        assert np.allclose(out, np.broadcast_to(B, out.shape), rtol=1e-14)
+
+
+def test_bezier_third_order_for_smooth_source():
+    """S = A e^(beta chi z) along z with the exact solution on the inflow
+    faces: at the centre column (away from the faces, whose nodes have
+    one-sided derivatives) the error falls eightfold per halving of the node
+    spacing (third order) where the linear scheme's falls fourfold."""
+    def errs(integ, chi_v):
+        out_e = []
+        for nz in (17, 33, 65):
+            grid, box = (9, 9, nz), (1.0, 1.0, 1.0)
+            P = _box(grid, L=3, G=1, alpha=chi_v, box=box)
+            P.set_integrator(integ)
+            _, _, dirs, _ = O.ordinates(P.nmu, P.nphi)
+            X, Y, Z = _node_xyz(grid, box)
+            beta, A, I0 = 1.5, 0.8, 0.3
+            mu = dirs[:, 2]
+            zd = _z_dominant(dirs) & (mu > 0)
+            tau = chi_v * Z[:, None] / np.where(mu > 0, mu, 1.0)[None, :]
+            S = A * np.exp(beta * chi_v * Z)
+            Nc = Z.size
+            eta = np.repeat((chi_v * S)[:, None, None], P.N, axis=2)
+            chi = np.full((Nc, 1, P.N), chi_v)
+            b = beta * mu[None, :]
+            exact = I0 * np.exp(-tau) + A * (np.exp(b * tau) - np.exp(-tau)) / (b + 1)
+            P.set_bc(2, exact[:, None, :])
+            out = P.sweep(np.zeros_like(eta), eta, chi)
+            centre = (np.abs(X - 0.5) < 1e-9) & (np.abs(Y - 0.5) < 1e-9)
+            out_e.append(np.max(np.abs(out[centre][:, 0, zd] - exact[centre][:, zd]) / np.abs(exact[centre][:, zd])))
+        return out_e
+    for chi_v in (1.0, 4.0):
+        eb, el = errs("bezier", chi_v), errs("linear", chi_v)
+        assert eb[-2] / eb[-1] > 6.0 and 3.5 < el[-2] / el[-1] < 4.5
+        assert eb[-1] < 0.2 * el[-1]
+
+
+def test_bezier_no_overshoot_at_a_step():
+    """A source jumping from 0 to 1 in an optically thick medium: the clamped
+    control points keep the curve within its end values, so the intensity
+    stays within [0, 1] (vacuum inflow) for every ordinate."""
+    grid = (6, 6, 16)
+    chi_v = 40.0
+    P = _box(grid, L=3, G=1, alpha=chi_v)
+    P.set_integrator("bezier")
+    X, Y, Z = _node_xyz(grid, (1.0, 1.0, 1.0))
+    S = np.where(Z > 0.45, 1.0, 0.0)
+    Nc = Z.size
+    eta = np.repeat((chi_v * S)[:, None, None], P.N, axis=2)
+    chi = np.full((Nc, 1, P.N), chi_v)
+    out = P.sweep(np.zeros_like(eta), eta, chi)
+    assert out.min() >= 0.0 and out.max() <= 1.0 + 1e-14
