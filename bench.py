@@ -421,9 +421,10 @@ def _do_bytes(spec, esize=4):
 
 
 def _fit_groups(make, G_full, free_bytes, frac=0.9, esize=4):
-    """The largest group count (G_full, then 3/4, 1/2, 3/8, 1/4 of it) whose
+    """The largest group count (G_full, then 3/4, 1/2, 3/8, 1/4, 3/16, 1/8 of it) whose
     problem fits in frac of the free device memory; returns (spec, G)."""
-    for G in [G_full, (3 * G_full) // 4, G_full // 2, (3 * G_full) // 8, G_full // 4]:
+    for G in [G_full, (3 * G_full) // 4, G_full // 2, (3 * G_full) // 8, G_full // 4, (3 * G_full) // 16,
+              G_full // 8]:
         spec = make(G)
         if _do_bytes(spec, esize) <= frac * free_bytes:
             return spec, G

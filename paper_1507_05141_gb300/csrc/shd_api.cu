@@ -171,7 +171,7 @@ void free_all(shd_ctx *c)
                      &c->d_tcs_Bl[1], &c->d_tcs_Yh[0], &c->d_tcs_Yh[1], &c->d_tcs_Yl[0], &c->d_tcs_Yl[1],
                      (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_fcheck,
                      &c->d_ng[0], &c->d_ng[1], &c->d_ng[2], (void **)&c->d_ngpart, &c->d_rk[0], &c->d_rk[1],
-                     &c->d_rk[2], (void **)&c->d_sums_save};
+                     &c->d_rk[2], (void **)&c->d_sums_save, &c->d_tcK};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
     c->rtab_n = 0;
@@ -212,7 +212,7 @@ void drop_sized(shd_ctx *c)
                      &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag,
                      (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
                      &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_ng[0], &c->d_ng[1], &c->d_ng[2],
-                     &c->d_rk[0], &c->d_rk[1], &c->d_rk[2]};
+                     &c->d_rk[0], &c->d_rk[1], &c->d_rk[2], &c->d_tcK};
     for (void **p : ptrs) dfree(*p);
     c->ntiles = 0;
     c->nmoving = 0;
@@ -1338,6 +1338,12 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
             if (r / G != r % G && hK[i] != 0.0) c->k_diagonal = false;
         }
     c->have_scat = true;
+    // the tensor-core source's BF16 operands of a group-mixing kernel
+    dfree(c->d_tcK);
+    if (c->precision == SHD_MIXED && !c->k_diagonal) {
+        if ((rc = dalloc(c, &c->d_tcK, source_tc_operand_bytes(c), "source operands"))) return rc;
+        CK(launch_source_tc_operands(c, c->stream), "source operands");
+    }
     if (c->have_fields) {
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
         else CK(launch_chi0<float>(c, c->stream), "chi0");

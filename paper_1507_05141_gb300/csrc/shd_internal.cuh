@@ -187,6 +187,9 @@ struct shd_ctx {
     void *d_tc_Yh = nullptr, *d_tc_Yl = nullptr;  // [tc_Np][tc_Kq] harmonics
     int tc_Kp = 0, tc_Np = 0, tc_Kq = 0;
     int *d_tc_err = nullptr;                      // set by a kernel whose wait timed out
+    // BF16 hi / lo of the scattering kernel K_l for the tensor-core source
+    // (MIXED with a kernel that mixes groups): [2][L+1][Gp][Kp]
+    void *d_tcK = nullptr;
     // segment tiling of the mixed path: group 0 = z- and y-class ordinates
     // over bw x (128/bw) boxes of (x, y) at one z; group 1 = x-class over
     // boxes of (y, z) at one x.  Segments {plane, a0, b0, 0}; the group's
@@ -747,6 +750,14 @@ cudaError_t launch_rk_stage(T *I, const T *A, T *B, T *acc, long long n, double 
 // one thread waits on an mbarrier nothing arrives on, `polls` times at most,
 // then raises *flag (the bounded-wait failure path of the tensor-core kernels)
 cudaError_t launch_wait_selftest(long long polls, int *flag, cudaStream_t st);
+
+// a2 on the tensor cores for group-mixing kernels (MIXED): usable, its
+// operands (built from d_K into d_tcK), and the source + partial sums pass
+bool source_tc_usable(const shd_ctx *ctx);
+size_t source_tc_operand_bytes(const shd_ctx *ctx);
+cudaError_t launch_source_tc_operands(shd_ctx *ctx, cudaStream_t st);
+cudaError_t launch_source_sums_tc(shd_ctx *ctx, const float *Ip, float *Sp, const float *mom, const float *Sprev,
+                                  bool have_prev, cudaStream_t st);
 
 size_t remap_smem_bytes(const shd_ctx *ctx);
 template <class T>

@@ -1696,6 +1696,17 @@ template <class T>
 cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, const T *Sprev, bool have_prev,
                                cudaStream_t st)
 {
+    if constexpr (sizeof(T) == 4) {
+        // group-mixing kernels in the mixed precision: on the tensor cores
+        if (source_tc_usable(ctx)) {
+            cudaError_t e = launch_source_sums_tc(ctx, (const float *)Ip, (float *)Sp, (const float *)mom,
+                                                  (const float *)Sprev, have_prev, st);
+            if (e != cudaSuccess) return e;
+            k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, ctx->n_partial, have_prev ? 1 : 0, ctx->d_sums);
+            note_launch();
+            return cudaGetLastError();
+        }
+    }
     Prob<T> P = make_prob<T>(ctx);
     const size_t sm = source_sums_smem(ctx);
     auto kern = ctx->k_diagonal && ctx->G <= 32 ? k_source_sums<T, true> : k_source_sums<T, false>;

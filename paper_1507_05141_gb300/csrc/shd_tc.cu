@@ -531,6 +531,220 @@ done:
 }
 
 // -------------------------------------------------------------------------
+// a2 on tensor cores for kernels that mix groups (Klein-Nishina, Sec. 2.3
+// eq:comptoncross): S_lm(c, g) = n_e/chi0 sum_g' K_l[g][g'] I_lm(c, g') + T.
+// For each l the 2l+1 harmonics of a tile of TN nodes form the rows of one
+// MMA, D_l[(node, m), g] = sum_g' I(node, g', l, m) K_l[g][g']: M = 128 rows
+// (TN (2l+1) <= 128 used), K = G' padded to Kp, N = G padded to Gp.  FP32
+// operands split into BF16 hi + lo, three products accumulate in FP32 in
+// tensor memory.  The tile's I_lm block [TN][G][NLM] is staged in shared
+// memory in one coalesced pass; each l's A is built from it and its results
+// overwrite that l's entries; then the block is finished exactly as
+// k_source_sums finishes a node (scale n_e/chi0, emission in p = 0, zero
+// where chi0 = 0) and written, with the step's FP64 partial sums.  One
+// thread issues the MMAs; the wait for their completion is bounded (on
+// timeout: *err raised, the MMA drained, tensor memory freed).
+// -------------------------------------------------------------------------
+template <int TN>
+__global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float *__restrict__ Ip,
+                                                      float *__restrict__ Sp, const float *__restrict__ mom,
+                                                      const float *__restrict__ Sprev, int have_prev,
+                                                      const uint16_t *__restrict__ gKh,
+                                                      const uint16_t *__restrict__ gKl, int Gp, int Kp,
+                                                      uint32_t tcols, double *partial, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int L = P.L, G = P.G, NLM = P.NLM;
+    const size_t kblk = (size_t)Gp * Kp;  // elements of one l's operand
+    uint16_t *Kh = reinterpret_cast<uint16_t *>(smem_raw);
+    uint16_t *Kl = Kh + (size_t)(L + 1) * kblk;
+    uint16_t *Ah = Kl + (size_t)(L + 1) * kblk;
+    uint16_t *Al = Ah + (size_t)128 * Kp;
+    float *blk = reinterpret_cast<float *>(Al + (size_t)128 * Kp);  // [TN][G][NLM]
+    float *rat = blk + (size_t)TN * G * NLM;                          // [TN][G] n_e/chi0 (0 where chi0 = 0)
+    float *emt = rat + (size_t)TN * G;                                // [TN][G] sqrt(4 pi) eta0/chi0
+    const size_t tail = ((size_t)(reinterpret_cast<unsigned char *>(emt + (size_t)TN * G) - smem_raw) + 7) & ~(size_t)7;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + tail);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    __shared__ double red[4][8];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        const uint4 *sh = reinterpret_cast<const uint4 *>(gKh), *sl = reinterpret_cast<const uint4 *>(gKl);
+        uint4 *dh = reinterpret_cast<uint4 *>(Kh), *dl = reinterpret_cast<uint4 *>(Kl);
+        const int n16 = (int)((L + 1) * kblk / 8);
+        for (int i = tid; i < n16; i += 256) {
+            dh[i] = sh[i];
+            dl[i] = sl[i];
+        }
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, tcols);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t sbo = (Kp / 8) * 128;
+    const uint32_t idesc = tc::idesc_bf16(128, Gp);
+    uint32_t phase = 0;
+    bool pending = false;
+    double e_sum = 0, ph_sum = 0, num = 0, den = 0;
+    const long long ntiles = (P.Nc + TN - 1) / TN;
+
+    for (long long w = blockIdx.x; w < ntiles; w += gridDim.x) {
+        const long long c0 = w * TN;
+        const int nn = (int)(P.Nc - c0 < TN ? P.Nc - c0 : TN);
+        const long long gbase = c0 * G * NLM;
+        const int nblk = nn * G * NLM;
+        for (int i = tid; i < nblk; i += 256) blk[i] = Ip[gbase + i];
+        for (int i = tid; i < nn * G; i += 256) {
+            const long long c = c0 + i / G;
+            const float chi = P.chi0[c * G + (i % G)];
+            rat[i] = chi > 0.f ? P.ne[c] / chi : 0.f;
+            emt[i] = chi > 0.f ? 3.5449077018110320546f * P.emis0[c * G + (i % G)] / chi : 0.f;  // sqrt(4 pi)
+        }
+        __syncthreads();
+        for (int l = 0; l <= L; ++l) {
+            const int nm = 2 * l + 1, rows = nn * nm, p0 = l * l;
+            // A_l: row r = (node r / nm, p = l^2 + r % nm), column g'; a warp's
+            // threads take consecutive rows (consecutive p: no bank conflicts on
+            // the block)
+            for (int e = tid; e < 128 * (Kp / 2); e += 256) {
+                const int r = e & 127, kk = 2 * (e >> 7);
+                float v0 = 0.f, v1 = 0.f;
+                if (r < rows) {
+                    const int node = r / nm, p = p0 + (r - node * nm);
+                    const float *b = blk + (size_t)node * G * NLM + p;
+                    if (kk < G) v0 = b[(size_t)kk * NLM];
+                    if (kk + 1 < G) v1 = b[(size_t)(kk + 1) * NLM];
+                }
+                uint32_t hi, lo;
+                split_bf16x2(v0, v1, hi, lo);
+                const int o = tc::canon_off(r, kk, Kp);
+                *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
+                *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
+            }
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al);
+                const uint32_t bh = tc::smem_u32(Kh + (size_t)l * kblk), bl = tc::smem_u32(Kl + (size_t)l * kblk);
+                for (int j = 0; j < Kp / 16; ++j) {
+                    const uint32_t koff = j * 256;
+                    const uint64_t dah = tc::sdesc(ah + koff, 128, sbo), dal = tc::sdesc(al + koff, 128, sbo);
+                    const uint64_t dbh = tc::sdesc(bh + koff, 128, sbo), dbl = tc::sdesc(bl + koff, 128, sbo);
+                    tc::mma_bf16(tmem, dah, dbh, idesc, j > 0 ? 1u : 0u);
+                    tc::mma_bf16(tmem, dah, dbl, idesc, 1u);
+                    tc::mma_bf16(tmem, dal, dbh, idesc, 1u);
+                }
+                tc::mma_commit(bar);
+            }
+            pending = true;
+            if (!cta_wait(bar, phase, abort_flag)) goto drain;
+            phase ^= 1;
+            pending = false;
+            tc::fence_after_sync();
+            {
+                // warps w and w+4 share tensor-memory lanes 32 (w % 4) ..; they split the columns
+                const int quad = warp & 3, half = warp >> 2;
+                const int r = quad * 32 + lane;
+                const bool valid = r < rows;
+                const int node = valid ? r / nm : 0, p = p0 + (valid ? r - node * nm : 0);
+                float *b = blk + (size_t)node * G * NLM + p;
+                const int cb = half * (Gp / 2), ce = half ? Gp : Gp / 2;
+                for (int cc = cb; cc < ce; cc += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cc, v);
+                    if (!valid) continue;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (cc + j < G) b[(size_t)(cc + j) * NLM] = v[j];
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+        }
+        // finish: S = n_e/chi0 D + emission (p = 0), the FP64 partial sums
+        for (int i = tid; i < nblk; i += 256) {
+            const int ng = i / NLM, p = i - ng * NLM;
+            // rat and emt are zero where chi0 = 0 (S = 0 there)
+            float sv = rat[ng] * blk[i];
+            if (p == 0) sv += emt[ng];
+            Sp[gbase + i] = sv;
+            const double sn = (double)sv;
+            den += sn * sn;
+            if (have_prev) {
+                const double d = sn - (double)Sprev[gbase + i];
+                num += d * d;
+            }
+        }
+        for (int i = tid; i < nn * G; i += 256) {
+            const int g = i % G;
+            const double J = (double)mom[(c0 * G + i) * 10];
+            const double de = P.edges[g + 1] - P.edges[g];
+            e_sum += 4.0 * kPi * J * de;
+            ph_sum += 4.0 * kPi * J * de / P.centre[g];
+        }
+        __syncthreads();
+    }
+    goto done;
+drain:
+    if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        if (pending) tc::mbar_wait(bar, phase, kWaitLimit);
+    }
+done:
+    // fixed-order reduction of the partial sums: lanes, then the 8 warps
+    for (int o = 16; o > 0; o >>= 1) {
+        e_sum += __shfl_down_sync(0xffffffffu, e_sum, o);
+        ph_sum += __shfl_down_sync(0xffffffffu, ph_sum, o);
+        num += __shfl_down_sync(0xffffffffu, num, o);
+        den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = e_sum;
+        red[1][warp] = ph_sum;
+        red[2][warp] = num;
+        red[3][warp] = den;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 4) {
+        double acc = 0;
+        for (int q = 0; q < 8; ++q) acc += red[tid][q];
+        partial[blockIdx.x * 4 + tid] = acc;
+    }
+    if (warp == 0) tc::tmem_dealloc(tmem, tcols);
+}
+
+// BF16 hi / lo of K_l[g][g'] (FP32 [L+1][G][G]) in the canonical K-major
+// layout of the source MMA: per l a [Gp][Kp] block, row g, column g', zero
+// padded.
+__global__ void k_source_tc_operands(const float *__restrict__ K, int L, int G, int Gp, int Kp, uint16_t *Kh,
+                                     uint16_t *Kl)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = (long long)(L + 1) * Gp * Kp;
+    if (i >= n) return;
+    const int l = (int)(i / ((long long)Gp * Kp));
+    const int rem = (int)(i - (long long)l * Gp * Kp);
+    const int g = rem / Kp, gp = rem - g * Kp;
+    const float v = (g < G && gp < G) ? K[((size_t)l * G + g) * G + gp] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(h));
+    const size_t o = (size_t)l * Gp * Kp + tc::canon_off(g, gp, Kp);
+    Kh[o] = __bfloat16_as_ushort(h);
+    Kl[o] = __bfloat16_as_ushort(lo);
+}
+
+// -------------------------------------------------------------------------
 // host side
 // -------------------------------------------------------------------------
 static constexpr int kProjKC = 32;
@@ -590,6 +804,81 @@ cudaError_t launch_sh2lab_tc(const shd_ctx *ctx, const float *Sp, float *eta, fl
     if (items < grid) grid = (int)items;
     k_sh2lab_tc<<<grid, 256, sm, st>>>(P, Sp, eta, chi, S0n, (const uint16_t *)ctx->d_tc_Yh,
                                       (const uint16_t *)ctx->d_tc_Yl, ctx->tc_Np, ctx->tc_Kq, ctx->d_tc_err);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- the tensor-core source (a2) ------------------------------------------
+
+static int round16(int x) { return (x + 15) / 16 * 16; }
+
+// Nodes per tile of k_source_tc: 8 where the rows of every l fit one MMA and
+// the shared memory allows, else 4, 2, 1; 0 when it cannot run.
+static int source_tc_tn(const shd_ctx *c, size_t *smem)
+{
+    const int Gp = round16(c->G), Kp = round16(c->G);
+    for (int tn : {8, 4, 2, 1}) {
+        if (tn * (2 * c->L + 1) > 128) continue;
+        const size_t sm = (size_t)2 * (c->L + 1) * Gp * Kp * 2 + (size_t)2 * 128 * Kp * 2 +
+                          (size_t)tn * c->G * c->NLM * 4 + (size_t)2 * tn * c->G * 4 + 8 + 8 + 64;
+        if (sm <= 200 * 1024) {
+            if (smem) *smem = sm;
+            return tn;
+        }
+    }
+    return 0;
+}
+
+bool source_tc_usable(const shd_ctx *c)
+{
+    return c->precision == SHD_MIXED && !c->k_diagonal && c->G <= 256 && c->d_tcK && source_tc_tn(c, nullptr) > 0;
+}
+
+cudaError_t launch_source_tc_operands(shd_ctx *c, cudaStream_t st)
+{
+    const int Gp = round16(c->G), Kp = round16(c->G);
+    const size_t n = (size_t)(c->L + 1) * Gp * Kp;
+    uint16_t *Kh = (uint16_t *)c->d_tcK, *Kl = Kh + n;
+    k_source_tc_operands<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float *)c->d_K, c->L, c->G, Gp, Kp, Kh,
+                                                                     Kl);
+    note_launch();
+    return cudaGetLastError();
+}
+
+size_t source_tc_operand_bytes(const shd_ctx *c)
+{
+    return (size_t)2 * (c->L + 1) * round16(c->G) * round16(c->G) * sizeof(uint16_t);
+}
+
+cudaError_t launch_source_sums_tc(shd_ctx *c, const float *Ip, float *Sp, const float *mom, const float *Sprev,
+                                  bool have_prev, cudaStream_t st)
+{
+    Prob<float> P = make_prob<float>(c);
+    size_t sm = 0;
+    const int tn = source_tc_tn(c, &sm);
+    const int Gp = round16(c->G), Kp = round16(c->G);
+    uint32_t cols = 32;
+    while ((int)cols < Gp) cols <<= 1;
+    const size_t n = (size_t)(c->L + 1) * Gp * Kp;
+    const uint16_t *Kh = (const uint16_t *)c->d_tcK, *Kl = Kh + n;
+    const int nb = c->n_partial;
+    cudaError_t e;
+#define SHD_SRC_TC(T)                                                                                         \
+    case T:                                                                                                   \
+        if ((e = cudaFuncSetAttribute(k_source_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=  \
+            cudaSuccess)                                                                                      \
+            return e;                                                                                         \
+        k_source_tc<T><<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, Kh, Kl, Gp, Kp, cols,     \
+                                            c->d_partial, c->d_tc_err);                                       \
+        break;
+    switch (tn) {
+        SHD_SRC_TC(8)
+        SHD_SRC_TC(4)
+        SHD_SRC_TC(2)
+        SHD_SRC_TC(1)
+        default: return cudaErrorInvalidConfiguration;
+    }
+#undef SHD_SRC_TC
     note_launch();
     return cudaGetLastError();
 }
