@@ -535,56 +535,82 @@ done:
 // eq:comptoncross): S_lm(c, g) = n_e/chi0 sum_g' K_l[g][g'] I_lm(c, g') + T.
 // For each l the 2l+1 harmonics of a tile of TN nodes form the rows of one
 // MMA, D_l[(node, m), g] = sum_g' I(node, g', l, m) K_l[g][g']: M = 128 rows
-// (TN (2l+1) <= 128 used), K = G' padded to Kp, N = G padded to Gp.  FP32
-// operands split into BF16 hi + lo, three products accumulate in FP32 in
-// tensor memory.  The tile's I_lm block [TN][G][NLM] is staged in shared
-// memory in one coalesced pass; each l's A is built from it and its results
-// overwrite that l's entries; then the block is finished exactly as
-// k_source_sums finishes a node (scale n_e/chi0, emission in p = 0, zero
-// where chi0 = 0) and written, with the step's FP64 partial sums.  One
-// thread issues the MMAs; the wait for their completion is bounded (on
-// timeout: *err raised, the MMA drained, tensor memory freed).
+// (TN (2l+1) <= 128 used), K = G' padded to Kp, N = G padded to Gp.
+// Precision: the sums over g' cancel for l >= 1 and the spectra span many
+// decades, so each FP32 operand is split into three BF16 pieces x = hi +
+// mid + lo (24 significant bits) and the six products of order <= 2 (hi.hi,
+// hi.mid, mid.hi, hi.lo, lo.hi, mid.mid) accumulate in FP32 in tensor
+// memory: the dropped terms are below 2^-24 of each product, as in FP32.
+// Flow per tile: the tile's I_lm block [TN][G][NLM] arrives by one bulk copy
+// (or plain loads when its size is not a multiple of 16 bytes); the l loop is
+// software-pipelined over two operand buffers and two accumulators (l+1's
+// operands are built while l's MMAs run); each l's results overwrite that
+// l's entries of the block; then the block is finished exactly as
+// k_source_sums finishes a node (n_e/chi0, emission in p = 0, zero where
+// chi0 = 0) and written, with the step's FP64 partial sums.  One thread
+// issues the MMAs and copies; every wait is bounded (on timeout: *err
+// raised, what was issued drained, tensor memory freed).
 // -------------------------------------------------------------------------
+__device__ inline void split3_bf16x2(float a, float b, uint32_t &hi, uint32_t &mid, uint32_t &lo)
+{
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    const float ra = a - __bfloat162float(ha), rb = b - __bfloat162float(hb);
+    const __nv_bfloat16 ma = __float2bfloat16_rn(ra), mb = __float2bfloat16_rn(rb);
+    const __nv_bfloat16 la = __float2bfloat16_rn(ra - __bfloat162float(ma));
+    const __nv_bfloat16 lb = __float2bfloat16_rn(rb - __bfloat162float(mb));
+    hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+    mid = (uint32_t)__bfloat16_as_ushort(ma) | ((uint32_t)__bfloat16_as_ushort(mb) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+}
+
+// bulk copy global -> shared (16-byte aligned ends, size a multiple of 16),
+// completion counted in bytes on `bar`
+__device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+                 : "memory");
+}
+
 template <int TN>
 __global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float *__restrict__ Ip,
                                                       float *__restrict__ Sp, const float *__restrict__ mom,
                                                       const float *__restrict__ Sprev, int have_prev,
-                                                      const uint16_t *__restrict__ gKh,
-                                                      const uint16_t *__restrict__ gKl, int Gp, int Kp,
-                                                      uint32_t tcols, double *partial, int *err)
+                                                      const uint16_t *__restrict__ gK, int Gp, int Kp,
+                                                      uint32_t acc_cols, double *partial, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int L = P.L, G = P.G, NLM = P.NLM;
-    const size_t kblk = (size_t)Gp * Kp;  // elements of one l's operand
-    uint16_t *Kh = reinterpret_cast<uint16_t *>(smem_raw);
-    uint16_t *Kl = Kh + (size_t)(L + 1) * kblk;
-    uint16_t *Ah = Kl + (size_t)(L + 1) * kblk;
-    uint16_t *Al = Ah + (size_t)128 * Kp;
-    float *blk = reinterpret_cast<float *>(Al + (size_t)128 * Kp);  // [TN][G][NLM]
-    float *rat = blk + (size_t)TN * G * NLM;                          // [TN][G] n_e/chi0 (0 where chi0 = 0)
-    float *emt = rat + (size_t)TN * G;                                // [TN][G] sqrt(4 pi) eta0/chi0
+    const size_t kblk = (size_t)Gp * Kp;       // elements of one l's operand piece
+    const size_t kall = (size_t)(L + 1) * kblk;  // one piece of every l
+    const size_t ablk = (size_t)128 * Kp;
+    uint16_t *Kop = reinterpret_cast<uint16_t *>(smem_raw);  // [3 pieces][L+1][Gp][Kp]
+    uint16_t *Aop = Kop + 3 * kall;                          // [2 buffers][3 pieces][128][Kp]
+    float *blk = reinterpret_cast<float *>(Aop + 6 * ablk);  // [TN][G][NLM]
+    float *rat = blk + (size_t)TN * G * NLM;                 // [TN][G] n_e/chi0 (0 where chi0 = 0)
+    float *emt = rat + (size_t)TN * G;                       // [TN][G] sqrt(4 pi) eta0/chi0 (0 there too)
     const size_t tail = ((size_t)(reinterpret_cast<unsigned char *>(emt + (size_t)TN * G) - smem_raw) + 7) & ~(size_t)7;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + tail);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + tail);  // [2] MMA completion, [2] block copy
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 3);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
     __shared__ double red[4][8];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {
-        const uint4 *sh = reinterpret_cast<const uint4 *>(gKh), *sl = reinterpret_cast<const uint4 *>(gKl);
-        uint4 *dh = reinterpret_cast<uint4 *>(Kh), *dl = reinterpret_cast<uint4 *>(Kl);
-        const int n16 = (int)((L + 1) * kblk / 8);
-        for (int i = tid; i < n16; i += 256) {
-            dh[i] = sh[i];
-            dl[i] = sl[i];
-        }
+        const uint4 *src = reinterpret_cast<const uint4 *>(gK);
+        uint4 *dst = reinterpret_cast<uint4 *>(Kop);
+        const int n16 = (int)(3 * kall / 8);
+        for (int i = tid; i < n16; i += 256) dst[i] = src[i];
     }
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::mbar_init(&bar[2], 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 0) tc::tmem_alloc(tslot, tcols);
+    if (warp == 0) tc::tmem_alloc(tslot, 2 * acc_cols);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -592,97 +618,160 @@ __global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float
     const uint32_t tmem = *tslot;
     const uint32_t sbo = (Kp / 8) * 128;
     const uint32_t idesc = tc::idesc_bf16(128, Gp);
-    uint32_t phase = 0;
-    bool pending = false;
+    uint32_t mphase[2] = {0, 0}, cphase = 0;
+    bool mpend[2] = {false, false}, cpend = false;
     double e_sum = 0, ph_sum = 0, num = 0, den = 0;
     const long long ntiles = (P.Nc + TN - 1) / TN;
+    const bool bulk = ((size_t)G * NLM * 4) % 16 == 0;
+
+    // operands of l into buffer b: row r = (node r / (2l+1), p = l^2 + r % (2l+1)),
+    // column g'; a warp's threads take consecutive rows (consecutive p)
+    auto build = [&](int l, int nn, int b) {
+        const int nm = 2 * l + 1, rows = nn * nm, p0 = l * l;
+        uint16_t *Ah = Aop + (size_t)(3 * b) * ablk, *Am = Ah + ablk, *Al = Am + ablk;
+        for (int e = tid; e < 128 * (Kp / 2); e += 256) {
+            const int r = e & 127, kk = 2 * (e >> 7);
+            float v0 = 0.f, v1 = 0.f;
+            if (r < rows) {
+                const int node = r / nm, p = p0 + (r - node * nm);
+                const float *bp = blk + (size_t)node * G * NLM + p;
+                if (kk < G) v0 = bp[(size_t)kk * NLM];
+                if (kk + 1 < G) v1 = bp[(size_t)(kk + 1) * NLM];
+            }
+            uint32_t hi, mid, lo;
+            split3_bf16x2(v0, v1, hi, mid, lo);
+            const int o = tc::canon_off(r, kk, Kp);
+            *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
+            *reinterpret_cast<uint32_t *>(&Am[o]) = mid;
+            *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
+        }
+    };
+    // the six products of l's operands (buffer b) with K_l into accumulator b
+    auto issue = [&](int l, int b) {
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_u32(Aop + (size_t)(3 * b) * ablk);
+        const uint32_t ap[3] = {a0, a0 + (uint32_t)(ablk * 2), a0 + (uint32_t)(ablk * 4)};
+        const uint32_t k0 = tc::smem_u32(Kop + (size_t)l * kblk);
+        const uint32_t kp[3] = {k0, k0 + (uint32_t)(kall * 2), k0 + (uint32_t)(kall * 4)};
+        const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+        const uint32_t d = tmem + (uint32_t)b * acc_cols;
+        for (int j = 0; j < Kp / 16; ++j) {
+            const uint32_t koff = j * 256;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const uint64_t da = tc::sdesc(ap[pa[q]] + koff, 128, sbo), db = tc::sdesc(kp[pb[q]] + koff, 128, sbo);
+                tc::mma_bf16(d, da, db, idesc, (j > 0 || q > 0) ? 1u : 0u);
+            }
+        }
+        tc::mma_commit(&bar[b]);
+    };
+    // accumulator b of l back into l's entries of the block
+    auto epilogue = [&](int l, int nn, int b) {
+        const int nm = 2 * l + 1, rows = nn * nm, p0 = l * l;
+        // warps w and w+4 share tensor-memory lanes 32 (w % 4) ..; they split the columns
+        const int quad = warp & 3, half = warp >> 2;
+        const int r = quad * 32 + lane;
+        const bool valid = r < rows;
+        const int node = valid ? r / nm : 0, p = p0 + (valid ? r - node * nm : 0);
+        float *bp = blk + (size_t)node * G * NLM + p;
+        const int cb = half * (Gp / 2), ce = half ? Gp : Gp / 2;
+        for (int cc = cb; cc < ce; cc += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * acc_cols + (uint32_t)cc, v);
+            if (!valid) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (cc + j < G) bp[(size_t)(cc + j) * NLM] = v[j];
+        }
+    };
 
     for (long long w = blockIdx.x; w < ntiles; w += gridDim.x) {
         const long long c0 = w * TN;
         const int nn = (int)(P.Nc - c0 < TN ? P.Nc - c0 : TN);
         const long long gbase = c0 * G * NLM;
         const int nblk = nn * G * NLM;
-        for (int i = tid; i < nblk; i += 256) blk[i] = Ip[gbase + i];
+        // the block: one bulk copy (the previous tile's generic accesses are
+        // ordered before it by the proxy fence and the barrier at its end)
+        if (bulk) {
+            if (tid == 0) {
+                tc::mbar_arrive_expect_tx(&bar[2], (uint32_t)nblk * 4u);
+                bulk_g2s(blk, Ip + gbase, (uint32_t)nblk * 4u, &bar[2]);
+            }
+            cpend = true;
+        } else {
+            for (int i = tid; i < nblk; i += 256) blk[i] = Ip[gbase + i];
+        }
         for (int i = tid; i < nn * G; i += 256) {
             const long long c = c0 + i / G;
             const float chi = P.chi0[c * G + (i % G)];
             rat[i] = chi > 0.f ? P.ne[c] / chi : 0.f;
             emt[i] = chi > 0.f ? 3.5449077018110320546f * P.emis0[c * G + (i % G)] / chi : 0.f;  // sqrt(4 pi)
         }
-        __syncthreads();
-        for (int l = 0; l <= L; ++l) {
-            const int nm = 2 * l + 1, rows = nn * nm, p0 = l * l;
-            // A_l: row r = (node r / nm, p = l^2 + r % nm), column g'; a warp's
-            // threads take consecutive rows (consecutive p: no bank conflicts on
-            // the block)
-            for (int e = tid; e < 128 * (Kp / 2); e += 256) {
-                const int r = e & 127, kk = 2 * (e >> 7);
-                float v0 = 0.f, v1 = 0.f;
-                if (r < rows) {
-                    const int node = r / nm, p = p0 + (r - node * nm);
-                    const float *b = blk + (size_t)node * G * NLM + p;
-                    if (kk < G) v0 = b[(size_t)kk * NLM];
-                    if (kk + 1 < G) v1 = b[(size_t)(kk + 1) * NLM];
-                }
-                uint32_t hi, lo;
-                split_bf16x2(v0, v1, hi, lo);
-                const int o = tc::canon_off(r, kk, Kp);
-                *reinterpret_cast<uint32_t *>(&Ah[o]) = hi;
-                *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
-            }
-            tc::fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after_sync();
-                const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al);
-                const uint32_t bh = tc::smem_u32(Kh + (size_t)l * kblk), bl = tc::smem_u32(Kl + (size_t)l * kblk);
-                for (int j = 0; j < Kp / 16; ++j) {
-                    const uint32_t koff = j * 256;
-                    const uint64_t dah = tc::sdesc(ah + koff, 128, sbo), dal = tc::sdesc(al + koff, 128, sbo);
-                    const uint64_t dbh = tc::sdesc(bh + koff, 128, sbo), dbl = tc::sdesc(bl + koff, 128, sbo);
-                    tc::mma_bf16(tmem, dah, dbh, idesc, j > 0 ? 1u : 0u);
-                    tc::mma_bf16(tmem, dah, dbl, idesc, 1u);
-                    tc::mma_bf16(tmem, dal, dbh, idesc, 1u);
-                }
-                tc::mma_commit(bar);
-            }
-            pending = true;
-            if (!cta_wait(bar, phase, abort_flag)) goto drain;
-            phase ^= 1;
-            pending = false;
-            tc::fence_after_sync();
-            {
-                // warps w and w+4 share tensor-memory lanes 32 (w % 4) ..; they split the columns
-                const int quad = warp & 3, half = warp >> 2;
-                const int r = quad * 32 + lane;
-                const bool valid = r < rows;
-                const int node = valid ? r / nm : 0, p = p0 + (valid ? r - node * nm : 0);
-                float *b = blk + (size_t)node * G * NLM + p;
-                const int cb = half * (Gp / 2), ce = half ? Gp : Gp / 2;
-                for (int cc = cb; cc < ce; cc += 16) {
-                    float v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cc, v);
-                    if (!valid) continue;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (cc + j < G) b[(size_t)(cc + j) * NLM] = v[j];
-                }
-            }
-            tc::fence_before_sync();
+        if (bulk) {
+            if (!cta_wait(&bar[2], cphase, abort_flag)) goto drain;
+            cphase ^= 1;
+            cpend = false;
+        } else {
             __syncthreads();
         }
+        build(0, nn, 0);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) issue(0, 0);
+        mpend[0] = true;
+        for (int l = 0; l <= L; ++l) {
+            const int b = l & 1;
+            if (l + 1 <= L) build(l + 1, nn, b ^ 1);  // accumulator b ^ 1 was drained at l - 1
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (l + 1 <= L) {
+                if (tid == 0) issue(l + 1, b ^ 1);
+                mpend[b ^ 1] = true;
+            }
+            if (!cta_wait(&bar[b], mphase[b], abort_flag)) goto drain;
+            mphase[b] ^= 1;
+            mpend[b] = false;
+            tc::fence_after_sync();
+            epilogue(l, nn, b);
+            tc::fence_before_sync();
+        }
+        __syncthreads();
         // finish: S = n_e/chi0 D + emission (p = 0), the FP64 partial sums
-        for (int i = tid; i < nblk; i += 256) {
-            const int ng = i / NLM, p = i - ng * NLM;
-            // rat and emt are zero where chi0 = 0 (S = 0 there)
-            float sv = rat[ng] * blk[i];
-            if (p == 0) sv += emt[ng];
-            Sp[gbase + i] = sv;
-            const double sn = (double)sv;
-            den += sn * sn;
-            if (have_prev) {
-                const double d = sn - (double)Sprev[gbase + i];
-                num += d * d;
+        if ((NLM & 3) == 0) {
+            const float4 *b4 = reinterpret_cast<const float4 *>(blk);
+            float4 *s4 = reinterpret_cast<float4 *>(Sp + gbase);
+            const float4 *q4 = reinterpret_cast<const float4 *>(Sprev + gbase);
+            const int n4 = nblk / 4;
+#pragma unroll 4
+            for (int i = tid; i < n4; i += 256) {
+                const int ng = (4 * i) / NLM, p = 4 * i - ng * NLM;
+                const float r_ = rat[ng];
+                float4 v = b4[i];
+                v.x = r_ * v.x + (p == 0 ? emt[ng] : 0.f);
+                v.y *= r_;
+                v.z *= r_;
+                v.w *= r_;
+                s4[i] = v;
+                den += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+                if (have_prev) {
+                    const float4 q = q4[i];
+                    const double d0 = (double)v.x - q.x, d1 = (double)v.y - q.y, d2 = (double)v.z - q.z,
+                                 d3 = (double)v.w - q.w;
+                    num += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+                }
+            }
+        } else {
+            for (int i = tid; i < nblk; i += 256) {
+                const int ng = i / NLM, p = i - ng * NLM;
+                float sv = rat[ng] * blk[i];
+                if (p == 0) sv += emt[ng];
+                Sp[gbase + i] = sv;
+                den += (double)sv * sv;
+                if (have_prev) {
+                    const double d = (double)sv - (double)Sprev[gbase + i];
+                    num += d * d;
+                }
             }
         }
         for (int i = tid; i < nn * G; i += 256) {
@@ -692,13 +781,16 @@ __global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float
             e_sum += 4.0 * kPi * J * de;
             ph_sum += 4.0 * kPi * J * de / P.centre[g];
         }
+        tc::fence_proxy_async();  // generic accesses to the block before the next bulk copy
         __syncthreads();
     }
     goto done;
 drain:
     if (threadIdx.x == 0) {
         atomicExch(err, 1);
-        if (pending) tc::mbar_wait(bar, phase, kWaitLimit);
+        for (int b = 0; b < 2; ++b)
+            if (mpend[b]) tc::mbar_wait(&bar[b], mphase[b], kWaitLimit);
+        if (cpend) tc::mbar_wait(&bar[2], cphase, kWaitLimit);
     }
 done:
     // fixed-order reduction of the partial sums: lanes, then the 8 warps
@@ -721,27 +813,29 @@ done:
         for (int q = 0; q < 8; ++q) acc += red[tid][q];
         partial[blockIdx.x * 4 + tid] = acc;
     }
-    if (warp == 0) tc::tmem_dealloc(tmem, tcols);
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * acc_cols);
 }
 
-// BF16 hi / lo of K_l[g][g'] (FP32 [L+1][G][G]) in the canonical K-major
-// layout of the source MMA: per l a [Gp][Kp] block, row g, column g', zero
-// padded.
-__global__ void k_source_tc_operands(const float *__restrict__ K, int L, int G, int Gp, int Kp, uint16_t *Kh,
-                                     uint16_t *Kl)
+// Three BF16 pieces hi, mid, lo of K_l[g][g'] (FP32 [L+1][G][G]) in the
+// canonical K-major layout of the source MMA: [piece][l][Gp][Kp], row g,
+// column g', zero padded.
+__global__ void k_source_tc_operands(const float *__restrict__ K, int L, int G, int Gp, int Kp, uint16_t *out)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long n = (long long)(L + 1) * Gp * Kp;
-    if (i >= n) return;
+    const long long all = (long long)(L + 1) * Gp * Kp;
+    if (i >= all) return;
     const int l = (int)(i / ((long long)Gp * Kp));
     const int rem = (int)(i - (long long)l * Gp * Kp);
     const int g = rem / Kp, gp = rem - g * Kp;
     const float v = (g < G && gp < G) ? K[((size_t)l * G + g) * G + gp] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(h));
+    const float r = v - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r - __bfloat162float(m));
     const size_t o = (size_t)l * Gp * Kp + tc::canon_off(g, gp, Kp);
-    Kh[o] = __bfloat16_as_ushort(h);
-    Kl[o] = __bfloat16_as_ushort(lo);
+    out[o] = __bfloat16_as_ushort(h);
+    out[all + o] = __bfloat16_as_ushort(m);
+    out[2 * all + o] = __bfloat16_as_ushort(lo);
 }
 
 // -------------------------------------------------------------------------
@@ -819,9 +913,9 @@ static int source_tc_tn(const shd_ctx *c, size_t *smem)
     const int Gp = round16(c->G), Kp = round16(c->G);
     for (int tn : {8, 4, 2, 1}) {
         if (tn * (2 * c->L + 1) > 128) continue;
-        const size_t sm = (size_t)2 * (c->L + 1) * Gp * Kp * 2 + (size_t)2 * 128 * Kp * 2 +
-                          (size_t)tn * c->G * c->NLM * 4 + (size_t)2 * tn * c->G * 4 + 8 + 8 + 64;
-        if (sm <= 200 * 1024) {
+        const size_t sm = (size_t)3 * (c->L + 1) * Gp * Kp * 2 + (size_t)6 * 128 * Kp * 2 +
+                          (size_t)tn * c->G * c->NLM * 4 + (size_t)2 * tn * c->G * 4 + 8 + 3 * 8 + 16;
+        if (sm <= 220 * 1024) {
             if (smem) *smem = sm;
             return tn;
         }
@@ -838,16 +932,15 @@ cudaError_t launch_source_tc_operands(shd_ctx *c, cudaStream_t st)
 {
     const int Gp = round16(c->G), Kp = round16(c->G);
     const size_t n = (size_t)(c->L + 1) * Gp * Kp;
-    uint16_t *Kh = (uint16_t *)c->d_tcK, *Kl = Kh + n;
-    k_source_tc_operands<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float *)c->d_K, c->L, c->G, Gp, Kp, Kh,
-                                                                     Kl);
+    k_source_tc_operands<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float *)c->d_K, c->L, c->G, Gp, Kp,
+                                                                     (uint16_t *)c->d_tcK);
     note_launch();
     return cudaGetLastError();
 }
 
 size_t source_tc_operand_bytes(const shd_ctx *c)
 {
-    return (size_t)2 * (c->L + 1) * round16(c->G) * round16(c->G) * sizeof(uint16_t);
+    return (size_t)3 * (c->L + 1) * round16(c->G) * round16(c->G) * sizeof(uint16_t);
 }
 
 cudaError_t launch_source_sums_tc(shd_ctx *c, const float *Ip, float *Sp, const float *mom, const float *Sprev,
@@ -859,8 +952,7 @@ cudaError_t launch_source_sums_tc(shd_ctx *c, const float *Ip, float *Sp, const 
     const int Gp = round16(c->G), Kp = round16(c->G);
     uint32_t cols = 32;
     while ((int)cols < Gp) cols <<= 1;
-    const size_t n = (size_t)(c->L + 1) * Gp * Kp;
-    const uint16_t *Kh = (const uint16_t *)c->d_tcK, *Kl = Kh + n;
+    const uint16_t *Kop = (const uint16_t *)c->d_tcK;
     const int nb = c->n_partial;
     cudaError_t e;
 #define SHD_SRC_TC(T)                                                                                         \
@@ -868,7 +960,7 @@ cudaError_t launch_source_sums_tc(shd_ctx *c, const float *Ip, float *Sp, const 
         if ((e = cudaFuncSetAttribute(k_source_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=  \
             cudaSuccess)                                                                                      \
             return e;                                                                                         \
-        k_source_tc<T><<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, Kh, Kl, Gp, Kp, cols,     \
+        k_source_tc<T><<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, Kop, Gp, Kp, cols,       \
                                             c->d_partial, c->d_tc_err);                                       \
         break;
     switch (tn) {
