@@ -254,6 +254,19 @@ int shd_get_state_dev(shd_ctx *ctx, double *dev_I, void *cuda_stream);
 int shd_set_sweep_schedule(shd_ctx *ctx, int C, int NT);
 int shd_get_sweep_schedule(shd_ctx *ctx, int *C, int *NT, int *ncand, float *cand);
 
+/* Source pass (stage a2) of a kernel that mixes groups (Klein-Nishina or a
+ * non-diagonal table) in SHD_MIXED: the contraction over g' runs either on
+ * the CUDA cores in FP32 or on the tcgen05 tensor cores (per l, the (node,
+ * m) rows of eight nodes times K_l, FP32 operands split into three BF16
+ * pieces, six products accumulated in FP32: FP32-level rounding).  By
+ * default (path 0) the first step outside a stream capture times both and
+ * keeps the faster; shd_set_source_path forces 1 (CUDA cores) or 2 (tensor
+ * cores; SHD_ERR_ARG where it does not apply).  shd_get_source_path reports
+ * the path in use (0 before the timing, 1 where only the CUDA cores apply)
+ * and the two timings in milliseconds (0 before). */
+int shd_set_source_path(shd_ctx *ctx, int path);
+int shd_get_source_path(shd_ctx *ctx, int *path, float *ms_cuda_cores, float *ms_tensor_cores);
+
 /* Self-check of the failure path of the tensor-core kernels' bounded waits
  * (no counterpart in the paper).  Every mbarrier wait in those kernels polls
  * a bounded number of times; when the limit runs out the kernel raises the

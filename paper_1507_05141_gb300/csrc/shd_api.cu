@@ -1340,6 +1340,7 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
     c->have_scat = true;
     // the tensor-core source's BF16 operands of a group-mixing kernel
     dfree(c->d_tcK);
+    c->source_choice = 0;
     if (c->precision == SHD_MIXED && !c->k_diagonal) {
         if ((rc = dalloc(c, &c->d_tcK, source_tc_operand_bytes(c), "source operands"))) return rc;
         CK(launch_source_tc_operands(c, c->stream), "source operands");
@@ -1675,6 +1676,29 @@ int shd_get_sweep_schedule(shd_ctx *c, int *C, int *NT, int *ncand, float *cand)
     if (cand)
         for (int i = 0; i < c->sweep_ntune; ++i)
             for (int q = 0; q < 3; ++q) cand[3 * i + q] = c->sweep_tune[i][q];
+    return SHD_OK;
+}
+
+int shd_set_source_path(shd_ctx *c, int path)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (path < 0 || path > 2) return fail(SHD_ERR_ARG, "source path must be 0 (timed), 1 (CUDA cores) or 2 (tensor cores)");
+    if (path == 2 && !source_tc_usable(c))
+        return fail(SHD_ERR_ARG, "no tensor-core source for this problem (MIXED with a group-mixing kernel, "
+                                 "operands within shared memory)");
+    c->source_choice = path;
+    drop_graphs(c);
+    return SHD_OK;
+}
+
+int shd_get_source_path(shd_ctx *c, int *path, float *ms_cuda_cores, float *ms_tensor_cores)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (path) *path = source_tc_usable(c) ? c->source_choice : 1;
+    if (ms_cuda_cores) *ms_cuda_cores = c->source_ms[0];
+    if (ms_tensor_cores) *ms_tensor_cores = c->source_ms[1];
     return SHD_OK;
 }
 

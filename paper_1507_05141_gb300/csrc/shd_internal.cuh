@@ -190,6 +190,11 @@ struct shd_ctx {
     // BF16 hi / lo of the scattering kernel K_l for the tensor-core source
     // (MIXED with a kernel that mixes groups): [2][L+1][Gp][Kp]
     void *d_tcK = nullptr;
+    // source pass of such a kernel in MIXED: 0 not timed yet, 1 CUDA cores,
+    // 2 tensor cores (the faster when first timed: source_ms = {CUDA-core,
+    // tensor-core} milliseconds)
+    int source_choice = 0;
+    float source_ms[2] = {0.f, 0.f};
     // segment tiling of the mixed path: group 0 = z- and y-class ordinates
     // over bw x (128/bw) boxes of (x, y) at one z; group 1 = x-class over
     // boxes of (y, z) at one x.  Segments {plane, a0, b0, 0}; the group's

@@ -1696,26 +1696,59 @@ template <class T>
 cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, const T *Sprev, bool have_prev,
                                cudaStream_t st)
 {
-    if constexpr (sizeof(T) == 4) {
-        // group-mixing kernels in the mixed precision: on the tensor cores
-        if (source_tc_usable(ctx)) {
-            cudaError_t e = launch_source_sums_tc(ctx, (const float *)Ip, (float *)Sp, (const float *)mom,
-                                                  (const float *)Sprev, have_prev, st);
-            if (e != cudaSuccess) return e;
-            k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, ctx->n_partial, have_prev ? 1 : 0, ctx->d_sums);
-            note_launch();
-            return cudaGetLastError();
-        }
-    }
     Prob<T> P = make_prob<T>(ctx);
     const size_t sm = source_sums_smem(ctx);
     auto kern = ctx->k_diagonal && ctx->G <= 32 ? k_source_sums<T, true> : k_source_sums<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int nb = ctx->n_partial;
-    kern<<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, ctx->d_partial);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    auto cuda_cores = [&]() {
+        kern<<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, ctx->d_partial);
+        note_launch();
+        return cudaGetLastError();
+    };
+    bool tc = false;
+    if constexpr (sizeof(T) == 4) {
+        // group-mixing kernels in the mixed precision: the tensor-core pass or
+        // the CUDA-core pass, whichever ran faster when first timed (outside
+        // a capture; both compute the same S_lm and partial sums)
+        if (source_tc_usable(ctx)) {
+            shd_ctx *c = const_cast<shd_ctx *>(ctx);  // the choice is a cache of the context
+            auto tc_pass = [&]() {
+                return launch_source_sums_tc(c, (const float *)Ip, (float *)Sp, (const float *)mom,
+                                             (const float *)Sprev, have_prev, st);
+            };
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (c->source_choice == 0 && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
+                cs == cudaStreamCaptureStatusNone) {
+                cudaEvent_t ev[3];
+                for (auto &x : ev) cudaEventCreate(&x);
+                float t_tc = 1e30f, t_cc = 1e30f;
+                cudaEventRecord(ev[0], st);
+                bool ok = tc_pass() == cudaSuccess;
+                cudaEventRecord(ev[1], st);
+                ok = ok && cuda_cores() == cudaSuccess;
+                cudaEventRecord(ev[2], st);
+                if (ok && cudaEventSynchronize(ev[2]) == cudaSuccess) {
+                    cudaEventElapsedTime(&t_tc, ev[0], ev[1]);
+                    cudaEventElapsedTime(&t_cc, ev[1], ev[2]);
+                }
+                for (auto &x : ev) cudaEventDestroy(x);
+                cudaGetLastError();
+                c->source_ms[0] = t_cc;
+                c->source_ms[1] = t_tc;
+                c->source_choice = t_tc < t_cc ? 2 : 1;
+            }
+            tc = c->source_choice == 2;
+        }
+    }
+    if (tc) {
+        e = launch_source_sums_tc(const_cast<shd_ctx *>(ctx), (const float *)Ip, (float *)Sp, (const float *)mom,
+                                  (const float *)Sprev, have_prev, st);
+    } else {
+        e = cuda_cores();
+    }
+    if (e != cudaSuccess) return e;
     k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
     note_launch();
     return cudaGetLastError();

@@ -66,6 +66,9 @@ _SIGS = {
     "shd_check_bounded_wait": (_i, [_vp, _ll]),
     "shd_set_ng": (_i, [_vp, _i]),
     "shd_set_integrator": (_i, [_vp, _i]),
+    "shd_set_source_path": (_i, [_vp, _i]),
+    "shd_get_source_path": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_float)]),
     "shd_set_time_scheme": (_i, [_vp, _i]),
     "shd_set_sweep_schedule": (_i, [_vp, _i, _i]),
     "shd_get_sweep_schedule": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -329,6 +332,18 @@ class Solver:
         paper's cubic Bezier short characteristic)."""
         code = {"linear": SC_LINEAR, "bezier": SC_BEZIER}[name] if isinstance(name, str) else int(name)
         _check(self._L.shd_set_integrator(self._h, code))
+
+    def set_source_path(self, path):
+        """Source pass of a group-mixing kernel in MIXED: 'auto' (timed),
+        'cuda' (CUDA cores) or 'tensor' (tcgen05)."""
+        code = {"auto": 0, "cuda": 1, "tensor": 2}[path] if isinstance(path, str) else int(path)
+        _check(self._L.shd_set_source_path(self._h, code))
+
+    def source_path(self):
+        """(path in use: 0 untimed, 1 CUDA cores, 2 tensor cores; ms CUDA cores; ms tensor cores)."""
+        p, a, b = _i(), ctypes.c_float(), ctypes.c_float()
+        _check(self._L.shd_get_source_path(self._h, ctypes.byref(p), ctypes.byref(a), ctypes.byref(b)))
+        return p.value, a.value, b.value
 
     def set_ng(self, period=4):
         """Ng acceleration of solve_static every `period` (>= 4) iterations; 0 = off."""

@@ -32,6 +32,8 @@ def test_kn_steps_mixed_tensor_core_source(native, G, L):
                         alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=K, sigma_out=so,
                         kappa=spec.kappa, box=spec.box)
     s = native.Solver.from_spec(spec, precision="mixed")
+    s.set_source_path("tensor")
+    assert s.source_path()[0] == 2
     I0 = inputs.random_state(spec, seed=9)
     s.set_state(I0)
     s.step(2)
@@ -46,4 +48,29 @@ def test_kn_steps_mixed_tensor_core_source(native, G, L):
     assert abs(e_g - sums[0]) <= MIXED_TOL * abs(sums[0])
     assert abs(p_g - sums[1]) <= MIXED_TOL * abs(sums[1])
     assert abs(r_g - sums[2]) <= 1e-3 * abs(sums[2]) + 1e-7
+    s.close()
+
+
+def test_source_path_timed_choice(native):
+    """The default times both source passes on the first step and keeps the
+    faster; both give the same step to within the mixed tolerance."""
+    spec = inputs.ragged_mixed(grid=(16, 8, 6), G=16, L=7, scattering="kn")
+    I0 = inputs.random_state(spec, seed=4)
+    out = {}
+    for path in ("auto", "cuda", "tensor"):
+        s = native.Solver.from_spec(spec, precision="mixed")
+        s.set_source_path(path)
+        s.set_state(I0)
+        s.step(2)
+        out[path] = s.get_state()
+        p, ms_cc, ms_tc = s.source_path()
+        if path == "auto":
+            assert p in (1, 2) and ms_cc > 0 and ms_tc > 0
+            assert p == (2 if ms_tc < ms_cc else 1)
+        s.close()
+    scale = np.max(np.abs(out["cuda"]))
+    assert float(np.max(np.abs(out["tensor"] - out["cuda"]))) < 1e-5 * scale
+    s = native.Solver.from_spec(inputs.ragged_mixed(), precision="mixed")  # Thomson: diagonal, CUDA cores only
+    with pytest.raises(native.ShdError):
+        s.set_source_path("tensor")
     s.close()
