@@ -165,6 +165,21 @@ def kn_table(edges, L: int, energy_weighted: bool = True):
     return K, so
 
 
+def kn_thermal_table(edges, L: int, theta: float, energy_weighted: bool = True):
+    """(K[l][g][g'], sigma_out[g']) of Compton scattering off isotropic
+    Maxwell-Juttner electrons at temperature theta = kT_e/m_e c^2 (the
+    reading of Sec. 2.3 for a temperature field: the cold kernel averaged
+    over the electrons), in sigma_T units, by the oracle's product
+    quadrature."""
+    edges = _f64(edges)
+    G = len(edges) - 1
+    K = np.zeros((L + 1, G, G))
+    so = np.zeros(G)
+    lib().orc_kn_thermal_table(ctypes.c_int(G), _p(edges), ctypes.c_int(L), ctypes.c_int(int(energy_weighted)),
+                               ctypes.c_double(float(theta)), _p(K), _p(so))
+    return K, so
+
+
 def thomson_table(G: int, L: int):
     """Thomson kernel: diagonal, K_0 = 1, K_2 = (1/2)/5 (Sec. 2.3, Thomson
     phase function 3/4(1 + cos^2) = 1 + P_2/2)."""

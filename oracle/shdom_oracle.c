@@ -400,6 +400,126 @@ int orc_kn_table(int G, const double *edges, int L, int ew, double *K, double *s
 }
 
 /* ------------------------------------------------------------------------ */
+/* Compton scattering off thermal electrons (reading of Sec. 2.3 for a       */
+/* temperature field; the paper's kernel is the cold-electron one)            */
+/* ------------------------------------------------------------------------ */
+
+/* Total Klein-Nishina cross-section of a photon of energy x (m_e c^2) on an
+ * electron at rest, in units of sigma_T (the textbook closed form; the
+ * Thomson limit 1 - 2x below x = 1e-4). */
+static double sigma_kn_total(double x)
+{
+    if (x < 1e-4) return 1.0 - 2.0 * x + 5.2 * x * x;
+    double l = log1p(2.0 * x);
+    return 0.75 * ((1.0 + x) / (x * x * x) * (2.0 * x * (1.0 + x) / (1.0 + 2.0 * x) - l) + l / (2.0 * x) -
+                   (1.0 + 3.0 * x) / ((1.0 + 2.0 * x) * (1.0 + 2.0 * x)));
+}
+
+/* Quadrature of the thermal kernel: NE points in ln(eps) per incident group,
+ * NMU in the laboratory scattering cosine, and over the isotropic
+ * Maxwell-Juttner electrons NS in s = sqrt((gamma - 1)/theta) on [0, SMAX],
+ * NME in the electron's direction cosine and NPHI in its azimuth (midpoints). */
+#define TH_NE 16
+#define TH_NMU 48
+#define TH_NS 24
+#define TH_SMAX 6.324555320336759 /* sqrt(40) */
+#define TH_NME 16
+#define TH_NPHI 16
+
+/* K_l^theta[g][g'] = (2 pi / de_g) Int_{g'} d eps Int d mu P_l(mu)
+ *      < (dsigma/dOmega1)_e (eps1/eps)^ew 1[eps1 in g] >_theta,
+ * sigma_out^theta[g'] = (1/de_g') Int_{g'} d eps < (1 - beta mu_e) sigma_KN(eps') >_theta
+ * for a photon along z scattered into the direction at cosine mu (azimuth
+ * 0; the average over isotropic electrons does not depend on it), and an
+ * electron of Lorentz factor gamma, speed beta, direction n_e
+ * (mu_e = n_e.z, mu_e1 = n_e.n1), all in units of m_e c^2 and sigma_T:
+ *   eps'  = gamma eps (1 - beta mu_e)                   (electron rest frame)
+ *   eps1  = eps (1 - beta mu_e) / ((1 - beta mu_e1) + (eps/gamma)(1 - mu))
+ *   eps1' = gamma eps1 (1 - beta mu_e1),  1 - cos T' = 1/eps1' - 1/eps'
+ *   (dsigma/dOmega1)_e = (1 - beta mu_e) (3/16 pi) (eps1/eps')^2
+ *                        (eps'/eps1' + eps1'/eps' - sin^2 T')
+ * (energy-momentum conservation; the rest-frame Klein-Nishina cross-section
+ * carried to the laboratory solid angle and weighted by the relative flux).
+ * The electron average uses the Maxwell-Juttner density gamma^2 beta
+ * e^{-(gamma-1)/theta} on the quadrature above, normalised on it.  With
+ * beta = 0 this is the cold kernel of orc_kn_table. */
+int orc_kn_thermal_table(int G, const double *edges, int L, int ew, double theta, double *K, double *sigma_out)
+{
+    double xs[TH_NS], ws[TH_NS], xme[TH_NME], wme[TH_NME], xmu[TH_NMU], wmu[TH_NMU], xe[TH_NE], we[TH_NE];
+    orc_gauss_legendre(TH_NS, xs, ws);
+    orc_gauss_legendre(TH_NME, xme, wme);
+    orc_gauss_legendre(TH_NMU, xmu, wmu);
+    orc_gauss_legendre(TH_NE, xe, we);
+    /* electrons: gamma, beta and weight per s node */
+    double gam[TH_NS], bet[TH_NS], wel[TH_NS], wsum = 0.0;
+    for (int i = 0; i < TH_NS; ++i) {
+        double sv = 0.5 * TH_SMAX * (xs[i] + 1.0);
+        gam[i] = 1.0 + theta * sv * sv;
+        bet[i] = sqrt(1.0 - 1.0 / (gam[i] * gam[i]));
+        /* d gamma = 2 theta s ds; density gamma^2 beta e^{-s^2} */
+        wel[i] = 0.5 * TH_SMAX * ws[i] * gam[i] * gam[i] * bet[i] * exp(-sv * sv) * 2.0 * theta * sv;
+        wsum += wel[i];
+    }
+    for (int i = 0; i < TH_NS; ++i) wel[i] /= wsum;
+    for (long i = 0; i < (long)(L + 1) * G * G; ++i) K[i] = 0.0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int gp = 0; gp < G; ++gp) {
+        double *acc = (double *)calloc((size_t)(L + 1) * G, sizeof(double));
+        double pl[32];
+        double tot = 0.0;
+        double t0 = log(edges[gp]), t1 = log(edges[gp + 1]);
+        double ht = 0.5 * (t1 - t0), mt = 0.5 * (t1 + t0);
+        for (int ie = 0; ie < TH_NE; ++ie) {
+            double eps = exp(mt + ht * xe[ie]);
+            double weps = we[ie] * ht * eps;
+            /* total cross-section: electrons only */
+            double avg = 0.0;
+            for (int is = 0; is < TH_NS; ++is)
+                for (int im = 0; im < TH_NME; ++im) {
+                    double f = 1.0 - bet[is] * xme[im];
+                    avg += wel[is] * 0.5 * wme[im] * f * sigma_kn_total(gam[is] * eps * f);
+                }
+            tot += weps * avg;
+            for (int iu = 0; iu < TH_NMU; ++iu) {
+                double mu = xmu[iu];
+                double smu = sqrt(1.0 - mu * mu);
+                pl[0] = 1.0;
+                if (L >= 1) pl[1] = mu;
+                for (int l = 2; l <= L; ++l) pl[l] = ((2.0 * l - 1.0) * mu * pl[l - 1] - (l - 1.0) * pl[l - 2]) / l;
+                for (int is = 0; is < TH_NS; ++is)
+                    for (int im = 0; im < TH_NME; ++im) {
+                        double cme = xme[im], sme = sqrt(1.0 - cme * cme);
+                        for (int ip = 0; ip < TH_NPHI; ++ip) {
+                            double phe = 2.0 * ORC_PI * (ip + 0.5) / TH_NPHI;
+                            double b = bet[is], gm = gam[is];
+                            double mue1 = sme * cos(phe) * smu + cme * mu; /* n_e . n1, n1 = (sin, 0, mu) */
+                            double a = 1.0 - b * cme;
+                            double eps1 = eps * a / ((1.0 - b * mue1) + (eps / gm) * (1.0 - mu));
+                            int g = -1;
+                            for (int q = 0; q < G; ++q)
+                                if (eps1 >= edges[q] && eps1 < edges[q + 1]) { g = q; break; }
+                            if (g < 0) continue;
+                            double ep = gm * eps * a, e1p = gm * eps1 * (1.0 - b * mue1);
+                            double ct = 1.0 - (1.0 / e1p - 1.0 / ep);
+                            double r = eps1 / ep;
+                            double dsdo = a * 3.0 / (16.0 * ORC_PI) * r * r * (ep / e1p + e1p / ep - (1.0 - ct * ct));
+                            if (ew) dsdo *= eps1 / eps;
+                            double wgt = weps * wmu[iu] * wel[is] * 0.5 * wme[im] / TH_NPHI * dsdo;
+                            for (int l = 0; l <= L; ++l) acc[(long)l * G + g] += wgt * pl[l];
+                        }
+                    }
+            }
+        }
+        for (int l = 0; l <= L; ++l)
+            for (int g = 0; g < G; ++g)
+                K[((long)l * G + g) * G + gp] = 2.0 * ORC_PI * acc[(long)l * G + g] / (edges[g + 1] - edges[g]);
+        sigma_out[gp] = tot / (edges[gp + 1] - edges[gp]);
+        free(acc);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The step                                                                  */
 /* ------------------------------------------------------------------------ */
 

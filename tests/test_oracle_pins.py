@@ -969,3 +969,81 @@ def test_bezier_no_overshoot_at_a_step():
     chi = np.full((Nc, 1, P.N), chi_v)
     out = P.sweep(np.zeros_like(eta), eta, chi)
     assert out.min() >= 0.0 and out.max() <= 1.0 + 1e-14
+
+
+# --------------------------------------------------------------------------
+# Compton scattering off thermal electrons (the temperature field's kernel)
+# --------------------------------------------------------------------------
+
+def test_thermal_kn_cold_limit():
+    """theta -> 0: the electron average collapses to electrons at rest; the
+    group-summed photon-number and energy kernels (smooth: the sum over
+    final groups removes the group indicator) equal the cold table's (the
+    thermal effects are of order theta = 1e-8).  The lowest incident group
+    is left out: its down-scattered photons leave the range, and the leak
+    edge is resolved differently by the two quadratures."""
+    edges = np.geomspace(1e-3, 1e1, 9)
+    de = np.diff(edges)
+    for ew in (True, False):
+        Kc, soc = O.kn_table(edges, 3, energy_weighted=ew)
+        Kt, sot = O.kn_thermal_table(edges, 3, 1e-8, energy_weighted=ew)
+        sc, st = (de[:, None] * Kc[0]).sum(axis=0), (de[:, None] * Kt[0]).sum(axis=0)
+        assert np.allclose(st[1:], sc[1:], rtol=1e-6)
+        assert np.allclose(sot, soc, rtol=1e-7)
+
+
+@pytest.mark.parametrize("theta", [0.01, 0.1])
+def test_thermal_kn_total_cross_section(theta):
+    """sigma_out^theta of a group against nested adaptive quadrature of
+    <(1 - beta mu_e) sigma_KN(gamma eps (1 - beta mu_e))> over the
+    Maxwell-Juttner density gamma^2 beta e^(-gamma/theta) / (theta K2(1/theta))
+    and the group's energies, sigma_KN the textbook total cross-section."""
+    from scipy.integrate import quad
+    from scipy.special import kve
+
+    def skn(x):
+        if x < 1e-4:
+            return 1 - 2 * x + 5.2 * x * x
+        l = np.log1p(2 * x)
+        return 0.75 * ((1 + x) / x ** 3 * (2 * x * (1 + x) / (1 + 2 * x) - l) + l / (2 * x)
+                       - (1 + 3 * x) / (1 + 2 * x) ** 2)
+    norm = theta * kve(2, 1.0 / theta)  # theta K2(1/theta) e^(1/theta), so dens carries e^(-(gamma-1)/theta)
+
+    def avg(eps):
+        def over_gamma(g):
+            b = np.sqrt(1 - 1 / (g * g))
+            dens = g * g * b * np.exp(-(g - 1) / theta) / norm
+            inner = quad(lambda m: 0.5 * (1 - b * m) * skn(g * eps * (1 - b * m)), -1, 1, epsabs=0, epsrel=1e-11)[0]
+            return dens * inner
+        return quad(over_gamma, 1.0, 1.0 + 60 * theta, epsabs=0, epsrel=1e-10, limit=200)[0]
+    edges = np.array([0.1, 0.3, 1.0])
+    _, so = O.kn_thermal_table(edges, 1, theta)
+    ref = quad(avg, edges[0], edges[1], epsabs=0, epsrel=1e-9)[0] / (edges[1] - edges[0])
+    assert so[0] == pytest.approx(ref, rel=1e-6)
+
+
+@pytest.mark.parametrize("theta", [0.01, 0.05, 0.2])
+def test_thermal_kn_mean_energy_gain_thomson_limit(theta):
+    """Low-energy photons (eps << theta, gamma eps << 1) gain on average
+    (4/3) <gamma^2 beta^2> = 4 theta K3(1/theta)/K2(1/theta) of their energy
+    per scattering (Thomson scattering off a relativistic Maxwellian), less
+    the recoil, which is below 0.3 % of it here: the ratio of the energy to
+    the photon-number group sums of the thermal tables."""
+    from scipy.special import kve
+    edges = np.geomspace(1e-6, 1e1, 29)
+    de = np.diff(edges)
+    KE, _ = O.kn_thermal_table(edges, 0, theta, energy_weighted=True)
+    KN, _ = O.kn_thermal_table(edges, 0, theta, energy_weighted=False)
+    gain = (de[:, None] * KE[0]).sum(axis=0) / (de[:, None] * KN[0]).sum(axis=0) - 1.0
+    ref = 4.0 * theta * kve(3, 1.0 / theta) / kve(2, 1.0 / theta)
+    for g in (3, 4, 5):   # eps ~ 1e-5 .. 3e-5, inside the range after up- and down-scattering
+        assert gain[g] == pytest.approx(ref, rel=1e-2), (g, gain[g], ref)
+
+
+def test_thermal_kn_upscatters_and_cold_does_not():
+    edges = np.geomspace(1e-3, 1e1, 9)
+    Kc, _ = O.kn_table(edges, 2)
+    Kt, _ = O.kn_thermal_table(edges, 2, 0.1)
+    up = np.triu(np.ones((8, 8), bool), k=1)  # g > g' is the lower triangle of K[g][g']; use the transpose
+    assert np.all(Kc[0][up.T] == 0.0)
+    assert np.max(Kt[0][up.T]) > 0.01 * np.max(Kt[0])
