@@ -613,7 +613,10 @@ def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spe
     def pinned(a):
         t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
         return t, t.numpy()
-    hold = [pinned(x) for x in (spec.alpha0, spec.ne, spec.u, spec.emis0)]
+    fields = [spec.alpha0, spec.ne, spec.u, spec.emis0]
+    if spec.extra.get("theta_e") is not None:
+        fields.append(spec.extra["theta_e"])
+    hold = [pinned(x) for x in fields]
     arrs = [h[1] for h in hold]
     h2d = sum(a.nbytes for a in arrs)
     d2h = spec.Nc * spec.G * 10 * 8

@@ -66,7 +66,13 @@ enum shd_scattering {
     SHD_SCAT_THOMSON = 2,  /* Thomson: K_0 = 1, K_2 = 1/10, sigma_out = 1       */
     SHD_SCAT_KN = 3,       /* cold-electron Klein-Nishina multigroup kernel,
                               built on the GPU from the group edges            */
-    SHD_SCAT_TABLE = 4     /* caller-supplied K[l][g][g'] and sigma_out[g']     */
+    SHD_SCAT_TABLE = 4,    /* caller-supplied K[l][g][g'] and sigma_out[g']     */
+    SHD_SCAT_KN_THERMAL = 5 /* Compton scattering off thermal electrons at each
+                              node's temperature theta_e (shd_set_fields):
+                              shd_set_scattering tabulates the kernel on the
+                              grid theta_i = 10^(-3 + i/4), i = 0..12, and each
+                              node blends its two bracketing tables linearly
+                              in log10(theta) (clamped into the grid)        */
 };
 
 enum shd_time_scheme {
@@ -116,6 +122,12 @@ int shd_set_groups(shd_ctx *ctx, int G, const double *edges);
  *   ne     [Nc]     scattering coefficient scale n_e sigma_T (>= 0)
  *   u      [Nc][3]  spatial 4-velocity Gamma v/c (finite)
  *   emis0  [Nc][G]  isotropic emissivity eta0 (>= 0)
+ *   theta_e [Nc]    electron temperature kT_e / m_e c^2 (>= 0), or NULL; read
+ *                   by the thermal Compton kernel (SHD_SCAT_KN_THERMAL),
+ *                   which needs it (its absence is reported at the next step
+ *                   with SHD_ERR_STATE); other kernels ignore it.  It is
+ *                   checked on the host (SHD_ERR_NAN, "theta_e"), after the
+ *                   other four fields.
  * Requires grid, angles and groups.  The host arrays are copied (the call
  * returns once the copies are done and checked); the check runs on the
  * device over a staging copy, before any field array changes, so a refused
@@ -123,7 +135,7 @@ int shd_set_groups(shd_ctx *ctx, int G, const double *edges);
  * -> SHD_ERR_NAN, naming the first offending field in the order alpha0, ne,
  * u, emis0.  A new flow on the same moving nodes keeps the captured step. */
 int shd_set_fields(shd_ctx *ctx, const double *alpha0, const double *ne, const double *u,
-                   const double *emis0);
+                   const double *emis0, const double *theta_e);
 
 /* Scattering kernel (Sec. 2.3): kind from enum shd_scattering.  For
  * SHD_SCAT_TABLE, K is [L+1][G][G] (row = final group) and sigma_out [G];
@@ -131,8 +143,19 @@ int shd_set_fields(shd_ctx *ctx, const double *alpha0, const double *ne, const d
  * chi0(c,g) = alpha0 + n_e sigma_out(g).  Requires angles and groups. */
 int shd_set_scattering(shd_ctx *ctx, int kind, const double *K, const double *sigma_out);
 
-/* Copy the active scattering table out: K [L+1][G][G], sigma_out [G]. */
+/* Copy the active scattering table out: K [L+1][G][G], sigma_out [G] (for
+ * SHD_SCAT_KN_THERMAL: the coldest table of the grid). */
 int shd_get_scattering(shd_ctx *ctx, double *K, double *sigma_out);
+
+/* The thermal Compton kernel's tables (after shd_set_scattering with
+ * SHD_SCAT_KN_THERMAL): K_th [13][L+1][G][G] and sigma_out_th [13][G] on the
+ * temperature grid 10^(-3 + i/4) (either may be NULL).  Each is the average
+ * of the single-electron Klein-Nishina scattering over isotropic
+ * Maxwell-Juttner electrons (laboratory kinematics; no counterpart formula
+ * in the paper, whose electrons are cold), by a fixed product quadrature in
+ * FP64: 16 energies per incident group, 48 scattering cosines, 24 x 16 x 16
+ * electron speeds, direction cosines and azimuths. */
+int shd_get_thermal_tables(shd_ctx *ctx, double *K_th, double *sigma_out_th);
 
 /* Inflow boundary intensity (enum shd_boundary); data as described there,
  * NULL for SHD_BC_VACUUM. */

@@ -44,6 +44,8 @@ class Problem(ctypes.Structure):
         ("kappa", ctypes.c_double),
         ("bc_mode", ctypes.c_int), ("bc", _dp),
         ("integrator", ctypes.c_int),
+        ("nth", ctypes.c_int), ("th_lg0", ctypes.c_double), ("th_dlg", ctypes.c_double),
+        ("K_th", _dp), ("so_th", _dp), ("theta_e", _dp),
     ]
 
 
@@ -180,6 +182,22 @@ def kn_thermal_table(edges, L: int, theta: float, energy_weighted: bool = True):
     return K, so
 
 
+# the temperature grid of the library's thermal Compton kernel:
+# theta_i = 10^(THERMAL_LG0 + i THERMAL_DLG), i < THERMAL_N
+THERMAL_LG0, THERMAL_DLG, THERMAL_N = -3.0, 0.25, 13
+
+
+def thermal_tables(edges, L: int, lg0=THERMAL_LG0, dlg=THERMAL_DLG, n=THERMAL_N):
+    """The thermal kernels (energy form) and out-scattering cross-sections on
+    the temperature grid 10^(lg0 + i dlg), i < n: ([n][L+1][G][G], [n][G])."""
+    Ks, sos = [], []
+    for i in range(n):
+        K, so = kn_thermal_table(edges, L, 10.0 ** (lg0 + i * dlg))
+        Ks.append(K)
+        sos.append(so)
+    return np.array(Ks), np.array(sos)
+
+
 def thomson_table(G: int, L: int):
     """Thomson kernel: diagonal, K_0 = 1, K_2 = (1/2)/5 (Sec. 2.3, Thomson
     phase function 3/4(1 + cos^2) = 1 + P_2/2)."""
@@ -205,7 +223,7 @@ class OracleProblem:
     """Holds the numpy arrays behind an ``orc_problem`` so they stay alive."""
 
     def __init__(self, *, grid, L, nmu, nphi, edges, alpha0, ne, u, emis0, K, sigma_out,
-                 kappa=0.0, bc_mode=0, bc=None, box=(1.0, 1.0, 1.0)):
+                 kappa=0.0, bc_mode=0, bc=None, box=(1.0, 1.0, 1.0), thermal=None):
         nx, ny, nz = grid
         self.grid = (nx, ny, nz)
         self.Nc = nx * ny * nz
@@ -231,6 +249,14 @@ class OracleProblem:
         s.kappa = float(kappa)
         s.bc_mode = int(bc_mode)
         s.bc = _p(self.bc) if self.bc is not None else None
+        if thermal is not None:
+            # {"theta_e": [Nc], "K_th": [nth][L+1][G][G], "so_th": [nth][G], "lg0": .., "dlg": ..}
+            self.theta_e = _f64(thermal["theta_e"]).reshape(self.Nc)
+            self.K_th = _f64(thermal["K_th"])
+            self.so_th = _f64(thermal["so_th"])
+            s.nth = int(self.so_th.shape[0])
+            s.th_lg0, s.th_dlg = float(thermal["lg0"]), float(thermal["dlg"])
+            s.K_th, s.so_th, s.theta_e = _p(self.K_th), _p(self.so_th), _p(self.theta_e)
 
     def set_integrator(self, name):
         """'linear' (linear-in-tau short characteristic) or 'bezier' (the

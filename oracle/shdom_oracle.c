@@ -63,6 +63,13 @@ typedef struct {
     int bc_mode;             /* 0 vacuum, 1 isotropic per group, 2 full array */
     const double *bc;        /* mode 1: [G]; mode 2: [c][g][k]                */
     int integrator;          /* 0 linear-in-tau, 1 cubic Bezier (sweep_pair) */
+    /* thermal electrons (nth > 0): kernels tabulated on the temperature grid
+     * theta_i = 10^(th_lg0 + i th_dlg), i < nth (K_th [nth][L+1][G][G],
+     * so_th [nth][G], by orc_kn_thermal_table), and the node temperatures
+     * theta_e [c] = kT_e / m_e c^2; they replace K and sigma_out */
+    int nth;
+    double th_lg0, th_dlg;
+    const double *K_th, *so_th, *theta_e;
 } orc_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -556,10 +563,52 @@ static void mesh_free(orc_mesh *M)
 
 static int is_rest(const double *u) { return u[0] == 0.0 && u[1] == 0.0 && u[2] == 0.0; }
 
+/* Temperature bracket of node c on the tabulated grid: tables i and i+1
+ * with weight w of the second, linear in log10(theta), theta clamped into
+ * the grid (a node at or below zero temperature takes the first table). */
+static void thermal_bracket(const orc_problem *P, long c, int *i, double *w)
+{
+    double th = P->theta_e[c];
+    double x = th > 0.0 ? (log10(th) - P->th_lg0) / P->th_dlg : 0.0;
+    if (x < 0.0) x = 0.0;
+    if (x > P->nth - 1) x = P->nth - 1;
+    int i0 = (int)floor(x);
+    if (i0 > P->nth - 2) i0 = P->nth - 2;
+    if (i0 < 0) i0 = 0;
+    *i = i0;
+    *w = P->nth > 1 ? x - i0 : 0.0;
+}
+
+/* sigma_out(g) and K_l[g][g'] of node c: the global ones, or with thermal
+ * electrons the blend of the node's two bracketing tables. */
+static double sigma_out_of(const orc_problem *P, long c, int g)
+{
+    if (P->nth <= 0) return P->sigma_out[g];
+    int i;
+    double w;
+    thermal_bracket(P, c, &i, &w);
+    double a = P->so_th[(long)i * P->G + g];
+    double b = P->nth > 1 ? P->so_th[(long)(i + 1) * P->G + g] : a;
+    return (1.0 - w) * a + w * b;
+}
+
+static double kernel_of(const orc_problem *P, long c, int l, int g, int gp)
+{
+    int G = P->G;
+    if (P->nth <= 0) return P->K[((long)l * G + g) * G + gp];
+    int i;
+    double w;
+    thermal_bracket(P, c, &i, &w);
+    long per = (long)(P->L + 1) * G * G;
+    double a = P->K_th[(long)i * per + ((long)l * G + g) * G + gp];
+    double b = P->nth > 1 ? P->K_th[(long)(i + 1) * per + ((long)l * G + g) * G + gp] : a;
+    return (1.0 - w) * a + w * b;
+}
+
 /* Comoving extinction chi0(c,g) = alpha0 + n_e sigma_out(g). */
 static double chi0_of(const orc_problem *P, long c, int g)
 {
-    return P->alpha0[c * P->G + g] + P->ne[c] * P->sigma_out[g];
+    return P->alpha0[c * P->G + g] + P->ne[c] * sigma_out_of(P, c, g);
 }
 
 /* Stage a1 + a1': Lorentz-transform the laboratory intensity to comoving
@@ -630,7 +679,8 @@ int orc_project(const orc_problem *P, const double *I, double *Ip, double *J, do
 /* Stage a2: comoving source in spherical harmonics (Sec. 2.3)
  *   S_p(c,g) = n_e(c)/chi0(c,g) sum_g' K_l(p)[g][g'] I_p(c,g')
  *              + delta_p0 sqrt(4 pi) eta0(c,g)/chi0(c,g).
- * A node with chi0 = 0 has S = 0. */
+ * A node with chi0 = 0 has S = 0.  With thermal electrons K and sigma_out
+ * are the node's blend (kernel_of, sigma_out_of). */
 int orc_source(const orc_problem *P, const double *Ip, double *Sp)
 {
     long Nc = (long)P->nx * P->ny * P->nz;
@@ -645,8 +695,7 @@ int orc_source(const orc_problem *P, const double *Ip, double *Sp)
                     double s = 0.0;
                     if (chi > 0.0) {
                         double acc = 0.0;
-                        for (int gp = 0; gp < G; ++gp)
-                            acc += P->K[((long)l * G + g) * G + gp] * Ip[(c * G + gp) * NLM + p];
+                        for (int gp = 0; gp < G; ++gp) acc += kernel_of(P, c, l, g, gp) * Ip[(c * G + gp) * NLM + p];
                         s = P->ne[c] / chi * acc;
                         if (p == 0) s += sqrt(4.0 * ORC_PI) * P->emis0[c * G + g] / chi;
                     }

@@ -171,7 +171,8 @@ void free_all(shd_ctx *c)
                      &c->d_tcs_Bl[1], &c->d_tcs_Yh[0], &c->d_tcs_Yh[1], &c->d_tcs_Yl[0], &c->d_tcs_Yl[1],
                      (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_fcheck,
                      &c->d_ng[0], &c->d_ng[1], &c->d_ng[2], (void **)&c->d_ngpart, &c->d_rk[0], &c->d_rk[1],
-                     &c->d_rk[2], (void **)&c->d_sums_save, &c->d_tcK};
+                     &c->d_rk[2], (void **)&c->d_sums_save, &c->d_tcK, (void **)&c->d_thb,
+                     (void **)&c->d_thperm, &c->d_thw, &c->d_thK, &c->d_thso, (void **)&c->d_thchunk};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
     c->rtab_n = 0;
@@ -212,7 +213,8 @@ void drop_sized(shd_ctx *c)
                      &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag,
                      (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
                      &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_ng[0], &c->d_ng[1], &c->d_ng[2],
-                     &c->d_rk[0], &c->d_rk[1], &c->d_rk[2], &c->d_tcK};
+                     &c->d_rk[0], &c->d_rk[1], &c->d_rk[2], &c->d_tcK, (void **)&c->d_thb,
+                     (void **)&c->d_thperm, &c->d_thw, &c->d_thK, &c->d_thso, (void **)&c->d_thchunk};
     for (void **p : ptrs) dfree(*p);
     c->ntiles = 0;
     c->nmoving = 0;
@@ -220,6 +222,9 @@ void drop_sized(shd_ctx *c)
     c->rtab_valid = false;
     c->fstage_n = 0;
     c->have_fields = c->have_scat = c->have_state = false;
+    c->have_theta = false;
+    c->h_theta.clear();
+    c->nthchunk = 0;
     c->bc_mode = SHD_BC_VACUUM;
     c->sprev_valid = false;
 }
@@ -721,6 +726,8 @@ int ready_for_step(shd_ctx *c)
     if (!sized(c)) return fail(SHD_ERR_STATE, "grid, angles and groups must be set");
     if (!c->have_fields) return fail(SHD_ERR_STATE, "fields not set");
     if (!c->have_scat) return fail(SHD_ERR_STATE, "scattering not set");
+    if (c->scat_kind == SHD_SCAT_KN_THERMAL && !c->have_theta)
+        return fail(SHD_ERR_STATE, "the thermal Compton kernel needs the electron temperatures (theta_e)");
     size_t limit = 227 * 1024;
     if (remap_smem_bytes(c) > limit)
         return fail(SHD_ERR_ARG, "groups x ordinates too large for the remap kernels (%zu bytes shared memory)",
@@ -1200,7 +1207,58 @@ int shd_set_groups(shd_ctx *c, int G, const double *edges)
     return SHD_OK;
 }
 
-int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const double *u, const double *emis0)
+// Node temperatures: the bracket of each node on the temperature grid and
+// the weight of the upper table (FP64 on the host, linear in log10(theta),
+// clamped into the grid), and the nodes grouped by bracket in chunks of at
+// most kThermalChunk for the source pass.
+int set_theta(shd_ctx *c, const double *theta)
+{
+    const size_t Nc = (size_t)c->Nc;
+    for (size_t i = 0; i < Nc; ++i)
+        if (!std::isfinite(theta[i]) || theta[i] < 0.0) return fail(SHD_ERR_NAN, "theta_e must be finite and >= 0");
+    const bool same = c->have_theta && c->h_theta.size() == Nc &&
+                      std::equal(theta, theta + Nc, c->h_theta.begin());
+    if (same) return SHD_OK;
+    drop_graphs(c);  // the source pass's chunks are baked into a captured step
+    c->h_theta.assign(theta, theta + Nc);
+    std::vector<int> b(Nc), cnt(kThermalN, 0);
+    std::vector<double> w(Nc);
+    for (size_t i = 0; i < Nc; ++i) {
+        double x = theta[i] > 0.0 ? (std::log10(theta[i]) - kThermalLg0) / kThermalDlg : 0.0;
+        x = std::min(std::max(x, 0.0), (double)(kThermalN - 1));
+        int i0 = std::min((int)std::floor(x), kThermalN - 2);
+        b[i] = i0;
+        w[i] = x - i0;
+        cnt[i0]++;
+    }
+    std::vector<int> start(kThermalN, 0), perm(Nc);
+    for (int k = 1; k < kThermalN; ++k) start[k] = start[k - 1] + cnt[k - 1];
+    std::vector<int> pos = start;
+    for (size_t i = 0; i < Nc; ++i) perm[pos[b[i]]++] = (int)i;
+    std::vector<int4> chunks;
+    for (int k = 0; k < kThermalN; ++k)
+        for (int j = 0; j < cnt[k]; j += kThermalChunk)
+            chunks.push_back(make_int4(start[k] + j, std::min(kThermalChunk, cnt[k] - j), k, 0));
+    int rc;
+    if ((rc = dalloc(c, (void **)&c->d_thb, Nc * sizeof(int), "theta brackets"))) return rc;
+    if ((rc = dalloc(c, (void **)&c->d_thperm, Nc * sizeof(int), "theta order"))) return rc;
+    if ((rc = dalloc(c, &c->d_thw, Nc * c->esize, "theta weights"))) return rc;
+    if ((rc = dalloc(c, (void **)&c->d_thchunk, chunks.size() * sizeof(int4), "theta chunks"))) return rc;
+    CK(cudaMemcpy(c->d_thb, b.data(), Nc * sizeof(int), cudaMemcpyHostToDevice), "theta brackets");
+    CK(cudaMemcpy(c->d_thperm, perm.data(), Nc * sizeof(int), cudaMemcpyHostToDevice), "theta order");
+    CK(cudaMemcpy(c->d_thchunk, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice), "theta chunks");
+    if (is_fp64(c)) {
+        if ((rc = upload_reals<double>(c, w.data(), c->d_thw, Nc))) return rc;
+    } else {
+        if ((rc = upload_reals<float>(c, w.data(), c->d_thw, Nc))) return rc;
+    }
+    c->nthchunk = (int)chunks.size();
+    c->have_theta = true;
+    return SHD_OK;
+}
+
+int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const double *u, const double *emis0,
+                   const double *theta_e)
 {
     int rc = ctx_check(c);
     if (rc) return rc;
@@ -1259,6 +1317,14 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         if ((rc = build_tiles(c, u))) return rc;
     }
     c->have_fields = true;
+    if (theta_e) {
+        if ((rc = set_theta(c, theta_e))) return rc;
+    } else if (c->have_theta) {
+        drop_graphs(c);
+        c->have_theta = false;
+        c->h_theta.clear();
+        c->nthchunk = 0;
+    }
     if (c->have_scat) {
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
         else CK(launch_chi0<float>(c, c->stream), "chi0");
@@ -1287,12 +1353,48 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
             return fail(SHD_ERR_NAN, "scattering table must be finite (sigma_out >= 0)");
         hK.assign(K, K + nK);
         hs.assign(sigma_out, sigma_out + G);
-    } else if (kind != SHD_SCAT_KN) {
+    } else if (kind != SHD_SCAT_KN && kind != SHD_SCAT_KN_THERMAL) {
         return fail(SHD_ERR_ARG, "unknown scattering kind %d", kind);
     }
+    if (kind == SHD_SCAT_KN_THERMAL && L > 15) return fail(SHD_ERR_ARG, "thermal Compton kernel needs L <= 15");
     if ((rc = dalloc(c, &c->d_K, nK * c->esize, "K"))) return rc;
     if ((rc = dalloc(c, &c->d_sigma_out, (size_t)G * c->esize, "sigma_out"))) return rc;
-    if (kind == SHD_SCAT_KN) {
+    if (kind == SHD_SCAT_KN_THERMAL) {
+        // every temperature's table built on the device in FP64, then kept
+        // in the working precision; K and sigma_out hold the coldest one
+        std::vector<double> q, x, w;
+        for (int n : {24, 16, 48, 16}) {  // electron speed, electron direction, scattering cosine, energy
+            gauss_legendre(n, x, w);
+            q.insert(q.end(), x.begin(), x.end());
+            q.insert(q.end(), w.begin(), w.end());
+        }
+        const size_t nT = (size_t)kThermalN * nK;
+        double *dK = nullptr, *ds = nullptr, *dq = nullptr;
+        CK(cudaMalloc(&dK, sizeof(double) * nT), "thermal scratch");
+        CK(cudaMalloc(&ds, sizeof(double) * kThermalN * G), "thermal scratch");
+        CK(cudaMalloc(&dq, sizeof(double) * q.size()), "thermal scratch");
+        CK(cudaMemcpy(dq, q.data(), sizeof(double) * q.size(), cudaMemcpyHostToDevice), "copy");
+        CK(launch_kn_thermal_tables(G, c->d_edges, L, dq, dK, ds, c->stream), "thermal tables");
+        if ((rc = dalloc(c, &c->d_thK, nT * c->esize, "thermal kernels"))) return rc;
+        if ((rc = dalloc(c, &c->d_thso, (size_t)kThermalN * G * c->esize, "thermal cross-sections"))) return rc;
+        if (is_fp64(c)) {
+            CK(cudaMemcpyAsync(c->d_thK, dK, sizeof(double) * nT, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            CK(cudaMemcpyAsync(c->d_thso, ds, sizeof(double) * kThermalN * G, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            CK(cudaMemcpyAsync(c->d_K, dK, sizeof(double) * nK, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            CK(cudaMemcpyAsync(c->d_sigma_out, ds, sizeof(double) * G, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        } else {
+            CK(launch_convert<float>(dK, (float *)c->d_thK, (long long)nT, c->stream), "convert");
+            CK(launch_convert<float>(ds, (float *)c->d_thso, (long long)kThermalN * G, c->stream), "convert");
+            CK(launch_convert<float>(dK, (float *)c->d_K, (long long)nK, c->stream), "convert");
+            CK(launch_convert<float>(ds, (float *)c->d_sigma_out, G, c->stream), "convert");
+        }
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        std::vector<double> hso((size_t)kThermalN * G);
+        CK(cudaMemcpy(hso.data(), ds, sizeof(double) * hso.size(), cudaMemcpyDeviceToHost), "sigma_out");
+        c->h_sigma_max = 0.0;
+        for (double v : hso) c->h_sigma_max = std::max(c->h_sigma_max, v);
+        cudaFree(dK); cudaFree(ds); cudaFree(dq);
+    } else if (kind == SHD_SCAT_KN) {
         // built on the device in FP64, then converted to the working precision
         const int nq = 32;
         std::vector<double> gx, gw;
@@ -1331,7 +1433,7 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
     }
     c->scat_kind = kind;
     // the source stage's one-product form needs every K_l diagonal
-    c->k_diagonal = kind != SHD_SCAT_KN;
+    c->k_diagonal = kind != SHD_SCAT_KN && kind != SHD_SCAT_KN_THERMAL;
     if (kind == SHD_SCAT_TABLE)
         for (size_t i = 0; i < nK && c->k_diagonal; ++i) {
             const size_t r = i % ((size_t)G * G);
@@ -1341,7 +1443,7 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
     // the tensor-core source's BF16 operands of a group-mixing kernel
     dfree(c->d_tcK);
     c->source_choice = 0;
-    if (c->precision == SHD_MIXED && !c->k_diagonal) {
+    if (c->precision == SHD_MIXED && !c->k_diagonal && kind != SHD_SCAT_KN_THERMAL) {
         if ((rc = dalloc(c, &c->d_tcK, source_tc_operand_bytes(c), "source operands"))) return rc;
         CK(launch_source_tc_operands(c, c->stream), "source operands");
     }
@@ -1632,6 +1734,23 @@ int shd_set_time_scheme(shd_ctx *c, int scheme)
         return SHD_OK;
     }
     if (sized(c)) return ensure_rk_buffers(c);
+    return SHD_OK;
+}
+
+int shd_get_thermal_tables(shd_ctx *c, double *K_th, double *sigma_out_th)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (c->scat_kind != SHD_SCAT_KN_THERMAL || !c->d_thK) return fail(SHD_ERR_STATE, "no thermal Compton kernel set");
+    const size_t nT = (size_t)kThermalN * (c->L + 1) * c->G * c->G, nS = (size_t)kThermalN * c->G;
+    if (K_th) {
+        if (is_fp64(c)) { if ((rc = download_reals<double>(c, c->d_thK, K_th, nT))) return rc; }
+        else if ((rc = download_reals<float>(c, c->d_thK, K_th, nT))) return rc;
+    }
+    if (sigma_out_th) {
+        if (is_fp64(c)) { if ((rc = download_reals<double>(c, c->d_thso, sigma_out_th, nS))) return rc; }
+        else if ((rc = download_reals<float>(c, c->d_thso, sigma_out_th, nS))) return rc;
+    }
     return SHD_OK;
 }
 

@@ -25,6 +25,14 @@ namespace shd {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// temperature grid of the thermal Compton kernel: theta_i = 10^(kThermalLg0 +
+// i kThermalDlg), i < kThermalN; nodes blend their two bracketing tables
+// linearly in log10(theta) (clamped into the grid)
+constexpr double kThermalLg0 = -3.0, kThermalDlg = 0.25;
+constexpr int kThermalN = 13;
+// nodes per chunk of the thermal source pass (all of one bracket)
+constexpr int kThermalChunk = 1024;
+
 // Per-ordinate constants, built on the host in FP64 (Sec. 2.2 mesh; the
 // sweep geometry of the short characteristic).
 struct Ordinate {
@@ -86,6 +94,17 @@ struct Prob {
     int lgu;               // group centres equally spaced in log energy; then
     T lgidl;               // 1 / that spacing,
     T lgx0, lgx1;          // the outer edges in units of it, from lc[0]
+    // thermal electrons (SHD_SCAT_KN_THERMAL): per node its bracket on the
+    // temperature grid and the weight of the upper table; the kernels and
+    // out-scattering cross-sections on the grid; nodes grouped by bracket
+    int thermal;
+    const int *thb;        // [Nc]
+    const T *thw;          // [Nc]
+    const T *thK;          // [kThermalN][L+1][G][G]
+    const T *thso;         // [kThermalN][G]
+    const int *thperm;     // [Nc] node ids ordered by bracket
+    const int4 *thchunk;   // {first index into thperm, count, bracket, 0}
+    int nthchunk;
 };
 
 // Per-stage CUDA events recorded on the launching stream without any host
@@ -236,6 +255,15 @@ struct shd_ctx {
     int time_scheme = SHD_TIME_EULER;
     // source interpolation of the sweep (SHD_SC_LINEAR / SHD_SC_BEZIER)
     int integrator = SHD_SC_LINEAR;
+    // thermal electrons: the node temperatures as given (host, FP64), their
+    // brackets and weights, the nodes grouped by bracket, the kernels on the
+    // temperature grid in the working precision
+    bool have_theta = false;
+    std::vector<double> h_theta;
+    int *d_thb = nullptr, *d_thperm = nullptr;
+    void *d_thw = nullptr, *d_thK = nullptr, *d_thso = nullptr;
+    int4 *d_thchunk = nullptr;
+    int nthchunk = 0;
     void *d_rk[3] = {nullptr, nullptr, nullptr};
     double *d_sums_save = nullptr;  // [2]
 
@@ -739,6 +767,15 @@ cudaError_t launch_convert_back(const T *src, double *dst, long long n, cudaStre
 
 cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, double *d_sigma_out,
                             const double *d_gx, const double *d_gw, int nq, cudaStream_t st);
+// the thermal Compton kernels on the temperature grid (FP64): quad holds the
+// Gauss-Legendre nodes and weights of the electron speed, electron direction,
+// scattering cosine and incident energy rules (see k_kn_thermal_table)
+cudaError_t launch_kn_thermal_tables(int G, const double *d_edges, int L, const double *d_quad, double *d_K,
+                                     double *d_so, cudaStream_t st);
+// thermal source pass (a2 + the a5 partials over grid CTAs)
+template <class T>
+cudaError_t launch_source_thermal(const shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, const T *Sprev,
+                                  bool have_prev, int *grid_used, cudaStream_t st);
 
 // Ng acceleration: FP64 inner products of the last four source iterates
 // into out5 (part: nblk * 5 doubles of scratch), and the extrapolation

@@ -47,6 +47,14 @@ Prob<T> make_prob(const shd_ctx *c)
     p.lgidl = (T)(1.0 / c->lg_dl);
     p.lgx0 = c->G ? (T)((std::log(c->h_edges[0]) - c->lg_c0) / c->lg_dl) : T(0);
     p.lgx1 = c->G ? (T)((std::log(c->h_edges[c->G]) - c->lg_c0) / c->lg_dl) : T(0);
+    p.thermal = (c->scat_kind == SHD_SCAT_KN_THERMAL && c->have_theta && c->d_thK) ? 1 : 0;
+    p.thb = c->d_thb;
+    p.thw = (const T *)c->d_thw;
+    p.thK = (const T *)c->d_thK;
+    p.thso = (const T *)c->d_thso;
+    p.thperm = c->d_thperm;
+    p.thchunk = c->d_thchunk;
+    p.nthchunk = c->nthchunk;
     return p;
 }
 
@@ -69,7 +77,14 @@ __global__ void k_chi0(Prob<T> P, T *chi0)
     if (i >= n) return;
     long long c = i / P.G;
     int g = (int)(i % P.G);
-    chi0[i] = P.alpha0[i] + P.ne[c] * P.sigma_out[g];
+    T so = P.sigma_out[g];
+    if (P.thermal) {
+        // the node's blend of its two bracketing temperature tables
+        const int b = P.thb[c];
+        const T w = P.thw[c];
+        so = (T(1) - w) * P.thso[(size_t)b * P.G + g] + w * P.thso[(size_t)(b + 1) * P.G + g];
+    }
+    chi0[i] = P.alpha0[i] + P.ne[c] * so;
 }
 
 // chi0 in the three sweep layouts, chi0L[d][g][o] = chi0[c(o, d)][g]: at a
@@ -1118,6 +1133,217 @@ __global__ void k_rk_stage(T *__restrict__ I, const T *__restrict__ A, T *__rest
 }
 
 // -------------------------------------------------------------------------
+// Compton scattering off thermal electrons (the temperature field's reading
+// of Sec. 2.3): the kernel of a photon of energy eps (incident group g')
+// scattered through the laboratory cosine mu into group g, averaged over
+// isotropic Maxwell-Juttner electrons at temperature theta:
+//   K_l[g][g'] = (2 pi / de_g) Int_g' d eps Int d mu P_l(mu)
+//                < (dsigma/dOmega1)_e (eps1/eps) 1[eps1 in g] >_theta
+// with eps' = gamma eps (1 - beta mu_e), eps1 = eps (1 - beta mu_e) /
+// ((1 - beta mu_e1) + (eps/gamma)(1 - mu)), eps1' = gamma eps1 (1 - beta
+// mu_e1), 1 - cos T' = 1/eps1' - 1/eps', and (dsigma/dOmega1)_e = (1 - beta
+// mu_e) (3/16 pi) (eps1/eps')^2 (eps'/eps1' + eps1'/eps' - sin^2 T');
+// sigma_out[g'] = (1/de_g') Int_g' d eps <(1 - beta mu_e) sigma_KN(eps')>.
+// Product quadrature (FP64): TN_E points in ln(eps), TN_MU in mu, and over
+// the electrons TN_S in s = sqrt((gamma - 1)/theta) on [0, sqrt 40] (density
+// gamma^2 beta e^(-s^2) 2 theta s, normalised on the rule), TN_ME in their
+// direction cosine, TN_PHI azimuths at midpoints.  One CTA per (g', theta_i);
+// shared-memory atomics collect the contributions of every final group.
+// -------------------------------------------------------------------------
+constexpr int TN_E = 16, TN_MU = 48, TN_S = 24, TN_ME = 16, TN_PHI = 16;
+constexpr double TN_SMAX = 6.324555320336759;  // sqrt(40)
+
+__device__ inline double sigma_kn_total(double x)
+{
+    if (x < 1e-4) return 1.0 - 2.0 * x + 5.2 * x * x;
+    const double l = log1p(2.0 * x);
+    return 0.75 * ((1.0 + x) / (x * x * x) * (2.0 * x * (1.0 + x) / (1.0 + 2.0 * x) - l) + l / (2.0 * x) -
+                   (1.0 + 3.0 * x) / ((1.0 + 2.0 * x) * (1.0 + 2.0 * x)));
+}
+
+__global__ void __launch_bounds__(256) k_kn_thermal_table(int G, const double *__restrict__ edges, int L,
+                                                          const double *__restrict__ quad, double *Kth, double *soth)
+{
+    extern __shared__ double tsm[];
+    double *acc = tsm;                         // [L+1][G]
+    double *gam = acc + (size_t)(L + 1) * G;  // [TN_S]
+    double *bet = gam + TN_S;
+    double *wel = bet + TN_S;
+    double *tot = wel + TN_S;                 // [1]
+    const double *xs = quad, *ws = xs + TN_S, *xme = ws + TN_S, *wme = xme + TN_ME, *xmu = wme + TN_ME,
+                 *wmu = xmu + TN_MU, *xe = wmu + TN_MU, *we = xe + TN_E;
+    const int gp = blockIdx.x % G, it = blockIdx.x / G;
+    const double theta = pow(10.0, kThermalLg0 + it * kThermalDlg);
+    for (int i = threadIdx.x; i < (L + 1) * G; i += blockDim.x) acc[i] = 0.0;
+    if (threadIdx.x < TN_S) {
+        const int i = threadIdx.x;
+        const double sv = 0.5 * TN_SMAX * (xs[i] + 1.0);
+        gam[i] = 1.0 + theta * sv * sv;
+        bet[i] = sqrt(1.0 - 1.0 / (gam[i] * gam[i]));
+        wel[i] = 0.5 * TN_SMAX * ws[i] * gam[i] * gam[i] * bet[i] * exp(-sv * sv) * 2.0 * theta * sv;
+    }
+    if (threadIdx.x == 0) *tot = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < TN_S; ++i) sum += wel[i];
+        for (int i = 0; i < TN_S; ++i) wel[i] /= sum;
+    }
+    __syncthreads();
+    const double t0 = log(edges[gp]), t1 = log(edges[gp + 1]);
+    const double ht = 0.5 * (t1 - t0), mt = 0.5 * (t1 + t0);
+    // the out-scattering cross-section: (eps, electron speed) pairs per thread
+    for (int q = threadIdx.x; q < TN_E * TN_S; q += blockDim.x) {
+        const int ie = q / TN_S, is = q - ie * TN_S;
+        const double eps = exp(mt + ht * xe[ie]);
+        const double weps = we[ie] * ht * eps;
+        double a = 0.0;
+        for (int im = 0; im < TN_ME; ++im) {
+            const double f = 1.0 - bet[is] * xme[im];
+            a += 0.5 * wme[im] * f * sigma_kn_total(gam[is] * eps * f);
+        }
+        atomicAdd(tot, weps * wel[is] * a);
+    }
+    // the kernel: (eps, mu) pairs per thread, the electrons in a loop
+    double pl[16];
+    for (int q = threadIdx.x; q < TN_E * TN_MU; q += blockDim.x) {
+        const int ie = q / TN_MU, iu = q - ie * TN_MU;
+        const double eps = exp(mt + ht * xe[ie]);
+        const double weps = we[ie] * ht * eps;
+        const double mu = xmu[iu], smu = sqrt(1.0 - mu * mu);
+        pl[0] = 1.0;
+        if (L >= 1) pl[1] = mu;
+        for (int l = 2; l <= L; ++l) pl[l] = ((2.0 * l - 1.0) * mu * pl[l - 1] - (l - 1.0) * pl[l - 2]) / l;
+        for (int is = 0; is < TN_S; ++is) {
+            const double b = bet[is], gm = gam[is];
+            for (int im = 0; im < TN_ME; ++im) {
+                const double cme = xme[im], sme = sqrt(1.0 - cme * cme);
+                const double a = 1.0 - b * cme;
+                for (int ip = 0; ip < TN_PHI; ++ip) {
+                    const double phe = 2.0 * kPi * (ip + 0.5) / TN_PHI;
+                    const double mue1 = sme * cos(phe) * smu + cme * mu;
+                    const double eps1 = eps * a / ((1.0 - b * mue1) + (eps / gm) * (1.0 - mu));
+                    if (!(eps1 >= edges[0] && eps1 < edges[G])) continue;
+                    int lo = 0, hi = G - 1;  // the group holding eps1
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (edges[mid] <= eps1) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const double ep = gm * eps * a, e1p = gm * eps1 * (1.0 - b * mue1);
+                    const double ct = 1.0 - (1.0 / e1p - 1.0 / ep);
+                    const double r = eps1 / ep;
+                    double dsdo = a * 3.0 / (16.0 * kPi) * r * r * (ep / e1p + e1p / ep - (1.0 - ct * ct));
+                    dsdo *= eps1 / eps;
+                    const double wgt = weps * wmu[iu] * wel[is] * 0.5 * wme[im] / TN_PHI * dsdo;
+                    for (int l = 0; l <= L; ++l) atomicAdd(&acc[l * G + lo], wgt * pl[l]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const size_t per = (size_t)(L + 1) * G * G;
+    for (int i = threadIdx.x; i < (L + 1) * G; i += blockDim.x) {
+        const int l = i / G, g = i - l * G;
+        Kth[(size_t)it * per + ((size_t)l * G + g) * G + gp] = 2.0 * kPi * acc[i] / (edges[g + 1] - edges[g]);
+    }
+    if (threadIdx.x == 0) soth[(size_t)it * G + gp] = *tot / (edges[gp + 1] - edges[gp]);
+}
+
+// -------------------------------------------------------------------------
+// a2 (+ a5 partials) with thermal electrons: chunks of nodes of one
+// temperature bracket b; the CTA holds K of tables b and b+1, each warp
+// stages a node's I_lm and forms S_p = n_e/chi0 ((1 - w) sum_g' K_b I +
+// w sum_g' K_(b+1) I) + delta_p0 sqrt(4 pi) eta0/chi0 (w the node's weight
+// of the upper table), with the FP64 partial sums of k_source_sums.
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_source_thermal(Prob<T> P, const T *__restrict__ Ip, T *__restrict__ Sp,
+                                                        const T *__restrict__ mom, const T *__restrict__ Sprev,
+                                                        int have_prev, double *partial)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4][8];
+    const int G = P.G, NLM = P.NLM, L = P.L;
+    const int W = blockDim.x >> 5;
+    const size_t per = (size_t)(L + 1) * G * G;
+    T *Ka = reinterpret_cast<T *>(smem_raw);
+    T *Kb = Ka + per;
+    T *sI = Kb + per;  // [W][G][NLM]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *wI = sI + (size_t)warp * G * NLM;
+    double e = 0, ph = 0, num = 0, den = 0;
+    for (int ch = blockIdx.x; ch < P.nthchunk; ch += gridDim.x) {
+        const int4 cd = P.thchunk[ch];
+        __syncthreads();  // the previous chunk's tables are no longer read
+        for (size_t i = threadIdx.x; i < per; i += blockDim.x) {
+            Ka[i] = P.thK[(size_t)cd.z * per + i];
+            Kb[i] = P.thK[(size_t)(cd.z + 1) * per + i];
+        }
+        __syncthreads();
+        for (int j = warp; j < cd.y; j += W) {
+            const long long c = P.thperm[cd.x + j];
+            const long long base = c * G * NLM;
+            const T ne = P.ne[c], w = P.thw[c];
+            for (int i = lane; i < G * NLM; i += 32) wI[i] = Ip[base + i];
+            __syncwarp();
+            for (int p = lane; p < NLM; p += 32) {
+                int l = 0;
+                while ((l + 1) * (l + 1) <= p) ++l;
+                for (int g = 0; g < G; ++g) {
+                    const T chi = P.chi0[c * G + g];
+                    T s = T(0);
+                    if (chi > T(0)) {
+                        const T *ra = Ka + (size_t)l * G * G + (size_t)g * G, *rb = Kb + (size_t)l * G * G + (size_t)g * G;
+                        T aa = T(0), ab = T(0);
+                        for (int gp = 0; gp < G; ++gp) {
+                            const T v = wI[gp * NLM + p];
+                            aa += ra[gp] * v;
+                            ab += rb[gp] * v;
+                        }
+                        s = ne / chi * ((T(1) - w) * aa + w * ab);
+                        if (p == 0) s += T(3.5449077018110320546) * P.emis0[c * G + g] / chi;  // sqrt(4 pi)
+                    }
+                    const long long i = base + (long long)g * NLM + p;
+                    Sp[i] = s;
+                    const double sn = (double)s;
+                    den += sn * sn;
+                    if (have_prev) {
+                        const double d = sn - (double)Sprev[i];
+                        num += d * d;
+                    }
+                }
+            }
+            for (int g = lane; g < G; g += 32) {
+                const double J = (double)mom[(c * G + g) * 10];
+                const double de = P.edges[g + 1] - P.edges[g];
+                e += 4.0 * kPi * J * de;
+                ph += 4.0 * kPi * J * de / P.centre[g];
+            }
+            __syncwarp();
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_down_sync(0xffffffffu, e, o);
+        ph += __shfl_down_sync(0xffffffffu, ph, o);
+        num += __shfl_down_sync(0xffffffffu, num, o);
+        den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = e;
+        red[1][warp] = ph;
+        red[2][warp] = num;
+        red[3][warp] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double acc = 0;
+        for (int w = 0; w < W; ++w) acc += red[threadIdx.x][w];
+        partial[blockIdx.x * 4 + threadIdx.x] = acc;
+    }
+}
+
+// -------------------------------------------------------------------------
 // layout conversions
 // -------------------------------------------------------------------------
 template <class T>
@@ -1287,6 +1513,8 @@ cudaError_t launch_chi0(const shd_ctx *ctx, cudaStream_t st)
 template <class T>
 cudaError_t launch_source(const shd_ctx *ctx, const T *Ip, T *Sp, cudaStream_t st)
 {
+    if (ctx->scat_kind == SHD_SCAT_KN_THERMAL)
+        return launch_source_thermal<T>(ctx, Ip, Sp, (const T *)ctx->d_mom, Sp, false, nullptr, st);
     Prob<T> P = make_prob<T>(ctx);
     size_t sm = (size_t)ctx->G * ctx->NLM * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1680,6 +1908,8 @@ cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev,
     return cudaGetLastError();
 }
 
+static int source_thermal_warps(const shd_ctx *c, size_t *sm);
+
 static size_t source_sums_smem(const shd_ctx *c)
 {
     return c->esize * ((((size_t)(c->L + 1) * (c->G * c->G + 1)) + 1 & ~(size_t)1) + (size_t)8 * c->G * c->NLM);
@@ -1688,6 +1918,7 @@ static size_t source_sums_smem(const shd_ctx *c)
 template <class T>
 bool source_sums_usable(const shd_ctx *ctx)
 {
+    if (ctx->scat_kind == SHD_SCAT_KN_THERMAL) return source_thermal_warps(ctx, nullptr) > 0;
     return source_sums_smem(ctx) <= 227 * 1024;
 }
 
@@ -1696,6 +1927,14 @@ template <class T>
 cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, const T *Sprev, bool have_prev,
                                cudaStream_t st)
 {
+    if (ctx->scat_kind == SHD_SCAT_KN_THERMAL) {
+        int grid = 0;
+        cudaError_t e = launch_source_thermal<T>(ctx, Ip, Sp, mom, Sprev, have_prev, &grid, st);
+        if (e != cudaSuccess) return e;
+        k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, grid, have_prev ? 1 : 0, ctx->d_sums);
+        note_launch();
+        return cudaGetLastError();
+    }
     Prob<T> P = make_prob<T>(ctx);
     const size_t sm = source_sums_smem(ctx);
     auto kern = ctx->k_diagonal && ctx->G <= 32 ? k_source_sums<T, true> : k_source_sums<T, false>;
@@ -1804,6 +2043,47 @@ cudaError_t launch_kn_table(int G, const double *d_edges, int L, double *d_K, do
     return cudaGetLastError();
 }
 
+cudaError_t launch_kn_thermal_tables(int G, const double *d_edges, int L, const double *d_quad, double *d_K,
+                                     double *d_so, cudaStream_t st)
+{
+    const size_t sm = sizeof(double) * ((size_t)(L + 1) * G + 3 * TN_S + 1);
+    k_kn_thermal_table<<<(unsigned)(G * kThermalN), 256, sm, st>>>(G, d_edges, L, d_quad, d_K, d_so);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// warps per CTA of the thermal source pass: as many as shared memory allows
+static int source_thermal_warps(const shd_ctx *c, size_t *sm)
+{
+    const size_t per = (size_t)(c->L + 1) * c->G * c->G;
+    for (int w = 8; w >= 1; w >>= 1) {
+        const size_t b = c->esize * (2 * per + (size_t)w * c->G * c->NLM);
+        if (b <= 227 * 1024) {
+            if (sm) *sm = b;
+            return w;
+        }
+    }
+    return 0;
+}
+
+template <class T>
+cudaError_t launch_source_thermal(const shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, const T *Sprev,
+                                  bool have_prev, int *grid_used, cudaStream_t st)
+{
+    Prob<T> P = make_prob<T>(ctx);
+    size_t sm = 0;
+    const int W = source_thermal_warps(ctx, &sm);
+    if (W == 0 || !P.thermal) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(k_source_thermal<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int grid = ctx->nthchunk < ctx->n_partial ? ctx->nthchunk : ctx->n_partial;
+    if (grid < 1) grid = 1;
+    k_source_thermal<T><<<grid, 32 * W, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, ctx->d_partial);
+    note_launch();
+    if (grid_used) *grid_used = grid;
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_ng_dots(const T *x0, const T *x1, const T *x2, const T *x3, long long n, double *part, int nblk,
                            double *out5, cudaStream_t st)
@@ -1857,7 +2137,9 @@ cudaError_t launch_rk_stage(T *I, const T *A, T *B, T *acc, long long n, double 
     template cudaError_t launch_ng_combine<T>(T *, const T *, const T *, long long, double, double,         \
                                               cudaStream_t);                                                \
     template cudaError_t launch_rk_stage<T>(T *, const T *, T *, T *, long long, double, bool, bool,         \
-                                            cudaStream_t);
+                                            cudaStream_t);                                                  \
+    template cudaError_t launch_source_thermal<T>(const shd_ctx *, const T *, T *, const T *, const T *,     \
+                                                  bool, int *, cudaStream_t);
 
 SHD_INSTANTIATE(double)
 SHD_INSTANTIATE(float)

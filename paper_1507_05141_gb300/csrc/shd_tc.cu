@@ -925,7 +925,8 @@ static int source_tc_tn(const shd_ctx *c, size_t *smem)
 
 bool source_tc_usable(const shd_ctx *c)
 {
-    return c->precision == SHD_MIXED && !c->k_diagonal && c->G <= 256 && c->d_tcK && source_tc_tn(c, nullptr) > 0;
+    return c->precision == SHD_MIXED && !c->k_diagonal && c->scat_kind != SHD_SCAT_KN_THERMAL && c->G <= 256 &&
+           c->d_tcK && source_tc_tn(c, nullptr) > 0;
 }
 
 cudaError_t launch_source_tc_operands(shd_ctx *c, cudaStream_t st)

@@ -265,10 +265,12 @@ def random_state(spec: ProblemSpec, seed=12345, scale=1.0, layout="cgk"):
     return I
 
 
-def ragged_mixed(grid=(11, 9, 7), G=5, L=3, gmax=3.0, seed=None, index=7, scattering="thomson"):
+def ragged_mixed(grid=(11, 9, 7), G=5, L=3, gmax=3.0, seed=None, index=7, scattering="thomson", theta_range=None):
     """A small non-cubic problem with flow, absorption, emission and
     scattering, for element-by-element parity on sizes that leave ragged
-    tiles.  Velocity: a tilted jet plus a weak random component."""
+    tiles.  Velocity: a tilted jet plus a weak random component.  With
+    theta_range = (lo, hi) the nodes also get electron temperatures
+    log-uniform in [lo, hi] (extra["theta_e"])."""
     rng = _rng(index, seed)
     nx, ny, nz = grid
     hx, hy, hz = 1.0 / (nx - 1), 1.2 / (ny - 1), 0.9 / (nz - 1)
@@ -291,8 +293,12 @@ def ragged_mixed(grid=(11, 9, 7), G=5, L=3, gmax=3.0, seed=None, index=7, scatte
     alpha0 = 0.5 * np.exp(0.3 * rng.standard_normal((Nc, G)))
     emis0 = (1.0 + rng.random((Nc, 1))) * centre[None, :] ** -0.5
     nmu, nphi = ordinate_counts(L)
+    extra = {}
+    if theta_range is not None:
+        lo, hi = np.log10(theta_range[0]), np.log10(theta_range[1])
+        extra["theta_e"] = 10.0 ** rng.uniform(lo, hi, Nc)
     return ProblemSpec("ragged_mixed", grid, (1.0, 1.2, 0.9), L, nmu, nphi, edges, alpha0, ne, u,
-                       emis0, scattering, kappa=1.0 / (0.5 * hx), steps=3)
+                       emis0, scattering, kappa=1.0 / (0.5 * hx), steps=3, extra=extra)
 
 
 # ----------------------------------------------------------------------------

@@ -16,12 +16,14 @@ from . import build as _build
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NAN, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 FP64, FP32, MIXED = 0, 1, 2
-SCAT_ISO, SCAT_THOMSON, SCAT_KN, SCAT_TABLE = 1, 2, 3, 4
+SCAT_ISO, SCAT_THOMSON, SCAT_KN, SCAT_TABLE, SCAT_KN_THERMAL = 1, 2, 3, 4, 5
+THERMAL_N = 13  # temperature grid of the thermal kernel: 10^(-3 + i/4)
 BC_VACUUM, BC_ISO, BC_FULL = 0, 1, 2
 TIME_EULER, TIME_RK4 = 0, 1
 SC_LINEAR, SC_BEZIER = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
-SCATTERING = {"iso": SCAT_ISO, "thomson": SCAT_THOMSON, "kn": SCAT_KN, "table": SCAT_TABLE}
+SCATTERING = {"iso": SCAT_ISO, "thomson": SCAT_THOMSON, "kn": SCAT_KN, "table": SCAT_TABLE,
+              "kn_thermal": SCAT_KN_THERMAL}
 STAGES = ("project", "source", "sums", "sh2lab", "sweep")
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -37,7 +39,8 @@ _SIGS = {
     "shd_set_grid": (_i, [_vp, _i, _i, _i, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "shd_set_angles": (_i, [_vp, _i, _i, _i]),
     "shd_set_groups": (_i, [_vp, _i, _dp]),
-    "shd_set_fields": (_i, [_vp, _dp, _dp, _dp, _dp]),
+    "shd_set_fields": (_i, [_vp, _dp, _dp, _dp, _dp, _dp]),
+    "shd_get_thermal_tables": (_i, [_vp, _dp, _dp]),
     "shd_set_scattering": (_i, [_vp, _i, _dp, _dp]),
     "shd_get_scattering": (_i, [_vp, _dp, _dp]),
     "shd_set_boundary": (_i, [_vp, _i, _dp]),
@@ -189,14 +192,22 @@ class Solver:
         _check(self._L.shd_set_groups(self._h, len(e) - 1, _ptr(e)))
         self.G = len(e) - 1
 
-    def set_fields(self, alpha0, ne, u, emis0):
+    def set_fields(self, alpha0, ne, u, emis0, theta_e=None):
         a, n, uu, em = _f64(alpha0), _f64(ne), _f64(u), _f64(emis0)
-        _check(self._L.shd_set_fields(self._h, _ptr(a), _ptr(n), _ptr(uu), _ptr(em)))
+        th = _f64(theta_e) if theta_e is not None else None
+        _check(self._L.shd_set_fields(self._h, _ptr(a), _ptr(n), _ptr(uu), _ptr(em), _ptr(th)))
 
     def set_scattering(self, kind, K=None, sigma_out=None):
         k = SCATTERING[kind] if isinstance(kind, str) else int(kind)
         K_, s_ = _f64(K), _f64(sigma_out)
         _check(self._L.shd_set_scattering(self._h, k, _ptr(K_), _ptr(s_)))
+
+    def get_thermal_tables(self):
+        """(K_th [13][L+1][G][G], sigma_out_th [13][G]) of the thermal kernel."""
+        K = np.zeros((THERMAL_N, self.L + 1, self.G, self.G))
+        s = np.zeros((THERMAL_N, self.G))
+        _check(self._L.shd_get_thermal_tables(self._h, _ptr(K), _ptr(s)))
+        return K, s
 
     def get_scattering(self):
         K = np.zeros((self.L + 1, self.G, self.G))
@@ -248,7 +259,7 @@ class Solver:
         s.set_angles(spec.L, spec.nmu, spec.nphi)
         s.set_groups(spec.edges)
         s.set_scattering(scattering or spec.scattering)
-        s.set_fields(spec.alpha0, spec.ne, spec.u, spec.emis0)
+        s.set_fields(spec.alpha0, spec.ne, spec.u, spec.emis0, spec.extra.get("theta_e"))
         s.set_time(spec.kappa)
         return s
 
