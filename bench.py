@@ -443,16 +443,12 @@ def _errors_vs_oracle(spec_small, precision, device, steps=3, scattering=None):
     spec = spec_small
     kind = scattering or spec.scattering
     I0 = inputs.random_state(spec, seed=11)
-    s = native.Solver.from_spec(spec, device=device, precision=precision)
+    s = native.Solver.from_spec(spec, device=device, precision=precision, scattering=kind)
     s.set_state(I0)
     s.step(steps)
     J, H, K, Ish = s.moments(with_sh=True)
     s.close()
-    Kt, so = {"thomson": lambda: O.thomson_table(spec.G, spec.L), "iso": lambda: O.iso_table(spec.G, spec.L),
-              "kn": lambda: O.kn_table(spec.edges, spec.L)}[kind]()
-    P = O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
-                        alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=Kt, sigma_out=so,
-                        kappa=spec.kappa, box=spec.box)
+    P = _oracle_problem(spec, kind)
     Ir, _, _ = P.step(I0, steps)
     Ish_r, J_r, H_r, K_r = P.project(Ir)
     Jd = np.maximum(np.abs(J_r), 1e-300)
@@ -465,16 +461,30 @@ def _errors_vs_oracle(spec_small, precision, device, steps=3, scattering=None):
                     f"{spec.N} ordinates, {steps} steps"}
 
 
-def _oracle_rate(spec, steps, scattering=None):
-    """The FP64 oracle's updates/s on `spec` over `steps` steps (host cores)."""
+def _oracle_problem(spec, kind):
+    """The FP64 oracle's problem for spec with scattering `kind` (thermal
+    electrons: the kernels on the library's temperature grid and the
+    recipe's temperature field)."""
     from oracle import oracle as O
-    from paper_1507_05141_gb300 import inputs
-    kind = scattering or spec.scattering
+    if kind == "kn_thermal":
+        Kth, soth = O.thermal_tables(spec.edges, spec.L)
+        th = {"theta_e": spec.extra["theta_e"], "K_th": Kth, "so_th": soth, "lg0": O.THERMAL_LG0,
+              "dlg": O.THERMAL_DLG}
+        return O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
+                               alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=Kth[0],
+                               sigma_out=soth[0], kappa=spec.kappa, box=spec.box, thermal=th)
     Kt, so = {"thomson": lambda: O.thomson_table(spec.G, spec.L), "iso": lambda: O.iso_table(spec.G, spec.L),
               "kn": lambda: O.kn_table(spec.edges, spec.L)}[kind]()
-    P = O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
-                        alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=Kt, sigma_out=so,
-                        kappa=spec.kappa, box=spec.box)
+    return O.OracleProblem(grid=spec.grid, L=spec.L, nmu=spec.nmu, nphi=spec.nphi, edges=spec.edges,
+                           alpha0=spec.alpha0, ne=spec.ne, u=spec.u, emis0=spec.emis0, K=Kt, sigma_out=so,
+                           kappa=spec.kappa, box=spec.box)
+
+
+def _oracle_rate(spec, steps, scattering=None):
+    """The FP64 oracle's updates/s on `spec` over `steps` steps (host cores;
+    the scattering tables are set up before the clock starts)."""
+    from paper_1507_05141_gb300 import inputs
+    P = _oracle_problem(spec, scattering or spec.scattering)
     I = inputs.random_state(spec, seed=1)
     t0 = time.perf_counter()
     P.step(I, steps)
@@ -605,10 +615,11 @@ def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spe
     from paper_1507_05141_gb300 import native
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    s = native.Solver.from_spec(spec, device=dev.index, precision=prec)
+    s = native.Solver.from_spec(spec, device=dev.index, precision=prec, scattering=scattering)
     s.zero_state()
     ms, stage, clk, launches = time_steps(s, spec, args.steps, args.warmup, stream, dev, lambda: None)
     sched = _sched(s)
+    src_path = s.source_path()
     upd = spec.updates_per_step
     value = upd * args.steps / (ms / 1e3)
 
@@ -636,7 +647,7 @@ def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spe
     torch.cuda.empty_cache()
     plain = None
     if plain_prec:
-        p = native.Solver.from_spec(spec, device=dev.index, precision=plain_prec)
+        p = native.Solver.from_spec(spec, device=dev.index, precision=plain_prec, scattering=scattering)
         p.zero_state()
         ms32, stage32, _, _ = time_steps(p, spec, args.steps, args.warmup, stream, dev, lambda: None)
         p.close()
@@ -657,6 +668,9 @@ def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spe
                          f"{cpu_spec.G} ({cpu_spec.updates_per_step:.3g} updates, {dt:.1f} s)"}
     e2e = {"value": upd * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "steps": e2e_steps}
+    extra = dict(extra)
+    extra["source_pass"] = {"path": {0: "untimed", 1: "CUDA cores", 2: "tensor cores"}[src_path[0]],
+                            "ms_cuda_cores": src_path[1], "ms_tensor_cores": src_path[2]}
     return _line(args, workload=workload, spec=spec, prec=prec, value=value, ms_step=ms / args.steps, stage=stage,
                  sched=sched, extra_config=extra, errors=errors, e2e=e2e, launches=launches, clk=clk, cpu=cpu,
                  sweep_ms=stage.get("sweep"), plain=plain, notes=notes)
@@ -669,12 +683,17 @@ def bench_config3(args, dev):
     free, _ = torch.cuda.mem_get_info(dev)
     spec, G = _fit_groups(lambda g: inputs.compton_shell(G=g), 32, free)
     note = None if G == 32 else f"G reduced from 32 to {G} to fit the device memory (stated deviation)"
+    kind = "kn_thermal" if args.thermal else "kn"
+    what = ("Compton scattering off thermal electrons at the recipe's temperature field" if args.thermal
+            else "cold Klein-Nishina")
     return bench_single(args, dev, spec=spec, prec="mixed",
                         workload=f"Compton shell 96^3, {G} groups (1e-4..1e2 m_e c^2), L=7, 16x32 ordinates, "
-                                 f"cold Klein-Nishina, shell flow Gamma 2..5",
-                        extra={"config": 3, "l2": "no flush: the intensity state is far larger than L2"},
-                        errors_spec=inputs.compton_shell(n=16, G=8), cpu_spec=inputs.compton_shell(n=20, G=G),
-                        plain_prec=None if args.no_compare else "fp32", notes=note)
+                                 f"{what}, shell flow Gamma 2..5",
+                        extra={"config": 3, "scattering": kind,
+                               "l2": "no flush: the intensity state is far larger than L2"},
+                        errors_spec=inputs.compton_shell(n=16, G=8),
+                        cpu_spec=inputs.compton_shell(n=20, G=8 if args.thermal else G),
+                        plain_prec=None if args.no_compare else "fp32", scattering=kind, notes=note)
 
 
 def bench_config5(args, dev):
@@ -802,6 +821,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 arm of a mixed run")
     ap.add_argument("--no-errors", action="store_true", help="skip the per-field error check against the oracle")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--thermal", action="store_true",
+                    help="config 3 with Compton scattering off thermal electrons (the temperature field's kernel)")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end leg (profiling: every launch then is a direct launch)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
