@@ -533,23 +533,22 @@ done:
 // -------------------------------------------------------------------------
 // a2 on tensor cores for kernels that mix groups (Klein-Nishina, Sec. 2.3
 // eq:comptoncross): S_lm(c, g) = n_e/chi0 sum_g' K_l[g][g'] I_lm(c, g') + T.
-// For each l the 2l+1 harmonics of a tile of TN nodes form the rows of one
-// MMA, D_l[(node, m), g] = sum_g' I(node, g', l, m) K_l[g][g']: M = 128 rows
-// (TN (2l+1) <= 128 used), K = G' padded to Kp, N = G padded to Gp.
-// Precision: the sums over g' cancel for l >= 1 and the spectra span many
-// decades, so each FP32 operand is split into three BF16 pieces x = hi +
-// mid + lo (24 significant bits) and the six products of order <= 2 (hi.hi,
-// hi.mid, mid.hi, hi.lo, lo.hi, mid.mid) accumulate in FP32 in tensor
-// memory: the dropped terms are below 2^-24 of each product, as in FP32.
-// Flow per tile: the tile's I_lm block [TN][G][NLM] arrives by one bulk copy
-// (or plain loads when its size is not a multiple of 16 bytes); the l loop is
-// software-pipelined over two operand buffers and two accumulators (l+1's
-// operands are built while l's MMAs run); each l's results overwrite that
-// l's entries of the block; then the block is finished exactly as
-// k_source_sums finishes a node (n_e/chi0, emission in p = 0, zero where
-// chi0 = 0) and written, with the step's FP64 partial sums.  One thread
-// issues the MMAs and copies; every wait is bounded (on timeout: *err
-// raised, what was issued drained, tensor memory freed).
+// A tile of TN nodes has, for each l, TN (2l+1) rows (node, m); they are
+// taken 128 at a time ("chunks", l by l), each chunk one MMA group
+// D[(node, m), g] = sum_g' I(node, g', l, m) K_l[g][g']  (M = 128, K = G'
+// padded to Kp, N = G padded to Gp).  Precision: the sums over g' cancel for
+// l >= 1 and the spectra span many decades, so each FP32 operand is split
+// into three BF16 pieces x = hi + mid + lo (24 significant bits) and the six
+// products of order <= 2 (hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid)
+// accumulate in FP32 in tensor memory: the dropped terms are below 2^-24 of
+// each product, as in FP32.  A chunk's operands are built straight from
+// I_lm in global memory (every element is read once) while the previous
+// chunk's products run (two operand buffers, two accumulators); its
+// epilogue finishes S exactly as k_source_sums does (n_e/chi0, emission in
+// p = 0, zero where chi0 = 0), stores it and adds the step's FP64 partial
+// sums.  Nothing of the tile is staged beyond the operands, so two CTAs
+// share an SM.  One thread issues the MMAs; every wait is bounded (on
+// timeout: *err raised, what was issued drained, tensor memory freed).
 // -------------------------------------------------------------------------
 __device__ inline void split3_bf16x2(float a, float b, uint32_t &hi, uint32_t &mid, uint32_t &lo)
 {
@@ -563,18 +562,8 @@ __device__ inline void split3_bf16x2(float a, float b, uint32_t &hi, uint32_t &m
     lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
 }
 
-// bulk copy global -> shared (16-byte aligned ends, size a multiple of 16),
-// completion counted in bytes on `bar`
-__device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     tc::smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
-                 : "memory");
-}
-
 template <int TN>
-__global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float *__restrict__ Ip,
+__global__ void __launch_bounds__(256, 2) k_source_tc(Prob<float> P, const float *__restrict__ Ip,
                                                       float *__restrict__ Sp, const float *__restrict__ mom,
                                                       const float *__restrict__ Sprev, int have_prev,
                                                       const uint16_t *__restrict__ gK, int Gp, int Kp,
@@ -582,17 +571,16 @@ __global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int L = P.L, G = P.G, NLM = P.NLM;
-    const size_t kblk = (size_t)Gp * Kp;       // elements of one l's operand piece
+    const size_t kblk = (size_t)Gp * Kp;         // elements of one l's operand piece
     const size_t kall = (size_t)(L + 1) * kblk;  // one piece of every l
     const size_t ablk = (size_t)128 * Kp;
-    uint16_t *Kop = reinterpret_cast<uint16_t *>(smem_raw);  // [3 pieces][L+1][Gp][Kp]
-    uint16_t *Aop = Kop + 3 * kall;                          // [2 buffers][3 pieces][128][Kp]
-    float *blk = reinterpret_cast<float *>(Aop + 6 * ablk);  // [TN][G][NLM]
-    float *rat = blk + (size_t)TN * G * NLM;                 // [TN][G] n_e/chi0 (0 where chi0 = 0)
-    float *emt = rat + (size_t)TN * G;                       // [TN][G] sqrt(4 pi) eta0/chi0 (0 there too)
+    uint16_t *Kop = reinterpret_cast<uint16_t *>(smem_raw);   // [3 pieces][L+1][Gp][Kp]
+    uint16_t *Aop = Kop + 3 * kall;                           // [2 buffers][3 pieces][128][Kp]
+    float *rat = reinterpret_cast<float *>(Aop + 6 * ablk);   // [TN][G] n_e/chi0 (0 where chi0 = 0)
+    float *emt = rat + (size_t)TN * G;                        // [TN][G] sqrt(4 pi) eta0/chi0 (0 there too)
     const size_t tail = ((size_t)(reinterpret_cast<unsigned char *>(emt + (size_t)TN * G) - smem_raw) + 7) & ~(size_t)7;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + tail);  // [2] MMA completion, [2] block copy
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 3);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + tail);  // [2] MMA completion
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
     __shared__ double red[4][8];
 
@@ -606,7 +594,6 @@ __global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float
     if (tid == 0) {
         tc::mbar_init(&bar[0], 1);
         tc::mbar_init(&bar[1], 1);
-        tc::mbar_init(&bar[2], 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -618,25 +605,30 @@ __global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float
     const uint32_t tmem = *tslot;
     const uint32_t sbo = (Kp / 8) * 128;
     const uint32_t idesc = tc::idesc_bf16(128, Gp);
-    uint32_t mphase[2] = {0, 0}, cphase = 0;
-    bool mpend[2] = {false, false}, cpend = false;
+    uint32_t mphase[2] = {0, 0};
+    bool mpend[2] = {false, false};
     double e_sum = 0, ph_sum = 0, num = 0, den = 0;
     const long long ntiles = (P.Nc + TN - 1) / TN;
-    const bool bulk = ((size_t)G * NLM * 4) % 16 == 0;
+    const size_t nstride = (size_t)G * NLM;  // floats per node in I_lm / S_lm
 
-    // operands of l into buffer b: row r = (node r / (2l+1), p = l^2 + r % (2l+1)),
-    // column g'; a warp's threads take consecutive rows (consecutive p)
-    auto build = [&](int l, int nn, int b) {
-        const int nm = 2 * l + 1, rows = nn * nm, p0 = l * l;
+    // chunk q of l: rows q*128 + r, r < 128, of the tile's (node, m) rows
+    // (node = row / (2l+1), p = l^2 + row % (2l+1)); nch(l) chunks per l
+    auto nch = [&](int l, int nn) { return (nn * (2 * l + 1) + 127) / 128; };
+    // operands of (l, q) into buffer b, straight from I_lm: a warp's threads
+    // take consecutive rows (consecutive p within a node)
+    auto build = [&](long long c0, int nn, int l, int q, int b) {
+        const int nm = 2 * l + 1, rows = nn * nm, p0 = l * l, r0 = q * 128;
         uint16_t *Ah = Aop + (size_t)(3 * b) * ablk, *Am = Ah + ablk, *Al = Am + ablk;
+#pragma unroll 4
         for (int e = tid; e < 128 * (Kp / 2); e += 256) {
             const int r = e & 127, kk = 2 * (e >> 7);
             float v0 = 0.f, v1 = 0.f;
-            if (r < rows) {
-                const int node = r / nm, p = p0 + (r - node * nm);
-                const float *bp = blk + (size_t)node * G * NLM + p;
-                if (kk < G) v0 = bp[(size_t)kk * NLM];
-                if (kk + 1 < G) v1 = bp[(size_t)(kk + 1) * NLM];
+            const int row = r0 + r;
+            if (row < rows) {
+                const int node = row / nm, p = p0 + (row - node * nm);
+                const float *bp = Ip + (size_t)(c0 + node) * nstride + p;
+                if (kk < G) v0 = __ldg(bp + (size_t)kk * NLM);
+                if (kk + 1 < G) v1 = __ldg(bp + (size_t)(kk + 1) * NLM);
             }
             uint32_t hi, mid, lo;
             split3_bf16x2(v0, v1, hi, mid, lo);
@@ -646,7 +638,7 @@ __global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float
             *reinterpret_cast<uint32_t *>(&Al[o]) = lo;
         }
     };
-    // the six products of l's operands (buffer b) with K_l into accumulator b
+    // the six products of buffer b's operands with K_l into accumulator b
     auto issue = [&](int l, int b) {
         tc::fence_after_sync();
         const uint32_t a0 = tc::smem_u32(Aop + (size_t)(3 * b) * ablk);
@@ -658,139 +650,99 @@ __global__ void __launch_bounds__(256, 1) k_source_tc(Prob<float> P, const float
         for (int j = 0; j < Kp / 16; ++j) {
             const uint32_t koff = j * 256;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                const uint64_t da = tc::sdesc(ap[pa[q]] + koff, 128, sbo), db = tc::sdesc(kp[pb[q]] + koff, 128, sbo);
-                tc::mma_bf16(d, da, db, idesc, (j > 0 || q > 0) ? 1u : 0u);
+            for (int qq = 0; qq < 6; ++qq) {
+                const uint64_t da = tc::sdesc(ap[pa[qq]] + koff, 128, sbo), db = tc::sdesc(kp[pb[qq]] + koff, 128, sbo);
+                tc::mma_bf16(d, da, db, idesc, (j > 0 || qq > 0) ? 1u : 0u);
             }
         }
         tc::mma_commit(&bar[b]);
     };
-    // accumulator b of l back into l's entries of the block
-    auto epilogue = [&](int l, int nn, int b) {
+    // accumulator b of (l, q): S = n_e/chi0 D + emission (p = 0) straight to
+    // S_lm, with the partial sums of |S|^2 and |S - S_prev|^2
+    auto epilogue = [&](long long c0, int nn, int l, int q, int b) {
         const int nm = 2 * l + 1, rows = nn * nm, p0 = l * l;
         // warps w and w+4 share tensor-memory lanes 32 (w % 4) ..; they split the columns
         const int quad = warp & 3, half = warp >> 2;
-        const int r = quad * 32 + lane;
-        const bool valid = r < rows;
-        const int node = valid ? r / nm : 0, p = p0 + (valid ? r - node * nm : 0);
-        float *bp = blk + (size_t)node * G * NLM + p;
+        const int r = quad * 32 + lane, row = q * 128 + r;
+        const bool valid = row < rows;
+        const int node = valid ? row / nm : 0, p = p0 + (valid ? row - node * nm : 0);
+        const size_t obase = (size_t)(c0 + node) * nstride + p;
         const int cb = half * (Gp / 2), ce = half ? Gp : Gp / 2;
         for (int cc = cb; cc < ce; cc += 16) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * acc_cols + (uint32_t)cc, v);
             if (!valid) continue;
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (cc + j < G) bp[(size_t)(cc + j) * NLM] = v[j];
+            for (int j = 0; j < 16; ++j) {
+                const int g = cc + j;
+                if (g >= G) break;
+                float sv = rat[node * G + g] * v[j];
+                if (p == 0) sv += emt[node * G + g];
+                const size_t o = obase + (size_t)g * NLM;
+                Sp[o] = sv;
+                den += (double)sv * sv;
+                if (have_prev) {
+                    const double dd = (double)sv - (double)Sprev[o];
+                    num += dd * dd;
+                }
+            }
         }
     };
 
     for (long long w = blockIdx.x; w < ntiles; w += gridDim.x) {
         const long long c0 = w * TN;
         const int nn = (int)(P.Nc - c0 < TN ? P.Nc - c0 : TN);
-        const long long gbase = c0 * G * NLM;
-        const int nblk = nn * G * NLM;
-        // the block: one bulk copy (the previous tile's generic accesses are
-        // ordered before it by the proxy fence and the barrier at its end)
-        if (bulk) {
-            if (tid == 0) {
-                tc::mbar_arrive_expect_tx(&bar[2], (uint32_t)nblk * 4u);
-                bulk_g2s(blk, Ip + gbase, (uint32_t)nblk * 4u, &bar[2]);
-            }
-            cpend = true;
-        } else {
-            for (int i = tid; i < nblk; i += 256) blk[i] = Ip[gbase + i];
-        }
         for (int i = tid; i < nn * G; i += 256) {
             const long long c = c0 + i / G;
             const float chi = P.chi0[c * G + (i % G)];
             rat[i] = chi > 0.f ? P.ne[c] / chi : 0.f;
             emt[i] = chi > 0.f ? 3.5449077018110320546f * P.emis0[c * G + (i % G)] / chi : 0.f;  // sqrt(4 pi)
+            const int g = i % G;
+            const double J = (double)mom[(c * G + g) * 10];
+            const double de = P.edges[g + 1] - P.edges[g];
+            e_sum += 4.0 * kPi * J * de;
+            ph_sum += 4.0 * kPi * J * de / P.centre[g];
         }
-        if (bulk) {
-            if (!cta_wait(&bar[2], cphase, abort_flag)) goto drain;
-            cphase ^= 1;
-            cpend = false;
-        } else {
-            __syncthreads();
-        }
-        build(0, nn, 0);
+        // the tile's chunks in order (l, q), software-pipelined: chunk i+1's
+        // operands are built while chunk i's products run
+        int l = 0, q = 0, b = 0;
+        build(c0, nn, 0, 0, 0);
         tc::fence_proxy_async();
-        __syncthreads();
+        __syncthreads();  // also makes rat / emt visible
         if (tid == 0) issue(0, 0);
         mpend[0] = true;
-        for (int l = 0; l <= L; ++l) {
-            const int b = l & 1;
-            if (l + 1 <= L) build(l + 1, nn, b ^ 1);  // accumulator b ^ 1 was drained at l - 1
+        while (true) {
+            // next chunk after (l, q)
+            int ln = l, qn = q + 1;
+            if (qn >= nch(l, nn)) { ln = l + 1; qn = 0; }
+            const bool more = ln <= L;
+            if (more) build(c0, nn, ln, qn, b ^ 1);  // accumulator b ^ 1 was drained by the previous epilogue
             tc::fence_proxy_async();
             tc::fence_before_sync();
             __syncthreads();
-            if (l + 1 <= L) {
-                if (tid == 0) issue(l + 1, b ^ 1);
+            if (more) {
+                if (tid == 0) issue(ln, b ^ 1);
                 mpend[b ^ 1] = true;
             }
             if (!cta_wait(&bar[b], mphase[b], abort_flag)) goto drain;
             mphase[b] ^= 1;
             mpend[b] = false;
             tc::fence_after_sync();
-            epilogue(l, nn, b);
+            epilogue(c0, nn, l, q, b);
             tc::fence_before_sync();
+            if (!more) break;
+            l = ln;
+            q = qn;
+            b ^= 1;
         }
-        __syncthreads();
-        // finish: S = n_e/chi0 D + emission (p = 0), the FP64 partial sums
-        if ((NLM & 3) == 0) {
-            const float4 *b4 = reinterpret_cast<const float4 *>(blk);
-            float4 *s4 = reinterpret_cast<float4 *>(Sp + gbase);
-            const float4 *q4 = reinterpret_cast<const float4 *>(Sprev + gbase);
-            const int n4 = nblk / 4;
-#pragma unroll 4
-            for (int i = tid; i < n4; i += 256) {
-                const int ng = (4 * i) / NLM, p = 4 * i - ng * NLM;
-                const float r_ = rat[ng];
-                float4 v = b4[i];
-                v.x = r_ * v.x + (p == 0 ? emt[ng] : 0.f);
-                v.y *= r_;
-                v.z *= r_;
-                v.w *= r_;
-                s4[i] = v;
-                den += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
-                if (have_prev) {
-                    const float4 q = q4[i];
-                    const double d0 = (double)v.x - q.x, d1 = (double)v.y - q.y, d2 = (double)v.z - q.z,
-                                 d3 = (double)v.w - q.w;
-                    num += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
-                }
-            }
-        } else {
-            for (int i = tid; i < nblk; i += 256) {
-                const int ng = i / NLM, p = i - ng * NLM;
-                float sv = rat[ng] * blk[i];
-                if (p == 0) sv += emt[ng];
-                Sp[gbase + i] = sv;
-                den += (double)sv * sv;
-                if (have_prev) {
-                    const double d = (double)sv - (double)Sprev[gbase + i];
-                    num += d * d;
-                }
-            }
-        }
-        for (int i = tid; i < nn * G; i += 256) {
-            const int g = i % G;
-            const double J = (double)mom[(c0 * G + i) * 10];
-            const double de = P.edges[g + 1] - P.edges[g];
-            e_sum += 4.0 * kPi * J * de;
-            ph_sum += 4.0 * kPi * J * de / P.centre[g];
-        }
-        tc::fence_proxy_async();  // generic accesses to the block before the next bulk copy
-        __syncthreads();
+        __syncthreads();  // rat / emt are rewritten by the next tile
     }
     goto done;
 drain:
     if (threadIdx.x == 0) {
         atomicExch(err, 1);
-        for (int b = 0; b < 2; ++b)
-            if (mpend[b]) tc::mbar_wait(&bar[b], mphase[b], kWaitLimit);
-        if (cpend) tc::mbar_wait(&bar[2], cphase, kWaitLimit);
+        for (int bb = 0; bb < 2; ++bb)
+            if (mpend[bb]) tc::mbar_wait(&bar[bb], mphase[bb], kWaitLimit);
     }
 done:
     // fixed-order reduction of the partial sums: lanes, then the 8 warps
@@ -810,7 +762,7 @@ done:
     __syncthreads();
     if (tid < 4) {
         double acc = 0;
-        for (int q = 0; q < 8; ++q) acc += red[tid][q];
+        for (int qq = 0; qq < 8; ++qq) acc += red[tid][qq];
         partial[blockIdx.x * 4 + tid] = acc;
     }
     if (warp == 0) tc::tmem_dealloc(tmem, 2 * acc_cols);
@@ -906,21 +858,18 @@ cudaError_t launch_sh2lab_tc(const shd_ctx *ctx, const float *Sp, float *eta, fl
 
 static int round16(int x) { return (x + 15) / 16 * 16; }
 
-// Nodes per tile of k_source_tc: 8 where the rows of every l fit one MMA and
-// the shared memory allows, else 4, 2, 1; 0 when it cannot run.
+// Nodes per tile of k_source_tc and its shared memory: operands of every l
+// (three pieces), two operand buffers, the tile's n_e/chi0 and emission; 0
+// when that exceeds what two CTAs per SM can share (113 KB each).
 static int source_tc_tn(const shd_ctx *c, size_t *smem)
 {
     const int Gp = round16(c->G), Kp = round16(c->G);
-    for (int tn : {8, 4, 2, 1}) {
-        if (tn * (2 * c->L + 1) > 128) continue;
-        const size_t sm = (size_t)3 * (c->L + 1) * Gp * Kp * 2 + (size_t)6 * 128 * Kp * 2 +
-                          (size_t)tn * c->G * c->NLM * 4 + (size_t)2 * tn * c->G * 4 + 8 + 3 * 8 + 16;
-        if (sm <= 220 * 1024) {
-            if (smem) *smem = sm;
-            return tn;
-        }
-    }
-    return 0;
+    const int tn = 64;
+    const size_t sm = (size_t)3 * (c->L + 1) * Gp * Kp * 2 + (size_t)6 * 128 * Kp * 2 + (size_t)2 * tn * c->G * 4 +
+                      8 + 2 * 8 + 16;
+    if (sm > 113 * 1024) return 0;  // two CTAs and their 1 KB reservations fill the SM's 228 KB
+    if (smem) *smem = sm;
+    return tn;
 }
 
 bool source_tc_usable(const shd_ctx *c)
@@ -965,10 +914,7 @@ cudaError_t launch_source_sums_tc(shd_ctx *c, const float *Ip, float *Sp, const 
                                             c->d_partial, c->d_tc_err);                                       \
         break;
     switch (tn) {
-        SHD_SRC_TC(8)
-        SHD_SRC_TC(4)
-        SHD_SRC_TC(2)
-        SHD_SRC_TC(1)
+        SHD_SRC_TC(64)
         default: return cudaErrorInvalidConfiguration;
     }
 #undef SHD_SRC_TC
