@@ -616,6 +616,8 @@ def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spe
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     s = native.Solver.from_spec(spec, device=dev.index, precision=prec, scattering=scattering)
+    if args.source_path != "auto":
+        s.set_source_path(args.source_path)
     s.zero_state()
     ms, stage, clk, launches = time_steps(s, spec, args.steps, args.warmup, stream, dev, lambda: None)
     sched = _sched(s)
@@ -681,13 +683,14 @@ def bench_config3(args, dev):
 
     from paper_1507_05141_gb300 import inputs
     free, _ = torch.cuda.mem_get_info(dev)
-    spec, G = _fit_groups(lambda g: inputs.compton_shell(G=g), 32, free)
+    n = args.grid or 96
+    spec, G = _fit_groups(lambda g: inputs.compton_shell(n=n, G=g), 32, free)
     note = None if G == 32 else f"G reduced from 32 to {G} to fit the device memory (stated deviation)"
     kind = "kn_thermal" if args.thermal else "kn"
     what = ("Compton scattering off thermal electrons at the recipe's temperature field" if args.thermal
             else "cold Klein-Nishina")
     return bench_single(args, dev, spec=spec, prec="mixed",
-                        workload=f"Compton shell 96^3, {G} groups (1e-4..1e2 m_e c^2), L=7, 16x32 ordinates, "
+                        workload=f"Compton shell {n}^3, {G} groups (1e-4..1e2 m_e c^2), L=7, 16x32 ordinates, "
                                  f"{what}, shell flow Gamma 2..5",
                         extra={"config": 3, "scattering": kind,
                                "l2": "no flush: the intensity state is far larger than L2"},
@@ -701,11 +704,12 @@ def bench_config5(args, dev):
 
     from paper_1507_05141_gb300 import inputs
     free, _ = torch.cuda.mem_get_info(dev)
-    spec, G = _fit_groups(lambda g: inputs.jet_cocoon(G=g), 64, free)
+    n = args.grid or 128
+    spec, G = _fit_groups(lambda g: inputs.jet_cocoon(n=n, G=g), 64, free)
     note = (f"G reduced from 64 to {G}: with the laboratory eta, chi materialised in FP32 the 64-group state "
             f"needs about {_do_bytes(inputs.jet_cocoon(n=16, G=64)) * 512 / 1e9:.0f} GB (stated deviation)")
     return bench_single(args, dev, spec=spec, prec="mixed",
-                        workload=f"jet in a cocoon 128^3, {G} groups (1e-4..1e2 m_e c^2), L=7, 16x32 ordinates, "
+                        workload=f"jet in a cocoon {n}^3, {G} groups (1e-4..1e2 m_e c^2), L=7, 16x32 ordinates, "
                                  f"Gamma=30 core, cold Klein-Nishina",
                         extra={"config": 5, "l2": "no flush: the intensity state is far larger than L2"},
                         errors_spec=inputs.jet_cocoon(n=16, G=8), cpu_spec=inputs.jet_cocoon(n=20, G=G),
@@ -828,8 +832,11 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="workload: 2 = the relativistic jet (the benchmark); 1 static FP64 box, 3 Compton shell, "
                          "4 batch of independent problems, 5 jet in a cocoon")
-    ap.add_argument("--grid", type=int, default=64,
-                    help="nodes per axis of the jet workload (64 is the benchmark; smaller for profiling)")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="nodes per axis (defaults: 64 for the jet, 96 for config 3, 128 for config 5; smaller "
+                         "for profiling)")
+    ap.add_argument("--source-path", default="auto", choices=["auto", "cuda", "tensor"],
+                    help="source pass of group-mixing kernels in MIXED (configs 3, 5): timed choice or forced")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -837,6 +844,8 @@ def main():
         return bench_reference(args)
     if args.config != 2:
         return bench_other(args)
+    if args.grid is None:
+        args.grid = 64
     return bench_ours(args)
 
 
