@@ -799,7 +799,7 @@ bool source_tc_usable(const shd_ctx *ctx);
 size_t source_tc_operand_bytes(const shd_ctx *ctx);
 cudaError_t launch_source_tc_operands(shd_ctx *ctx, cudaStream_t st);
 cudaError_t launch_source_sums_tc(shd_ctx *ctx, const float *Ip, float *Sp, const float *mom, const float *Sprev,
-                                  bool have_prev, cudaStream_t st);
+                                  bool have_prev, int *grid_used, cudaStream_t st);
 
 size_t remap_smem_bytes(const shd_ctx *ctx);
 template <class T>

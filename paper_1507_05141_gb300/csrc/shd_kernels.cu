@@ -1953,9 +1953,10 @@ cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, c
         // a capture; both compute the same S_lm and partial sums)
         if (source_tc_usable(ctx)) {
             shd_ctx *c = const_cast<shd_ctx *>(ctx);  // the choice is a cache of the context
+            int grid_tc = 0;
             auto tc_pass = [&]() {
                 return launch_source_sums_tc(c, (const float *)Ip, (float *)Sp, (const float *)mom,
-                                             (const float *)Sprev, have_prev, st);
+                                             (const float *)Sprev, have_prev, &grid_tc, st);
             };
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
             if (c->source_choice == 0 && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
@@ -1981,9 +1982,10 @@ cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, c
             tc = c->source_choice == 2;
         }
     }
+    int nparts = nb;  // partial-sum rows the final reduction adds
     if (tc) {
         e = launch_source_sums_tc(const_cast<shd_ctx *>(ctx), (const float *)Ip, (float *)Sp, (const float *)mom,
-                                  (const float *)Sprev, have_prev, st);
+                                  (const float *)Sprev, have_prev, &nparts, st);
     } else {
         e = cuda_cores();
     }

@@ -894,7 +894,7 @@ size_t source_tc_operand_bytes(const shd_ctx *c)
 }
 
 cudaError_t launch_source_sums_tc(shd_ctx *c, const float *Ip, float *Sp, const float *mom, const float *Sprev,
-                                  bool have_prev, cudaStream_t st)
+                                  bool have_prev, int *grid_used, cudaStream_t st)
 {
     Prob<float> P = make_prob<float>(c);
     size_t sm = 0;
@@ -903,11 +903,22 @@ cudaError_t launch_source_sums_tc(shd_ctx *c, const float *Ip, float *Sp, const 
     uint32_t cols = 32;
     while ((int)cols < Gp) cols <<= 1;
     const uint16_t *Kop = (const uint16_t *)c->d_tcK;
-    const int nb = c->n_partial;
+    // persistent: two CTAs per SM (no more than there are tiles); every CTA
+    // loads the K operands once
+    const long long ntiles = (c->Nc + tn - 1) / tn;
+    long long nbl = 2LL * num_sms_tc(c);
+    if (nbl > ntiles) nbl = ntiles;
+    if (nbl > c->n_partial) nbl = c->n_partial;
+    const int nb = (int)nbl;
+    if (grid_used) *grid_used = nb;
     cudaError_t e;
 #define SHD_SRC_TC(T)                                                                                         \
     case T:                                                                                                   \
         if ((e = cudaFuncSetAttribute(k_source_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=  \
+            cudaSuccess)                                                                                      \
+            return e;                                                                                         \
+        /* all of the SM's unified memory as shared memory: two CTAs fit */                                   \
+        if ((e = cudaFuncSetAttribute(k_source_tc<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) !=   \
             cudaSuccess)                                                                                      \
             return e;                                                                                         \
         k_source_tc<T><<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, Kop, Gp, Kp, cols,       \
