@@ -303,7 +303,17 @@ def bench_ours(args):
 
     # warm-up (also fills the state with a physical solution), then the
     # device-resident timed region
-    ms, stage, clk_summary, launches = time_steps(solver, spec, args.steps, args.warmup, stream, dev, barrier)
+    # the production path: every timed step replays the captured step graph
+    # (shd_step without per-stage events); then the same number of steps as
+    # direct launches with per-stage CUDA events for the stage times and the
+    # sweep's roofline (--no-e2e, used for profiling, keeps to direct launches)
+    if args.no_e2e:
+        ms, stage, clk_summary, launches = time_steps(solver, spec, args.steps, args.warmup, stream, dev, barrier)
+        ms_direct = ms
+    else:
+        ms, _, clk_summary, launches = time_steps(solver, spec, args.steps, args.warmup, stream, dev, barrier,
+                                                  with_timing=False)
+        ms_direct, stage, _, _ = time_steps(solver, spec, args.steps, 1, stream, dev, barrier)
     ms = max_over_ranks(ms, dev)
     (sw_C, sw_NT), sw_rows = solver.sweep_schedule()
     sweep_sched = {"cluster_ctas": sw_C, "threads": sw_NT,
@@ -377,6 +387,10 @@ def bench_ours(args):
                        "l2": f"no flush: the {do_gb:.1f} GB intensity state is far larger than L2",
                        "parallelism": f"replicas x{ws}"},
             "stage_ms": stage,
+            "timing": {"value_from": "graph replays of the captured step (shd_step's production path)"
+                                     if not args.no_e2e else "direct launches with per-stage events",
+                       "ms_per_step_direct_launches": ms_direct / args.steps,
+                       "stage_ms_from": "direct launches with per-stage CUDA events"},
             "sweep_schedule": sweep_sched,
             "plain_fp32": plain,
             "err_vs_fp64_oracle": errors,

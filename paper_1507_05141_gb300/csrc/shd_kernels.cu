@@ -1990,7 +1990,7 @@ cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, c
         e = cuda_cores();
     }
     if (e != cudaSuccess) return e;
-    k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, nb, have_prev ? 1 : 0, ctx->d_sums);
+    k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, nparts, have_prev ? 1 : 0, ctx->d_sums);
     note_launch();
     return cudaGetLastError();
 }
