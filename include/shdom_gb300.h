@@ -290,6 +290,16 @@ int shd_get_sweep_schedule(shd_ctx *ctx, int *C, int *NT, int *ncand, float *can
 int shd_set_source_path(shd_ctx *ctx, int path);
 int shd_get_source_path(shd_ctx *ctx, int *path, float *ms_cuda_cores, float *ms_tensor_cores);
 
+/* Which kernels carry the transforms of the configured problem, Eq. 12-14
+ * (stage a1, DO -> SH) and Eq. 3 with the Lorentz remap of Eq. 8-9 (stage a3,
+ * SH -> DO): 0 the CUDA-core kernels (FP64 and FP32 precisions, or a mixed
+ * problem no tensor-core form fits), 1 the tensor-core tile kernels, 2 the
+ * tensor-core segment kernels fed and drained by TMA, 3 the same segment
+ * kernels with 4-byte cp.async loads and direct stores (planes whose rows
+ * are not multiples of 4 nodes, which no tensor map can stride).  Read
+ * only; SHD_ERR_STATE before the grid, angles and groups are set. */
+int shd_get_transform_path(shd_ctx *ctx, int *path);
+
 /* Self-check of the failure path of the tensor-core kernels' bounded waits
  * (no counterpart in the paper).  Every mbarrier wait in those kernels polls
  * a bounded number of times; when the limit runs out the kernel raises the

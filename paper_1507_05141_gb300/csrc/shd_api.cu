@@ -1821,6 +1821,20 @@ int shd_get_source_path(shd_ctx *c, int *path, float *ms_cuda_cores, float *ms_t
     return SHD_OK;
 }
 
+int shd_get_transform_path(shd_ctx *c, int *path)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!sized(c)) return fail(SHD_ERR_STATE, "grid, angles and groups must be set");
+    int p = 0;
+    if (c->precision == SHD_MIXED) {
+        if (seg_usable(c)) p = seg_manual(c) ? 3 : 2;
+        else if (tc_usable(c)) p = 1;
+    }
+    if (path) *path = p;
+    return SHD_OK;
+}
+
 int shd_check_bounded_wait(shd_ctx *c, long long polls)
 {
     int rc = ctx_check(c);

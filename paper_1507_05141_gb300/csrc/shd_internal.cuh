@@ -721,6 +721,7 @@ template <class T>
 cudaError_t launch_project_scratch(const shd_ctx *ctx, const T *I, T *Ip, T *mom, T *scratch, cudaStream_t st);
 bool tc_usable(const shd_ctx *ctx);
 bool seg_usable(const shd_ctx *ctx);
+bool seg_manual(const shd_ctx *ctx);
 cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, float *mom, float *nm0, float *nm1,
                                cudaStream_t st);
 cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,

@@ -99,6 +99,34 @@ struct SegArgs {
                         //  internal index of the class's first ordinate, ordinates in the class}
 };
 
+// Index of row r's node within the sweep layout of the class behind map
+// `mi` of the tile's group (group A: 0 = z-class (x, y, z), 1 = y-class
+// (x, z, y); group B: the x-class (y, z, x)); -1 outside the grid.
+__device__ inline long long seg_li(const Prob<float> &P, const SegArgs &S, int4 sd, int r, int mi)
+{
+    const int a = sd.y + (r & (S.bw - 1)), b = sd.z + r / S.bw;
+    if (!S.groupB) {
+        if (a >= P.nx || b >= P.ny) return -1;
+        return mi == 0 ? ((long long)sd.x * P.ny + b) * P.nx + a : ((long long)b * P.nz + sd.x) * P.nx + a;
+    }
+    if (a >= P.ny || b >= P.nz) return -1;
+    return ((long long)sd.x * P.nz + b) * P.ny + a;
+}
+
+// 4-byte asynchronous copy global -> shared; src_size 0 writes a zero and
+// reads nothing.
+__device__ inline void cp_async4(uint32_t dst, const float *src, uint32_t src_size)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(src_size) : "memory");
+}
+// One arrival on `bar` once every earlier cp.async of this thread has landed
+// (the barrier's count already includes it).
+__device__ inline void cp_async_arrive(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Node of row r of a segment tile; false outside the grid.
 __device__ inline bool seg_node(const Prob<float> &P, const SegArgs &S, int4 sd, int r, long long &c)
 {
@@ -140,17 +168,22 @@ __device__ inline void box_coords(const SegArgs &S, int ROWS, long long w, int G
 
 // -------------------------------------------------------------------------
 // a1.  Warps 0-7 converters, 8-11 epilogue (tensor-memory lane quadrants
-// 0-3), 12 TMA producer, 13 MMA issuer.  Shared memory: Bh, Bl [nb][Kp]
+// 0-3), 12 TMA producer, 13 MMA issuer.  MAN (planes whose rows are not
+// 16-byte multiples, which no tensor map can stride): warps 12 and 14 fill
+// the same staging boxes with 4-byte cp.async copies from the sweep layout
+// (rows 0-63 and 64-127; zeros outside the grid and past the class's
+// ordinates), each lane arriving on the stage's barrier when its copies land.  Shared memory: Bh, Bl [nb][Kp]
 // resident; FP32 staging [NSTG][box]; BF16 ring [NR][hi, lo][128][32]
 // (canonical); the barriers.  Segment mode: the converters also copy the
 // laboratory I of moving rows to nmo, node-major [m][g][k], for the remap.
 // -------------------------------------------------------------------------
-template <int NSTG, int NR, int ROWS>
-__global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
-                                                        float *__restrict__ Ip, float *__restrict__ mom,
-                                                        float *__restrict__ nmo, const uint16_t *__restrict__ gBh,
-                                                        const uint16_t *__restrict__ gBl, int *err)
+template <int NSTG, int NR, int ROWS, int MAN>
+__global__ void __launch_bounds__(MAN ? 480 : 448, 1)
+    k_project_seg(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S, const float *__restrict__ Iin,
+                  float *__restrict__ Ip, float *__restrict__ mom, float *__restrict__ nmo,
+                  const uint16_t *__restrict__ gBh, const uint16_t *__restrict__ gBl, int *err)
 {
+    static_assert(!(MAN && ROWS), "rows mode always has a tensor map");
     constexpr uint32_t ACC_COLS = 128;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (tc::smem_u32(smem_raw) & 1023) {  // the swizzled staging needs 1024-byte alignment
@@ -184,7 +217,7 @@ __global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __g
     }
     if (tid == 0) {
         for (int i = 0; i < NSTG; ++i) {
-            tc::mbar_init(&sfull[i], 1);
+            tc::mbar_init(&sfull[i], MAN ? 64 : 1);
             tc::mbar_init(&sempty[i], kNConv);
         }
         for (int i = 0; i < NR; ++i) {
@@ -282,6 +315,38 @@ __global__ void __launch_bounds__(448, 1) k_project_seg(Prob<float> P, const __g
             }
         }
     conv_out:;
+    } else if (MAN && (warp == 12 || warp == 14)) {
+        // ---------------- cp.async producers ----------------
+        const int r0 = (warp == 12 ? 0 : 64) + lane;  // rows r0 and r0 + 32
+        const long long gstride = (long long)G * P.Nc;
+        const uint32_t sdst0 = tc::smem_u32(stg) + 4u * (uint32_t)r0;
+        long long it = 0;
+        for (long long w = blockIdx.x; w < S.nitem; w += gridDim.x) {
+            const long long sg = w / G;
+            const int g = (int)(w - sg * G);
+            const int4 sd = S.segs[sg];
+            const long long l00 = seg_li(P, S, sd, r0, 0), l01 = seg_li(P, S, sd, r0 + 32, 0);
+            const long long l10 = S.groupB ? -1 : seg_li(P, S, sd, r0, 1);
+            const long long l11 = S.groupB ? -1 : seg_li(P, S, sd, r0 + 32, 1);
+            for (int ch = 0; ch < nchunk; ++ch, ++it) {
+                const int s = (int)(it % NSTG);
+                if (it >= NSTG && !wait(&sempty[s], (uint32_t)((it / NSTG - 1) & 1))) goto man_out;
+                const int4 ci = S.chunk[ch];
+                const long long la = ci.x ? l10 : l00, lb = ci.x ? l11 : l01;
+                const float *src = Iin + (long long)(ci.z + ci.y) * gstride + (long long)g * P.Nc;
+                const uint32_t d = sdst0 + (uint32_t)s * (kBox * 4);
+#pragma unroll 8
+                for (int k = 0; k < kKC; ++k, src += gstride) {
+                    const bool kin = ci.y + k < ci.w;
+                    const bool oa = kin && la >= 0, ob = kin && lb >= 0;
+                    cp_async4(d + 512u * k, oa ? src + la : Iin, oa ? 4u : 0u);
+                    cp_async4(d + 512u * k + 128u, ob ? src + lb : Iin, ob ? 4u : 0u);
+                }
+                cp_async_arrive(&sfull[s]);
+            }
+        }
+    man_out:
+        cp_async_wait_all();  // no copy may still be landing when the CTA leaves
     } else if (warp == 12) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
@@ -622,13 +687,19 @@ done:
 //               each into one of two tensor-memory accumulators of 256
 //               columns, alternating
 // Barriers: metaFull / itemDone per item parity (row tables), aFull / aEmpty
-// (the A operand), tFull / tEmpty per accumulator.
+// (the A operand), tFull / tEmpty per accumulator.  MAN (planes whose rows
+// are not 16-byte multiples): each epilogue lane writes its own row's 16
+// values of a chunk straight into the sweep layout (eta_out, chi_out), one
+// coalesced 4-byte store per ordinate, instead of staging a box for TMA.
 // -------------------------------------------------------------------------
+template <int MAN>
 __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __grid_constant__ SegMaps maps, SegArgs S,
                                                       const float *__restrict__ Sp, const float *__restrict__ etan,
                                                       const float *__restrict__ chin,
                                                       const uint16_t *__restrict__ gYh,
-                                                      const uint16_t *__restrict__ gYl, int Kq, int *err)
+                                                      const uint16_t *__restrict__ gYl, int Kq,
+                                                      float *__restrict__ eta_out, float *__restrict__ chi_out,
+                                                      int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (tc::smem_u32(smem_raw) & 1023) {
@@ -823,13 +894,31 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
             const long long nbase = m >= 0 ? ((long long)m * G + g) * N : 0;
             const bool anym = __any_sync(0xffffffffu, m >= 0);
             // the previous item's stores have read this warp's tiles
-            if (lane == 0) tc::bulk_wait_read<0>();
+            if (!MAN && lane == 0) tc::bulk_wait_read<0>();
             __syncwarp();
             auto store = [&](int cn, const float *src) {
                 const int4 ci = S.chunk[cn];
                 const int kk = ci.y + 16 * half;
                 const bool yc = !S.groupB && ci.x == 1;
                 tc::tma_store_5d(mp_base + ci.x, as, yc ? sd.x : bs, yc ? bs : sd.x, g, kk, src);
+            };
+            // MAN: row r's 16 values of chunk cn, written where they live
+            long long li0 = -1, li1 = -1;
+            if (MAN) {
+                li0 = seg_li(P, S, sd, r, 0);
+                li1 = S.groupB ? -1 : seg_li(P, S, sd, r, 1);
+            }
+            const long long gstride = (long long)G * P.Nc;
+            float *const out = eta_w ? eta_out : chi_out;
+            auto store_row = [&](int cn, const float (&v)[16]) {
+                const int4 ci = S.chunk[cn];
+                const long long l = ci.x ? li1 : li0;
+                if (l < 0) return;
+                const int kl0 = ci.y + 16 * half;
+                float *dst = out + (long long)(ci.z + kl0) * gstride + (long long)g * P.Nc + l;
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (kl0 + q < ci.w) dst[q * gstride] = v[q];
             };
             // a moving row's 16 values of chunk cn (its own node-major row, 16-byte
             // loads where aligned) into registers, one chunk ahead of their use
@@ -852,7 +941,12 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
             };
             bool ok = true;
             if (!eta_w && !anym) {
-                if (S.chi_all) {
+                if (S.chi_all && MAN) {
+                    float cv[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) cv[q] = chr;
+                    for (int cn = 0; cn < nchunk; ++cn) store_row(cn, cv);
+                } else if (S.chi_all) {
                     // every row at rest: one constant chi tile serves every chunk
 #pragma unroll
                     for (int q = 0; q < 16; ++q) W[q * 32 + lane] = chr;
@@ -878,12 +972,26 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
                         tc::fence_after_sync();
                     }
                     const int b = cn & 1;
-                    if (lane == 0) tc::bulk_wait_read<1>();  // the store of chunk cn - 2 has read buffer b
+                    if (!MAN && lane == 0) tc::bulk_wait_read<1>();  // the store of chunk cn - 2 has read buffer b
                     __syncwarp();
                     float cur[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) cur[q] = mv[q];
                     if (anym && cn + 1 < nchunk) load_moving(cn + 1);
+                    if (MAN) {
+                        float o[16];
+                        if (eta_w) {
+                            float v[16];
+                            tc::tmem_ld16(trow + (uint32_t)(256 * jb + (cn & 7) * kKC + 16 * half), v);
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) o[q] = m < 0 ? chr * v[q] : cur[q];
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) o[q] = m < 0 ? chr : cur[q];
+                        }
+                        store_row(cn, o);
+                        continue;
+                    }
                     float *Wb = W + (size_t)b * 512 + lane;
                     if (eta_w) {
                         float v[16];
@@ -910,7 +1018,7 @@ __global__ void __launch_bounds__(672, 1) k_sh2lab_ws(Prob<float> P, const __gri
             j += njob;
             tc::mbar_arrive(&itemDone[pb]);
         }
-        if (lane == 0) tc::bulk_wait_all();
+        if (!MAN && lane == 0) tc::bulk_wait_all();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -974,8 +1082,10 @@ bool seg_usable(const shd_ctx *c)
 {
     if (c->precision != SHD_MIXED || !c->seg_ready || c->NB > 128 || !c->d_tc_Bh || !c->d_tc_Yh || !encoder())
         return false;
-    // 16-byte strides of the tensor maps
-    if (c->nx % 4 || c->ny % 4 || c->N % 4) return false;
+    // 16-byte row strides of the node-major maps (the segment tiles of planes
+    // whose rows are not 16-byte multiples go through cp.async and plain
+    // stores instead of tensor maps)
+    if (c->N % 4) return false;
     if (c->tc_Kp > 512 || c->tc_Kp / kKC > 16) return false;
     int a, b;
     for (int grp = 0; grp < 2; ++grp) {
@@ -1092,21 +1202,27 @@ static cudaError_t group_maps(const shd_ctx *c, int grp, const float *base, CUte
     return class_map(c, &m0[0], base, 0, ba, bb, bk);
 }
 
-template <int ROWS>
+// Planes whose rows are not 16-byte multiples: no tensor map can stride
+// them, so the segment tiles are loaded by cp.async and stored directly.
+bool seg_manual(const shd_ctx *c) { return c->nx % 4 != 0 || c->ny % 4 != 0; }
+
+template <int ROWS, int MAN>
 static cudaError_t run_project_seg(const shd_ctx *ctx, const Prob<float> &P, const SegMaps &maps, const SegArgs &a,
-                                   float *Ip, float *mom, float *nmo, const void *Bh, const void *Bl, cudaStream_t st)
+                                   const float *I, float *Ip, float *mom, float *nmo, const void *Bh, const void *Bl,
+                                   cudaStream_t st)
 {
     int nstg = 0, nr = 0;
     if (!pick_depths(a.nb, a.Kp, nstg, nr)) return cudaErrorInvalidConfiguration;
     const size_t sm = project_seg_smem(a.nb, a.Kp, nstg, nr);
-    auto kern = nr == 4 ? k_project_seg<4, 4, ROWS>
-                        : (nr == 3 ? k_project_seg<4, 3, ROWS>
-                                   : (nstg == 4 ? k_project_seg<4, 2, ROWS> : k_project_seg<3, 2, ROWS>));
+    auto kern = nr == 4 ? k_project_seg<4, 4, ROWS, MAN>
+                        : (nr == 3 ? k_project_seg<4, 3, ROWS, MAN>
+                                   : (nstg == 4 ? k_project_seg<4, 2, ROWS, MAN> : k_project_seg<3, 2, ROWS, MAN>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int grid = num_sms_seg(ctx);
     if (a.nitem < grid) grid = (int)a.nitem;
-    kern<<<grid, 448, sm, st>>>(P, maps, a, Ip, mom, nmo, (const uint16_t *)Bh, (const uint16_t *)Bl, ctx->d_tc_err);
+    kern<<<grid, MAN ? 480 : 448, sm, st>>>(P, maps, a, I, Ip, mom, nmo, (const uint16_t *)Bh, (const uint16_t *)Bl,
+                                            ctx->d_tc_err);
     note_launch();
     return cudaGetLastError();
 }
@@ -1128,10 +1244,12 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
         a.accumulate = first ? 0 : 1;
         first = false;
         SegMaps maps{};
-        if ((e = group_maps(ctx, grp, I, maps.m, false)) != cudaSuccess) return e;
-        if ((e = run_project_seg<0>(ctx, P, maps, a, Ip, mom, ctx->nmoving > 0 ? nm0 : nullptr, ctx->d_tcs_Bh[grp],
-                                    ctx->d_tcs_Bl[grp], st)) != cudaSuccess)
-            return e;
+        float *nmo = ctx->nmoving > 0 ? nm0 : nullptr;
+        if (seg_manual(ctx))
+            e = run_project_seg<0, 1>(ctx, P, maps, a, I, Ip, mom, nmo, ctx->d_tcs_Bh[grp], ctx->d_tcs_Bl[grp], st);
+        else if ((e = group_maps(ctx, grp, I, maps.m, false)) == cudaSuccess)
+            e = run_project_seg<0, 0>(ctx, P, maps, a, I, Ip, mom, nmo, ctx->d_tcs_Bh[grp], ctx->d_tcs_Bl[grp], st);
+        if (e != cudaSuccess) return e;
     }
     if (ctx->nmoving > 0) {
         if ((e = launch_remap_to_comoving_f(ctx, nm0, nm1, st)) != cudaSuccess) return e;
@@ -1139,7 +1257,8 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
         a.nb = nlm16(ctx);
         SegMaps maps{};
         if ((e = rows_map(ctx, &maps.m[0], nm1)) != cudaSuccess) return e;
-        if ((e = run_project_seg<1>(ctx, P, maps, a, Ip, mom, nullptr, ctx->d_tc_Bh, ctx->d_tc_Bl, st)) != cudaSuccess)
+        if ((e = run_project_seg<1, 0>(ctx, P, maps, a, nm1, Ip, mom, nullptr, ctx->d_tc_Bh, ctx->d_tc_Bl, st)) !=
+            cudaSuccess)
             return e;
     }
     return cudaSuccess;
@@ -1163,7 +1282,9 @@ static cudaError_t run_sh2lab_rows(const shd_ctx *ctx, const Prob<float> &P, con
 // laboratory eta, chi (nm1, nm2), then eta, chi of every node into the sweep
 // layout (moving rows taken from nm1, nm2).  Without full_chi, chi is stored
 // only for the 32-node runs that hold a moving node: every 4-node piece the
-// sweep reads from chi lies in such a run.
+// sweep reads from chi lies in such a run.  (Not so when a plane's rows are
+// not multiples of 4 nodes: a piece may straddle two rows, so those grids
+// always store every chi.)
 cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,
                               float *nm2, cudaStream_t st, bool full_chi)
 {
@@ -1181,18 +1302,21 @@ cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, f
     for (int grp = 0; grp < 2; ++grp) {
         if (ctx->tcs_nchunk[grp] == 0 || ctx->nseg[grp] == 0) continue;
         SegArgs a = seg_args(ctx, grp);
-        a.chi_all = full_chi ? 1 : 0;
+        const bool man = seg_manual(ctx);
+        a.chi_all = (full_chi || man) ? 1 : 0;
         SegMaps maps{};
-        if ((e = group_maps(ctx, grp, eta, &maps.m[0], true)) != cudaSuccess) return e;
-        if ((e = group_maps(ctx, grp, chi, &maps.m[2], true)) != cudaSuccess) return e;
+        if (!man) {
+            if ((e = group_maps(ctx, grp, eta, &maps.m[0], true)) != cudaSuccess) return e;
+            if ((e = group_maps(ctx, grp, chi, &maps.m[2], true)) != cudaSuccess) return e;
+        }
+        auto kern = man ? k_sh2lab_ws<1> : k_sh2lab_ws<0>;
         const size_t sm = sh2lab_ws_smem(a.Kp, ctx->tc_Kq);
-        if ((e = cudaFuncSetAttribute(k_sh2lab_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
-            cudaSuccess)
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
             return e;
         int grid = num_sms_seg(ctx);
         if (a.nitem < grid) grid = (int)a.nitem;
-        k_sh2lab_ws<<<grid, 672, sm, st>>>(P, maps, a, Sp, nm1, nm2, (const uint16_t *)ctx->d_tcs_Yh[grp],
-                                           (const uint16_t *)ctx->d_tcs_Yl[grp], ctx->tc_Kq, ctx->d_tc_err);
+        kern<<<grid, 672, sm, st>>>(P, maps, a, Sp, nm1, nm2, (const uint16_t *)ctx->d_tcs_Yh[grp],
+                                    (const uint16_t *)ctx->d_tcs_Yl[grp], ctx->tc_Kq, eta, chi, ctx->d_tc_err);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

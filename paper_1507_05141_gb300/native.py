@@ -72,6 +72,7 @@ _SIGS = {
     "shd_set_source_path": (_i, [_vp, _i]),
     "shd_get_source_path": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(ctypes.c_float)]),
+    "shd_get_transform_path": (_i, [_vp, ctypes.POINTER(_i)]),
     "shd_set_time_scheme": (_i, [_vp, _i]),
     "shd_set_sweep_schedule": (_i, [_vp, _i, _i]),
     "shd_get_sweep_schedule": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -355,6 +356,14 @@ class Solver:
         p, a, b = _i(), ctypes.c_float(), ctypes.c_float()
         _check(self._L.shd_get_source_path(self._h, ctypes.byref(p), ctypes.byref(a), ctypes.byref(b)))
         return p.value, a.value, b.value
+
+    def transform_path(self):
+        """Kernels carrying the transforms: 0 CUDA cores, 1 tensor-core tiles,
+        2 tensor-core segments through TMA, 3 the segment kernels with
+        cp.async loads and direct stores (rows not multiples of 4 nodes)."""
+        p = _i()
+        _check(self._L.shd_get_transform_path(self._h, ctypes.byref(p)))
+        return p.value
 
     def set_ng(self, period=4):
         """Ng acceleration of solve_static every `period` (>= 4) iterations; 0 = off."""

@@ -316,6 +316,7 @@ def test_steps_mixed_tma_tiles(native, grid):
     spec = inputs.ragged_mixed(grid=grid, G=3)
     P = _oracle(spec)
     s = native.Solver.from_spec(spec, precision="mixed")
+    assert s.transform_path() == 2
     I0 = inputs.random_state(spec, seed=6)
     s.set_state(I0)
     n0 = native.launch_count()
@@ -329,6 +330,33 @@ def test_steps_mixed_tma_tiles(native, grid):
     assert rel(Ish, Ish_r) < MIXED_TOL
     f = O.moments_to_eddington(J, K)
     assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < MIXED_TOL
+
+
+@pytest.mark.parametrize("grid", [(11, 9, 7), (62, 6, 6), (130, 6, 5), (17, 13, 9)])
+def test_steps_mixed_ragged_rows(native, grid):
+    """Mixed path on grids whose plane rows are not multiples of 4 nodes (no
+    tensor map can stride them): the segment kernels load their tiles with
+    4-byte cp.async copies and store eta, chi directly.  (62, 6, 6) keeps the
+    planes 16-byte aligned, so the sweep reads chi0 at rest and per-ordinate
+    chi only on pieces with a moving node, pieces that here straddle two
+    rows; (130, 6, 5) has two tiles along x; (17, 13, 9) leaves most of each
+    32-wide tile row outside the grid.  Two steps against the oracle."""
+    spec = inputs.ragged_mixed(grid=grid, G=3)
+    P = _oracle(spec)
+    s = native.Solver.from_spec(spec, precision="mixed")
+    assert s.transform_path() == 3
+    I0 = inputs.random_state(spec, seed=8)
+    s.set_state(I0)
+    s.step(2)
+    J, H, K, Ish = s.moments(with_sh=True)
+    I_ref, _, _ = P.step(I0, 2)
+    Ish_r, J_r, H_r, K_r = P.project(I_ref)
+    assert rel_elem(J, J_r) < MIXED_TOL
+    assert rel(H, H_r) < MIXED_TOL
+    assert rel(K, K_r) < MIXED_TOL
+    assert rel(Ish, Ish_r) < MIXED_TOL
+    I = s.get_state()
+    assert rel(I, I_ref) < MIXED_TOL
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("mixed", MIXED_TOL)])
