@@ -322,6 +322,22 @@ __device__ inline double dlog<double>(double x) { return log(x); }
 template <>
 __device__ inline float dlog<float>(float x) { return logf(x); }
 
+// Rounding and clamping in the argument's own precision: on GB300 a float
+// taken through double runs on the FP64 pipe, dozens of times slower.
+template <class T>
+__device__ inline T dfloor(T x);
+template <>
+__device__ inline double dfloor<double>(double x) { return ::floor(x); }
+template <>
+__device__ inline float dfloor<float>(float x) { return floorf(x); }
+
+template <class T>
+__device__ inline T dclamp(T x, T lo, T hi);
+template <>
+__device__ inline double dclamp<double>(double x, double lo, double hi) { return ::fmin(::fmax(x, lo), hi); }
+template <>
+__device__ inline float dclamp<float>(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+
 template <class T>
 __device__ inline T datan2(T y, T x);
 template <>

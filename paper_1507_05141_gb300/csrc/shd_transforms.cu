@@ -544,13 +544,28 @@ template <class T>
 __device__ inline void stage_node(T *dst, const T *src, int n)
 {
     constexpr int V = 16 / sizeof(T);
-    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && n % V == 0) {
-        using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-        const V4 *s4 = reinterpret_cast<const V4 *>(src);
-        V4 *d4 = reinterpret_cast<V4 *>(dst);
-        for (int i = threadIdx.x; i < n / V; i += blockDim.x) d4[i] = s4[i];
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && n % V == 0) {
+        // every 16-byte piece of the node in flight at once: one memory round
+        // trip per CTA (the caller's barrier publishes the copies)
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+        for (int i = threadIdx.x; i < n / V; i += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * (uint32_t)i),
+                         "l"(src + (size_t)i * V)
+                         : "memory");
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+        // B loads in flight per thread before their stores
+        constexpr int B = sizeof(T) == 4 ? 8 : 4;
+        const int nt = blockDim.x;
+        int i = threadIdx.x;
+        for (; i + (B - 1) * nt < n; i += B * nt) {
+            T v[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) v[j] = src[i + j * nt];
+#pragma unroll
+            for (int j = 0; j < B; ++j) dst[i + j * nt] = v[j];
+        }
+        for (; i < n; i += nt) dst[i] = src[i];
     }
 }
 
@@ -660,9 +675,9 @@ __device__ inline UniformShift<T> uniform_shift(const Prob<T> &P, T l)
 {
     UniformShift<T> u;
     u.x = l * P.lgidl;
-    const T f = floor(u.x);
+    const T f = dfloor<T>(u.x);
     const T lim = T(P.G + 1);  // shifts beyond the group range act alike
-    u.s = (int)fmin(fmax(f, -lim), lim);
+    u.s = (int)dclamp<T>(f, -lim, lim);
     u.t = u.x - f;
     return u;
 }
@@ -710,10 +725,15 @@ __device__ inline T chi_mix(const T *schi, const T *slr, int ga, T t)
 // laboratory I (node-major) -> comoving I0 (node-major), one CTA per moving
 // node: I0(k0, g0) = (ebar_g0/eps)^3 I_lab(n, eps), n = boost of n_k0 to the
 // laboratory, eps = ebar_g0 (Gamma + u.n_k0)   (Sec. 2.2)
-template <class T>
+// TAB: the boosts and stencils come from the per-flow table (FP32 only);
+// otherwise they are computed in place.  Two instantiations, so that the
+// table path carries none of the computed path's FP64 boost code, which the
+// compiler would otherwise evaluate alongside it.
+template <class T, int TAB>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__restrict__ I0,
                                                            const float4 *__restrict__ tab)
 {
+    static_assert(!TAB || sizeof(T) == 4, "the remap tables are FP32");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G, N = P.N;
     T *sI = reinterpret_cast<T *>(smem_raw);  // [G][N] internal order
@@ -722,7 +742,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
     const long long c = P.moving[m];
     // the first two table entries of this thread, in flight during the staging
     float4 epre[2] = {};
-    if (sizeof(T) == 4 && tab) {
+    if constexpr (TAB) {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int kk = threadIdx.x + i * blockDim.x;
@@ -740,7 +760,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
     for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x, ++iter) {
         T q;  // nu/nu0
         Stencil<T> st;
-        if (sizeof(T) == 4 && tab) {
+        if constexpr (TAB) {
             const float4 e = iter == 0 ? epre[0] : (iter == 1 ? epre[1] : tab[m * N + k0]);
             q = (T)e.w;
             st = table_stencil<T>(e, P.nphi, tb.m2i);
@@ -808,10 +828,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
 // comoving S0 (node-major) -> laboratory eta, chi (node-major):
 // D = Gamma - u.n_k, n0 = comoving direction, eps0 = ebar_g D,
 // S_lab = S0(n0, eps0)/D^3, chi_lab = chi0(eps0) D, eta_lab = chi_lab S_lab
-template <class T>
+template <class T, int TAB>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restrict__ eta_n,
                                                       T *__restrict__ chi_n, const float4 *__restrict__ tab)
 {
+    static_assert(!TAB || sizeof(T) == 4, "the remap tables are FP32");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G, N = P.N;
     T *sS = reinterpret_cast<T *>(smem_raw);  // [G][N] internal order
@@ -835,7 +856,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         T D;  // nu0/nu
         Stencil<T> st;
-        if (sizeof(T) == 4 && tab) {
+        if constexpr (TAB) {
             const float4 e = tab[m * N + k];
             D = (T)e.w;
             st = table_stencil<T>(e, P.nphi, tb.m2i);
@@ -1003,10 +1024,11 @@ static cudaError_t run_remap_to_comoving(const shd_ctx *ctx, const T *nm0, T *nm
 {
     Prob<T> P = make_prob<T>(ctx);
     size_t sm = remap_smem_bytes(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_remap_to_comoving<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     const float4 *tab = sizeof(T) == 4 && ctx->rtab_valid ? (const float4 *)ctx->d_rtab[0] : nullptr;
-    k_remap_to_comoving<T><<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1, tab);
+    auto kern = (sizeof(T) == 4 && tab) ? k_remap_to_comoving<T, sizeof(T) == 4> : k_remap_to_comoving<T, 0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1, tab);
     note_launch();
     return cudaGetLastError();
 }
@@ -1016,10 +1038,11 @@ static cudaError_t run_remap_to_lab(const shd_ctx *ctx, const T *nm0, T *nm1, T 
 {
     Prob<T> P = make_prob<T>(ctx);
     size_t sr = remap_smem_bytes(ctx);
-    cudaError_t e = cudaFuncSetAttribute(k_remap_to_lab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
-    if (e != cudaSuccess) return e;
     const float4 *tab = sizeof(T) == 4 && ctx->rtab_valid ? (const float4 *)ctx->d_rtab[1] : nullptr;
-    k_remap_to_lab<T><<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2, tab);
+    auto kern = (sizeof(T) == 4 && tab) ? k_remap_to_lab<T, sizeof(T) == 4> : k_remap_to_lab<T, 0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2, tab);
     note_launch();
     return cudaGetLastError();
 }
