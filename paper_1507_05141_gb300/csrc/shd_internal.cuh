@@ -608,7 +608,9 @@ __device__ inline float freq_mix_lr<float>(float fa, float lr, float t)
 
 // Linear-in-tau short-characteristic weights with e = exp(-x):
 //   I_P = I_U e + S_P wp + S_U wu,  wp = 1 - (1-e)/x,  wu = (1-e)/x - e.
-// Below the threshold the Taylor series (Horner) avoids the cancellation.
+// Below the threshold the Taylor series (Horner) avoids the cancellation;
+// its coefficients are constants folded at compile time (a division by a
+// constant would be a full division sequence on every update).
 template <class T>
 __device__ inline void sc_weights(T x, T &e, T &wp, T &wu);
 
@@ -617,8 +619,8 @@ __device__ inline void sc_weights<double>(double x, double &e, double &wp, doubl
 {
     if (x < 0.05) {
         // wp = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!,  wu = sum_{n>=1} (-1)^{n+1} n x^n/(n+1)!
-        wp = x * (1.0 / 2 - x * (1.0 / 6 - x * (1.0 / 24 - x * (1.0 / 120 - x * (1.0 / 720 - x * (1.0 / 5040 - x * (1.0 / 40320 - x / 362880.0)))))));
-        wu = x * (1.0 / 2 - x * (1.0 / 3 - x * (1.0 / 8 - x * (1.0 / 30 - x * (1.0 / 144 - x * (1.0 / 840 - x * (1.0 / 5760 - x / 45360.0)))))));
+        wp = x * (1.0 / 2 - x * (1.0 / 6 - x * (1.0 / 24 - x * (1.0 / 120 - x * (1.0 / 720 - x * (1.0 / 5040 - x * (1.0 / 40320 - x * (1.0 / 362880.0))))))));
+        wu = x * (1.0 / 2 - x * (1.0 / 3 - x * (1.0 / 8 - x * (1.0 / 30 - x * (1.0 / 144 - x * (1.0 / 840 - x * (1.0 / 5760 - x * (1.0 / 45360.0))))))));
         e = exp(-x);
         return;
     }
@@ -650,8 +652,8 @@ __device__ inline void sc_weights_narrow<float>(float x, float &e, float &wp, fl
 {
     e = hw_exp2(-x * kLog2eF);
     if (x < 0.5f) {
-        wp = x * (1.f / 2 - x * (1.f / 6 - x * (1.f / 24 - x * (1.f / 120 - x * (1.f / 720 - x * (1.f / 5040 - x * (1.f / 40320 - x / 362880.f)))))));
-        wu = x * (1.f / 2 - x * (1.f / 3 - x * (1.f / 8 - x * (1.f / 30 - x * (1.f / 144 - x * (1.f / 840 - x * (1.f / 5760 - x / 45360.f)))))));
+        wp = x * (1.f / 2 - x * (1.f / 6 - x * (1.f / 24 - x * (1.f / 120 - x * (1.f / 720 - x * (1.f / 5040 - x * (1.f / 40320 - x * (1.f / 362880.f))))))));
+        wu = x * (1.f / 2 - x * (1.f / 3 - x * (1.f / 8 - x * (1.f / 30 - x * (1.f / 144 - x * (1.f / 840 - x * (1.f / 5760 - x * (1.f / 45360.f))))))));
         return;
     }
     // x >= 1/2: e <= 0.61, so 1 - e carries no cancellation

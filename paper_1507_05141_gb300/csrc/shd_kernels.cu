@@ -603,6 +603,12 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
         }
     }
     const int d1 = o.s1 * n2, d2 = o.s2;
+    // the moving-node bits of this thread's chi pieces (plane <= U NT nodes,
+    // 4 a piece: at most MP pieces a thread) for the current 64-plane
+    // window, held in registers and reloaded when the window changes
+    constexpr int MP = (U + 3) / 4;
+    unsigned long long mw[MP];
+    int mwin = -1;
 
     auto issue = [&](int step) {
         if (step < nd) {
@@ -612,11 +618,21 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
             const int nv = plane / 4;  // 16-byte pieces per array
             for (int q = tid; q < nv; q += NT) cp_async_n<16>(&r[q * 4], &I[pb + q * 4]);
             for (int q = tid; q < nv; q += NT) cp_async_n<16>(&r[pstride + q * 4], &eta[pb + q * 4]);
-            for (int q = tid; q < nv; q += NT) {
+            if (CB && (id >> 6) != mwin) {
+                mwin = id >> 6;
+#pragma unroll
+                for (int pi = 0; pi < MP; ++pi) {
+                    const int q = tid + pi * NT;
+                    mw[pi] = q < nv ? mb[(size_t)mwin * npc + q] : 0ull;
+                }
+            }
+#pragma unroll
+            for (int pi = 0; pi < MP; ++pi) {
+                const int q = tid + pi * NT;
+                if (q >= nv) break;
                 const int off = q * 4;
                 const float *src = chi + pb + off;
-                if (CB && !((mb[(size_t)(id >> 6) * npc + q] >> (id & 63)) & 1ull))
-                    src = c0base + (long long)id * plane + off;
+                if (CB && !((mw[pi] >> (id & 63)) & 1ull)) src = c0base + (long long)id * plane + off;
                 cp_async_n<16>(&r[2 * pstride + off], src);
             }
         }
@@ -739,6 +755,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sweep_cl(Prob<float> P, float
         }
     }
     const int d1 = o.s1 * n2, d2 = o.s2;
+    // moving-node bits of this thread's chi pieces, as in k_sweep_pp
+    constexpr int MP = (U + 3) / 4;
+    unsigned long long mw[MP];
+    int mwin = -1;
 
     auto issue = [&](int step) {
         if (step < nd) {
@@ -748,11 +768,21 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sweep_cl(Prob<float> P, float
             const int nv = nloc / 4;  // 16-byte pieces per array
             for (int q = tid; q < nv; q += NT) cp_async_n<16>(&rg[q * 4], &I[pb + q * 4]);
             for (int q = tid; q < nv; q += NT) cp_async_n<16>(&rg[pstride + q * 4], &eta[pb + q * 4]);
-            for (int q = tid; q < nv; q += NT) {
+            if (CB && (id >> 6) != mwin) {
+                mwin = id >> 6;
+#pragma unroll
+                for (int pi = 0; pi < MP; ++pi) {
+                    const int q = tid + pi * NT;
+                    mw[pi] = q < nv ? mb[(size_t)mwin * npc + (j0 >> 2) + q] : 0ull;
+                }
+            }
+#pragma unroll
+            for (int pi = 0; pi < MP; ++pi) {
+                const int q = tid + pi * NT;
+                if (q >= nv) break;
                 const int off = q * 4;
                 const float *src = chi + pb + off;
-                if (CB && !((mb[(size_t)(id >> 6) * npc + (j0 >> 2) + q] >> (id & 63)) & 1ull))
-                    src = c0base + (long long)id * plane + j0 + off;
+                if (CB && !((mw[pi] >> (id & 63)) & 1ull)) src = c0base + (long long)id * plane + j0 + off;
                 cp_async_n<16>(&rg[2 * pstride + off], src);
             }
         }
