@@ -291,6 +291,9 @@ def bench_ours(args):
     spec = inputs.jet(n=args.grid)
     prec = args.precision
     solver = native.Solver.from_spec(spec, device=local, precision=prec)
+    if args.sweep_schedule:
+        sc, snt = (int(v) for v in args.sweep_schedule.split(","))
+        solver.set_sweep_schedule(sc, snt)
     solver.zero_state()
     stream = torch.cuda.Stream(dev)  # a real stream: its handle is never 0
     torch.cuda.set_stream(stream)
@@ -849,6 +852,8 @@ def main():
     ap.add_argument("--grid", type=int, default=None,
                     help="nodes per axis (defaults: 64 for the jet, 96 for config 3, 128 for config 5; smaller "
                          "for profiling)")
+    ap.add_argument("--sweep-schedule", default=None, metavar="C,NT",
+                    help="force the FP32 sweep schedule (cluster CTAs, threads) instead of timing the candidates")
     ap.add_argument("--source-path", default="auto", choices=["auto", "cuda", "tensor"],
                     help="source pass of group-mixing kernels in MIXED (configs 3, 5): timed choice or forced")
     args = ap.parse_args()

@@ -647,6 +647,31 @@ __device__ inline void sc_weights_narrow<double>(double x, double &e, double &wp
     sc_weights<double>(x, e, wp, wu);
 }
 
+// The same weights with the two series of the small-x branch advanced
+// together by packed FP32 instructions (lane 0 wp, lane 1 wu; each lane
+// rounds exactly as the scalar fused multiply-add does).
+__device__ inline void sc_weights_narrow_x2(float x, float &e, float &wp, float &wu)
+{
+    e = hw_exp2(-x * kLog2eF);
+    if (x < 0.5f) {
+        const float2 nx = make_float2(-x, -x);
+        float2 a = __ffma2_rn(nx, make_float2(1.f / 362880.f, 1.f / 45360.f), make_float2(1.f / 40320, 1.f / 5760));
+        a = __ffma2_rn(nx, a, make_float2(1.f / 5040, 1.f / 840));
+        a = __ffma2_rn(nx, a, make_float2(1.f / 720, 1.f / 144));
+        a = __ffma2_rn(nx, a, make_float2(1.f / 120, 1.f / 30));
+        a = __ffma2_rn(nx, a, make_float2(1.f / 24, 1.f / 8));
+        a = __ffma2_rn(nx, a, make_float2(1.f / 6, 1.f / 3));
+        a = __ffma2_rn(nx, a, make_float2(1.f / 2, 1.f / 2));
+        a = __fmul2_rn(make_float2(x, x), a);
+        wp = a.x;
+        wu = a.y;
+        return;
+    }
+    float a0 = (1.f - e) * hw_rcp(x);
+    wp = 1.f - a0;
+    wu = a0 - e;
+}
+
 template <>
 __device__ inline void sc_weights_narrow<float>(float x, float &e, float &wp, float &wu)
 {

@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
                 const float dtau = s * 0.5f * (cu + ct);
                 float ew, wp, wu;
                 if constexpr (WIDE) sc_weights<float>(dtau, ew, wp, wu);
-                else sc_weights_narrow<float>(dtau, ew, wp, wu);
+                else sc_weights_narrow_x2(dtau, ew, wp, wu);
                 inew = iu * ew + st * wp + su * wu;
             }
             Qn[j] = make_float4(inew, st, ct, 0.f);
@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sweep_cl(Prob<float> P, float
                 const float dtau = s * 0.5f * (cu + ct);
                 float ew, wp, wu;
                 if constexpr (WIDE) sc_weights<float>(dtau, ew, wp, wu);
-                else sc_weights_narrow<float>(dtau, ew, wp, wu);
+                else sc_weights_narrow_x2(dtau, ew, wp, wu);
                 inew = iu * ew + st * wp + su * wu;
             }
             Qn[j] = make_float4(inew, st, ct, 0.f);
