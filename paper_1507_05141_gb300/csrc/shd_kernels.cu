@@ -644,24 +644,30 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
         asm volatile("cp.async.wait_group 0;\n" ::);
         __syncthreads();  // this plane's copies and the previous plane's state are visible
         issue(step + 1);
-        const float *r = ring + (size_t)(step & 1) * 3 * pstride;
-        const float4 *Qp = Q + (size_t)((step + 1) & 1) * pstride;  // plane step - 1
-        float4 *Qn = Q + (size_t)(step & 1) * pstride;               // plane step
         const bool first = step == 0;
         const int id = o.sd > 0 ? step : nd - 1 - step;
         const long long pb = base + (long long)id * plane;
+        // per-plane bases of this thread's accesses: node u of the thread is
+        // at a constant offset NT u from each (the upwind ones are formed for
+        // every node but read only off the inflow faces)
+        const float *rI = ring + (size_t)(step & 1) * 3 * pstride + tid;
+        const float *rE = rI + pstride, *rC = rI + 2 * pstride;
+        const float4 *qa = Q + (size_t)((step + 1) & 1) * pstride + tid;  // plane step - 1
+        const float4 *qb = qa - d1, *qc = qa - d2, *qd = qa - d1 - d2;
+        float4 *qn = Q + (size_t)(step & 1) * pstride + tid;               // plane step
+        float *ig = I + pb + tid;
+        const unsigned bnd = first ? ~0u : face;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int j = tid + NT * u;
-            if (j >= plane) break;
-            const float In = r[j];
-            const float ct = r[2 * pstride + j] + kap;
-            const float st = ct > 0.f ? (r[pstride + j] + kap * In) * hw_rcp(ct) : 0.f;
+            if (tid + NT * u >= plane) break;
+            const float In = rI[NT * u];
+            const float ct = rC[NT * u] + kap;
+            const float st = ct > 0.f ? (rE[NT * u] + kap * In) * hw_rcp(ct) : 0.f;
             float inew;
-            if (first || ((face >> u) & 1u)) {
-                inew = bc_full ? P.bc[pb + j] : bc_iso;
+            if ((bnd >> u) & 1u) {
+                inew = bc_full ? P.bc[pb + tid + NT * u] : bc_iso;
             } else {
-                const float4 q00 = Qp[j], q10 = Qp[j - d1], q01 = Qp[j - d2], q11 = Qp[j - d1 - d2];
+                const float4 q00 = qa[NT * u], q10 = qb[NT * u], q01 = qc[NT * u], q11 = qd[NT * u];
                 const float iu = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
                 const float su = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
                 const float cu = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
@@ -671,8 +677,8 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
                 else sc_weights_narrow_x2(dtau, ew, wp, wu);
                 inew = iu * ew + st * wp + su * wu;
             }
-            Qn[j] = make_float4(inew, st, ct, 0.f);
-            I[pb + j] = inew;
+            qn[NT * u] = make_float4(inew, st, ct, 0.f);
+            ig[NT * u] = inew;
         }
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
