@@ -169,7 +169,8 @@ void free_all(shd_ctx *c)
                      (void **)&c->d_int2mesh, (void **)&c->d_mesh2int,
                      &c->d_chi0L, (void **)&c->d_mbits, &c->d_seg[0], &c->d_seg[1], &c->d_tcs_Bh[0], &c->d_tcs_Bh[1], &c->d_tcs_Bl[0],
                      &c->d_tcs_Bl[1], &c->d_tcs_Yh[0], &c->d_tcs_Yh[1], &c->d_tcs_Yl[0], &c->d_tcs_Yl[1],
-                     (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_fcheck,
+                     (void **)&c->d_tc_err, &c->d_rtab[0], &c->d_rtab[1], (void **)&c->d_rrng[0],
+                     (void **)&c->d_rrng[1], &c->d_dirs64, &c->d_fstage, &c->d_fcheck,
                      &c->d_ng[0], &c->d_ng[1], &c->d_ng[2], (void **)&c->d_ngpart, &c->d_rk[0], &c->d_rk[1],
                      &c->d_rk[2], (void **)&c->d_sums_save, &c->d_tcK, (void **)&c->d_thb,
                      (void **)&c->d_thperm, &c->d_thw, &c->d_thK, &c->d_thso, (void **)&c->d_thchunk};
@@ -212,7 +213,8 @@ void drop_sized(shd_ctx *c)
                      (void **)&c->d_partial, (void **)&c->d_stage,
                      &c->d_tiles, (void **)&c->d_moving, (void **)&c->d_mflag,
                      (void **)&c->d_midx, (void **)&c->d_mtiles, &c->d_nm[0], &c->d_nm[1], &c->d_nm[2],
-                     &c->d_rtab[0], &c->d_rtab[1], &c->d_fstage, &c->d_ng[0], &c->d_ng[1], &c->d_ng[2],
+                     &c->d_rtab[0], &c->d_rtab[1], (void **)&c->d_rrng[0], (void **)&c->d_rrng[1], &c->d_fstage,
+                     &c->d_ng[0], &c->d_ng[1], &c->d_ng[2],
                      &c->d_rk[0], &c->d_rk[1], &c->d_rk[2], &c->d_tcK, (void **)&c->d_thb,
                      (void **)&c->d_thperm, &c->d_thw, &c->d_thK, &c->d_thso, (void **)&c->d_thchunk};
     for (void **p : ptrs) dfree(*p);
@@ -479,6 +481,7 @@ void order_ordinates(shd_ctx *c)
 int upload_angles(shd_ctx *c)
 {
     dfree(c->d_ord); dfree(c->d_W); dfree(c->d_dirs); dfree(c->d_Y); dfree(c->d_mu); dfree(c->d_Bproj);
+    dfree(c->d_dirs64);
     dfree((void *&)c->d_int2mesh); dfree((void *&)c->d_mesh2int);
     order_ordinates(c);
     build_geometry(c);
@@ -507,6 +510,8 @@ int upload_angles(shd_ctx *c)
         c->d_mu = to_device_vec<float>(c->h_mu, c->bytes, e); CK(e, "mu");
         c->d_Bproj = to_device_vec<float>(Bp, c->bytes, e); CK(e, "Bproj");
     }
+    // FP64 directions for the remap tables' edge decisions
+    c->d_dirs64 = to_device_vec<double>(c->h_dirs, c->bytes, e); CK(e, "dirs (FP64)");
     return upload_tc_operands(c, Bp);
 }
 
@@ -835,17 +840,26 @@ cudaError_t check_fields(shd_ctx *c, const double *alpha0, const double *ne, con
 // kernels compute the boosts and stencils in place.
 int ensure_remap_tables(shd_ctx *c, cudaStream_t st)
 {
-    if (is_fp64(c) || c->rtab_valid || c->nmoving == 0 || !c->have_fields || !c->have_angles || c->nmu > 1024)
-        return SHD_OK;  // (the entries pack the ring index in 10 bits)
+    // (the entries pack the ring index in 10 bits, the group ranges in 8)
+    if (is_fp64(c) || c->rtab_valid || c->nmoving == 0 || !c->have_fields || !c->have_angles || c->nmu > 1024 ||
+        c->G > 255 || !c->d_fstage || !c->fstage_u_current || !c->d_dirs64)
+        return SHD_OK;
     const size_t n = (size_t)c->nmoving * c->N;
     int rc;
-    if (n != c->rtab_n || !c->d_rtab[0] || !c->d_rtab[1]) {
+    if (n != c->rtab_n || !c->d_rtab[0] || !c->d_rtab[1] || !c->d_rrng[0] || !c->d_rrng[1]) {
         c->rtab_n = 0;
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < 2; ++i) {
             if ((rc = dalloc(c, &c->d_rtab[i], n * sizeof(float4), "remap tables"))) return rc;
+            if ((rc = dalloc(c, (void **)&c->d_rrng[i], n * sizeof(unsigned short), "remap group ranges"))) return rc;
+        }
         c->rtab_n = n;
     }
-    CK(launch_remap_tables_f(c, (float4 *)c->d_rtab[0], (float4 *)c->d_rtab[1], c->stream), "remap tables");
+    // the flow as last given (FP64), still in the field staging area
+    const size_t nCG = (size_t)c->Nc * c->G;
+    const double *u64 = (const double *)c->d_fstage + 2 * nCG + (size_t)c->Nc;
+    CK(launch_remap_tables_f(c, (float4 *)c->d_rtab[0], (float4 *)c->d_rtab[1], c->d_rrng[0], c->d_rrng[1], u64,
+                             (const double *)c->d_dirs64, c->stream),
+       "remap tables");
     if (st) {
         if ((rc = stream_after(st, c->stream))) return rc;
     } else {
@@ -1276,6 +1290,7 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         c->fstage_n = nf;
     }
     double *sa = (double *)c->d_fstage, *se = sa + nCG, *sn = se + nCG, *su = sn + Nc;
+    c->fstage_u_current = false;  // until these fields are accepted
     CK(cudaMemcpyAsync(sa, alpha0, nCG * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D alpha0");
     CK(cudaMemcpyAsync(se, emis0, nCG * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D emis0");
     CK(cudaMemcpyAsync(sn, ne, Nc * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D ne");
@@ -1317,6 +1332,7 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         if ((rc = build_tiles(c, u))) return rc;
     }
     c->have_fields = true;
+    c->fstage_u_current = true;
     if (theta_e) {
         if ((rc = set_theta(c, theta_e))) return rc;
     } else if (c->have_theta) {
@@ -1852,6 +1868,7 @@ int shd_stage_project(shd_ctx *c, const double *I, double *Ish, double *J, doubl
     int rc = ctx_check(c);
     if (rc) return rc;
     if ((rc = ready_for_step(c))) return rc;
+    if ((rc = ensure_remap_tables(c, nullptr))) return rc;  // the remaps as a step runs them
     if (!I) return fail(SHD_ERR_ARG, "I is NULL");
     if ((rc = shd_set_state(c, I))) return rc;
     return shd_get_moments(c, J, H, K, Ish);
@@ -1879,6 +1896,7 @@ int shd_stage_sh2lab(shd_ctx *c, const double *Ssh, double *eta_lab, double *chi
     int rc = ctx_check(c);
     if (rc) return rc;
     if ((rc = ready_for_step(c))) return rc;
+    if ((rc = ensure_remap_tables(c, nullptr))) return rc;  // the remaps as a step runs them
     if (!Ssh || !eta_lab || !chi_lab) return fail(SHD_ERR_ARG, "null array");
     size_t n = (size_t)c->Nc * c->G * c->NLM;
     if (is_fp64(c)) {

@@ -198,6 +198,9 @@ struct shd_ctx {
     // laboratory, nu/nu0), [1] laboratory remap (n_k boosted to the comoving
     // frame, nu0/nu); rebuilt after the fields or angles change
     void *d_rtab[2] = {nullptr, nullptr};
+    unsigned short *d_rrng[2] = {nullptr, nullptr};  // FP64-decided in-range output groups of the remap tables
+    void *d_dirs64 = nullptr;                         // internal-order directions in FP64
+    bool fstage_u_current = false;                    // the staging area holds the flow in use
     size_t rtab_n = 0;
     bool rtab_valid = false;
     void *d_lc = nullptr, *d_linv = nullptr;  // log-energy group tables
@@ -769,7 +772,8 @@ cudaError_t launch_project_seg(const shd_ctx *ctx, const float *I, float *Ip, fl
                                cudaStream_t st);
 cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,
                               float *nm2, cudaStream_t st, bool full_chi);
-cudaError_t launch_remap_tables_f(const shd_ctx *ctx, float4 *tc, float4 *tl, cudaStream_t st);
+cudaError_t launch_remap_tables_f(const shd_ctx *ctx, float4 *tc, float4 *tl, unsigned short *rc, unsigned short *rl,
+                                  const double *u64, const double *dirs64, cudaStream_t st);
 cudaError_t launch_remap_to_comoving_f(const shd_ctx *ctx, const float *nm0, float *nm1, cudaStream_t st);
 cudaError_t launch_remap_to_lab_f(const shd_ctx *ctx, const float *nm0, float *nm1, float *nm2, cudaStream_t st);
 size_t project_tc_smem_bytes(const shd_ctx *ctx);

@@ -1705,7 +1705,8 @@ static cudaError_t run_sweep_sched(const shd_ctx *ctx, const SweepSched &sc, flo
     }
 #define SHD_CL(NTv, Uv) \
     if (sc.NT == NTv && sc.U == Uv) return launch_sweep_cl_t<Uv, NTv>(ctx, sc, I, eta, chi, st, bits, wide, n, tune_stride);
-    SHD_CL(256, 2) SHD_CL(256, 4) SHD_CL(512, 2) SHD_CL(512, 4) SHD_CL(1024, 2) SHD_CL(1024, 4)
+    SHD_CL(256, 2) SHD_CL(256, 4) SHD_CL(384, 3) SHD_CL(512, 2) SHD_CL(512, 4) SHD_CL(768, 3) SHD_CL(1024, 2)
+    SHD_CL(1024, 4)
 #undef SHD_CL
     return cudaErrorInvalidConfiguration;
 }
@@ -1725,10 +1726,15 @@ static bool sweep_sched_make(const shd_ctx *c, int C, int NT, SweepSched &sc)
         return true;
     }
     if (C != 2 && C != 4 && C != 8) return false;
-    if (NT != 256 && NT != 512 && NT != 1024) return false;
+    if (NT != 256 && NT != 384 && NT != 512 && NT != 768 && NT != 1024) return false;
     const int nl = sweep_nloc_max(c, C);
     int U = 0;
-    if (nl <= 2 * NT) U = 2;
+    if (NT == 384 || NT == 768) {
+        // three nodes a thread: blocks that 2 or 4 a thread would fit loosely
+        // (1152 nodes: 384 x 3 exactly, against 512 x 4 with a third idle)
+        if (nl <= 2 * NT || nl > 3 * NT) return false;
+        U = 3;
+    } else if (nl <= 2 * NT) U = 2;
     else if (nl <= 4 * NT) U = 4;
     else return false;
     if (nl <= NT / 2) return false;  // half the threads or more would idle
@@ -1745,7 +1751,7 @@ static std::vector<SweepSched> sweep_candidates(const shd_ctx *c)
     SweepSched sc;
     if (sweep_sched_make(c, 1, 1024, sc)) v.push_back(sc);
     for (int C : {2, 4, 8})
-        for (int NT : {256, 512, 1024})
+        for (int NT : {256, 384, 512, 768, 1024})
             if (sweep_sched_make(c, C, NT, sc)) v.push_back(sc);
     return v;
 }

@@ -646,7 +646,23 @@ __device__ inline Stencil<T> table_stencil(const float4 &e, int nphi, const int 
 // kernels would compute them: tc for the comoving remap (n_k taken to the
 // laboratory, nu/nu0), tl for the laboratory remap (n_k taken to the
 // comoving frame, nu0/nu).  They depend only on the flow and the angles.
-__global__ void __launch_bounds__(256) k_remap_tables(Prob<float> P, float4 *__restrict__ tc, float4 *__restrict__ tl)
+// rc, rl: the output groups whose looked-up energy (centre x the ratio) lies
+// within the outer group edges, [lo, hi) packed as lo | hi << 8, decided in
+// FP64 from the FP64 flow and directions.  Beyond the edges the remapped
+// intensity is zero (Sec. 2.2), a jump that a single-precision ratio would
+// place a rounding away from where the FP64 definition puts it.
+__device__ inline unsigned short group_range(const Prob<float> &P, double r)
+{
+    const int G = P.G;
+    int lo = 0, hi = G;
+    while (lo < G && P.centre[lo] * r < P.edges[0]) ++lo;
+    while (hi > lo && P.centre[hi - 1] * r > P.edges[G]) --hi;
+    return (unsigned short)(lo | (hi << 8));
+}
+
+__global__ void __launch_bounds__(256) k_remap_tables(Prob<float> P, float4 *__restrict__ tc, float4 *__restrict__ tl,
+                                                      unsigned short *__restrict__ rc, unsigned short *__restrict__ rl,
+                                                      const double *__restrict__ u64, const double *__restrict__ dirs64)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.nmoving * P.N) return;
@@ -660,6 +676,11 @@ __global__ void __launch_bounds__(256) k_remap_tables(Prob<float> P, float4 *__r
     tc[i] = table_entry(stencil_params<float>(P.mu, P.nmu, P.nphi, nb), q);
     const float D = boost_any<float>(u, nk, nb, 1.f, P.fp64_boost);
     tl[i] = table_entry(stencil_params<float>(P.mu, P.nmu, P.nphi, nb), D);
+    const double ud[3] = {u64[3 * c], u64[3 * c + 1], u64[3 * c + 2]};
+    const double nd[3] = {dirs64[3 * k], dirs64[3 * k + 1], dirs64[3 * k + 2]};
+    double od[3];
+    rc[i] = group_range(P, boost_dir<double>(ud, nd, od, -1.0));
+    rl[i] = group_range(P, boost_dir<double>(ud, nd, od, 1.0));
 }
 
 // Energy offset x = l / (log spacing) of equally spaced log centres, split
@@ -731,7 +752,8 @@ __device__ inline T chi_mix(const T *schi, const T *slr, int ga, T t)
 // compiler would otherwise evaluate alongside it.
 template <class T, int TAB>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comoving(Prob<T> P, const T *__restrict__ In, T *__restrict__ I0,
-                                                           const float4 *__restrict__ tab)
+                                                           const float4 *__restrict__ tab,
+                                                           const unsigned short *__restrict__ rng)
 {
     static_assert(!TAB || sizeof(T) == 4, "the remap tables are FP32");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -760,10 +782,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
     for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x, ++iter) {
         T q;  // nu/nu0
         Stencil<T> st;
+        // output groups [glo, ghi) look up energies within the outer edges
+        // (the table's FP64 decision; in place, the working precision's)
+        int glo = 0, ghi = G;
         if constexpr (TAB) {
             const float4 e = iter == 0 ? epre[0] : (iter == 1 ? epre[1] : tab[m * N + k0]);
             q = (T)e.w;
             st = table_stencil<T>(e, P.nphi, tb.m2i);
+            const unsigned r = rng[m * N + k0];
+            glo = (int)(r & 255u);
+            ghi = (int)(r >> 8);
         } else {
             T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
             T n[3];
@@ -786,7 +814,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
             T *out = dst + k0;
             if (gm0 > 0) {
                 const T v0 = fs.eval(sI, spole, N, 0);
-                for (int g0 = 0; g0 < gm0; ++g0, out += N) *out = (T(g0) + us.x >= P.lgx0 ? v0 : T(0)) * iq3;
+                for (int g0 = 0; g0 < gm0; ++g0, out += N) {
+                    const bool in = TAB ? g0 >= glo : T(g0) + us.x >= P.lgx0;
+                    *out = (in ? v0 : T(0)) * iq3;
+                }
             }
             if (gm1 > gm0) {
                 int ga = gm0 + us.s, g0 = gm0;
@@ -805,13 +836,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
             }
             if (gm1 < G) {
                 const T v1 = fs.eval(sI, spole, N, G - 1);
-                for (int g0 = gm1; g0 < G; ++g0, out += N) *out = (T(g0) + us.x <= P.lgx1 ? v1 : T(0)) * iq3;
+                for (int g0 = gm1; g0 < G; ++g0, out += N) {
+                    const bool in = TAB ? g0 < ghi : T(g0) + us.x <= P.lgx1;
+                    *out = (in ? v1 : T(0)) * iq3;
+                }
             }
             continue;
         }
         int hint = 0;
         for (int g0 = 0; g0 < G; ++g0) {
             FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, tb.lc[g0] + lq, hint);
+            if (TAB) {  // inside or beyond the edges as the table decided
+                if (g0 < glo || g0 >= ghi) fb.mode = 0;
+                else if (fb.mode == 0) fb.mode = 1;  // the nearest outer group (fb.ga)
+            }
             T v = 0;
             if (fb.mode == 1) {
                 v = cache.get(st, sI, spole, N, fb.ga);
@@ -830,7 +868,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
 // S_lab = S0(n0, eps0)/D^3, chi_lab = chi0(eps0) D, eta_lab = chi_lab S_lab
 template <class T, int TAB>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Prob<T> P, const T *__restrict__ S0, T *__restrict__ eta_n,
-                                                      T *__restrict__ chi_n, const float4 *__restrict__ tab)
+                                                      T *__restrict__ chi_n, const float4 *__restrict__ tab,
+                                                      const unsigned short *__restrict__ rng)
 {
     static_assert(!TAB || sizeof(T) == 4, "the remap tables are FP32");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -856,10 +895,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         T D;  // nu0/nu
         Stencil<T> st;
+        // output groups [glo, ghi) look up source energies within the outer
+        // edges (the table's FP64 decision; in place, the working precision's)
+        int glo = 0, ghi = G;
         if constexpr (TAB) {
             const float4 e = tab[m * N + k];
             D = (T)e.w;
             st = table_stencil<T>(e, P.nphi, tb.m2i);
+            const unsigned r = rng[m * N + k];
+            glo = (int)(r & 255u);
+            ghi = (int)(r >> 8);
         } else {
             T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
             T n0[3];
@@ -881,8 +926,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
                 const T v0 = fs.eval(sS, spole, N, 0);
                 const T chl = schi[0] * D;
                 for (int g = 0; g < gm0; ++g, oe += N, oc += N) {
+                    const bool in = TAB ? g >= glo : T(g) + us.x >= P.lgx0;
                     *oc = chl;
-                    *oe = chl * (T(g) + us.x >= P.lgx0 ? v0 : T(0)) * iD3;
+                    *oe = chl * (in ? v0 : T(0)) * iD3;
                 }
             }
             if (gm1 > gm0) {
@@ -915,8 +961,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
                 const T v1 = fs.eval(sS, spole, N, G - 1);
                 const T chl = schi[G - 1] * D;
                 for (int g = gm1; g < G; ++g, oe += N, oc += N) {
+                    const bool in = TAB ? g < ghi : T(g) + us.x <= P.lgx1;
                     *oc = chl;
-                    *oe = chl * (T(g) + us.x <= P.lgx1 ? v1 : T(0)) * iD3;
+                    *oe = chl * (in ? v1 : T(0)) * iD3;
                 }
             }
             continue;
@@ -924,6 +971,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
         int hint = 0;
         for (int g = 0; g < G; ++g) {
             FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, tb.lc[g] + lD, hint);
+            if (TAB) {  // inside or beyond the edges as the table decided
+                if (g < glo || g >= ghi) fb.mode = 0;
+                else if (fb.mode == 0) fb.mode = 1;  // the nearest outer group (fb.ga)
+            }
             T s = 0, ch;
             if (fb.mode == 0) {
                 ch = schi[fb.ga];
@@ -1028,7 +1079,7 @@ static cudaError_t run_remap_to_comoving(const shd_ctx *ctx, const T *nm0, T *nm
     auto kern = (sizeof(T) == 4 && tab) ? k_remap_to_comoving<T, sizeof(T) == 4> : k_remap_to_comoving<T, 0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1, tab);
+    kern<<<(unsigned)ctx->nmoving, 256, sm, st>>>(P, nm0, nm1, tab, tab ? ctx->d_rrng[0] : nullptr);
     note_launch();
     return cudaGetLastError();
 }
@@ -1042,17 +1093,18 @@ static cudaError_t run_remap_to_lab(const shd_ctx *ctx, const T *nm0, T *nm1, T 
     auto kern = (sizeof(T) == 4 && tab) ? k_remap_to_lab<T, sizeof(T) == 4> : k_remap_to_lab<T, 0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2, tab);
+    kern<<<(unsigned)ctx->nmoving, 256, sr, st>>>(P, nm0, nm1, nm2, tab, tab ? ctx->d_rrng[1] : nullptr);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_remap_tables_f(const shd_ctx *ctx, float4 *tc, float4 *tl, cudaStream_t st)
+cudaError_t launch_remap_tables_f(const shd_ctx *ctx, float4 *tc, float4 *tl, unsigned short *rc, unsigned short *rl,
+                                  const double *u64, const double *dirs64, cudaStream_t st)
 {
     Prob<float> P = make_prob<float>(ctx);
     const long long n = ctx->nmoving * ctx->N;
     if (n == 0) return cudaSuccess;
-    k_remap_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, tc, tl);
+    k_remap_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, tc, tl, rc, rl, u64, dirs64);
     note_launch();
     return cudaGetLastError();
 }

@@ -332,6 +332,51 @@ def test_steps_mixed_tma_tiles(native, grid):
     assert np.max(np.abs(f - O.moments_to_eddington(J_r, K_r))) < MIXED_TOL
 
 
+def _closest_edge_lookup(spec):
+    """Smallest distance, in log energy, between an outer group edge and an
+    energy a remap looks up (group centre times Gamma -/+ u.n, Sec. 2.2) over
+    the moving nodes, ordinates and groups, in FP64."""
+    mv = np.nonzero(np.any(spec.u != 0, axis=1))[0]
+    u = spec.u[mv]
+    gam = np.sqrt(1.0 + np.sum(u * u, axis=1))
+    mu, _ = np.polynomial.legendre.leggauss(spec.nmu)
+    ph = 2.0 * np.pi * np.arange(spec.nphi) / spec.nphi
+    st = np.sqrt(1.0 - mu * mu)
+    n = np.stack([np.outer(st, np.cos(ph)).ravel(), np.outer(st, np.sin(ph)).ravel(),
+                  np.repeat(mu, spec.nphi)], axis=1)
+    cen = np.sqrt(spec.edges[:-1] * spec.edges[1:])
+    lo, hi = np.log(spec.edges[0]), np.log(spec.edges[-1])
+    best = np.inf
+    for sgn in (1.0, -1.0):
+        r = gam[:, None] - sgn * (u @ n.T)
+        for g in range(spec.G):
+            le = np.log(cen[g] * r)
+            best = min(best, float(np.min(np.minimum(np.abs(le - lo), np.abs(le - hi)))))
+    return best
+
+
+def test_remap_edges_decided_in_fp64(native):
+    """Beyond the outer group edges the remapped intensity is zero (Sec.
+    2.2): a jump in the Doppler ratio.  On this flow one moving node's
+    ordinate looks up an energy 1.4e-7 (in log energy) above the top edge,
+    within the rounding of a single-precision ratio, which would put it
+    inside.  The remap tables decide every edge in FP64 from the FP64 flow
+    and directions, as the oracle does, so the FP32 and MIXED laboratory
+    emissivities match the oracle there as everywhere else."""
+    spec = inputs.ragged_mixed(grid=(48, 48, 16), G=2, L=3)
+    assert _closest_edge_lookup(spec) < 1e-6  # the case this test is about
+    P = _oracle(spec)
+    I0 = inputs.random_state(spec, seed=41)
+    S = P.source(P.project(I0)[0])
+    eta_r, chi_r = P.sh2lab(S)
+    for precision, tol in (("fp32", FP32_TOL), ("mixed", MIXED_TOL)):
+        s = native.Solver.from_spec(spec, precision=precision)
+        eta, chi = s.stage_sh2lab(S)
+        s.close()
+        assert rel(eta, eta_r) < tol, precision
+        assert rel(chi, chi_r) < tol, precision
+
+
 @pytest.mark.parametrize("grid", [(11, 9, 7), (62, 6, 6), (130, 6, 5), (17, 13, 9)])
 def test_steps_mixed_ragged_rows(native, grid):
     """Mixed path on grids whose plane rows are not multiples of 4 nodes (no

@@ -13,8 +13,13 @@ eq:shdom, Sec. 2.1 eq:time).  Grids:
   cluster barrier);
 * (62, 52, 6): rows of 62 nodes, so a block must hold an even number of rows
   to start on a 16-byte boundary;
-* (96, 96, 4): 9216-node planes, too large for one CTA's shared memory (only
-  clusters can sweep them).
+* (96, 96, 32): 9216-node planes, too large for one CTA's shared memory (only
+  clusters can sweep them).  The z spacing is 2.8 times the x spacing, so the
+  ordinates of the outer rings (|mu| = 0.96: |n_z| / |n_x| = 3.4) cross z
+  faces first and the z-class, whose planes these are, is not empty (a grid
+  of 4 z-nodes would leave it empty and sweep only 384-node planes).  8 x 384
+  and 4 x 768 threads hold its blocks of 1152 and 2304 nodes at exactly three
+  nodes a thread.
 """
 import numpy as np
 import pytest
@@ -25,8 +30,8 @@ from paper_1507_05141_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 2e-5
-SCHEDULES = [(1, 1024), (2, 256), (2, 512), (2, 1024), (4, 256), (4, 512), (4, 1024), (8, 256), (8, 512),
-             (8, 1024)]
+SCHEDULES = [(1, 1024), (2, 256), (2, 384), (2, 512), (2, 768), (2, 1024), (4, 256), (4, 384), (4, 512),
+             (4, 768), (4, 1024), (8, 256), (8, 384), (8, 512), (8, 768), (8, 1024)]
 
 
 @pytest.fixture(scope="module")
@@ -47,13 +52,13 @@ def _oracle_step(spec, I0):
     return I
 
 
-@pytest.mark.parametrize("grid", [(60, 52, 6), (62, 52, 6), (96, 96, 4)])
+@pytest.mark.parametrize("grid", [(60, 52, 6), (62, 52, 6), (96, 96, 32)])
 def test_every_schedule(native, grid):
     spec = inputs.ragged_mixed(grid=grid, G=2, L=3)
     I0 = inputs.random_state(spec, seed=41)
     I_ref = _oracle_step(spec, I0)
     scale = np.max(np.abs(I_ref), axis=0, keepdims=True)
-    results = {}
+    ran, first = [], None
     s = native.Solver.from_spec(spec, precision="fp32")
     for C, NT in SCHEDULES:
         try:
@@ -66,14 +71,16 @@ def test_every_schedule(native, grid):
         assert s.sweep_schedule()[0] == (C, NT)
         err = float(np.max(np.abs(I - I_ref) / scale))
         assert err < FP32_TOL, ((C, NT), err)
-        results[(C, NT)] = I
+        if first is None:
+            first = ((C, NT), I)
+        else:
+            assert np.array_equal(I, first[1]), ((C, NT), first[0])
+        ran.append((C, NT))
     s.close()
-    assert any(c > 1 for c, _ in results), "no cluster schedule ran"
-    if grid == (96, 96, 4):
-        assert (1, 1024) not in results  # the 9216-node planes need a cluster
-    keys = list(results)
-    for key in keys[1:]:
-        assert np.array_equal(results[key], results[keys[0]]), (key, keys[0])
+    assert any(c > 1 for c, _ in ran), "no cluster schedule ran"
+    if grid == (96, 96, 32):
+        assert (1, 1024) not in ran  # the 9216-node planes need a cluster
+        assert (8, 384) in ran and (4, 768) in ran  # three nodes a thread
 
 
 def test_automatic_choice_is_timed_and_kept(native):
