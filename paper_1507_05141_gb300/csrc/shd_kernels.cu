@@ -232,6 +232,10 @@ __global__ void __launch_bounds__(256, 3) k_source_sums(Prob<T> P, const T *__re
         } else {
         for (int i = lane; i < G * NLM; i += 32) wI[i] = Ip[base + i];
         __syncwarp();
+        // the node's part of |S|^2 and |S - S_prev|^2 in working precision,
+        // added to the FP64 totals once per node (an FP64 operation per
+        // output would occupy the narrow FP64 pipe longer than the source)
+        T dn = T(0), nm = T(0);
         for (int p = lane; p < NLM; p += 32) {
             int l = 0;
             while ((l + 1) * (l + 1) <= p) ++l;
@@ -247,14 +251,15 @@ __global__ void __launch_bounds__(256, 3) k_source_sums(Prob<T> P, const T *__re
                 }
                 const long long i = base + (long long)g * NLM + p;
                 Sp[i] = s;
-                const double sn = (double)s;
-                den += sn * sn;
+                dn += s * s;
                 if (have_prev) {
-                    const double d = sn - (double)Sprev[i];
-                    num += d * d;
+                    const T d = s - Sprev[i];
+                    nm += d * d;
                 }
             }
         }
+        den += (double)dn;
+        num += (double)nm;
         }
         for (int g = lane; g < G; g += 32) {
             const double J = (double)mom[(c * G + g) * 10];
@@ -282,6 +287,182 @@ __global__ void __launch_bounds__(256, 3) k_source_sums(Prob<T> P, const T *__re
         double acc = 0;
         for (int w = 0; w < 8; ++w) acc += red[threadIdx.x][w];
         partial[blockIdx.x * 4 + threadIdx.x] = acc;
+    }
+}
+
+// asynchronous copy of BYTES (4, 8 or 16) from global to shared memory
+template <int BYTES>
+__device__ inline void cp_async_n(void *smem, const void *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES));
+}
+
+// -------------------------------------------------------------------------
+// a2 + a5 for kernels that mix groups (Klein-Nishina, any non-diagonal
+// table), FP32: per l the dense contraction S_l[g][(c, m)] = n_e/chi0 sum_g'
+// K_l[g][g'] I_l[g'][(c, m)] (Sec. 2.3, eq:source) on the CUDA cores,
+// register-blocked.  A unit is (l, group block of 4, m); a thread holds its
+// unit's 4 groups x TN nodes of one harmonic p and, per g', takes the four
+// K_l[g][g'] in one 16-byte load (K stored [l][g'][g]) and the TN values
+// I[c][g'][p] as broadcasts: 32 FMAs a 9 loads at TN = 8.  Units run
+// l-major, m fastest, so the lanes of a warp share a K row.  Tiles of TN
+// consecutive nodes (one contiguous [TN][G][NLM] block of I_lm) stream
+// through a two-stage cp.async ring; the CTA is persistent over tiles.  The
+// residual parts |S|^2, |S - S_prev|^2 accumulate per unit in FP32 and join
+// the FP64 totals once per unit; the energy and photon sums stay FP64.
+// -------------------------------------------------------------------------
+template <int TN>
+__global__ void __launch_bounds__(512, 1) k_source_kn(Prob<float> P, const float *__restrict__ Ip,
+                                                      float *__restrict__ Sp, const float *__restrict__ mom,
+                                                      const float *__restrict__ Sprev, int have_prev,
+                                                      double *partial)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4][16];
+    const int G = P.G, NLM = P.NLM, L = P.L;
+    const int Gb = (G + 3) / 4, G4 = 4 * Gb;
+    const int tile_f = TN * G * NLM;  // floats of one tile of I_lm
+    float *sK = reinterpret_cast<float *>(smem_raw);  // [L+1][G][G4]: K_l[g][g'] at [l][g'][g]
+    float *sI = sK + (size_t)(L + 1) * G * G4;        // [2][TN][G][NLM]
+    float *sR = sI + (size_t)2 * tile_f;              // [TN][G4] n_e/chi0 (0 where chi0 <= 0)
+    float *sE = sR + TN * G4;                         // [TN][G4] sqrt(4 pi) eta0/chi0
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < (L + 1) * G * G4; i += nt) {
+        const int l = i / (G * G4), rem = i - l * G * G4, gp = rem / G4, g = rem - gp * G4;
+        sK[i] = g < G ? P.K[((size_t)l * G + g) * G + gp] : 0.f;
+    }
+    const long long ntile = (P.Nc + TN - 1) / TN;
+    auto load = [&](long long t, int buf) {
+        if (t < ntile) {
+            const long long c0 = t * TN;
+            const int nn = (int)(P.Nc - c0 < TN ? P.Nc - c0 : TN);
+            const int nv = nn * G * NLM / 4;  // 16-byte pieces (G NLM is a multiple of 4)
+            const float *src = Ip + c0 * G * NLM;
+            float *dst = sI + (size_t)buf * tile_f;
+            for (int q = tid; q < nv; q += nt) cp_async_n<16>(dst + 4 * q, src + 4 * q);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+    double e = 0, ph = 0, num = 0, den = 0;
+    const int nunit = Gb * NLM;
+    load(blockIdx.x, 0);
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const long long c0 = t * TN;
+        const int nn = (int)(P.Nc - c0 < TN ? P.Nc - c0 : TN);
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncthreads();  // this tile's I_lm landed; the previous tile's reads of sR, sE and its buffer are done
+        load(t + gridDim.x, buf ^ 1);
+        for (int i = tid; i < TN * G4; i += nt) {
+            const int n = i / G4, g = i - n * G4;
+            float r = 0.f, em = 0.f;
+            if (n < nn && g < G) {
+                const long long c = c0 + n;
+                const float chi = P.chi0[c * G + g];
+                if (chi > 0.f) {
+                    r = P.ne[c] / chi;
+                    em = 3.5449077018110320546f * P.emis0[c * G + g] / chi;  // sqrt(4 pi)
+                }
+            }
+            sR[i] = r;
+            sE[i] = em;
+        }
+        for (int i = tid; i < nn * G; i += nt) {
+            const int g = i % G;
+            const double J = (double)mom[(c0 * G + i) * 10];
+            const double de = P.edges[g + 1] - P.edges[g];
+            e += 4.0 * kPi * J * de;
+            ph += 4.0 * kPi * J * de / P.centre[g];
+        }
+        __syncthreads();
+        const float *tI = sI + (size_t)buf * tile_f;
+        for (int u = tid; u < nunit; u += nt) {
+            // unit u: band l holds the Gb (2l + 1) units from Gb l^2 on
+            int l = (int)sqrtf((float)(u / Gb));
+            while (Gb * (l + 1) * (l + 1) <= u) ++l;
+            while (Gb * l * l > u) --l;
+            const int r = u - Gb * l * l, gb = r / (2 * l + 1), p = l * l + (r - gb * (2 * l + 1));
+            float acc[4][TN];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int n = 0; n < TN; ++n) acc[j][n] = 0.f;
+            const float4 *kr = reinterpret_cast<const float4 *>(sK + (size_t)l * G * G4) + gb;
+            const float *ir = tI + p;
+#pragma unroll 4
+            for (int gp = 0; gp < G; ++gp) {
+                const float4 k4 = kr[(size_t)gp * Gb];
+                float iv[TN];
+#pragma unroll
+                for (int n = 0; n < TN; ++n) iv[n] = ir[((size_t)n * G + gp) * NLM];
+#pragma unroll
+                for (int n = 0; n < TN; ++n) {
+                    acc[0][n] += k4.x * iv[n];
+                    acc[1][n] += k4.y * iv[n];
+                    acc[2][n] += k4.z * iv[n];
+                    acc[3][n] += k4.w * iv[n];
+                }
+            }
+            // per group of the unit: its TN outputs, then their TN values of
+            // S_prev loaded together (predicated, in flight at once), then
+            // the stores and the residual parts
+            float dn = 0.f, nmr = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int g = 4 * gb + j;
+                const bool gv = g < G;
+                const long long ob = ((c0 * G + g) * NLM + p);  // node n adds n G NLM
+                float sv[TN], pv[TN];
+#pragma unroll
+                for (int n = 0; n < TN; ++n) {
+                    sv[n] = sR[n * G4 + g] * acc[j][n];
+                    if (p == 0) sv[n] += sE[n * G4 + g];
+                    pv[n] = 0.f;
+                }
+                if (have_prev) {
+#pragma unroll
+                    for (int n = 0; n < TN; ++n)
+                        if (gv && n < nn) pv[n] = Sprev[ob + (long long)n * G * NLM];
+                }
+#pragma unroll
+                for (int n = 0; n < TN; ++n) {
+                    if (gv && n < nn) {
+                        Sp[ob + (long long)n * G * NLM] = sv[n];
+                        dn += sv[n] * sv[n];
+                        const float d = sv[n] - pv[n];
+                        if (have_prev) nmr += d * d;
+                    }
+                }
+            }
+            den += (double)dn;
+            num += (double)nmr;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    // fixed-order reduction: lanes by shuffle, then the warps
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_down_sync(0xffffffffu, e, o);
+        ph += __shfl_down_sync(0xffffffffu, ph, o);
+        num += __shfl_down_sync(0xffffffffu, num, o);
+        den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = e;
+        red[1][warp] = ph;
+        red[2][warp] = num;
+        red[3][warp] = den;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double a = 0;
+        for (int w = 0; w < nw; ++w) a += red[tid][w];
+        partial[blockIdx.x * 4 + tid] = a;
     }
 }
 
@@ -380,15 +561,6 @@ __device__ inline double fast_recip<double>(double x) { return 1.0 / x; }
 template <>
 __device__ inline float fast_recip<float>(float x) { return hw_rcp(x); }
 
-template <int BYTES>
-__device__ inline void cp_async_n(void *smem, const void *gmem)
-{
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES));
-}
 
 // With `mbits` (16-byte copies only), chi comes from the per-ordinate chi_lab
 // only for the 4-node pieces of a plane that hold a moving node (bit id % 64
@@ -1034,13 +1206,22 @@ __global__ void k_sums_partial(Prob<T> P, const T *__restrict__ mom, const T *__
         e += 4.0 * kPi * J * de;
         ph += 4.0 * kPi * J * de / P.centre[g];
     }
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nS; i += stride) {
-        double sn = (double)Sp[i];
-        den += sn * sn;
-        if (have_prev) {
-            double d = sn - (double)Sprev[i];
-            num += d * d;
+    // |S|^2 and |S - S_prev|^2 in working precision over runs of 64 of a
+    // thread's elements, each run's sums then added in FP64 (an FP64
+    // operation per element would occupy the narrow FP64 pipe)
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    while (i < nS) {
+        T dn = T(0), nm = T(0);
+        for (int r = 0; r < 64 && i < nS; ++r, i += stride) {
+            const T sv = Sp[i];
+            dn += sv * sv;
+            if (have_prev) {
+                const T d = sv - Sprev[i];
+                nm += d * d;
+            }
         }
+        den += (double)dn;
+        num += (double)nm;
     }
     red[0][threadIdx.x] = e;
     red[1][threadIdx.x] = ph;
@@ -1287,6 +1468,177 @@ __global__ void __launch_bounds__(256) k_kn_thermal_table(int G, const double *_
 }
 
 // -------------------------------------------------------------------------
+// The thermal form of k_source_kn (FP32): chunks of nodes of one temperature
+// bracket b, the CTA persistent over chunks; per chunk the transposed K of
+// tables b and b+1 in shared memory, tiles of TN of the chunk's nodes (each
+// node's I_lm row contiguous) through the two-stage ring, and per unit two
+// accumulator sets, blended by the node's weight w of the upper table:
+// S_p = n_e/chi0 ((1 - w) sum_g' K_b I + w sum_g' K_(b+1) I) + delta_p0
+// sqrt(4 pi) eta0/chi0.
+// -------------------------------------------------------------------------
+template <int TN>
+__global__ void __launch_bounds__(512, 1) k_source_kn_th(Prob<float> P, const float *__restrict__ Ip,
+                                                         float *__restrict__ Sp, const float *__restrict__ mom,
+                                                         const float *__restrict__ Sprev, int have_prev,
+                                                         double *partial)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4][16];
+    __shared__ long long sC[2][TN];
+    const int G = P.G, NLM = P.NLM, L = P.L;
+    const int Gb = (G + 3) / 4, G4 = 4 * Gb;
+    const int row_f = G * NLM, tile_f = TN * row_f;
+    const size_t kper = (size_t)(L + 1) * G * G4;
+    float *sKa = reinterpret_cast<float *>(smem_raw);  // [L+1][G][G4] transposed, table b
+    float *sKb = sKa + kper;                            // table b + 1
+    float *sI = sKb + kper;                             // [2][TN][G][NLM]
+    float *sR = sI + (size_t)2 * tile_f;                // [TN][G4]
+    float *sE = sR + TN * G4;                           // [TN][G4]
+    float *sW = sE + TN * G4;                           // [TN]
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nunit = Gb * NLM;
+    double e = 0, ph = 0, num = 0, den = 0;
+    for (int ch = blockIdx.x; ch < P.nthchunk; ch += gridDim.x) {
+        const int4 cd = P.thchunk[ch];
+        const int ntile = (cd.y + TN - 1) / TN;
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncthreads();  // the previous chunk's reads of the tables and buffers are done
+        const size_t per = (size_t)(L + 1) * G * G;
+        for (int i = tid; i < (int)kper; i += nt) {
+            const int l = i / (G * G4), rem = i - l * G * G4, gp = rem / G4, g = rem - gp * G4;
+            const size_t src = ((size_t)l * G + g) * G + gp;
+            sKa[i] = g < G ? P.thK[(size_t)cd.z * per + src] : 0.f;
+            sKb[i] = g < G ? P.thK[(size_t)(cd.z + 1) * per + src] : 0.f;
+        }
+        auto load = [&](int t, int buf) {
+            if (t < ntile) {
+                const int j0 = t * TN, nn = cd.y - j0 < TN ? cd.y - j0 : TN;
+                const int pr = row_f / 4;  // 16-byte pieces of a node's row
+                for (int q = tid; q < nn * pr; q += nt) {
+                    const int n = q / pr, qq = q - n * pr;
+                    const long long c = P.thperm[cd.x + j0 + n];
+                    cp_async_n<16>(sI + (size_t)buf * tile_f + (size_t)n * row_f + 4 * qq, Ip + c * row_f + 4 * qq);
+                }
+                if (tid < nn) sC[buf][tid] = P.thperm[cd.x + j0 + tid];
+            }
+            asm volatile("cp.async.commit_group;\n" ::);
+        };
+        load(0, 0);
+        for (int t = 0; t < ntile; ++t) {
+            const int buf = t & 1;
+            const int nn = cd.y - t * TN < TN ? cd.y - t * TN : TN;
+            asm volatile("cp.async.wait_group 0;\n" ::);
+            __syncthreads();  // the tile (and at t = 0 the tables) landed; the previous tile is done
+            load(t + 1, buf ^ 1);
+            for (int i = tid; i < TN * G4; i += nt) {
+                const int n = i / G4, g = i - n * G4;
+                float r = 0.f, em = 0.f;
+                if (n < nn && g < G) {
+                    const long long c = sC[buf][n];
+                    const float chi = P.chi0[c * G + g];
+                    if (chi > 0.f) {
+                        r = P.ne[c] / chi;
+                        em = 3.5449077018110320546f * P.emis0[c * G + g] / chi;  // sqrt(4 pi)
+                    }
+                }
+                sR[i] = r;
+                sE[i] = em;
+            }
+            if (tid < TN) sW[tid] = tid < nn ? P.thw[sC[buf][tid]] : 0.f;
+            for (int i = tid; i < nn * G; i += nt) {
+                const int n = i / G, g = i - n * G;
+                const double J = (double)mom[(sC[buf][n] * G + g) * 10];
+                const double de = P.edges[g + 1] - P.edges[g];
+                e += 4.0 * kPi * J * de;
+                ph += 4.0 * kPi * J * de / P.centre[g];
+            }
+            __syncthreads();
+            const float *tI = sI + (size_t)buf * tile_f;
+            for (int u = tid; u < nunit; u += nt) {
+                int l = (int)sqrtf((float)(u / Gb));
+                while (Gb * (l + 1) * (l + 1) <= u) ++l;
+                while (Gb * l * l > u) --l;
+                const int r = u - Gb * l * l, gb = r / (2 * l + 1), p = l * l + (r - gb * (2 * l + 1));
+                float aa[4][TN], ab[4][TN];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int n = 0; n < TN; ++n) aa[j][n] = ab[j][n] = 0.f;
+                const float4 *ka = reinterpret_cast<const float4 *>(sKa + (size_t)l * G * G4) + gb;
+                const float4 *kb = reinterpret_cast<const float4 *>(sKb + (size_t)l * G * G4) + gb;
+                const float *ir = tI + p;
+#pragma unroll 2
+                for (int gp = 0; gp < G; ++gp) {
+                    const float4 a4 = ka[(size_t)gp * Gb], b4 = kb[(size_t)gp * Gb];
+                    float iv[TN];
+#pragma unroll
+                    for (int n = 0; n < TN; ++n) iv[n] = ir[((size_t)n * G + gp) * NLM];
+#pragma unroll
+                    for (int n = 0; n < TN; ++n) {
+                        aa[0][n] += a4.x * iv[n]; aa[1][n] += a4.y * iv[n];
+                        aa[2][n] += a4.z * iv[n]; aa[3][n] += a4.w * iv[n];
+                        ab[0][n] += b4.x * iv[n]; ab[1][n] += b4.y * iv[n];
+                        ab[2][n] += b4.z * iv[n]; ab[3][n] += b4.w * iv[n];
+                    }
+                }
+                float dn = 0.f, nmr = 0.f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int g = 4 * gb + j;
+                    const bool gv = g < G;
+                    float sv[TN], pv[TN];
+                    long long o[TN];
+#pragma unroll
+                    for (int n = 0; n < TN; ++n) {
+                        const float w = sW[n];
+                        sv[n] = sR[n * G4 + g] * ((1.f - w) * aa[j][n] + w * ab[j][n]);
+                        if (p == 0) sv[n] += sE[n * G4 + g];
+                        o[n] = (sC[buf][n] * G + g) * NLM + p;
+                        pv[n] = 0.f;
+                    }
+                    if (have_prev) {
+#pragma unroll
+                        for (int n = 0; n < TN; ++n)
+                            if (gv && n < nn) pv[n] = Sprev[o[n]];
+                    }
+#pragma unroll
+                    for (int n = 0; n < TN; ++n) {
+                        if (gv && n < nn) {
+                            Sp[o[n]] = sv[n];
+                            dn += sv[n] * sv[n];
+                            const float d = sv[n] - pv[n];
+                            if (have_prev) nmr += d * d;
+                        }
+                    }
+                }
+                den += (double)dn;
+                num += (double)nmr;
+            }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_down_sync(0xffffffffu, e, o);
+        ph += __shfl_down_sync(0xffffffffu, ph, o);
+        num += __shfl_down_sync(0xffffffffu, num, o);
+        den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = e;
+        red[1][warp] = ph;
+        red[2][warp] = num;
+        red[3][warp] = den;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double a = 0;
+        for (int w = 0; w < nw; ++w) a += red[tid][w];
+        partial[blockIdx.x * 4 + tid] = a;
+    }
+}
+
+// -------------------------------------------------------------------------
 // a2 (+ a5 partials) with thermal electrons: chunks of nodes of one
 // temperature bracket b; the CTA holds K of tables b and b+1, each warp
 // stages a node's I_lm and forms S_p = n_e/chi0 ((1 - w) sum_g' K_b I +
@@ -1323,6 +1675,7 @@ __global__ void __launch_bounds__(256) k_source_thermal(Prob<T> P, const T *__re
             const T ne = P.ne[c], w = P.thw[c];
             for (int i = lane; i < G * NLM; i += 32) wI[i] = Ip[base + i];
             __syncwarp();
+            T dn = T(0), nm = T(0);  // the node's residual parts, as in k_source_sums
             for (int p = lane; p < NLM; p += 32) {
                 int l = 0;
                 while ((l + 1) * (l + 1) <= p) ++l;
@@ -1342,14 +1695,15 @@ __global__ void __launch_bounds__(256) k_source_thermal(Prob<T> P, const T *__re
                     }
                     const long long i = base + (long long)g * NLM + p;
                     Sp[i] = s;
-                    const double sn = (double)s;
-                    den += sn * sn;
+                    dn += s * s;
                     if (have_prev) {
-                        const double d = sn - (double)Sprev[i];
-                        num += d * d;
+                        const T d = s - Sprev[i];
+                        nm += d * d;
                     }
                 }
             }
+            den += (double)dn;
+            num += (double)nm;
             for (int g = lane; g < G; g += 32) {
                 const double J = (double)mom[(c * G + g) * 10];
                 const double de = P.edges[g + 1] - P.edges[g];
@@ -1952,6 +2306,39 @@ cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev,
 
 static int source_thermal_warps(const shd_ctx *c, size_t *sm);
 
+// k_source_kn: shared memory at tile size tn, and the largest tile size
+// (8, 4 or 2 nodes) that fits; 0 where the kernel does not apply (G NLM not
+// a multiple of 4, more than 64 groups) and k_source_sums takes over.
+static size_t source_kn_smem(const shd_ctx *c, int tn)
+{
+    const size_t G4 = 4 * (size_t)((c->G + 3) / 4);
+    return sizeof(float) * ((size_t)(c->L + 1) * c->G * G4 + (size_t)2 * tn * c->G * c->NLM + (size_t)2 * tn * G4);
+}
+static int source_kn_tile(const shd_ctx *c)
+{
+    if (((long long)c->G * c->NLM) % 4 != 0 || c->G > 64) return 0;
+    for (int tn : {8, 4, 2})
+        if (source_kn_smem(c, tn) <= 227 * 1024) return tn;
+    return 0;
+}
+
+// k_source_kn_th: shared memory at tile size tn (two transposed tables, two
+// tiles, the tile's factors and weights), and the largest tile size (4 or 2)
+// that fits; 0 where k_source_thermal takes over.
+static size_t source_kn_th_smem(const shd_ctx *c, int tn)
+{
+    const size_t G4 = 4 * (size_t)((c->G + 3) / 4);
+    return sizeof(float) * ((size_t)2 * (c->L + 1) * c->G * G4 + (size_t)2 * tn * c->G * c->NLM +
+                            (size_t)2 * tn * G4 + (size_t)tn);
+}
+static int source_kn_th_tile(const shd_ctx *c)
+{
+    if (((long long)c->G * c->NLM) % 4 != 0 || c->G > 64) return 0;
+    for (int tn : {4, 2})
+        if (source_kn_th_smem(c, tn) <= 227 * 1024) return tn;
+    return 0;
+}
+
 static size_t source_sums_smem(const shd_ctx *c)
 {
     return c->esize * ((((size_t)(c->L + 1) * (c->G * c->G + 1)) + 1 & ~(size_t)1) + (size_t)8 * c->G * c->NLM);
@@ -1983,9 +2370,38 @@ cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, c
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int nb = ctx->n_partial;
-    auto cuda_cores = [&]() {
+    int grid_cc = nb;  // partial-sum rows of the CUDA-core pass
+    auto cuda_cores = [&]() -> cudaError_t {
+        if constexpr (sizeof(T) == 4) {
+            const int tn = ctx->k_diagonal && ctx->G <= 32 ? 0 : source_kn_tile(ctx);
+            if (tn > 0) {
+                const size_t smk = source_kn_smem(ctx, tn);
+                auto kk = tn == 8 ? k_source_kn<8> : (tn == 4 ? k_source_kn<4> : k_source_kn<2>);
+                cudaError_t e2 = cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smk);
+                if (e2 != cudaSuccess) return e2;
+                const long long ntile = (ctx->Nc + tn - 1) / tn;
+                const int units = ((ctx->G + 3) / 4) * ctx->NLM;
+                const int nt = units >= 512 ? 512 : (units + 31) / 32 * 32;
+                // persistent: as many CTAs as fit on every SM at once (few
+                // groups make small CTAs, several a SM)
+                int g = 0, per_sm = 0;
+                if (cudaDeviceGetAttribute(&g, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || g <= 0)
+                    g = 148;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kk, nt, smk) != cudaSuccess || per_sm < 1)
+                    per_sm = 1;
+                g *= per_sm;
+                if (g > nb) g = nb;
+                if (ntile < g) g = (int)ntile;
+                kk<<<g, nt, smk, st>>>(P, (const float *)Ip, (float *)Sp, (const float *)mom, (const float *)Sprev,
+                                       have_prev ? 1 : 0, ctx->d_partial);
+                note_launch();
+                grid_cc = g;
+                return cudaGetLastError();
+            }
+        }
         kern<<<nb, 256, sm, st>>>(P, Ip, Sp, mom, Sprev, have_prev ? 1 : 0, ctx->d_partial);
         note_launch();
+        grid_cc = nb;
         return cudaGetLastError();
     };
     bool tc = false;
@@ -2030,6 +2446,7 @@ cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, c
                                   (const float *)Sprev, have_prev, &nparts, st);
     } else {
         e = cuda_cores();
+        nparts = grid_cc;
     }
     if (e != cudaSuccess) return e;
     k_sums_final<<<1, kSumsThreads, 0, st>>>(ctx->d_partial, nparts, have_prev ? 1 : 0, ctx->d_sums);
@@ -2115,6 +2532,32 @@ cudaError_t launch_source_thermal(const shd_ctx *ctx, const T *Ip, T *Sp, const 
                                   bool have_prev, int *grid_used, cudaStream_t st)
 {
     Prob<T> P = make_prob<T>(ctx);
+    if constexpr (sizeof(T) == 4) {
+        // the register-blocked form where its two tables and tiles fit
+        const int tn = source_kn_th_tile(ctx);
+        if (tn > 0 && P.thermal) {
+            const size_t smk = source_kn_th_smem(ctx, tn);
+            auto kk = tn == 4 ? k_source_kn_th<4> : k_source_kn_th<2>;
+            cudaError_t e2 = cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smk);
+            if (e2 != cudaSuccess) return e2;
+            const int units = ((ctx->G + 3) / 4) * ctx->NLM;
+            const int nt = units >= 512 ? 512 : (units + 31) / 32 * 32;
+            int g = 0, per_sm = 0;
+            if (cudaDeviceGetAttribute(&g, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || g <= 0)
+                g = 148;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kk, nt, smk) != cudaSuccess || per_sm < 1)
+                per_sm = 1;
+            g *= per_sm;
+            if (g > ctx->n_partial) g = ctx->n_partial;
+            if (g > ctx->nthchunk) g = ctx->nthchunk;
+            if (g < 1) g = 1;
+            kk<<<g, nt, smk, st>>>(P, (const float *)Ip, (float *)Sp, (const float *)mom, (const float *)Sprev,
+                                   have_prev ? 1 : 0, ctx->d_partial);
+            note_launch();
+            if (grid_used) *grid_used = g;
+            return cudaGetLastError();
+        }
+    }
     size_t sm = 0;
     const int W = source_thermal_warps(ctx, &sm);
     if (W == 0 || !P.thermal) return cudaErrorInvalidConfiguration;

@@ -668,6 +668,10 @@ __global__ void __launch_bounds__(256, 2) k_source_tc(Prob<float> P, const float
         const int node = valid ? row / nm : 0, p = p0 + (valid ? row - node * nm : 0);
         const size_t obase = (size_t)(c0 + node) * nstride + p;
         const int cb = half * (Gp / 2), ce = half ? Gp : Gp / 2;
+        // this row's part of |S|^2 and |S - S_prev|^2 in FP32, added to the
+        // FP64 totals once (an FP64 operation per output would occupy the
+        // narrow FP64 pipe)
+        float dn = 0.f, nmr = 0.f;
         for (int cc = cb; cc < ce; cc += 16) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * acc_cols + (uint32_t)cc, v);
@@ -680,13 +684,15 @@ __global__ void __launch_bounds__(256, 2) k_source_tc(Prob<float> P, const float
                 if (p == 0) sv += emt[node * G + g];
                 const size_t o = obase + (size_t)g * NLM;
                 Sp[o] = sv;
-                den += (double)sv * sv;
+                dn += sv * sv;
                 if (have_prev) {
-                    const double dd = (double)sv - (double)Sprev[o];
-                    num += dd * dd;
+                    const float dd = sv - Sprev[o];
+                    nmr += dd * dd;
                 }
             }
         }
+        den += (double)dn;
+        num += (double)nmr;
     };
 
     for (long long w = blockIdx.x; w < ntiles; w += gridDim.x) {
