@@ -335,6 +335,13 @@ template <>
 __device__ inline float dfloor<float>(float x) { return floorf(x); }
 
 template <class T>
+__device__ inline T dabs(T x);
+template <>
+__device__ inline double dabs<double>(double x) { return ::fabs(x); }
+template <>
+__device__ inline float dabs<float>(float x) { return fabsf(x); }
+
+template <class T>
 __device__ inline T dclamp(T x, T lo, T hi);
 template <>
 __device__ inline double dclamp<double>(double x, double lo, double hi) { return ::fmin(::fmax(x, lo), hi); }

@@ -651,6 +651,11 @@ __device__ inline Stencil<T> table_stencil(const float4 &e, int nphi, const int 
 // FP64 from the FP64 flow and directions.  Beyond the edges the remapped
 // intensity is zero (Sec. 2.2), a jump that a single-precision ratio would
 // place a rounding away from where the FP64 definition puts it.
+// Within this distance of an outer edge (in group spacings, or in log
+// energy for unequal groups) a single-precision lookup defers to the table's
+// FP64 range: its own rounding stays below 1e-6 there.
+constexpr float kEdgeTol = 1e-5f;
+
 __device__ inline unsigned short group_range(const Prob<float> &P, double r)
 {
     const int G = P.G;
@@ -784,14 +789,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
         Stencil<T> st;
         // output groups [glo, ghi) look up energies within the outer edges
         // (the table's FP64 decision; in place, the working precision's)
-        int glo = 0, ghi = G;
+        // (read only for a lookup within kEdgeTol of an edge, where the
+        // single-precision test could differ from the FP64 one)
+        int glo = -1, ghi = -1;
+        auto range = [&]() {
+            if (glo < 0) {
+                const unsigned r = rng[m * N + k0];
+                glo = (int)(r & 255u);
+                ghi = (int)(r >> 8);
+            }
+        };
         if constexpr (TAB) {
             const float4 e = iter == 0 ? epre[0] : (iter == 1 ? epre[1] : tab[m * N + k0]);
             q = (T)e.w;
             st = table_stencil<T>(e, P.nphi, tb.m2i);
-            const unsigned r = rng[m * N + k0];
-            glo = (int)(r & 255u);
-            ghi = (int)(r >> 8);
         } else {
             T n0[3] = {P.dirs[3 * k0], P.dirs[3 * k0 + 1], P.dirs[3 * k0 + 2]};
             T n[3];
@@ -815,7 +826,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
             if (gm0 > 0) {
                 const T v0 = fs.eval(sI, spole, N, 0);
                 for (int g0 = 0; g0 < gm0; ++g0, out += N) {
-                    const bool in = TAB ? g0 >= glo : T(g0) + us.x >= P.lgx0;
+                    const T dx = T(g0) + us.x - P.lgx0;
+                    bool in = dx >= T(0);
+                    if (TAB && dabs<T>(dx) < T(kEdgeTol)) {
+                        range();
+                        in = g0 >= glo;
+                    }
                     *out = (in ? v0 : T(0)) * iq3;
                 }
             }
@@ -837,7 +853,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
             if (gm1 < G) {
                 const T v1 = fs.eval(sI, spole, N, G - 1);
                 for (int g0 = gm1; g0 < G; ++g0, out += N) {
-                    const bool in = TAB ? g0 < ghi : T(g0) + us.x <= P.lgx1;
+                    const T dx = T(g0) + us.x - P.lgx1;
+                    bool in = dx <= T(0);
+                    if (TAB && dabs<T>(dx) < T(kEdgeTol)) {
+                        range();
+                        in = g0 < ghi;
+                    }
                     *out = (in ? v1 : T(0)) * iq3;
                 }
             }
@@ -845,8 +866,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_comovi
         }
         int hint = 0;
         for (int g0 = 0; g0 < G; ++g0) {
-            FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, tb.lc[g0] + lq, hint);
-            if (TAB) {  // inside or beyond the edges as the table decided
+            const T le = tb.lc[g0] + lq;
+            FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, le, hint);
+            if (TAB && (dabs<T>(le - P.le0) < T(kEdgeTol) || dabs<T>(le - P.leG) < T(kEdgeTol))) {
+                range();  // inside or beyond the edges as the table decided
                 if (g0 < glo || g0 >= ghi) fb.mode = 0;
                 else if (fb.mode == 0) fb.mode = 1;  // the nearest outer group (fb.ga)
             }
@@ -897,14 +920,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
         Stencil<T> st;
         // output groups [glo, ghi) look up source energies within the outer
         // edges (the table's FP64 decision; in place, the working precision's)
-        int glo = 0, ghi = G;
+        // (read only for a lookup within kEdgeTol of an edge, as above)
+        int glo = -1, ghi = -1;
+        auto range = [&]() {
+            if (glo < 0) {
+                const unsigned r = rng[m * N + k];
+                glo = (int)(r & 255u);
+                ghi = (int)(r >> 8);
+            }
+        };
         if constexpr (TAB) {
             const float4 e = tab[m * N + k];
             D = (T)e.w;
             st = table_stencil<T>(e, P.nphi, tb.m2i);
-            const unsigned r = rng[m * N + k];
-            glo = (int)(r & 255u);
-            ghi = (int)(r >> 8);
         } else {
             T n[3] = {P.dirs[3 * k], P.dirs[3 * k + 1], P.dirs[3 * k + 2]};
             T n0[3];
@@ -926,7 +954,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
                 const T v0 = fs.eval(sS, spole, N, 0);
                 const T chl = schi[0] * D;
                 for (int g = 0; g < gm0; ++g, oe += N, oc += N) {
-                    const bool in = TAB ? g >= glo : T(g) + us.x >= P.lgx0;
+                    const T dx = T(g) + us.x - P.lgx0;
+                    bool in = dx >= T(0);
+                    if (TAB && dabs<T>(dx) < T(kEdgeTol)) {
+                        range();
+                        in = g >= glo;
+                    }
                     *oc = chl;
                     *oe = chl * (in ? v0 : T(0)) * iD3;
                 }
@@ -961,7 +994,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
                 const T v1 = fs.eval(sS, spole, N, G - 1);
                 const T chl = schi[G - 1] * D;
                 for (int g = gm1; g < G; ++g, oe += N, oc += N) {
-                    const bool in = TAB ? g < ghi : T(g) + us.x <= P.lgx1;
+                    const T dx = T(g) + us.x - P.lgx1;
+                    bool in = dx <= T(0);
+                    if (TAB && dabs<T>(dx) < T(kEdgeTol)) {
+                        range();
+                        in = g < ghi;
+                    }
                     *oc = chl;
                     *oe = chl * (in ? v1 : T(0)) * iD3;
                 }
@@ -970,8 +1008,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4) k_remap_to_lab(Pr
         }
         int hint = 0;
         for (int g = 0; g < G; ++g) {
-            FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, tb.lc[g] + lD, hint);
-            if (TAB) {  // inside or beyond the edges as the table decided
+            const T le = tb.lc[g] + lD;
+            FreqBracket<T> fb = freq_bracket<T>(tb.lc, tb.linv, P.le0, P.leG, G, le, hint);
+            if (TAB && (dabs<T>(le - P.le0) < T(kEdgeTol) || dabs<T>(le - P.leG) < T(kEdgeTol))) {
+                range();  // inside or beyond the edges as the table decided
                 if (g < glo || g >= ghi) fb.mode = 0;
                 else if (fb.mode == 0) fb.mode = 1;  // the nearest outer group (fb.ga)
             }
