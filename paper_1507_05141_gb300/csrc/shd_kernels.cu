@@ -310,12 +310,13 @@ __device__ inline void cp_async_n(void *smem, const void *gmem)
 // K_l[g][g'] in one 16-byte load (K stored [l][g'][g]) and the TN values
 // I[c][g'][p] as broadcasts: 32 FMAs a 9 loads at TN = 8.  Units run
 // l-major, m fastest, so the lanes of a warp share a K row.  Tiles of TN
-// consecutive nodes (one contiguous [TN][G][NLM] block of I_lm) stream
-// through a two-stage cp.async ring; the CTA is persistent over tiles.  The
+// consecutive nodes (one contiguous [TN][G][NLM] block of I_lm, and the
+// same block of S_prev for the residual) stream through a two-stage
+// cp.async ring; the CTA is persistent over tiles.  The
 // residual parts |S|^2, |S - S_prev|^2 accumulate per unit in FP32 and join
 // the FP64 totals once per unit; the energy and photon sums stay FP64.
 // -------------------------------------------------------------------------
-template <int TN>
+template <int TN, bool PS>
 __global__ void __launch_bounds__(512, 1) k_source_kn(Prob<float> P, const float *__restrict__ Ip,
                                                       float *__restrict__ Sp, const float *__restrict__ mom,
                                                       const float *__restrict__ Sprev, int have_prev,
@@ -328,7 +329,8 @@ __global__ void __launch_bounds__(512, 1) k_source_kn(Prob<float> P, const float
     const int tile_f = TN * G * NLM;  // floats of one tile of I_lm
     float *sK = reinterpret_cast<float *>(smem_raw);  // [L+1][G][G4]: K_l[g][g'] at [l][g'][g]
     float *sI = sK + (size_t)(L + 1) * G * G4;        // [2][TN][G][NLM]
-    float *sR = sI + (size_t)2 * tile_f;              // [TN][G4] n_e/chi0 (0 where chi0 <= 0)
+    float *sP = sI + (size_t)2 * tile_f;              // PS: [2][TN][G][NLM] S_prev of the tile
+    float *sR = sP + (PS ? (size_t)2 * tile_f : 0);   // [TN][G4] n_e/chi0 (0 where chi0 <= 0)
     float *sE = sR + TN * G4;                         // [TN][G4] sqrt(4 pi) eta0/chi0
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < (L + 1) * G * G4; i += nt) {
@@ -344,6 +346,11 @@ __global__ void __launch_bounds__(512, 1) k_source_kn(Prob<float> P, const float
             const float *src = Ip + c0 * G * NLM;
             float *dst = sI + (size_t)buf * tile_f;
             for (int q = tid; q < nv; q += nt) cp_async_n<16>(dst + 4 * q, src + 4 * q);
+            if (PS && have_prev) {  // the tile's S_prev, read by the epilogue
+                const float *sp = Sprev + c0 * G * NLM;
+                float *dp = sP + (size_t)buf * tile_f;
+                for (int q = tid; q < nv; q += nt) cp_async_n<16>(dp + 4 * q, sp + 4 * q);
+            }
         }
         asm volatile("cp.async.commit_group;\n" ::);
     };
@@ -381,6 +388,7 @@ __global__ void __launch_bounds__(512, 1) k_source_kn(Prob<float> P, const float
         }
         __syncthreads();
         const float *tI = sI + (size_t)buf * tile_f;
+        const float *tP = sP + (size_t)buf * tile_f;
         for (int u = tid; u < nunit; u += nt) {
             // unit u: band l holds the Gb (2l + 1) units from Gb l^2 on
             int l = (int)sqrtf((float)(u / Gb));
@@ -408,9 +416,9 @@ __global__ void __launch_bounds__(512, 1) k_source_kn(Prob<float> P, const float
                     acc[3][n] += k4.w * iv[n];
                 }
             }
-            // per group of the unit: its TN outputs, then their TN values of
-            // S_prev loaded together (predicated, in flight at once), then
-            // the stores and the residual parts
+            // per group of the unit: its TN outputs and S_prev (PS: the
+            // tile's, in shared memory; else TN predicated loads in flight
+            // together), then the stores and the residual parts
             float dn = 0.f, nmr = 0.f;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -427,7 +435,8 @@ __global__ void __launch_bounds__(512, 1) k_source_kn(Prob<float> P, const float
                 if (have_prev) {
 #pragma unroll
                     for (int n = 0; n < TN; ++n)
-                        if (gv && n < nn) pv[n] = Sprev[ob + (long long)n * G * NLM];
+                        if (gv && n < nn)
+                            pv[n] = PS ? tP[((size_t)n * G + g) * NLM + p] : Sprev[ob + (long long)n * G * NLM];
                 }
 #pragma unroll
                 for (int n = 0; n < TN; ++n) {
@@ -2306,19 +2315,29 @@ cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev,
 
 static int source_thermal_warps(const shd_ctx *c, size_t *sm);
 
-// k_source_kn: shared memory at tile size tn, and the largest tile size
+// k_source_kn: shared memory at tile size tn (the transposed K, two tiles of
+// I_lm, with ps two of S_prev, the tile's factors), and the largest tile size
 // (8, 4 or 2 nodes) that fits; 0 where the kernel does not apply (G NLM not
 // a multiple of 4, more than 64 groups) and k_source_sums takes over.
-static size_t source_kn_smem(const shd_ctx *c, int tn)
+static size_t source_kn_smem(const shd_ctx *c, int tn, bool ps)
 {
     const size_t G4 = 4 * (size_t)((c->G + 3) / 4);
-    return sizeof(float) * ((size_t)(c->L + 1) * c->G * G4 + (size_t)2 * tn * c->G * c->NLM + (size_t)2 * tn * G4);
+    return sizeof(float) * ((size_t)(c->L + 1) * c->G * G4 + (size_t)(ps ? 4 : 2) * tn * c->G * c->NLM +
+                            (size_t)2 * tn * G4);
 }
-static int source_kn_tile(const shd_ctx *c)
+// the largest tile first, with S_prev in shared memory where that still fits
+// (a smaller tile costs more than the prefetch saves); 0: k_source_sums
+static int source_kn_tile(const shd_ctx *c, bool &ps)
 {
+    ps = false;
     if (((long long)c->G * c->NLM) % 4 != 0 || c->G > 64) return 0;
-    for (int tn : {8, 4, 2})
-        if (source_kn_smem(c, tn) <= 227 * 1024) return tn;
+    for (int tn : {8, 4, 2}) {
+        for (bool p : {true, false})
+            if (source_kn_smem(c, tn, p) <= 227 * 1024) {
+                ps = p;
+                return tn;
+            }
+    }
     return 0;
 }
 
@@ -2373,10 +2392,13 @@ cudaError_t launch_source_sums(shd_ctx *ctx, const T *Ip, T *Sp, const T *mom, c
     int grid_cc = nb;  // partial-sum rows of the CUDA-core pass
     auto cuda_cores = [&]() -> cudaError_t {
         if constexpr (sizeof(T) == 4) {
-            const int tn = ctx->k_diagonal && ctx->G <= 32 ? 0 : source_kn_tile(ctx);
+            bool ps = false;
+            const int tn = ctx->k_diagonal && ctx->G <= 32 ? 0 : source_kn_tile(ctx, ps);
             if (tn > 0) {
-                const size_t smk = source_kn_smem(ctx, tn);
-                auto kk = tn == 8 ? k_source_kn<8> : (tn == 4 ? k_source_kn<4> : k_source_kn<2>);
+                const size_t smk = source_kn_smem(ctx, tn, ps);
+                auto kk = tn == 8 ? (ps ? k_source_kn<8, true> : k_source_kn<8, false>)
+                                  : (tn == 4 ? (ps ? k_source_kn<4, true> : k_source_kn<4, false>)
+                                             : (ps ? k_source_kn<2, true> : k_source_kn<2, false>));
                 cudaError_t e2 = cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smk);
                 if (e2 != cudaSuccess) return e2;
                 const long long ntile = (ctx->Nc + tn - 1) / tn;
