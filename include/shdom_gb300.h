@@ -352,10 +352,22 @@ unsigned long long shd_launch_count(void);
  *   after its state was set, and every step while its per-stage timing is on,
  *   runs as direct launches.  Errors: those of shd_step, per problem (the
  *   message names it).
+ *   In sweep mode 1 (the default) the replayed steps of FP32 backward-Euler
+ *   problems with the linear short-characteristics integrator, planes the
+ *   one-CTA sweep holds, and no cluster schedule forced or timed more than
+ *   3 % faster (shd_get_sweep_schedule) run stages a1-a3 per problem and
+ *   then stage a4 of all of them in one persistent launch per kernel
+ *   variant, over a work list of every such problem's (ordinate, group)
+ *   pairs; the other problems sweep in their own launches.  Results are
+ *   those of shd_step, bit for bit.
+ * shd_batch_set_sweep_mode: 1 (default) as above; 0 every problem sweeps in
+ *   its own launches.  Synchronises the device when the mode changes.
+ *   Errors: SHD_ERR_ARG (NULL batch, mode not 0 or 1).
  * shd_batch_destroy: frees the batch (not the contexts). */
 typedef struct shd_batch shd_batch;
 int shd_batch_create(shd_batch **out, int nprob, shd_ctx *const *problems);
 int shd_batch_step(shd_batch *batch, int nsteps, void *cuda_stream);
+int shd_batch_set_sweep_mode(shd_batch *batch, int mode);
 void shd_batch_destroy(shd_batch *batch);
 
 /* ---- projection without allocation --------------------------------------

@@ -525,9 +525,11 @@ int ensure_buffers(shd_ctx *c)
     size_t es = c->esize;
     size_t nDO = (size_t)c->Nc * c->G * c->N, nSH = (size_t)c->Nc * c->G * c->NLM, nCG = (size_t)c->Nc * c->G;
     int rc;
-    if ((rc = dalloc(c, &c->d_I, nDO * es, "I"))) return rc;
-    if ((rc = dalloc(c, &c->d_eta, nDO * es, "eta_lab"))) return rc;
-    if ((rc = dalloc(c, &c->d_chi, nDO * es, "chi_lab"))) return rc;
+    // (+16 bytes: the FP32 sweep copies a plane's aligned cover, which may
+    // reach up to 12 bytes past the last plane)
+    if ((rc = dalloc(c, &c->d_I, nDO * es + 16, "I"))) return rc;
+    if ((rc = dalloc(c, &c->d_eta, nDO * es + 16, "eta_lab"))) return rc;
+    if ((rc = dalloc(c, &c->d_chi, nDO * es + 16, "chi_lab"))) return rc;
     if ((rc = dalloc(c, &c->d_Ip, nSH * es, "I_lm"))) return rc;
     if ((rc = dalloc(c, &c->d_Sp, nSH * es, "S_lm"))) return rc;
     if ((rc = dalloc(c, &c->d_Sprev, nSH * es, "S_lm prev"))) return rc;
@@ -902,7 +904,8 @@ int step_once(shd_ctx *c, cudaStream_t st, cudaEvent_t *ev, const std::function<
     const bool c0L = sweep_uses_chi0L<T>(c);
     CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st, !c0L), "sh2lab");
     if (tm) CK(cudaEventRecord(ev[4], st), "event");
-    CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st, c0L), "sweep");
+    if (!c->skip_sweep)  // (a batch sweeps every problem of it in one launch)
+        CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st, c0L), "sweep");
     if (tm) CK(cudaEventRecord(ev[5], st), "event");
     return SHD_OK;
 }
@@ -975,12 +978,64 @@ void drop_graphs(shd_ctx *c)
     for (int i = 0; i < 2; ++i) {
         if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
         if (c->graph[i]) cudaGraphDestroy(c->graph[i]);
+        if (c->graph_ns[i]) cudaGraphDestroy(c->graph_ns[i]);
         c->gexec[i] = nullptr;
         c->graph[i] = nullptr;
         c->graph_sp[i] = nullptr;
         c->graph_kernels[i] = 0;
+        c->graph_ns[i] = nullptr;
+        c->graph_ns_sp[i] = nullptr;
+        c->graph_ns_kernels[i] = 0;
     }
     c->graph_gen++;
+}
+
+// The step without its sweep (a backward-Euler step), as the context stands,
+// captured for a batch that sweeps its problems together; *slot is its
+// graph_ns slot, -1 when it cannot be captured.
+template <class T>
+int capture_presweep(shd_ctx *c, int *slot)
+{
+    *slot = -1;
+    for (int i = 0; i < 2; ++i)
+        if (c->graph_ns[i] && c->graph_ns_sp[i] == c->d_Sp) {
+            *slot = i;
+            return SHD_OK;
+        }
+    if (c->time_scheme != SHD_TIME_EULER) return SHD_OK;
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+    int rt = ensure_remap_tables(c, nullptr);
+    if (rt) return rt;
+    const int i = c->graph_ns[0] ? 1 : 0;
+    if (c->graph_ns[i]) {
+        cudaGraphDestroy(c->graph_ns[i]);
+        c->graph_ns[i] = nullptr;
+    }
+    const unsigned long long n0 = shd_launch_count_now();
+    void *sp0 = c->d_Sp, *sprev0 = c->d_Sprev;
+    const bool valid0 = c->sprev_valid;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    c->skip_sweep = true;
+    const int rc = step_once<T>(c, c->cap_stream, nullptr);
+    c->skip_sweep = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->d_Sp = sp0;
+    c->d_Sprev = sprev0;
+    c->sprev_valid = valid0;
+    const unsigned long long n = shd_launch_count_now() - n0;
+    forget_launches(n);
+    cudaGetLastError();
+    if (rc != SHD_OK || ee != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        return SHD_OK;  // this problem's batch step keeps its own sweep
+    }
+    c->graph_ns[i] = graph;
+    c->graph_ns_sp[i] = c->d_Sp;
+    c->graph_ns_kernels[i] = n;
+    c->graph_gen++;
+    *slot = i;
+    return SHD_OK;
 }
 
 // Capture one step, as the context stands, into graph slot i.
@@ -1989,11 +2044,21 @@ int shd_get_timing(shd_ctx *c, double *stage_ms, long long *steps)
 struct shd_batch {
     std::vector<shd_ctx *> probs;
     int device = 0;
+    int sweep_mode = 1;  // 1: one plane-sweep launch per class of problems
     // cached graphs of one batch step: the key is each problem's graph
-    // generation and slot (slot -1: that problem steps by direct launches)
+    // generation, slot (-1: that problem steps by direct launches) and
+    // sweep class (0: the problem's graph holds its own sweep; otherwise the
+    // slot is that of its sweep-less graph and the class's launch sweeps it)
+    struct Key {
+        unsigned long long gen;
+        int slot, cls;
+        bool operator==(const Key &o) const { return gen == o.gen && slot == o.slot && cls == o.cls; }
+    };
     struct Entry {
-        std::vector<std::pair<unsigned long long, int>> key;
+        std::vector<Key> key;
         cudaGraphExec_t exec = nullptr;
+        std::vector<void *> desc;    // device work lists of the batched sweeps
+        unsigned long long extra = 0;  // kernels of those sweeps per launch
     };
     std::vector<Entry> cache;
 };
@@ -2001,9 +2066,91 @@ struct shd_batch {
 namespace {
 void batch_drop(shd_batch *b)
 {
-    for (auto &e : b->cache)
+    bool lists = false;
+    for (auto &e : b->cache) lists |= !e.desc.empty();
+    if (lists) cudaDeviceSynchronize();  // a launched step may still read its work lists
+    for (auto &e : b->cache) {
         if (e.exec) cudaGraphExecDestroy(e.exec);
+        for (void *d : e.desc) cudaFree(d);
+    }
     b->cache.clear();
+}
+
+// The batch graph of one step for key: each problem's step (or its
+// sweep-less step) as a child graph, and per sweep class one persistent
+// plane sweep over the work list of its problems' (ordinate, group) pairs,
+// after their sweep-less steps.  The work list is ordered by falling node
+// count, so that the static stride of the persistent CTAs meets the long
+// items first.
+int batch_build(shd_batch *b, const std::vector<shd_batch::Key> &key, shd_batch::Entry &ent)
+{
+    const int np = (int)b->probs.size();
+    cudaGraph_t bg = nullptr;
+    CK(cudaGraphCreate(&bg, 0), "batch graph");
+    cudaError_t e = cudaSuccess;
+    std::vector<cudaGraphNode_t> node(np, nullptr);
+    for (int p = 0; p < np && e == cudaSuccess; ++p) {
+        if (key[p].slot < 0) continue;
+        shd_ctx *c = b->probs[p];
+        cudaGraph_t child = key[p].cls ? c->graph_ns[key[p].slot] : c->graph[key[p].slot];
+        e = cudaGraphAddChildGraphNode(&node[p], bg, nullptr, 0, child);
+    }
+    std::vector<int> classes;
+    for (int p = 0; p < np; ++p)
+        if (key[p].slot >= 0 && key[p].cls && std::find(classes.begin(), classes.end(), key[p].cls) == classes.end())
+            classes.push_back(key[p].cls);
+    cudaStream_t cs = nullptr;
+    for (size_t q = 0; q < classes.size() && e == cudaSuccess; ++q) {
+        const int cls = classes[q];
+        std::vector<int> mem;
+        for (int p = 0; p < np; ++p)
+            if (key[p].slot >= 0 && key[p].cls == cls) mem.push_back(p);
+        std::stable_sort(mem.begin(), mem.end(), [&](int x, int y) { return b->probs[x]->Nc > b->probs[y]->Nc; });
+        std::vector<SweepBatchProb> h(mem.size());
+        std::vector<cudaGraphNode_t> deps;
+        long long items = 0;
+        size_t smem = 0;
+        for (size_t k = 0; k < mem.size(); ++k) {
+            shd_ctx *c = b->probs[mem[k]];
+            sweep_batch_fill(c, h[k], items);
+            items += (long long)c->N * c->G;
+            smem = std::max(smem, sweep_batch_smem(c));
+            deps.push_back(node[mem[k]]);
+        }
+        void *d = nullptr;
+        e = cudaMalloc(&d, h.size() * sizeof(SweepBatchProb));
+        if (e != cudaSuccess) break;
+        ent.desc.push_back(d);
+        e = cudaMemcpy(d, h.data(), h.size() * sizeof(SweepBatchProb), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+        if (!cs && (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
+        const unsigned long long n0 = shd_launch_count_now();
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        const cudaError_t el = launch_sweep_batch(cls, (const SweepBatchProb *)d, (int)h.size(), items, smem,
+                                                  b->device, cs);
+        cudaGraph_t sg = nullptr;
+        e = cudaStreamEndCapture(cs, &sg);
+        const unsigned long long n = shd_launch_count_now() - n0;
+        forget_launches(n);
+        ent.extra += n;
+        if (e == cudaSuccess) e = el;
+        if (e == cudaSuccess) {
+            cudaGraphNode_t sn;
+            e = cudaGraphAddChildGraphNode(&sn, bg, deps.data(), deps.size(), sg);
+        }
+        if (sg) cudaGraphDestroy(sg);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ent.exec, bg, 0);
+    cudaGraphDestroy(bg);
+    if (e != cudaSuccess) {
+        for (void *d : ent.desc) cudaFree(d);
+        ent.desc.clear();
+        ent.exec = nullptr;
+        return cuda_fail(e, "batch graph");
+    }
+    return SHD_OK;
 }
 }  // namespace
 
@@ -2045,45 +2192,46 @@ int shd_batch_step(shd_batch *b, int nsteps, void *stream)
         if (rc) return rc;
     }
     for (int s = 0; s < nsteps; ++s) {
-        std::vector<std::pair<unsigned long long, int>> key(np);
+        std::vector<shd_batch::Key> key(np);
         for (int p = 0; p < np; ++p) {
             shd_ctx *c = b->probs[p];
-            int slot = -1, rc;
+            int slot = -1, cls = 0, rc;
             rc = is_fp64(c) ? graph_slot<double>(c, slot) : graph_slot<float>(c, slot);
             if (rc) return fail(rc, "problem %d: %s", p, std::string(g_err).c_str());
             if (slot < 0) {
                 // direct launches for this problem's step
                 rc = is_fp64(c) ? run_steps<double>(c, 1, st, false) : run_steps<float>(c, 1, st, false);
                 if (rc) return fail(rc, "problem %d: %s", p, std::string(g_err).c_str());
+            } else if (b->sweep_mode == 1 && (cls = sweep_batch_class(c)) != 0) {
+                int ns = -1;
+                rc = capture_presweep<float>(c, &ns);
+                if (rc) return fail(rc, "problem %d: %s", p, std::string(g_err).c_str());
+                if (ns >= 0) slot = ns;
+                else cls = 0;
             }
-            key[p] = {c->graph_gen, slot};
+            key[p] = {c->graph_gen, slot, cls};
         }
         bool any = false;
-        for (auto &k : key) any |= k.second >= 0;
+        for (auto &k : key) any |= k.slot >= 0;
         if (any) {
-            cudaGraphExec_t exec = nullptr;
+            const shd_batch::Entry *ent = nullptr;
             for (auto &e : b->cache)
-                if (e.key == key) exec = e.exec;
-            if (!exec) {
-                cudaGraph_t bg = nullptr;
-                CK(cudaGraphCreate(&bg, 0), "batch graph");
-                cudaError_t e = cudaSuccess;
-                for (int p = 0; p < np && e == cudaSuccess; ++p) {
-                    if (key[p].second < 0) continue;
-                    cudaGraphNode_t node;
-                    e = cudaGraphAddChildGraphNode(&node, bg, nullptr, 0, b->probs[p]->graph[key[p].second]);
-                }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, bg, 0);
-                cudaGraphDestroy(bg);
-                CK(e, "batch graph");
+                if (e.key == key) ent = &e;
+            if (!ent) {
                 if (b->cache.size() >= 8) batch_drop(b);  // problems changed: start over
-                b->cache.push_back({key, exec});
+                shd_batch::Entry fresh;
+                fresh.key = key;
+                int rc = batch_build(b, key, fresh);
+                if (rc) return rc;
+                b->cache.push_back(fresh);
+                ent = &b->cache.back();
             }
-            CK(cudaGraphLaunch(exec, st), "batch graph launch");
+            CK(cudaGraphLaunch(ent->exec, st), "batch graph launch");
+            count_launches(ent->extra);
             for (int p = 0; p < np; ++p) {
-                if (key[p].second < 0) continue;
+                if (key[p].slot < 0) continue;
                 shd_ctx *c = b->probs[p];
-                count_launches(c->graph_kernels[key[p].second]);
+                count_launches(key[p].cls ? c->graph_ns_kernels[key[p].slot] : c->graph_kernels[key[p].slot]);
                 std::swap(c->d_Sp, c->d_Sprev);
             }
         }
@@ -2091,6 +2239,19 @@ int shd_batch_step(shd_batch *b, int nsteps, void *stream)
     for (int p = 0; p < np; ++p) {
         int rc = stream_after(b->probs[p]->stream, st);
         if (rc) return rc;
+    }
+    return SHD_OK;
+}
+
+int shd_batch_set_sweep_mode(shd_batch *b, int mode)
+{
+    if (!b) return fail(SHD_ERR_ARG, "null batch");
+    if (mode != 0 && mode != 1) return fail(SHD_ERR_ARG, "sweep mode %d (0 or 1)", mode);
+    if (mode != b->sweep_mode) {
+        CK(cudaSetDevice(b->device), "cudaSetDevice");
+        CK(cudaDeviceSynchronize(), "synchronize");
+        batch_drop(b);
+        b->sweep_mode = mode;
     }
     return SHD_OK;
 }

@@ -278,6 +278,13 @@ struct shd_ctx {
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     unsigned long long graph_gen = 0;  // bumped whenever a graph is captured or dropped
+    // the step without its sweep, per S_lm buffer (graph_ns_sp[i]), for a
+    // batch that sweeps its problems in one launch; captured on demand and
+    // dropped with the graphs
+    cudaGraph_t graph_ns[2] = {nullptr, nullptr};
+    void *graph_ns_sp[2] = {nullptr, nullptr};
+    unsigned long long graph_ns_kernels[2] = {0, 0};
+    bool skip_sweep = false;  // set only while the sweep-less step is captured
     void *graph_sp[2] = {nullptr, nullptr};
     unsigned long long graph_kernels[2] = {0, 0};  // kernel launches per replay
     cudaStream_t cap_stream = nullptr;
@@ -799,6 +806,28 @@ cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, c
 template <class T>
 bool sweep_uses_chi0L(const shd_ctx *ctx);
 bool sweep_schedule_valid(const shd_ctx *ctx, int C, int NT);
+
+// One problem of a batched plane sweep (k_sweep_batch): its fields, arrays
+// and flags, and the first of its items ((ordinate, group) pairs) in the
+// batch's work list.
+struct SweepBatchProb {
+    Prob<float> P;
+    float *I;
+    const float *eta, *chi, *chi0L;
+    const unsigned long long *mbits;
+    int npc, nwin, cb, wide;
+    long long item0;
+};
+// The class of the one-CTA plane sweep a batch runs for the problem (U in
+// bits 0-2, the chi0 table bit 3, FP64 weights bit 4; problems of one class
+// share a launch); 0 when its sweep is not that kernel's (FP64, Bezier,
+// planes that are not 16-byte multiples or too large) or when a cluster
+// schedule, forced or timed more than 3 % faster, sweeps it.
+int sweep_batch_class(const shd_ctx *ctx);
+size_t sweep_batch_smem(const shd_ctx *ctx);
+void sweep_batch_fill(const shd_ctx *ctx, SweepBatchProb &d, long long item0);
+cudaError_t launch_sweep_batch(int cls, const SweepBatchProb *d_probs, int nprob, long long nitems, size_t smem,
+                               int device, cudaStream_t st);
 bool sweep_bez_usable(const shd_ctx *ctx);
 template <class T>
 cudaError_t launch_sums(shd_ctx *ctx, const T *mom, const T *Sp, const T *Sprev, bool have_prev, cudaStream_t st);

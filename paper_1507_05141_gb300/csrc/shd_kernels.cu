@@ -738,29 +738,38 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pipe(Prob<T> P, T *__restrict
 // the other, so one barrier per plane suffices: it makes plane s-1's state
 // and the copies of plane s visible, and every read of the buffer plane s
 // overwrites (plane s-2's) is done by then.  The inputs of plane s+1 stream
-// into a two-stage ring as in k_sweep_pipe (16-byte copies); with CB the
-// moving-piece bits are read from global memory when a plane's copies are
-// issued.
+// into a two-stage ring as in k_sweep_pipe (16-byte copies; a plane that
+// does not start on a 16-byte boundary is copied as its aligned cover and
+// read from its offset in the slot, so grids of any size keep the 16-byte
+// copies); with CB (aligned planes only) the moving-piece bits are read
+// from global memory when a plane's copies are issued.
 // -------------------------------------------------------------------------
-template <int U, bool CB, bool WIDE>
-__global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__restrict__ I,
-                                                      const float *__restrict__ eta, const float *__restrict__ chi,
-                                                      const float *__restrict__ chi0L,
-                                                      const unsigned long long *__restrict__ mbits, int npc, int nwin,
-                                                      int tune_stride)
+// One (ordinate, group) pair of the plane sweep by the CTA (tune_stride > 0,
+// schedule timing only: into column blockIdx.x of a scratch intensity).
+// reals by which p lies past the 16-byte boundary below it (p 4-byte aligned)
+__device__ __forceinline__ int shift16(const float *p)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return (int)((reinterpret_cast<unsigned long long>(p) >> 2) & 3ull);
+}
+
+template <int U, bool CB, bool WIDE>
+__device__ __forceinline__ void sweep_pair_pp(const Prob<float> &P, float *__restrict__ I,
+                                              const float *__restrict__ eta, const float *__restrict__ chi,
+                                              const float *__restrict__ chi0L,
+                                              const unsigned long long *__restrict__ mbits, int npc, int nwin,
+                                              int pair, int tune_stride, unsigned char *smem_raw)
+{
     constexpr int NT = 1024;
-    // tune_stride > 0 (schedule timing only): CTA b sweeps pair b * tune_stride
-    // with its intensity in column b of a scratch array I [b][Nc]
-    const int pair = tune_stride > 0 ? (int)blockIdx.x * tune_stride : (int)blockIdx.x;
     const int k = pair / P.G;
     const int g = pair - k * P.G;
     const Ordinate o = P.ord[k];
     const int dims[3] = {P.nx, P.ny, P.nz};
     const int nd = dims[o.d], n1 = dims[o.e1], n2 = dims[o.e2];
     const int plane = n1 * n2;
-    const int pstride = (plane + 3) & ~3;
+    // planes whose start is not 16-byte aligned (grids with a plane or Nc
+    // not a multiple of 4) are copied as their aligned cover, up to 3 reals
+    // on either side: 4 reals of room past the rounded plane
+    const int pstride = ((plane + 3) & ~3) + 4;
     float4 *Q = reinterpret_cast<float4 *>(smem_raw);              // [2][pstride]
     float *ring = reinterpret_cast<float *>(Q + 2 * (size_t)pstride);  // [2][3][pstride]
     const long long base = ((long long)k * P.G + g) * P.Nc;
@@ -796,7 +805,20 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
             const int id = o.sd > 0 ? step : nd - 1 - step;
             const long long pb = base + (long long)id * plane;
             float *r = ring + (size_t)(step & 1) * 3 * pstride;
-            const int nv = plane / 4;  // 16-byte pieces per array
+            if constexpr (!CB) {
+                // the aligned cover of the plane in each array, shifted by
+                // the start's offset a within its 16 bytes (reals [a, a+plane)
+                // of the slot hold the plane)
+                const int aI = shift16(I + pb), aE = shift16(eta + pb), aC = shift16(chi + pb);
+                const float *gI = I + pb - aI, *gE = eta + pb - aE, *gC = chi + pb - aC;
+                const int nI = (aI + plane + 3) >> 2, nE = (aE + plane + 3) >> 2, nC = (aC + plane + 3) >> 2;
+                for (int q = tid; q < nI; q += NT) cp_async_n<16>(&r[q * 4], gI + q * 4);
+                for (int q = tid; q < nE; q += NT) cp_async_n<16>(&r[pstride + q * 4], gE + q * 4);
+                for (int q = tid; q < nC; q += NT) cp_async_n<16>(&r[2 * pstride + q * 4], gC + q * 4);
+                asm volatile("cp.async.commit_group;\n" ::);
+                return;
+            }
+            const int nv = plane / 4;  // 16-byte pieces per array (aligned planes)
             for (int q = tid; q < nv; q += NT) cp_async_n<16>(&r[q * 4], &I[pb + q * 4]);
             for (int q = tid; q < nv; q += NT) cp_async_n<16>(&r[pstride + q * 4], &eta[pb + q * 4]);
             if (CB && (id >> 6) != mwin) {
@@ -833,6 +855,11 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
         // every node but read only off the inflow faces)
         const float *rI = ring + (size_t)(step & 1) * 3 * pstride + tid;
         const float *rE = rI + pstride, *rC = rI + 2 * pstride;
+        if constexpr (!CB) {
+            rI += shift16(I + pb);
+            rE += shift16(eta + pb);
+            rC += shift16(chi + pb);
+        }
         const float4 *qa = Q + (size_t)((step + 1) & 1) * pstride + tid;  // plane step - 1
         const float4 *qb = qa - d1, *qc = qa - d2, *qd = qa - d1 - d2;
         float4 *qn = Q + (size_t)(step & 1) * pstride + tid;               // plane step
@@ -863,6 +890,44 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
         }
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+template <int U, bool CB, bool WIDE>
+__global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__restrict__ I,
+                                                      const float *__restrict__ eta, const float *__restrict__ chi,
+                                                      const float *__restrict__ chi0L,
+                                                      const unsigned long long *__restrict__ mbits, int npc, int nwin,
+                                                      int tune_stride)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // tune_stride > 0 (schedule timing only): CTA b sweeps pair b * tune_stride
+    // with its intensity in column b of a scratch array I [b][Nc]
+    const int pair = tune_stride > 0 ? (int)blockIdx.x * tune_stride : (int)blockIdx.x;
+    sweep_pair_pp<U, CB, WIDE>(P, I, eta, chi, chi0L, mbits, npc, nwin, pair, tune_stride, smem_raw);
+}
+
+// The plane sweeps of a batch of problems in one persistent launch: CTAs
+// walk the work list of every problem's (ordinate, group) pairs (problem p
+// owns items [item0, item0 + N G)), each item as k_sweep_pp sweeps it, with
+// the problem's own fields and arrays.  One launch per class of problems
+// that share the kernel's variant (U, CB, WIDE).
+template <int U, bool CB, bool WIDE>
+__global__ void __launch_bounds__(1024, 1) k_sweep_batch(const SweepBatchProb *__restrict__ bp, int nprob,
+                                                         long long nitems)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
+        int lo = 0, hi = nprob - 1;  // the last problem whose first item is <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bp[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const SweepBatchProb &b = bp[lo];
+        __syncthreads();  // the previous item's reads of the shared buffers are done
+        sweep_pair_pp<U, CB, WIDE>(b.P, b.I, b.eta, b.chi, b.chi0L, b.mbits, b.npc, b.nwin, (int)(it - b.item0), 0,
+                                   smem_raw);
+    }
 }
 
 // -------------------------------------------------------------------------
@@ -1970,7 +2035,7 @@ static cudaError_t launch_sweep_pipe(const shd_ctx *ctx, T *I, const T *eta, con
 // 2-stage ring of the three inputs
 static size_t sweep_pp_smem_bytes(const shd_ctx *c)
 {
-    size_t ps = ((size_t)sweep_plane_max(c) + 3) & ~(size_t)3;
+    size_t ps = (((size_t)sweep_plane_max(c) + 3) & ~(size_t)3) + 4;  // k_sweep_pp's plane stride
     return sizeof(float) * ps * 14;
 }
 
@@ -2076,11 +2141,14 @@ static cudaError_t run_sweep_sched(const shd_ctx *ctx, const SweepSched &sc, flo
 
 // The schedule (C, NT) with its U, buffer stride and shared memory, if it
 // fits this problem; false otherwise.
+template <class T>
+static bool sweep_vec(const shd_ctx *ctx);
+
 static bool sweep_sched_make(const shd_ctx *c, int C, int NT, SweepSched &sc)
 {
     sc = SweepSched();
     const size_t limit = 227 * 1024;
-    if (C == 1) {
+    if (C == 1) {  // any grid: k_sweep_pp copies unaligned planes as their aligned cover
         if (NT != 1024) return false;
         const int u = (sweep_plane_max(c) + 1023) / 1024;
         if (u > 4 || sweep_pp_smem_bytes(c) > limit) return false;
@@ -2089,6 +2157,7 @@ static bool sweep_sched_make(const shd_ctx *c, int C, int NT, SweepSched &sc)
         return true;
     }
     if (C != 2 && C != 4 && C != 8) return false;
+    if (!sweep_vec<float>(c)) return false;  // the cluster sweep's blocks need 16-byte aligned planes
     if (NT != 256 && NT != 384 && NT != 512 && NT != 768 && NT != 1024) return false;
     const int nl = sweep_nloc_max(c, C);
     int U = 0;
@@ -2143,7 +2212,8 @@ static bool sweep_schedule(const shd_ctx *cc, cudaStream_t st, const float *eta,
         const int n = npairs < 4 * sms ? npairs : 4 * sms;
         const int stride = npairs / n;
         float *scratch = nullptr;
-        if (cudaMalloc(&scratch, sizeof(float) * (size_t)n * c->Nc) != cudaSuccess) {
+        // (+16 bytes: the aligned cover of an unaligned last plane)
+        if (cudaMalloc(&scratch, sizeof(float) * (size_t)n * c->Nc + 16) != cudaSuccess) {
             cudaGetLastError();
             return true;  // no room to time them: the first candidate
         }
@@ -2204,11 +2274,76 @@ static bool sweep_vec(const shd_ctx *ctx)
            ((long long)ctx->nx * ctx->nz) % V == 0;
 }
 
+size_t sweep_batch_smem(const shd_ctx *c) { return sweep_pp_smem_bytes(c); }
+
+// the descriptor of problem c as its own sweep launch would see it
+void sweep_batch_fill(const shd_ctx *c, SweepBatchProb &d, long long item0)
+{
+    d.P = make_prob<float>(c);
+    d.I = (float *)c->d_I;
+    d.eta = (const float *)c->d_eta;
+    d.chi = (const float *)c->d_chi;
+    const bool bits = sweep_uses_chi0L<float>(c);
+    d.chi0L = bits ? (const float *)c->d_chi0L : nullptr;
+    d.mbits = bits ? c->d_mbits : nullptr;
+    d.npc = c->mbits_npc;
+    d.nwin = c->mbits_nwin;
+    d.cb = bits ? 1 : 0;
+    d.wide = sweep_tau_bounded(c) ? 0 : 1;
+    d.item0 = item0;
+}
+
+int sweep_batch_class(const shd_ctx *c)
+{
+    if (c->precision == SHD_FP64 || c->integrator != SHD_SC_LINEAR) return 0;
+    SweepSched sc;
+    if (!sweep_sched_make(c, 1, 1024, sc)) return 0;
+    if (c->sweep_force_C > 0 && c->sweep_force_C != 1) return 0;
+    if (c->sweep_force_C <= 0 && c->sweep_C > 1) {
+        // a cluster schedule won the problem's timing: it joins only if the
+        // one-CTA sweep timed within 3 % of that
+        float pp = -1.f, best = 1e30f;
+        for (int k = 0; k < c->sweep_ntune; ++k) {
+            if (c->sweep_tune[k][0] == 1.f) pp = c->sweep_tune[k][2];
+            best = fminf(best, c->sweep_tune[k][2]);
+        }
+        if (!(pp > 0.f && pp <= 1.03f * best)) return 0;
+    }
+    // class: U (bits 0-2), chi0 table (bit 3), FP64 weights (bit 4)
+    return sc.U | (sweep_uses_chi0L<float>(c) ? 8 : 0) | (sweep_tau_bounded(c) ? 0 : 16);
+}
+
+cudaError_t launch_sweep_batch(int cls, const SweepBatchProb *d_probs, int nprob, long long nitems, size_t smem,
+                               int device, cudaStream_t st)
+{
+    if (nprob <= 0 || nitems <= 0) return cudaSuccess;
+    using KB = void (*)(const SweepBatchProb *, int, long long);
+    const int U = cls & 7;
+    const bool cb = (cls & 8) != 0, wide = (cls & 16) != 0;
+    KB kern;
+    if (U <= 1) kern = cb ? (wide ? k_sweep_batch<1, true, true> : k_sweep_batch<1, true, false>)
+                          : (wide ? k_sweep_batch<1, false, true> : k_sweep_batch<1, false, false>);
+    else if (U <= 2) kern = cb ? (wide ? k_sweep_batch<2, true, true> : k_sweep_batch<2, true, false>)
+                               : (wide ? k_sweep_batch<2, false, true> : k_sweep_batch<2, false, false>);
+    else kern = cb ? (wide ? k_sweep_batch<4, true, true> : k_sweep_batch<4, true, false>)
+                   : (wide ? k_sweep_batch<4, false, true> : k_sweep_batch<4, false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 0, per = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || nsm <= 0) nsm = 148;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 1024, smem) != cudaSuccess || per < 1) per = 1;
+    long long grid = (long long)nsm * per;  // persistent: every CTA that fits at once
+    if (grid > nitems) grid = nitems;
+    kern<<<(unsigned)grid, 1024, smem, st>>>(d_probs, nprob, nitems);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // (C, NT) is a schedule of the FP32 plane sweep for this problem
 bool sweep_schedule_valid(const shd_ctx *c, int C, int NT)
 {
     SweepSched sc;
-    return c->precision != SHD_FP64 && sweep_vec<float>(c) && sweep_sched_make(c, C, NT, sc);
+    return c->precision != SHD_FP64 && sweep_sched_make(c, C, NT, sc);
 }
 
 template <class T>
@@ -2264,7 +2399,7 @@ cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, c
     }
     size_t smp = sweep_pipe_smem_bytes(ctx);
     if constexpr (sizeof(T) == 4) {
-        if (sweep_vec<T>(ctx)) {
+        {
             const bool bits = use_chi0L && sweep_uses_chi0L<T>(ctx);
             const bool wide = !sweep_tau_bounded(ctx);
             SweepSched sc;

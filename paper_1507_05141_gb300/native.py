@@ -65,6 +65,7 @@ _SIGS = {
     "shd_launch_count": (ctypes.c_ulonglong, []),
     "shd_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "shd_batch_step": (_i, [_vp, _i, _vp]),
+    "shd_batch_set_sweep_mode": (_i, [_vp, _i]),
     "shd_batch_destroy": (None, [_vp]),
     "shd_check_bounded_wait": (_i, [_vp, _ll]),
     "shd_set_ng": (_i, [_vp, _i]),
@@ -415,6 +416,11 @@ class Batch:
         """Enqueue nsteps steps of every problem on ``stream`` (a cudaStream_t
         as int, or None for the first problem's own stream)."""
         _check(self._L.shd_batch_step(self._h, int(nsteps), stream))
+
+    def set_sweep_mode(self, mode):
+        """1 (default): the sweeps of every problem that allows it in one
+        persistent launch per kernel variant; 0: each problem sweeps alone."""
+        _check(self._L.shd_batch_set_sweep_mode(self._h, int(mode)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -82,3 +82,51 @@ def test_batch_after_setter_and_more_steps(native):
     for sb, s1 in zip(bs, ss):
         assert np.array_equal(sb.moments()[0], s1.moments()[0])
     b.close()
+
+
+def test_batched_sweep_matches_single_and_per_problem_sweeps(native):
+    """Sweep mode 1 (one persistent plane sweep per kernel variant over the
+    batch's work list) against mode 0 (each problem sweeps alone) and single
+    stepping: uneven FP32 problems of several variants (one ordinate block
+    per plane, two, a ragged grid the one-CTA sweep cannot take), an RK4
+    problem that keeps its own sweep, and a Bezier one; enough steps to
+    replay both S_lm buffers' graphs."""
+    probs = [(inputs.jet(n=16, G=3, L=3, tau_r=3.0, gmax=4.0), "mixed", "euler", "linear"),
+             (inputs.relax_box(n=8), "fp32", "euler", "linear"),
+             (inputs.jet(n=40, G=2, L=3, tau_r=3.0, gmax=4.0), "fp32", "euler", "linear"),
+             (inputs.ragged_mixed(grid=(12, 8, 8), G=2), "mixed", "euler", "linear"),
+             (inputs.ragged_mixed(grid=(11, 9, 7), G=2), "mixed", "euler", "linear"),
+             (inputs.relax_box(n=12), "fp32", "rk4", "linear"),
+             (inputs.jet(n=12, G=2, L=3, tau_r=3.0, gmax=4.0), "mixed", "euler", "bezier")]
+    groups = {"b1": [], "b0": [], "one": []}
+    for i, (spec, prec, scheme, integ) in enumerate(probs):
+        I0 = inputs.random_state(spec, seed=40 + i)
+        for g in groups.values():
+            s = native.Solver.from_spec(spec, precision=prec)
+            s.set_time_scheme(scheme)
+            s.set_integrator(integ)
+            s.set_state(I0)
+            g.append(s)
+    b1, b0 = native.Batch(groups["b1"]), native.Batch(groups["b0"])
+    b0.set_sweep_mode(0)
+    nsteps = 5
+    b1.step(2)
+    b0.step(2)
+    n = native.launch_count()
+    b1.step(nsteps - 2)
+    n1 = native.launch_count() - n
+    n = native.launch_count()
+    b0.step(nsteps - 2)
+    n0 = native.launch_count() - n
+    # the linear Euler problems whose planes the one-CTA sweep takes share one
+    # launch per kernel variant in place of one each
+    assert 0 < n1 < n0, (n1, n0)
+    for s in groups["one"]:
+        s.step(nsteps)
+    for k, (sb1, sb0, s1) in enumerate(zip(groups["b1"], groups["b0"], groups["one"])):
+        for a, b, c in zip(sb1.moments(), sb0.moments(), s1.moments()):
+            assert np.array_equal(a, c), k
+            assert np.array_equal(b, c), k
+        assert np.array_equal(np.array(sb1.sums()), np.array(s1.sums())), k
+    b1.close()
+    b0.close()
