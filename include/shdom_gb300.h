@@ -259,11 +259,13 @@ int shd_stage_sweep(shd_ctx *ctx, const double *I_old, const double *eta_lab, co
 int shd_set_state_dev(shd_ctx *ctx, const double *dev_I, void *cuda_stream);
 int shd_get_state_dev(shd_ctx *ctx, double *dev_I, void *cuda_stream);
 
-/* Schedule of the single-precision sweep (SHD_FP32 and SHD_MIXED, grids
- * whose planes are multiples of 4 nodes): every plane of an (ordinate,
- * group) pair is split over a thread-block cluster of C CTAs (C = 1, 2, 4
- * or 8) of NT threads (256, 512 or 1024; C = 1 takes 1024), each CTA owning
- * a block of rows; rows next to another CTA's block read it through
+/* Schedule of the single-precision sweep (SHD_FP32 and SHD_MIXED, the
+ * linear integrator): every plane of an (ordinate, group) pair is swept by
+ * one CTA of NT threads (C = 1; NT = 1024, or 512 / 256 for planes of at
+ * most 4 NT nodes, several CTAs an SM; any grid) or split over a
+ * thread-block cluster of C CTAs (C = 2, 4 or 8; NT = 256, 384, 512, 768 or
+ * 1024; grids whose planes and node count are multiples of 4), each CTA
+ * owning a block of rows; rows next to another CTA's block read it through
  * distributed shared memory.  The result does not depend on the schedule
  * (the same arithmetic per node).  By default the library times every
  * schedule that fits on the first sweep run outside a stream capture (over

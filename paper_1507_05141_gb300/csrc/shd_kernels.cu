@@ -752,14 +752,13 @@ __device__ __forceinline__ int shift16(const float *p)
     return (int)((reinterpret_cast<unsigned long long>(p) >> 2) & 3ull);
 }
 
-template <int U, bool CB, bool WIDE>
+template <int U, bool CB, bool WIDE, int NT = 1024>
 __device__ __forceinline__ void sweep_pair_pp(const Prob<float> &P, float *__restrict__ I,
                                               const float *__restrict__ eta, const float *__restrict__ chi,
                                               const float *__restrict__ chi0L,
                                               const unsigned long long *__restrict__ mbits, int npc, int nwin,
                                               int pair, int tune_stride, unsigned char *smem_raw)
 {
-    constexpr int NT = 1024;
     const int k = pair / P.G;
     const int g = pair - k * P.G;
     const Ordinate o = P.ord[k];
@@ -892,8 +891,10 @@ __device__ __forceinline__ void sweep_pair_pp(const Prob<float> &P, float *__res
     asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
-template <int U, bool CB, bool WIDE>
-__global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__restrict__ I,
+// NT threads a CTA (1024, or 512 / 256 for small planes, 1024 / NT CTAs
+// an SM at the same 64 registers a thread)
+template <int U, bool CB, bool WIDE, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_sweep_pp(Prob<float> P, float *__restrict__ I,
                                                       const float *__restrict__ eta, const float *__restrict__ chi,
                                                       const float *__restrict__ chi0L,
                                                       const unsigned long long *__restrict__ mbits, int npc, int nwin,
@@ -903,7 +904,7 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_pp(Prob<float> P, float *__re
     // tune_stride > 0 (schedule timing only): CTA b sweeps pair b * tune_stride
     // with its intensity in column b of a scratch array I [b][Nc]
     const int pair = tune_stride > 0 ? (int)blockIdx.x * tune_stride : (int)blockIdx.x;
-    sweep_pair_pp<U, CB, WIDE>(P, I, eta, chi, chi0L, mbits, npc, nwin, pair, tune_stride, smem_raw);
+    sweep_pair_pp<U, CB, WIDE, NT>(P, I, eta, chi, chi0L, mbits, npc, nwin, pair, tune_stride, smem_raw);
 }
 
 // The plane sweeps of a batch of problems in one persistent launch: CTAs
@@ -2039,7 +2040,7 @@ static size_t sweep_pp_smem_bytes(const shd_ctx *c)
     return sizeof(float) * ps * 14;
 }
 
-template <int U>
+template <int U, int NT>
 static cudaError_t launch_sweep_pp(const shd_ctx *ctx, float *I, const float *eta, const float *chi, cudaStream_t st,
                                    bool bits, bool wide, unsigned nblocks, int tune_stride)
 {
@@ -2047,18 +2048,19 @@ static cudaError_t launch_sweep_pp(const shd_ctx *ctx, float *I, const float *et
     const float *c0L = bits ? (const float *)ctx->d_chi0L : nullptr;
     const unsigned long long *mb = bits ? ctx->d_mbits : nullptr;
     const size_t sm = sweep_pp_smem_bytes(ctx);
-    auto kern = bits ? (wide ? k_sweep_pp<U, true, true> : k_sweep_pp<U, true, false>)
-                     : (wide ? k_sweep_pp<U, false, true> : k_sweep_pp<U, false, false>);
+    auto kern = bits ? (wide ? k_sweep_pp<U, true, true, NT> : k_sweep_pp<U, true, false, NT>)
+                     : (wide ? k_sweep_pp<U, false, true, NT> : k_sweep_pp<U, false, false, NT>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<nblocks, 1024, sm, st>>>(P, I, eta, chi, c0L, mb, ctx->mbits_npc, ctx->mbits_nwin, tune_stride);
+    kern<<<nblocks, NT, sm, st>>>(P, I, eta, chi, c0L, mb, ctx->mbits_npc, ctx->mbits_nwin, tune_stride);
     note_launch();
     return cudaGetLastError();
 }
 
 // ---- schedules of the FP32 plane sweep ------------------------------------
 // A schedule splits every plane over a cluster of C CTAs of NT threads, U
-// nodes a thread (C = 1: k_sweep_pp, one 1024-thread CTA a plane).
+// nodes a thread (C = 1: k_sweep_pp, one CTA of NT = 1024, 512 or 256
+// threads a plane).
 
 struct SweepSched {
     int C = 0, NT = 0, U = 0, pstride = 0;
@@ -2127,9 +2129,13 @@ static cudaError_t run_sweep_sched(const shd_ctx *ctx, const SweepSched &sc, flo
                                    const float *chi, cudaStream_t st, bool bits, bool wide, int n, int tune_stride)
 {
     if (sc.C == 1) {
-        if (sc.U <= 1) return launch_sweep_pp<1>(ctx, I, eta, chi, st, bits, wide, (unsigned)n, tune_stride);
-        if (sc.U <= 2) return launch_sweep_pp<2>(ctx, I, eta, chi, st, bits, wide, (unsigned)n, tune_stride);
-        return launch_sweep_pp<4>(ctx, I, eta, chi, st, bits, wide, (unsigned)n, tune_stride);
+#define SHD_PP(Uv, NTv) \
+    if (sc.U == Uv && sc.NT == NTv) return launch_sweep_pp<Uv, NTv>(ctx, I, eta, chi, st, bits, wide, (unsigned)n, tune_stride);
+        SHD_PP(1, 1024) SHD_PP(2, 1024) SHD_PP(4, 1024)
+        SHD_PP(1, 512) SHD_PP(2, 512) SHD_PP(4, 512)
+        SHD_PP(1, 256) SHD_PP(2, 256) SHD_PP(4, 256)
+#undef SHD_PP
+        return cudaErrorInvalidConfiguration;
     }
 #define SHD_CL(NTv, Uv) \
     if (sc.NT == NTv && sc.U == Uv) return launch_sweep_cl_t<Uv, NTv>(ctx, sc, I, eta, chi, st, bits, wide, n, tune_stride);
@@ -2149,10 +2155,14 @@ static bool sweep_sched_make(const shd_ctx *c, int C, int NT, SweepSched &sc)
     sc = SweepSched();
     const size_t limit = 227 * 1024;
     if (C == 1) {  // any grid: k_sweep_pp copies unaligned planes as their aligned cover
-        if (NT != 1024) return false;
-        const int u = (sweep_plane_max(c) + 1023) / 1024;
+        if (NT != 1024 && NT != 512 && NT != 256) return false;
+        const int pm = sweep_plane_max(c);
+        const int u = (pm + NT - 1) / NT;
         if (u > 4 || sweep_pp_smem_bytes(c) > limit) return false;
-        sc.C = 1; sc.NT = 1024; sc.U = u <= 1 ? 1 : (u <= 2 ? 2 : 4);
+        // smaller CTAs only where they keep more than half their threads busy
+        if (NT < 1024 && pm <= NT / 2) return false;
+        if (NT < 1024 && (1024 / NT) * sweep_pp_smem_bytes(c) > limit) return false;  // their CTAs share the SM
+        sc.C = 1; sc.NT = NT; sc.U = u <= 1 ? 1 : (u <= 2 ? 2 : 4);
         sc.smem = sweep_pp_smem_bytes(c);
         return true;
     }
@@ -2182,6 +2192,8 @@ static std::vector<SweepSched> sweep_candidates(const shd_ctx *c)
     std::vector<SweepSched> v;
     SweepSched sc;
     if (sweep_sched_make(c, 1, 1024, sc)) v.push_back(sc);
+    for (int NT : {512, 256})
+        if (sweep_sched_make(c, 1, NT, sc)) v.push_back(sc);
     for (int C : {2, 4, 8})
         for (int NT : {256, 384, 512, 768, 1024})
             if (sweep_sched_make(c, C, NT, sc)) v.push_back(sc);
@@ -2298,13 +2310,13 @@ int sweep_batch_class(const shd_ctx *c)
     if (c->precision == SHD_FP64 || c->integrator != SHD_SC_LINEAR) return 0;
     SweepSched sc;
     if (!sweep_sched_make(c, 1, 1024, sc)) return 0;
-    if (c->sweep_force_C > 0 && c->sweep_force_C != 1) return 0;
-    if (c->sweep_force_C <= 0 && c->sweep_C > 1) {
-        // a cluster schedule won the problem's timing: it joins only if the
-        // one-CTA sweep timed within 3 % of that
+    if (c->sweep_force_C > 0 && !(c->sweep_force_C == 1 && c->sweep_force_NT == 1024)) return 0;
+    if (c->sweep_force_C <= 0 && c->sweep_C > 0 && !(c->sweep_C == 1 && c->sweep_NT == 1024)) {
+        // another schedule won the problem's timing: it joins only if the
+        // 1024-thread one-CTA sweep (the batch's) timed within 3 % of that
         float pp = -1.f, best = 1e30f;
         for (int k = 0; k < c->sweep_ntune; ++k) {
-            if (c->sweep_tune[k][0] == 1.f) pp = c->sweep_tune[k][2];
+            if (c->sweep_tune[k][0] == 1.f && c->sweep_tune[k][1] == 1024.f) pp = c->sweep_tune[k][2];
             best = fminf(best, c->sweep_tune[k][2]);
         }
         if (!(pp > 0.f && pp <= 1.03f * best)) return 0;

@@ -20,6 +20,11 @@ eq:shdom, Sec. 2.1 eq:time).  Grids:
   of 4 z-nodes would leave it empty and sweep only 384-node planes).  8 x 384
   and 4 x 768 threads hold its blocks of 1152 and 2304 nodes at exactly three
   nodes a thread.
+* (21, 22, 19): a ragged grid (no plane, and not Nc, a multiple of 4), which
+  only one-CTA schedules sweep: 1024, 512 and 256 threads, each plane copied
+  as its 16-byte aligned cover;
+* (32, 32, 8): 1024-node planes, swept by one CTA of 1024, 512 or 256
+  threads as well as by clusters.
 """
 import numpy as np
 import pytest
@@ -30,7 +35,7 @@ from paper_1507_05141_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 2e-5
-SCHEDULES = [(1, 1024), (2, 256), (2, 384), (2, 512), (2, 768), (2, 1024), (4, 256), (4, 384), (4, 512),
+SCHEDULES = [(1, 1024), (1, 512), (1, 256), (2, 256), (2, 384), (2, 512), (2, 768), (2, 1024), (4, 256), (4, 384), (4, 512),
              (4, 768), (4, 1024), (8, 256), (8, 384), (8, 512), (8, 768), (8, 1024)]
 
 
@@ -52,7 +57,7 @@ def _oracle_step(spec, I0):
     return I
 
 
-@pytest.mark.parametrize("grid", [(60, 52, 6), (62, 52, 6), (96, 96, 32)])
+@pytest.mark.parametrize("grid", [(60, 52, 6), (62, 52, 6), (96, 96, 32), (21, 22, 19), (32, 32, 8)])
 def test_every_schedule(native, grid):
     spec = inputs.ragged_mixed(grid=grid, G=2, L=3)
     I0 = inputs.random_state(spec, seed=41)
@@ -77,6 +82,11 @@ def test_every_schedule(native, grid):
             assert np.array_equal(I, first[1]), ((C, NT), first[0])
         ran.append((C, NT))
     s.close()
+    if grid in ((21, 22, 19), (32, 32, 8)):
+        assert (1, 512) in ran and (1, 256) in ran, ran
+    if grid == (21, 22, 19):
+        assert all(c == 1 for c, _ in ran), ran  # clusters need aligned planes
+        return
     assert any(c > 1 for c, _ in ran), "no cluster schedule ran"
     if grid == (96, 96, 32):
         assert (1, 1024) not in ran  # the 9216-node planes need a cluster
