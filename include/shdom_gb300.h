@@ -354,7 +354,7 @@ unsigned long long shd_launch_count(void);
  *   after its state was set, and every step while its per-stage timing is on,
  *   runs as direct launches.  Errors: those of shd_step, per problem (the
  *   message names it).
- *   In sweep mode 1 (the default) the replayed steps of FP32 backward-Euler
+ *   In sweep mode 1 the replayed steps of FP32 backward-Euler
  *   problems with the linear short-characteristics integrator, planes the
  *   one-CTA sweep holds, and no cluster schedule forced or timed more than
  *   3 % faster (shd_get_sweep_schedule) run stages a1-a3 per problem and
@@ -362,8 +362,10 @@ unsigned long long shd_launch_count(void);
  *   variant, over a work list of every such problem's (ordinate, group)
  *   pairs; the other problems sweep in their own launches.  Results are
  *   those of shd_step, bit for bit.
- * shd_batch_set_sweep_mode: 1 (default) as above; 0 every problem sweeps in
- *   its own launches.  Synchronises the device when the mode changes.
+ * shd_batch_set_sweep_mode: 0 (default) every problem sweeps in its own
+ *   launches, concurrent with the other problems' stages; 1 as above (one
+ *   launch, after every member's stages a1-a3).  Synchronises the device
+ *   when the mode changes.
  *   Errors: SHD_ERR_ARG (NULL batch, mode not 0 or 1).
  * shd_batch_destroy: frees the batch (not the contexts). */
 typedef struct shd_batch shd_batch;

@@ -206,6 +206,7 @@ int dalloc(shd_ctx *c, void **p, size_t bytes, const char *what)
 // drop everything that depends on the problem sizes
 void drop_sized(shd_ctx *c)
 {
+    c->chi_rest_valid = false;
     c->sweep_C = c->sweep_NT = 0;  // the sweep schedule depends on the sizes
     c->sweep_ntune = 0;
     void **ptrs[] = {&c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
@@ -569,6 +570,7 @@ int stream_after(cudaStream_t waiter, cudaStream_t producer)
 // brick by brick so that a brick's remap CTAs run side by side.
 int build_tiles(shd_ctx *c, const double *u)
 {
+    c->chi_rest_valid = false;  // nodes that stop moving need chi0 in chi_lab again
     dfree(c->d_tiles); dfree((void *&)c->d_moving); dfree((void *&)c->d_mflag); dfree((void *&)c->d_mbits);
     dfree((void *&)c->d_midx); dfree((void *&)c->d_mtiles);
     for (int i = 0; i < 3; ++i) dfree(c->d_nm[i]);
@@ -871,6 +873,26 @@ int ensure_remap_tables(shd_ctx *c, cudaStream_t st)
     return SHD_OK;
 }
 
+// The segment transform (MIXED) stores chi_lab only where a node moves; the
+// entries at rest then come from one fill with chi0.
+template <class T>
+bool rest_chi_kept(const shd_ctx *c)
+{
+    if constexpr (sizeof(T) == 4) return c->precision == SHD_MIXED && seg_usable(c) && c->d_chi0L;
+    return false;
+}
+
+// The fill of chi_lab at rest on st, unless it still holds (kept outside
+// captured steps: capture_step and the batch call this before capturing).
+template <class T>
+int ensure_chi_rest(shd_ctx *c, cudaStream_t st)
+{
+    if (c->chi_rest_valid || !rest_chi_kept<T>(c)) return SHD_OK;
+    CK(launch_chi_rest_fill<T>(c, (T *)c->d_chi, st), "chi at rest");
+    c->chi_rest_valid = true;
+    return SHD_OK;
+}
+
 // The kernels of one step on stream st (timing events around the stages when
 // ev is given); S_lm / S_prev are not swapped here.
 template <class T>
@@ -899,10 +921,16 @@ int step_once(shd_ctx *c, cudaStream_t st, cudaEvent_t *ev, const std::function<
         int rc = (*after_source)();
         if (rc) return rc;
     }
-    // the sweep takes chi at nodes at rest from the chi0 layouts, so chi_lab
-    // is needed only where a node moves
+    // the sweep takes chi at nodes at rest from the chi0 layouts (c0L), or
+    // from chi_lab, where the segment transform leaves chi0 of the one-time
+    // fill: either way a3 stores chi only where a node moves
     const bool c0L = sweep_uses_chi0L<T>(c);
-    CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st, !c0L), "sh2lab");
+    bool full_chi = !c0L;
+    if (rest_chi_kept<T>(c)) {
+        if (int rc = ensure_chi_rest<T>(c, st)) return rc;
+        full_chi = false;
+    }
+    CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st, full_chi), "sh2lab");
     if (tm) CK(cudaEventRecord(ev[4], st), "event");
     if (!c->skip_sweep)  // (a batch sweeps every problem of it in one launch)
         CK(launch_sweep<T>(c, (T *)c->d_I, (const T *)c->d_eta, (const T *)c->d_chi, st, c0L), "sweep");
@@ -1107,6 +1135,7 @@ int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false,
 {
     if (int rc = ensure_remap_tables(c, st)) return rc;
     if (int rc = ensure_rk_buffers(c)) return rc;
+    if (int rc = ensure_chi_rest<T>(c, st)) return rc;  // before any capture
     for (int s = 0; s < nsteps; ++s) {
         // a replay of the captured step: a step with S_prev, no timing events
         if (graphs) {
@@ -1397,6 +1426,7 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         c->nthchunk = 0;
     }
     if (c->have_scat) {
+        c->chi_rest_valid = false;  // chi0 changes: chi_lab at rest is filled again
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
         else CK(launch_chi0<float>(c, c->stream), "chi0");
     }
@@ -1519,6 +1549,7 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
         CK(launch_source_tc_operands(c, c->stream), "source operands");
     }
     if (c->have_fields) {
+        c->chi_rest_valid = false;  // chi0 changes: chi_lab at rest is filled again
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
         else CK(launch_chi0<float>(c, c->stream), "chi0");
     }
@@ -2044,7 +2075,7 @@ int shd_get_timing(shd_ctx *c, double *stage_ms, long long *steps)
 struct shd_batch {
     std::vector<shd_ctx *> probs;
     int device = 0;
-    int sweep_mode = 1;  // 1: one plane-sweep launch per class of problems
+    int sweep_mode = 0;  // 1: one plane-sweep launch per class of problems
     // cached graphs of one batch step: the key is each problem's graph
     // generation, slot (-1: that problem steps by direct launches) and
     // sweep class (0: the problem's graph holds its own sweep; otherwise the
@@ -2196,6 +2227,8 @@ int shd_batch_step(shd_batch *b, int nsteps, void *stream)
         for (int p = 0; p < np; ++p) {
             shd_ctx *c = b->probs[p];
             int slot = -1, cls = 0, rc;
+            rc = is_fp64(c) ? ensure_chi_rest<double>(c, st) : ensure_chi_rest<float>(c, st);
+            if (rc) return fail(rc, "problem %d: %s", p, std::string(g_err).c_str());
             rc = is_fp64(c) ? graph_slot<double>(c, slot) : graph_slot<float>(c, slot);
             if (rc) return fail(rc, "problem %d: %s", p, std::string(g_err).c_str());
             if (slot < 0) {

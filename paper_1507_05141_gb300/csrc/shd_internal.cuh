@@ -285,6 +285,10 @@ struct shd_ctx {
     void *graph_ns_sp[2] = {nullptr, nullptr};
     unsigned long long graph_ns_kernels[2] = {0, 0};
     bool skip_sweep = false;  // set only while the sweep-less step is captured
+    // chi_lab at every node at rest holds chi0 (k_chi_rest_fill since the
+    // last change of chi0, of the moving set or of the buffers), so a3 need
+    // not store it every step
+    bool chi_rest_valid = false;
     void *graph_sp[2] = {nullptr, nullptr};
     unsigned long long graph_kernels[2] = {0, 0};  // kernel launches per replay
     cudaStream_t cap_stream = nullptr;
@@ -805,6 +809,10 @@ cudaError_t launch_sweep(const shd_ctx *ctx, T *I, const T *eta, const T *chi, c
                          bool use_chi0L = false);
 template <class T>
 bool sweep_uses_chi0L(const shd_ctx *ctx);
+// chi_lab[k][g][o] = chi0L[d(k)][g][o] for every ordinate, group and node
+// (the value a3 stores at a node at rest, in the sweep layout)
+template <class T>
+cudaError_t launch_chi_rest_fill(const shd_ctx *ctx, T *chi, cudaStream_t st);
 bool sweep_schedule_valid(const shd_ctx *ctx, int C, int NT);
 
 // One problem of a batched plane sweep (k_sweep_batch): its fields, arrays

@@ -1961,6 +1961,35 @@ static int sweep_plane_max(const shd_ctx *c)
 }
 size_t sweep_smem_bytes(const shd_ctx *c) { return (size_t)3 * c->esize * sweep_plane_max(c); }
 
+// chi at rest in every ordinate's sweep layout: row (k, g) of chi_lab is row
+// (d(k), g) of the chi0 layouts, d(k) the sweep axis of ordinate k.
+template <class T>
+__global__ void k_chi_rest_fill(Prob<T> P, const T *__restrict__ chi0L, T *__restrict__ chi)
+{
+    const long long rows = (long long)P.N * P.G;
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int k = (int)(row / P.G), g = (int)(row - (long long)k * P.G);
+        const T *src = chi0L + ((long long)P.ord[k].d * P.G + g) * P.Nc;
+        T *dst = chi + row * P.Nc;
+        for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < P.Nc;
+             o += (long long)gridDim.x * blockDim.x)
+            dst[o] = src[o];
+    }
+}
+
+template <class T>
+cudaError_t launch_chi_rest_fill(const shd_ctx *ctx, T *chi, cudaStream_t st)
+{
+    if (!ctx->d_chi0L) return cudaErrorInvalidValue;
+    Prob<T> P = make_prob<T>(ctx);
+    const long long rows = (long long)ctx->N * ctx->G;
+    const int bx = (int)std::min<long long>((ctx->Nc + 255) / 256, 64);
+    const int by = (int)std::min<long long>(rows, 16384);
+    k_chi_rest_fill<T><<<dim3((unsigned)bx, (unsigned)by), 256, 0, st>>>(P, (const T *)ctx->d_chi0L, chi);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_chi0(const shd_ctx *ctx, cudaStream_t st)
 {
@@ -2777,6 +2806,7 @@ cudaError_t launch_rk_stage(T *I, const T *A, T *B, T *acc, long long n, double 
     template cudaError_t launch_chi0<T>(const shd_ctx *, cudaStream_t);                                     \
     template cudaError_t launch_source<T>(const shd_ctx *, const T *, T *, cudaStream_t);                   \
     template cudaError_t launch_sweep<T>(const shd_ctx *, T *, const T *, const T *, cudaStream_t, bool);   \
+    template cudaError_t launch_chi_rest_fill<T>(const shd_ctx *, T *, cudaStream_t);                         \
     template bool sweep_uses_chi0L<T>(const shd_ctx *);                                                     \
     template cudaError_t launch_sums<T>(shd_ctx *, const T *, const T *, const T *, bool, cudaStream_t);    \
     template cudaError_t launch_source_sums<T>(shd_ctx *, const T *, T *, const T *, const T *, bool,       \

@@ -1281,10 +1281,10 @@ static cudaError_t run_sh2lab_rows(const shd_ctx *ctx, const Prob<float> &P, con
 // a3: the comoving S0 of moving nodes (node-major, nm0), their remap to the
 // laboratory eta, chi (nm1, nm2), then eta, chi of every node into the sweep
 // layout (moving rows taken from nm1, nm2).  Without full_chi, chi is stored
-// only for the 32-node runs that hold a moving node: every 4-node piece the
-// sweep reads from chi lies in such a run.  (Not so when a plane's rows are
-// not multiples of 4 nodes: a piece may straddle two rows, so those grids
-// always store every chi.)
+// only for the 32-node runs that hold a moving node; the caller keeps chi0
+// in chi_lab at every node at rest (k_chi_rest_fill once per change of chi0
+// or of the moving set), so every chi the sweep reads is valid, also in a
+// 4-node piece that straddles two rows.
 cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, float *chi, float *nm0, float *nm1,
                               float *nm2, cudaStream_t st, bool full_chi)
 {
@@ -1303,7 +1303,7 @@ cudaError_t launch_sh2lab_seg(const shd_ctx *ctx, const float *Sp, float *eta, f
         if (ctx->tcs_nchunk[grp] == 0 || ctx->nseg[grp] == 0) continue;
         SegArgs a = seg_args(ctx, grp);
         const bool man = seg_manual(ctx);
-        a.chi_all = (full_chi || man) ? 1 : 0;
+        a.chi_all = full_chi ? 1 : 0;
         SegMaps maps{};
         if (!man) {
             if ((e = group_maps(ctx, grp, eta, &maps.m[0], true)) != cudaSuccess) return e;

@@ -418,8 +418,9 @@ class Batch:
         _check(self._L.shd_batch_step(self._h, int(nsteps), stream))
 
     def set_sweep_mode(self, mode):
-        """1 (default): the sweeps of every problem that allows it in one
-        persistent launch per kernel variant; 0: each problem sweeps alone."""
+        """0 (default): each problem sweeps in its own launches; 1: the
+        sweeps of every problem that allows it in one persistent launch per
+        kernel variant."""
         _check(self._L.shd_batch_set_sweep_mode(self._h, int(mode)))
 
     def close(self):

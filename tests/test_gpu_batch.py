@@ -108,7 +108,7 @@ def test_batched_sweep_matches_single_and_per_problem_sweeps(native):
             s.set_state(I0)
             g.append(s)
     b1, b0 = native.Batch(groups["b1"]), native.Batch(groups["b0"])
-    b0.set_sweep_mode(0)
+    b1.set_sweep_mode(1)
     nsteps = 5
     b1.step(2)
     b0.step(2)
