@@ -622,10 +622,12 @@ def bench_config1(args, dev):
 
 
 def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spec, plain_prec=None,
-                 scattering=None, notes=None):
+                 scattering=None, notes=None, report_every=None):
     """Device-timed steps of one problem, its end-to-end leg (fields
     uploaded, one step, the FP64 sums read back every step, as in the
-    benchmark's own leg) and the oracle's rate on a sample."""
+    benchmark's own leg; with report_every, that many steps and then the
+    moments J, H, K read back, the workload's Eddington-tensor report) and
+    the oracle's rate on a sample."""
     import numpy as np
     import torch
 
@@ -652,13 +654,16 @@ def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spe
     arrs = [h[1] for h in hold]
     h2d = sum(a.nbytes for a in arrs)
     d2h = 3 * 8
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = report_every or max(1, min(args.steps, 3))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         s.set_fields(*arrs)
         s.step(1, stream.cuda_stream)
         s.sums()
+    if report_every:
+        J, H, K = s.moments()  # the report: f_ij = K_ij / J on the host
+        d2h += (J.nbytes + H.nbytes + K.nbytes) / report_every
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     s.close()
@@ -687,6 +692,8 @@ def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spe
                          f"{cpu_spec.G} ({cpu_spec.updates_per_step:.3g} updates, {dt:.1f} s)"}
     e2e = {"value": upd * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "steps": e2e_steps}
+    if report_every:
+        e2e["report"] = f"J, H, K read back after the {report_every} steps (the Eddington tensor report)"
     extra = dict(extra)
     extra["source_pass"] = {"path": {0: "untimed", 1: "CUDA cores", 2: "tensor cores"}[src_path[0]],
                             "ms_cuda_cores": src_path[1], "ms_tensor_cores": src_path[2]}
@@ -730,7 +737,7 @@ def bench_config5(args, dev):
                                  f"Gamma=30 core, cold Klein-Nishina",
                         extra={"config": 5, "l2": "no flush: the intensity state is far larger than L2"},
                         errors_spec=inputs.jet_cocoon(n=16, G=8), cpu_spec=inputs.jet_cocoon(n=20, G=G),
-                        plain_prec=None, notes=note)
+                        plain_prec=None, notes=note, report_every=50)
 
 
 def bench_config4(args, dev):
