@@ -858,7 +858,8 @@ def bench_other(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 100, the jet workload's run length, for config 2; 20 otherwise)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
@@ -880,6 +881,8 @@ def main():
     ap.add_argument("--source-path", default="auto", choices=["auto", "cuda", "tensor"],
                     help="source pass of group-mixing kernels in MIXED (configs 3, 5): timed choice or forced")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 100 if (args.config == 2 and args.impl == "ours") else 20
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
