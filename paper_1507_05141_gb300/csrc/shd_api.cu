@@ -173,7 +173,8 @@ void free_all(shd_ctx *c)
                      (void **)&c->d_rrng[1], &c->d_dirs64, &c->d_fstage, &c->d_fcheck,
                      &c->d_ng[0], &c->d_ng[1], &c->d_ng[2], (void **)&c->d_ngpart, &c->d_rk[0], &c->d_rk[1],
                      &c->d_rk[2], (void **)&c->d_sums_save, &c->d_tcK, (void **)&c->d_thb,
-                     (void **)&c->d_thperm, &c->d_thw, &c->d_thK, &c->d_thso, (void **)&c->d_thchunk};
+                     (void **)&c->d_thperm, &c->d_thw, &c->d_thK, &c->d_thso, (void **)&c->d_thchunk,
+                     (void **)&c->d_chi_dirty};
     for (void **p : ptrs) dfree(*p);
     c->bytes = 0;
     c->rtab_n = 0;
@@ -206,7 +207,7 @@ int dalloc(shd_ctx *c, void **p, size_t bytes, const char *what)
 // drop everything that depends on the problem sizes
 void drop_sized(shd_ctx *c)
 {
-    c->chi_rest_valid = false;
+    c->chi_rest_state = 2;
     c->sweep_C = c->sweep_NT = 0;  // the sweep schedule depends on the sizes
     c->sweep_ntune = 0;
     void **ptrs[] = {&c->d_alpha0, &c->d_ne, &c->d_u, &c->d_emis0, &c->d_chi0, &c->d_K, &c->d_sigma_out, &c->d_bc,
@@ -539,6 +540,9 @@ int ensure_buffers(shd_ctx *c)
     if ((rc = dalloc(c, &c->d_emis0, nCG * es, "emis0"))) return rc;
     if ((rc = dalloc(c, &c->d_chi0, nCG * es, "chi0"))) return rc;
     if ((rc = dalloc(c, &c->d_chi0L, 3 * nCG * es, "chi0 layouts"))) return rc;
+    if ((rc = dalloc(c, (void **)&c->d_chi_dirty, sizeof(int), "chi0 change word"))) return rc;
+    CK(cudaMemset(c->d_chi_dirty, 0, sizeof(int)), "chi0 change word");
+    c->chi_rest_state = 2;
     if ((rc = dalloc(c, &c->d_ne, (size_t)c->Nc * es, "ne"))) return rc;
     if ((rc = dalloc(c, &c->d_u, (size_t)c->Nc * 3 * es, "u"))) return rc;
     c->n_partial = 8 * 152;
@@ -570,7 +574,7 @@ int stream_after(cudaStream_t waiter, cudaStream_t producer)
 // brick by brick so that a brick's remap CTAs run side by side.
 int build_tiles(shd_ctx *c, const double *u)
 {
-    c->chi_rest_valid = false;  // nodes that stop moving need chi0 in chi_lab again
+    c->chi_rest_state = 2;  // nodes that stop moving need chi0 in chi_lab again
     dfree(c->d_tiles); dfree((void *&)c->d_moving); dfree((void *&)c->d_mflag); dfree((void *&)c->d_mbits);
     dfree((void *&)c->d_midx); dfree((void *&)c->d_mtiles);
     for (int i = 0; i < 3; ++i) dfree(c->d_nm[i]);
@@ -873,23 +877,33 @@ int ensure_remap_tables(shd_ctx *c, cudaStream_t st)
     return SHD_OK;
 }
 
-// The segment transform (MIXED) stores chi_lab only where a node moves; the
-// entries at rest then come from one fill with chi0.
+// The segment transform (MIXED) stores chi_lab only where a node moves.  The
+// sweep reads chi at rest from the chi0 layout table where it can (aligned
+// rows, c0L); elsewhere -- other sweep kernels, or rows not a multiple of 4
+// nodes, where a 4-node piece may straddle a moving and a resting row -- it
+// reads chi_lab, whose entries at rest then come from one fill with chi0.
 template <class T>
 bool rest_chi_kept(const shd_ctx *c)
 {
-    if constexpr (sizeof(T) == 4) return c->precision == SHD_MIXED && seg_usable(c) && c->d_chi0L;
+    if constexpr (sizeof(T) == 4)
+        return c->precision == SHD_MIXED && seg_usable(c) && c->d_chi0L && c->d_chi_dirty;
     return false;
 }
+template <class T>
+bool rest_chi_read(const shd_ctx *c)
+{
+    return rest_chi_kept<T>(c) && (!sweep_uses_chi0L<T>(c) || seg_manual(c));
+}
 
-// The fill of chi_lab at rest on st, unless it still holds (kept outside
-// captured steps: capture_step and the batch call this before capturing).
+// The fill of chi_lab at rest on st where the sweep reads it and chi0 or the
+// moving set changed (kept outside captured steps: run_steps and the batch
+// call this before capturing; with chi0 unchanged it exits at once).
 template <class T>
 int ensure_chi_rest(shd_ctx *c, cudaStream_t st)
 {
-    if (c->chi_rest_valid || !rest_chi_kept<T>(c)) return SHD_OK;
-    CK(launch_chi_rest_fill<T>(c, (T *)c->d_chi, st), "chi at rest");
-    c->chi_rest_valid = true;
+    if (c->chi_rest_state == 0 || !rest_chi_read<T>(c)) return SHD_OK;
+    CK(launch_chi_rest_fill<T>(c, (T *)c->d_chi, st, c->chi_rest_state == 2), "chi at rest");
+    c->chi_rest_state = 0;
     return SHD_OK;
 }
 
@@ -927,7 +941,7 @@ int step_once(shd_ctx *c, cudaStream_t st, cudaEvent_t *ev, const std::function<
     const bool c0L = sweep_uses_chi0L<T>(c);
     bool full_chi = !c0L;
     if (rest_chi_kept<T>(c)) {
-        if (int rc = ensure_chi_rest<T>(c, st)) return rc;
+        if (int rc = ensure_chi_rest<T>(c, st)) return rc;  // where the sweep reads chi_lab at rest
         full_chi = false;
     }
     CK(launch_sh2lab<T>(c, (const T *)c->d_Sp, (T *)c->d_eta, (T *)c->d_chi, st, full_chi), "sh2lab");
@@ -1426,7 +1440,7 @@ int shd_set_fields(shd_ctx *c, const double *alpha0, const double *ne, const dou
         c->nthchunk = 0;
     }
     if (c->have_scat) {
-        c->chi_rest_valid = false;  // chi0 changes: chi_lab at rest is filled again
+        c->chi_rest_state = std::max(c->chi_rest_state, 1);  // chi0 may change: k_chi0_layout says
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
         else CK(launch_chi0<float>(c, c->stream), "chi0");
     }
@@ -1549,7 +1563,7 @@ int shd_set_scattering(shd_ctx *c, int kind, const double *K, const double *sigm
         CK(launch_source_tc_operands(c, c->stream), "source operands");
     }
     if (c->have_fields) {
-        c->chi_rest_valid = false;  // chi0 changes: chi_lab at rest is filled again
+        c->chi_rest_state = std::max(c->chi_rest_state, 1);  // chi0 may change: k_chi0_layout says
         if (is_fp64(c)) CK(launch_chi0<double>(c, c->stream), "chi0");
         else CK(launch_chi0<float>(c, c->stream), "chi0");
     }

@@ -285,10 +285,12 @@ struct shd_ctx {
     void *graph_ns_sp[2] = {nullptr, nullptr};
     unsigned long long graph_ns_kernels[2] = {0, 0};
     bool skip_sweep = false;  // set only while the sweep-less step is captured
-    // chi_lab at every node at rest holds chi0 (k_chi_rest_fill since the
-    // last change of chi0, of the moving set or of the buffers), so a3 need
-    // not store it every step
-    bool chi_rest_valid = false;
+    // chi_lab at the nodes at rest against chi0 (k_chi_rest_fill), so that a3
+    // need not store it every step: 0 it holds chi0; 1 it holds chi0 unless
+    // the device word d_chi_dirty says chi0 changed since the last fill
+    // (k_chi0_layout raises it); 2 it must be filled (new buffers or moving set)
+    int chi_rest_state = 2;
+    int *d_chi_dirty = nullptr;
     void *graph_sp[2] = {nullptr, nullptr};
     unsigned long long graph_kernels[2] = {0, 0};  // kernel launches per replay
     cudaStream_t cap_stream = nullptr;
@@ -811,8 +813,9 @@ template <class T>
 bool sweep_uses_chi0L(const shd_ctx *ctx);
 // chi_lab[k][g][o] = chi0L[d(k)][g][o] for every ordinate, group and node
 // (the value a3 stores at a node at rest, in the sweep layout)
+// force = 0: only if *d_chi_dirty is set; the word is cleared after the fill
 template <class T>
-cudaError_t launch_chi_rest_fill(const shd_ctx *ctx, T *chi, cudaStream_t st);
+cudaError_t launch_chi_rest_fill(const shd_ctx *ctx, T *chi, cudaStream_t st, bool force);
 bool sweep_schedule_valid(const shd_ctx *ctx, int C, int NT);
 
 // One problem of a batched plane sweep (k_sweep_batch): its fields, arrays

@@ -92,7 +92,7 @@ __global__ void k_chi0(Prob<T> P, T *chi0)
 // with u = 0), so the sweep reads it from this small table instead of the
 // per-ordinate chi_lab.
 template <class T>
-__global__ void k_chi0_layout(Prob<T> P, const T *__restrict__ chi0, T *__restrict__ chi0L)
+__global__ void k_chi0_layout(Prob<T> P, const T *__restrict__ chi0, T *__restrict__ chi0L, int *__restrict__ dirty)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long per = (long long)P.G * P.Nc;
@@ -110,7 +110,9 @@ __global__ void k_chi0_layout(Prob<T> P, const T *__restrict__ chi0, T *__restri
         iy = (int)(o % P.ny); iz = (int)((o / P.ny) % P.nz); ix = (int)(o / ((long long)P.ny * P.nz));
     }
     const long long c = ((long long)iz * P.ny + iy) * P.nx + ix;
-    chi0L[i] = chi0[c * P.G + g];
+    const T v = chi0[c * P.G + g];
+    if (dirty && chi0L[i] != v) *dirty = 1;  // chi_lab at rest no longer holds chi0
+    chi0L[i] = v;
 }
 
 // -------------------------------------------------------------------------
@@ -1964,8 +1966,10 @@ size_t sweep_smem_bytes(const shd_ctx *c) { return (size_t)3 * c->esize * sweep_
 // chi at rest in every ordinate's sweep layout: row (k, g) of chi_lab is row
 // (d(k), g) of the chi0 layouts, d(k) the sweep axis of ordinate k.
 template <class T>
-__global__ void k_chi_rest_fill(Prob<T> P, const T *__restrict__ chi0L, T *__restrict__ chi)
+__global__ void k_chi_rest_fill(Prob<T> P, const T *__restrict__ chi0L, T *__restrict__ chi,
+                                const int *__restrict__ dirty, int force)
 {
+    if (!force && *dirty == 0) return;  // chi0 unchanged since the last fill
     const long long rows = (long long)P.N * P.G;
     for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
         const int k = (int)(row / P.G), g = (int)(row - (long long)k * P.G);
@@ -1978,16 +1982,19 @@ __global__ void k_chi_rest_fill(Prob<T> P, const T *__restrict__ chi0L, T *__res
 }
 
 template <class T>
-cudaError_t launch_chi_rest_fill(const shd_ctx *ctx, T *chi, cudaStream_t st)
+cudaError_t launch_chi_rest_fill(const shd_ctx *ctx, T *chi, cudaStream_t st, bool force)
 {
-    if (!ctx->d_chi0L) return cudaErrorInvalidValue;
+    if (!ctx->d_chi0L || !ctx->d_chi_dirty) return cudaErrorInvalidValue;
     Prob<T> P = make_prob<T>(ctx);
     const long long rows = (long long)ctx->N * ctx->G;
-    const int bx = (int)std::min<long long>((ctx->Nc + 255) / 256, 64);
-    const int by = (int)std::min<long long>(rows, 16384);
-    k_chi_rest_fill<T><<<dim3((unsigned)bx, (unsigned)by), 256, 0, st>>>(P, (const T *)ctx->d_chi0L, chi);
+    const int bx = (int)std::min<long long>((ctx->Nc + 255) / 256, 32);
+    const int by = (int)std::min<long long>(rows, 64);  // 32 x 64 CTAs stride over the rows
+    k_chi_rest_fill<T><<<dim3((unsigned)bx, (unsigned)by), 256, 0, st>>>(P, (const T *)ctx->d_chi0L, chi,
+                                                                          ctx->d_chi_dirty, force ? 1 : 0);
     note_launch();
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(ctx->d_chi_dirty, 0, sizeof(int), st);
 }
 
 template <class T>
@@ -1999,7 +2006,8 @@ cudaError_t launch_chi0(const shd_ctx *ctx, cudaStream_t st)
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !ctx->d_chi0L) return e;
-    k_chi0_layout<T><<<blocks_for(3 * n, 256), 256, 0, st>>>(P, (const T *)ctx->d_chi0, (T *)ctx->d_chi0L);
+    k_chi0_layout<T><<<blocks_for(3 * n, 256), 256, 0, st>>>(P, (const T *)ctx->d_chi0, (T *)ctx->d_chi0L,
+                                                            ctx->d_chi_dirty);
     note_launch();
     return cudaGetLastError();
 }
@@ -2806,7 +2814,7 @@ cudaError_t launch_rk_stage(T *I, const T *A, T *B, T *acc, long long n, double 
     template cudaError_t launch_chi0<T>(const shd_ctx *, cudaStream_t);                                     \
     template cudaError_t launch_source<T>(const shd_ctx *, const T *, T *, cudaStream_t);                   \
     template cudaError_t launch_sweep<T>(const shd_ctx *, T *, const T *, const T *, cudaStream_t, bool);   \
-    template cudaError_t launch_chi_rest_fill<T>(const shd_ctx *, T *, cudaStream_t);                         \
+    template cudaError_t launch_chi_rest_fill<T>(const shd_ctx *, T *, cudaStream_t, bool);                   \
     template bool sweep_uses_chi0L<T>(const shd_ctx *);                                                     \
     template cudaError_t launch_sums<T>(shd_ctx *, const T *, const T *, const T *, bool, cudaStream_t);    \
     template cudaError_t launch_source_sums<T>(shd_ctx *, const T *, T *, const T *, const T *, bool,       \

@@ -519,7 +519,8 @@ def test_chi_at_rest_follows_fields_and_flow(native, grid, integrator):
     through the segment transform's row path; the Bezier sweep on an aligned
     grid) while the transform stores chi only where a node moves: the entries
     at rest hold chi0 from a one-time fill, which must follow a new
-    absorption (chi0 changes, the captured step is kept) and a flow in which
+    absorption (chi0 changes, the captured step is kept; the same fields
+    uploaded again change nothing and skip the fill) and a flow in which
     some nodes come to rest (the moving set changes).  Three legs of two
     steps against the oracle running the same sequence (Sec. 2 eq:shdom,
     Sec. 2.1 eq:time, Sec. 2.2)."""
@@ -535,7 +536,9 @@ def test_chi_at_rest_follows_fields_and_flow(native, grid, integrator):
     s.step(2)
     spec2 = dataclasses.replace(spec, alpha0=spec.alpha0 * 1.7)
     s.set_fields(spec2.alpha0, spec2.ne, spec2.u, spec2.emis0)
-    s.step(2)
+    s.step(1)
+    s.set_fields(spec2.alpha0, spec2.ne, spec2.u, spec2.emis0)  # unchanged: the fill is skipped
+    s.step(1)
     u3 = spec2.u.copy()
     u3[::5] = 0.0  # some nodes come to rest
     spec3 = dataclasses.replace(spec2, u=u3)
