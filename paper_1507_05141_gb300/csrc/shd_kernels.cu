@@ -946,10 +946,12 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_batch(const SweepBatchProb *_
 // cluster's barrier wait overlaps another's compute; planes larger than one
 // CTA's shared memory fit across the cluster.  Every CTA runs every barrier
 // (no early exit) and a final one keeps its buffers alive until the peers'
-// last reads are done.
+// last reads are done.  At 384 threads (three nodes a thread) the register
+// cap is 56, so three CTAs share an SM: one more cluster's compute under
+// each barrier wait.
 // -------------------------------------------------------------------------
 template <int U, bool CB, bool WIDE, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_sweep_cl(Prob<float> P, float *__restrict__ I, const float *__restrict__ eta,
+__global__ void __launch_bounds__(NT, NT == 384 ? 3 : 1024 / NT) k_sweep_cl(Prob<float> P, float *__restrict__ I, const float *__restrict__ eta,
                                                  const float *__restrict__ chi, const float *__restrict__ chi0L,
                                                  const unsigned long long *__restrict__ mbits, int npc, int nwin,
                                                  int pstride, int tune_stride)
@@ -2140,6 +2142,10 @@ static cudaError_t launch_sweep_cl_t(const shd_ctx *ctx, const SweepSched &sc, f
     auto kern = bits ? (wide ? k_sweep_cl<U, true, true, NT> : k_sweep_cl<U, true, false, NT>)
                      : (wide ? k_sweep_cl<U, false, true, NT> : k_sweep_cl<U, false, false, NT>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.smem);
+    if (e != cudaSuccess) return e;
+    // the whole unified L1 as shared memory, so that the CTAs the register
+    // budget allows (three of 384 threads at 56 registers) also fit there
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nclusters * sc.C));
