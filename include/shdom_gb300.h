@@ -263,7 +263,7 @@ int shd_get_state_dev(shd_ctx *ctx, double *dev_I, void *cuda_stream);
  * linear integrator): every plane of an (ordinate, group) pair is swept by
  * one CTA of NT threads (C = 1; NT = 1024, or 512 / 256 for planes of at
  * most 4 NT nodes, several CTAs an SM; any grid) or split over a
- * thread-block cluster of C CTAs (C = 2, 4 or 8; NT = 256, 384, 512, 768 or
+ * thread-block cluster of C CTAs (C = 2, 4, 8 or 16; NT = 256, 384, 512, 768 or
  * 1024; grids whose planes and node count are multiples of 4), each CTA
  * owning a block of rows; rows next to another CTA's block read it through
  * distributed shared memory.  The result does not depend on the schedule

@@ -2147,6 +2147,10 @@ static cudaError_t launch_sweep_cl_t(const shd_ctx *ctx, const SweepSched &sc, f
     // budget allows (three of 384 threads at 56 registers) also fit there
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
+    if (sc.C > 8) {  // 16-CTA clusters are beyond the portable size: opted in per kernel
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nclusters * sc.C));
     cfg.blockDim = dim3(NT);
@@ -2209,7 +2213,7 @@ static bool sweep_sched_make(const shd_ctx *c, int C, int NT, SweepSched &sc)
         sc.smem = sweep_pp_smem_bytes(c);
         return true;
     }
-    if (C != 2 && C != 4 && C != 8) return false;
+    if (C != 2 && C != 4 && C != 8 && C != 16) return false;
     if (!sweep_vec<float>(c)) return false;  // the cluster sweep's blocks need 16-byte aligned planes
     if (NT != 256 && NT != 384 && NT != 512 && NT != 768 && NT != 1024) return false;
     const int nl = sweep_nloc_max(c, C);
@@ -2237,7 +2241,7 @@ static std::vector<SweepSched> sweep_candidates(const shd_ctx *c)
     if (sweep_sched_make(c, 1, 1024, sc)) v.push_back(sc);
     for (int NT : {512, 256})
         if (sweep_sched_make(c, 1, NT, sc)) v.push_back(sc);
-    for (int C : {2, 4, 8})
+    for (int C : {2, 4, 8, 16})
         for (int NT : {256, 384, 512, 768, 1024})
             if (sweep_sched_make(c, C, NT, sc)) v.push_back(sc);
     return v;

@@ -36,7 +36,8 @@ pytestmark = pytest.mark.gpu
 
 FP32_TOL = 2e-5
 SCHEDULES = [(1, 1024), (1, 512), (1, 256), (2, 256), (2, 384), (2, 512), (2, 768), (2, 1024), (4, 256), (4, 384), (4, 512),
-             (4, 768), (4, 1024), (8, 256), (8, 384), (8, 512), (8, 768), (8, 1024)]
+             (4, 768), (4, 1024), (8, 256), (8, 384), (8, 512), (8, 768), (8, 1024),
+             (16, 256), (16, 384), (16, 512), (16, 1024)]
 
 
 @pytest.fixture(scope="module")
