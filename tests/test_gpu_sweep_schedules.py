@@ -24,7 +24,9 @@ eq:shdom, Sec. 2.1 eq:time).  Grids:
   only one-CTA schedules sweep: 1024, 512 and 256 threads, each plane copied
   as its 16-byte aligned cover;
 * (32, 32, 8): 1024-node planes, swept by one CTA of 1024, 512 or 256
-  threads as well as by clusters.
+  threads as well as by clusters;
+* (128, 128, 32): 16384-node planes, whose 8-CTA blocks of 2048 nodes fill
+  every slot of 512 threads x 4 nodes (the 128^3 workload's schedule).
 """
 import numpy as np
 import pytest
@@ -58,7 +60,8 @@ def _oracle_step(spec, I0):
     return I
 
 
-@pytest.mark.parametrize("grid", [(60, 52, 6), (62, 52, 6), (96, 96, 32), (21, 22, 19), (32, 32, 8)])
+@pytest.mark.parametrize("grid", [(60, 52, 6), (62, 52, 6), (96, 96, 32), (21, 22, 19), (32, 32, 8),
+                                  (128, 128, 32)])
 def test_every_schedule(native, grid):
     spec = inputs.ragged_mixed(grid=grid, G=2, L=3)
     I0 = inputs.random_state(spec, seed=41)
@@ -89,6 +92,8 @@ def test_every_schedule(native, grid):
         assert all(c == 1 for c, _ in ran), ran  # clusters need aligned planes
         return
     assert any(c > 1 for c, _ in ran), "no cluster schedule ran"
+    if grid == (128, 128, 32):
+        assert (8, 512) in ran and (1, 1024) not in ran, ran
     if grid == (96, 96, 32):
         assert (1, 1024) not in ran  # the 9216-node planes need a cluster
         assert (8, 384) in ran and (4, 768) in ran  # three nodes a thread
