@@ -270,7 +270,10 @@ int shd_get_state_dev(shd_ctx *ctx, double *dev_I, void *cuda_stream);
  * (the same arithmetic per node).  By default the library times every
  * schedule that fits on the first sweep run outside a stream capture (over
  * a sample of pairs, on a scratch intensity it allocates and frees there)
- * and keeps the fastest until the grid, angles or groups change.
+ * and keeps the fastest until the grid, angles or groups change.  The choice
+ * is also kept for the process: a later context of the same shape (device,
+ * grid, groups, ordinates per sweep class, chi0-table use) takes it, with its
+ * timing record, instead of timing again.
  * shd_set_sweep_schedule forces (C, NT) (SHD_ERR_ARG if it does not fit the
  * problem), or with C = 0 returns to the automatic choice.
  * shd_get_sweep_schedule reports the schedule in use (0, 0 before the first

@@ -13,6 +13,8 @@
 #include <cstring>
 #include <new>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "shd_internal.cuh"
@@ -1143,10 +1145,63 @@ int graph_slot(shd_ctx *c, int &slot)
     return SHD_OK;
 }
 
+// The timed choice of the FP32 sweep schedule, shared by every context of
+// the same shape in the process: a problem whose shape was timed before
+// takes that choice (and its timing record) instead of timing again.
+struct SchedKey {
+    int device, nx, ny, nz, G, N, ncls[3], bits;
+    bool operator<(const SchedKey &o) const { return std::memcmp(this, &o, sizeof(SchedKey)) < 0; }
+};
+struct SchedChoice {
+    int C, NT, ntune;
+    float tune[16][3];
+};
+std::mutex g_sched_mu;
+std::map<SchedKey, SchedChoice> g_sched_cache;
+
+bool sched_key(const shd_ctx *c, SchedKey &k)
+{
+    if (c->precision == SHD_FP64 || c->integrator != SHD_SC_LINEAR || c->sweep_force_C > 0) return false;
+    std::memset(&k, 0, sizeof(k));
+    k.device = c->device;
+    k.nx = c->nx; k.ny = c->ny; k.nz = c->nz;
+    k.G = c->G; k.N = c->N;
+    for (const Ordinate &o : c->h_ord) k.ncls[o.d]++;
+    k.bits = sweep_uses_chi0L<float>(c) ? 1 : 0;
+    return true;
+}
+
+void sched_cache_take(shd_ctx *c)
+{
+    SchedKey k;
+    if (c->sweep_C > 0 || !sched_key(c, k)) return;
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    auto it = g_sched_cache.find(k);
+    if (it == g_sched_cache.end() || !sweep_schedule_valid(c, it->second.C, it->second.NT)) return;
+    c->sweep_C = it->second.C;
+    c->sweep_NT = it->second.NT;
+    c->sweep_ntune = it->second.ntune;
+    std::memcpy(c->sweep_tune, it->second.tune, sizeof(c->sweep_tune));
+}
+
+void sched_cache_keep(const shd_ctx *c)
+{
+    SchedKey k;
+    if (c->sweep_C <= 0 || c->sweep_ntune <= 0 || !sched_key(c, k)) return;
+    SchedChoice v;
+    v.C = c->sweep_C;
+    v.NT = c->sweep_NT;
+    v.ntune = c->sweep_ntune;
+    std::memcpy(v.tune, c->sweep_tune, sizeof(v.tune));
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    g_sched_cache.emplace(k, v);
+}
+
 template <class T>
 int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false,
               const std::function<int()> *after_source = nullptr)
 {
+    if constexpr (sizeof(T) == 4) sched_cache_take(c);
     if (int rc = ensure_remap_tables(c, st)) return rc;
     if (int rc = ensure_rk_buffers(c)) return rc;
     if (int rc = ensure_chi_rest<T>(c, st)) return rc;  // before any capture
@@ -1167,6 +1222,7 @@ int run_steps(shd_ctx *c, int nsteps, cudaStream_t st, bool graphs = false,
         if (rc) return rc;
         std::swap(c->d_Sp, c->d_Sprev);
         c->sprev_valid = true;
+        if constexpr (sizeof(T) == 4) sched_cache_keep(c);
     }
     return SHD_OK;
 }

@@ -114,4 +114,21 @@ def test_automatic_choice_is_timed_and_kept(native):
     assert s.sweep_schedule()[0] == (C, NT)  # kept
     with pytest.raises(native.ShdError):
         s.set_sweep_schedule(3, 256)
+    # a second context of the same shape takes the choice without timing
+    s2 = native.Solver.from_spec(spec, precision="mixed")
+    s2.set_state(inputs.random_state(spec, seed=3))
+    s3 = native.Solver.from_spec(spec, precision="mixed")
+    s3.set_state(inputs.random_state(spec, seed=3))
+    s3.set_sweep_schedule(C, NT)  # forced: the same kernels, never timed
+    n0 = native.launch_count()
+    s2.step(2)
+    n_cached = native.launch_count() - n0
+    n0 = native.launch_count()
+    s3.step(2)
+    n_forced = native.launch_count() - n0
+    assert s2.sweep_schedule()[0] == (C, NT)
+    assert n_cached == n_forced, (n_cached, n_forced)  # no timing launches
+    assert np.array_equal(s2.get_state(), s3.get_state())
+    s2.close()
+    s3.close()
     s.close()
