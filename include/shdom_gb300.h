@@ -237,6 +237,17 @@ int shd_solve_static(shd_ctx *ctx, double rel_tol, int max_iter, int *iters_out,
  * projection Ish [c][g][p].  Any output may be NULL.  Synchronous. */
 int shd_get_moments(shd_ctx *ctx, double *J, double *H, double *K, double *Ish);
 
+/* The same moments of the current state (Sec. 2: the projection of stage a1)
+ * into caller-owned device memory: dev_mom [c][g][10] doubles on ctx's
+ * device, J, H_x, H_y, H_z, K_xx, K_yy, K_zz, K_xy, K_xz, K_yz per node and
+ * group, divided by 4 pi, the values shd_get_moments returns (single-precision
+ * results widened exactly).  Asynchronous on cuda_stream (NULL = the
+ * context's stream), ordered after the context's earlier work and before its
+ * later work; nothing is copied to the host.  A bounded-wait flag raised by
+ * the projection is reported by the next synchronous call.  Errors:
+ * SHD_ERR_ARG (dev_mom NULL), SHD_ERR_STATE (not configured, no state). */
+int shd_get_moments_dev(shd_ctx *ctx, double *dev_mom, void *cuda_stream);
+
 /* FP64 diagnostics of the last step (stage a5) of the state it started
  * from: energy = sum 4 pi J de_g, photons = sum 4 pi J de_g / ebar_g, resid =
  * ||S_new - S_old|| / ||S_new|| over all (c, g, p).  Synchronous. */

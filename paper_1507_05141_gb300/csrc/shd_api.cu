@@ -1871,6 +1871,43 @@ int shd_get_moments(shd_ctx *c, double *J, double *H, double *K, double *Ish)
     return SHD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// working-precision moments into the caller's FP64 array (an exact widening)
+template <class T>
+__global__ void k_widen(const T *__restrict__ src, double *__restrict__ dst, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+}  // namespace
+
+extern "C" {
+
+int shd_get_moments_dev(shd_ctx *c, double *dev_mom, void *stream)
+{
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!dev_mom) return fail(SHD_ERR_ARG, "dev_mom is NULL");
+    if ((rc = ready_for_step(c))) return rc;
+    if (!c->have_state) return fail(SHD_ERR_STATE, "state not set");
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    if ((rc = stream_after(st, c->stream))) return rc;
+    const long long n = (long long)c->Nc * c->G * 10;
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 4LL * 152);
+    if (is_fp64(c)) {
+        CK(launch_project<double>(c, (const double *)c->d_I, (double *)c->d_Ip, (double *)c->d_mom, st), "project");
+        CK(cudaMemcpyAsync(dev_mom, c->d_mom, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "moments");
+    } else {
+        CK(launch_project<float>(c, (const float *)c->d_I, (float *)c->d_Ip, (float *)c->d_mom, st), "project");
+        k_widen<float><<<blocks, 256, 0, st>>>((const float *)c->d_mom, dev_mom, n);
+        note_launch();
+        CK(cudaGetLastError(), "moments");
+    }
+    return stream_after(c->stream, st);
+}
+
 int shd_get_sums(shd_ctx *c, double *energy, double *photons, double *resid)
 {
     int rc = ctx_check(c);

@@ -65,6 +65,7 @@ _SIGS = {
     "shd_launch_count": (ctypes.c_ulonglong, []),
     "shd_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "shd_batch_step": (_i, [_vp, _i, _vp]),
+    "shd_get_moments_dev": (_i, [_vp, _vp, _vp]),
     "shd_batch_set_sweep_mode": (_i, [_vp, _i]),
     "shd_batch_destroy": (None, [_vp]),
     "shd_check_bounded_wait": (_i, [_vp, _ll]),
@@ -286,6 +287,16 @@ class Solver:
         _check(self._L.shd_get_moments(self._h, _ptr(J), _ptr(H), _ptr(K), _ptr(Ish)))
         del nCG
         return (J, H, K, Ish) if with_sh else (J, H, K)
+
+    def moments_dev(self, mom, stream=None):
+        """J, H, K of the current state into the CUDA tensor ``mom`` (float64,
+        [Nc][G][10] contiguous, on this solver's device): J, H_x, H_y, H_z,
+        K_xx, K_yy, K_zz, K_xy, K_xz, K_yz, as moments() returns them."""
+        import torch
+        if (mom.dtype != torch.float64 or not mom.is_cuda or not mom.is_contiguous()
+                or mom.numel() != self.Nc * self.G * 10):
+            raise ValueError("mom must be a contiguous float64 CUDA tensor of Nc*G*10 elements")
+        _check(self._L.shd_get_moments_dev(self._h, mom.data_ptr(), stream))
 
     def sums(self):
         e, p, r = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
