@@ -637,6 +637,9 @@ def bench_single(args, dev, *, spec, prec, workload, extra, errors_spec, cpu_spe
     s = native.Solver.from_spec(spec, device=dev.index, precision=prec, scattering=scattering)
     if args.source_path != "auto":
         s.set_source_path(args.source_path)
+    if args.sweep_schedule:
+        sc, snt = (int(v) for v in args.sweep_schedule.split(","))
+        s.set_sweep_schedule(sc, snt)
     s.zero_state()
     ms, stage, clk, launches = time_steps(s, spec, args.steps, args.warmup, stream, dev, lambda: None)
     sched = _sched(s)
@@ -708,14 +711,16 @@ def bench_config3(args, dev):
     from paper_1507_05141_gb300 import inputs
     free, _ = torch.cuda.mem_get_info(dev)
     n = args.grid or 96
-    spec, G = _fit_groups(lambda g: inputs.compton_shell(n=n, G=g), 32, free)
-    note = None if G == 32 else f"G reduced from 32 to {G} to fit the device memory (stated deviation)"
+    L = args.order or 7
+    spec, G = _fit_groups(lambda g: inputs.compton_shell(n=n, G=g, L=L), args.groups or 32, free)
+    note = None if G == 32 else (f"G = {G} by --groups (a profiling case, not the workload)" if args.groups
+                                 else f"G reduced from 32 to {G} to fit the device memory (stated deviation)")
     kind = "kn_thermal" if args.thermal else "kn"
     what = ("Compton scattering off thermal electrons at the recipe's temperature field" if args.thermal
             else "cold Klein-Nishina")
     return bench_single(args, dev, spec=spec, prec="mixed",
-                        workload=f"Compton shell {n}^3, {G} groups (1e-4..1e2 m_e c^2), L=7, 16x32 ordinates, "
-                                 f"{what}, shell flow Gamma 2..5",
+                        workload=f"Compton shell {n}^3, {G} groups (1e-4..1e2 m_e c^2), L={L}, "
+                                 f"{spec.nmu}x{spec.nphi} ordinates, {what}, shell flow Gamma 2..5",
                         extra={"config": 3, "scattering": kind,
                                "l2": "no flush: the intensity state is far larger than L2"},
                         errors_spec=inputs.compton_shell(n=16, G=8),
@@ -873,6 +878,10 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="workload: 2 = the relativistic jet (the benchmark); 1 static FP64 box, 3 Compton shell, "
                          "4 batch of independent problems, 5 jet in a cocoon")
+    ap.add_argument("--groups", type=int, default=None,
+                    help="config 3: groups (default 32; fewer for small profiling captures)")
+    ap.add_argument("--order", type=int, default=None,
+                    help="config 3: angular order L (default 7; lower for small profiling captures)")
     ap.add_argument("--grid", type=int, default=None,
                     help="nodes per axis (defaults: 64 for the jet, 96 for config 3, 128 for config 5; smaller "
                          "for profiling)")

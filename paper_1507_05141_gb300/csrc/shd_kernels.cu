@@ -1046,10 +1046,29 @@ __global__ void __launch_bounds__(NT, NT == 384 ? 3 : 1024 / NT) k_sweep_cl(Prob
         asm volatile("cp.async.commit_group;\n" ::);
     };
 
+    // The cluster barrier is split: a thread arrives (release: its writes of
+    // the plane buffer and its landed copies) and then stores the previous
+    // plane's intensities to global memory before it waits, so that a release
+    // never waits for that plane's global stores; the next arrival covers
+    // them a plane later.
+    float inew_u[U];
+    long long pb_prev = -1;
+    auto store_prev = [&]() {
+        if (pb_prev < 0) return;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = tid + NT * u;
+            if (j >= nloc) break;
+            I[pb_prev + j] = inew_u[u];
+        }
+    };
     issue(0);
     for (int step = 0; step < nd; ++step) {
         asm volatile("cp.async.wait_group 0;\n" ::);
-        cl.sync();  // this plane's copies and the cluster's previous-plane state are visible
+        // this plane's copies and the cluster's previous-plane state are visible after the wait
+        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+        store_prev();
+        asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
         issue(step + 1);
         const float *rg = ring + (size_t)(step & 1) * 3 * pstride;
         const size_t pprev = (size_t)((step + 1) & 1) * pstride;
@@ -1059,6 +1078,7 @@ __global__ void __launch_bounds__(NT, NT == 384 ? 3 : 1024 / NT) k_sweep_cl(Prob
         const bool first = step == 0;
         const int id = o.sd > 0 ? step : nd - 1 - step;
         const long long pb = base + (long long)id * plane + j0;
+        pb_prev = pb;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = tid + NT * u;
@@ -1090,11 +1110,13 @@ __global__ void __launch_bounds__(NT, NT == 384 ? 3 : 1024 / NT) k_sweep_cl(Prob
                 inew = iu * ew + st * wp + su * wu;
             }
             Qn[j] = make_float4(inew, st, ct, 0.f);
-            I[pb + j] = inew;
+            inew_u[u] = inew;
         }
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
-    cl.sync();  // the peers' reads of this CTA's buffers are done
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    store_prev();  // the last plane
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");  // the peers' reads of this CTA's buffers are done
 }
 
 // -------------------------------------------------------------------------
