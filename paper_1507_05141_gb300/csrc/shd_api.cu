@@ -2110,6 +2110,7 @@ int shd_stage_sweep(shd_ctx *c, const double *I_old, const double *eta_lab, cons
     if (rc) return rc;
     if ((rc = ready_for_step(c))) return rc;
     if (!I_old || !eta_lab || !chi_lab || !I_new) return fail(SHD_ERR_ARG, "null array");
+    c->chi_rest_state = 2;  // chi_lab becomes the caller's: the next step fills chi0 at rest again
     if (is_fp64(c)) {
         if ((rc = set_state_impl<double>(c, eta_lab, true, c->stream, (double *)c->d_eta))) return rc;
         if ((rc = set_state_impl<double>(c, chi_lab, true, c->stream, (double *)c->d_chi))) return rc;
